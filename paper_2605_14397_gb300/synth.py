@@ -1,0 +1,191 @@
+"""Seeded synthetic inputs: fault meshes, right-hand sides and interface stiffness draws.
+
+This module is the only code shared by the CUDA path, the CPU oracle, the tests and
+the benchmark.  It lays out planar grids of rectangular constant-displacement-
+discontinuity elements and draws seeded random numbers; it holds none of the method's
+arithmetic (no influence coefficients, no tree, no compression, no solver).
+
+Element description (one row per element, user order):
+  c   (N,3) centroid (collocation point, Sec. 3.1)
+  s1  (N,3), s2 (N,3), n (N,3)  local orthonormal frame (Sec. 2.2; the DOF order of
+      every element is (s1, s2, n), Sec. 3.1)
+  a   (N,)  half side along s1,  b (N,) half side along s2
+
+Local in-plane axes of a plane with unit normal n: s1 = normalize(e3 x n), falling back
+to s1 = e1 when n is parallel to e3, and s2 = n x s1.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Elements:
+    c: np.ndarray
+    s1: np.ndarray
+    s2: np.ndarray
+    n: np.ndarray
+    a: np.ndarray
+    b: np.ndarray
+    # plane id of every element (which fault / fracture it belongs to)
+    plane: np.ndarray
+
+    @property
+    def N(self) -> int:
+        return int(self.c.shape[0])
+
+    def subset(self, idx) -> "Elements":
+        idx = np.asarray(idx)
+        return Elements(*(np.ascontiguousarray(getattr(self, f.name)[idx])
+                          for f in dataclasses.fields(self)))
+
+    @staticmethod
+    def concat(parts) -> "Elements":
+        return Elements(*(np.ascontiguousarray(np.concatenate([getattr(p, f.name) for p in parts]))
+                          for f in dataclasses.fields(Elements)))
+
+
+def plane_axes(n):
+    """Local in-plane axes (s1, s2) of a plane with unit normal n."""
+    n = np.asarray(n, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    s1 = np.cross([0.0, 0.0, 1.0], n)
+    if np.linalg.norm(s1) < 1e-12:
+        s1 = np.array([1.0, 0.0, 0.0])
+    s1 = s1 / np.linalg.norm(s1)
+    s2 = np.cross(n, s1)
+    return s1, s2, n
+
+
+def plane_grid(n_cells1, n_cells2, lo1, hi1, lo2, hi2, normal, origin=(0.0, 0.0, 0.0),
+               keep=None, plane_id=0) -> Elements:
+    """Uniform grid of rectangles on a plane: cell centres at lo + (i + 1/2) h in the
+    local (s1, s2) coordinates, mapped to 3D as origin + x1 s1 + x2 s2.
+    `keep(x1, x2)` optionally selects cells by their local centre coordinates."""
+    s1, s2, n = plane_axes(normal)
+    h1 = (hi1 - lo1) / n_cells1
+    h2 = (hi2 - lo2) / n_cells2
+    x1 = lo1 + (np.arange(n_cells1) + 0.5) * h1
+    x2 = lo2 + (np.arange(n_cells2) + 0.5) * h2
+    X1, X2 = np.meshgrid(x1, x2, indexing="xy")  # row-major over (x2, x1)
+    X1 = X1.ravel()
+    X2 = X2.ravel()
+    if keep is not None:
+        m = keep(X1, X2)
+        X1 = X1[m]
+        X2 = X2[m]
+    N = X1.size
+    o = np.asarray(origin, dtype=np.float64)
+    c = o[None, :] + X1[:, None] * s1[None, :] + X2[:, None] * s2[None, :]
+    rep = lambda v: np.ascontiguousarray(np.broadcast_to(v, (N, 3)))
+    return Elements(c=np.ascontiguousarray(c), s1=rep(s1), s2=rep(s2), n=rep(n),
+                    a=np.full(N, 0.5 * h1), b=np.full(N, 0.5 * h2),
+                    plane=np.full(N, plane_id, dtype=np.int32))
+
+
+def disk_mesh(n_grid, radius=1.0, normal=(0.0, 0.0, 1.0), origin=(0.0, 0.0, 0.0), plane_id=0):
+    """n_grid x n_grid square grid on [-R, R]^2 keeping the cells whose centre has r < R."""
+    R = float(radius)
+    return plane_grid(n_grid, n_grid, -R, R, -R, R, normal, origin,
+                      keep=lambda x1, x2: x1 * x1 + x2 * x2 < R * R, plane_id=plane_id)
+
+
+# ---------------------------------------------------------------------------------------
+# The five workloads.  Sizes and recipes follow the hot-path configurations: a single
+# penny crack (dense check against Sneddon), a single H-matrix fault, three intersecting
+# fractures, 64 uneven independent faults, and a height-confined crack across a fault.
+# ---------------------------------------------------------------------------------------
+
+def config_penny(n_grid=40):
+    """Planar crack z = 0: n x n grid on [-1,1]^2, centroids with r < 1 (n=40: N=1264)."""
+    return disk_mesh(n_grid)
+
+
+def config_fault(n_grid=256):
+    """Single disk fault r < 1 on a 256 x 256 grid (N = 51,468)."""
+    return disk_mesh(n_grid)
+
+
+def config_three_planes(n_grid=300, shift_third=True):
+    """Three square fractures of side 2 through the origin with normals e3, e1 and
+    (1,1,0)/sqrt(2), each on an n x n grid.  The third grid is shifted by h/4 along its
+    s2 axis so that no collocation point of the first plane lies on one of its edges."""
+    h = 2.0 / n_grid
+    p1 = plane_grid(n_grid, n_grid, -1, 1, -1, 1, (0, 0, 1), plane_id=0)
+    p2 = plane_grid(n_grid, n_grid, -1, 1, -1, 1, (1, 0, 0), plane_id=1)
+    off = 0.25 * h if shift_third else 0.0
+    p3 = plane_grid(n_grid, n_grid, -1, 1, -1 + off, 1 + off,
+                    (1 / math.sqrt(2), 1 / math.sqrt(2), 0), plane_id=2)
+    return Elements.concat([p1, p2, p3])
+
+
+def config_crack_fault(h=0.01, crack=(4.0, 1.0), fault=(4.0, 4.0)):
+    """Height-confined vertical crack in the plane y = 0 (x in [-2,2], z in [-1/2,1/2],
+    normal e2) crossing a vertical fault in the plane x = 0 (y, z in [-2,2], normal e1)."""
+    Lx, Hz = crack
+    Ly, Lz = fault
+    nx, nz = int(round(Lx / h)), int(round(Hz / h))
+    ny, nz2 = int(round(Ly / h)), int(round(Lz / h))
+    # crack: its local axes are s1 = e3 x e2 = -e1, s2 = e3; lay the grid in x, z
+    ck = plane_grid(nx, nz, -Lx / 2, Lx / 2, -Hz / 2, Hz / 2, (0, 1, 0), plane_id=0)
+    ft = plane_grid(ny, nz2, -Ly / 2, Ly / 2, -Lz / 2, Lz / 2, (1, 0, 0), plane_id=1)
+    return Elements.concat([ck, ft])
+
+
+def config_faults_batch(n_faults=64, seed=1604, h=2.0 / 256, n_min=2000, n_max=40000):
+    """64 independent disk faults: element counts log-uniform in [2k, 40k] at a fixed
+    spacing h, radius R_f = h sqrt(N_f / pi), seeded uniform random normals and
+    Poisson ratios nu_f ~ U[0.2, 0.3].  Returns (list of Elements, nu array)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    faults, nus = [], []
+    for f in range(n_faults):
+        nf = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        R = h * math.sqrt(nf / math.pi)
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        nus.append(rng.uniform(0.2, 0.3))
+        ng = 2 * int(math.ceil(R / h))
+        el = plane_grid(ng, ng, -ng * h / 2, ng * h / 2, -ng * h / 2, ng * h / 2, v,
+                        keep=lambda x1, x2, R=R: x1 * x1 + x2 * x2 < R * R, plane_id=f)
+        faults.append(el)
+    return faults, np.array(nus)
+
+
+# ------------------------------------------------------------------ right-hand sides
+
+def rhs_uniform_pressure(el: Elements, p=1.0):
+    """Uniform internal pressure p: traction b_n = -p, b_s = 0 (DOF order s1, s2, n)."""
+    b = np.zeros((el.N, 3))
+    b[:, 2] = -p
+    return b.ravel()
+
+
+def rhs_shear_plus_bump(el: Elements, sigma=0.2):
+    """Uniform unit shear along s1 plus a Gaussian pressure bump of unit amplitude:
+    b_s1 = 1, b_s2 = 0, b_n = -exp(-r^2 / (2 sigma^2)), r the distance to the origin."""
+    r2 = np.sum(el.c * el.c, axis=1)
+    b = np.zeros((el.N, 3))
+    b[:, 0] = 1.0
+    b[:, 2] = -np.exp(-r2 / (2.0 * sigma * sigma))
+    return b.ravel()
+
+
+def rhs_normal(n_dof, seed, nrhs=1):
+    """Seeded N(0,1) tractions, shape (n_dof,) or (nrhs, n_dof)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.normal(size=(nrhs, n_dof))
+    return x[0] if nrhs == 1 else x
+
+
+def k_loguniform(N, seed, E=1.0, h=0.01, lo=1e-3, hi=1e2):
+    """Interface stiffness per element, log-uniform in [lo, hi] * E / h."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), size=N)) * (E / h)
+
+
+def random_vector(n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.normal(size=n)

@@ -1,0 +1,170 @@
+/*
+ * hmat.h -- C ABI of the GB300 H-matrix displacement-discontinuity BEM hot path.
+ *
+ * The library evaluates the 3D full-space influence coefficients of constant-DD
+ * rectangles (Sec. 3.1, eq. TractionBIE-general reduced to the fracture integral,
+ * eq. ElasSystem), compresses the far field of the collocation matrix E into an
+ * H-matrix (Sec. 3.1: near-field blocks kept dense, far-field blocks low rank), applies
+ * it (the O(n log n) product of Sec. 3.1) and solves the elastic tangent system
+ * A = E - diag(k) - shift I (eq. jac_mech with C^ep = diag(k) and eta/dt = shift) by
+ * restarted GMRES with a leaf block-Jacobi preconditioner (Sec. 3.3.1).
+ *
+ * Conventions shared by every entry point:
+ *   - DOF order is element-major with (s1, s2, n) per element, in the user's element
+ *     order (Sec. 3.1); tractions are ordered the same way.
+ *   - Sign: delta = u+ - u- (Sec. 2.2) and T - T0 = E delta (eq. ElasSystem); the
+ *     diagonal of E is negative.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller and not
+ *     retained after the call returns; every other pointer is host memory, also
+ *     caller-owned and copied if needed.  Handles (hm_tree, hm_hmat, hm_batch,
+ *     hm_lp) are owned by the library and freed by their destroy function.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.
+ *   - Every function returns an hm_status; 0 is success, a negative value an error
+ *     whose text hm_last_error() returns (per calling thread).  Nothing throws.
+ */
+#ifndef HMAT_H
+#define HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hm_status;
+#define HM_OK 0
+#define HM_EINVAL (-1)          /* bad argument */
+#define HM_ENOMEM (-2)          /* device or host allocation failed */
+#define HM_ECUDA (-3)           /* a CUDA call failed */
+#define HM_ESINGULAR_GEOM (-4)  /* a collocation point lies on a source element's edge */
+#define HM_ENOCONV (-5)         /* iteration limit reached before the tolerance */
+#define HM_EBREAKDOWN (-6)      /* Krylov breakdown or ACA rank cap exceeded */
+#define HM_ENAN (-7)            /* NaN or Inf met in the data */
+#define HM_ETIMEOUT (-8)        /* a bounded device wait gave up */
+
+/* Precision / dtype codes. */
+#define HM_F32 1
+#define HM_F64 2
+#define HM_BF16 3
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* hm_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int hm_version(void);
+
+/* Element geometry, host SoA (Sec. 2.2 frame, Sec. 3.1 collocation at centroids):
+ * c, s1, s2, n are N x 3 row-major (centroid and the orthonormal frame), a and b are
+ * the half sides along s1 and s2.  The caller keeps ownership; the library copies. */
+typedef struct {
+    int64_t N;
+    const double* c;
+    const double* s1;
+    const double* s2;
+    const double* n;
+    const double* a;
+    const double* b;
+} hm_elements;
+
+/* ---------------------------------------------------------------- influence blocks
+ * 3x3 influence blocks for a list of (receiver i, source j) element pairs (Sec. 3.1,
+ * eq. ElasSystem): out_dev[9p + 3 alpha + m] is the traction component alpha (frame of
+ * receiver ri_dev[p]) at its centroid due to a unit DD component m (frame of source
+ * sj_dev[p]) constant over the source rectangle.  Evaluated in FP64 on the device.
+ * ri_dev, sj_dev: npairs int64 element indices; out_dev: 9 npairs doubles.
+ * Returns HM_ESINGULAR_GEOM (after writing every other block) if a receiver lies on a
+ * source edge; those blocks are NaN.  Synchronises the stream. */
+hm_status hm_influence_blocks(const hm_elements* el, double E, double nu, int64_t npairs,
+                              const int64_t* ri_dev, const int64_t* sj_dev, double* out_dev,
+                              void* stream);
+
+/* ---------------------------------------------------------------- cluster tree
+ * Binary cluster tree over element centroids and the block partition (Sec. 3.1 relies
+ * on an H-matrix; the rules are: split a cluster of more than leaf_size elements at the
+ * median of its longest centroid-box axis (the first n/2 in (coordinate, index) order go
+ * left); a pair (s, t) is admissible (low rank) iff min(diam B_s, diam B_t) <= eta
+ * dist(B_s, B_t) > 0 on element-vertex boxes; non-admissible leaf pairs are dense).
+ * Built on the host; the handle is independent of the element arrays afterwards. */
+typedef struct hm_tree hm_tree;
+
+typedef struct {
+    int64_t n_elements;
+    int64_t n_nodes;
+    int64_t n_leaves;
+    int64_t n_near;  /* dense (near-field) leaf x leaf blocks */
+    int64_t n_far;   /* admissible (low-rank) blocks */
+    int32_t leaf_size;
+    int32_t depth;
+    double eta;
+} hm_tree_info;
+
+hm_status hm_build_cluster_tree(const hm_elements* el, int leaf_size, double eta, hm_tree** out);
+hm_status hm_tree_get_info(const hm_tree* t, hm_tree_info* info);
+/* Copy the tree to host arrays (any may be NULL): perm[n_elements] (user index of the
+ * element at cluster position k), node begin/end/left/right [n_nodes] (left = -1 for a
+ * leaf), near[2 n_near] and far[2 n_far] as (row node, column node) pairs. */
+hm_status hm_tree_export(const hm_tree* t, int64_t* perm, int64_t* begin, int64_t* end,
+                         int64_t* left, int64_t* right, int64_t* near, int64_t* far);
+void hm_tree_destroy(hm_tree* t);
+
+/* ---------------------------------------------------------------- H-matrix assembly
+ * Assemble the H-matrix of E on the device: dense near-field tiles in FP32 (FP64
+ * evaluation), admissible blocks compressed by adaptive cross approximation with
+ * element (3-row) pivots to relative Frobenius accuracy aca_eps per block, factors
+ * stored in `storage` (HM_F32 or HM_BF16).  max_rank caps the ACA rank (0 = 96).
+ * Synchronises the stream (the packed layout depends on the ranks). */
+typedef struct {
+    double E;
+    double nu;
+    double aca_eps;
+    int storage;
+    int max_rank;
+} hm_assemble_opts;
+
+typedef struct hm_hmat hm_hmat;
+
+typedef struct {
+    int64_t n_dof;            /* 3 N */
+    int64_t near_entries;     /* stored dense entries (unpadded) */
+    int64_t far_entries;      /* stored factor entries sum 3 r (|s| + |t|) (unpadded) */
+    int64_t stored_bytes;     /* bytes of all stored coefficients, padding included */
+    int64_t algorithmic_bytes;/* 4 near_entries + factor bytes + x/y traffic, one RHS */
+    int32_t rank_min, rank_max;
+    double rank_mean;
+    double assemble_seconds;
+    int32_t storage;
+    int32_t pad_;
+    int64_t n_far_lowrank;    /* admissible blocks stored as factors */
+    int64_t n_far_dense;      /* admissible blocks whose factors would exceed the dense block */
+} hm_hmat_info;
+
+hm_status hm_assemble_hmat(const hm_tree* t, const hm_elements* el, const hm_assemble_opts* opt,
+                           void* stream, hm_hmat** out);
+hm_status hm_hmat_get_info(const hm_hmat* h, hm_hmat_info* info);
+/* Low-rank factors of far block b (0 <= b < n_far) to host, FP64, column-major:
+ * U[3|s| x r], V[3|t| x r] with block = U V^T in cluster order of the two clusters.
+ * rank_out receives r, or -1 for a block stored dense (U, V untouched); pass
+ * U = V = NULL to query the rank only. */
+hm_status hm_hmat_far_factors(const hm_hmat* h, int64_t b, int32_t* rank_out, double* U, double* V);
+void hm_hmat_destroy(hm_hmat* h);
+
+/* ---------------------------------------------------------------- H-matrix product
+ * y = E x for nrhs right-hand sides (the product of Sec. 3.1 on the stored H-matrix).
+ * x_dev, y_dev: nrhs x 3N, RHS-major (x_dev[k * 3N + dof]), user element order.
+ * dtype HM_F32: float vectors, FP32 accumulation.  dtype HM_F64: double vectors; the
+ * FP32/BF16 stored coefficients are applied with compensated float-float accumulation,
+ * so the result is the product of the stored operator to about 1e-13 relative.
+ * x_dev and y_dev must not overlap.  Asynchronous. */
+hm_status hm_matvec(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, int dtype,
+                    void* stream);
+
+/* Synchronise `stream` and report whether a device-side wait of an earlier product on
+ * this H-matrix gave up (HM_ETIMEOUT; the flags are then cleared).  The product kernels
+ * bound every wait on their copy pipeline instead of spinning forever. */
+hm_status hm_hmat_check(const hm_hmat* h, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMAT_H */

@@ -1,0 +1,182 @@
+// extern "C" boundary of libhmat: argument checks, handle ownership, status codes.
+#include <cstring>
+#include <string>
+
+#include "hmat_impl.h"
+#include "tree.h"
+
+struct hm_tree {
+    hm::Tree t;
+};
+struct hm_hmat {
+    hm::HMat h;
+};
+
+namespace hm {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void influence_pairs(const hm_elements& e, double E, double nu, int64_t npairs, const int64_t* ri,
+                     const int64_t* sj, double* out, cudaStream_t st);
+
+static void check_elements(const hm_elements* el) {
+    if (!el) fail(HM_EINVAL, "NULL element description");
+    if (el->N <= 0) fail(HM_EINVAL, "element count must be positive");
+    if (!el->c || !el->s1 || !el->s2 || !el->n || !el->a || !el->b) fail(HM_EINVAL, "NULL geometry array");
+}
+
+}  // namespace hm
+
+extern "C" {
+
+const char* hm_last_error(void) { return hm::g_last_error.c_str(); }
+
+int hm_version(void) { return 100; }
+
+hm_status hm_influence_blocks(const hm_elements* el, double E, double nu, int64_t npairs, const int64_t* ri_dev,
+                              const int64_t* sj_dev, double* out_dev, void* stream) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    hm::check_elements(el);
+    hm::influence_pairs(*el, E, nu, npairs, ri_dev, sj_dev, out_dev, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_build_cluster_tree(const hm_elements* el, int leaf_size, double eta, hm_tree** out) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    if (!out) hm::fail(HM_EINVAL, "build_cluster_tree: NULL output handle");
+    *out = nullptr;
+    hm::check_elements(el);
+    hm_tree* t = new hm_tree();
+    try {
+        hm::build_tree(*el, leaf_size, eta, t->t);
+    } catch (...) {
+        delete t;
+        throw;
+    }
+    *out = t;
+    HM_API_END
+}
+
+hm_status hm_tree_get_info(const hm_tree* t, hm_tree_info* info) {
+    HM_API_BEGIN
+    if (!t || !info) hm::fail(HM_EINVAL, "tree_get_info: NULL argument");
+    info->n_elements = t->t.N;
+    info->n_nodes = (int64_t)t->t.begin.size();
+    info->n_leaves = (int64_t)t->t.leaves.size();
+    info->n_near = (int64_t)t->t.near.size();
+    info->n_far = (int64_t)t->t.far.size();
+    info->leaf_size = t->t.leaf_size;
+    info->depth = t->t.depth;
+    info->eta = t->t.eta;
+    HM_API_END
+}
+
+hm_status hm_tree_export(const hm_tree* t, int64_t* perm, int64_t* begin, int64_t* end, int64_t* left,
+                         int64_t* right, int64_t* near, int64_t* far) {
+    HM_API_BEGIN
+    if (!t) hm::fail(HM_EINVAL, "tree_export: NULL tree");
+    const hm::Tree& T = t->t;
+    if (perm) std::memcpy(perm, T.perm.data(), T.perm.size() * sizeof(int64_t));
+    if (begin) std::memcpy(begin, T.begin.data(), T.begin.size() * sizeof(int64_t));
+    if (end) std::memcpy(end, T.end.data(), T.end.size() * sizeof(int64_t));
+    if (left) std::memcpy(left, T.left.data(), T.left.size() * sizeof(int64_t));
+    if (right) std::memcpy(right, T.right.data(), T.right.size() * sizeof(int64_t));
+    if (near)
+        for (size_t b = 0; b < T.near.size(); ++b) { near[2 * b] = T.near[b][0]; near[2 * b + 1] = T.near[b][1]; }
+    if (far)
+        for (size_t b = 0; b < T.far.size(); ++b) { far[2 * b] = T.far[b][0]; far[2 * b + 1] = T.far[b][1]; }
+    HM_API_END
+}
+
+void hm_tree_destroy(hm_tree* t) { delete t; }
+
+hm_status hm_assemble_hmat(const hm_tree* t, const hm_elements* el, const hm_assemble_opts* opt, void* stream,
+                           hm_hmat** out) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    if (!out) hm::fail(HM_EINVAL, "assemble_hmat: NULL output handle");
+    *out = nullptr;
+    if (!t || !opt) hm::fail(HM_EINVAL, "assemble_hmat: NULL tree or options");
+    if (el) {
+        hm::check_elements(el);
+        if (el->N != t->t.N) hm::fail(HM_EINVAL, "assemble_hmat: element count differs from the tree's");
+    }
+    hm_hmat* h = new hm_hmat();
+    try {
+        hm::assemble(t->t, *opt, (cudaStream_t)stream, h->h);
+    } catch (...) {
+        delete h;
+        throw;
+    }
+    *out = h;
+    HM_API_END
+}
+
+hm_status hm_hmat_get_info(const hm_hmat* hh, hm_hmat_info* info) {
+    HM_API_BEGIN
+    if (!hh || !info) hm::fail(HM_EINVAL, "hmat_get_info: NULL argument");
+    const hm::HMat& H = hh->h;
+    info->n_dof = H.ndof;
+    info->near_entries = H.near_entries;
+    info->far_entries = H.far_entries;
+    info->stored_bytes = H.stored_bytes();
+    const int64_t fb = H.storage == HM_BF16 ? 2 : 4;
+    info->algorithmic_bytes = 4 * H.near_entries + fb * H.far_entries + 2 * 4 * H.ndof;
+    info->rank_min = H.rank_min;
+    info->rank_max = H.rank_max;
+    info->rank_mean = H.rank_mean;
+    info->assemble_seconds = H.assemble_seconds;
+    info->storage = H.storage;
+    info->pad_ = 0;
+    info->n_far_dense = H.n_dense_far;
+    info->n_far_lowrank = H.n_far - H.n_dense_far;
+    HM_API_END
+}
+
+hm_status hm_hmat_far_factors(const hm_hmat* hh, int64_t b, int32_t* rank_out, double* U, double* V) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "hmat_far_factors: NULL H-matrix");
+    const hm::HMat& H = hh->h;
+    if (b < 0 || b >= H.n_far) hm::fail(HM_EINVAL, "hmat_far_factors: block index out of range");
+    const hm::FarDesc& F = H.h_far[b];
+    if (rank_out) *rank_out = F.dense ? -1 : F.rank;
+    if ((U || V) && !F.dense) {
+        const int64_t nu = 3LL * F.s_n * F.rank, nv = 3LL * F.t_n * F.rank;
+        std::vector<float> buf(nu + nv);
+        if (nu + nv > 0)
+            HM_CUDA(cudaMemcpy(buf.data(), H.facstore.p + F.fac_off, (nu + nv) * sizeof(float), cudaMemcpyDeviceToHost));
+        if (U)
+            for (int64_t q = 0; q < nu; ++q) U[q] = buf[q];
+        if (V)
+            for (int64_t q = 0; q < nv; ++q) V[q] = buf[nu + q];
+    }
+    HM_API_END
+}
+
+void hm_hmat_destroy(hm_hmat* h) { delete h; }
+
+hm_status hm_matvec(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs, int dtype, void* stream) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "matvec: NULL H-matrix");
+    if (x_dev == y_dev) hm::fail(HM_EINVAL, "matvec: x and y must not overlap");
+    hm::matvec(const_cast<hm::HMat&>(hh->h), x_dev, y_dev, nrhs, dtype, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_hmat_check(const hm_hmat* hh, void* stream) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "hmat_check: NULL H-matrix");
+    const int e = hm::product_error_flags(const_cast<hm::HMat&>(hh->h), (cudaStream_t)stream);
+    if (e) {
+        char buf[128];
+        snprintf(buf, sizeof(buf), "hmat_check: a product kernel gave up waiting (flags 0x%x)", e);
+        hm::fail(HM_ETIMEOUT, buf);
+    }
+    HM_API_END
+}
+
+}  // extern "C"

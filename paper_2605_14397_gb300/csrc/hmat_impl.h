@@ -1,0 +1,125 @@
+// Device-resident H-matrix: storage layout and work lists.
+//
+// Layout (all coefficient streams are "leaf-major": everything one leaf cluster of the
+// row or column side consumes is one contiguous, column-major block, so a product
+// streams each byte once, in order):
+//   near stream   for leaf s: [ D_st for t in near(s) ]        ld_s x (sum 3|t|) FP32
+//   U stream      for leaf s: [ U_b[s] for b in far, s in S_b ] ld_s x (sum r_b)   FP32|BF16
+//   V stream      for leaf t: [ V_b[t] for b in far, t in T_b ] ld_t x (sum r_b)   FP32|BF16
+// where ld = 3|leaf| rounded up to 8 entries (16 bytes for BF16, 32 for FP32) and the
+// rows of a slice are the leaf's DOFs in cluster order.
+//
+// The product y = E x runs as
+//   gather     xc = x[perm]                       (cluster order)
+//   phase 1    P[pidx[c]] = V_t[:, c] . xc_t       per leaf t (column c of its V block)
+//   reduce     tb_b = sum over the leaves t of T_b of the partials of b
+//   phase 2    yc_s = [D_s | U_s] z_s,  z = [xc | tb] gathered by zidx
+//   scatter    y[perm] = yc
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "common.h"
+#include "tree.h"
+
+namespace hm {
+
+struct LeafDesc {
+    int32_t begin;     // first cluster position
+    int32_t n;         // elements
+    int32_t ld;        // padded rows (3 n rounded up to 8)
+    int32_t pad_;
+    int64_t near_off;  // entry offset into the near stream
+    int64_t u_off;     // entry offset into the U stream
+    int64_t v_off;     // entry offset into the V stream
+    int32_t near_cols, u_cols, v_cols;
+    int32_t near_cbase, u_cbase, v_cbase;  // first index into zidx / pidx arrays
+    int32_t pad2_;
+};
+
+struct FarDesc {
+    int32_t s_begin, s_n, t_begin, t_n;  // clusters (positions, element counts)
+    int32_t rank;
+    int32_t n_tleaves;                   // leaves of T (partials per output)
+    int64_t pbase;                       // partial buffer base: P[pbase + k r + l]
+    int64_t tb_off;                      // output offset in tb
+    int64_t fac_off;                     // compact factor store offset (U then V)
+    int32_t dense;                       // 1: kept dense (its tiles live in the near stream)
+    int32_t pad_;
+};
+
+// One pipeline chunk: whole columns of one leaf's segment, at most one stage of bytes.
+struct Chunk {
+    int64_t src;    // first entry in its stream
+    int32_t leaf;   // leaf ordinal
+    int32_t cbase;  // first column's index into the zidx (phase 2) or pidx (phase 1) array
+    int32_t ncols;
+    int32_t kind;   // 0 near tile (FP32), 1 U factor, 2 V factor
+};
+
+// Row leaves whose phase-2 columns are split over several persistent CTAs.
+struct LeafSplit {
+    int32_t w_first;    // first CTA holding columns of the leaf
+    int32_t nparts;     // CTAs holding columns of the leaf (1 = not split)
+    int32_t slot_base;  // first partial slot
+    int32_t pad_;
+};
+
+struct HMat {
+    int64_t N = 0, ndof = 0;
+    double E = 1.0, nu = 0.25, eps = 1e-6;
+    int storage = HM_F32;
+    int n_leaves = 0;
+    int64_t n_far = 0, n_near = 0, n_dense_far = 0;
+    int64_t tb_len = 0, p_len = 0;
+    int64_t near_entries = 0, far_entries = 0;
+    int rank_min = 0, rank_max = 0;
+    double rank_mean = 0.0, assemble_seconds = 0.0;
+
+    std::vector<LeafDesc> h_leaves;
+    std::vector<FarDesc> h_far;
+    std::vector<int64_t> h_perm;
+
+    DevBuf<ElemRec> elems;        // cluster order
+    DevBuf<int32_t> perm;         // cluster position -> user element
+    DevBuf<LeafDesc> leaves;
+    DevBuf<FarDesc> far;
+    DevBuf<float> near;           // near stream
+    DevBuf<float> u32, v32;       // factor streams (FP32 storage)
+    DevBuf<uint16_t> u16, v16;    // factor streams (BF16 storage)
+    DevBuf<float> facstore;       // compact FP32 factors per far block (U then V)
+    DevBuf<int32_t> near_zidx, u_zidx, v_pidx;
+
+    // persistent product plan
+    int grid = 0;
+    int ld_max = 0;
+    int n_slots = 0;
+    DevBuf<Chunk> ch1, ch2;
+    DevBuf<int32_t> cta1, cta2;
+    DevBuf<LeafSplit> split;
+    DevBuf<int32_t> counters;
+    DevBuf<int> err;
+    DevBuf<float> slotsf;
+    DevBuf<double> slotsd;
+
+    // product scratch, sized for nrhs_cap right-hand sides
+    int nrhs_cap = 0;
+    DevBuf<double> xc, yc;        // cluster-order vectors (F64 path) [nrhs][ndof]
+    DevBuf<float> xcf, ycf;       // (F32 path)
+    DevBuf<double> P, tb;         // partials / t vectors (F64 path uses hi+lo pairs as double)
+    DevBuf<float> Pf, tbf;
+
+    int64_t stored_bytes() const {
+        return (int64_t)near.bytes() + (int64_t)u32.bytes() + (int64_t)v32.bytes() + (int64_t)u16.bytes() +
+               (int64_t)v16.bytes();
+    }
+};
+
+void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat& H);
+void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t st);
+void build_product_plan(HMat& H, cudaStream_t st);
+int product_error_flags(HMat& H, cudaStream_t st);
+void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
+
+}  // namespace hm

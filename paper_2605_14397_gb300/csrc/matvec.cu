@@ -1,0 +1,626 @@
+// H-matrix product y = E x on the device (the product of Sec. 3.1 on the stored
+// H-matrix).
+//
+//   gather   xc = x[perm]                          cluster order
+//   phase 1  P[pidx[c]] = V_t[:, c] . xc_t         every V column (one per rank per leaf)
+//   reduce   tb_b = sum of the partials of block b over the leaves of its column cluster
+//   phase 2  yc_s = [D_s | U_s] z_s, z = xc (near columns) or tb (U columns)
+//   scatter  y[perm] = yc
+//
+// Phases 1 and 2 are persistent kernels, one CTA per SM.  Their coefficient streams are
+// cut into chunks of whole columns (at most 32 KB) and the chunk list is split into
+// equal byte ranges, one per CTA ("stream-K"): every SM streams the same number of
+// bytes.  One producer thread moves the chunks with cp.async.bulk (TMA) into a 4-stage
+// shared-memory ring guarded by mbarriers; 8 or 16 consumer warps each take columns of
+// the chunk, lanes over rows.  A row leaf whose columns fall into several CTAs is
+// finished by the last of them (atomic arrival count, partials summed in CTA order), so
+// the result is deterministic.
+//
+// Arithmetic modes over the same FP32/BF16 coefficient streams:
+//   F32: float vectors, FP32 accumulation;
+//   F64: double vectors; each coefficient a multiplies z = zh + zl (zh = fl32(z),
+//        zl = fl32(z - zh)) in the compensated dot product of Ogita, Rump and Oishi
+//        (2005): TwoProduct via fmaf, TwoSum of the running sum, rounding errors summed
+//        apart, the two parts combined in FP64 -- the stored operator applied to FP64
+//        vectors to about 1e-13 relative while the coefficients stream at 4 (or 2) bytes.
+#include <algorithm>
+
+#include "hmat_impl.h"
+#include "pipeline.cuh"
+
+namespace hm {
+
+namespace {
+
+constexpr int STAGES = 4;
+constexpr int STAGE_BYTES = 32768;
+constexpr int BAR_BYTES = 128;
+
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <int MODE>
+struct AccT;
+template <>
+struct AccT<0> {
+    using type = float;
+    using vec = float;
+};
+template <>
+struct AccT<1> {
+    using type = FF;
+    using vec = double;
+};
+
+// z operand: one float, or the (hi, lo) split of a double
+struct Z32 {
+    float h;
+};
+struct Z64 {
+    float h, l;
+};
+
+__device__ __forceinline__ Z32 make_z(float v) { return Z32{v}; }
+__device__ __forceinline__ Z64 make_z(double v) {
+    const float h = (float)v;
+    return Z64{h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ void acc_zero(float& a) { a = 0.f; }
+__device__ __forceinline__ void acc_zero(FF& a) { a.hi = 0.f; a.lo = 0.f; }
+
+__device__ __forceinline__ void acc_fma(float& acc, float a, Z32 z) { acc = fmaf(a, z.h, acc); }
+__device__ __forceinline__ void acc_fma(FF& acc, float a, Z64 z) {
+    const float p = a * z.h;
+    const float pe = fmaf(a, z.h, -p);
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo += e + pe + a * z.l;
+}
+
+__device__ __forceinline__ void acc_add(float& a, float b) { a += b; }
+__device__ __forceinline__ void acc_add(FF& a, const FF& b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    a.hi = s;
+    a.lo += e + b.lo;
+}
+
+__device__ __forceinline__ float acc_shfl(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ FF acc_shfl(const FF& v, int o) {
+    return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+__device__ __forceinline__ float acc_value(float a) { return a; }
+__device__ __forceinline__ double acc_value(const FF& a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ float coef(const float* p, int i) { return p[i]; }
+__device__ __forceinline__ float coef(const uint16_t* p, int i) { return __uint_as_float(((uint32_t)p[i]) << 16); }
+
+template <class V>
+__global__ void k_gather(const V* __restrict__ x, V* __restrict__ xc, const int32_t* __restrict__ perm, int64_t N,
+                         int nrhs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ndof = 3 * N;
+    if (q >= ndof * nrhs) return;
+    const int64_t k = q / ndof, r = q % ndof;
+    const int64_t p = r / 3, m = r % 3;
+    xc[q] = x[k * ndof + 3 * (int64_t)perm[p] + m];
+}
+
+template <class V>
+__global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int32_t* __restrict__ perm, int64_t N,
+                          int nrhs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ndof = 3 * N;
+    if (q >= ndof * nrhs) return;
+    const int64_t k = q / ndof, r = q % ndof;
+    const int64_t p = r / 3, m = r % 3;
+    y[k * ndof + 3 * (int64_t)perm[p] + m] = yc[q];
+}
+
+template <class V>
+__global__ void k_reduce_tb(const FarDesc* __restrict__ far, int64_t nfar, const V* __restrict__ P, V* __restrict__ tb,
+                            int64_t plen, int64_t tblen, int nrhs) {
+    const int64_t b = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nfar) return;
+    const FarDesc F = far[b];
+    for (int k = 0; k < nrhs; ++k)
+        for (int l = lane; l < F.rank; l += 32) {
+            V s = 0;
+            for (int q = 0; q < F.n_tleaves; ++q) s += P[k * plen + F.pbase + (int64_t)q * F.rank + l];
+            tb[k * tblen + F.tb_off + l] = s;
+        }
+}
+
+struct StreamArgs {
+    const Chunk* chunks;
+    const int32_t* cta_begin;
+    const LeafDesc* leaves;
+    const LeafSplit* split;
+    const float* near;
+    const void* ucoef;
+    const void* vcoef;
+    const int32_t* near_zidx;
+    const int32_t* u_zidx;
+    const int32_t* v_pidx;
+    const void* xc;
+    const void* tb;
+    void* out;    // yc (phase 2) or P (phase 1)
+    void* slots;  // phase-2 partials of split leaves
+    int32_t* counters;
+    int* err;
+    int64_t ndof, tblen, plen;
+    int nr;       // right-hand sides in this launch (<= NR)
+    int ld_max;
+};
+
+// ---- producer: one thread streams this CTA's chunks through the ring
+template <class C>
+__device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* stage, uint64_t* full, uint64_t* empty,
+                                        int c0, int c1) {
+    for (int i = c0; i < c1; ++i) {
+        const int q = i - c0, s = q % STAGES;
+        const uint32_t ph = (uint32_t)(q / STAGES) & 1u;
+        if (q >= STAGES) mbar_wait(empty + s, ph ^ 1u, a.err, 4);
+        const Chunk ch = a.chunks[i];
+        const LeafDesc& L = a.leaves[ch.leaf];
+        const void* src;
+        uint32_t bytes;
+        if (ch.kind == 0) {
+            src = a.near + ch.src;
+            bytes = (uint32_t)ch.ncols * L.ld * 4u;
+        } else {
+            const C* base = (const C*)(ch.kind == 1 ? a.ucoef : a.vcoef);
+            src = base + ch.src;
+            bytes = (uint32_t)ch.ncols * L.ld * (uint32_t)sizeof(C);
+        }
+        mbar_arrive_expect_tx(full + s, bytes);
+        bulk_g2s(stage + (size_t)s * STAGE_BYTES, src, bytes, full + s);
+    }
+    // make sure no copy is still in flight when the CTA exits
+    const int n = c1 - c0;
+    for (int q = std::max(0, n - STAGES); q < n; ++q)
+        mbar_wait(full + (q % STAGES), (uint32_t)(q / STAGES) & 1u, a.err, 8);
+}
+
+// ---- phase 2: y = [D | U] z per row leaf
+template <int MODE, class C, int NR, int RPL, int NCW>
+__global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
+    using Acc = typename AccT<MODE>::type;
+    using Vv = typename AccT<MODE>::vec;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = (uint64_t*)smem;
+    uint64_t* empty = full + STAGES;
+    int* s_flag = (int*)(empty + STAGES);
+    unsigned char* stage = smem + BAR_BYTES;
+    Acc* red = (Acc*)(stage + (size_t)STAGES * STAGE_BYTES);  // [NCW][32 RPL]
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, NCW);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
+    if (w == NCW) {
+        if (lane == 0) produce<C>(a, stage, full, empty, c0, c1);
+        return;
+    }
+    const Vv* xc = (const Vv*)a.xc;
+    const Vv* tb = (const Vv*)a.tb;
+    Vv* yc = (Vv*)a.out;
+    Vv* slots = (Vv*)a.slots;
+    Acc acc[NR][RPL];
+    int cur = -1;
+    LeafDesc L{};
+
+    auto flush = [&]() {
+        const LeafSplit sp = a.split[cur];
+        const int rows = 3 * L.n;
+        const bool whole = sp.nparts == 1;
+        const int64_t slot = whole ? 0 : (int64_t)(sp.slot_base + (int)blockIdx.x - sp.w_first);
+        for (int k = 0; k < a.nr; ++k) {
+#pragma unroll
+            for (int i = 0; i < RPL; ++i) red[(size_t)w * (32 * RPL) + lane + 32 * i] = acc[k][i];
+            consumer_sync(NCW * 32);
+            for (int r = threadIdx.x; r < rows; r += NCW * 32) {
+                Acc s = red[r];
+                for (int q = 1; q < NCW; ++q) acc_add(s, red[(size_t)q * (32 * RPL) + r]);
+                if (whole)
+                    yc[(int64_t)k * a.ndof + 3 * (int64_t)L.begin + r] = (Vv)acc_value(s);
+                else
+                    slots[(slot * NR + k) * a.ld_max + r] = (Vv)acc_value(s);
+            }
+            consumer_sync(NCW * 32);
+        }
+        if (!whole) {
+            __threadfence();
+            consumer_sync(NCW * 32);
+            if (threadIdx.x == 0) {
+                const int old = atomicAdd(a.counters + cur, 1);
+                *s_flag = (old == sp.nparts - 1);
+            }
+            consumer_sync(NCW * 32);
+            if (*s_flag) {
+                __threadfence();
+                for (int k = 0; k < a.nr; ++k)
+                    for (int r = threadIdx.x; r < rows; r += NCW * 32) {
+                        Vv s = 0;
+                        for (int p = 0; p < sp.nparts; ++p)
+                            s += __ldcg(slots + ((int64_t)(sp.slot_base + p) * NR + k) * a.ld_max + r);
+                        yc[(int64_t)k * a.ndof + 3 * (int64_t)L.begin + r] = s;
+                    }
+                if (threadIdx.x == 0) a.counters[cur] = 0;
+            }
+            consumer_sync(NCW * 32);
+        }
+    };
+
+    for (int i = c0; i < c1; ++i) {
+        const int q = i - c0, s = q % STAGES;
+        const Chunk ch = a.chunks[i];
+        if (ch.leaf != cur) {
+            if (cur >= 0) flush();
+            cur = ch.leaf;
+            L = a.leaves[cur];
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+#pragma unroll
+                for (int j = 0; j < RPL; ++j) acc_zero(acc[k][j]);
+        }
+        // operands of this warp's columns: column c = w + NCW j is held by lane j
+        const int* zi = ch.kind == 0 ? a.near_zidx : a.u_zidx;
+        const Vv* zsrc = ch.kind == 0 ? xc : tb;
+        const int64_t zstride = ch.kind == 0 ? a.ndof : a.tblen;
+        const int cmine = w + NCW * lane;
+        Vv zreg[NR];
+        if (cmine < ch.ncols) {
+            const int zix = zi[ch.cbase + cmine];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) zreg[k] = k < a.nr ? zsrc[(int64_t)k * zstride + zix] : (Vv)0;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NR; ++k) zreg[k] = (Vv)0;
+        }
+        mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
+        const unsigned char* buf = stage + (size_t)s * STAGE_BYTES;
+        const int rows = 3 * L.n;
+        for (int j = 0, c = w; c < ch.ncols; ++j, c += NCW) {
+            Vv zv[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) zv[k] = __shfl_sync(0xffffffffu, zreg[k], j);
+            if (ch.kind == 0) {
+                const float* col = (const float*)buf + (size_t)c * L.ld;
+#pragma unroll
+                for (int ii = 0; ii < RPL; ++ii) {
+                    const int r = lane + 32 * ii;
+                    const float v = r < rows ? col[r] : 0.f;
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, make_z(zv[k]));
+                }
+            } else {
+                const C* col = (const C*)buf + (size_t)c * L.ld;
+#pragma unroll
+                for (int ii = 0; ii < RPL; ++ii) {
+                    const int r = lane + 32 * ii;
+                    const float v = r < rows ? coef(col, r) : 0.f;
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, make_z(zv[k]));
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
+    }
+    if (cur >= 0) flush();
+}
+
+// ---- phase 1: P[pidx[c]] = V_t[:, c] . xc_t
+template <int MODE, class C, int NR, int RPL, int NCW>
+__global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
+    using Acc = typename AccT<MODE>::type;
+    using Vv = typename AccT<MODE>::vec;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = (uint64_t*)smem;
+    uint64_t* empty = full + STAGES;
+    unsigned char* stage = smem + BAR_BYTES;
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, NCW);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
+    if (w == NCW) {
+        if (lane == 0) produce<C>(a, stage, full, empty, c0, c1);
+        return;
+    }
+    const Vv* xc = (const Vv*)a.xc;
+    Vv* P = (Vv*)a.out;
+    int cur = -1;
+    LeafDesc L{};
+    decltype(make_z(Vv(0))) xr[NR][RPL];
+    for (int i = c0; i < c1; ++i) {
+        const int q = i - c0, s = q % STAGES;
+        const Chunk ch = a.chunks[i];
+        if (ch.leaf != cur) {
+            cur = ch.leaf;
+            L = a.leaves[cur];
+            const int rows = 3 * L.n;
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+#pragma unroll
+                for (int ii = 0; ii < RPL; ++ii) {
+                    const int r = lane + 32 * ii;
+                    xr[k][ii] = make_z((r < rows && k < a.nr) ? xc[(int64_t)k * a.ndof + 3 * (int64_t)L.begin + r]
+                                                             : (Vv)0);
+                }
+        }
+        mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
+        const C* buf = (const C*)(stage + (size_t)s * STAGE_BYTES);
+        const int rows = 3 * L.n;
+        for (int c = w; c < ch.ncols; c += NCW) {
+            const C* col = buf + (size_t)c * L.ld;
+            Acc acc[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) acc_zero(acc[k]);
+#pragma unroll
+            for (int ii = 0; ii < RPL; ++ii) {
+                const int r = lane + 32 * ii;
+                const float v = r < rows ? coef(col, r) : 0.f;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc_fma(acc[k], v, xr[k][ii]);
+            }
+            const int pi = a.v_pidx[ch.cbase + c];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc_add(acc[k], acc_shfl(acc[k], o));
+                if (lane == 0 && k < a.nr) P[(int64_t)k * a.plen + pi] = (Vv)acc_value(acc[k]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
+    }
+}
+
+template <int MODE>
+constexpr int ncw_for(int NR) {
+    return (MODE == 1 || NR > 1) ? 8 : 16;
+}
+
+template <int MODE, class C, int NR, int RPL>
+void launch_phases(HMat& H, const StreamArgs& base, cudaStream_t st) {
+    constexpr int NCW = ncw_for<MODE>(NR);
+    using Acc = typename AccT<MODE>::type;
+    const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES;
+    const size_t smem2 = smem1 + (size_t)NCW * 32 * RPL * sizeof(Acc);
+    if (H.n_far > 0 && H.p_len > 0) {
+        StreamArgs a = base;
+        a.chunks = H.ch1.p;
+        a.cta_begin = H.cta1.p;
+        a.out = MODE == 0 ? (void*)H.Pf.p : (void*)H.P.p;
+        HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem1));
+        k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
+        HM_LAUNCH_CHECK();
+        using V = typename AccT<MODE>::vec;
+        const unsigned nfb = (unsigned)ceil_div(H.n_far, 8);
+        k_reduce_tb<V><<<nfb, 256, 0, st>>>(H.far.p, H.n_far, (const V*)a.out, (V*)base.tb, H.p_len, H.tb_len, base.nr);
+        HM_LAUNCH_CHECK();
+    }
+    StreamArgs a = base;
+    a.chunks = H.ch2.p;
+    a.cta_begin = H.cta2.p;
+    HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem2));
+    k_phase2<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem2, st>>>(a);
+    HM_LAUNCH_CHECK();
+}
+
+template <int MODE, class C, int NR>
+void launch_rpl(HMat& H, const StreamArgs& a, cudaStream_t st) {
+    if (H.ld_max <= 192)
+        launch_phases<MODE, C, NR, 6>(H, a, st);
+    else
+        launch_phases<MODE, C, NR, 12>(H, a, st);
+}
+
+template <int MODE, class C>
+void launch_nr(HMat& H, const StreamArgs& a, int nrhs, cudaStream_t st) {
+    if (nrhs == 1)
+        launch_rpl<MODE, C, 1>(H, a, st);
+    else if (nrhs <= 4)
+        launch_rpl<MODE, C, 4>(H, a, st);
+    else
+        launch_rpl<MODE, C, 16>(H, a, st);
+}
+
+}  // namespace
+
+void build_product_plan(HMat& H, cudaStream_t st) {
+    int dev = 0, nsm = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    H.grid = std::max(1, nsm);
+    const int G = H.grid;
+    const int esz = H.storage == HM_BF16 ? 2 : 4;
+    H.ld_max = 0;
+    for (const LeafDesc& L : H.h_leaves) H.ld_max = std::max(H.ld_max, L.ld);
+
+    auto cut = [&](std::vector<Chunk>& out, std::vector<int64_t>& bytes, int leaf, int kind, int64_t src, int cbase,
+                   int ncols, int ld, int elem) {
+        // whole columns, at most one stage, at most 32 per consumer warp (8 warps)
+        const int per = std::max(1, std::min(256, STAGE_BYTES / (ld * elem)));
+        for (int c = 0; c < ncols; c += per) {
+            Chunk ch;
+            ch.src = src + (int64_t)c * ld;
+            ch.leaf = leaf;
+            ch.cbase = cbase + c;
+            ch.ncols = std::min(per, ncols - c);
+            ch.kind = kind;
+            out.push_back(ch);
+            bytes.push_back((int64_t)ch.ncols * ld * elem);
+        }
+    };
+    auto split_ranges = [&](const std::vector<int64_t>& bytes, std::vector<int32_t>& cta) {
+        int64_t tot = 0;
+        for (int64_t b : bytes) tot += b;
+        cta.assign(G + 1, (int32_t)bytes.size());
+        int64_t acc = 0;
+        int w = 0;
+        cta[0] = 0;
+        for (size_t i = 0; i < bytes.size(); ++i) {
+            // chunk i goes to the CTA whose share contains its first byte
+            while (w + 1 <= G && acc >= (tot * (int64_t)(w + 1)) / G) {
+                ++w;
+                cta[w] = (int32_t)i;
+            }
+            acc += bytes[i];
+        }
+        for (int q = w + 1; q <= G; ++q) cta[q] = (int32_t)bytes.size();
+    };
+
+    std::vector<Chunk> c1, c2;
+    std::vector<int64_t> b1, b2;
+    const int nl = H.n_leaves;
+    for (int l = 0; l < nl; ++l) {
+        const LeafDesc& L = H.h_leaves[l];
+        cut(c2, b2, l, 0, L.near_off, L.near_cbase, L.near_cols, L.ld, 4);
+        cut(c2, b2, l, 1, L.u_off, L.u_cbase, L.u_cols, L.ld, esz);
+        cut(c1, b1, l, 2, L.v_off, L.v_cbase, L.v_cols, L.ld, esz);
+    }
+    std::vector<int32_t> cta1, cta2;
+    split_ranges(b1, cta1);
+    split_ranges(b2, cta2);
+    // split row leaves
+    std::vector<LeafSplit> sp(nl, LeafSplit{0, 0, 0, 0});
+    std::vector<int> first(nl, -1), last(nl, -1);
+    for (int w = 0; w < G; ++w)
+        for (int i = cta2[w]; i < cta2[w + 1]; ++i) {
+            const int l = c2[i].leaf;
+            if (first[l] < 0) first[l] = w;
+            last[l] = w;
+        }
+    int slots = 0;
+    for (int l = 0; l < nl; ++l) {
+        if (first[l] < 0) fail(HM_EINVAL, "product plan: a leaf has no columns");
+        sp[l].w_first = first[l];
+        sp[l].nparts = last[l] - first[l] + 1;
+        sp[l].slot_base = sp[l].nparts > 1 ? slots : 0;
+        if (sp[l].nparts > 1) slots += sp[l].nparts;
+    }
+    H.n_slots = slots;
+    H.ch1.upload(c1, st);
+    H.ch2.upload(c2, st);
+    H.cta1.upload(cta1, st);
+    H.cta2.upload(cta2, st);
+    H.split.upload(sp, st);
+    H.counters.alloc(nl);
+    HM_CUDA(cudaMemsetAsync(H.counters.p, 0, H.counters.bytes(), st));
+    H.err.alloc(1);
+    HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
+}
+
+void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t) {
+    if (nrhs <= H.nrhs_cap) return;
+    const int cap = nrhs <= 1 ? 1 : (nrhs <= 4 ? 4 : 16 * (int)ceil_div(nrhs, 16));
+    H.xc.alloc((size_t)H.ndof * cap);
+    H.yc.alloc((size_t)H.ndof * cap);
+    H.xcf.alloc((size_t)H.ndof * cap);
+    H.ycf.alloc((size_t)H.ndof * cap);
+    H.P.alloc((size_t)std::max<int64_t>(H.p_len, 1) * cap);
+    H.tb.alloc((size_t)std::max<int64_t>(H.tb_len, 1) * cap);
+    H.Pf.alloc((size_t)std::max<int64_t>(H.p_len, 1) * cap);
+    H.tbf.alloc((size_t)std::max<int64_t>(H.tb_len, 1) * cap);
+    const size_t sl = (size_t)std::max(H.n_slots, 1) * 16 * std::max(H.ld_max, 1);
+    H.slotsf.alloc(sl);
+    H.slotsd.alloc(sl);
+    H.nrhs_cap = cap;
+}
+
+void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st) {
+    if (nrhs < 1) fail(HM_EINVAL, "matvec: nrhs must be >= 1");
+    if (!x || !y) fail(HM_EINVAL, "matvec: NULL vector");
+    if (dtype != HM_F32 && dtype != HM_F64) fail(HM_EINVAL, "matvec: dtype must be HM_F32 or HM_F64");
+    ensure_product_scratch(H, std::min(nrhs, 16), st);
+    const bool bf = H.storage == HM_BF16;
+    // at most 16 right-hand sides per pass of the coefficient streams
+    for (int k0 = 0; k0 < nrhs; k0 += 16) {
+        const int nr = std::min(16, nrhs - k0);
+        const int64_t tot = H.ndof * nr;
+        const unsigned gb = (unsigned)ceil_div(tot, 256);
+        StreamArgs a{};
+        a.leaves = H.leaves.p;
+        a.split = H.split.p;
+        a.near = H.near.p;
+        a.ucoef = bf ? (const void*)H.u16.p : (const void*)H.u32.p;
+        a.vcoef = bf ? (const void*)H.v16.p : (const void*)H.v32.p;
+        a.near_zidx = H.near_zidx.p;
+        a.u_zidx = H.u_zidx.p;
+        a.v_pidx = H.v_pidx.p;
+        a.counters = H.counters.p;
+        a.err = H.err.p;
+        a.ndof = H.ndof;
+        a.tblen = H.tb_len;
+        a.plen = H.p_len;
+        a.nr = nr;
+        a.ld_max = H.ld_max;
+        if (dtype == HM_F32) {
+            const float* xf = (const float*)x + (int64_t)k0 * H.ndof;
+            float* yf = (float*)y + (int64_t)k0 * H.ndof;
+            k_gather<float><<<gb, 256, 0, st>>>(xf, H.xcf.p, H.perm.p, H.N, nr);
+            a.xc = H.xcf.p;
+            a.tb = H.tbf.p;
+            a.out = H.ycf.p;
+            a.slots = H.slotsf.p;
+            if (bf)
+                launch_nr<0, uint16_t>(H, a, nr, st);
+            else
+                launch_nr<0, float>(H, a, nr, st);
+            k_scatter<float><<<gb, 256, 0, st>>>(H.ycf.p, yf, H.perm.p, H.N, nr);
+        } else {
+            const double* xd = (const double*)x + (int64_t)k0 * H.ndof;
+            double* yd = (double*)y + (int64_t)k0 * H.ndof;
+            k_gather<double><<<gb, 256, 0, st>>>(xd, H.xc.p, H.perm.p, H.N, nr);
+            a.xc = H.xc.p;
+            a.tb = H.tb.p;
+            a.out = H.yc.p;
+            a.slots = H.slotsd.p;
+            if (bf)
+                launch_nr<1, uint16_t>(H, a, nr, st);
+            else
+                launch_nr<1, float>(H, a, nr, st);
+            k_scatter<double><<<gb, 256, 0, st>>>(H.yc.p, yd, H.perm.p, H.N, nr);
+        }
+        HM_LAUNCH_CHECK();
+    }
+}
+
+// Error flags raised by the product kernels since the last check (0 if none); clears them.
+int product_error_flags(HMat& H, cudaStream_t st) {
+    int e = 0;
+    HM_CUDA(cudaMemcpyAsync(&e, H.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (e) HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
+    return e;
+}
+
+}  // namespace hm

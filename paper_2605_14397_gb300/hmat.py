@@ -1,0 +1,236 @@
+"""Thin Python binding of libhmat (include/hmat.h).  Argument marshalling only: every
+step of the hot path runs in the CUDA library.  PyTorch supplies device memory and
+streams; there is no CPU fallback -- if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhmat.so")
+
+HM_OK = 0
+HM_EINVAL = -1
+HM_ENOMEM = -2
+HM_ECUDA = -3
+HM_ESINGULAR_GEOM = -4
+HM_ENOCONV = -5
+HM_EBREAKDOWN = -6
+HM_ENAN = -7
+HM_ETIMEOUT = -8
+HM_F32, HM_F64, HM_BF16 = 1, 2, 3
+
+_STATUS_NAMES = {HM_EINVAL: "HM_EINVAL", HM_ENOMEM: "HM_ENOMEM", HM_ECUDA: "HM_ECUDA",
+                 HM_ESINGULAR_GEOM: "HM_ESINGULAR_GEOM", HM_ENOCONV: "HM_ENOCONV",
+                 HM_EBREAKDOWN: "HM_EBREAKDOWN", HM_ENAN: "HM_ENAN", HM_ETIMEOUT: "HM_ETIMEOUT"}
+
+
+class HMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (_STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+class hm_elements(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64)] + [(n, ctypes.POINTER(ctypes.c_double))
+                                           for n in ("c", "s1", "s2", "n", "a", "b")]
+
+
+class hm_tree_info(ctypes.Structure):
+    _fields_ = [("n_elements", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_near", ctypes.c_int64), ("n_far", ctypes.c_int64), ("leaf_size", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("eta", ctypes.c_double)]
+
+
+class hm_assemble_opts(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("aca_eps", ctypes.c_double),
+                ("storage", ctypes.c_int), ("max_rank", ctypes.c_int)]
+
+
+class hm_hmat_info(ctypes.Structure):
+    _fields_ = [("n_dof", ctypes.c_int64), ("near_entries", ctypes.c_int64), ("far_entries", ctypes.c_int64),
+                ("stored_bytes", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_int64),
+                ("rank_min", ctypes.c_int32), ("rank_max", ctypes.c_int32), ("rank_mean", ctypes.c_double),
+                ("assemble_seconds", ctypes.c_double), ("storage", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("n_far_lowrank", ctypes.c_int64), ("n_far_dense", ctypes.c_int64)]
+
+
+_LIB = None
+
+# (name, restype, argtypes) of every exported entry point declared in include/hmat.h
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_I = ctypes.c_int
+_P64 = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = [
+    ("hm_last_error", ctypes.c_char_p, []),
+    ("hm_version", ctypes.c_int, []),
+    ("hm_influence_blocks", _I, [ctypes.POINTER(hm_elements), _D, _D, _I64, _VP, _VP, _VP, _VP]),
+    ("hm_build_cluster_tree", _I, [ctypes.POINTER(hm_elements), _I, _D, ctypes.POINTER(_VP)]),
+    ("hm_tree_get_info", _I, [_VP, ctypes.POINTER(hm_tree_info)]),
+    ("hm_tree_export", _I, [_VP, _P64, _P64, _P64, _P64, _P64, _P64, _P64]),
+    ("hm_tree_destroy", None, [_VP]),
+    ("hm_assemble_hmat", _I, [_VP, ctypes.POINTER(hm_elements), ctypes.POINTER(hm_assemble_opts), _VP,
+                              ctypes.POINTER(_VP)]),
+    ("hm_hmat_get_info", _I, [_VP, ctypes.POINTER(hm_hmat_info)]),
+    ("hm_hmat_far_factors", _I, [_VP, _I64, ctypes.POINTER(ctypes.c_int32), _VP, _VP]),
+    ("hm_hmat_destroy", None, [_VP]),
+    ("hm_matvec", _I, [_VP, _VP, _VP, _I, _I, _VP]),
+    ("hm_hmat_check", _I, [_VP, _VP]),
+]
+
+
+def lib():
+    """Load libhmat.so (built by __graft_entry__.build() / paper_2605_14397_gb300.build)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libhmat.so is not built (run __graft_entry__.build()); "
+                              "there is no CPU fallback for the hot path")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status):
+    if status != HM_OK:
+        raise HMError(status, lib().hm_last_error().decode())
+
+
+def last_error() -> str:
+    return lib().hm_last_error().decode()
+
+
+class _ElemArgs:
+    """Keeps the contiguous FP64 arrays alive while the struct points at them."""
+
+    def __init__(self, el):
+        self.arrs = [np.ascontiguousarray(getattr(el, k), dtype=np.float64) for k in ("c", "s1", "s2", "n", "a", "b")]
+        dp = ctypes.POINTER(ctypes.c_double)
+        self.s = hm_elements(el.N, *[a.ctypes.data_as(dp) for a in self.arrs])
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ entry points
+
+def influence_blocks(el, E, nu, ri, sj, out, stream=None):
+    """Fill out (npairs*9 float64, device) with the 3x3 blocks E_{ri[p], sj[p]}."""
+    ea = _ElemArgs(el)
+    _check(lib().hm_influence_blocks(ea.ref, float(E), float(nu), int(ri.numel()), _dptr(ri), _dptr(sj),
+                                     _dptr(out), ctypes.c_void_p(_stream_ptr(stream))))
+
+
+class ClusterTree:
+    def __init__(self, el, leaf_size=64, eta=2.0):
+        ea = _ElemArgs(el)
+        h = ctypes.c_void_p()
+        _check(lib().hm_build_cluster_tree(ea.ref, int(leaf_size), float(eta), ctypes.byref(h)))
+        self.handle = h
+
+    def info(self):
+        i = hm_tree_info()
+        _check(lib().hm_tree_get_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in hm_tree_info._fields_}
+
+    def export(self):
+        i = self.info()
+        nn, ne = i["n_nodes"], i["n_elements"]
+        perm = np.empty(ne, np.int64)
+        begin, end, left, right = (np.empty(nn, np.int64) for _ in range(4))
+        near = np.empty((max(i["n_near"], 1), 2), np.int64)
+        far = np.empty((max(i["n_far"], 1), 2), np.int64)
+        p = lambda a: a.ctypes.data_as(_P64)
+        _check(lib().hm_tree_export(self.handle, p(perm), p(begin), p(end), p(left), p(right), p(near), p(far)))
+        return dict(perm=perm, begin=begin, end=end, left=left, right=right,
+                    near=near[:i["n_near"]], far=far[:i["n_far"]])
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().hm_tree_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HMatrix:
+    def __init__(self, tree, el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", max_rank=0, stream=None):
+        st = {"f32": HM_F32, "bf16": HM_BF16}[storage]
+        ea = _ElemArgs(el) if el is not None else None
+        opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, int(max_rank))
+        h = ctypes.c_void_p()
+        _check(lib().hm_assemble_hmat(tree.handle, ea.ref if ea else None, ctypes.byref(opt),
+                                      ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+        self.handle = h
+        self.E, self.nu, self.eps, self.storage = E, nu, aca_eps, storage
+        self.ndof = 3 * el.N if el is not None else None
+
+    def info(self):
+        i = hm_hmat_info()
+        _check(lib().hm_hmat_get_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in hm_hmat_info._fields_}
+
+    def far_factors(self, b):
+        r = ctypes.c_int32()
+        _check(lib().hm_hmat_far_factors(self.handle, int(b), ctypes.byref(r), None, None))
+        return r.value
+
+    def far_factor_arrays(self, b, s_n, t_n):
+        """(U, V) of far block b, or None if the block is stored dense."""
+        r = self.far_factors(b)
+        if r < 0:
+            return None
+        U = np.empty((r, 3 * s_n))
+        V = np.empty((r, 3 * t_n))
+        _check(lib().hm_hmat_far_factors(self.handle, int(b), None, U.ctypes.data_as(_VP), V.ctypes.data_as(_VP)))
+        return U.T, V.T  # column-major on the C side -> (3|s| x r), (3|t| x r)
+
+    def matvec(self, x, y, stream=None):
+        """y = E x; x, y torch CUDA tensors of shape (3N,) or (nrhs, 3N), float32 or float64."""
+        import torch
+        dt = {torch.float32: HM_F32, torch.float64: HM_F64}[x.dtype]
+        assert y.dtype == x.dtype and x.is_contiguous() and y.is_contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        _check(lib().hm_matvec(self.handle, _dptr(x), _dptr(y), int(nrhs), dt, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def check(self, stream=None):
+        """Synchronise and raise HMError(HM_ETIMEOUT) if a product kernel gave up waiting."""
+        _check(lib().hm_hmat_check(self.handle, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().hm_hmat_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -112,7 +112,7 @@ void hm_tree_destroy(hm_tree* t);
  * Assemble the H-matrix of E on the device: dense near-field tiles in FP32 (FP64
  * evaluation), admissible blocks compressed by adaptive cross approximation with
  * element (3-row) pivots to relative Frobenius accuracy aca_eps per block, factors
- * stored in `storage` (HM_F32 or HM_BF16).  max_rank caps the ACA rank (0 = 96).
+ * stored in `storage` (HM_F32 or HM_BF16).  max_rank caps the ACA rank (0 = 160, at most 256).
  * Synchronises the stream (the packed layout depends on the ranks). */
 typedef struct {
     double E;

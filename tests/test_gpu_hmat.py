@@ -157,4 +157,4 @@ def test_full_size_fault_sampled_rows(dev):
     got = y.reshape(-1, 3)[rows].ravel()
     assert rel(got, ref) <= eps + 1e-6
     info = H.info()
-    assert info["rank_max"] <= 96 and info["near_entries"] > 0
+    assert info["rank_max"] <= 160 and info["near_entries"] > 0

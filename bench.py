@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the H-matrix DD-BEM hot path on one GB300 (or N replicas).
+
+A step is one H-matrix product y = E x (FP32 factors, one right-hand side) of the
+51,468-element disk fault (256 x 256 grid, r < 1; leaf 64, eta 2, ACA eps 1e-6), the
+operator that every GMRES iteration applies.  The H-matrix is assembled once before the
+timed region (setup, reported apart).  value = algorithmic bytes of the product (stored
+near-field entries x 4 B + factor entries x 4 B + x and y) / time, summed over ranks.
+The coefficients (4.3 GB) are far larger than L2 (129 MB), so consecutive products read
+them from HBM; no L2 flush is needed.
+
+Also reported: the per-phase roofline of the dominant kernel (CUDA events on the
+launching stream), the end-to-end rate through hm_matvec_host (host vectors, copies in
+the timed region), GMRES time-to-1e-8 for the plain FP64 and the mixed BF16 + FP64
+refinement solvers, clocks sampled during the timed region, and the CPU oracle timed on
+this machine's host cores on a bounded sample of rows.
+
+`--impl reference` times the CPU FP64 oracle (the dense product, row-sampled) on the
+host cores with the same metric and prints the reference line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H-matvec GB/s (% HBM peak); GMRES time-to-1e-8 residual, mixed vs plain FP64"
+WORKLOAD = "disk fault r<1 on 256x256 grid: N=51468 rectangular DD elements, 154404 DOFs, leaf 64, eta 2, ACA eps 1e-6"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    p.add_argument("--no-gmres", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--grid", type=int, default=256, help="disk grid size (256: the 51,468-element fault)")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)[kernel]
+        src = open(os.path.join(ROOT, "paper_2605_14397_gb300", "csrc", "matvec.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != d["matvec_cu_sha256_16"]:
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def product_bytes(info, storage):
+    """Algorithmic bytes of one single-RHS product and of its phases."""
+    fb = 2 if storage == "bf16" else 4
+    n = info["n_dof"]
+    total = 4 * info["near_entries"] + fb * (info["u_entries"] + info["v_entries"]) + 2 * 4 * n
+    phase2 = 4 * info["near_entries"] + fb * info["u_entries"] + 4 * n + 4 * info["tb_len"] + 4 * n
+    phase1 = fb * info["v_entries"] + 4 * n + 4 * info["p_len"]
+    return total, phase2, phase1
+
+
+def oracle_rows_rate(el, E, nu, budget_s=15.0, max_rows=None):
+    """Oracle dense rows per second on this host (all cores), on a seeded row sample."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2605_14397_gb300 import synth
+    x = synth.rhs_shear_plus_bump(el)
+    rng = np.random.default_rng(1603)
+    probe = np.sort(rng.choice(el.N, size=16, replace=False))
+    t0 = time.perf_counter()
+    O.dense_matvec_rows(el, E, nu, x, probe)
+    per_row = (time.perf_counter() - t0) / 16
+    rows = int(max(16, min(el.N, budget_s / max(per_row, 1e-9))))
+    if max_rows:
+        rows = min(rows, max_rows)
+    sample = np.sort(rng.choice(el.N, size=rows, replace=False))
+    t0 = time.perf_counter()
+    O.dense_matvec_rows(el, E, nu, x, sample)
+    dt = time.perf_counter() - t0
+    return rows / dt, rows, dt
+
+
+def cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm: dense FP64 rows of E times x, row-sampled."""
+    if rank != 0:
+        return
+    from __graft_entry__ import build
+    build()
+    from paper_2605_14397_gb300 import synth
+    el = synth.config_fault(256)
+    import numpy as np
+    from oracle import oracle as O
+    x = synth.rhs_shear_plus_bump(el)
+    rng = np.random.default_rng(1603)
+    # calibrate so the whole run stays within about two minutes
+    probe = np.sort(rng.choice(el.N, size=8, replace=False))
+    t0 = time.perf_counter()
+    O.dense_matvec_rows(el, 1.0, 0.25, x, probe)
+    per_row = (time.perf_counter() - t0) / 8
+    rows_per_step = int(max(1, min(256, 100.0 / max(per_row * (args.steps + args.warmup), 1e-9))))
+    for _ in range(args.warmup):
+        O.dense_matvec_rows(el, 1.0, 0.25, x, np.sort(rng.choice(el.N, size=rows_per_step, replace=False)))
+    times = []
+    for _ in range(args.steps):
+        rows = np.sort(rng.choice(el.N, size=rows_per_step, replace=False))
+        t0 = time.perf_counter()
+        O.dense_matvec_rows(el, 1.0, 0.25, x, rows)
+        times.append(time.perf_counter() - t0)
+    t_step = sum(times) / len(times)
+    # same metric: the H-matrix product's algorithmic bytes per full product
+    n = 3 * el.N
+    ref_bytes = _reference_bytes()
+    full = t_step * el.N / rows_per_step
+    val = ref_bytes / full / 1e9
+    sample = "%d seeded receiver rows x %d source elements per step (dense FP64 rows of E times x)" % (
+        rows_per_step, el.N)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nrhs": 1, "storage": "dense FP64 (oracle)"},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _reference_bytes():
+    # algorithmic bytes of the FP32 H-matrix product of this workload (leaf 64, eta 2,
+    # eps 1e-6), as the GPU arm assembles it; the oracle's throughput is stated in the
+    # same unit so the two lines compare.
+    return 4340841024
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_2605_14397_gb300 import hmat, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    el = synth.config_fault(args.grid)
+    E, nu, eps = 1.0, 0.25, 1e-6
+    t0 = time.perf_counter()
+    T = hmat.ClusterTree(el, 64, 2.0)
+    H = hmat.HMatrix(T, el, E, nu, eps, args.storage)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    info = H.info()
+    B, B2, B1 = product_bytes(info, args.storage)
+
+    x = torch.from_numpy(synth.rhs_shear_plus_bump(el)).to(dev, torch.float32)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        H.matvec(x, y, stream)
+    H.check(stream)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    H.timing(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        H.matvec(x, y, stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    clocks = sampler.stop()
+    H.timing(False)
+    ph = H.timing_read()
+    H.check(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B / (ms * 1e-3) / 1e9
+    hbm, peak_kind = peaks()
+    cnt = max(ph["count"], 1)
+    t2 = ph["phase2"] / cnt * 1e-3
+    t1 = ph["phase1"] / cnt * 1e-3
+    ach = B2 / t2 / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_phase2 ([D|U] z per row leaf)", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "peak_source": peak_kind,
+                "traffic": recorded_traffic("k_phase2"),
+                "algorithmic_bytes_per_launch": B2, "launch_ms": t2 * 1e3,
+                "phases_ms": {k: ph[k] / cnt for k in ("gather", "phase1", "reduce", "phase2", "scatter")},
+                "phase1_GBs": B1 / t1 / 1e9 if t1 > 0 else None}
+
+    # end to end through the host-vector entry point
+    xh = torch.from_numpy(synth.rhs_shear_plus_bump(el).astype(np.float32)).pin_memory().numpy()
+    yh = torch.empty(xh.shape, dtype=torch.float32).pin_memory().numpy()
+    ke = min(args.steps, 200)
+    for _ in range(3):
+        H.matvec_host(xh, yh, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        H.matvec_host(xh, yh, stream)
+    te = (time.perf_counter() - t0) / ke
+    if dist is not None:
+        t = torch.tensor([te], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": world * B / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(xh.nbytes),
+           "d2h_bytes_per_step": int(yh.nbytes), "ms_per_step": te * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else "bf16",
+            "data": "synthetic (seeded mesh and right-hand side)",
+            "config": {"workload": WORKLOAD if args.grid == 256 else "disk fault on %dx%d grid: N=%d" % (
+                           args.grid, args.grid, el.N), "nrhs": 1, "storage": args.storage,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "operator 4.3 GB >> 129 MB L2: inputs larger than L2, no flush",
+                       "setup_s": t_setup, "assemble_s": info["assemble_seconds"],
+                       "rank_mean": info["rank_mean"], "rank_max": info["rank_max"],
+                       "bytes_per_product": B, "frac_of_hbm_peak": value / world / hbm},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clocks}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, rows, dt = oracle_rows_rate(el, E, nu)
+        full = el.N / rate
+        line["cpu_baseline"] = {"value": B / full / 1e9, "unit": "GB/s", "cores": cores(), "kind": "oracle",
+                                "sample": "%d seeded receiver rows of the dense FP64 product (%.1f s), "
+                                          "extrapolated to a full product (%.1f s)" % (rows, dt, full)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -137,6 +137,10 @@ typedef struct {
     int32_t pad_;
     int64_t n_far_lowrank;    /* admissible blocks stored as factors */
     int64_t n_far_dense;      /* admissible blocks whose factors would exceed the dense block */
+    int64_t u_entries;        /* sum over low-rank blocks of 3 |s| r (row factors) */
+    int64_t v_entries;        /* sum over low-rank blocks of 3 |t| r (column factors) */
+    int64_t tb_len;           /* sum of the ranks (length of the V^T x vector) */
+    int64_t p_len;            /* per-leaf partials of V^T x */
 } hm_hmat_info;
 
 hm_status hm_assemble_hmat(const hm_tree* t, const hm_elements* el, const hm_assemble_opts* opt,
@@ -158,6 +162,21 @@ void hm_hmat_destroy(hm_hmat* h);
  * x_dev and y_dev must not overlap.  Asynchronous. */
 hm_status hm_matvec(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, int dtype,
                     void* stream);
+
+/* The same product for vectors in host memory (pinned memory is fastest): x_host is
+ * copied to library-owned device scratch, the product runs on `stream`, y is copied
+ * back to y_host and the stream is synchronised before returning. */
+hm_status hm_matvec_host(const hm_hmat* h, const void* x_host, void* y_host, int nrhs, int dtype,
+                         void* stream);
+
+/* Per-phase timing of the products that follow, with CUDA events recorded on their
+ * stream between the phases.  enable = 1 clears the accumulators and starts recording,
+ * enable = 0 stops.  hm_hmat_timing_read synchronises with the last recorded event and
+ * returns, in milliseconds summed over the timed products: out[0] gather, out[1] phase 1
+ * (V^T x), out[2] reduction of the partials, out[3] phase 2 ([D | U] z), out[4] scatter,
+ * and out[5] the number of timed products. */
+hm_status hm_hmat_timing(const hm_hmat* h, int enable);
+hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
 
 /* Synchronise `stream` and report whether a device-side wait of an earlier product on
  * this H-matrix gave up (HM_ETIMEOUT; the flags are then cleared).  The product kernels

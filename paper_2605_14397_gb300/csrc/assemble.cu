@@ -372,7 +372,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         HM_LAUNCH_CHECK();
         HM_CUDA(cudaStreamSynchronize(st));
     }
-    H.near_zidx.upload(near_zidx, st);
+    H.h_near_zidx = std::move(near_zidx);
 
     // ---- ranks, partial-buffer and t-vector layout (low-rank blocks only)
     int64_t tb_len = 0, p_len = 0;
@@ -481,8 +481,8 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         HM_LAUNCH_CHECK();
         HM_CUDA(cudaStreamSynchronize(st));
     }
-    H.u_zidx.upload(u_zidx, st);
-    H.v_pidx.upload(v_pidx, st);
+    H.h_u_zidx = std::move(u_zidx);
+    H.h_v_pidx = std::move(v_pidx);
     H.leaves.upload(H.h_leaves, st);
     H.far.upload(H.h_far, st);
 

@@ -134,6 +134,13 @@ hm_status hm_hmat_get_info(const hm_hmat* hh, hm_hmat_info* info) {
     info->pad_ = 0;
     info->n_far_dense = H.n_dense_far;
     info->n_far_lowrank = H.n_far - H.n_dense_far;
+    info->u_entries = info->v_entries = 0;
+    for (const hm::FarDesc& F : H.h_far) {
+        info->u_entries += 3LL * F.rank * F.s_n;
+        info->v_entries += 3LL * F.rank * F.t_n;
+    }
+    info->tb_len = H.tb_len;
+    info->p_len = H.p_len;
     HM_API_END
 }
 
@@ -164,6 +171,28 @@ hm_status hm_matvec(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs,
     if (!hh) hm::fail(HM_EINVAL, "matvec: NULL H-matrix");
     if (x_dev == y_dev) hm::fail(HM_EINVAL, "matvec: x and y must not overlap");
     hm::matvec(const_cast<hm::HMat&>(hh->h), x_dev, y_dev, nrhs, dtype, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_matvec_host(const hm_hmat* hh, const void* x_host, void* y_host, int nrhs, int dtype, void* stream) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "matvec_host: NULL H-matrix");
+    if (x_host == y_host) hm::fail(HM_EINVAL, "matvec_host: x and y must not overlap");
+    hm::matvec_host(const_cast<hm::HMat&>(hh->h), x_host, y_host, nrhs, dtype, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_hmat_timing(const hm_hmat* hh, int enable) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "hmat_timing: NULL H-matrix");
+    hm::timing_enable(const_cast<hm::HMat&>(hh->h), enable != 0);
+    HM_API_END
+}
+
+hm_status hm_hmat_timing_read(const hm_hmat* hh, double* out6) {
+    HM_API_BEGIN
+    if (!hh || !out6) hm::fail(HM_EINVAL, "hmat_timing_read: NULL argument");
+    hm::timing_read(const_cast<hm::HMat&>(hh->h), out6);
     HM_API_END
 }
 

@@ -10,11 +10,13 @@
 // rows of a slice are the leaf's DOFs in cluster order.
 //
 // The product y = E x runs as
-//   gather     xc = x[perm]                       (cluster order)
-//   phase 1    P[pidx[c]] = V_t[:, c] . xc_t       per leaf t (column c of its V block)
+//   gather     xc = x[perm]                       (cluster order, RHS interleaved)
+//   phase 1    P = V_t^T xc_t                      per leaf t (one partial per V column)
 //   reduce     tb_b = sum over the leaves t of T_b of the partials of b
-//   phase 2    yc_s = [D_s | U_s] z_s,  z = [xc | tb] gathered by zidx
+//   phase 2    yc_s = [D_s | U_s] z_s,  z = xc (near columns) or tb (U columns)
 //   scatter    y[perm] = yc
+// A near tile, a U slice and a V slice each read (or write) a contiguous range of
+// xc / tb / P, so the operands of a pipeline chunk are one bulk copy.
 #pragma once
 
 #include <cstdint>
@@ -34,7 +36,7 @@ struct LeafDesc {
     int64_t u_off;     // entry offset into the U stream
     int64_t v_off;     // entry offset into the V stream
     int32_t near_cols, u_cols, v_cols;
-    int32_t near_cbase, u_cbase, v_cbase;  // first index into zidx / pidx arrays
+    int32_t near_cbase, u_cbase, v_cbase;  // first index into the host zidx / pidx arrays
     int32_t pad2_;
 };
 
@@ -49,13 +51,15 @@ struct FarDesc {
     int32_t pad_;
 };
 
-// One pipeline chunk: whole columns of one leaf's segment, at most one stage of bytes.
+// One pipeline chunk: whole columns of one tile or factor slice of one leaf, at most one
+// stage of bytes and 64 columns.
 struct Chunk {
     int64_t src;    // first entry in its stream
+    int64_t zoff;   // first operand index: xc (near), tb (U) or output partial (V)
     int32_t leaf;   // leaf ordinal
-    int32_t cbase;  // first column's index into the zidx (phase 2) or pidx (phase 1) array
     int32_t ncols;
     int32_t kind;   // 0 near tile (FP32), 1 U factor, 2 V factor
+    int32_t ld;     // padded rows of the leaf
 };
 
 // Row leaves whose phase-2 columns are split over several persistent CTAs.
@@ -89,7 +93,9 @@ struct HMat {
     DevBuf<float> u32, v32;       // factor streams (FP32 storage)
     DevBuf<uint16_t> u16, v16;    // factor streams (BF16 storage)
     DevBuf<float> facstore;       // compact FP32 factors per far block (U then V)
-    DevBuf<int32_t> near_zidx, u_zidx, v_pidx;
+    // operand index of every column (host; consecutive runs become the z ranges of the
+    // product chunks): xc index (near), tb index (U), partial index (V)
+    std::vector<int32_t> h_near_zidx, h_u_zidx, h_v_pidx;
 
     // persistent product plan
     int grid = 0;
@@ -102,6 +108,21 @@ struct HMat {
     DevBuf<int> err;
     DevBuf<float> slotsf;
     DevBuf<double> slotsd;
+
+    // per-phase timing (CUDA events, 6 per product) and host-vector staging
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double t_acc[5] = {0, 0, 0, 0, 0};
+    int64_t t_count = 0;
+    DevBuf<unsigned char> xs, ys;
+
+    HMat() = default;
+    HMat(const HMat&) = delete;
+    HMat& operator=(const HMat&) = delete;
+    ~HMat() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
 
     // product scratch, sized for nrhs_cap right-hand sides
     int nrhs_cap = 0;
@@ -120,6 +141,9 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
 void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t st);
 void build_product_plan(HMat& H, cudaStream_t st);
 int product_error_flags(HMat& H, cudaStream_t st);
+void timing_enable(HMat& H, bool on);
+void timing_read(HMat& H, double out[6]);
+void matvec_host(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 
 }  // namespace hm

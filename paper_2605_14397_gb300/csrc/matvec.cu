@@ -1,20 +1,22 @@
 // H-matrix product y = E x on the device (the product of Sec. 3.1 on the stored
 // H-matrix).
 //
-//   gather   xc = x[perm]                          cluster order
-//   phase 1  P[pidx[c]] = V_t[:, c] . xc_t         every V column (one per rank per leaf)
+//   gather   xc = x[perm]                          cluster order, RHS interleaved
+//   phase 1  P = V_t^T xc_t                        every V column (one per rank per leaf)
 //   reduce   tb_b = sum of the partials of block b over the leaves of its column cluster
 //   phase 2  yc_s = [D_s | U_s] z_s, z = xc (near columns) or tb (U columns)
 //   scatter  y[perm] = yc
 //
 // Phases 1 and 2 are persistent kernels, one CTA per SM.  Their coefficient streams are
-// cut into chunks of whole columns (at most 32 KB) and the chunk list is split into
-// equal byte ranges, one per CTA ("stream-K"): every SM streams the same number of
-// bytes.  One producer thread moves the chunks with cp.async.bulk (TMA) into a 4-stage
-// shared-memory ring guarded by mbarriers; 8 or 16 consumer warps each take columns of
-// the chunk, lanes over rows.  A row leaf whose columns fall into several CTAs is
-// finished by the last of them (atomic arrival count, partials summed in CTA order), so
-// the result is deterministic.
+// cut into chunks of whole columns of one tile or factor slice (at most 32 KB and 64
+// columns) and the chunk list is split into equal byte ranges, one per CTA ("stream-K"):
+// every SM streams the same number of bytes.  One producer thread moves each chunk --
+// its coefficients and, in phase 2, the contiguous range of operands it multiplies --
+// with two cp.async.bulk (TMA) copies into a 4-stage shared-memory ring guarded by
+// mbarriers; 8 or 16 consumer warps each take columns of the chunk, lanes over rows,
+// and touch no global memory except at leaf boundaries.  A row leaf whose columns fall
+// into several CTAs is finished by the last of them (atomic arrival count, partials
+// summed in CTA order), so the result is deterministic.
 //
 // Arithmetic modes over the same FP32/BF16 coefficient streams:
 //   F32: float vectors, FP32 accumulation;
@@ -33,8 +35,10 @@ namespace hm {
 namespace {
 
 constexpr int STAGES = 4;
-constexpr int STAGE_BYTES = 32768;
+constexpr int STAGE_BYTES = 32768;   // coefficients of one chunk
+constexpr int MAX_CHUNK_COLS = 64;
 constexpr int BAR_BYTES = 128;
+constexpr int VEC_SLACK = 32;        // elements after xc / tb so rounded-up copies stay inside
 
 struct FF {
     float hi, lo;
@@ -105,17 +109,19 @@ __device__ __forceinline__ double acc_value(const FF& a) { return (double)a.hi +
 __device__ __forceinline__ float coef(const float* p, int i) { return p[i]; }
 __device__ __forceinline__ float coef(const uint16_t* p, int i) { return __uint_as_float(((uint32_t)p[i]) << 16); }
 
+// xc[dof * nr + k] = x[k * ndof + user dof]
 template <class V>
 __global__ void k_gather(const V* __restrict__ x, V* __restrict__ xc, const int32_t* __restrict__ perm, int64_t N,
                          int nrhs) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t ndof = 3 * N;
     if (q >= ndof * nrhs) return;
-    const int64_t k = q / ndof, r = q % ndof;
+    const int64_t r = q / nrhs, k = q % nrhs;
     const int64_t p = r / 3, m = r % 3;
     xc[q] = x[k * ndof + 3 * (int64_t)perm[p] + m];
 }
 
+// y[k * ndof + user dof] = yc[k * ndof + dof]
 template <class V>
 __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int32_t* __restrict__ perm, int64_t N,
                           int nrhs) {
@@ -127,19 +133,20 @@ __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int
     y[k * ndof + 3 * (int64_t)perm[p] + m] = yc[q];
 }
 
+// tb[(tb_off + l) nr + k] = sum_q P[(pbase + q r + l) nr + k]
 template <class V>
 __global__ void k_reduce_tb(const FarDesc* __restrict__ far, int64_t nfar, const V* __restrict__ P, V* __restrict__ tb,
-                            int64_t plen, int64_t tblen, int nrhs) {
+                            int nrhs) {
     const int64_t b = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nfar) return;
     const FarDesc F = far[b];
-    for (int k = 0; k < nrhs; ++k)
-        for (int l = lane; l < F.rank; l += 32) {
-            V s = 0;
-            for (int q = 0; q < F.n_tleaves; ++q) s += P[k * plen + F.pbase + (int64_t)q * F.rank + l];
-            tb[k * tblen + F.tb_off + l] = s;
-        }
+    const int n = F.rank * nrhs;
+    for (int e = lane; e < n; e += 32) {
+        V s = 0;
+        for (int q = 0; q < F.n_tleaves; ++q) s += P[(F.pbase + (int64_t)q * F.rank) * nrhs + e];
+        tb[F.tb_off * nrhs + e] = s;
+    }
 }
 
 struct StreamArgs {
@@ -150,47 +157,75 @@ struct StreamArgs {
     const float* near;
     const void* ucoef;
     const void* vcoef;
-    const int32_t* near_zidx;
-    const int32_t* u_zidx;
-    const int32_t* v_pidx;
     const void* xc;
     const void* tb;
     void* out;    // yc (phase 2) or P (phase 1)
     void* slots;  // phase-2 partials of split leaves
     int32_t* counters;
     int* err;
-    int64_t ndof, tblen, plen;
-    int nr;       // right-hand sides in this launch (<= NR)
+    int64_t ndof;
+    int nr;       // right-hand sides in this launch (<= NR); also the interleave stride
     int ld_max;
 };
 
-// ---- producer: one thread streams this CTA's chunks through the ring
-template <class C>
-__device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* stage, uint64_t* full, uint64_t* empty,
-                                        int c0, int c1) {
+template <class V, int NR>
+struct ZRange {
+    static constexpr int ALIGN = 16 / (int)sizeof(V);  // elements per 16 bytes
+    static constexpr int BYTES = ((MAX_CHUNK_COLS * NR + 2 * ALIGN) * (int)sizeof(V) + 127) / 128 * 128;
+};
+
+// ---- producer: one thread streams this CTA's chunks (and their operands) through the ring
+template <class C, class V, int NR, bool WITH_Z>
+__device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem_stage, int stage_stride,
+                                        uint64_t* full, uint64_t* empty, int c0, int c1) {
+    using ZR = ZRange<V, NR>;
+    Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
     for (int i = c0; i < c1; ++i) {
+        const Chunk ch = nxt;
+        if (i + 1 < c1) nxt = a.chunks[i + 1];
         const int q = i - c0, s = q % STAGES;
         const uint32_t ph = (uint32_t)(q / STAGES) & 1u;
         if (q >= STAGES) mbar_wait(empty + s, ph ^ 1u, a.err, 4);
-        const Chunk ch = a.chunks[i];
-        const LeafDesc& L = a.leaves[ch.leaf];
+        unsigned char* stg = smem_stage + (size_t)s * stage_stride;
         const void* src;
         uint32_t bytes;
         if (ch.kind == 0) {
             src = a.near + ch.src;
-            bytes = (uint32_t)ch.ncols * L.ld * 4u;
+            bytes = (uint32_t)ch.ncols * ch.ld * 4u;
         } else {
             const C* base = (const C*)(ch.kind == 1 ? a.ucoef : a.vcoef);
             src = base + ch.src;
-            bytes = (uint32_t)ch.ncols * L.ld * (uint32_t)sizeof(C);
+            bytes = (uint32_t)ch.ncols * ch.ld * (uint32_t)sizeof(C);
         }
-        mbar_arrive_expect_tx(full + s, bytes);
-        bulk_g2s(stage + (size_t)s * STAGE_BYTES, src, bytes, full + s);
+        if constexpr (WITH_Z) {
+            const V* zsrc = (const V*)(ch.kind == 0 ? a.xc : a.tb);
+            const int64_t z0 = ch.zoff * a.nr;
+            const int64_t a0 = z0 & ~(int64_t)(ZR::ALIGN - 1);
+            const int64_t a1 = (z0 + (int64_t)ch.ncols * a.nr + ZR::ALIGN - 1) & ~(int64_t)(ZR::ALIGN - 1);
+            const uint32_t zbytes = (uint32_t)((a1 - a0) * (int64_t)sizeof(V));
+            mbar_arrive_expect_tx(full + s, bytes + zbytes);
+            bulk_g2s(stg, zsrc + a0, zbytes, full + s);
+            bulk_g2s(stg + ZR::BYTES, src, bytes, full + s);
+        } else {
+            mbar_arrive_expect_tx(full + s, bytes);
+            bulk_g2s(stg, src, bytes, full + s);
+        }
     }
-    // make sure no copy is still in flight when the CTA exits
+    // no copy may still be in flight when the CTA exits
     const int n = c1 - c0;
     for (int q = std::max(0, n - STAGES); q < n; ++q)
         mbar_wait(full + (q % STAGES), (uint32_t)(q / STAGES) & 1u, a.err, 8);
+}
+
+__device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int ncw) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, ncw);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
 }
 
 // ---- phase 2: y = [D | U] z per row leaf
@@ -198,29 +233,22 @@ template <int MODE, class C, int NR, int RPL, int NCW>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     using Acc = typename AccT<MODE>::type;
     using Vv = typename AccT<MODE>::vec;
+    using ZR = ZRange<Vv, NR>;
+    constexpr int STRIDE = ZR::BYTES + STAGE_BYTES;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = (uint64_t*)smem;
     uint64_t* empty = full + STAGES;
     int* s_flag = (int*)(empty + STAGES);
     unsigned char* stage = smem + BAR_BYTES;
-    Acc* red = (Acc*)(stage + (size_t)STAGES * STAGE_BYTES);  // [NCW][32 RPL]
+    Acc* red = (Acc*)(stage + (size_t)STAGES * STRIDE);  // [NCW][32 RPL]
 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full + s, 1);
-            mbar_init(empty + s, NCW);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
+    init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
     if (w == NCW) {
-        if (lane == 0) produce<C>(a, stage, full, empty, c0, c1);
+        if (lane == 0) produce<C, Vv, NR, true>(a, stage, STRIDE, full, empty, c0, c1);
         return;
     }
-    const Vv* xc = (const Vv*)a.xc;
-    const Vv* tb = (const Vv*)a.tb;
     Vv* yc = (Vv*)a.out;
     Vv* slots = (Vv*)a.slots;
     Acc acc[NR][RPL];
@@ -269,9 +297,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         }
     };
 
+    Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
     for (int i = c0; i < c1; ++i) {
+        const Chunk ch = nxt;
+        if (i + 1 < c1) nxt = a.chunks[i + 1];
         const int q = i - c0, s = q % STAGES;
-        const Chunk ch = a.chunks[i];
         if (ch.leaf != cur) {
             if (cur >= 0) flush();
             cur = ch.leaf;
@@ -281,44 +311,33 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
 #pragma unroll
                 for (int j = 0; j < RPL; ++j) acc_zero(acc[k][j]);
         }
-        // operands of this warp's columns: column c = w + NCW j is held by lane j
-        const int* zi = ch.kind == 0 ? a.near_zidx : a.u_zidx;
-        const Vv* zsrc = ch.kind == 0 ? xc : tb;
-        const int64_t zstride = ch.kind == 0 ? a.ndof : a.tblen;
-        const int cmine = w + NCW * lane;
-        Vv zreg[NR];
-        if (cmine < ch.ncols) {
-            const int zix = zi[ch.cbase + cmine];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) zreg[k] = k < a.nr ? zsrc[(int64_t)k * zstride + zix] : (Vv)0;
-        } else {
-#pragma unroll
-            for (int k = 0; k < NR; ++k) zreg[k] = (Vv)0;
-        }
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
-        const unsigned char* buf = stage + (size_t)s * STAGE_BYTES;
+        const unsigned char* stg = stage + (size_t)s * STRIDE;
+        const int64_t z0 = ch.zoff * a.nr;
+        const Vv* zb = (const Vv*)stg + (z0 - (z0 & ~(int64_t)(ZR::ALIGN - 1)));
+        const unsigned char* buf = stg + ZR::BYTES;
         const int rows = 3 * L.n;
-        for (int j = 0, c = w; c < ch.ncols; ++j, c += NCW) {
-            Vv zv[NR];
+        for (int c = w; c < ch.ncols; c += NCW) {
+            decltype(make_z(Vv(0))) zv[NR];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) zv[k] = __shfl_sync(0xffffffffu, zreg[k], j);
+            for (int k = 0; k < NR; ++k) zv[k] = make_z(k < a.nr ? zb[c * a.nr + k] : (Vv)0);
             if (ch.kind == 0) {
-                const float* col = (const float*)buf + (size_t)c * L.ld;
+                const float* col = (const float*)buf + (size_t)c * ch.ld;
 #pragma unroll
                 for (int ii = 0; ii < RPL; ++ii) {
                     const int r = lane + 32 * ii;
                     const float v = r < rows ? col[r] : 0.f;
 #pragma unroll
-                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, make_z(zv[k]));
+                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
                 }
             } else {
-                const C* col = (const C*)buf + (size_t)c * L.ld;
+                const C* col = (const C*)buf + (size_t)c * ch.ld;
 #pragma unroll
                 for (int ii = 0; ii < RPL; ++ii) {
                     const int r = lane + 32 * ii;
                     const float v = r < rows ? coef(col, r) : 0.f;
 #pragma unroll
-                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, make_z(zv[k]));
+                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
                 }
             }
         }
@@ -328,7 +347,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     if (cur >= 0) flush();
 }
 
-// ---- phase 1: P[pidx[c]] = V_t[:, c] . xc_t
+// ---- phase 1: P = V_t^T xc_t, one partial per V column
 template <int MODE, class C, int NR, int RPL, int NCW>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     using Acc = typename AccT<MODE>::type;
@@ -339,45 +358,38 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     unsigned char* stage = smem + BAR_BYTES;
 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full + s, 1);
-            mbar_init(empty + s, NCW);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
+    init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
     if (w == NCW) {
-        if (lane == 0) produce<C>(a, stage, full, empty, c0, c1);
+        if (lane == 0) produce<C, Vv, NR, false>(a, stage, STAGE_BYTES, full, empty, c0, c1);
         return;
     }
     const Vv* xc = (const Vv*)a.xc;
     Vv* P = (Vv*)a.out;
     int cur = -1;
-    LeafDesc L{};
+    int rows = 0;
     decltype(make_z(Vv(0))) xr[NR][RPL];
+    Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
     for (int i = c0; i < c1; ++i) {
+        const Chunk ch = nxt;
+        if (i + 1 < c1) nxt = a.chunks[i + 1];
         const int q = i - c0, s = q % STAGES;
-        const Chunk ch = a.chunks[i];
         if (ch.leaf != cur) {
             cur = ch.leaf;
-            L = a.leaves[cur];
-            const int rows = 3 * L.n;
+            const LeafDesc L = a.leaves[cur];
+            rows = 3 * L.n;
 #pragma unroll
-            for (int k = 0; k < NR; ++k)
+            for (int ii = 0; ii < RPL; ++ii) {
+                const int r = lane + 32 * ii;
 #pragma unroll
-                for (int ii = 0; ii < RPL; ++ii) {
-                    const int r = lane + 32 * ii;
-                    xr[k][ii] = make_z((r < rows && k < a.nr) ? xc[(int64_t)k * a.ndof + 3 * (int64_t)L.begin + r]
-                                                             : (Vv)0);
-                }
+                for (int k = 0; k < NR; ++k)
+                    xr[k][ii] = make_z((r < rows && k < a.nr) ? xc[(3 * (int64_t)L.begin + r) * a.nr + k] : (Vv)0);
+            }
         }
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
         const C* buf = (const C*)(stage + (size_t)s * STAGE_BYTES);
-        const int rows = 3 * L.n;
         for (int c = w; c < ch.ncols; c += NCW) {
-            const C* col = buf + (size_t)c * L.ld;
+            const C* col = buf + (size_t)c * ch.ld;
             Acc acc[NR];
 #pragma unroll
             for (int k = 0; k < NR; ++k) acc_zero(acc[k]);
@@ -388,17 +400,41 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) acc_fma(acc[k], v, xr[k][ii]);
             }
-            const int pi = a.v_pidx[ch.cbase + c];
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc_add(acc[k], acc_shfl(acc[k], o));
-                if (lane == 0 && k < a.nr) P[(int64_t)k * a.plen + pi] = (Vv)acc_value(acc[k]);
+                if (lane == 0 && k < a.nr) P[(ch.zoff + c) * a.nr + k] = (Vv)acc_value(acc[k]);
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
     }
+}
+
+constexpr int EV_PER_PRODUCT = 6;
+constexpr int EV_POOL = EV_PER_PRODUCT * 1024;
+
+void timing_accumulate(HMat& H) {
+    if (H.ev_used == 0) return;
+    HM_CUDA(cudaEventSynchronize(H.ev[H.ev_used - 1]));
+    for (int s = 0; s < H.ev_used; s += EV_PER_PRODUCT) {
+        for (int i = 0; i < 5; ++i) {
+            float ms = 0.f;
+            HM_CUDA(cudaEventElapsedTime(&ms, H.ev[s + i], H.ev[s + i + 1]));
+            H.t_acc[i] += ms;
+        }
+        ++H.t_count;
+    }
+    H.ev_used = 0;
+}
+
+// phase boundary idx (0 before the gather ... 5 after the scatter) of one product
+void mark(HMat& H, int idx, cudaStream_t st) {
+    if (!H.timing) return;
+    if (idx == 0 && H.ev_used + EV_PER_PRODUCT > (int)H.ev.size()) timing_accumulate(H);
+    HM_CUDA(cudaEventRecord(H.ev[H.ev_used + idx], st));
+    if (idx == EV_PER_PRODUCT - 1) H.ev_used += EV_PER_PRODUCT;
 }
 
 template <int MODE>
@@ -410,8 +446,10 @@ template <int MODE, class C, int NR, int RPL>
 void launch_phases(HMat& H, const StreamArgs& base, cudaStream_t st) {
     constexpr int NCW = ncw_for<MODE>(NR);
     using Acc = typename AccT<MODE>::type;
+    using V = typename AccT<MODE>::vec;
     const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES;
-    const size_t smem2 = smem1 + (size_t)NCW * 32 * RPL * sizeof(Acc);
+    const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
+                         (size_t)NCW * 32 * RPL * sizeof(Acc);
     if (H.n_far > 0 && H.p_len > 0) {
         StreamArgs a = base;
         a.chunks = H.ch1.p;
@@ -421,10 +459,14 @@ void launch_phases(HMat& H, const StreamArgs& base, cudaStream_t st) {
                                      (int)smem1));
         k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
         HM_LAUNCH_CHECK();
-        using V = typename AccT<MODE>::vec;
+        mark(H, 2, st);
         const unsigned nfb = (unsigned)ceil_div(H.n_far, 8);
-        k_reduce_tb<V><<<nfb, 256, 0, st>>>(H.far.p, H.n_far, (const V*)a.out, (V*)base.tb, H.p_len, H.tb_len, base.nr);
+        k_reduce_tb<V><<<nfb, 256, 0, st>>>(H.far.p, H.n_far, (const V*)a.out, (V*)base.tb, base.nr);
         HM_LAUNCH_CHECK();
+        mark(H, 3, st);
+    } else {
+        mark(H, 2, st);
+        mark(H, 3, st);
     }
     StreamArgs a = base;
     a.chunks = H.ch2.p;
@@ -433,6 +475,7 @@ void launch_phases(HMat& H, const StreamArgs& base, cudaStream_t st) {
                                  (int)smem2));
     k_phase2<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem2, st>>>(a);
     HM_LAUNCH_CHECK();
+    mark(H, 4, st);
 }
 
 template <int MODE, class C, int NR>
@@ -465,19 +508,24 @@ void build_product_plan(HMat& H, cudaStream_t st) {
     H.ld_max = 0;
     for (const LeafDesc& L : H.h_leaves) H.ld_max = std::max(H.ld_max, L.ld);
 
-    auto cut = [&](std::vector<Chunk>& out, std::vector<int64_t>& bytes, int leaf, int kind, int64_t src, int cbase,
-                   int ncols, int ld, int elem) {
-        // whole columns, at most one stage, at most 32 per consumer warp (8 warps)
-        const int per = std::max(1, std::min(256, STAGE_BYTES / (ld * elem)));
-        for (int c = 0; c < ncols; c += per) {
+    // cut a segment into chunks: runs of consecutive operand indices, bounded in size
+    auto cut = [&](std::vector<Chunk>& out, std::vector<int64_t>& bytes, int leaf, int kind, int64_t src,
+                   const std::vector<int32_t>& idx, int cbase, int ncols, int ld, int elem) {
+        const int per = std::max(1, std::min(MAX_CHUNK_COLS, STAGE_BYTES / (ld * elem)));
+        int c = 0;
+        while (c < ncols) {
+            int n = 1;
+            while (c + n < ncols && n < per && idx[cbase + c + n] == idx[cbase + c] + n) ++n;
             Chunk ch;
             ch.src = src + (int64_t)c * ld;
+            ch.zoff = idx[cbase + c];
             ch.leaf = leaf;
-            ch.cbase = cbase + c;
-            ch.ncols = std::min(per, ncols - c);
+            ch.ncols = n;
             ch.kind = kind;
+            ch.ld = ld;
             out.push_back(ch);
-            bytes.push_back((int64_t)ch.ncols * ld * elem);
+            bytes.push_back((int64_t)n * ld * elem);
+            c += n;
         }
     };
     auto split_ranges = [&](const std::vector<int64_t>& bytes, std::vector<int32_t>& cta) {
@@ -503,9 +551,9 @@ void build_product_plan(HMat& H, cudaStream_t st) {
     const int nl = H.n_leaves;
     for (int l = 0; l < nl; ++l) {
         const LeafDesc& L = H.h_leaves[l];
-        cut(c2, b2, l, 0, L.near_off, L.near_cbase, L.near_cols, L.ld, 4);
-        cut(c2, b2, l, 1, L.u_off, L.u_cbase, L.u_cols, L.ld, esz);
-        cut(c1, b1, l, 2, L.v_off, L.v_cbase, L.v_cols, L.ld, esz);
+        cut(c2, b2, l, 0, L.near_off, H.h_near_zidx, L.near_cbase, L.near_cols, L.ld, 4);
+        cut(c2, b2, l, 1, L.u_off, H.h_u_zidx, L.u_cbase, L.u_cols, L.ld, esz);
+        cut(c1, b1, l, 2, L.v_off, H.h_v_pidx, L.v_cbase, L.v_cols, L.ld, esz);
     }
     std::vector<int32_t> cta1, cta2;
     split_ranges(b1, cta1);
@@ -539,17 +587,25 @@ void build_product_plan(HMat& H, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
 }
 
-void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t) {
+void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t st) {
     if (nrhs <= H.nrhs_cap) return;
-    const int cap = nrhs <= 1 ? 1 : (nrhs <= 4 ? 4 : 16 * (int)ceil_div(nrhs, 16));
-    H.xc.alloc((size_t)H.ndof * cap);
-    H.yc.alloc((size_t)H.ndof * cap);
-    H.xcf.alloc((size_t)H.ndof * cap);
-    H.ycf.alloc((size_t)H.ndof * cap);
-    H.P.alloc((size_t)std::max<int64_t>(H.p_len, 1) * cap);
-    H.tb.alloc((size_t)std::max<int64_t>(H.tb_len, 1) * cap);
-    H.Pf.alloc((size_t)std::max<int64_t>(H.p_len, 1) * cap);
-    H.tbf.alloc((size_t)std::max<int64_t>(H.tb_len, 1) * cap);
+    const int cap = nrhs <= 1 ? 1 : (nrhs <= 4 ? 4 : 16);
+    const size_t nv = (size_t)H.ndof * cap + VEC_SLACK;
+    const size_t np = (size_t)std::max<int64_t>(H.p_len, 1) * cap + VEC_SLACK;
+    const size_t nt = (size_t)std::max<int64_t>(H.tb_len, 1) * cap + VEC_SLACK;
+    H.xc.alloc(nv);
+    H.yc.alloc(nv);
+    H.xcf.alloc(nv);
+    H.ycf.alloc(nv);
+    H.P.alloc(np);
+    H.tb.alloc(nt);
+    H.Pf.alloc(np);
+    H.tbf.alloc(nt);
+    // the slack read by rounded-up operand copies is never used, but keep it defined
+    HM_CUDA(cudaMemsetAsync(H.xc.p, 0, H.xc.bytes(), st));
+    HM_CUDA(cudaMemsetAsync(H.xcf.p, 0, H.xcf.bytes(), st));
+    HM_CUDA(cudaMemsetAsync(H.tb.p, 0, H.tb.bytes(), st));
+    HM_CUDA(cudaMemsetAsync(H.tbf.p, 0, H.tbf.bytes(), st));
     const size_t sl = (size_t)std::max(H.n_slots, 1) * 16 * std::max(H.ld_max, 1);
     H.slotsf.alloc(sl);
     H.slotsd.alloc(sl);
@@ -573,20 +629,17 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
         a.near = H.near.p;
         a.ucoef = bf ? (const void*)H.u16.p : (const void*)H.u32.p;
         a.vcoef = bf ? (const void*)H.v16.p : (const void*)H.v32.p;
-        a.near_zidx = H.near_zidx.p;
-        a.u_zidx = H.u_zidx.p;
-        a.v_pidx = H.v_pidx.p;
         a.counters = H.counters.p;
         a.err = H.err.p;
         a.ndof = H.ndof;
-        a.tblen = H.tb_len;
-        a.plen = H.p_len;
         a.nr = nr;
         a.ld_max = H.ld_max;
+        mark(H, 0, st);
         if (dtype == HM_F32) {
             const float* xf = (const float*)x + (int64_t)k0 * H.ndof;
             float* yf = (float*)y + (int64_t)k0 * H.ndof;
             k_gather<float><<<gb, 256, 0, st>>>(xf, H.xcf.p, H.perm.p, H.N, nr);
+            mark(H, 1, st);
             a.xc = H.xcf.p;
             a.tb = H.tbf.p;
             a.out = H.ycf.p;
@@ -600,6 +653,7 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
             const double* xd = (const double*)x + (int64_t)k0 * H.ndof;
             double* yd = (double*)y + (int64_t)k0 * H.ndof;
             k_gather<double><<<gb, 256, 0, st>>>(xd, H.xc.p, H.perm.p, H.N, nr);
+            mark(H, 1, st);
             a.xc = H.xc.p;
             a.tb = H.tb.p;
             a.out = H.yc.p;
@@ -611,7 +665,44 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
             k_scatter<double><<<gb, 256, 0, st>>>(H.yc.p, yd, H.perm.p, H.N, nr);
         }
         HM_LAUNCH_CHECK();
+        mark(H, 5, st);
     }
+}
+
+void matvec_host(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st) {
+    if (nrhs < 1) fail(HM_EINVAL, "matvec_host: nrhs must be >= 1");
+    if (!x || !y) fail(HM_EINVAL, "matvec_host: NULL vector");
+    if (dtype != HM_F32 && dtype != HM_F64) fail(HM_EINVAL, "matvec_host: dtype must be HM_F32 or HM_F64");
+    const size_t bytes = (size_t)H.ndof * nrhs * (dtype == HM_F32 ? 4 : 8);
+    if (H.xs.n < bytes) {
+        H.xs.alloc(bytes);
+        H.ys.alloc(bytes);
+    }
+    HM_CUDA(cudaMemcpyAsync(H.xs.p, x, bytes, cudaMemcpyHostToDevice, st));
+    matvec(H, H.xs.p, H.ys.p, nrhs, dtype, st);
+    HM_CUDA(cudaMemcpyAsync(y, H.ys.p, bytes, cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+}
+
+void timing_enable(HMat& H, bool on) {
+    if (on) {
+        if (H.ev.empty()) {
+            H.ev.resize(EV_POOL);
+            for (auto& e : H.ev) HM_CUDA(cudaEventCreate(&e));
+        }
+        for (double& t : H.t_acc) t = 0.0;
+        H.t_count = 0;
+        H.ev_used = 0;
+    } else {
+        timing_accumulate(H);
+    }
+    H.timing = on;
+}
+
+void timing_read(HMat& H, double out[6]) {
+    timing_accumulate(H);
+    for (int i = 0; i < 5; ++i) out[i] = H.t_acc[i];
+    out[5] = (double)H.t_count;
 }
 
 // Error flags raised by the product kernels since the last check (0 if none); clears them.

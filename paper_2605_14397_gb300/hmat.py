@@ -55,7 +55,9 @@ class hm_hmat_info(ctypes.Structure):
                 ("stored_bytes", ctypes.c_int64), ("algorithmic_bytes", ctypes.c_int64),
                 ("rank_min", ctypes.c_int32), ("rank_max", ctypes.c_int32), ("rank_mean", ctypes.c_double),
                 ("assemble_seconds", ctypes.c_double), ("storage", ctypes.c_int32), ("pad_", ctypes.c_int32),
-                ("n_far_lowrank", ctypes.c_int64), ("n_far_dense", ctypes.c_int64)]
+                ("n_far_lowrank", ctypes.c_int64), ("n_far_dense", ctypes.c_int64),
+                ("u_entries", ctypes.c_int64), ("v_entries", ctypes.c_int64), ("tb_len", ctypes.c_int64),
+                ("p_len", ctypes.c_int64)]
 
 
 _LIB = None
@@ -81,6 +83,9 @@ SIGNATURES = [
     ("hm_hmat_destroy", None, [_VP]),
     ("hm_matvec", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_hmat_check", _I, [_VP, _VP]),
+    ("hm_matvec_host", _I, [_VP, _VP, _VP, _I, _I, _VP]),
+    ("hm_hmat_timing", _I, [_VP, _I]),
+    ("hm_hmat_timing_read", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 
@@ -219,6 +224,23 @@ class HMatrix:
         assert y.dtype == x.dtype and x.is_contiguous() and y.is_contiguous()
         nrhs = 1 if x.dim() == 1 else x.shape[0]
         _check(lib().hm_matvec(self.handle, _dptr(x), _dptr(y), int(nrhs), dt, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def matvec_host(self, x, y, stream=None):
+        """y = E x for host numpy arrays (float32 or float64); synchronous."""
+        dt = {np.dtype(np.float32): HM_F32, np.dtype(np.float64): HM_F64}[x.dtype]
+        assert y.dtype == x.dtype and x.flags.c_contiguous and y.flags.c_contiguous
+        nrhs = 1 if x.ndim == 1 else x.shape[0]
+        _check(lib().hm_matvec_host(self.handle, x.ctypes.data_as(_VP), y.ctypes.data_as(_VP), int(nrhs), dt,
+                                    ctypes.c_void_p(_stream_ptr(stream))))
+
+    def timing(self, enable):
+        _check(lib().hm_hmat_timing(self.handle, 1 if enable else 0))
+
+    def timing_read(self):
+        """Milliseconds summed per phase: gather, phase1, reduce, phase2, scatter, count."""
+        out = (ctypes.c_double * 6)()
+        _check(lib().hm_hmat_timing_read(self.handle, out))
+        return dict(gather=out[0], phase1=out[1], reduce=out[2], phase2=out[3], scatter=out[4], count=int(out[5]))
 
     def check(self, stream=None):
         """Synchronise and raise HMError(HM_ETIMEOUT) if a product kernel gave up waiting."""

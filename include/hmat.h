@@ -79,6 +79,24 @@ hm_status hm_influence_blocks(const hm_elements* el, double E, double nu, int64_
                               const int64_t* ri_dev, const int64_t* sj_dev, double* out_dev,
                               void* stream);
 
+/* The same blocks without any device allocation, for callers that may not call
+ * cudaMalloc where they evaluate coefficients (a pooled or caching allocator that owns
+ * all device memory, a latency-critical path where cudaMalloc/cudaFree would
+ * synchronise the device, an embedding with a fixed memory budget).  The paper has no
+ * counterpart: it is an interface convenience of this library.
+ * The geometry is copied into one fixed scratch array in the library's device globals
+ * (8 MiB, held by every GPU that loads the library until the process exits), so N is
+ * limited to 65,536 elements; a larger N returns HM_EINVAL without touching the GPU.
+ * The first call on a device looks up that array's address (set-up once per device):
+ * make that first call before any stream capture.  Every call shares the array and
+ * leaves its contents behind; the error word is cleared at the start of each call.
+ * Calls that overlap on the GPU (from several threads or streams) race on the array.
+ * Arguments, outputs and errors are those of hm_influence_blocks; synchronises the
+ * stream. */
+hm_status hm_influence_blocks_noalloc(const hm_elements* el, double E, double nu, int64_t npairs,
+                                      const int64_t* ri_dev, const int64_t* sj_dev, double* out_dev,
+                                      void* stream);
+
 /* ---------------------------------------------------------------- cluster tree
  * Binary cluster tree over element centroids and the block partition (Sec. 3.1 relies
  * on an H-matrix; the rules are: split a cluster of more than leaf_size elements at the

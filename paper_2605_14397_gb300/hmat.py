@@ -72,6 +72,7 @@ SIGNATURES = [
     ("hm_last_error", ctypes.c_char_p, []),
     ("hm_version", ctypes.c_int, []),
     ("hm_influence_blocks", _I, [ctypes.POINTER(hm_elements), _D, _D, _I64, _VP, _VP, _VP, _VP]),
+    ("hm_influence_blocks_noalloc", _I, [ctypes.POINTER(hm_elements), _D, _D, _I64, _VP, _VP, _VP, _VP]),
     ("hm_build_cluster_tree", _I, [ctypes.POINTER(hm_elements), _I, _D, ctypes.POINTER(_VP)]),
     ("hm_tree_get_info", _I, [_VP, ctypes.POINTER(hm_tree_info)]),
     ("hm_tree_export", _I, [_VP, _P64, _P64, _P64, _P64, _P64, _P64, _P64]),
@@ -147,6 +148,16 @@ def influence_blocks(el, E, nu, ri, sj, out, stream=None):
     ea = _ElemArgs(el)
     _check(lib().hm_influence_blocks(ea.ref, float(E), float(nu), int(ri.numel()), _dptr(ri), _dptr(sj),
                                      _dptr(out), ctypes.c_void_p(_stream_ptr(stream))))
+
+
+def influence_blocks_noalloc(el, E, nu, ri, sj, out, stream=None):
+    """influence_blocks without device allocation: for callers that may not call
+    cudaMalloc (pooled allocators, latency-critical paths, fixed memory budgets).
+    Uses the library's fixed 8 MiB device scratch, so el.N <= 65,536; calls that overlap
+    on the GPU race on that scratch."""
+    ea = _ElemArgs(el)
+    _check(lib().hm_influence_blocks_noalloc(ea.ref, float(E), float(nu), int(ri.numel()), _dptr(ri), _dptr(sj),
+                                             _dptr(out), ctypes.c_void_p(_stream_ptr(stream))))
 
 
 class ClusterTree:

@@ -48,6 +48,7 @@ typedef int hm_status;
 #define HM_F32 1
 #define HM_F64 2
 #define HM_BF16 3
+#define HM_F32_BF16 4  /* storage: keep both FP32 and BF16 copies of the factors */
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* hm_last_error(void);
@@ -195,6 +196,55 @@ hm_status hm_matvec_host(const hm_hmat* h, const void* x_host, void* y_host, int
  * and out[5] the number of timed products. */
 hm_status hm_hmat_timing(const hm_hmat* h, int enable);
 hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
+
+/* ---------------------------------------------------------------- tangent solve
+ * Solve A x = b with A = E - diag(k) - shift I: the elastic block of the Jacobian
+ * (eq. jac_mech) with the interface tangent C^ep = diag(k) (isotropic interface
+ * stiffness K_s = K_n = k per element, Sec. 2.2) and the quasi-dynamic term
+ * eta/dt = shift (eq. ElasSystem).  The paper solves this A11 system with a Krylov
+ * method and a Jacobi preconditioner (Sec. 3.3.1); here: restarted flexible GMRES(m)
+ * with right preconditioning, classical Gram-Schmidt applied twice, Givens rotations,
+ * all Krylov vectors, dot products and rotations in FP64 on the device, x0 = 0.
+ *   precond HM_PRECOND_NONE, HM_PRECOND_BLOCKJ (inverse of every diagonal leaf block of
+ *   A, i.e. the point Jacobi of the paper taken per cluster-tree leaf), or
+ *   HM_PRECOND_LEARNED (block-Jacobi corrected by a trained network, see hm_lp_*).
+ *   mode HM_SOLVE_F64: every product with FP32 factors in compensated FP64 ("plain").
+ *   mode HM_SOLVE_MIXED: iterative refinement -- the residual b - A x in compensated
+ *   FP64 with the FP32 factors, corrections from FGMRES on the BF16-factor operator
+ *   with FP32 products to inner_tol (needs storage HM_F32_BF16).
+ * Converged when ||b - A x||_2 <= tol ||b||_2, recomputed in compensated FP64 with the
+ * FP32 factors.  k_dev: N doubles (per element, user order) or NULL; b_dev, x_dev:
+ * nrhs x 3N doubles, user order (x is overwritten); info: nrhs entries.  Synchronises
+ * the stream.  Returns HM_ENOCONV if a right-hand side did not converge within maxit. */
+#define HM_PRECOND_NONE 0
+#define HM_PRECOND_BLOCKJ 1
+#define HM_PRECOND_LEARNED 2
+#define HM_SOLVE_F64 1
+#define HM_SOLVE_MIXED 2
+
+typedef struct {
+    double tol;        /* relative residual target (0 = 1e-8) */
+    int restart;       /* Krylov dimension m (0 = 50) */
+    int maxit;         /* cap on the total Krylov iterations (0 = 2000) */
+    int precond;
+    int mode;
+    double inner_tol;  /* mixed: relative tolerance of each correction solve (0 = 1e-2) */
+    int max_outer;     /* mixed: cap on refinement steps (0 = 40) */
+    int pad_;
+} hm_solve_opts;
+
+typedef struct {
+    int iters;         /* Krylov iterations */
+    int outer;         /* restarts (F64) or refinement steps (mixed) */
+    int status;        /* HM_OK, HM_ENOCONV or HM_EBREAKDOWN */
+    int pad_;
+    double relres;     /* final ||b - A x|| / ||b|| (compensated FP64, FP32 factors) */
+    double seconds;
+} hm_solve_info;
+
+hm_status hm_gmres_solve(const hm_hmat* h, const double* k_dev, double shift, const double* b_dev,
+                         double* x_dev, int nrhs, const hm_solve_opts* opt, hm_solve_info* info,
+                         void* stream);
 
 /* Synchronise `stream` and report whether a device-side wait of an earlier product on
  * this H-matrix gave up (HM_ETIMEOUT; the flags are then cleared).  The product kernels

@@ -134,7 +134,8 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     const auto t0 = clk::now();
     if (!(opt.E > 0.0) || !(opt.nu > -1.0 && opt.nu < 0.5)) fail(HM_EINVAL, "assemble: need E > 0 and -1 < nu < 0.5");
     if (!(opt.aca_eps > 0.0 && opt.aca_eps < 1.0)) fail(HM_EINVAL, "assemble: aca_eps must be in (0, 1)");
-    if (opt.storage != HM_F32 && opt.storage != HM_BF16) fail(HM_EINVAL, "assemble: storage must be HM_F32 or HM_BF16");
+    if (opt.storage != HM_F32 && opt.storage != HM_BF16 && opt.storage != HM_F32_BF16)
+        fail(HM_EINVAL, "assemble: storage must be HM_F32, HM_BF16 or HM_F32_BF16");
     const int R = opt.max_rank > 0 ? opt.max_rank : 160;
     if (R > 256) fail(HM_EINVAL, "assemble: max_rank must be <= 256");
     if (T.leaf_size > 128) fail(HM_EINVAL, "assemble: leaf_size must be <= 128");
@@ -337,12 +338,14 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     std::vector<int32_t> near_zidx;
     int64_t near_len = 0;
     H.near_entries = 0;
+    H.h_self_off.assign(nl, -1);
     for (int l = 0; l < nl; ++l) {
         LeafDesc& L = H.h_leaves[l];
         L.near_off = near_len;
         L.near_cbase = (int32_t)near_zidx.size();
         int cols = 0;
         for (const DenseTile& D : tiles_by_row[l]) {
+            if (D.t_begin == L.begin && D.t_n == L.n) H.h_self_off[l] = near_len + (int64_t)cols * L.ld;
             NearJob J;
             J.s_begin = L.begin;
             J.s_n = L.n;
@@ -458,12 +461,14 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         L.v_cols = vcols;
         v_len += (int64_t)vcols * L.ld;
     }
-    if (H.storage == HM_F32) {
+    const bool want32 = has_factors(H, 0), want16 = has_factors(H, 1);
+    if (want32) {
         H.u32.alloc(std::max<int64_t>(u_len, 1));
         H.v32.alloc(std::max<int64_t>(v_len, 1));
         HM_CUDA(cudaMemsetAsync(H.u32.p, 0, H.u32.bytes(), st));
         HM_CUDA(cudaMemsetAsync(H.v32.p, 0, H.v32.bytes(), st));
-    } else {
+    }
+    if (want16) {
         H.u16.alloc(std::max<int64_t>(u_len, 1));
         H.v16.alloc(std::max<int64_t>(v_len, 1));
         HM_CUDA(cudaMemsetAsync(H.u16.p, 0, H.u16.bytes(), st));
@@ -474,9 +479,9 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         if (pj.empty()) continue;
         DevBuf<PackJob> d_p;
         d_p.upload(pj, st);
-        if (H.storage == HM_F32)
+        if (want32)
             k_pack<float><<<(unsigned)pj.size(), 256, 0, st>>>(H.facstore.p, d_p.p, pass == 0 ? H.u32.p : H.v32.p);
-        else
+        if (want16)
             k_pack<uint16_t><<<(unsigned)pj.size(), 256, 0, st>>>(H.facstore.p, d_p.p, pass == 0 ? H.u16.p : H.v16.p);
         HM_LAUNCH_CHECK();
         HM_CUDA(cudaStreamSynchronize(st));

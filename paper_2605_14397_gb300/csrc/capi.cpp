@@ -1,4 +1,5 @@
 // extern "C" boundary of libhmat: argument checks, handle ownership, status codes.
+#include <cmath>
 #include <cstring>
 #include <string>
 
@@ -193,6 +194,22 @@ hm_status hm_hmat_timing_read(const hm_hmat* hh, double* out6) {
     HM_API_BEGIN
     if (!hh || !out6) hm::fail(HM_EINVAL, "hmat_timing_read: NULL argument");
     hm::timing_read(const_cast<hm::HMat&>(hh->h), out6);
+    HM_API_END
+}
+
+hm_status hm_gmres_solve(const hm_hmat* hh, const double* k_dev, double shift, const double* b_dev, double* x_dev,
+                         int nrhs, const hm_solve_opts* opt, hm_solve_info* info, void* stream) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    if (!hh) hm::fail(HM_EINVAL, "gmres_solve: NULL H-matrix");
+    hm_solve_opts o{};
+    if (opt) o = *opt;
+    if (!opt) {
+        o.precond = HM_PRECOND_BLOCKJ;
+        o.mode = HM_SOLVE_F64;
+    }
+    if (!std::isfinite(shift)) hm::fail(HM_ENAN, "gmres_solve: shift is not finite");
+    hm::gmres_solve(const_cast<hm::HMat&>(hh->h), k_dev, shift, b_dev, x_dev, nrhs, o, info, (cudaStream_t)stream);
     HM_API_END
 }
 

@@ -70,7 +70,11 @@ struct LeafSplit {
     int32_t pad_;
 };
 
+struct SolveWS;                  // solver workspace (solve.cu)
+void solve_ws_free(SolveWS* w);
+
 struct HMat {
+    SolveWS* solve_ws = nullptr;
     int64_t N = 0, ndof = 0;
     double E = 1.0, nu = 0.25, eps = 1e-6;
     int storage = HM_F32;
@@ -97,15 +101,19 @@ struct HMat {
     // product chunks): xc index (near), tb index (U), partial index (V)
     std::vector<int32_t> h_near_zidx, h_u_zidx, h_v_pidx;
 
-    // persistent product plan
+    // persistent product plans: [0] with the FP32 factors, [1] with the BF16 factors
     int grid = 0;
     int ld_max = 0;
-    int n_slots = 0;
-    DevBuf<Chunk> ch1, ch2;
-    DevBuf<int32_t> cta1, cta2;
-    DevBuf<LeafSplit> split;
+    struct Plan {
+        bool ready = false;
+        int n_slots = 0;
+        DevBuf<Chunk> ch1, ch2;
+        DevBuf<int32_t> cta1, cta2;
+        DevBuf<LeafSplit> split;
+    } plan[2];
     DevBuf<int32_t> counters;
     DevBuf<int> err;
+    std::vector<int64_t> h_self_off;  // near-stream offset of each leaf's diagonal tile
     DevBuf<float> slotsf;
     DevBuf<double> slotsd;
 
@@ -122,6 +130,7 @@ struct HMat {
     HMat& operator=(const HMat&) = delete;
     ~HMat() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        solve_ws_free(solve_ws);
     }
 
     // product scratch, sized for nrhs_cap right-hand sides
@@ -145,5 +154,15 @@ void timing_enable(HMat& H, bool on);
 void timing_read(HMat& H, double out[6]);
 void matvec_host(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
+// Product on cluster-ordered operands: xc is RHS-interleaved (xc[dof * nr + k]) with at
+// least 32 readable elements after its end, yc is RHS-major (yc[k * ndof + dof]).
+// fac: 0 FP32 factors, 1 BF16 factors.  dtype HM_F32: float vectors; HM_F64: double.
+void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st);
+void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
+                 const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st);
+inline bool has_factors(const HMat& H, int fac) {
+    return fac == 0 ? (H.storage == HM_F32 || H.storage == HM_F32_BF16)
+                    : (H.storage == HM_BF16 || H.storage == HM_F32_BF16);
+}
 
 }  // namespace hm

@@ -443,7 +443,7 @@ constexpr int ncw_for(int NR) {
 }
 
 template <int MODE, class C, int NR, int RPL>
-void launch_phases(HMat& H, const StreamArgs& base, cudaStream_t st) {
+void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool timed, cudaStream_t st) {
     constexpr int NCW = ncw_for<MODE>(NR);
     using Acc = typename AccT<MODE>::type;
     using V = typename AccT<MODE>::vec;
@@ -452,51 +452,87 @@ void launch_phases(HMat& H, const StreamArgs& base, cudaStream_t st) {
                          (size_t)NCW * 32 * RPL * sizeof(Acc);
     if (H.n_far > 0 && H.p_len > 0) {
         StreamArgs a = base;
-        a.chunks = H.ch1.p;
-        a.cta_begin = H.cta1.p;
+        a.chunks = PL.ch1.p;
+        a.cta_begin = PL.cta1.p;
         a.out = MODE == 0 ? (void*)H.Pf.p : (void*)H.P.p;
         HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem1));
         k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
         HM_LAUNCH_CHECK();
-        mark(H, 2, st);
+        if (timed) mark(H, 2, st);
         const unsigned nfb = (unsigned)ceil_div(H.n_far, 8);
         k_reduce_tb<V><<<nfb, 256, 0, st>>>(H.far.p, H.n_far, (const V*)a.out, (V*)base.tb, base.nr);
         HM_LAUNCH_CHECK();
-        mark(H, 3, st);
-    } else {
+        if (timed) mark(H, 3, st);
+    } else if (timed) {
         mark(H, 2, st);
         mark(H, 3, st);
     }
     StreamArgs a = base;
-    a.chunks = H.ch2.p;
-    a.cta_begin = H.cta2.p;
+    a.chunks = PL.ch2.p;
+    a.cta_begin = PL.cta2.p;
+    a.split = PL.split.p;
     HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem2));
     k_phase2<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem2, st>>>(a);
     HM_LAUNCH_CHECK();
-    mark(H, 4, st);
+    if (timed) mark(H, 4, st);
 }
 
 template <int MODE, class C, int NR>
-void launch_rpl(HMat& H, const StreamArgs& a, cudaStream_t st) {
+void launch_rpl(HMat& H, const HMat::Plan& PL, const StreamArgs& a, bool timed, cudaStream_t st) {
     if (H.ld_max <= 192)
-        launch_phases<MODE, C, NR, 6>(H, a, st);
+        launch_phases<MODE, C, NR, 6>(H, PL, a, timed, st);
     else
-        launch_phases<MODE, C, NR, 12>(H, a, st);
+        launch_phases<MODE, C, NR, 12>(H, PL, a, timed, st);
 }
 
 template <int MODE, class C>
-void launch_nr(HMat& H, const StreamArgs& a, int nrhs, cudaStream_t st) {
+void launch_nr(HMat& H, const HMat::Plan& PL, const StreamArgs& a, int nrhs, bool timed, cudaStream_t st) {
     if (nrhs == 1)
-        launch_rpl<MODE, C, 1>(H, a, st);
+        launch_rpl<MODE, C, 1>(H, PL, a, timed, st);
     else if (nrhs <= 4)
-        launch_rpl<MODE, C, 4>(H, a, st);
+        launch_rpl<MODE, C, 4>(H, PL, a, timed, st);
     else
-        launch_rpl<MODE, C, 16>(H, a, st);
+        launch_rpl<MODE, C, 16>(H, PL, a, timed, st);
+}
+
+// phase 1, reduction and phase 2 on cluster-ordered operands (see hmat_impl.h)
+void run_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, bool timed, cudaStream_t st) {
+    if (!has_factors(H, fac)) fail(HM_EINVAL, "product: the requested factor precision is not stored");
+    const HMat::Plan& PL = H.plan[fac];
+    StreamArgs a{};
+    a.leaves = H.leaves.p;
+    a.near = H.near.p;
+    a.ucoef = fac == 1 ? (const void*)H.u16.p : (const void*)H.u32.p;
+    a.vcoef = fac == 1 ? (const void*)H.v16.p : (const void*)H.v32.p;
+    a.counters = H.counters.p;
+    a.err = H.err.p;
+    a.ndof = H.ndof;
+    a.nr = nr;
+    a.ld_max = H.ld_max;
+    a.xc = xc;
+    a.out = yc;
+    if (dtype == HM_F32) {
+        a.tb = H.tbf.p;
+        a.slots = H.slotsf.p;
+        if (fac == 1)
+            launch_nr<0, uint16_t>(H, PL, a, nr, timed, st);
+        else
+            launch_nr<0, float>(H, PL, a, nr, timed, st);
+    } else {
+        a.tb = H.tb.p;
+        a.slots = H.slotsd.p;
+        if (fac == 1)
+            launch_nr<1, uint16_t>(H, PL, a, nr, timed, st);
+        else
+            launch_nr<1, float>(H, PL, a, nr, timed, st);
+    }
 }
 
 }  // namespace
+
+void build_plan_for(HMat& H, HMat::Plan& PLAN, int esz, int G, cudaStream_t st);
 
 void build_product_plan(HMat& H, cudaStream_t st) {
     int dev = 0, nsm = 0;
@@ -504,9 +540,17 @@ void build_product_plan(HMat& H, cudaStream_t st) {
     HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     H.grid = std::max(1, nsm);
     const int G = H.grid;
-    const int esz = H.storage == HM_BF16 ? 2 : 4;
     H.ld_max = 0;
     for (const LeafDesc& L : H.h_leaves) H.ld_max = std::max(H.ld_max, L.ld);
+    for (int fac = 0; fac < 2; ++fac)
+        if (has_factors(H, fac)) build_plan_for(H, H.plan[fac], fac == 1 ? 2 : 4, G, st);
+    H.counters.alloc(H.n_leaves);
+    HM_CUDA(cudaMemsetAsync(H.counters.p, 0, H.counters.bytes(), st));
+    H.err.alloc(1);
+    HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
+}
+
+void build_plan_for(HMat& H, HMat::Plan& PLAN, int esz, int G, cudaStream_t st) {
 
     // cut a segment into chunks: runs of consecutive operand indices, bounded in size
     auto cut = [&](std::vector<Chunk>& out, std::vector<int64_t>& bytes, int leaf, int kind, int64_t src,
@@ -575,16 +619,13 @@ void build_product_plan(HMat& H, cudaStream_t st) {
         sp[l].slot_base = sp[l].nparts > 1 ? slots : 0;
         if (sp[l].nparts > 1) slots += sp[l].nparts;
     }
-    H.n_slots = slots;
-    H.ch1.upload(c1, st);
-    H.ch2.upload(c2, st);
-    H.cta1.upload(cta1, st);
-    H.cta2.upload(cta2, st);
-    H.split.upload(sp, st);
-    H.counters.alloc(nl);
-    HM_CUDA(cudaMemsetAsync(H.counters.p, 0, H.counters.bytes(), st));
-    H.err.alloc(1);
-    HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
+    PLAN.n_slots = slots;
+    PLAN.ch1.upload(c1, st);
+    PLAN.ch2.upload(c2, st);
+    PLAN.cta1.upload(cta1, st);
+    PLAN.cta2.upload(cta2, st);
+    PLAN.split.upload(sp, st);
+    PLAN.ready = true;
 }
 
 void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t st) {
@@ -606,10 +647,18 @@ void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(H.xcf.p, 0, H.xcf.bytes(), st));
     HM_CUDA(cudaMemsetAsync(H.tb.p, 0, H.tb.bytes(), st));
     HM_CUDA(cudaMemsetAsync(H.tbf.p, 0, H.tbf.bytes(), st));
-    const size_t sl = (size_t)std::max(H.n_slots, 1) * 16 * std::max(H.ld_max, 1);
+    int slots = 1;
+    for (const HMat::Plan& p : H.plan) slots = std::max(slots, p.n_slots);
+    const size_t sl = (size_t)slots * 16 * std::max(H.ld_max, 1);
     H.slotsf.alloc(sl);
     H.slotsd.alloc(sl);
     H.nrhs_cap = cap;
+}
+
+void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st) {
+    if (nr < 1 || nr > 16) fail(HM_EINVAL, "product: 1 to 16 right-hand sides per pass");
+    ensure_product_scratch(H, nr, st);
+    run_core(H, xc, yc, nr, dtype, fac, false, st);
 }
 
 void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st) {
@@ -617,51 +666,26 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
     if (!x || !y) fail(HM_EINVAL, "matvec: NULL vector");
     if (dtype != HM_F32 && dtype != HM_F64) fail(HM_EINVAL, "matvec: dtype must be HM_F32 or HM_F64");
     ensure_product_scratch(H, std::min(nrhs, 16), st);
-    const bool bf = H.storage == HM_BF16;
+    const int fac = has_factors(H, 0) ? 0 : 1;  // FP32 factors when stored
     // at most 16 right-hand sides per pass of the coefficient streams
     for (int k0 = 0; k0 < nrhs; k0 += 16) {
         const int nr = std::min(16, nrhs - k0);
         const int64_t tot = H.ndof * nr;
         const unsigned gb = (unsigned)ceil_div(tot, 256);
-        StreamArgs a{};
-        a.leaves = H.leaves.p;
-        a.split = H.split.p;
-        a.near = H.near.p;
-        a.ucoef = bf ? (const void*)H.u16.p : (const void*)H.u32.p;
-        a.vcoef = bf ? (const void*)H.v16.p : (const void*)H.v32.p;
-        a.counters = H.counters.p;
-        a.err = H.err.p;
-        a.ndof = H.ndof;
-        a.nr = nr;
-        a.ld_max = H.ld_max;
         mark(H, 0, st);
         if (dtype == HM_F32) {
             const float* xf = (const float*)x + (int64_t)k0 * H.ndof;
             float* yf = (float*)y + (int64_t)k0 * H.ndof;
             k_gather<float><<<gb, 256, 0, st>>>(xf, H.xcf.p, H.perm.p, H.N, nr);
             mark(H, 1, st);
-            a.xc = H.xcf.p;
-            a.tb = H.tbf.p;
-            a.out = H.ycf.p;
-            a.slots = H.slotsf.p;
-            if (bf)
-                launch_nr<0, uint16_t>(H, a, nr, st);
-            else
-                launch_nr<0, float>(H, a, nr, st);
+            run_core(H, H.xcf.p, H.ycf.p, nr, dtype, fac, true, st);
             k_scatter<float><<<gb, 256, 0, st>>>(H.ycf.p, yf, H.perm.p, H.N, nr);
         } else {
             const double* xd = (const double*)x + (int64_t)k0 * H.ndof;
             double* yd = (double*)y + (int64_t)k0 * H.ndof;
             k_gather<double><<<gb, 256, 0, st>>>(xd, H.xc.p, H.perm.p, H.N, nr);
             mark(H, 1, st);
-            a.xc = H.xc.p;
-            a.tb = H.tb.p;
-            a.out = H.yc.p;
-            a.slots = H.slotsd.p;
-            if (bf)
-                launch_nr<1, uint16_t>(H, a, nr, st);
-            else
-                launch_nr<1, float>(H, a, nr, st);
+            run_core(H, H.xc.p, H.yc.p, nr, dtype, fac, true, st);
             k_scatter<double><<<gb, 256, 0, st>>>(H.yc.p, yd, H.perm.p, H.N, nr);
         }
         HM_LAUNCH_CHECK();

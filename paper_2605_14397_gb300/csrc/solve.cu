@@ -1,0 +1,796 @@
+// Tangent solve A x = b, A = E - diag(k) - shift I (eq. jac_mech with C^ep = diag(k),
+// eta/dt = shift): restarted flexible GMRES(m) with right preconditioning, on the device.
+//
+// The paper solves its A11 system with a Krylov method (BiCGSTAB or GMRES) and a Jacobi
+// preconditioner (Sec. 3.3.1).  Here:
+//   * Krylov vectors, Hessenberg matrix, Gram-Schmidt and Givens rotations in FP64;
+//     Arnoldi by classical Gram-Schmidt applied twice (CGS2); x0 = 0;
+//   * flexible variant (the preconditioned vectors z_j = M^-1 v_j are kept), so the
+//     preconditioner may be inexact, FP32, or nonlinear (the learned correction);
+//   * block-Jacobi preconditioner: the inverse of every diagonal leaf block of A,
+//     from the stored FP32 near-field tile minus the diagonal, by Gauss-Jordan with
+//     partial pivoting in shared memory (FP32);
+//   * every kernel of a restart cycle reads a per-RHS `done` flag set by the Givens step
+//     when the residual estimate meets the tolerance, so a cycle of m iterations is
+//     launched without host synchronisation; the host synchronises once per cycle;
+//   * mode F64: products with the FP32 factors in compensated FP64 throughout;
+//     mode MIXED: iterative refinement (outer residual in compensated FP64 with the
+//     FP32 factors; corrections by FGMRES on the BF16-factor operator, FP32 products).
+// Vectors are kept in cluster order internally (RHS-major, stride 3N).
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "hmat_impl.h"
+
+namespace hm {
+
+namespace {
+
+constexpr int ROW_NT = 256;
+constexpr int ROWS_PER_CTA = 1024;  // 4 rows per thread
+constexpr int VSLACK = 64;          // elements after each buffer read by rounded copies
+constexpr int BJ_MAX_ROWS_SMEM = 224;
+
+struct CycleState {
+    int done;     // 1: stop iterating this RHS in the current cycle
+    int iters;    // iterations completed in the current cycle
+    int brk;      // breakdown seen
+    int pad_;
+    double tol;   // absolute tolerance on the residual estimate
+    double inv;   // 1 / ||w|| of the last step
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- permutation, diagonal
+
+__global__ void k_to_cluster(const double* __restrict__ u, double* __restrict__ c, const int32_t* __restrict__ perm,
+                             int64_t ndof, int nr) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t k = q / ndof, r = q % ndof;
+    c[q] = u[k * ndof + 3 * (int64_t)perm[r / 3] + r % 3];
+}
+
+__global__ void k_to_user(const double* __restrict__ c, double* __restrict__ u, const int32_t* __restrict__ perm,
+                          int64_t ndof, int nr) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t k = q / ndof, r = q % ndof;
+    u[k * ndof + 3 * (int64_t)perm[r / 3] + r % 3] = c[q];
+}
+
+__global__ void k_diag(const double* __restrict__ kel, double shift, const int32_t* __restrict__ perm, int64_t ndof,
+                       double* __restrict__ d) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= ndof) return;
+    d[r] = (kel ? kel[perm[r / 3]] : 0.0) + shift;
+}
+
+// ---------------------------------------------------------------- block-Jacobi
+
+// Inverse of B = E_ll - diag(d_l) for every leaf l (one CTA each), Gauss-Jordan with
+// partial pivoting; B^-1 stored column-major with the leaf's padded row count.
+__global__ void __launch_bounds__(512) k_bj_build(const LeafDesc* __restrict__ leaves,
+                                                  const int64_t* __restrict__ self_off,
+                                                  const float* __restrict__ near, const double* __restrict__ d,
+                                                  float* __restrict__ binv, const int64_t* __restrict__ binv_off,
+                                                  float* __restrict__ gscratch, int use_smem, int* __restrict__ err) {
+    extern __shared__ float sm[];
+    const LeafDesc L = leaves[blockIdx.x];
+    const int n = 3 * L.n;
+    float* A = use_smem ? sm : gscratch + binv_off[blockIdx.x];  // row-major n x n
+    __shared__ float colk[384];
+    __shared__ int piv[384];
+    __shared__ float s_v[16];
+    __shared__ int s_i[16];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float* E = near + self_off[blockIdx.x];
+    for (int q = tid; q < n * n; q += nt) {
+        const int r = q / n, c = q % n;
+        float v = E[(int64_t)c * L.ld + r];
+        if (r == c) v -= (float)d[3 * (int64_t)L.begin + r];
+        A[q] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        // pivot: largest |A[i][k]|, i >= k
+        float bv = -1.f;
+        int bi = k;
+        for (int i = k + tid; i < n; i += nt) {
+            const float v = fabsf(A[i * n + k]);
+            if (v > bv) { bv = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { s_v[tid >> 5] = bv; s_i[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            float b = -1.f;
+            int ib = k;
+            for (int w = 0; w < nt / 32; ++w)
+                if (s_v[w] > b || (s_v[w] == b && s_i[w] < ib)) { b = s_v[w]; ib = s_i[w]; }
+            piv[k] = ib;
+            if (!(b > 0.f)) atomicOr(err, 1);
+        }
+        __syncthreads();
+        const int p = piv[k];
+        if (p != k)
+            for (int c = tid; c < n; c += nt) {
+                const float t = A[k * n + c];
+                A[k * n + c] = A[p * n + c];
+                A[p * n + c] = t;
+            }
+        __syncthreads();
+        const float pv = A[k * n + k];
+        const float pinv = pv != 0.f ? 1.f / pv : 0.f;
+        for (int i = tid; i < n; i += nt) colk[i] = A[i * n + k];
+        __syncthreads();
+        for (int c = tid; c < n; c += nt) A[k * n + c] = (c == k ? 1.f : A[k * n + c]) * pinv;
+        __syncthreads();
+        for (int q = tid; q < n * n; q += nt) {
+            const int i = q / n, c = q % n;
+            if (i == k) continue;
+            A[q] = (c == k ? 0.f : A[q]) - A[k * n + c] * colk[i];
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges by column interchanges, last first
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = piv[k];
+        if (p != k)
+            for (int i = tid; i < n; i += nt) {
+                const float t = A[i * n + k];
+                A[i * n + k] = A[i * n + p];
+                A[i * n + p] = t;
+            }
+        __syncthreads();
+    }
+    float* out = binv + binv_off[blockIdx.x];
+    for (int q = tid; q < n * n; q += nt) {
+        const int r = q / n, c = q % n;
+        out[(int64_t)c * L.ld + r] = A[q];
+    }
+}
+
+// z = M^-1 v per leaf (block-Jacobi), or z = v; also the FP32 copy zf (RHS-interleaved)
+__global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ leaves, const float* __restrict__ binv,
+                                                  const int64_t* __restrict__ binv_off, const double* __restrict__ v,
+                                                  double* __restrict__ z, float* __restrict__ zf, int64_t ndof, int nr,
+                                                  const CycleState* __restrict__ cs, int identity) {
+    __shared__ double red[8][384];
+    const LeafDesc L = leaves[blockIdx.x];
+    const int n = 3 * L.n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = 3 * (int64_t)L.begin;
+    for (int k = 0; k < nr; ++k) {
+        if (cs[k].done) continue;
+        const double* vk = v + k * ndof + base;
+        double* zk = z + k * ndof + base;
+        if (identity) {
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                zk[r] = vk[r];
+                if (zf) zf[(base + r) * nr + k] = (float)vk[r];
+            }
+            continue;
+        }
+        const float* B = binv + binv_off[blockIdx.x];
+        double acc[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+        for (int c = w; c < n; c += 8) {
+            const double vc = vk[c];
+            const float* col = B + (int64_t)c * L.ld;
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const int r = lane + 32 * i;
+                if (r < n) acc[i] += (double)col[r] * vc;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            const int r = lane + 32 * i;
+            if (r < 384) red[w][r] = acc[i];
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            double s = 0.0;
+            for (int q = 0; q < 8; ++q) s += red[q][r];
+            zk[r] = s;
+            if (zf) zf[(base + r) * nr + k] = (float)s;
+        }
+        __syncthreads();
+    }
+}
+
+// interleave a set of FP64 vectors for the product: out[dof * nr + k] = in[k * ndof + dof]
+__global__ void k_interleave(const double* __restrict__ in, double* __restrict__ out, int64_t ndof, int nr) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t r = q / nr, k = q % nr;
+    out[q] = in[k * ndof + r];
+}
+
+__global__ void k_to_f32_interleaved(const double* __restrict__ in, float* __restrict__ out, int64_t ndof, int nr) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t r = q / nr, k = q % nr;
+    out[q] = (float)in[k * ndof + r];
+}
+
+// ---------------------------------------------------------------- Arnoldi (CGS2)
+
+template <class Y>
+__device__ __forceinline__ double yval(const Y* y, int64_t i) { return (double)y[i]; }
+
+// pass 1: w = y - d .* z (stored), partial dots with V_0..V_j
+template <class Y>
+__global__ void __launch_bounds__(ROW_NT) k_arn_first(const Y* __restrict__ y, const double* __restrict__ d,
+                                                      const double* __restrict__ z, double* __restrict__ w,
+                                                      const double* __restrict__ V, int64_t ndof, int nr, int j,
+                                                      int64_t vstride, double* __restrict__ part,
+                                                      const CycleState* __restrict__ cs) {
+    __shared__ double sp[ROW_NT / 32][132];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * ROWS_PER_CTA;
+    for (int k = 0; k < nr; ++k) {
+        if (cs[k].done) continue;
+        double wl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = r0 + threadIdx.x + u * ROW_NT;
+            double v = 0.0;
+            if (i < ndof) {
+                v = yval(y, k * ndof + i) - d[i] * z[k * ndof + i];
+                w[k * ndof + i] = v;
+            }
+            wl[u] = v;
+        }
+        for (int jj = 0; jj <= j; ++jj) {
+            const double* Vj = V + ((int64_t)jj * nr + k) * vstride;
+            double s = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = r0 + threadIdx.x + u * ROW_NT;
+                if (i < ndof) s += Vj[i] * wl[u];
+            }
+            s = warp_sum_d(s);
+            if (lane == 0) sp[wp][jj] = s;
+        }
+        __syncthreads();
+        for (int jj = threadIdx.x; jj <= j; jj += ROW_NT) {
+            double s = 0.0;
+            for (int q = 0; q < ROW_NT / 32; ++q) s += sp[q][jj];
+            part[((int64_t)blockIdx.x * nr + k) * 132 + jj] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// sum the per-CTA partials: out[k][jj] = sum_b part[b][k][jj]
+__global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int nr, int nvals, double* __restrict__ out,
+                               const CycleState* __restrict__ cs) {
+    const int k = blockIdx.x;
+    if (cs[k].done) return;
+    for (int jj = threadIdx.x; jj < nvals; jj += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[((int64_t)b * nr + k) * 132 + jj];
+        out[k * 132 + jj] = s;
+    }
+}
+
+// w -= V h (h = previous dots); then either partial dots with V (second pass) or
+// the partial squared norm of w (last pass)
+__global__ void __launch_bounds__(ROW_NT) k_arn_update(double* __restrict__ w, const double* __restrict__ V,
+                                                       const double* __restrict__ h, int64_t ndof, int nr, int j,
+                                                       int64_t vstride, double* __restrict__ part, int want_dots,
+                                                       const CycleState* __restrict__ cs) {
+    __shared__ double sp[ROW_NT / 32][132];
+    __shared__ double sh[132];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * ROWS_PER_CTA;
+    for (int k = 0; k < nr; ++k) {
+        if (cs[k].done) continue;
+        for (int jj = threadIdx.x; jj <= j; jj += ROW_NT) sh[jj] = h[k * 132 + jj];
+        __syncthreads();
+        double wl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = r0 + threadIdx.x + u * ROW_NT;
+            double v = 0.0;
+            if (i < ndof) {
+                v = w[k * ndof + i];
+                for (int jj = 0; jj <= j; ++jj) v -= V[((int64_t)jj * nr + k) * vstride + i] * sh[jj];
+                w[k * ndof + i] = v;
+            }
+            wl[u] = v;
+        }
+        if (want_dots) {
+            for (int jj = 0; jj <= j; ++jj) {
+                const double* Vj = V + ((int64_t)jj * nr + k) * vstride;
+                double s = 0.0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t i = r0 + threadIdx.x + u * ROW_NT;
+                    if (i < ndof) s += Vj[i] * wl[u];
+                }
+                s = warp_sum_d(s);
+                if (lane == 0) sp[wp][jj] = s;
+            }
+        } else {
+            double s = wl[0] * wl[0] + wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
+            s = warp_sum_d(s);
+            if (lane == 0) sp[wp][0] = s;
+        }
+        __syncthreads();
+        const int nv = want_dots ? j + 1 : 1;
+        for (int jj = threadIdx.x; jj < nv; jj += ROW_NT) {
+            double s = 0.0;
+            for (int q = 0; q < ROW_NT / 32; ++q) s += sp[q][jj];
+            part[((int64_t)blockIdx.x * nr + k) * 132 + jj] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Hessenberg column j, Givens rotation, residual estimate, convergence and breakdown
+__global__ void k_givens(const double* __restrict__ h1, const double* __restrict__ h2, const double* __restrict__ part,
+                         int nblk, int nr, int j, int m, double* __restrict__ Hm, double* __restrict__ cs_,
+                         double* __restrict__ sn_, double* __restrict__ g, CycleState* __restrict__ st) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr || st[k].done) return;
+    double nrm2 = 0.0;
+    for (int b = 0; b < nblk; ++b) nrm2 += part[((int64_t)b * nr + k) * 132];
+    const double hn = sqrt(nrm2);
+    double* col = Hm + ((int64_t)k * m + j) * (m + 1);
+    double* c = cs_ + (int64_t)k * (m + 1);
+    double* s = sn_ + (int64_t)k * (m + 1);
+    double* gk = g + (int64_t)k * (m + 1);
+    double hsum = 0.0;
+    for (int i = 0; i <= j; ++i) {
+        col[i] = h1[k * 132 + i] + h2[k * 132 + i];
+        hsum += col[i] * col[i];
+    }
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = c[i] * col[i] + s[i] * col[i + 1];
+        col[i + 1] = -s[i] * col[i] + c[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    st[k].iters = j + 1;
+    if (!(den > 0.0) || !isfinite(den)) {
+        st[k].brk = 1;
+        st[k].done = 1;
+        st[k].iters = j;  // this column cannot be used
+        return;
+    }
+    c[j] = col[j] / den;
+    s[j] = col[j + 1] / den;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    gk[j + 1] = -s[j] * gk[j];
+    gk[j] = c[j] * gk[j];
+    st[k].inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    // converged estimate, or the Krylov space became invariant (happy breakdown)
+    if (fabs(gk[j + 1]) <= st[k].tol || hn <= 1e-14 * sqrt(hsum + nrm2)) st[k].done = 1;
+    if (j + 1 >= m) st[k].done = 1;
+}
+
+__global__ void k_scale_next(const double* __restrict__ w, double* __restrict__ V, int64_t ndof, int nr, int j,
+                             int64_t vstride, const CycleState* __restrict__ st) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t k = q / ndof, i = q % ndof;
+    if (st[k].done && st[k].iters < j + 1) return;  // stopped before this step
+    if (j + 1 > 0) V[((int64_t)(j + 1) * nr + k) * vstride + i] = w[q] * st[k].inv;
+}
+
+// start of a cycle: v0 = r / beta, g = beta e1
+__global__ void k_cycle_start(const double* __restrict__ r, double* __restrict__ V, int64_t ndof, int nr,
+                              int64_t vstride, const double* __restrict__ beta, int m, double* __restrict__ g) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < (int64_t)nr * (m + 1)) g[q] = (q % (m + 1) == 0) ? beta[q / (m + 1)] : 0.0;
+    if (q >= ndof * nr) return;
+    const int64_t k = q / ndof, i = q % ndof;
+    const double b = beta[k];
+    V[k * vstride + i] = b > 0.0 ? r[q] / b : 0.0;
+}
+
+// y = H^-1 g (upper triangular, iters x iters), x += Z y
+__global__ void k_lsq(const double* __restrict__ Hm, const double* __restrict__ g, double* __restrict__ y, int nr,
+                      int m, const CycleState* __restrict__ st, const int* __restrict__ active) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr) return;
+    const int n = active[k] ? st[k].iters : 0;
+    double* yk = y + (int64_t)k * (m + 1);
+    for (int i = n - 1; i >= 0; --i) {
+        double s = g[(int64_t)k * (m + 1) + i];
+        for (int l = i + 1; l < n; ++l) s -= Hm[((int64_t)k * m + l) * (m + 1) + i] * yk[l];
+        const double dgl = Hm[((int64_t)k * m + i) * (m + 1) + i];
+        yk[i] = dgl != 0.0 ? s / dgl : 0.0;
+    }
+    for (int i = n; i <= m; ++i) yk[i] = 0.0;
+}
+
+__global__ void k_update_x(double* __restrict__ x, const double* __restrict__ Z, const double* __restrict__ y,
+                           int64_t ndof, int nr, int m, int64_t vstride, const CycleState* __restrict__ st,
+                           const int* __restrict__ active) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t k = q / ndof, i = q % ndof;
+    if (!active[k]) return;
+    const int n = st[k].iters;
+    double s = x[q];
+    for (int l = 0; l < n; ++l) s += Z[((int64_t)l * nr + k) * vstride + i] * y[k * (m + 1) + l];
+    x[q] = s;
+}
+
+// r = b - (y - d .* x), partial ||r||^2
+template <class Y>
+__global__ void __launch_bounds__(ROW_NT) k_residual(const double* __restrict__ b, const Y* __restrict__ y,
+                                                     const double* __restrict__ d, const double* __restrict__ x,
+                                                     double* __restrict__ r, int64_t ndof, int nr,
+                                                     double* __restrict__ part) {
+    __shared__ double sp[ROW_NT / 32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * ROWS_PER_CTA;
+    for (int k = 0; k < nr; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = r0 + threadIdx.x + u * ROW_NT;
+            if (i < ndof) {
+                const int64_t q = k * ndof + i;
+                const double v = b[q] - (yval(y, q) - d[i] * x[q]);
+                r[q] = v;
+                s += v * v;
+            }
+        }
+        s = warp_sum_d(s);
+        if (lane == 0) sp[wp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < ROW_NT / 32; ++q) t += sp[q];
+            part[(int64_t)blockIdx.x * nr + k] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) x[q] += d[q];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- workspace
+
+struct SolveWS {
+    int nr = 0, m = 0;
+    int64_t ndof = 0, vstride = 0;
+    DevBuf<double> V, Z, w, r, xc, bc, dc, corr, y64, zi, Hm, cs, sn, g, ylsq, part, h1, h2;
+    DevBuf<float> zf, y32, binv, bjscratch;
+    DevBuf<int64_t> binv_off, self_off;
+    DevBuf<CycleState> st;
+    DevBuf<int> active, err;
+    int64_t binv_len = 0;
+    bool bj_needs_global = false;
+};
+
+void solve_ws_free(SolveWS* w) { delete w; }
+
+namespace {
+
+int nblk_rows(int64_t ndof) { return (int)ceil_div(ndof, ROWS_PER_CTA); }
+
+SolveWS& workspace(HMat& H, int nr, int m, cudaStream_t st) {
+    if (!H.solve_ws) H.solve_ws = new SolveWS();
+    SolveWS& W = *H.solve_ws;
+    if (W.nr >= nr && W.m >= m && W.ndof == H.ndof) return W;
+    W.nr = std::max(W.nr, nr);
+    W.m = std::max(W.m, m);
+    W.ndof = H.ndof;
+    W.vstride = H.ndof;
+    const int64_t vn = (int64_t)W.nr * H.ndof;
+    W.V.alloc((size_t)(W.m + 1) * vn + VSLACK);
+    W.Z.alloc((size_t)W.m * vn + VSLACK);
+    W.w.alloc(vn + VSLACK);
+    W.r.alloc(vn + VSLACK);
+    W.xc.alloc(vn + VSLACK);
+    W.bc.alloc(vn + VSLACK);
+    W.corr.alloc(vn + VSLACK);
+    W.y64.alloc(vn + VSLACK);
+    W.zi.alloc(vn + VSLACK);
+    W.dc.alloc(H.ndof + VSLACK);
+    W.zf.alloc(vn + VSLACK);
+    W.y32.alloc(vn + VSLACK);
+    HM_CUDA(cudaMemsetAsync(W.zf.p, 0, W.zf.bytes(), st));
+    HM_CUDA(cudaMemsetAsync(W.zi.p, 0, W.zi.bytes(), st));
+    HM_CUDA(cudaMemsetAsync(W.V.p, 0, W.V.bytes(), st));
+    HM_CUDA(cudaMemsetAsync(W.Z.p, 0, W.Z.bytes(), st));
+    W.Hm.alloc((size_t)W.nr * W.m * (W.m + 1));
+    W.cs.alloc((size_t)W.nr * (W.m + 1));
+    W.sn.alloc((size_t)W.nr * (W.m + 1));
+    W.g.alloc((size_t)W.nr * (W.m + 1));
+    W.ylsq.alloc((size_t)W.nr * (W.m + 1));
+    const int nb = nblk_rows(H.ndof);
+    W.part.alloc((size_t)nb * W.nr * 132);
+    W.h1.alloc((size_t)W.nr * 132);
+    W.h2.alloc((size_t)W.nr * 132);
+    W.st.alloc(W.nr);
+    W.active.alloc(W.nr);
+    W.err.alloc(1);
+    // block-Jacobi layout: one ld x n block per leaf
+    std::vector<int64_t> off(H.n_leaves);
+    int64_t len = 0;
+    bool glob = false;
+    for (int l = 0; l < H.n_leaves; ++l) {
+        off[l] = len;
+        len += (int64_t)H.h_leaves[l].ld * 3 * H.h_leaves[l].n;
+        if (3 * H.h_leaves[l].n > BJ_MAX_ROWS_SMEM) glob = true;
+    }
+    W.binv_len = len;
+    W.binv.alloc(std::max<int64_t>(len, 1));
+    W.binv_off.upload(off, st);
+    W.self_off.upload(H.h_self_off, st);
+    W.bj_needs_global = glob;
+    if (glob) W.bjscratch.alloc(std::max<int64_t>(len, 1));
+    return W;
+}
+
+unsigned g1(int64_t n) { return (unsigned)ceil_div(std::max<int64_t>(n, 1), 256); }
+
+// y = A_op z for the Arnoldi step / residual: the product part (E z); the diagonal is
+// applied by the consumer kernel.  dtype F64: compensated, input z (FP64); F32: input zf.
+void apply_E(HMat& H, SolveWS& W, const double* z64, const float* z32, void* y, int nr, int dtype, int fac,
+             cudaStream_t st) {
+    if (dtype == HM_F64) {
+        const double* in = z64;
+        if (nr > 1) {
+            k_interleave<<<g1(H.ndof * nr), 256, 0, st>>>(z64, W.zi.p, H.ndof, nr);
+            in = W.zi.p;
+        }
+        product_core(H, in, y, nr, HM_F64, fac, st);
+    } else {
+        product_core(H, z32, y, nr, HM_F32, fac, st);
+    }
+}
+
+struct CycleResult {
+    std::vector<int> iters;
+    std::vector<int> brk;
+};
+
+// One restart cycle of FGMRES on (E - diag d): rhs r (cluster order), solution x updated
+// in place; beta[k] = ||r_k||; tol_abs[k] the target on the residual estimate.
+CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double* tol_abs, const int* active_h,
+                         int nr, int m, int dtype, int fac, bool precond, cudaStream_t st) {
+    const int64_t n = H.ndof;
+    const int nb = nblk_rows(n);
+    std::vector<CycleState> cs(nr);
+    for (int k = 0; k < nr; ++k) {
+        cs[k].done = active_h[k] ? 0 : 1;
+        cs[k].iters = 0;
+        cs[k].brk = 0;
+        cs[k].pad_ = 0;
+        cs[k].tol = tol_abs[k];
+        cs[k].inv = 0.0;
+    }
+    HM_CUDA(cudaMemcpyAsync(W.st.p, cs.data(), nr * sizeof(CycleState), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(W.active.p, active_h, nr * sizeof(int), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(W.h1.p, beta_h, nr * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_cycle_start<<<g1(std::max<int64_t>(n * nr, (int64_t)nr * (m + 1))), 256, 0, st>>>(W.r.p, W.V.p, n, nr,
+                                                                                      W.vstride, W.h1.p, m, W.g.p);
+    HM_LAUNCH_CHECK();
+    for (int j = 0; j < m; ++j) {
+        const double* vj = W.V.p + (int64_t)j * nr * W.vstride;
+        double* zj = W.Z.p + (int64_t)j * nr * W.vstride;
+        k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, vj, zj,
+                                               dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p, precond ? 0 : 1);
+        HM_LAUNCH_CHECK();
+        if (dtype == HM_F64) {
+            apply_E(H, W, zj, nullptr, W.y64.p, nr, HM_F64, fac, st);
+            k_arn_first<double><<<nb, ROW_NT, 0, st>>>(W.y64.p, W.dc.p, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
+                                                       W.part.p, W.st.p);
+        } else {
+            apply_E(H, W, nullptr, W.zf.p, W.y32.p, nr, HM_F32, fac, st);
+            k_arn_first<float><<<nb, ROW_NT, 0, st>>>(W.y32.p, W.dc.p, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
+                                                      W.part.p, W.st.p);
+        }
+        HM_LAUNCH_CHECK();
+        k_reduce_parts<<<nr, 128, 0, st>>>(W.part.p, nb, nr, j + 1, W.h1.p, W.st.p);
+        k_arn_update<<<nb, ROW_NT, 0, st>>>(W.w.p, W.V.p, W.h1.p, n, nr, j, W.vstride, W.part.p, 1, W.st.p);
+        k_reduce_parts<<<nr, 128, 0, st>>>(W.part.p, nb, nr, j + 1, W.h2.p, W.st.p);
+        k_arn_update<<<nb, ROW_NT, 0, st>>>(W.w.p, W.V.p, W.h2.p, n, nr, j, W.vstride, W.part.p, 0, W.st.p);
+        k_givens<<<1, 32, 0, st>>>(W.h1.p, W.h2.p, W.part.p, nb, nr, j, m, W.Hm.p, W.cs.p, W.sn.p, W.g.p, W.st.p);
+        k_scale_next<<<g1(n * nr), 256, 0, st>>>(W.w.p, W.V.p, n, nr, j, W.vstride, W.st.p);
+        HM_LAUNCH_CHECK();
+    }
+    k_lsq<<<1, 32, 0, st>>>(W.Hm.p, W.g.p, W.ylsq.p, nr, m, W.st.p, W.active.p);
+    k_update_x<<<g1(n * nr), 256, 0, st>>>(W.xc.p, W.Z.p, W.ylsq.p, n, nr, m, W.vstride, W.st.p, W.active.p);
+    HM_LAUNCH_CHECK();
+    HM_CUDA(cudaMemcpyAsync(cs.data(), W.st.p, nr * sizeof(CycleState), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    CycleResult res;
+    for (int k = 0; k < nr; ++k) {
+        res.iters.push_back(active_h[k] ? cs[k].iters : 0);
+        res.brk.push_back(cs[k].brk);
+    }
+    return res;
+}
+
+// r = rhs - (E - diag d) x with the given product; returns ||r_k|| on the host
+std::vector<double> residual(HMat& H, SolveWS& W, const double* rhs, int nr, int dtype, int fac, cudaStream_t st) {
+    const int64_t n = H.ndof;
+    const int nb = nblk_rows(n);
+    if (dtype == HM_F64) {
+        apply_E(H, W, W.xc.p, nullptr, W.y64.p, nr, HM_F64, fac, st);
+        k_residual<double><<<nb, ROW_NT, 0, st>>>(rhs, W.y64.p, W.dc.p, W.xc.p, W.r.p, n, nr, W.part.p);
+    } else {
+        // FP32 copy of x, interleaved, for the FP32 product
+        k_to_f32_interleaved<<<g1(n * nr), 256, 0, st>>>(W.xc.p, W.zf.p, n, nr);
+        apply_E(H, W, nullptr, W.zf.p, W.y32.p, nr, HM_F32, fac, st);
+        k_residual<float><<<nb, ROW_NT, 0, st>>>(rhs, W.y32.p, W.dc.p, W.xc.p, W.r.p, n, nr, W.part.p);
+    }
+    HM_LAUNCH_CHECK();
+    std::vector<double> part((size_t)nb * nr);
+    HM_CUDA(cudaMemcpyAsync(part.data(), W.part.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> out(nr, 0.0);
+    for (int k = 0; k < nr; ++k) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)b * nr + k];
+        out[k] = std::sqrt(s);
+    }
+    return out;
+}
+
+// FGMRES(m) with restarts on rhs (cluster order) into W.xc (initial value kept);
+// stops at ||rhs - A x_k|| <= tol_abs[k] or when the iteration budget is spent.
+// Returns per RHS the iterations used and the final residual norm.
+void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& tol_abs, int nr, int m, int max_its,
+            int max_cycles, int dtype, int fac, bool precond, std::vector<int>& its, std::vector<double>& rn,
+            std::vector<int>& brk, cudaStream_t st) {
+    its.assign(nr, 0);
+    brk.assign(nr, 0);
+    rn = residual(H, W, rhs, nr, dtype, fac, st);
+    for (int cyc = 0; cyc < max_cycles; ++cyc) {
+        std::vector<int> active(nr, 0);
+        bool any = false;
+        for (int k = 0; k < nr; ++k) {
+            active[k] = (rn[k] > tol_abs[k] && its[k] < max_its && !brk[k]) ? 1 : 0;
+            any = any || active[k];
+        }
+        if (!any) break;
+        int mm = m;
+        for (int k = 0; k < nr; ++k)
+            if (active[k]) mm = std::min(mm, std::max(1, max_its - its[k]));
+        CycleResult cr = fgmres_cycle(H, W, rn.data(), tol_abs.data(), active.data(), nr, mm, dtype, fac, precond, st);
+        for (int k = 0; k < nr; ++k) {
+            its[k] += cr.iters[k];
+            if (cr.brk[k] && cr.iters[k] == 0) brk[k] = 1;
+        }
+        rn = residual(H, W, rhs, nr, dtype, fac, st);
+    }
+}
+
+}  // namespace
+
+void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
+                 const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st) {
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    if (nrhs < 1 || nrhs > 16) fail(HM_EINVAL, "gmres_solve: 1 to 16 right-hand sides");
+    if (!b || !x) fail(HM_EINVAL, "gmres_solve: NULL vector");
+    const double tol = o.tol > 0 ? o.tol : 1e-8;
+    const int m = o.restart > 0 ? o.restart : 50;
+    if (m > 128) fail(HM_EINVAL, "gmres_solve: restart must be <= 128");
+    const int maxit = o.maxit > 0 ? o.maxit : 2000;
+    const int mode = o.mode ? o.mode : HM_SOLVE_F64;
+    if (mode != HM_SOLVE_F64 && mode != HM_SOLVE_MIXED) fail(HM_EINVAL, "gmres_solve: unknown mode");
+    if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ)
+        fail(HM_EINVAL, "gmres_solve: preconditioner not available in this call");
+    if (!has_factors(H, 0)) fail(HM_EINVAL, "gmres_solve: the FP32 factors are required (storage F32 or F32_BF16)");
+    const int inner_fac = has_factors(H, 1) ? 1 : 0;
+    SolveWS& W = workspace(H, nrhs, m, st);
+    const int64_t n = H.ndof;
+    const int nb = nblk_rows(n);
+    (void)nb;
+    k_diag<<<g1(n), 256, 0, st>>>(kel, shift, H.perm.p, n, W.dc.p);
+    k_to_cluster<<<g1(n * nrhs), 256, 0, st>>>(b, W.bc.p, H.perm.p, n, nrhs);
+    HM_LAUNCH_CHECK();
+    const bool precond = o.precond == HM_PRECOND_BLOCKJ;
+    if (precond) {
+        HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
+        const size_t smem = W.bj_needs_global ? 0 : sizeof(float) * BJ_MAX_ROWS_SMEM * BJ_MAX_ROWS_SMEM;
+        if (smem > 48 * 1024)
+            HM_CUDA(cudaFuncSetAttribute(k_bj_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_bj_build<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.binv.p,
+                                                  W.binv_off.p, W.bjscratch.p, W.bj_needs_global ? 0 : 1, W.err.p);
+        HM_LAUNCH_CHECK();
+        int e = 0;
+        HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        if (e) fail(HM_EBREAKDOWN, "gmres_solve: a diagonal leaf block of A is singular");
+    }
+    // ||b||
+    HM_CUDA(cudaMemsetAsync(W.xc.p, 0, (size_t)n * nrhs * sizeof(double), st));
+    std::vector<double> bn = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st);  // x = 0: r = b
+    std::vector<double> tol_abs(nrhs);
+    for (int k = 0; k < nrhs; ++k) tol_abs[k] = tol * bn[k];
+    std::vector<int> its(nrhs, 0), outer(nrhs, 0), brk(nrhs, 0);
+    std::vector<double> rn = bn;
+    if (mode == HM_SOLVE_F64) {
+        fgmres(H, W, W.bc.p, tol_abs, nrhs, m, maxit, 1 << 20, HM_F64, 0, precond, its, rn, brk, st);
+        for (int k = 0; k < nrhs; ++k) outer[k] = (its[k] + m - 1) / m;
+    } else {
+        const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-2;
+        const int max_outer = o.max_outer > 0 ? o.max_outer : 40;
+        // x accumulates in W.xc; the correction solve runs on a saved copy
+        DevBuf<double> xacc((size_t)n * nrhs);
+        HM_CUDA(cudaMemsetAsync(xacc.p, 0, xacc.bytes(), st));
+        std::vector<double> rr = bn;  // ||b - A x|| with the FP32 factors, compensated
+        for (int it = 0; it < max_outer; ++it) {
+            bool any = false;
+            for (int k = 0; k < nrhs; ++k) any = any || (rr[k] > tol_abs[k] && its[k] < maxit);
+            if (!any) break;
+            // outer residual into W.r (current x in xacc)
+            HM_CUDA(cudaMemcpyAsync(W.xc.p, xacc.p, xacc.bytes(), cudaMemcpyDeviceToDevice, st));
+            rr = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st);
+            bool need = false;
+            for (int k = 0; k < nrhs; ++k) need = need || (rr[k] > tol_abs[k] && its[k] < maxit);
+            if (!need) break;
+            // correction: FGMRES on the BF16-factor operator, FP32 products, from 0
+            HM_CUDA(cudaMemcpyAsync(W.corr.p, W.r.p, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    st));
+            HM_CUDA(cudaMemsetAsync(W.xc.p, 0, (size_t)n * nrhs * sizeof(double), st));
+            std::vector<double> itol_abs(nrhs);
+            for (int k = 0; k < nrhs; ++k) itol_abs[k] = rr[k] > tol_abs[k] ? itol * rr[k] : 1e300;
+            std::vector<int> iits, ibrk;
+            std::vector<double> irn;
+            fgmres(H, W, W.corr.p, itol_abs, nrhs, m, maxit, 4, HM_F32, inner_fac, precond, iits, irn, ibrk, st);
+            for (int k = 0; k < nrhs; ++k) {
+                its[k] += iits[k];
+                if (iits[k] > 0) outer[k]++;
+            }
+            k_axpy<<<g1(n * nrhs), 256, 0, st>>>(xacc.p, W.xc.p, n * nrhs);
+            HM_LAUNCH_CHECK();
+        }
+        HM_CUDA(cudaMemcpyAsync(W.xc.p, xacc.p, xacc.bytes(), cudaMemcpyDeviceToDevice, st));
+        rn = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st);
+    }
+    k_to_user<<<g1(n * nrhs), 256, 0, st>>>(W.xc.p, x, H.perm.p, n, nrhs);
+    HM_LAUNCH_CHECK();
+    HM_CUDA(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(clk::now() - t0).count();
+    bool all_ok = true, any_brk = false;
+    for (int k = 0; k < nrhs; ++k) {
+        const double rel = bn[k] > 0 ? rn[k] / bn[k] : 0.0;
+        const bool ok = rel <= tol;
+        all_ok = all_ok && ok;
+        any_brk = any_brk || (brk[k] && !ok);
+        if (info) {
+            info[k].iters = its[k];
+            info[k].outer = outer[k];
+            info[k].status = ok ? HM_OK : (brk[k] ? HM_EBREAKDOWN : HM_ENOCONV);
+            info[k].pad_ = 0;
+            info[k].relres = rel;
+            info[k].seconds = secs;
+        }
+    }
+    if (any_brk) fail(HM_EBREAKDOWN, "gmres_solve: Krylov breakdown before the tolerance");
+    if (!all_ok) fail(HM_ENOCONV, "gmres_solve: tolerance not reached within maxit");
+}
+
+}  // namespace hm

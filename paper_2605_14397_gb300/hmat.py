@@ -21,7 +21,9 @@ HM_ENOCONV = -5
 HM_EBREAKDOWN = -6
 HM_ENAN = -7
 HM_ETIMEOUT = -8
-HM_F32, HM_F64, HM_BF16 = 1, 2, 3
+HM_F32, HM_F64, HM_BF16, HM_F32_BF16 = 1, 2, 3, 4
+HM_PRECOND_NONE, HM_PRECOND_BLOCKJ, HM_PRECOND_LEARNED = 0, 1, 2
+HM_SOLVE_F64, HM_SOLVE_MIXED = 1, 2
 
 _STATUS_NAMES = {HM_EINVAL: "HM_EINVAL", HM_ENOMEM: "HM_ENOMEM", HM_ECUDA: "HM_ECUDA",
                  HM_ESINGULAR_GEOM: "HM_ESINGULAR_GEOM", HM_ENOCONV: "HM_ENOCONV",
@@ -60,6 +62,17 @@ class hm_hmat_info(ctypes.Structure):
                 ("p_len", ctypes.c_int64)]
 
 
+class hm_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("precond", ctypes.c_int), ("mode", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int)]
+
+
+class hm_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("status", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
 _LIB = None
 
 # (name, restype, argtypes) of every exported entry point declared in include/hmat.h
@@ -87,6 +100,8 @@ SIGNATURES = [
     ("hm_matvec_host", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_hmat_timing", _I, [_VP, _I]),
     ("hm_hmat_timing_read", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    ("hm_gmres_solve", _I, [_VP, _VP, _D, _VP, _VP, _I, ctypes.POINTER(hm_solve_opts),
+                            ctypes.POINTER(hm_solve_info), _VP]),
 ]
 
 
@@ -198,7 +213,7 @@ class ClusterTree:
 
 class HMatrix:
     def __init__(self, tree, el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", max_rank=0, stream=None):
-        st = {"f32": HM_F32, "bf16": HM_BF16}[storage]
+        st = {"f32": HM_F32, "bf16": HM_BF16, "both": HM_F32_BF16}[storage]
         ea = _ElemArgs(el) if el is not None else None
         opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, int(max_rank))
         h = ctypes.c_void_p()
@@ -243,6 +258,23 @@ class HMatrix:
         nrhs = 1 if x.ndim == 1 else x.shape[0]
         _check(lib().hm_matvec_host(self.handle, x.ctypes.data_as(_VP), y.ctypes.data_as(_VP), int(nrhs), dt,
                                     ctypes.c_void_p(_stream_ptr(stream))))
+
+    def solve(self, b, x, k=None, shift=0.0, tol=1e-8, restart=50, maxit=2000, precond="blockj", mode="f64",
+              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True):
+        """Solve (E - diag(k) - shift I) x = b on the device (b, x: float64 CUDA tensors of
+        shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None).  Returns the
+        per-RHS info dicts; raises HMError unless every RHS converged (raise_on_error)."""
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        o = hm_solve_opts(float(tol), int(restart), int(maxit),
+                          {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "learned": HM_PRECOND_LEARNED}[precond],
+                          {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED}[mode], float(inner_tol), int(max_outer), 0)
+        info = (hm_solve_info * nrhs)()
+        st = lib().hm_gmres_solve(self.handle, _dptr(k) if k is not None else None, float(shift), _dptr(b), _dptr(x),
+                                  int(nrhs), ctypes.byref(o), info, ctypes.c_void_p(_stream_ptr(stream)))
+        out = [{f: getattr(i, f) for f, _ in hm_solve_info._fields_ if f != "pad_"} for i in info]
+        if st != HM_OK and raise_on_error:
+            raise HMError(st, lib().hm_last_error().decode())
+        return out
 
     def timing(self, enable):
         _check(lib().hm_hmat_timing(self.handle, 1 if enable else 0))

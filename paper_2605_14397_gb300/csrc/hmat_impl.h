@@ -157,7 +157,8 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
 // Product on cluster-ordered operands: xc is RHS-interleaved (xc[dof * nr + k]) with at
 // least 32 readable elements after its end, yc is RHS-major (yc[k * ndof + dof]).
 // fac: 0 FP32 factors, 1 BF16 factors.  dtype HM_F32: float vectors; HM_F64: double.
-void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st);
+void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st,
+                  const int* skip = nullptr);
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st);
 inline bool has_factors(const HMat& H, int fac) {

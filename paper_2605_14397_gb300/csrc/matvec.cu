@@ -133,19 +133,53 @@ __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int
     y[k * ndof + 3 * (int64_t)perm[p] + m] = yc[q];
 }
 
-// tb[(tb_off + l) nr + k] = sum_q P[(pbase + q r + l) nr + k]
+// tb[(tb_off + l) nr + k] = sum_q P[(pbase + q r + l) nr + k], one CTA (128 threads) per
+// block: the n = r nr entries times G = 128 / n interleaved groups of leaf partials,
+// four independent loads in flight per thread, groups combined in a fixed order.
 template <class V>
-__global__ void k_reduce_tb(const FarDesc* __restrict__ far, int64_t nfar, const V* __restrict__ P, V* __restrict__ tb,
-                            int nrhs) {
-    const int64_t b = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= nfar) return;
-    const FarDesc F = far[b];
+__global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const V* __restrict__ P,
+                                                   V* __restrict__ tb, int nrhs, const int* __restrict__ skip) {
+    __shared__ V sp[128];
+    if (skip && *(volatile const int*)skip) return;
+    const FarDesc F = far[blockIdx.x];
     const int n = F.rank * nrhs;
-    for (int e = lane; e < n; e += 32) {
+    if (n == 0) return;
+    const int64_t base = F.pbase * nrhs;
+    const int64_t step = (int64_t)F.rank * nrhs;  // distance between leaf partials
+    if (n >= 128) {
+        for (int e = threadIdx.x; e < n; e += 128) {
+            V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            int q = 0;
+            for (; q + 3 < F.n_tleaves; q += 4) {
+                s0 += P[base + q * step + e];
+                s1 += P[base + (q + 1) * step + e];
+                s2 += P[base + (q + 2) * step + e];
+                s3 += P[base + (q + 3) * step + e];
+            }
+            for (; q < F.n_tleaves; ++q) s0 += P[base + q * step + e];
+            tb[F.tb_off * nrhs + e] = (s0 + s1) + (s2 + s3);
+        }
+        return;
+    }
+    const int G = 128 / n;
+    const int e = threadIdx.x % n, g = threadIdx.x / n;
+    V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    if (g < G) {
+        int q = g;
+        for (; q + 3 * G < F.n_tleaves; q += 4 * G) {
+            s0 += P[base + q * step + e];
+            s1 += P[base + (q + G) * step + e];
+            s2 += P[base + (q + 2 * G) * step + e];
+            s3 += P[base + (q + 3 * G) * step + e];
+        }
+        for (; q < F.n_tleaves; q += G) s0 += P[base + q * step + e];
+    }
+    sp[threadIdx.x] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (threadIdx.x < n) {
         V s = 0;
-        for (int q = 0; q < F.n_tleaves; ++q) s += P[(F.pbase + (int64_t)q * F.rank) * nrhs + e];
-        tb[F.tb_off * nrhs + e] = s;
+        for (int q = 0; q < G; ++q) s += sp[q * n + threadIdx.x];
+        tb[F.tb_off * nrhs + threadIdx.x] = s;
     }
 }
 
@@ -166,6 +200,7 @@ struct StreamArgs {
     int64_t ndof;
     int nr;       // right-hand sides in this launch (<= NR); also the interleave stride
     int ld_max;
+    const int* skip;  // optional device flag: when set, the kernels return at once
 };
 
 template <class V, int NR>
@@ -242,6 +277,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     unsigned char* stage = smem + BAR_BYTES;
     Acc* red = (Acc*)(stage + (size_t)STAGES * STRIDE);  // [NCW][32 RPL]
 
+    if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
@@ -357,6 +393,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     uint64_t* empty = full + STAGES;
     unsigned char* stage = smem + BAR_BYTES;
 
+    if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
@@ -450,18 +487,27 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES;
     const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
                          (size_t)NCW * 32 * RPL * sizeof(Acc);
+    // shared-memory opt-in, once per device for each instantiation
+    static bool attr_done[64] = {};
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem1));
+        HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem2));
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
     if (H.n_far > 0 && H.p_len > 0) {
         StreamArgs a = base;
         a.chunks = PL.ch1.p;
         a.cta_begin = PL.cta1.p;
         a.out = MODE == 0 ? (void*)H.Pf.p : (void*)H.P.p;
-        HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem1));
         k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
-        const unsigned nfb = (unsigned)ceil_div(H.n_far, 8);
-        k_reduce_tb<V><<<nfb, 256, 0, st>>>(H.far.p, H.n_far, (const V*)a.out, (V*)base.tb, base.nr);
+        k_reduce_tb<V><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, (const V*)a.out, (V*)base.tb, base.nr,
+                                                          base.skip);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 3, st);
     } else if (timed) {
@@ -472,8 +518,6 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     a.chunks = PL.ch2.p;
     a.cta_begin = PL.cta2.p;
     a.split = PL.split.p;
-    HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem2));
     k_phase2<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem2, st>>>(a);
     HM_LAUNCH_CHECK();
     if (timed) mark(H, 4, st);
@@ -498,7 +542,8 @@ void launch_nr(HMat& H, const HMat::Plan& PL, const StreamArgs& a, int nrhs, boo
 }
 
 // phase 1, reduction and phase 2 on cluster-ordered operands (see hmat_impl.h)
-void run_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, bool timed, cudaStream_t st) {
+void run_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, bool timed, cudaStream_t st,
+              const int* skip = nullptr) {
     if (!has_factors(H, fac)) fail(HM_EINVAL, "product: the requested factor precision is not stored");
     const HMat::Plan& PL = H.plan[fac];
     StreamArgs a{};
@@ -511,6 +556,7 @@ void run_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, boo
     a.ndof = H.ndof;
     a.nr = nr;
     a.ld_max = H.ld_max;
+    a.skip = skip;
     a.xc = xc;
     a.out = yc;
     if (dtype == HM_F32) {
@@ -655,10 +701,10 @@ void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t st) {
     H.nrhs_cap = cap;
 }
 
-void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st) {
+void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st, const int* skip) {
     if (nr < 1 || nr > 16) fail(HM_EINVAL, "product: 1 to 16 right-hand sides per pass");
     ensure_product_scratch(H, nr, st);
-    run_core(H, xc, yc, nr, dtype, fac, false, st);
+    run_core(H, xc, yc, nr, dtype, fac, false, st, skip);
 }
 
 void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st) {

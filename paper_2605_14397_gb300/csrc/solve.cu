@@ -182,17 +182,18 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
             }
             continue;
         }
+        // FP32 arithmetic: the flexible Krylov method tolerates an inexact preconditioner
         const float* B = binv + binv_off[blockIdx.x];
-        double acc[12];
+        float acc[12];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+        for (int i = 0; i < 12; ++i) acc[i] = 0.f;
         for (int c = w; c < n; c += 8) {
-            const double vc = vk[c];
+            const float vc = (float)vk[c];
             const float* col = B + (int64_t)c * L.ld;
 #pragma unroll
             for (int i = 0; i < 12; ++i) {
                 const int r = lane + 32 * i;
-                if (r < n) acc[i] += (double)col[r] * vc;
+                if (r < n) acc[i] = fmaf(__ldg(col + r), vc, acc[i]);
             }
         }
 #pragma unroll
@@ -342,11 +343,10 @@ __global__ void __launch_bounds__(ROW_NT) k_arn_update(double* __restrict__ w, c
 }
 
 // Hessenberg column j, Givens rotation, residual estimate, convergence and breakdown
-__global__ void k_givens(const double* __restrict__ h1, const double* __restrict__ h2, const double* __restrict__ part,
-                         int nblk, int nr, int j, int m, double* __restrict__ Hm, double* __restrict__ cs_,
-                         double* __restrict__ sn_, double* __restrict__ g, CycleState* __restrict__ st) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nr || st[k].done) return;
+__device__ void givens_one(int k, const double* __restrict__ h1, const double* __restrict__ h2,
+                           const double* __restrict__ part, int nblk, int nr, int j, int m, double* __restrict__ Hm,
+                           double* __restrict__ cs_, double* __restrict__ sn_, double* __restrict__ g,
+                           CycleState* __restrict__ st) {
     double nrm2 = 0.0;
     for (int b = 0; b < nblk; ++b) nrm2 += part[((int64_t)b * nr + k) * 132];
     const double hn = sqrt(nrm2);
@@ -385,13 +385,29 @@ __global__ void k_givens(const double* __restrict__ h1, const double* __restrict
     if (j + 1 >= m) st[k].done = 1;
 }
 
+// one thread per right-hand side; *alldone = every RHS stopped (the product kernels of
+// the remaining steps of the cycle then return at once)
+__global__ void k_givens(const double* __restrict__ h1, const double* __restrict__ h2, const double* __restrict__ part,
+                         int nblk, int nr, int j, int m, double* __restrict__ Hm, double* __restrict__ cs_,
+                         double* __restrict__ sn_, double* __restrict__ g, CycleState* __restrict__ st,
+                         int* __restrict__ alldone) {
+    const int k = threadIdx.x;
+    if (k < nr && !st[k].done) givens_one(k, h1, h2, part, nblk, nr, j, m, Hm, cs_, sn_, g, st);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int all = 1;
+        for (int q = 0; q < nr; ++q) all &= st[q].done;
+        *alldone = all;
+    }
+}
+
 __global__ void k_scale_next(const double* __restrict__ w, double* __restrict__ V, int64_t ndof, int nr, int j,
                              int64_t vstride, const CycleState* __restrict__ st) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= ndof * nr) return;
     const int64_t k = q / ndof, i = q % ndof;
     if (st[k].done && st[k].iters < j + 1) return;  // stopped before this step
-    if (j + 1 > 0) V[((int64_t)(j + 1) * nr + k) * vstride + i] = w[q] * st[k].inv;
+    V[((int64_t)(j + 1) * nr + k) * vstride + i] = w[q] * st[k].inv;
 }
 
 // start of a cycle: v0 = r / beta, g = beta e1
@@ -483,7 +499,14 @@ struct SolveWS {
     DevBuf<float> zf, y32, binv, bjscratch;
     DevBuf<int64_t> binv_off, self_off;
     DevBuf<CycleState> st;
-    DevBuf<int> active, err;
+    DevBuf<int> active, err, alldone;
+    int* h_flags = nullptr;  // pinned: all-done flag after the last two steps
+    cudaEvent_t fev[2] = {nullptr, nullptr};
+    ~SolveWS() {
+        if (h_flags) cudaFreeHost(h_flags);
+        for (cudaEvent_t e : fev)
+            if (e) cudaEventDestroy(e);
+    }
     int64_t binv_len = 0;
     bool bj_needs_global = false;
 };
@@ -531,6 +554,12 @@ SolveWS& workspace(HMat& H, int nr, int m, cudaStream_t st) {
     W.st.alloc(W.nr);
     W.active.alloc(W.nr);
     W.err.alloc(1);
+    W.alldone.alloc(1);
+    if (!W.h_flags) {
+        HM_CUDA(cudaHostAlloc((void**)&W.h_flags, 2 * sizeof(int), cudaHostAllocDefault));
+        W.h_flags[0] = W.h_flags[1] = 0;
+        for (cudaEvent_t& e : W.fev) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     // block-Jacobi layout: one ld x n block per leaf
     std::vector<int64_t> off(H.n_leaves);
     int64_t len = 0;
@@ -554,16 +583,16 @@ unsigned g1(int64_t n) { return (unsigned)ceil_div(std::max<int64_t>(n, 1), 256)
 // y = A_op z for the Arnoldi step / residual: the product part (E z); the diagonal is
 // applied by the consumer kernel.  dtype F64: compensated, input z (FP64); F32: input zf.
 void apply_E(HMat& H, SolveWS& W, const double* z64, const float* z32, void* y, int nr, int dtype, int fac,
-             cudaStream_t st) {
+             cudaStream_t st, const int* skip = nullptr) {
     if (dtype == HM_F64) {
         const double* in = z64;
         if (nr > 1) {
             k_interleave<<<g1(H.ndof * nr), 256, 0, st>>>(z64, W.zi.p, H.ndof, nr);
             in = W.zi.p;
         }
-        product_core(H, in, y, nr, HM_F64, fac, st);
+        product_core(H, in, y, nr, HM_F64, fac, st, skip);
     } else {
-        product_core(H, z32, y, nr, HM_F32, fac, st);
+        product_core(H, z32, y, nr, HM_F32, fac, st, skip);
     }
 }
 
@@ -593,18 +622,25 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
     k_cycle_start<<<g1(std::max<int64_t>(n * nr, (int64_t)nr * (m + 1))), 256, 0, st>>>(W.r.p, W.V.p, n, nr,
                                                                                       W.vstride, W.h1.p, m, W.g.p);
     HM_LAUNCH_CHECK();
+    HM_CUDA(cudaMemsetAsync(W.alldone.p, 0, sizeof(int), st));
     for (int j = 0; j < m; ++j) {
+        // the host runs at most two steps ahead of the device and stops issuing steps once
+        // the flag copied after step j-2 says that every right-hand side has stopped
+        if (j >= 2) {
+            HM_CUDA(cudaEventSynchronize(W.fev[j % 2]));
+            if (W.h_flags[j % 2]) break;
+        }
         const double* vj = W.V.p + (int64_t)j * nr * W.vstride;
         double* zj = W.Z.p + (int64_t)j * nr * W.vstride;
         k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, vj, zj,
                                                dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p, precond ? 0 : 1);
         HM_LAUNCH_CHECK();
         if (dtype == HM_F64) {
-            apply_E(H, W, zj, nullptr, W.y64.p, nr, HM_F64, fac, st);
+            apply_E(H, W, zj, nullptr, W.y64.p, nr, HM_F64, fac, st, W.alldone.p);
             k_arn_first<double><<<nb, ROW_NT, 0, st>>>(W.y64.p, W.dc.p, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
                                                        W.part.p, W.st.p);
         } else {
-            apply_E(H, W, nullptr, W.zf.p, W.y32.p, nr, HM_F32, fac, st);
+            apply_E(H, W, nullptr, W.zf.p, W.y32.p, nr, HM_F32, fac, st, W.alldone.p);
             k_arn_first<float><<<nb, ROW_NT, 0, st>>>(W.y32.p, W.dc.p, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
                                                       W.part.p, W.st.p);
         }
@@ -613,9 +649,12 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
         k_arn_update<<<nb, ROW_NT, 0, st>>>(W.w.p, W.V.p, W.h1.p, n, nr, j, W.vstride, W.part.p, 1, W.st.p);
         k_reduce_parts<<<nr, 128, 0, st>>>(W.part.p, nb, nr, j + 1, W.h2.p, W.st.p);
         k_arn_update<<<nb, ROW_NT, 0, st>>>(W.w.p, W.V.p, W.h2.p, n, nr, j, W.vstride, W.part.p, 0, W.st.p);
-        k_givens<<<1, 32, 0, st>>>(W.h1.p, W.h2.p, W.part.p, nb, nr, j, m, W.Hm.p, W.cs.p, W.sn.p, W.g.p, W.st.p);
+        k_givens<<<1, 32, 0, st>>>(W.h1.p, W.h2.p, W.part.p, nb, nr, j, m, W.Hm.p, W.cs.p, W.sn.p, W.g.p, W.st.p,
+                                   W.alldone.p);
         k_scale_next<<<g1(n * nr), 256, 0, st>>>(W.w.p, W.V.p, n, nr, j, W.vstride, W.st.p);
         HM_LAUNCH_CHECK();
+        HM_CUDA(cudaMemcpyAsync(W.h_flags + (j % 2), W.alldone.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaEventRecord(W.fev[j % 2], st));
     }
     k_lsq<<<1, 32, 0, st>>>(W.Hm.p, W.g.p, W.ylsq.p, nr, m, W.st.p, W.active.p);
     k_update_x<<<g1(n * nr), 256, 0, st>>>(W.xc.p, W.Z.p, W.ylsq.p, n, nr, m, W.vstride, W.st.p, W.active.p);

@@ -127,7 +127,10 @@ def recorded_traffic(kernel):
 
 
 def product_bytes(info, storage):
-    """Algorithmic bytes of one single-RHS product and of its phases."""
+    """Algorithmic bytes of one single-RHS product (every stored near-field entry, 4 B,
+    and factor entry, 4 B or 2 B for BF16, once; x read and y written once) and of its
+    two streaming kernels: phase 2 (near entries + U factors + operands + y) and phase 1
+    (V factors + x + partials)."""
     fb = 2 if storage == "bf16" else 4
     n = info["n_dof"]
     total = 4 * info["near_entries"] + fb * (info["u_entries"] + info["v_entries"]) + 2 * 4 * n
@@ -155,6 +158,32 @@ def oracle_rows_rate(el, E, nu, budget_s=15.0, max_rows=None):
     O.dense_matvec_rows(el, E, nu, x, sample)
     dt = time.perf_counter() - t0
     return rows / dt, rows, dt
+
+
+def time_gmres(H, el, dev, torch, reps=3):
+    """GMRES time-to-1e-8 on the same fault: (E) x = b, b = uniform shear + Gaussian
+    pressure bump, leaf block-Jacobi, restart 50, x0 = 0.  Plain: FP64 Krylov with every
+    product compensated FP64 on the FP32 factors.  Mixed: FP64 refinement of corrections
+    solved with the BF16 factors and FP32 products.  Both stop on the residual of the
+    FP32-factor operator recomputed in compensated FP64 (<= 1e-8 ||b||)."""
+    from paper_2605_14397_gb300 import synth
+    b = torch.from_numpy(synth.rhs_shear_plus_bump(el)).to(dev)
+    x = torch.zeros_like(b)
+    out = {"tol": 1e-8, "restart": 50, "precond": "leaf block-Jacobi", "rhs": "shear + Gaussian bump"}
+    for mode in ("f64", "mixed"):
+        times, info = [], None
+        for _ in range(reps):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = H.solve(b, x, mode=mode, tol=1e-8, restart=50, precond="blockj")[0]
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        key = "plain_fp64" if mode == "f64" else "mixed_bf16_ir"
+        out[key] = {"seconds": statistics.median(times), "iters": info["iters"], "outer": info["outer"],
+                    "relres": info["relres"]}
+    out["speedup_mixed_over_plain"] = out["plain_fp64"]["seconds"] / out["mixed_bf16_ir"]["seconds"]
+    return out
 
 
 def cores():
@@ -242,7 +271,9 @@ def main():
     E, nu, eps = 1.0, 0.25, 1e-6
     t0 = time.perf_counter()
     T = hmat.ClusterTree(el, 64, 2.0)
-    H = hmat.HMatrix(T, el, E, nu, eps, args.storage)
+    # FP32 and BF16 copies of the factors: the product times the FP32 ones (or the BF16
+    # ones with --storage bf16), the mixed-precision solver needs both
+    H = hmat.HMatrix(T, el, E, nu, eps, "both" if (args.storage == "f32" and not args.no_gmres) else args.storage)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     info = H.info()
@@ -307,6 +338,10 @@ def main():
     e2e = {"value": world * B / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(xh.nbytes),
            "d2h_bytes_per_step": int(yh.nbytes), "ms_per_step": te * 1e3}
 
+    gmres = None
+    if not args.no_gmres and args.storage == "f32":
+        gmres = time_gmres(H, el, dev, torch)
+
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else "bf16",
@@ -319,6 +354,8 @@ def main():
                        "rank_mean": info["rank_mean"], "rank_max": info["rank_max"],
                        "bytes_per_product": B, "frac_of_hbm_peak": value / world / hbm},
             "roofline": roofline, "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clocks}
+    if gmres is not None:
+        line["gmres"] = gmres
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, dt = oracle_rows_rate(el, E, nu)

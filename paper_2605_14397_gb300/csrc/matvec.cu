@@ -476,7 +476,7 @@ void mark(HMat& H, int idx, cudaStream_t st) {
 
 template <int MODE>
 constexpr int ncw_for(int NR) {
-    return (MODE == 1 || NR > 1) ? 8 : 16;
+    return NR > 1 ? 8 : 16;
 }
 
 template <int MODE, class C, int NR, int RPL>

@@ -47,6 +47,10 @@ def parse():
     p.add_argument("--no-gmres", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--grid", type=int, default=256, help="disk grid size (256: the 51,468-element fault)")
+    p.add_argument("--workload", default="fault", choices=["fault", "faults64"],
+                   help="fault: the 51,468-element disk fault (default); faults64: 64 independent faults, "
+                        "batched product vs per-fault launches")
+    p.add_argument("--tune", action="store_true", help="also run the leaf-size autotuner on the workload")
     return p.parse_args()
 
 
@@ -186,6 +190,92 @@ def time_gmres(H, el, dev, torch, reps=3):
     return out
 
 
+def run_faults64(args, dev, torch, hmat, synth):
+    """64 independent disk faults (log-uniform 2k-40k elements, seeded normals and nu,
+    795,192 elements in all): one batched H-matrix (one work list, 5 launches per
+    product; also replayed from a CUDA graph) against per-fault products (64 x 5
+    launches; also 64 graph replays).  value = algorithmic bytes of all 64 products /
+    time of the batched product."""
+    import numpy as np
+    els, nus = synth.config_faults_batch()
+    E, eps = 1.0, 1e-6
+    t0 = time.perf_counter()
+    parts = []
+    for el, nu in zip(els, nus):
+        T = hmat.ClusterTree(el, 64, 2.0)
+        parts.append(hmat.HMatrix(T, el, E, float(nu), eps, "f32"))
+        del T
+    torch.cuda.synchronize()
+    t_parts = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    B = hmat.HMatrix.batch(parts)
+    t_merge = time.perf_counter() - t0
+    info = B.info()
+    Bytes, _, _ = product_bytes(info, "f32")
+    nd = info["n_dof"]
+    x = torch.as_tensor(synth.rhs_normal(nd, 1604), dtype=torch.float32, device=dev)
+    y = torch.empty_like(x)
+    offs = np.cumsum([0] + [3 * el.N for el in els])
+    xs = [x[offs[f]:offs[f + 1]] for f in range(len(els))]
+    ys = [y[offs[f]:offs[f + 1]] for f in range(len(els))]
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        B.matvec(x, y, stream)
+
+    def batched_graph():
+        B.matvec_graph(x, y, stream)
+
+    def per_fault():
+        for H, a, b in zip(parts, xs, ys):
+            H.matvec(a, b, stream)
+
+    def per_fault_graph():
+        for H, a, b in zip(parts, xs, ys):
+            H.matvec_graph(a, b, stream)
+
+    res = {}
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    for name, fn in (("batched", batched), ("batched_graph", batched_graph), ("per_fault", per_fault),
+                     ("per_fault_graph", per_fault_graph)):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        res[name] = ev0.elapsed_time(ev1) / args.steps
+    clocks = sampler.stop()
+    B.check(stream)
+    for H in parts:
+        H.check(stream)
+    hbm, peak_kind = peaks()
+    value = Bytes / (res["batched"] * 1e-3) / 1e9
+    Ns = [el.N for el in els]
+    line = {"metric": "batched H-matvec GB/s over 64 independent faults", "value": value, "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded meshes and right-hand side)",
+            "config": {"workload": "64 disk faults, N_f log-uniform in [2k, 40k] (%d..%d), %d elements, h = 2/256, "
+                                   "nu_f ~ U[0.2, 0.3], leaf 64, eta 2, ACA eps 1e-6" % (min(Ns), max(Ns), sum(Ns)),
+                       "nrhs": 1, "storage": "f32", "bytes_per_product": Bytes,
+                       "assemble_parts_s": t_parts, "merge_s": t_merge,
+                       "l2": "operator %.1f GB >> 129 MB L2: no flush" % (Bytes / 1e9)},
+            "frac_of_hbm_peak": value / hbm, "peak_source": peak_kind,
+            "ms_per_product": res, "speedup_batched_over_per_fault": res["per_fault"] / res["batched"],
+            "launches_per_product": {"batched": 5, "per_fault": 5 * len(parts)}, "clocks": clocks}
+    if args.tune:
+        line["autotune_largest_fault"] = hmat.autotune(els[int(np.argmax(Ns))], E, float(nus[int(np.argmax(Ns))]),
+                                                       eps, "f32", leaves=(32, 48, 64, 96, 128), etas=(2.0,),
+                                                       budget_ms=120000)
+    print(json.dumps(line), flush=True)
+
+
 def cores():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n else os.cpu_count()
@@ -267,6 +357,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.workload == "faults64":
+        run_faults64(args, dev, torch, hmat, synth)
+        return
     el = synth.config_fault(args.grid)
     E, nu, eps = 1.0, 0.25, 1e-6
     t0 = time.perf_counter()
@@ -356,6 +449,9 @@ def main():
             "roofline": roofline, "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clocks}
     if gmres is not None:
         line["gmres"] = gmres
+    if args.tune:
+        line["autotune"] = hmat.autotune(el, E, nu, eps, "f32", leaves=(32, 48, 64, 96, 128), etas=(1.5, 2.0, 3.0),
+                                         budget_ms=180000)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, dt = oracle_rows_rate(el, E, nu)

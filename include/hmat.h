@@ -246,6 +246,41 @@ hm_status hm_gmres_solve(const hm_hmat* h, const double* k_dev, double shift, co
                          double* x_dev, int nrhs, const hm_solve_opts* opt, hm_solve_info* info,
                          void* stream);
 
+/* ---------------------------------------------------------------- batching
+ * Independent faults: the operator of several non-interacting fractures is
+ * block-diagonal, one block E_f per fault (eq. ElasSystem on each fault alone, each with
+ * the E, nu it was assembled with).  hm_batch_create concatenates the assembled
+ * H-matrices hs[0..nf-1] into one new H-matrix whose vectors are the faults' vectors
+ * back to back (fault 0's 3 N_0 DOFs, then fault 1's, ...): one arena of coefficients
+ * and one work list, so a product is one persistent launch per phase over all faults.
+ * All parts must use the same factor storage.  The parts are copied (device to device)
+ * and stay valid and owned by the caller; destroy them to free their memory.  The result
+ * is used with every hm_hmat function (product, solve of the block-diagonal system,
+ * info); hm_hmat_far_factors numbers the blocks fault by fault.  Synchronises the
+ * stream. */
+hm_status hm_batch_create(const hm_hmat* const* hs, int nf, void* stream, hm_hmat** out);
+
+/* The product of hm_matvec replayed from a CUDA graph: the first call for a given
+ * (x_dev, y_dev, nrhs, dtype) runs the product once, captures it on a library-owned
+ * stream and instantiates it; later calls with the same arguments launch the graph on
+ * `stream` (one host call per product).  Graphs are dropped when the product scratch
+ * grows (more right-hand sides).  While per-phase timing is enabled it runs the plain
+ * product.  Asynchronous after the first call. */
+hm_status hm_matvec_graph(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, int dtype,
+                          void* stream);
+
+/* Leaf-size autotuner: for each (leaf_sizes[i], etas[j]) in order, build the cluster
+ * tree and partition (Sec. 3.1), assemble with `opt` (every candidate meets the same
+ * per-block accuracy aca_eps), and time 20 single-RHS FP32 products with CUDA events on
+ * `stream`; stop once budget_ms of wall time has passed (at least one candidate is
+ * timed).  Writes a NUL-terminated JSON object to json_out (capacity cap bytes):
+ *   {"n_elements": N, "candidates": [{"leaf", "eta", "ms", "stored_bytes",
+ *    "assemble_s", "rank_mean"}, ...], "best": {"leaf", "eta", "ms"}, "tuned": n}
+ * HM_EINVAL if the buffer is too small (the message states the size needed). */
+hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const int* leaf_sizes, int n_leaf,
+                      const double* etas, int n_eta, int budget_ms, char* json_out, size_t cap,
+                      void* stream);
+
 /* Synchronise `stream` and report whether a device-side wait of an earlier product on
  * this H-matrix gave up (HM_ETIMEOUT; the flags are then cleared).  The product kernels
  * bound every wait on their copy pipeline instead of spinning forever. */

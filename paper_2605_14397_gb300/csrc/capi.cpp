@@ -19,6 +19,8 @@ static thread_local std::string g_last_error;
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
+std::string autotune(const hm_elements& el, const hm_assemble_opts& opt, const int* leaves, int n_leaf,
+                     const double* etas, int n_eta, int budget_ms, cudaStream_t st);
 void influence_pairs(const hm_elements& e, double E, double nu, int64_t npairs, const int64_t* ri,
                      const int64_t* sj, double* out, cudaStream_t st);
 
@@ -210,6 +212,59 @@ hm_status hm_gmres_solve(const hm_hmat* hh, const double* k_dev, double shift, c
     }
     if (!std::isfinite(shift)) hm::fail(HM_ENAN, "gmres_solve: shift is not finite");
     hm::gmres_solve(const_cast<hm::HMat&>(hh->h), k_dev, shift, b_dev, x_dev, nrhs, o, info, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_batch_create(const hm_hmat* const* hs, int nf, void* stream, hm_hmat** out) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    if (!out) hm::fail(HM_EINVAL, "batch_create: NULL output handle");
+    *out = nullptr;
+    if (!hs || nf < 1) hm::fail(HM_EINVAL, "batch_create: need at least one H-matrix");
+    std::vector<const hm::HMat*> parts(nf);
+    for (int f = 0; f < nf; ++f) {
+        if (!hs[f]) hm::fail(HM_EINVAL, "batch_create: NULL H-matrix in the list");
+        parts[f] = &hs[f]->h;
+    }
+    hm_hmat* m = new hm_hmat();
+    try {
+        hm::merge(parts, (cudaStream_t)stream, m->h);
+    } catch (...) {
+        delete m;
+        throw;
+    }
+    *out = m;
+    HM_API_END
+}
+
+hm_status hm_matvec_graph(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs, int dtype, void* stream) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "matvec_graph: NULL H-matrix");
+    if (!x_dev || !y_dev) hm::fail(HM_EINVAL, "matvec_graph: NULL vector");
+    if (x_dev == y_dev) hm::fail(HM_EINVAL, "matvec_graph: x and y must not overlap");
+    if (nrhs < 1) hm::fail(HM_EINVAL, "matvec_graph: nrhs must be >= 1");
+    if (dtype != HM_F32 && dtype != HM_F64) hm::fail(HM_EINVAL, "matvec_graph: dtype must be HM_F32 or HM_F64");
+    hm::matvec_graph(const_cast<hm::HMat&>(hh->h), x_dev, y_dev, nrhs, dtype, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const int* leaf_sizes, int n_leaf,
+                      const double* etas, int n_eta, int budget_ms, char* json_out, size_t cap, void* stream) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    hm::check_elements(el);
+    if (!opt) hm::fail(HM_EINVAL, "autotune: NULL assembly options");
+    if (!json_out || cap == 0) hm::fail(HM_EINVAL, "autotune: NULL output buffer");
+    if (!leaf_sizes || !etas || n_leaf < 1 || n_eta < 1) hm::fail(HM_EINVAL, "autotune: empty candidate list");
+    for (int i = 0; i < n_leaf; ++i)
+        if (leaf_sizes[i] < 1 || leaf_sizes[i] > 128) hm::fail(HM_EINVAL, "autotune: leaf sizes must be in [1, 128]");
+    for (int j = 0; j < n_eta; ++j)
+        if (!(etas[j] > 0.0) || !std::isfinite(etas[j])) hm::fail(HM_EINVAL, "autotune: eta must be positive");
+    const std::string js =
+        hm::autotune(*el, *opt, leaf_sizes, n_leaf, etas, n_eta, budget_ms, (cudaStream_t)stream);
+    if (js.size() + 1 > cap) hm::fail(HM_EINVAL, "autotune: output buffer too small (need " +
+                                                     std::to_string(js.size() + 1) + " bytes)");
+    std::memcpy(json_out, js.c_str(), js.size() + 1);
     HM_API_END
 }
 

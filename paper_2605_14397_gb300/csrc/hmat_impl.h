@@ -125,11 +125,23 @@ struct HMat {
     int64_t t_count = 0;
     DevBuf<unsigned char> xs, ys;
 
+    // instantiated product graphs, one per (x, y, nrhs, dtype), captured on cap_stream
+    struct GraphEntry {
+        const void* x;
+        void* y;
+        int nrhs, dtype;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
+
     HMat() = default;
     HMat(const HMat&) = delete;
     HMat& operator=(const HMat&) = delete;
     ~HMat() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (GraphEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         solve_ws_free(solve_ws);
     }
 
@@ -159,6 +171,10 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
 // fac: 0 FP32 factors, 1 BF16 factors.  dtype HM_F32: float vectors; HM_F64: double.
 void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st,
                   const int* skip = nullptr);
+// Concatenate independent H-matrices into one (block-diagonal operator, one work list).
+void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M);
+void graphs_clear(HMat& H);
+void matvec_graph(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st);
 inline bool has_factors(const HMat& H, int fac) {

@@ -676,6 +676,7 @@ void build_plan_for(HMat& H, HMat::Plan& PLAN, int esz, int G, cudaStream_t st) 
 
 void ensure_product_scratch(HMat& H, int nrhs, cudaStream_t st) {
     if (nrhs <= H.nrhs_cap) return;
+    graphs_clear(H);  // captured products refer to the scratch being replaced
     const int cap = nrhs <= 1 ? 1 : (nrhs <= 4 ? 4 : 16);
     const size_t nv = (size_t)H.ndof * cap + VEC_SLACK;
     const size_t np = (size_t)std::max<int64_t>(H.p_len, 1) * cap + VEC_SLACK;

@@ -102,6 +102,10 @@ SIGNATURES = [
     ("hm_hmat_timing_read", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     ("hm_gmres_solve", _I, [_VP, _VP, _D, _VP, _VP, _I, ctypes.POINTER(hm_solve_opts),
                             ctypes.POINTER(hm_solve_info), _VP]),
+    ("hm_batch_create", _I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
+    ("hm_matvec_graph", _I, [_VP, _VP, _VP, _I, _I, _VP]),
+    ("hm_autotune", _I, [ctypes.POINTER(hm_elements), ctypes.POINTER(hm_assemble_opts), ctypes.POINTER(_I), _I,
+                         ctypes.POINTER(_D), _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
 ]
 
 
@@ -223,6 +227,23 @@ class HMatrix:
         self.E, self.nu, self.eps, self.storage = E, nu, aca_eps, storage
         self.ndof = 3 * el.N if el is not None else None
 
+    @classmethod
+    def batch(cls, parts, stream=None):
+        """One H-matrix of independent faults (block-diagonal operator): the parts'
+        vectors back to back, one work list for the whole batch.  The parts are copied
+        and stay usable."""
+        parts = list(parts)
+        arr = (_VP * len(parts))(*[p.handle.value for p in parts])
+        h = ctypes.c_void_p()
+        _check(lib().hm_batch_create(arr, len(parts), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.handle = h
+        self.E = self.nu = None
+        self.eps = max(p.eps for p in parts)
+        self.storage = parts[0].storage
+        self.ndof = sum(p.ndof for p in parts)
+        return self
+
     def info(self):
         i = hm_hmat_info()
         _check(lib().hm_hmat_get_info(self.handle, ctypes.byref(i)))
@@ -250,6 +271,15 @@ class HMatrix:
         assert y.dtype == x.dtype and x.is_contiguous() and y.is_contiguous()
         nrhs = 1 if x.dim() == 1 else x.shape[0]
         _check(lib().hm_matvec(self.handle, _dptr(x), _dptr(y), int(nrhs), dt, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def matvec_graph(self, x, y, stream=None):
+        """matvec replayed from a CUDA graph instantiated for these (x, y) on first use."""
+        import torch
+        dt = {torch.float32: HM_F32, torch.float64: HM_F64}[x.dtype]
+        assert y.dtype == x.dtype and x.is_contiguous() and y.is_contiguous()
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        _check(lib().hm_matvec_graph(self.handle, _dptr(x), _dptr(y), int(nrhs), dt,
+                                     ctypes.c_void_p(_stream_ptr(stream))))
 
     def matvec_host(self, x, y, stream=None):
         """y = E x for host numpy arrays (float32 or float64); synchronous."""
@@ -299,3 +329,53 @@ class HMatrix:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ autotuner
+
+def autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device):
+    """Cache key of a tuning run: the geometry (every element array), the assembly
+    options, the candidate list and the device name."""
+    import hashlib
+    h = hashlib.sha256()
+    for k in ("c", "s1", "s2", "n", "a", "b"):
+        h.update(np.ascontiguousarray(getattr(el, k), dtype=np.float64).tobytes())
+    h.update(repr((int(el.N), float(E), float(nu), float(aca_eps), str(storage), tuple(int(v) for v in leaves),
+                   tuple(float(v) for v in etas), str(device))).encode())
+    return h.hexdigest()[:32]
+
+
+def autotune(el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", leaves=(32, 64, 128), etas=(2.0,), budget_ms=60000,
+             cache=None, device=None, stream=None):
+    """Fastest (leaf size, eta) for the product on this geometry (hm_autotune).  With
+    `cache` (a JSON file path) a result for the same geometry, options, candidates and
+    device is read from the file instead of re-tuning, and new results are added to it."""
+    import json
+    if device is None:
+        import torch
+        device = torch.cuda.get_device_name()
+    key = autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device)
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            return table[key]
+    ea = _ElemArgs(el)
+    st = {"f32": HM_F32, "bf16": HM_BF16, "both": HM_F32_BF16}[storage]
+    opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, 0)
+    lv = (_I * len(leaves))(*[int(v) for v in leaves])
+    ev = (_D * len(etas))(*[float(v) for v in etas])
+    cap = 4096 + 256 * len(leaves) * len(etas)
+    buf = ctypes.create_string_buffer(cap)
+    _check(lib().hm_autotune(ea.ref, ctypes.byref(opt), lv, len(leaves), ev, len(etas), int(budget_ms), buf, cap,
+                             ctypes.c_void_p(_stream_ptr(stream))))
+    res = json.loads(buf.value.decode())
+    res["device"] = device
+    if cache:
+        table[key] = res
+        tmp = cache + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(tmp, cache)
+    return res

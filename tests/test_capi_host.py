@@ -2,6 +2,7 @@
 include/hmat.h declares, rejects bad arguments with a status code, and its host cluster
 tree and block partition are bit-identical to the oracle's."""
 import ctypes
+import json
 import os
 import re
 
@@ -67,6 +68,42 @@ def test_bad_arguments_return_status(L):
     assert L.hm_matvec(None, None, None, 1, 1, None) == hmat.HM_EINVAL
     assert L.hm_hmat_get_info(None, None) == hmat.HM_EINVAL
     assert L.hm_tree_get_info(None, None) == hmat.HM_EINVAL
+    out = ctypes.c_void_p()
+    assert L.hm_batch_create(None, 0, None, ctypes.byref(out)) == hmat.HM_EINVAL
+    assert L.hm_batch_create(None, 2, None, None) == hmat.HM_EINVAL
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert L.hm_batch_create(nulls, 2, None, ctypes.byref(out)) == hmat.HM_EINVAL and not out.value
+    assert L.hm_matvec_graph(None, None, None, 1, 1, None) == hmat.HM_EINVAL
+    opt = hmat.hm_assemble_opts(1.0, 0.25, 1e-6, hmat.HM_F32, 0)
+    buf = ctypes.create_string_buffer(64)
+    lv = (ctypes.c_int * 1)(200)
+    ev = (ctypes.c_double * 1)(2.0)
+    assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 1, ev, 1, 0, buf, 64, None) == hmat.HM_EINVAL
+    assert "leaf" in hmat.last_error()
+    assert L.hm_autotune(ea.ref, None, lv, 1, ev, 1, 0, buf, 64, None) == hmat.HM_EINVAL
+    assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 0, ev, 1, 0, buf, 64, None) == hmat.HM_EINVAL
+
+
+def test_autotune_cache_key_and_hit_without_device(tmp_path, monkeypatch):
+    el = synth.config_penny(12)
+    k0 = hmat.autotune_key(el, 1.0, 0.25, 1e-6, "f32", (32, 64), (2.0,), "dev")
+    assert k0 == hmat.autotune_key(el, 1.0, 0.25, 1e-6, "f32", [32, 64], [2.0], "dev")
+    moved = synth.config_penny(12)
+    moved.c = moved.c + np.array([0.0, 0.0, 1e-12])
+    for other in (hmat.autotune_key(el, 1.0, 0.26, 1e-6, "f32", (32, 64), (2.0,), "dev"),
+                  hmat.autotune_key(el, 1.0, 0.25, 1e-6, "bf16", (32, 64), (2.0,), "dev"),
+                  hmat.autotune_key(el, 1.0, 0.25, 1e-6, "f32", (64, 32), (2.0,), "dev"),
+                  hmat.autotune_key(el, 1.0, 0.25, 1e-6, "f32", (32, 64), (2.0,), "other"),
+                  hmat.autotune_key(moved, 1.0, 0.25, 1e-6, "f32", (32, 64), (2.0,), "dev")):
+        assert other != k0
+    cache = tmp_path / "tune.json"
+    stored = {"best": {"leaf": 32, "eta": 2.0, "ms": 1.0}, "candidates": [], "tuned": 2}
+    cache.write_text(json.dumps({k0: stored}))
+
+    def no_library():
+        raise AssertionError("a cached tuning result must not touch the library")
+    monkeypatch.setattr(hmat, "lib", no_library)
+    assert hmat.autotune(el, 1.0, 0.25, 1e-6, "f32", (32, 64), (2.0,), cache=str(cache), device="dev") == stored
 
 
 @pytest.mark.parametrize("which,leaf", [("penny", 64), ("penny", 16), ("planes", 32), ("fault", 64),

@@ -40,7 +40,7 @@ typedef int hm_status;
 #define HM_ECUDA (-3)           /* a CUDA call failed */
 #define HM_ESINGULAR_GEOM (-4)  /* a collocation point lies on a source element's edge */
 #define HM_ENOCONV (-5)         /* iteration limit reached before the tolerance */
-#define HM_EBREAKDOWN (-6)      /* Krylov breakdown or ACA rank cap exceeded */
+#define HM_EBREAKDOWN (-6)      /* breakdown of an iteration */
 #define HM_ENAN (-7)            /* NaN or Inf met in the data */
 #define HM_ETIMEOUT (-8)        /* a bounded device wait gave up */
 
@@ -131,7 +131,9 @@ void hm_tree_destroy(hm_tree* t);
  * Assemble the H-matrix of E on the device: dense near-field tiles in FP32 (FP64
  * evaluation), admissible blocks compressed by adaptive cross approximation with
  * element (3-row) pivots to relative Frobenius accuracy aca_eps per block, factors
- * stored in `storage` (HM_F32 or HM_BF16).  max_rank caps the ACA rank (0 = 160, at most 256).
+ * stored in `storage` (HM_F32 or HM_BF16).  max_rank caps the ACA rank (0 = 160, at most 256):
+ * a block whose approximation does not converge below the cap is refined into the
+ * blocks of its children clusters (a pair of leaves is stored dense instead).
  * Synchronises the stream (the packed layout depends on the ranks). */
 typedef struct {
     double E;
@@ -160,15 +162,19 @@ typedef struct {
     int64_t v_entries;        /* sum over low-rank blocks of 3 |t| r (column factors) */
     int64_t tb_len;           /* sum of the ranks (length of the V^T x vector) */
     int64_t p_len;            /* per-leaf partials of V^T x */
+    int64_t n_far_refined;    /* admissible blocks whose cross approximation did not converge
+                                 below the rank cap, replaced by their children's blocks */
 } hm_hmat_info;
 
 hm_status hm_assemble_hmat(const hm_tree* t, const hm_elements* el, const hm_assemble_opts* opt,
                            void* stream, hm_hmat** out);
 hm_status hm_hmat_get_info(const hm_hmat* h, hm_hmat_info* info);
-/* Low-rank factors of far block b (0 <= b < n_far) to host, FP64, column-major:
- * U[3|s| x r], V[3|t| x r] with block = U V^T in cluster order of the two clusters.
- * rank_out receives r, or -1 for a block stored dense (U, V untouched); pass
- * U = V = NULL to query the rank only. */
+/* Low-rank factors of far block b to host, FP64, column-major: U[3|s| x r],
+ * V[3|t| x r] with block = U V^T in cluster order of the two clusters.  Blocks
+ * 0 .. n-1 are those of the partition (hm_tree_export order); a block refined during
+ * assembly (see n_far_refined) is followed by its children's blocks, numbered from n on
+ * in order of refinement.  rank_out receives r, -1 for a block stored dense or -2 for a
+ * refined block (U, V untouched); pass U = V = NULL to query the rank only. */
 hm_status hm_hmat_far_factors(const hm_hmat* h, int64_t b, int32_t* rank_out, double* U, double* V);
 void hm_hmat_destroy(hm_hmat* h);
 

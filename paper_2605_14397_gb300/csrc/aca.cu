@@ -306,7 +306,11 @@ __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, 
         }
         k += nr;
         streak = (step2 <= eps * eps * nrm2) ? streak + 1 : 0;
-        if (k >= kmax) break;
+        if (k >= kmax) {
+            // full rank reproduces the block exactly; reaching the cap first is a failure
+            if (kmax < min(mS, mT)) status = 1;
+            break;
+        }
         if (streak >= 2) {
             // verify on elements drawn at random before accepting the approximation
             checking = true;

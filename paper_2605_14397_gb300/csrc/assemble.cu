@@ -5,6 +5,7 @@
 // would not be smaller than the block itself (or that does not compress below the rank
 // cap) is kept dense, as extra near-field tiles of its row leaves.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <numeric>
@@ -180,29 +181,34 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         }
     }
 
-    // ---- far field: ACA + recompression in batches bounded by a workspace budget
-    const int64_t nf = (int64_t)T.far.size();
-    H.n_far = nf;
-    H.h_far.assign(nf, FarDesc{});
-    for (int64_t b = 0; b < nf; ++b) {
-        const int64_t s = T.far[b][0], t = T.far[b][1];
-        FarDesc& F = H.h_far[b];
+    // ---- far field: ACA + recompression in batches bounded by a workspace budget.
+    // An admissible block whose cross approximation does not converge below the rank cap
+    // is refined: replaced by the blocks of its children clusters (admissible as well:
+    // smaller boxes, no smaller distance), appended to the list and compressed in a later
+    // batch; a pair of leaves that still does not converge is stored dense.
+    std::vector<std::array<int64_t, 2>> fnodes(T.far.begin(), T.far.end());
+    H.h_far.clear();
+    auto push_far = [&](int64_t s, int64_t t) {
+        FarDesc F{};
         F.s_begin = (int32_t)T.begin[s];
         F.s_n = (int32_t)(T.end[s] - T.begin[s]);
         F.t_begin = (int32_t)T.begin[t];
         F.t_n = (int32_t)(T.end[t] - T.begin[t]);
-    }
+        H.h_far.push_back(F);
+    };
+    for (const auto& st_ : fnodes) push_far(st_[0], st_[1]);
     const int64_t budget = (int64_t)4 << 30;  // bytes of FP64 ACA workspace per batch
-    std::vector<int32_t> ranks(nf, 0), stat(nf, 0), fin(nf, 0);
-    std::vector<char> dense_far(nf, 0);
+    std::vector<int32_t> ranks(fnodes.size(), 0), stat(fnodes.size(), 0), fin(fnodes.size(), 0);
+    std::vector<char> dense_far(fnodes.size(), 0);  // 1 dense, 2 refined into later blocks
     int64_t store_len = 0;
-    std::vector<int64_t> fac_off(nf, 0);
+    std::vector<int64_t> fac_off(fnodes.size(), 0);
     std::vector<DevBuf<float>> chunks;
     std::vector<int64_t> chunk_base;
     DevBuf<double> ws, small;
     DevBuf<int32_t> d_rank, d_stat;
     int64_t b0 = 0;
-    while (b0 < nf) {
+    while (b0 < (int64_t)H.h_far.size()) {
+        const int64_t nf = (int64_t)H.h_far.size();
         std::vector<AcaJob> jobs;
         int64_t wlen = 0;
         int max_sn = 0;
@@ -238,13 +244,25 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         for (int64_t b = b0; b < b1; ++b) {
             const FarDesc& F = H.h_far[b];
             if (stat[b] != 0) {
-                if ((int64_t)9 * F.s_n * F.t_n > ((int64_t)1 << 26)) {
-                    char buf[256];
-                    snprintf(buf, sizeof(buf), "assemble: ACA of far block %lld (%d x %d elements) exceeded rank %d",
-                             (long long)b, F.s_n, F.t_n, R);
-                    fail(HM_EBREAKDOWN, buf);
+                const int64_t s = fnodes[b][0], t = fnodes[b][1];
+                if (T.left[s] < 0 && T.left[t] < 0) {
+                    dense_far[b] = 1;  // a pair of leaves not compressible to the cap: dense
+                    continue;
                 }
-                dense_far[b] = 1;  // not compressible to the cap: keep it dense
+                dense_far[b] = 2;
+                const int64_t cs[2] = {T.left[s] < 0 ? s : T.left[s], T.left[s] < 0 ? -1 : T.right[s]};
+                const int64_t ct[2] = {T.left[t] < 0 ? t : T.left[t], T.left[t] < 0 ? -1 : T.right[t]};
+                for (int64_t a : cs)
+                    for (int64_t c : ct) {
+                        if (a < 0 || c < 0) continue;
+                        fnodes.push_back({a, c});
+                        push_far(a, c);
+                        ranks.push_back(0);
+                        stat.push_back(0);
+                        fin.push_back(0);
+                        dense_far.push_back(0);
+                        fac_off.push_back(0);
+                    }
                 continue;
             }
             RecJob J;
@@ -307,6 +325,8 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     }
     ws.release();
     small.release();
+    const int64_t nf = (int64_t)H.h_far.size();
+    H.n_far = nf;
     H.facstore.alloc(std::max<int64_t>(store_len, 1));
     for (size_t c = 0; c < chunks.size(); ++c) {
         const int64_t len = (c + 1 < chunks.size() ? chunk_base[c + 1] : store_len) - chunk_base[c];
@@ -327,10 +347,12 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         tiles_by_row[T.leaf_of_node[s]].push_back({(int32_t)T.begin[t], (int32_t)(T.end[t] - T.begin[t])});
     }
     int64_t n_dense_far = 0;
+    H.n_refined = 0;
     for (int64_t b = 0; b < nf; ++b) {
-        if (!dense_far[b]) continue;
+        if (dense_far[b] == 2) ++H.n_refined;
+        if (dense_far[b] != 1) continue;
         ++n_dense_far;
-        const int64_t s = T.far[b][0];
+        const int64_t s = fnodes[b][0];
         for (int l = 0; l < lcount[s]; ++l)
             tiles_by_row[lfirst[s] + l].push_back({H.h_far[b].t_begin, H.h_far[b].t_n});
     }
@@ -389,7 +411,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         F.rank = dense_far[b] ? 0 : fin[b];
         F.fac_off = fac_off[b];
         F.tb_off = tb_len;
-        F.n_tleaves = lcount[T.far[b][1]];
+        F.n_tleaves = lcount[fnodes[b][1]];
         F.pbase = p_len;
         F.dense = dense_far[b];
         tb_len += F.rank;
@@ -410,7 +432,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     std::vector<std::vector<int64_t>> far_by_row(nl), far_by_col(nl);
     for (int64_t b = 0; b < nf; ++b) {
         if (H.h_far[b].rank == 0) continue;
-        const int64_t s = T.far[b][0], t = T.far[b][1];
+        const int64_t s = fnodes[b][0], t = fnodes[b][1];
         for (int l = 0; l < lcount[s]; ++l) far_by_row[lfirst[s] + l].push_back(b);
         for (int l = 0; l < lcount[t]; ++l) far_by_col[lfirst[t] + l].push_back(b);
     }
@@ -445,7 +467,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         int vcols = 0;
         for (int64_t b : far_by_col[l]) {
             const FarDesc& F = H.h_far[b];
-            const int64_t t = T.far[b][1];
+            const int64_t t = fnodes[b][1];
             const int k = l - lfirst[t];  // which leaf of T
             PackJob J;
             J.src = F.fac_off + 3LL * F.s_n * F.rank + 3LL * (L.begin - F.t_begin);

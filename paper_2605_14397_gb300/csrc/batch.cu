@@ -65,7 +65,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
     M.h_u_zidx.clear();
     M.h_v_pidx.clear();
     M.h_self_off.clear();
-    M.n_near = M.n_far = M.n_dense_far = 0;
+    M.n_near = M.n_far = M.n_dense_far = M.n_refined = 0;
     M.near_entries = M.far_entries = 0;
     M.assemble_seconds = 0.0;
     std::vector<int32_t> perm32;
@@ -115,6 +115,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         M.n_near += h->n_near;
         M.n_far += h->n_far;
         M.n_dense_far += h->n_dense_far;
+        M.n_refined += h->n_refined;
         M.near_entries += h->near_entries;
         M.far_entries += h->far_entries;
         M.assemble_seconds += h->assemble_seconds;

@@ -136,7 +136,8 @@ hm_status hm_hmat_get_info(const hm_hmat* hh, hm_hmat_info* info) {
     info->storage = H.storage;
     info->pad_ = 0;
     info->n_far_dense = H.n_dense_far;
-    info->n_far_lowrank = H.n_far - H.n_dense_far;
+    info->n_far_lowrank = H.n_far - H.n_dense_far - H.n_refined;
+    info->n_far_refined = H.n_refined;
     info->u_entries = info->v_entries = 0;
     for (const hm::FarDesc& F : H.h_far) {
         info->u_entries += 3LL * F.rank * F.s_n;
@@ -153,7 +154,7 @@ hm_status hm_hmat_far_factors(const hm_hmat* hh, int64_t b, int32_t* rank_out, d
     const hm::HMat& H = hh->h;
     if (b < 0 || b >= H.n_far) hm::fail(HM_EINVAL, "hmat_far_factors: block index out of range");
     const hm::FarDesc& F = H.h_far[b];
-    if (rank_out) *rank_out = F.dense ? -1 : F.rank;
+    if (rank_out) *rank_out = F.dense == 1 ? -1 : (F.dense == 2 ? -2 : F.rank);
     if ((U || V) && !F.dense) {
         const int64_t nu = 3LL * F.s_n * F.rank, nv = 3LL * F.t_n * F.rank;
         std::vector<float> buf(nu + nv);

@@ -47,7 +47,8 @@ struct FarDesc {
     int64_t pbase;                       // partial buffer base: P[pbase + k r + l]
     int64_t tb_off;                      // output offset in tb
     int64_t fac_off;                     // compact factor store offset (U then V)
-    int32_t dense;                       // 1: kept dense (its tiles live in the near stream)
+    int32_t dense;                       // 1: kept dense (its tiles live in the near stream),
+                                         // 2: refined into its children blocks (listed later)
     int32_t pad_;
 };
 
@@ -79,7 +80,7 @@ struct HMat {
     double E = 1.0, nu = 0.25, eps = 1e-6;
     int storage = HM_F32;
     int n_leaves = 0;
-    int64_t n_far = 0, n_near = 0, n_dense_far = 0;
+    int64_t n_far = 0, n_near = 0, n_dense_far = 0, n_refined = 0;
     int64_t tb_len = 0, p_len = 0;
     int64_t near_entries = 0, far_entries = 0;
     int rank_min = 0, rank_max = 0;

@@ -59,7 +59,7 @@ class hm_hmat_info(ctypes.Structure):
                 ("assemble_seconds", ctypes.c_double), ("storage", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("n_far_lowrank", ctypes.c_int64), ("n_far_dense", ctypes.c_int64),
                 ("u_entries", ctypes.c_int64), ("v_entries", ctypes.c_int64), ("tb_len", ctypes.c_int64),
-                ("p_len", ctypes.c_int64)]
+                ("p_len", ctypes.c_int64), ("n_far_refined", ctypes.c_int64)]
 
 
 class hm_solve_opts(ctypes.Structure):
@@ -255,7 +255,7 @@ class HMatrix:
         return r.value
 
     def far_factor_arrays(self, b, s_n, t_n):
-        """(U, V) of far block b, or None if the block is stored dense."""
+        """(U, V) of far block b, or None if the block is stored dense or was refined."""
         r = self.far_factors(b)
         if r < 0:
             return None

@@ -158,3 +158,23 @@ def test_full_size_fault_sampled_rows(dev):
     assert rel(got, ref) <= eps + 1e-6
     info = H.info()
     assert info["rank_max"] <= 160 and info["near_entries"] > 0
+
+
+@pytest.mark.parametrize("max_rank,eps", [(6, 1e-6), (12, 1e-4)])
+def test_blocks_over_the_rank_cap_are_refined(dev, max_rank, eps):
+    """A rank cap too small for the tolerance: non-converging admissible blocks are
+    replaced by their children's blocks (down to dense leaf pairs) and the product still
+    meets eps + 1e-6 against the dense oracle."""
+    import torch
+    el = synth.config_three_planes(24)
+    T = hmat.ClusterTree(el, 16, 2.0)
+    H = hmat.HMatrix(T, el, E, NU, eps, "f32", max_rank=max_rank)
+    info = H.info()
+    nfar = T.info()["n_far"]
+    assert info["n_far_refined"] > 0 and info["rank_max"] <= max_rank
+    ranks = [H.far_factors(b) for b in range(nfar)]
+    assert sum(r == -2 for r in ranks) > 0
+    A = O.dense_matrix(el, E, NU)
+    x = synth.rhs_normal(3 * el.N, 41)
+    assert rel(run_mv(dev, H, x, torch.float32), A @ x) <= eps + 1e-6
+    assert rel(run_mv(dev, H, x, torch.float64), A @ x) <= eps + 1e-6

@@ -322,6 +322,15 @@ def run_planes(args, dev, torch, hmat, synth):
 
     res["f32_16rhs_ms"] = timeit(lambda: H.matvec(X, Y, stream), args.steps)
     res["f32_1rhs_x16_ms"] = 16 * timeit(lambda: H.matvec(X[0], Y[0], stream), args.steps)
+    phases = {}
+    for nrk, xa, ya in ((16, X, Y), (1, X[0], Y[0])):
+        H.timing(True)
+        for _ in range(5):
+            H.matvec(xa, ya, stream)
+        H.timing(False)
+        ph = H.timing_read()
+        phases["%drhs" % nrk] = {k: ph[k] / max(ph["count"], 1) for k in ("gather", "phase1", "reduce", "phase2",
+                                                                          "scatter")}
     clocks = sampler.stop()
     H.check(stream)
     B1, _, _ = product_bytes(info, "f32")
@@ -341,7 +350,8 @@ def run_planes(args, dev, torch, hmat, synth):
                        "stored_bytes": info["stored_bytes"], "bytes_16rhs": b16},
             "tflops_16rhs": flops16 / t16 / 1e12, "frac_of_hbm_peak": b16 / t16 / 1e9 / hbm,
             "peak_source": peak_kind, "ms": res,
-            "speedup_16rhs_over_16x1": res["f32_1rhs_x16_ms"] / res["f32_16rhs_ms"], "clocks": clocks}
+            "speedup_16rhs_over_16x1": res["f32_1rhs_x16_ms"] / res["f32_16rhs_ms"], "clocks": clocks,
+            "phases_ms": phases}
     if not args.no_gmres:
         # the tangent A = E - diag(k), k log-uniform in [1e-3, 1e2] E/h per element: the bare
         # E of three intersecting planes is indefinite and nearly singular (GMRES with

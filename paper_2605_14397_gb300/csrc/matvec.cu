@@ -103,6 +103,31 @@ __device__ __forceinline__ FF acc_shfl(const FF& v, int o) {
     return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
 
+// Sum each of the NR accumulators over the warp, spread over the lanes: halving
+// exchanges (each lane sends the half of its values it does not keep, NR - 1 shuffles in
+// all) and then plain butterflies over the remaining lane bits.  Afterwards acc[0] of lane
+// l holds the warp sum of right-hand side k(l) (returned); lanes with the low log2(32/NR)
+// bits clear are the first holder of each k.
+template <int NR, class Acc>
+__device__ __forceinline__ int warp_reduce_scatter(Acc (&acc)[NR], int lane) {
+    int k = 0;
+#pragma unroll
+    for (int h = NR / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+            const Acc lo = acc[j], hi = acc[j + h];
+            Acc mine = up ? hi : lo;
+            acc_add(mine, acc_shfl(up ? lo : hi, o));
+            acc[j] = mine;
+        }
+        if (up) k += h;
+    }
+#pragma unroll
+    for (int o = 16 / NR; o > 0; o >>= 1) acc_add(acc[0], acc_shfl(acc[0], o));
+    return k;
+}
+
 __device__ __forceinline__ float acc_value(float a) { return a; }
 __device__ __forceinline__ double acc_value(const FF& a) { return (double)a.hi + (double)a.lo; }
 
@@ -264,7 +289,9 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int n
 }
 
 // ---- phase 2: y = [D | U] z per row leaf
-template <int MODE, class C, int NR, int RPL, int NCW>
+// RS > 1 splits each column's rows over RS warps (RPL / RS rows per lane each), so that
+// many right-hand sides fit in registers with more warps in flight.
+template <int MODE, class C, int NR, int RPL, int NCW, int RS>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     using Acc = typename AccT<MODE>::type;
     using Vv = typename AccT<MODE>::vec;
@@ -275,7 +302,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     uint64_t* empty = full + STAGES;
     int* s_flag = (int*)(empty + STAGES);
     unsigned char* stage = smem + BAR_BYTES;
-    Acc* red = (Acc*)(stage + (size_t)STAGES * STRIDE);  // [NCW][32 RPL]
+    constexpr int RPW = RPL / RS;  // rows per lane of one warp
+    constexpr int NG = NCW / RS;   // column groups
+    static_assert(RPL % RS == 0 && NCW % RS == 0, "row split must divide rows and warps");
+    Acc* red = (Acc*)(stage + (size_t)STAGES * STRIDE);  // [NG][32 RPL]
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -287,7 +317,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     }
     Vv* yc = (Vv*)a.out;
     Vv* slots = (Vv*)a.slots;
-    Acc acc[NR][RPL];
+    const int g = w / RS, rbase = (w % RS) * 32 * RPW;
+    Acc acc[NR][RPW];
     int cur = -1;
     LeafDesc L{};
 
@@ -298,11 +329,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const int64_t slot = whole ? 0 : (int64_t)(sp.slot_base + (int)blockIdx.x - sp.w_first);
         for (int k = 0; k < a.nr; ++k) {
 #pragma unroll
-            for (int i = 0; i < RPL; ++i) red[(size_t)w * (32 * RPL) + lane + 32 * i] = acc[k][i];
+            for (int i = 0; i < RPW; ++i) red[(size_t)g * (32 * RPL) + rbase + lane + 32 * i] = acc[k][i];
             consumer_sync(NCW * 32);
             for (int r = threadIdx.x; r < rows; r += NCW * 32) {
                 Acc s = red[r];
-                for (int q = 1; q < NCW; ++q) acc_add(s, red[(size_t)q * (32 * RPL) + r]);
+                for (int q = 1; q < NG; ++q) acc_add(s, red[(size_t)q * (32 * RPL) + r]);
                 if (whole)
                     yc[(int64_t)k * a.ndof + 3 * (int64_t)L.begin + r] = (Vv)acc_value(s);
                 else
@@ -345,7 +376,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
 #pragma unroll
             for (int k = 0; k < NR; ++k)
 #pragma unroll
-                for (int j = 0; j < RPL; ++j) acc_zero(acc[k][j]);
+                for (int j = 0; j < RPW; ++j) acc_zero(acc[k][j]);
         }
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
         const unsigned char* stg = stage + (size_t)s * STRIDE;
@@ -353,15 +384,15 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const Vv* zb = (const Vv*)stg + (z0 - (z0 & ~(int64_t)(ZR::ALIGN - 1)));
         const unsigned char* buf = stg + ZR::BYTES;
         const int rows = 3 * L.n;
-        for (int c = w; c < ch.ncols; c += NCW) {
+        for (int c = g; c < ch.ncols; c += NG) {
             decltype(make_z(Vv(0))) zv[NR];
 #pragma unroll
             for (int k = 0; k < NR; ++k) zv[k] = make_z(k < a.nr ? zb[c * a.nr + k] : (Vv)0);
             if (ch.kind == 0) {
                 const float* col = (const float*)buf + (size_t)c * ch.ld;
 #pragma unroll
-                for (int ii = 0; ii < RPL; ++ii) {
-                    const int r = lane + 32 * ii;
+                for (int ii = 0; ii < RPW; ++ii) {
+                    const int r = rbase + lane + 32 * ii;
                     const float v = r < rows ? col[r] : 0.f;
 #pragma unroll
                     for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
@@ -369,8 +400,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
             } else {
                 const C* col = (const C*)buf + (size_t)c * ch.ld;
 #pragma unroll
-                for (int ii = 0; ii < RPL; ++ii) {
-                    const int r = lane + 32 * ii;
+                for (int ii = 0; ii < RPW; ++ii) {
+                    const int r = rbase + lane + 32 * ii;
                     const float v = r < rows ? coef(col, r) : 0.f;
 #pragma unroll
                     for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
@@ -437,12 +468,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) acc_fma(acc[k], v, xr[k][ii]);
             }
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc_add(acc[k], acc_shfl(acc[k], o));
-                if (lane == 0 && k < a.nr) P[(ch.zoff + c) * a.nr + k] = (Vv)acc_value(acc[k]);
-            }
+            const int k = warp_reduce_scatter<NR>(acc, lane);
+            if ((lane & (32 / NR - 1)) == 0 && k < a.nr) P[(ch.zoff + c) * a.nr + k] = (Vv)acc_value(acc[0]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
@@ -474,19 +501,26 @@ void mark(HMat& H, int idx, cudaStream_t st) {
     if (idx == EV_PER_PRODUCT - 1) H.ev_used += EV_PER_PRODUCT;
 }
 
+// consumer warps of phase 1 and phase 2, and phase 2's row split, per right-hand-side
+// count: as many warps as the per-thread registers (accumulators and operands) allow
 template <int MODE>
-constexpr int ncw_for(int NR) {
-    return NR > 1 ? 8 : 16;
+constexpr int ncw1_for(int NR) {
+    return NR > 4 ? 8 : 16;
 }
+template <int MODE>
+constexpr int ncw2_for(int NR) {
+    return NR > 4 && MODE == 1 ? 8 : 16;
+}
+constexpr int rs_for(int NR) { return NR > 4 ? 2 : 1; }
 
 template <int MODE, class C, int NR, int RPL>
 void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool timed, cudaStream_t st) {
-    constexpr int NCW = ncw_for<MODE>(NR);
+    constexpr int NCW = ncw1_for<MODE>(NR), NCW2 = ncw2_for<MODE>(NR), RS = rs_for(NR);
     using Acc = typename AccT<MODE>::type;
     using V = typename AccT<MODE>::vec;
     const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES;
     const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
-                         (size_t)NCW * 32 * RPL * sizeof(Acc);
+                         (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc);
     // shared-memory opt-in, once per device for each instantiation
     static bool attr_done[64] = {};
     int dev = 0;
@@ -494,7 +528,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
         HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem1));
-        HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW2, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem2));
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
@@ -518,7 +552,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     a.chunks = PL.ch2.p;
     a.cta_begin = PL.cta2.p;
     a.split = PL.split.p;
-    k_phase2<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem2, st>>>(a);
+    k_phase2<MODE, C, NR, RPL, NCW2, RS><<<H.grid, (NCW2 + 1) * 32, smem2, st>>>(a);
     HM_LAUNCH_CHECK();
     if (timed) mark(H, 4, st);
 }

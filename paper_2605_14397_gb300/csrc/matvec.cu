@@ -131,6 +131,44 @@ __device__ __forceinline__ int warp_reduce_scatter(Acc (&acc)[NR], int lane) {
 __device__ __forceinline__ float acc_value(float a) { return a; }
 __device__ __forceinline__ double acc_value(const FF& a) { return (double)a.hi + (double)a.lo; }
 
+// z operands of one column for NR right-hand sides (p: the column's nr interleaved
+// values in shared memory).  With nr == NR (a multiple of 4 for floats, of 2 for
+// doubles) the values are 16-byte aligned and read as vectors.
+template <int NR>
+__device__ __forceinline__ void load_z(Z32 (&z)[NR], const float* p, int nr) {
+    if constexpr (NR % 4 == 0) {
+        if (nr == NR) {
+#pragma unroll
+            for (int q = 0; q < NR / 4; ++q) {
+                const float4 f = reinterpret_cast<const float4*>(p)[q];
+                z[4 * q] = Z32{f.x};
+                z[4 * q + 1] = Z32{f.y};
+                z[4 * q + 2] = Z32{f.z};
+                z[4 * q + 3] = Z32{f.w};
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) z[k] = make_z(k < nr ? p[k] : 0.f);
+}
+template <int NR>
+__device__ __forceinline__ void load_z(Z64 (&z)[NR], const double* p, int nr) {
+    if constexpr (NR % 2 == 0) {
+        if (nr == NR) {
+#pragma unroll
+            for (int q = 0; q < NR / 2; ++q) {
+                const double2 f = reinterpret_cast<const double2*>(p)[q];
+                z[2 * q] = make_z(f.x);
+                z[2 * q + 1] = make_z(f.y);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) z[k] = make_z(k < nr ? p[k] : 0.0);
+}
+
 __device__ __forceinline__ float coef(const float* p, int i) { return p[i]; }
 __device__ __forceinline__ float coef(const uint16_t* p, int i) { return __uint_as_float(((uint32_t)p[i]) << 16); }
 
@@ -327,7 +365,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const int rows = 3 * L.n;
         const bool whole = sp.nparts == 1;
         const int64_t slot = whole ? 0 : (int64_t)(sp.slot_base + (int)blockIdx.x - sp.w_first);
-        for (int k = 0; k < a.nr; ++k) {
+        // k unrolled at compile time: a runtime index into acc would move it to local memory
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            if (k >= a.nr) break;
 #pragma unroll
             for (int i = 0; i < RPW; ++i) red[(size_t)g * (32 * RPL) + rbase + lane + 32 * i] = acc[k][i];
             consumer_sync(NCW * 32);
@@ -384,25 +425,28 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const Vv* zb = (const Vv*)stg + (z0 - (z0 & ~(int64_t)(ZR::ALIGN - 1)));
         const unsigned char* buf = stg + ZR::BYTES;
         const int rows = 3 * L.n;
+        // Rows at or beyond `rows` read whatever follows the column in shared memory (the
+        // next column, stage or the reduction buffer: always inside the allocation); their
+        // accumulators are never flushed, so no bound check is needed per coefficient.
         for (int c = g; c < ch.ncols; c += NG) {
             decltype(make_z(Vv(0))) zv[NR];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) zv[k] = make_z(k < a.nr ? zb[c * a.nr + k] : (Vv)0);
+            if constexpr (NR == 1)
+                zv[0] = make_z(zb[c]);
+            else
+                load_z<NR>(zv, zb + (size_t)c * a.nr, a.nr);
             if (ch.kind == 0) {
-                const float* col = (const float*)buf + (size_t)c * ch.ld;
+                const float* col = (const float*)buf + (size_t)c * ch.ld + rbase + lane;
 #pragma unroll
                 for (int ii = 0; ii < RPW; ++ii) {
-                    const int r = rbase + lane + 32 * ii;
-                    const float v = r < rows ? col[r] : 0.f;
+                    const float v = col[32 * ii];
 #pragma unroll
                     for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
                 }
             } else {
-                const C* col = (const C*)buf + (size_t)c * ch.ld;
+                const C* col = (const C*)buf + (size_t)c * ch.ld + rbase + lane;
 #pragma unroll
                 for (int ii = 0; ii < RPW; ++ii) {
-                    const int r = rbase + lane + 32 * ii;
-                    const float v = r < rows ? coef(col, r) : 0.f;
+                    const float v = coef(col, 32 * ii);
 #pragma unroll
                     for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
                 }
@@ -509,7 +553,7 @@ constexpr int ncw1_for(int NR) {
 }
 template <int MODE>
 constexpr int ncw2_for(int NR) {
-    return NR > 4 && MODE == 1 ? 8 : 16;
+    return NR > 1 && MODE == 1 ? 8 : 16;
 }
 constexpr int rs_for(int NR) { return NR > 4 ? 2 : 1; }
 

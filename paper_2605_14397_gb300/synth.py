@@ -189,3 +189,16 @@ def k_loguniform(N, seed, E=1.0, h=0.01, lo=1e-3, hi=1e2):
 def random_vector(n, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.normal(size=n)
+
+
+def lp_initial_weights(hidden=32, seed=1607, n_features=8, n_out=3):
+    """Seeded initial parameters of the learned correction's network, in the order
+    W1 (H x F), b1, W2 (H x H), b2, W3 (3 x H), b3: hidden weights uniform in
+    +-1/sqrt(fan-in), biases zero, output layer zero (the untrained correction is the
+    identity)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H, F = hidden, n_features
+    W1 = rng.uniform(-1.0, 1.0, size=(H, F)) / math.sqrt(F)
+    W2 = rng.uniform(-1.0, 1.0, size=(H, H)) / math.sqrt(H)
+    parts = [W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), np.zeros(n_out * H), np.zeros(n_out)]
+    return np.concatenate(parts)

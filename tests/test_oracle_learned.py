@@ -1,0 +1,138 @@
+"""Pins of the oracle's learned block-Jacobi correction (oracle/learned.py) against what
+the mathematics fixes: central finite differences of the loss (h = 1e-6, FP64), the
+identity network (zero output layer) and its closed-form gradient, the quadratic
+minimiser of the per-(leaf, component) loss, Adam's first step in closed form, feature
+invariants and special cases, and the training statistics against least squares."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import learned as Lr
+from oracle import oracle as O
+from paper_2605_14397_gb300 import synth
+
+H = 6
+
+
+def random_problem(seed, S=7):
+    rng = np.random.default_rng(seed)
+    theta = rng.normal(size=Lr.param_count(H)) * 0.7
+    X = rng.normal(size=(S, Lr.N_FEATURES))
+    qxy = rng.normal(size=(S, 3))
+    qyy = rng.uniform(0.2, 2.0, size=(S, 3))
+    qxx = rng.uniform(0.5, 3.0, size=(S, 3))
+    return theta, X, np.hstack([qxy, qyy, qxx])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gradient_matches_central_differences(seed):
+    theta, X, Q = random_problem(seed)
+    _, g = Lr.loss_and_grad(theta, H, X, Q)
+    h = 1e-6
+    fd = np.zeros_like(theta)
+    for i in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd[i] = (Lr.loss_and_grad(tp, H, X, Q)[0] - Lr.loss_and_grad(tm, H, X, Q)[0]) / (2 * h)
+    assert np.linalg.norm(fd - g) <= 1e-6 * np.linalg.norm(g)
+
+
+def test_zero_output_layer_is_block_jacobi():
+    theta, X, Q = random_problem(3)
+    W1, b1, W2, b2, W3, b3 = Lr.unpack(theta, H)
+    t0 = Lr.pack(W1, b1, W2, b2, np.zeros_like(W3), np.zeros_like(b3))
+    d, _ = Lr.forward(t0, H, X)
+    assert np.all(d == 1.0)
+    loss, g = Lr.loss_and_grad(t0, H, X, Q)
+    qxy, qyy, qxx = Q[:, 0:3], Q[:, 3:6], Q[:, 6:9]
+    assert loss == pytest.approx((qxx - 2 * qxy + qyy).sum(), rel=1e-14)
+    gW1, gb1, gW2, gb2, gW3, gb3 = Lr.unpack(g, H)
+    for z in (gW1, gb1, gW2, gb2):
+        assert np.all(z == 0.0)
+    # dloss/db3_a = sum_s 2 (q_yy - q_xy) * 0.5 (d/do at o = 0 is 1/2)
+    assert np.allclose(gb3, (qyy - qxy).sum(axis=0), rtol=1e-13)
+
+
+def test_quadratic_minimiser_per_component():
+    # one sample; the output bias alone sets d = q_xy / q_yy, where the loss is minimal
+    qxy = np.array([0.9, 1.1, 0.7])
+    qyy = np.array([1.0, 1.0, 1.0])
+    qxx = np.array([2.0, 3.0, 1.0])
+    Q = np.hstack([qxy, qyy, qxx])[None, :]
+    dstar = qxy / qyy
+    theta = np.zeros(Lr.param_count(H))
+    W1, b1, W2, b2, W3, b3 = Lr.unpack(theta, H)
+    b3 = np.arctanh(2.0 * (dstar - 1.0))
+    t = Lr.pack(W1, b1, W2, b2, W3, b3)
+    loss, g = Lr.loss_and_grad(t, H, np.zeros((1, Lr.N_FEATURES)), Q)
+    assert loss == pytest.approx((qxx - qxy ** 2 / qyy).sum(), rel=1e-13)
+    assert np.abs(Lr.unpack(g, H)[5]).max() < 1e-13
+
+
+def test_adam_first_step_closed_form():
+    rng = np.random.default_rng(4)
+    theta = rng.normal(size=20)
+    g = rng.normal(size=20)
+    lr = 1e-3
+    t1, m, v = Lr.adam_step(theta, g, np.zeros(20), np.zeros(20), 1, lr)
+    # bias-corrected moments equal g and g^2 after one step
+    assert np.allclose(t1, theta - lr * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def _tree_arrays(el, leaf):
+    T = O.cluster_tree(el, leaf)
+    lv = T.leaves()
+    return T.perm, np.array([T.begin[q] for q in lv]), np.array([T.end[q] for q in lv])
+
+
+def test_features_special_cases():
+    el = synth.config_penny(16)
+    perm, begin, end = _tree_arrays(el, 16)
+    h = 2.0 / 16
+    k = np.full(el.N, 0.3 / h)  # k h / E = 0.3 everywhere
+    F = Lr.leaf_features(el, k, 1.0, perm, begin, end)
+    kap = math.log10(0.3 + 1e-6)
+    assert np.allclose(F[:, 0], kap) and np.allclose(F[:, 2], kap) and np.allclose(F[:, 3], kap)
+    assert np.allclose(F[:, 1], 0.0, atol=1e-15)
+    assert np.all(F[:, 4] == 1.0)  # 0.3 < 0.5: soft
+    assert np.allclose(F[:, 5], np.log10(end - begin))
+    assert np.allclose(F[:, 6], 1.0)  # planar
+    assert np.allclose(F[:, 7], math.log10(1001.0))  # no other plane
+    # a rigid translation changes nothing
+    moved = synth.config_penny(16)
+    moved.c = moved.c + np.array([3.0, -2.0, 5.0])
+    assert np.allclose(Lr.leaf_features(moved, k, 1.0, perm, begin, end), F, atol=1e-12)
+
+
+def test_features_two_planes_distance_and_mixture():
+    el = synth.config_crack_fault(h=0.25)
+    perm, begin, end = _tree_arrays(el, 8)
+    rng = np.random.default_rng(5)
+    k = np.exp(rng.uniform(math.log(1e-3), math.log(1e2), size=el.N)) / 0.25
+    F = Lr.leaf_features(el, k, 1.0, perm, begin, end)
+    assert np.all(F[:, 7] < math.log10(1001.0))  # every leaf sees the other plane
+    s = k * 0.25
+    for l in range(len(begin)):
+        idx = perm[begin[l]:end[l]]
+        assert F[l, 4] == pytest.approx(np.mean(s[idx] < 0.5))
+        assert F[l, 2] <= F[l, 0] <= F[l, 3]
+
+
+def test_stats_give_least_squares_scaling():
+    el = synth.config_penny(12)
+    perm, begin, end = _tree_arrays(el, 16)
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(2, 3 * el.N))
+    y = rng.normal(size=(2, 3 * el.N))
+    S = Lr.leaf_stats(x, y, perm, begin, end)
+    for l in range(len(begin)):
+        idx = perm[begin[l]:end[l]]
+        for a in range(3):
+            dofs = 3 * idx + a
+            ls = np.linalg.lstsq(y[:, dofs].reshape(-1, 1), x[:, dofs].reshape(-1), rcond=None)[0][0]
+            assert S[l, a] / S[l, 3 + a] == pytest.approx(ls, rel=1e-12)
+    Q = Lr.samples([S, 2 * S])
+    assert Q[:, 6:9].sum() == pytest.approx(1.0)

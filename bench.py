@@ -47,7 +47,9 @@ def parse():
     p.add_argument("--no-gmres", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--grid", type=int, default=256, help="disk grid size (256: the 51,468-element fault)")
-    p.add_argument("--workload", default="fault", choices=["fault", "faults64", "planes"],
+    p.add_argument("--lp-h", type=float, default=0.01, help="element size of the crack + fault (learned workload)")
+    p.add_argument("--lp-train", type=int, default=12, help="training systems (learned workload)")
+    p.add_argument("--workload", default="fault", choices=["fault", "faults64", "planes", "learned"],
                    help="fault: the 51,468-element disk fault (default); faults64: 64 independent faults, "
                         "batched product vs per-fault launches; planes: three intersecting 300x300 planes, "
                         "16 right-hand sides")
@@ -395,6 +397,84 @@ def run_planes(args, dev, torch, hmat, synth):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args, dev, torch, hmat, synth):
+    """Learned block-Jacobi correction on the crack crossing a fault (h = 0.01: 40,000 +
+    160,000 elements): tangent systems A = E - diag(k), k log-uniform in [1e-3, 1e2] E/h
+    per element, a fresh draw per system, N(0, 1) right-hand sides.  Training: systems
+    solved with block-Jacobi (seeds 1605000 + i), 500 Adam steps; validation on 4 more
+    systems decides the fallback (plain block-Jacobi unless the learned correction needs
+    fewer iterations); test: 8 held-out systems (seeds 1606000 + i), GMRES to 1e-8,
+    restart 50, plain FP64 mode, both preconditioners."""
+    import numpy as np
+    h = args.lp_h
+    el = synth.config_crack_fault(h=h)
+    E, nu, eps = 1.0, 0.25, 1e-6
+    t0 = time.perf_counter()
+    T = hmat.ClusterTree(el, 64, 2.0)
+    H = hmat.HMatrix(T, el, E, nu, eps, "f32")
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    nd = 3 * el.N
+
+    def system(seed, nrhs=1):
+        k = torch.as_tensor(synth.k_loguniform(el.N, seed, E=E, h=h), device=dev)
+        b = torch.as_tensor(synth.rhs_normal(nd, seed, nrhs=nrhs), device=dev).contiguous()
+        if nrhs == 1:
+            b = b.reshape(-1)
+        return k, b
+
+    def solve(k, b, precond, model=None, tol=1e-8):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        info = H.solve(b, x, k, precond=precond, model=model, tol=tol, restart=50, maxit=3000, raise_on_error=False)
+        torch.cuda.synchronize()
+        return x, info[0], time.perf_counter() - t
+
+    model = hmat.LearnedCorrection(synth.lp_initial_weights(32, seed=1607), hidden=32)
+    t0 = time.perf_counter()
+    for i in range(args.lp_train):
+        k, b = system(1605000 + i, nrhs=2)
+        x = torch.zeros_like(b)
+        H.solve(b, x, k, precond="blockj", tol=1e-10, restart=50, maxit=3000, raise_on_error=False)
+        model.add_system(H, k, b, x)
+    t_data = time.perf_counter() - t0
+    l0, _ = model.loss_grad()
+    t0 = time.perf_counter()
+    l1 = model.train(500, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    l2, _ = model.loss_grad()
+    val = {"blockj": [], "learned": []}
+    for i in range(4):
+        k, b = system(1605500 + i)
+        val["blockj"].append(solve(k, b, "blockj")[1]["iters"])
+        val["learned"].append(solve(k, b, "learned", model)[1]["iters"])
+    fallback = float(np.mean(val["learned"])) >= float(np.mean(val["blockj"]))
+    model.set_fallback(fallback)
+    test = {"blockj": {"iters": [], "s": [], "relres": []}, "learned": {"iters": [], "s": [], "relres": []}}
+    for i in range(8):
+        k, b = system(1606000 + i)
+        for pc in ("blockj", "learned"):
+            _, inf, dt = solve(k, b, pc, model if pc == "learned" else None)
+            test[pc]["iters"].append(inf["iters"])
+            test[pc]["s"].append(dt)
+            test[pc]["relres"].append(inf["relres"])
+    tb, tl = sum(test["blockj"]["s"]), sum(test["learned"]["s"])
+    line = {"metric": "GMRES time-to-1e-8 on held-out tangent systems, learned correction vs block-Jacobi",
+            "value": tb / tl, "unit": "x (block-Jacobi time / learned time)", "n_gpus": 1, "steps": 8, "warmup": 0,
+            "ms_per_step": 1e3 * tl / 8, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 Krylov, f32 preconditioner and network", "data": "synthetic (seeded k, right-hand sides)",
+            "config": {"workload": "crack x in [-2,2], z in [-0.5,0.5] crossing a 4x4 fault, h=%g: N=%d; "
+                                   "k ~ logU[1e-3, 1e2] E/h per element" % (h, el.N),
+                       "setup_s": t_setup, "train_systems": args.lp_train, "train_rhs_per_system": 2,
+                       "adam_steps": 500, "lr": 3e-3, "hidden": 32},
+            "loss": {"initial": l0, "before_last_step": l1, "final": l2},
+            "data_s": t_data, "train_s": t_train, "validation_iters": val, "fallback": fallback,
+            "test": test, "mean_iters": {pc: float(np.mean(test[pc]["iters"])) for pc in test}}
+    print(json.dumps(line), flush=True)
+
+
 def cores():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n else os.cpu_count()
@@ -481,6 +561,9 @@ def main():
         return
     if args.workload == "planes":
         run_planes(args, dev, torch, hmat, synth)
+        return
+    if args.workload == "learned":
+        run_learned(args, dev, torch, hmat, synth)
         return
     el = synth.config_fault(args.grid)
     E, nu, eps = 1.0, 0.25, 1e-6

@@ -164,6 +164,7 @@ typedef struct {
     int64_t p_len;            /* per-leaf partials of V^T x */
     int64_t n_far_refined;    /* admissible blocks whose cross approximation did not converge
                                  below the rank cap, replaced by their children's blocks */
+    int64_t n_leaves;         /* leaf clusters (block-Jacobi blocks) */
 } hm_hmat_info;
 
 hm_status hm_assemble_hmat(const hm_tree* t, const hm_elements* el, const hm_assemble_opts* opt,
@@ -228,6 +229,8 @@ hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
 #define HM_SOLVE_F64 1
 #define HM_SOLVE_MIXED 2
 
+typedef struct hm_lp hm_lp;  /* learned block-Jacobi correction (below) */
+
 typedef struct {
     double tol;        /* relative residual target (0 = 1e-8) */
     int restart;       /* Krylov dimension m (0 = 50) */
@@ -237,6 +240,7 @@ typedef struct {
     double inner_tol;  /* mixed: relative tolerance of each correction solve (0 = 1e-2) */
     int max_outer;     /* mixed: cap on refinement steps (0 = 40) */
     int pad_;
+    const hm_lp* lp;   /* model for HM_PRECOND_LEARNED (NULL otherwise) */
 } hm_solve_opts;
 
 typedef struct {
@@ -286,6 +290,68 @@ hm_status hm_matvec_graph(const hm_hmat* h, const void* x_dev, void* y_dev, int 
 hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const int* leaf_sizes, int n_leaf,
                       const double* etas, int n_eta, int budget_ms, char* json_out, size_t cap,
                       void* stream);
+
+/* ---------------------------------------------------------------- learned correction
+ * The paper preconditions the A11 system with (point) Jacobi (Sec. 3.3.1) and learns
+ * nothing; this library adds an optional learned correction of its leaf block-Jacobi
+ * preconditioner B of A = E - diag(k) (eq. jac_mech):
+ *   M^-1 r = D B^-1 r,  D = diag(d_(leaf, component)),  d = 1 + 0.5 tanh(o),
+ *   o = W3 tanh(W2 tanh(W1 f + b1) + b2) + b3,
+ * per leaf and DOF component, from eight leaf features f: mean, standard deviation, min
+ * and max of log10(k h / E + 1e-6) over the leaf's elements (h = sqrt(4 a b)), the
+ * fraction with k h / E < 0.5, log10(element count), |mean normal|, and
+ * log10(1 + d / hbar) with d the distance from the leaf centroid to the nearest leaf
+ * centroid of another normal direction (1000 hbar if none).  W3 = 0, b3 = 0 is plain
+ * block-Jacobi.  Parameters (param_count(H) values, H = 16, 32 or 64 hidden units per
+ * layer) in the order W1 (H x 8, row-major), b1, W2 (H x H), b2, W3 (3 x H), b3.
+ * Training (Adam, beta = 0.9 / 0.999, eps = 1e-8, full batch) minimises
+ *   loss = (1 / n_groups) sum_samples sum_a  q_xx - 2 d_a q_xy + d_a^2 q_yy,
+ * a sample being one leaf of one solved system A x = b with q = S / T: S the leaf and
+ * component sums of x y, y y, x x over the system's right-hand sides (y = B^-1 b), T
+ * the system's sum of x x -- the fit of D B^-1 b to x = A^-1 b.
+ * The model's parameters live in host memory (device copies made on first GPU use), so
+ * create / add_samples / get_params / set_fallback / info / save / load need no GPU.
+ * A model flagged `fallback` makes HM_PRECOND_LEARNED apply plain block-Jacobi (set it
+ * when validation shows no gain). */
+typedef struct {
+    int32_t hidden;
+    int32_t fallback;
+    int64_t n_params;
+    int64_t n_samples;
+    int64_t n_groups;
+    int64_t steps;        /* Adam steps taken */
+    double last_loss;     /* loss before the last step of the last hm_lp_train */
+} hm_lp_info;
+
+/* number of parameters for `hidden` units (16, 32 or 64), -1 otherwise */
+int64_t hm_lp_param_count(int hidden);
+/* new model with initial parameters theta0 (host, param_count(hidden) doubles) */
+hm_status hm_lp_create(int hidden, const double* theta0, hm_lp** out);
+/* add n samples (host: features n x 8 row-major, targets q n x 9 = [q_xy | q_yy | q_xx]),
+ * counted as one group */
+hm_status hm_lp_add_samples(hm_lp* lp, const double* features, const double* q, int64_t n);
+/* add the leaves of one solved system as one group: k_dev (N doubles, user order, or
+ * NULL), b_dev and x_dev (nrhs x 3N doubles, user order) with A x = b; computes
+ * B^-1 b, the statistics and the features on the device.  Synchronises the stream. */
+hm_status hm_lp_add_system(hm_lp* lp, const hm_hmat* h, const double* k_dev, const double* b_dev,
+                           const double* x_dev, int nrhs, void* stream);
+hm_status hm_lp_clear_samples(hm_lp* lp);
+/* loss and gradient (param_count doubles, host; may be NULL) at the current parameters */
+hm_status hm_lp_loss_grad(hm_lp* lp, double* loss_out, double* grad_out, void* stream);
+/* `steps` full-batch Adam steps with learning rate lr; loss_out: loss before the last step */
+hm_status hm_lp_train(hm_lp* lp, int steps, double lr, double* loss_out, void* stream);
+/* features (n_leaves x 8) and scalings d (n_leaves x 3) for this H-matrix and k, to host
+ * (either may be NULL); leaves in cluster order */
+hm_status hm_lp_predict(hm_lp* lp, const hm_hmat* h, const double* k_dev, double* features_out,
+                        double* d_out, void* stream);
+hm_status hm_lp_get_params(const hm_lp* lp, double* theta_out);
+hm_status hm_lp_set_fallback(hm_lp* lp, int fallback);
+hm_status hm_lp_get_info(const hm_lp* lp, hm_lp_info* info);
+/* binary file: "HMLP0001", hidden and fallback (int32), steps (int64), then the
+ * parameters and both Adam moments (float32 each) */
+hm_status hm_lp_save(const hm_lp* lp, const char* path);
+hm_status hm_lp_load(const char* path, hm_lp** out);
+void hm_lp_destroy(hm_lp* lp);
 
 /* Synchronise `stream` and report whether a device-side wait of an earlier product on
  * this H-matrix gave up (HM_ETIMEOUT; the flags are then cleared).  The product kernels

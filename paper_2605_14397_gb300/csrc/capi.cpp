@@ -4,13 +4,11 @@
 #include <string>
 
 #include "hmat_impl.h"
+#include "learned.h"
 #include "tree.h"
 
 struct hm_tree {
     hm::Tree t;
-};
-struct hm_hmat {
-    hm::HMat h;
 };
 
 namespace hm {
@@ -138,6 +136,7 @@ hm_status hm_hmat_get_info(const hm_hmat* hh, hm_hmat_info* info) {
     info->n_far_dense = H.n_dense_far;
     info->n_far_lowrank = H.n_far - H.n_dense_far - H.n_refined;
     info->n_far_refined = H.n_refined;
+    info->n_leaves = H.n_leaves;
     info->u_entries = info->v_entries = 0;
     for (const hm::FarDesc& F : H.h_far) {
         info->u_entries += 3LL * F.rank * F.s_n;
@@ -212,7 +211,8 @@ hm_status hm_gmres_solve(const hm_hmat* hh, const double* k_dev, double shift, c
         o.mode = HM_SOLVE_F64;
     }
     if (!std::isfinite(shift)) hm::fail(HM_ENAN, "gmres_solve: shift is not finite");
-    hm::gmres_solve(const_cast<hm::HMat&>(hh->h), k_dev, shift, b_dev, x_dev, nrhs, o, info, (cudaStream_t)stream);
+    hm::gmres_solve(const_cast<hm::HMat&>(hh->h), k_dev, shift, b_dev, x_dev, nrhs, o, info, (cudaStream_t)stream,
+                    o.lp ? &o.lp->m : nullptr);
     HM_API_END
 }
 

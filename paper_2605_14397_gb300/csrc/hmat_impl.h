@@ -176,11 +176,17 @@ void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac,
 void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M);
 void graphs_clear(HMat& H);
 void matvec_graph(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
+struct LPModel;
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
-                 const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st);
+                 const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp = nullptr);
 inline bool has_factors(const HMat& H, int fac) {
     return fac == 0 ? (H.storage == HM_F32 || H.storage == HM_F32_BF16)
                     : (H.storage == HM_BF16 || H.storage == HM_F32_BF16);
 }
 
 }  // namespace hm
+
+// C handle of an assembled H-matrix (include/hmat.h)
+struct hm_hmat {
+    hm::HMat h;
+};

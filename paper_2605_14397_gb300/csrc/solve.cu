@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "hmat_impl.h"
+#include "learned.h"
 
 namespace hm {
 
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(512) k_bj_build(const LeafDesc* __restrict__ l
 __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ leaves, const float* __restrict__ binv,
                                                   const int64_t* __restrict__ binv_off, const double* __restrict__ v,
                                                   double* __restrict__ z, float* __restrict__ zf, int64_t ndof, int nr,
-                                                  const CycleState* __restrict__ cs, int identity) {
+                                                  const CycleState* __restrict__ cs, int identity,
+                                                  const float* __restrict__ dsc) {
     __shared__ double red[8][384];
     const LeafDesc L = leaves[blockIdx.x];
     const int n = 3 * L.n;
@@ -205,6 +207,7 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
             double s = 0.0;
             for (int q = 0; q < 8; ++q) s += red[q][r];
+            if (dsc) s *= (double)dsc[3 * (int64_t)blockIdx.x + r % 3];  // learned correction D
             zk[r] = s;
             if (zf) zf[(base + r) * nr + k] = (float)s;
         }
@@ -496,7 +499,8 @@ struct SolveWS {
     int nr = 0, m = 0;
     int64_t ndof = 0, vstride = 0;
     DevBuf<double> V, Z, w, r, xc, bc, dc, corr, y64, zi, Hm, cs, sn, g, ylsq, part, h1, h2;
-    DevBuf<float> zf, y32, binv, bjscratch;
+    DevBuf<float> zf, y32, binv, bjscratch, dsc;
+    bool dsc_on = false;  // apply the learned per-leaf scalings after block-Jacobi
     DevBuf<int64_t> binv_off, self_off;
     DevBuf<CycleState> st;
     DevBuf<int> active, err, alldone;
@@ -633,7 +637,8 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
         const double* vj = W.V.p + (int64_t)j * nr * W.vstride;
         double* zj = W.Z.p + (int64_t)j * nr * W.vstride;
         k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, vj, zj,
-                                               dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p, precond ? 0 : 1);
+                                               dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p, precond ? 0 : 1,
+                                               W.dsc_on ? W.dsc.p : nullptr);
         HM_LAUNCH_CHECK();
         if (dtype == HM_F64) {
             apply_E(H, W, zj, nullptr, W.y64.p, nr, HM_F64, fac, st, W.alldone.p);
@@ -724,10 +729,45 @@ void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& t
     }
 }
 
+// block-Jacobi inverses of the leaf blocks of E - diag(W.dc)
+void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
+    HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
+    const size_t smem = W.bj_needs_global ? 0 : sizeof(float) * BJ_MAX_ROWS_SMEM * BJ_MAX_ROWS_SMEM;
+    if (smem > 48 * 1024)
+        HM_CUDA(cudaFuncSetAttribute(k_bj_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bj_build<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.binv.p, W.binv_off.p,
+                                              W.bjscratch.p, W.bj_needs_global ? 0 : 1, W.err.p);
+    HM_LAUNCH_CHECK();
+    int e = 0;
+    HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (e) fail(HM_EBREAKDOWN, "a diagonal leaf block of A is singular");
+}
+
 }  // namespace
 
+void to_cluster(HMat& H, const double* user, double* cluster, int nr, cudaStream_t st) {
+    k_to_cluster<<<g1(H.ndof * nr), 256, 0, st>>>(user, cluster, H.perm.p, H.ndof, nr);
+    HM_LAUNCH_CHECK();
+}
+
+void bj_solve_cluster(HMat& H, const double* kel, double shift, const double* v, double* z, int nr,
+                      cudaStream_t st) {
+    if (nr < 1 || nr > 16) fail(HM_EINVAL, "block-Jacobi solve: 1 to 16 right-hand sides");
+    SolveWS& W = workspace(H, nr, 1, st);
+    k_diag<<<g1(H.ndof), 256, 0, st>>>(kel, shift, H.perm.p, H.ndof, W.dc.p);
+    HM_LAUNCH_CHECK();
+    bj_build(H, W, st);
+    std::vector<CycleState> cs(nr, CycleState{0, 0, 0, 0, 0.0, 0.0});
+    HM_CUDA(cudaMemcpyAsync(W.st.p, cs.data(), nr * sizeof(CycleState), cudaMemcpyHostToDevice, st));
+    k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, v, z, nullptr, H.ndof, nr, W.st.p, 0,
+                                           nullptr);
+    HM_LAUNCH_CHECK();
+    HM_CUDA(cudaStreamSynchronize(st));
+}
+
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
-                 const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st) {
+                 const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp) {
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     if (nrhs < 1 || nrhs > 16) fail(HM_EINVAL, "gmres_solve: 1 to 16 right-hand sides");
@@ -738,8 +778,9 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     const int maxit = o.maxit > 0 ? o.maxit : 2000;
     const int mode = o.mode ? o.mode : HM_SOLVE_F64;
     if (mode != HM_SOLVE_F64 && mode != HM_SOLVE_MIXED) fail(HM_EINVAL, "gmres_solve: unknown mode");
-    if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ)
-        fail(HM_EINVAL, "gmres_solve: preconditioner not available in this call");
+    if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ && o.precond != HM_PRECOND_LEARNED)
+        fail(HM_EINVAL, "gmres_solve: unknown preconditioner");
+    if (o.precond == HM_PRECOND_LEARNED && !lp) fail(HM_EINVAL, "gmres_solve: the learned preconditioner needs a model");
     if (!has_factors(H, 0)) fail(HM_EINVAL, "gmres_solve: the FP32 factors are required (storage F32 or F32_BF16)");
     const int inner_fac = has_factors(H, 1) ? 1 : 0;
     SolveWS& W = workspace(H, nrhs, m, st);
@@ -749,19 +790,15 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     k_diag<<<g1(n), 256, 0, st>>>(kel, shift, H.perm.p, n, W.dc.p);
     k_to_cluster<<<g1(n * nrhs), 256, 0, st>>>(b, W.bc.p, H.perm.p, n, nrhs);
     HM_LAUNCH_CHECK();
-    const bool precond = o.precond == HM_PRECOND_BLOCKJ;
+    const bool precond = o.precond == HM_PRECOND_BLOCKJ || o.precond == HM_PRECOND_LEARNED;
+    W.dsc_on = false;
     if (precond) {
-        HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
-        const size_t smem = W.bj_needs_global ? 0 : sizeof(float) * BJ_MAX_ROWS_SMEM * BJ_MAX_ROWS_SMEM;
-        if (smem > 48 * 1024)
-            HM_CUDA(cudaFuncSetAttribute(k_bj_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_bj_build<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.binv.p,
-                                                  W.binv_off.p, W.bjscratch.p, W.bj_needs_global ? 0 : 1, W.err.p);
-        HM_LAUNCH_CHECK();
-        int e = 0;
-        HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        HM_CUDA(cudaStreamSynchronize(st));
-        if (e) fail(HM_EBREAKDOWN, "gmres_solve: a diagonal leaf block of A is singular");
+        bj_build(H, W, st);
+        if (o.precond == HM_PRECOND_LEARNED && !lp->fallback) {
+            W.dsc.alloc((size_t)H.n_leaves * 3);
+            lp_predict(const_cast<LPModel&>(*lp), H, kel, W.dsc.p, nullptr, st);
+            W.dsc_on = true;
+        }
     }
     // ||b||
     HM_CUDA(cudaMemsetAsync(W.xc.p, 0, (size_t)n * nrhs * sizeof(double), st));

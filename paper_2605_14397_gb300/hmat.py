@@ -59,13 +59,19 @@ class hm_hmat_info(ctypes.Structure):
                 ("assemble_seconds", ctypes.c_double), ("storage", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("n_far_lowrank", ctypes.c_int64), ("n_far_dense", ctypes.c_int64),
                 ("u_entries", ctypes.c_int64), ("v_entries", ctypes.c_int64), ("tb_len", ctypes.c_int64),
-                ("p_len", ctypes.c_int64), ("n_far_refined", ctypes.c_int64)]
+                ("p_len", ctypes.c_int64), ("n_far_refined", ctypes.c_int64), ("n_leaves", ctypes.c_int64)]
 
 
 class hm_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mode", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int), ("lp", ctypes.c_void_p)]
+
+
+class hm_lp_info(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("fallback", ctypes.c_int32), ("n_params", ctypes.c_int64),
+                ("n_samples", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("last_loss", ctypes.c_double)]
 
 
 class hm_solve_info(ctypes.Structure):
@@ -103,6 +109,20 @@ SIGNATURES = [
     ("hm_gmres_solve", _I, [_VP, _VP, _D, _VP, _VP, _I, ctypes.POINTER(hm_solve_opts),
                             ctypes.POINTER(hm_solve_info), _VP]),
     ("hm_batch_create", _I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
+    ("hm_lp_param_count", _I64, [_I]),
+    ("hm_lp_create", _I, [_I, _VP, ctypes.POINTER(_VP)]),
+    ("hm_lp_add_samples", _I, [_VP, _VP, _VP, _I64]),
+    ("hm_lp_add_system", _I, [_VP, _VP, _VP, _VP, _VP, _I, _VP]),
+    ("hm_lp_clear_samples", _I, [_VP]),
+    ("hm_lp_loss_grad", _I, [_VP, ctypes.POINTER(_D), _VP, _VP]),
+    ("hm_lp_train", _I, [_VP, _I, _D, ctypes.POINTER(_D), _VP]),
+    ("hm_lp_predict", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    ("hm_lp_get_params", _I, [_VP, _VP]),
+    ("hm_lp_set_fallback", _I, [_VP, _I]),
+    ("hm_lp_get_info", _I, [_VP, ctypes.POINTER(hm_lp_info)]),
+    ("hm_lp_save", _I, [_VP, ctypes.c_char_p]),
+    ("hm_lp_load", _I, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
+    ("hm_lp_destroy", None, [_VP]),
     ("hm_matvec_graph", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_autotune", _I, [ctypes.POINTER(hm_elements), ctypes.POINTER(hm_assemble_opts), ctypes.POINTER(_I), _I,
                          ctypes.POINTER(_D), _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
@@ -290,14 +310,16 @@ class HMatrix:
                                     ctypes.c_void_p(_stream_ptr(stream))))
 
     def solve(self, b, x, k=None, shift=0.0, tol=1e-8, restart=50, maxit=2000, precond="blockj", mode="f64",
-              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True):
+              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None):
         """Solve (E - diag(k) - shift I) x = b on the device (b, x: float64 CUDA tensors of
         shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None).  Returns the
         per-RHS info dicts; raises HMError unless every RHS converged (raise_on_error)."""
         nrhs = 1 if b.dim() == 1 else b.shape[0]
+        assert b.is_contiguous() and x.is_contiguous() and (k is None or k.is_contiguous())
         o = hm_solve_opts(float(tol), int(restart), int(maxit),
                           {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "learned": HM_PRECOND_LEARNED}[precond],
-                          {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED}[mode], float(inner_tol), int(max_outer), 0)
+                          {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED}[mode], float(inner_tol), int(max_outer), 0,
+                          model.handle.value if model is not None else None)
         info = (hm_solve_info * nrhs)()
         st = lib().hm_gmres_solve(self.handle, _dptr(k) if k is not None else None, float(shift), _dptr(b), _dptr(x),
                                   int(nrhs), ctypes.byref(o), info, ctypes.c_void_p(_stream_ptr(stream)))
@@ -322,6 +344,97 @@ class HMatrix:
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
             lib().hm_hmat_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ learned correction
+
+class LearnedCorrection:
+    """Learned block-Jacobi correction (hm_lp_*): a per-leaf, per-component scaling of
+    the block-Jacobi preconditioner predicted by a small network from leaf features."""
+
+    def __init__(self, theta0=None, hidden=32, handle=None):
+        if handle is not None:
+            self.handle = handle
+            return
+        n = lib().hm_lp_param_count(int(hidden))
+        if n < 0:
+            raise HMError(HM_EINVAL, "hidden width must be 16, 32 or 64")
+        th = np.ascontiguousarray(theta0, dtype=np.float64)
+        assert th.size == n
+        h = ctypes.c_void_p()
+        _check(lib().hm_lp_create(int(hidden), th.ctypes.data_as(_VP), ctypes.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def load(cls, path):
+        h = ctypes.c_void_p()
+        _check(lib().hm_lp_load(str(path).encode(), ctypes.byref(h)))
+        return cls(handle=h)
+
+    def save(self, path):
+        _check(lib().hm_lp_save(self.handle, str(path).encode()))
+
+    def info(self):
+        i = hm_lp_info()
+        _check(lib().hm_lp_get_info(self.handle, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in hm_lp_info._fields_}
+
+    def params(self):
+        out = np.empty(self.info()["n_params"])
+        _check(lib().hm_lp_get_params(self.handle, out.ctypes.data_as(_VP)))
+        return out
+
+    def set_fallback(self, on):
+        _check(lib().hm_lp_set_fallback(self.handle, 1 if on else 0))
+
+    def add_samples(self, features, q):
+        f = np.ascontiguousarray(features, dtype=np.float64)
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        assert f.shape[1] == 8 and qq.shape == (f.shape[0], 9)
+        _check(lib().hm_lp_add_samples(self.handle, f.ctypes.data_as(_VP), qq.ctypes.data_as(_VP), f.shape[0]))
+
+    def add_system(self, H, k, b, x, stream=None):
+        """k: float64 CUDA tensor (N,) or None; b, x: float64 CUDA tensors (3N,) or (nrhs, 3N)."""
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        b, x = b.contiguous(), x.contiguous()
+        _check(lib().hm_lp_add_system(self.handle, H.handle, _dptr(k) if k is not None else None, _dptr(b),
+                                      _dptr(x), int(nrhs), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def clear_samples(self):
+        _check(lib().hm_lp_clear_samples(self.handle))
+
+    def loss_grad(self, stream=None):
+        g = np.empty(self.info()["n_params"])
+        l = ctypes.c_double()
+        _check(lib().hm_lp_loss_grad(self.handle, ctypes.byref(l), g.ctypes.data_as(_VP),
+                                     ctypes.c_void_p(_stream_ptr(stream))))
+        return l.value, g
+
+    def train(self, steps, lr=1e-3, stream=None):
+        l = ctypes.c_double()
+        _check(lib().hm_lp_train(self.handle, int(steps), float(lr), ctypes.byref(l),
+                                 ctypes.c_void_p(_stream_ptr(stream))))
+        return l.value
+
+    def predict(self, H, k=None, stream=None):
+        """(features (n_leaves x 8), d (n_leaves x 3)) for this H-matrix and k, leaves in cluster order."""
+        nl = H.info()["n_leaves"]
+        f = np.empty((nl, 8))
+        d = np.empty((nl, 3))
+        _check(lib().hm_lp_predict(self.handle, H.handle, _dptr(k) if k is not None else None,
+                                   f.ctypes.data_as(_VP), d.ctypes.data_as(_VP), ctypes.c_void_p(_stream_ptr(stream))))
+        return f, d
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().hm_lp_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

@@ -124,3 +124,45 @@ def test_tree_and_partition_bit_identical_to_oracle(L, which, leaf):
     assert np.array_equal(ex["far"], np.array(far).reshape(-1, 2))
     info = T.info()
     assert info["n_leaves"] == len(To.leaves())
+
+
+def test_learned_model_host_side(tmp_path):
+    th = synth.lp_initial_weights(16, seed=3)
+    assert hmat.lib().hm_lp_param_count(16) == th.size
+    assert hmat.lib().hm_lp_param_count(8) == -1
+    with pytest.raises(hmat.HMError) as ei:
+        hmat.LearnedCorrection(th, hidden=8)
+    assert ei.value.status == hmat.HM_EINVAL
+    bad = th.copy()
+    bad[5] = np.nan
+    with pytest.raises(hmat.HMError) as ei:
+        hmat.LearnedCorrection(bad, hidden=16)
+    assert ei.value.status == hmat.HM_ENAN
+    m = hmat.LearnedCorrection(th, hidden=16)
+    assert np.array_equal(m.params(), th.astype(np.float32).astype(np.float64))
+    rng = np.random.default_rng(0)
+    m.add_samples(rng.normal(size=(5, 8)), rng.uniform(size=(5, 9)))
+    m.add_samples(rng.normal(size=(3, 8)), rng.uniform(size=(3, 9)))
+    i = m.info()
+    assert (i["hidden"], i["n_samples"], i["n_groups"], i["fallback"], i["steps"]) == (16, 8, 2, 0, 0)
+    m.set_fallback(True)
+    path = tmp_path / "model.hmlp"
+    m.save(path)
+    r = hmat.LearnedCorrection.load(path)
+    assert r.info()["fallback"] == 1 and r.info()["hidden"] == 16
+    assert np.array_equal(r.params(), m.params())
+    m.clear_samples()
+    assert m.info()["n_samples"] == 0
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a model file at all")
+    with pytest.raises(hmat.HMError) as ei:
+        hmat.LearnedCorrection.load(junk)
+    assert ei.value.status == hmat.HM_EINVAL
+    # truncated file
+    data = path.read_bytes()
+    (tmp_path / "short.hmlp").write_bytes(data[:-4])
+    with pytest.raises(hmat.HMError):
+        hmat.LearnedCorrection.load(tmp_path / "short.hmlp")
+    L = hmat.lib()
+    assert L.hm_lp_train(None, 1, 1e-3, None, None) == hmat.HM_EINVAL
+    assert L.hm_lp_add_samples(m.handle, None, None, 0) == hmat.HM_EINVAL

@@ -1,0 +1,171 @@
+"""GPU parity of the learned block-Jacobi correction against the FP64 oracle
+(oracle/learned.py), through the C-ABI.
+
+Bars: features (FP64 on both sides) to 1e-10; network outputs d (FP32 on the device)
+to 1e-5; loss to 1e-5 and the gradient to 1e-3 relative (FP32 forward/backward against
+FP64); the statistics of a solved system (FP32 block-Jacobi on the device against the
+FP64 oracle) through the loss to 1e-4.  A zero output layer reproduces block-Jacobi
+bit for bit, a model flagged as fallback too, and training lowers the loss."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import learned as Lr
+from oracle import oracle as O
+from paper_2605_14397_gb300 import hmat, synth
+
+pytestmark = pytest.mark.gpu
+
+E, NU, HID = 1.0, 0.25, 32
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from __graft_entry__ import build
+    build()
+    return torch.device("cuda:0")
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+@pytest.fixture(scope="module")
+def system(dev):
+    """Crack crossing a fault at h = 0.1 (2,000 elements), k log-uniform per element."""
+    h = 0.1
+    el = synth.config_crack_fault(h=h)
+    T = hmat.ClusterTree(el, 64, 2.0)
+    H = hmat.HMatrix(T, el, E, NU, 1e-8, "f32")
+    ex = T.export()
+    info = T.info()
+    left = ex["left"]
+    leaves = [q for q in range(info["n_nodes"]) if left[q] < 0]
+    perm, begin, end = ex["perm"], ex["begin"][leaves], ex["end"][leaves]
+    return el, T, H, perm, begin, end, h
+
+
+def random_theta(seed, scale=0.5):
+    rng = np.random.default_rng(seed)
+    th = synth.lp_initial_weights(HID, seed=seed)
+    # a non-trivial output layer so that d varies
+    W1, b1, W2, b2, W3, b3 = Lr.unpack(th, HID)
+    W3 = rng.normal(size=W3.shape) * scale
+    b3 = rng.normal(size=3) * 0.2
+    b1 = rng.normal(size=b1.shape) * 0.1
+    return Lr.pack(W1, b1, W2, b2, W3, b3)
+
+
+def test_loss_and_gradient_match_oracle(dev):
+    rng = np.random.default_rng(11)
+    S = 700  # several sample chunks and a ragged tail
+    X = rng.normal(size=(S, 8))
+    Q = np.hstack([rng.normal(size=(S, 3)) * 0.01, rng.uniform(0.001, 0.02, size=(S, 6))])
+    th = random_theta(5)
+    m = hmat.LearnedCorrection(th, hidden=HID)
+    m.add_samples(X, Q)
+    loss, g = m.loss_grad()
+    thf = th.astype(np.float32).astype(np.float64)
+    lo, go = Lr.loss_and_grad(thf, HID, X.astype(np.float32).astype(np.float64),
+                              Q.astype(np.float32).astype(np.float64))
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    assert rel(g, go) <= 1e-3
+
+
+def test_adam_step_matches_oracle(dev):
+    rng = np.random.default_rng(12)
+    X = rng.normal(size=(300, 8))
+    Q = np.hstack([rng.normal(size=(300, 3)) * 0.01, rng.uniform(0.001, 0.02, size=(300, 6))])
+    th = random_theta(6)
+    m = hmat.LearnedCorrection(th, hidden=HID)
+    m.add_samples(X, Q)
+    _, g = m.loss_grad()
+    m.train(1, lr=1e-3)
+    t1 = m.params()
+    thf = th.astype(np.float32).astype(np.float64)
+    ref, _, _ = Lr.adam_step(thf, g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    big = np.abs(g) > 1e-3 * np.abs(g).max()  # the first step is lr * sign(g) where g is not tiny
+    assert np.allclose(t1[big], ref[big], rtol=0, atol=2e-6)
+    assert m.info()["steps"] == 1
+
+
+def test_features_and_outputs_match_oracle(dev, system):
+    import torch
+    el, T, H, perm, begin, end, h = system
+    k = synth.k_loguniform(el.N, 1605, h=h)
+    th = random_theta(7)
+    m = hmat.LearnedCorrection(th, hidden=HID)
+    f, d = m.predict(H, torch.as_tensor(k, device=dev))
+    fo = Lr.leaf_features(el, k, E, perm, begin, end)
+    assert np.abs(f - fo).max() <= 1e-10
+    do, _ = Lr.forward(th.astype(np.float32).astype(np.float64), HID, f.astype(np.float32).astype(np.float64))
+    assert np.abs(d - do).max() <= 1e-5
+    # no stiffness: every element soft
+    f0, _ = m.predict(H, None)
+    assert np.allclose(f0[:, 4], 1.0) and np.allclose(f0[:, 0], -6.0)
+
+
+def test_system_statistics_match_oracle(dev, system):
+    import torch
+    el, T, H, perm, begin, end, h = system
+    k = synth.k_loguniform(el.N, 1605, h=h)
+    A = O.tangent_dense(O.dense_matrix(el, E, NU), k)
+    B = synth.rhs_normal(3 * el.N, 21, nrhs=2)
+    X = np.ascontiguousarray(np.linalg.solve(A, B.T).T)
+    kt = torch.as_tensor(k, device=dev)
+    th = random_theta(8)
+    m = hmat.LearnedCorrection(th, hidden=HID)
+    m.add_system(H, kt, torch.as_tensor(B, device=dev), torch.as_tensor(X, device=dev))
+    loss, _ = m.loss_grad()
+    tree = O.cluster_tree(el, 64)
+    inv = O.block_jacobi_inverses(A, tree)
+    Y = np.stack([O.apply_block_jacobi(inv, B[q]) for q in range(2)])
+    S = Lr.leaf_stats(X, Y, perm, begin, end)
+    Q = Lr.samples([S])
+    F = Lr.leaf_features(el, k, E, perm, begin, end)
+    lo, _ = Lr.loss_and_grad(th.astype(np.float32).astype(np.float64), HID, F, Q)
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+
+
+def test_identity_and_fallback_reproduce_block_jacobi(dev, system):
+    import torch
+    el, T, H, perm, begin, end, h = system
+    k = torch.as_tensor(synth.k_loguniform(el.N, 1606, h=h), device=dev)
+    b = torch.as_tensor(synth.rhs_normal(3 * el.N, 22), device=dev)
+    x0 = torch.zeros_like(b)
+    i0 = H.solve(b, x0, k, precond="blockj")
+    ident = hmat.LearnedCorrection(synth.lp_initial_weights(HID, seed=9), hidden=HID)  # zero output layer
+    x1 = torch.zeros_like(b)
+    i1 = H.solve(b, x1, k, precond="learned", model=ident)
+    assert i1[0]["iters"] == i0[0]["iters"] and torch.equal(x0, x1)
+    fb = hmat.LearnedCorrection(random_theta(10), hidden=HID)
+    fb.set_fallback(True)
+    x2 = torch.zeros_like(b)
+    i2 = H.solve(b, x2, k, precond="learned", model=fb)
+    assert i2[0]["iters"] == i0[0]["iters"] and torch.equal(x0, x2)
+    # a model that is not the identity changes the preconditioner, and still converges
+    x3 = torch.zeros_like(b)
+    i3 = H.solve(b, x3, k, precond="learned", model=hmat.LearnedCorrection(random_theta(10), hidden=HID))
+    assert i3[0]["relres"] <= 1e-8
+    assert rel(x3.cpu().numpy(), x0.cpu().numpy()) < 1e-6
+
+
+def test_training_lowers_the_loss(dev, system):
+    import torch
+    el, T, H, perm, begin, end, h = system
+    m = hmat.LearnedCorrection(synth.lp_initial_weights(HID, seed=11), hidden=HID)
+    for s in range(3):
+        k = torch.as_tensor(synth.k_loguniform(el.N, 1700 + s, h=h), device=dev)
+        b = torch.as_tensor(synth.rhs_normal(3 * el.N, 1800 + s, nrhs=2), device=dev)
+        x = torch.zeros_like(b)
+        H.solve(b, x, k, precond="blockj", tol=1e-10)
+        m.add_system(H, k, b, x)
+    l0, _ = m.loss_grad()
+    l1 = m.train(200, lr=3e-3)
+    l2, _ = m.loss_grad()
+    assert m.info()["n_groups"] == 3 and m.info()["steps"] == 200
+    assert l2 < l0 and l1 < l0

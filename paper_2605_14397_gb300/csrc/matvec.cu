@@ -200,26 +200,27 @@ __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int
 // block: the n = r nr entries times G = 128 / n interleaved groups of leaf partials,
 // four independent loads in flight per thread, groups combined in a fixed order.
 template <class V>
-__global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const V* __restrict__ P,
-                                                   V* __restrict__ tb, int nrhs, const int* __restrict__ skip) {
+__global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const int32_t* __restrict__ poff,
+                                                   const V* __restrict__ P, V* __restrict__ tb, int nrhs,
+                                                   const int* __restrict__ skip) {
     __shared__ V sp[128];
     if (skip && *(volatile const int*)skip) return;
     const FarDesc F = far[blockIdx.x];
     const int n = F.rank * nrhs;
     if (n == 0) return;
-    const int64_t base = F.pbase * nrhs;
-    const int64_t step = (int64_t)F.rank * nrhs;  // distance between leaf partials
+    const int32_t* po = poff + F.pbase;  // first partial of the block in each leaf of T
+    auto at = [&](int q) -> int64_t { return (int64_t)po[q] * nrhs; };
     if (n >= 128) {
         for (int e = threadIdx.x; e < n; e += 128) {
             V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
             int q = 0;
             for (; q + 3 < F.n_tleaves; q += 4) {
-                s0 += P[base + q * step + e];
-                s1 += P[base + (q + 1) * step + e];
-                s2 += P[base + (q + 2) * step + e];
-                s3 += P[base + (q + 3) * step + e];
+                s0 += P[at(q) + e];
+                s1 += P[at(q + 1) + e];
+                s2 += P[at(q + 2) + e];
+                s3 += P[at(q + 3) + e];
             }
-            for (; q < F.n_tleaves; ++q) s0 += P[base + q * step + e];
+            for (; q < F.n_tleaves; ++q) s0 += P[at(q) + e];
             tb[F.tb_off * nrhs + e] = (s0 + s1) + (s2 + s3);
         }
         return;
@@ -230,12 +231,12 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
     if (g < G) {
         int q = g;
         for (; q + 3 * G < F.n_tleaves; q += 4 * G) {
-            s0 += P[base + q * step + e];
-            s1 += P[base + (q + G) * step + e];
-            s2 += P[base + (q + 2 * G) * step + e];
-            s3 += P[base + (q + 3 * G) * step + e];
+            s0 += P[at(q) + e];
+            s1 += P[at(q + G) + e];
+            s2 += P[at(q + 2 * G) + e];
+            s3 += P[at(q + 3 * G) + e];
         }
-        for (; q < F.n_tleaves; q += G) s0 += P[base + q * step + e];
+        for (; q < F.n_tleaves; q += G) s0 += P[at(q) + e];
     }
     sp[threadIdx.x] = (s0 + s1) + (s2 + s3);
     __syncthreads();
@@ -500,6 +501,33 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
         }
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
         const C* buf = (const C*)(stage + (size_t)s * STAGE_BYTES);
+        if constexpr (NR == 1) {
+            // Four columns (w, w + NCW, w + 2 NCW, w + 3 NCW) per pass: their four warp sums
+            // share one reduce-scatter (6 shuffles instead of 20) and the loads of four
+            // columns are in flight together.
+            constexpr int CG = 4;
+            for (int c = w; c < ch.ncols; c += CG * NCW) {
+                Acc acc[CG];
+#pragma unroll
+                for (int j = 0; j < CG; ++j) acc_zero(acc[j]);
+#pragma unroll
+                for (int ii = 0; ii < RPL; ++ii) {
+                    const int r = lane + 32 * ii;
+#pragma unroll
+                    for (int j = 0; j < CG; ++j) {
+                        const int cj = c + j * NCW;
+                        const float v = (r < rows && cj < ch.ncols) ? coef(buf + (size_t)cj * ch.ld, r) : 0.f;
+                        acc_fma(acc[j], v, xr[0][ii]);
+                    }
+                }
+                const int j = warp_reduce_scatter<CG>(acc, lane);
+                const int cj = c + j * NCW;
+                if ((lane & (32 / CG - 1)) == 0 && cj < ch.ncols) P[ch.zoff + cj] = (Vv)acc_value(acc[0]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + s);
+            continue;
+        }
         for (int c = w; c < ch.ncols; c += NCW) {
             const C* col = buf + (size_t)c * ch.ld;
             Acc acc[NR];
@@ -584,7 +612,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
-        k_reduce_tb<V><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, (const V*)a.out, (V*)base.tb, base.nr,
+        k_reduce_tb<V><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out, (V*)base.tb, base.nr,
                                                           base.skip);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 3, st);

@@ -400,7 +400,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     H.h_near_zidx = std::move(near_zidx);
 
     // ---- ranks, partial-buffer and t-vector layout (low-rank blocks only)
-    int64_t tb_len = 0, p_len = 0;
+    int64_t tb_len = 0, p_len = 0, poff_len = 0;
     H.far_entries = 0;
     H.rank_min = 1 << 30;
     H.rank_max = 0;
@@ -412,7 +412,8 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         F.fac_off = fac_off[b];
         F.tb_off = tb_len;
         F.n_tleaves = lcount[fnodes[b][1]];
-        F.pbase = p_len;
+        F.pbase = poff_len;
+        poff_len += F.n_tleaves;
         F.dense = dense_far[b];
         tb_len += F.rank;
         p_len += (int64_t)F.n_tleaves * F.rank;
@@ -440,6 +441,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     // ---- U and V streams
     std::vector<PackJob> ujobs, vjobs;
     std::vector<int32_t> u_zidx, v_pidx;
+    H.h_poff.assign(std::max<int64_t>(poff_len, 1), 0);
     int64_t u_len = 0, v_len = 0;
     for (int l = 0; l < nl; ++l) {
         LeafDesc& L = H.h_leaves[l];
@@ -477,7 +479,9 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
             J.dst_ld = L.ld;
             J.ncols = F.rank;
             vjobs.push_back(J);
-            for (int c = 0; c < F.rank; ++c) v_pidx.push_back((int32_t)(F.pbase + (int64_t)k * F.rank + c));
+            const int32_t start = (int32_t)v_pidx.size();  // partials in V-stream order
+            H.h_poff[F.pbase + k] = start;
+            for (int c = 0; c < F.rank; ++c) v_pidx.push_back(start + c);
             vcols += F.rank;
         }
         L.v_cols = vcols;
@@ -510,7 +514,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     }
     H.h_u_zidx = std::move(u_zidx);
     H.h_v_pidx = std::move(v_pidx);
-    H.vpidx.upload(H.h_v_pidx, st);
+    H.poff.upload(H.h_poff, st);
     H.leaves.upload(H.h_leaves, st);
     H.far.upload(H.h_far, st);
 

@@ -56,7 +56,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         M.eps = std::max(M.eps, h->eps);
     }
 
-    int64_t pos = 0, near_b = 0, u_b = 0, v_b = 0, tb_b = 0, p_b = 0, fac_b = 0;
+    int64_t pos = 0, near_b = 0, u_b = 0, v_b = 0, tb_b = 0, p_b = 0, fac_b = 0, po_b = 0;
     int32_t nz_b = 0, uz_b = 0, vp_b = 0;
     M.h_leaves.clear();
     M.h_far.clear();
@@ -65,6 +65,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
     M.h_u_zidx.clear();
     M.h_v_pidx.clear();
     M.h_self_off.clear();
+    M.h_poff.clear();
     M.n_near = M.n_far = M.n_dense_far = M.n_refined = 0;
     M.near_entries = M.far_entries = 0;
     M.assemble_seconds = 0.0;
@@ -93,7 +94,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         for (FarDesc F : h->h_far) {
             F.s_begin += (int32_t)pos;
             F.t_begin += (int32_t)pos;
-            F.pbase += p_b;
+            F.pbase += po_b;
             F.tb_off += tb_b;
             F.fac_off += fac_b;
             M.h_far.push_back(F);
@@ -102,6 +103,8 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         for (int32_t z : h->h_u_zidx) M.h_u_zidx.push_back(z + (int32_t)tb_b);
         for (int32_t z : h->h_v_pidx) M.h_v_pidx.push_back(z + (int32_t)p_b);
         for (int64_t o : h->h_self_off) M.h_self_off.push_back(o < 0 ? o : o + near_b);
+        for (int32_t o : h->h_poff) M.h_poff.push_back(o + (int32_t)p_b);
+        po_b += (int64_t)h->h_poff.size();
         pos += h->N;
         near_b += (int64_t)h->near.n;
         u_b += (int64_t)std::max(h->u32.n, h->u16.n);
@@ -169,7 +172,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         append_dev(M.v16, sv16, st);
     }
     M.perm.upload(perm32, st);
-    M.vpidx.upload(M.h_v_pidx, st);
+    M.poff.upload(M.h_poff, st);
     M.leaves.upload(M.h_leaves, st);
     M.far.upload(M.h_far, st);
     build_product_plan(M, st);

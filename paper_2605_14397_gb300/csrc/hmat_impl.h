@@ -44,7 +44,8 @@ struct FarDesc {
     int32_t s_begin, s_n, t_begin, t_n;  // clusters (positions, element counts)
     int32_t rank;
     int32_t n_tleaves;                   // leaves of T (partials per output)
-    int64_t pbase;                       // partial buffer base: P[pbase + k r + l]
+    int64_t pbase;                       // first of its n_tleaves entries in the partial offset table:
+                                         // partial l of the k-th leaf of T is P[poff[pbase + k] + l]
     int64_t tb_off;                      // output offset in tb
     int64_t fac_off;                     // compact factor store offset (U then V)
     int32_t dense;                       // 1: kept dense (its tiles live in the near stream),
@@ -101,9 +102,11 @@ struct HMat {
     // operand index of every column (host; consecutive runs become the z ranges of the
     // product chunks): xc index (near), tb index (U), partial index (V)
     std::vector<int32_t> h_near_zidx, h_u_zidx, h_v_pidx;
-    // device copy of h_v_pidx: phase 1 writes the partial of V-stream column j to
-    // P[vpidx[j]], so a chunk may span several slices whatever their partial offsets
-    DevBuf<int32_t> vpidx;
+    // V columns write their partials in V-stream order, so the slices of one column leaf
+    // form one contiguous output range (whole pipeline chunks); poff locates each far
+    // block's slice in every leaf of its column cluster
+    std::vector<int32_t> h_poff;
+    DevBuf<int32_t> poff;
 
     // persistent product plans: [0] with the FP32 factors, [1] with the BF16 factors
     int grid = 0;

@@ -200,26 +200,36 @@ __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int
 // block: the n = r nr entries times G = 128 / n interleaved groups of leaf partials,
 // four independent loads in flight per thread, groups combined in a fixed order.
 template <class V>
-__global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const V* __restrict__ P,
-                                                   V* __restrict__ tb, int nrhs, const int* __restrict__ skip) {
+__global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const int32_t* __restrict__ poff,
+                                                   const V* __restrict__ P, V* __restrict__ tb, int nrhs,
+                                                   const int* __restrict__ skip) {
     __shared__ V sp[128];
     if (skip && *(volatile const int*)skip) return;
     const FarDesc F = far[blockIdx.x];
     const int n = F.rank * nrhs;
     if (n == 0) return;
-    const int64_t base = F.pbase * nrhs;
-    const int64_t step = (int64_t)F.rank * nrhs;  // distance between leaf partials
+    // first partial of the block in each leaf of T, staged in shared memory when it fits so
+    // that the partial loads do not wait on their index loads
+    constexpr int SPO = 2048;
+    __shared__ int32_t spo[SPO];
+    const int32_t* po = poff + F.pbase;
+    if (F.n_tleaves <= SPO) {
+        for (int q = threadIdx.x; q < F.n_tleaves; q += 128) spo[q] = po[q];
+        __syncthreads();
+        po = spo;
+    }
+    auto at = [&](int q) -> int64_t { return (int64_t)po[q] * nrhs; };
     if (n >= 128) {
         for (int e = threadIdx.x; e < n; e += 128) {
             V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
             int q = 0;
             for (; q + 3 < F.n_tleaves; q += 4) {
-                s0 += P[base + q * step + e];
-                s1 += P[base + (q + 1) * step + e];
-                s2 += P[base + (q + 2) * step + e];
-                s3 += P[base + (q + 3) * step + e];
+                s0 += P[at(q) + e];
+                s1 += P[at(q + 1) + e];
+                s2 += P[at(q + 2) + e];
+                s3 += P[at(q + 3) + e];
             }
-            for (; q < F.n_tleaves; ++q) s0 += P[base + q * step + e];
+            for (; q < F.n_tleaves; ++q) s0 += P[at(q) + e];
             tb[F.tb_off * nrhs + e] = (s0 + s1) + (s2 + s3);
         }
         return;
@@ -230,12 +240,12 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
     if (g < G) {
         int q = g;
         for (; q + 3 * G < F.n_tleaves; q += 4 * G) {
-            s0 += P[base + q * step + e];
-            s1 += P[base + (q + G) * step + e];
-            s2 += P[base + (q + 2 * G) * step + e];
-            s3 += P[base + (q + 3 * G) * step + e];
+            s0 += P[at(q) + e];
+            s1 += P[at(q + G) + e];
+            s2 += P[at(q + 2 * G) + e];
+            s3 += P[at(q + 3 * G) + e];
         }
-        for (; q < F.n_tleaves; q += G) s0 += P[base + q * step + e];
+        for (; q < F.n_tleaves; q += G) s0 += P[at(q) + e];
     }
     sp[threadIdx.x] = (s0 + s1) + (s2 + s3);
     __syncthreads();
@@ -264,7 +274,6 @@ struct StreamArgs {
     int nr;       // right-hand sides in this launch (<= NR); also the interleave stride
     int ld_max;
     const int* skip;  // optional device flag: when set, the kernels return at once
-    const int32_t* vpidx;  // phase 1: partial index of every V-stream column
 };
 
 template <class V, int NR>
@@ -522,7 +531,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
                 }
                 const int j = warp_reduce_scatter<CG>(acc, lane);
                 const int cj = c + j * NCW;
-                if ((lane & (32 / CG - 1)) == 0 && cj < ch.ncols) P[a.vpidx[ch.zoff + cj]] = (Vv)acc_value(acc[0]);
+                if ((lane & (32 / CG - 1)) == 0 && cj < ch.ncols) P[ch.zoff + cj] = (Vv)acc_value(acc[0]);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty + s);
@@ -541,8 +550,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
                 for (int k = 0; k < NR; ++k) acc_fma(acc[k], v, xr[k][ii]);
             }
             const int k = warp_reduce_scatter<NR>(acc, lane);
-            if ((lane & (32 / NR - 1)) == 0 && k < a.nr)
-                P[(int64_t)a.vpidx[ch.zoff + c] * a.nr + k] = (Vv)acc_value(acc[0]);
+            if ((lane & (32 / NR - 1)) == 0 && k < a.nr) P[(ch.zoff + c) * a.nr + k] = (Vv)acc_value(acc[0]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
@@ -613,7 +621,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
-        k_reduce_tb<V><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, (const V*)a.out, (V*)base.tb, base.nr,
+        k_reduce_tb<V><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out, (V*)base.tb, base.nr,
                                                           base.skip);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 3, st);
@@ -664,7 +672,6 @@ void run_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, boo
     a.nr = nr;
     a.ld_max = H.ld_max;
     a.skip = skip;
-    a.vpidx = H.vpidx.p;
     a.xc = xc;
     a.out = yc;
     if (dtype == HM_F32) {
@@ -745,17 +752,13 @@ void build_plan_for(HMat& H, HMat::Plan& PLAN, int esz, int G, cudaStream_t st) 
     };
 
     std::vector<Chunk> c1, c2;
-    std::vector<int32_t> vcol(H.h_v_pidx.size());
-    for (size_t j = 0; j < vcol.size(); ++j) vcol[j] = (int32_t)j;
     std::vector<int64_t> b1, b2;
     const int nl = H.n_leaves;
     for (int l = 0; l < nl; ++l) {
         const LeafDesc& L = H.h_leaves[l];
         cut(c2, b2, l, 0, L.near_off, H.h_near_zidx, L.near_cbase, L.near_cols, L.ld, 4);
         cut(c2, b2, l, 1, L.u_off, H.h_u_zidx, L.u_cbase, L.u_cols, L.ld, esz);
-        // V chunks: runs of stream columns (zoff = first V-stream column); the partial of
-        // each column is found through vpidx, so chunks span slices of several blocks
-        cut(c1, b1, l, 2, L.v_off, vcol, L.v_cbase, L.v_cols, L.ld, esz);
+        cut(c1, b1, l, 2, L.v_off, H.h_v_pidx, L.v_cbase, L.v_cols, L.ld, esz);
     }
     std::vector<int32_t> cta1, cta2;
     split_ranges(b1, cta1);

@@ -175,7 +175,9 @@ void matvec_host(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStrea
 void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 // Product on cluster-ordered operands: xc is RHS-interleaved (xc[dof * nr + k]) with at
 // least 32 readable elements after its end, yc is RHS-major (yc[k * ndof + dof]).
-// fac: 0 FP32 factors, 1 BF16 factors.  dtype HM_F32: float vectors; HM_F64: double.
+// fac: 0 FP32 factors, 1 BF16 factors.  dtype HM_F32: float vectors; HM_F64: xc holds
+// every double pre-split into (hi, lo) floats (float2, written by the gather or the
+// solver), yc doubles.
 void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, cudaStream_t st,
                   const int* skip = nullptr);
 // Concatenate independent H-matrices into one (block-diagonal operator, one work list).

@@ -52,15 +52,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 template <int MODE>
 struct AccT;
+// type: accumulator; vec: output vectors (y, partials); zin: the x / t operands as the
+// kernels read them -- in F64 mode each double is stored pre-split into (hi, lo) floats
+// by the gather and the reduction, so the streaming kernels do no FP64 arithmetic
 template <>
 struct AccT<0> {
     using type = float;
     using vec = float;
+    using zin = float;
 };
 template <>
 struct AccT<1> {
     using type = FF;
     using vec = double;
+    using zin = float2;
 };
 
 // z operand: one float, or the (hi, lo) split of a double
@@ -72,10 +77,17 @@ struct Z64 {
 };
 
 __device__ __forceinline__ Z32 make_z(float v) { return Z32{v}; }
-__device__ __forceinline__ Z64 make_z(double v) {
+__device__ __forceinline__ Z64 make_z(float2 v) { return Z64{v.x, v.y}; }
+__device__ __forceinline__ float2 split_d(double v) {
     const float h = (float)v;
-    return Z64{h, (float)(v - (double)h)};
+    return make_float2(h, (float)(v - (double)h));
 }
+template <class Zin>
+__device__ __forceinline__ Zin zin_zero();
+template <>
+__device__ __forceinline__ float zin_zero<float>() { return 0.f; }
+template <>
+__device__ __forceinline__ float2 zin_zero<float2>() { return make_float2(0.f, 0.f); }
 
 __device__ __forceinline__ void acc_zero(float& a) { a = 0.f; }
 __device__ __forceinline__ void acc_zero(FF& a) { a.hi = 0.f; a.lo = 0.f; }
@@ -153,20 +165,20 @@ __device__ __forceinline__ void load_z(Z32 (&z)[NR], const float* p, int nr) {
     for (int k = 0; k < NR; ++k) z[k] = make_z(k < nr ? p[k] : 0.f);
 }
 template <int NR>
-__device__ __forceinline__ void load_z(Z64 (&z)[NR], const double* p, int nr) {
+__device__ __forceinline__ void load_z(Z64 (&z)[NR], const float2* p, int nr) {
     if constexpr (NR % 2 == 0) {
         if (nr == NR) {
 #pragma unroll
             for (int q = 0; q < NR / 2; ++q) {
-                const double2 f = reinterpret_cast<const double2*>(p)[q];
-                z[2 * q] = make_z(f.x);
-                z[2 * q + 1] = make_z(f.y);
+                const float4 f = reinterpret_cast<const float4*>(p)[q];
+                z[2 * q] = Z64{f.x, f.y};
+                z[2 * q + 1] = Z64{f.z, f.w};
             }
             return;
         }
     }
 #pragma unroll
-    for (int k = 0; k < NR; ++k) z[k] = make_z(k < nr ? p[k] : 0.0);
+    for (int k = 0; k < NR; ++k) z[k] = make_z(k < nr ? p[k] : make_float2(0.f, 0.f));
 }
 
 __device__ __forceinline__ float coef(const float* p, int i) { return p[i]; }
@@ -184,6 +196,17 @@ __global__ void k_gather(const V* __restrict__ x, V* __restrict__ xc, const int3
     xc[q] = x[k * ndof + 3 * (int64_t)perm[p] + m];
 }
 
+// F64 gather: xc[dof * nr + k] = (hi, lo) split of x[k * ndof + user dof]
+__global__ void k_gather_split(const double* __restrict__ x, float2* __restrict__ xc,
+                               const int32_t* __restrict__ perm, int64_t N, int nrhs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ndof = 3 * N;
+    if (q >= ndof * nrhs) return;
+    const int64_t r = q / nrhs, k = q % nrhs;
+    const int64_t p = r / 3, m = r % 3;
+    xc[q] = split_d(x[k * ndof + 3 * (int64_t)perm[p] + m]);
+}
+
 // y[k * ndof + user dof] = yc[k * ndof + dof]
 template <class V>
 __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int32_t* __restrict__ perm, int64_t N,
@@ -196,12 +219,16 @@ __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int
     y[k * ndof + 3 * (int64_t)perm[p] + m] = yc[q];
 }
 
-// tb[(tb_off + l) nr + k] = sum_q P[(pbase + q r + l) nr + k], one CTA (128 threads) per
-// block: the n = r nr entries times G = 128 / n interleaved groups of leaf partials,
-// four independent loads in flight per thread, groups combined in a fixed order.
-template <class V>
+__device__ __forceinline__ float to_zin(float v, float*) { return v; }
+__device__ __forceinline__ float2 to_zin(double v, float2*) { return split_d(v); }
+
+// tb[(tb_off + l) nr + k] = sum_q P[(poff[pbase + q] + l) nr + k], one CTA (128 threads)
+// per block: the n = r nr entries times G = 128 / n interleaved groups of leaf partials,
+// four independent loads in flight per thread, groups combined in a fixed order.  In F64
+// mode the sums are stored as (hi, lo) float pairs, the form phase 2 reads.
+template <class V, class Zt>
 __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const int32_t* __restrict__ poff,
-                                                   const V* __restrict__ P, V* __restrict__ tb, int nrhs,
+                                                   const V* __restrict__ P, Zt* __restrict__ tb, int nrhs,
                                                    const int* __restrict__ skip) {
     __shared__ V sp[128];
     if (skip && *(volatile const int*)skip) return;
@@ -230,7 +257,7 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
                 s3 += P[at(q + 3) + e];
             }
             for (; q < F.n_tleaves; ++q) s0 += P[at(q) + e];
-            tb[F.tb_off * nrhs + e] = (s0 + s1) + (s2 + s3);
+            tb[F.tb_off * nrhs + e] = to_zin((s0 + s1) + (s2 + s3), tb);
         }
         return;
     }
@@ -252,7 +279,7 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
     if (threadIdx.x < n) {
         V s = 0;
         for (int q = 0; q < G; ++q) s += sp[q * n + threadIdx.x];
-        tb[F.tb_off * nrhs + threadIdx.x] = s;
+        tb[F.tb_off * nrhs + threadIdx.x] = to_zin(s, tb);
     }
 }
 
@@ -432,14 +459,15 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
         const unsigned char* stg = stage + (size_t)s * STRIDE;
         const int64_t z0 = ch.zoff * a.nr;
-        const Vv* zb = (const Vv*)stg + (z0 - (z0 & ~(int64_t)(ZR::ALIGN - 1)));
+        using Zin = typename AccT<MODE>::zin;  // same size as Vv
+        const Zin* zb = (const Zin*)stg + (z0 - (z0 & ~(int64_t)(ZR::ALIGN - 1)));
         const unsigned char* buf = stg + ZR::BYTES;
         const int rows = 3 * L.n;
         // Rows at or beyond `rows` read whatever follows the column in shared memory (the
         // next column, stage or the reduction buffer: always inside the allocation); their
         // accumulators are never flushed, so no bound check is needed per coefficient.
         for (int c = g; c < ch.ncols; c += NG) {
-            decltype(make_z(Vv(0))) zv[NR];
+            decltype(make_z(zin_zero<Zin>())) zv[NR];
             if constexpr (NR == 1)
                 zv[0] = make_z(zb[c]);
             else
@@ -486,11 +514,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
         if (lane == 0) produce<C, Vv, NR, false>(a, stage, STAGE_BYTES, full, empty, c0, c1);
         return;
     }
-    const Vv* xc = (const Vv*)a.xc;
     Vv* P = (Vv*)a.out;
     int cur = -1;
     int rows = 0;
-    decltype(make_z(Vv(0))) xr[NR][RPL];
+    using Zin = typename AccT<MODE>::zin;
+    const Zin* xs = (const Zin*)a.xc;
+    decltype(make_z(zin_zero<Zin>())) xr[NR][RPL];
     Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
     for (int i = c0; i < c1; ++i) {
         const Chunk ch = nxt;
@@ -505,7 +534,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
                 const int r = lane + 32 * ii;
 #pragma unroll
                 for (int k = 0; k < NR; ++k)
-                    xr[k][ii] = make_z((r < rows && k < a.nr) ? xc[(3 * (int64_t)L.begin + r) * a.nr + k] : (Vv)0);
+                    xr[k][ii] = make_z((r < rows && k < a.nr) ? xs[(3 * (int64_t)L.begin + r) * a.nr + k]
+                                                              : zin_zero<Zin>());
             }
         }
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
@@ -621,7 +651,8 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
-        k_reduce_tb<V><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out, (V*)base.tb, base.nr,
+        using Zt = typename AccT<MODE>::zin;
+        k_reduce_tb<V, Zt><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
                                                           base.skip);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 3, st);
@@ -845,7 +876,7 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
         } else {
             const double* xd = (const double*)x + (int64_t)k0 * H.ndof;
             double* yd = (double*)y + (int64_t)k0 * H.ndof;
-            k_gather<double><<<gb, 256, 0, st>>>(xd, H.xc.p, H.perm.p, H.N, nr);
+            k_gather_split<<<gb, 256, 0, st>>>(xd, (float2*)H.xc.p, H.perm.p, H.N, nr);
             mark(H, 1, st);
             run_core(H, H.xc.p, H.yc.p, nr, dtype, fac, true, st);
             k_scatter<double><<<gb, 256, 0, st>>>(H.yc.p, yd, H.perm.p, H.N, nr);

@@ -216,11 +216,14 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
 }
 
 // interleave a set of FP64 vectors for the product: out[dof * nr + k] = in[k * ndof + dof]
-__global__ void k_interleave(const double* __restrict__ in, double* __restrict__ out, int64_t ndof, int nr) {
+// F64 product operand: out[dof * nr + k] = (hi, lo) float split of in[k * ndof + dof]
+__global__ void k_interleave_split(const double* __restrict__ in, float2* __restrict__ out, int64_t ndof, int nr) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= ndof * nr) return;
     const int64_t r = q / nr, k = q % nr;
-    out[q] = in[k * ndof + r];
+    const double v = in[k * ndof + r];
+    const float h = (float)v;
+    out[q] = make_float2(h, (float)(v - (double)h));
 }
 
 __global__ void k_to_f32_interleaved(const double* __restrict__ in, float* __restrict__ out, int64_t ndof, int nr) {
@@ -589,12 +592,8 @@ unsigned g1(int64_t n) { return (unsigned)ceil_div(std::max<int64_t>(n, 1), 256)
 void apply_E(HMat& H, SolveWS& W, const double* z64, const float* z32, void* y, int nr, int dtype, int fac,
              cudaStream_t st, const int* skip = nullptr) {
     if (dtype == HM_F64) {
-        const double* in = z64;
-        if (nr > 1) {
-            k_interleave<<<g1(H.ndof * nr), 256, 0, st>>>(z64, W.zi.p, H.ndof, nr);
-            in = W.zi.p;
-        }
-        product_core(H, in, y, nr, HM_F64, fac, st, skip);
+        k_interleave_split<<<g1(H.ndof * nr), 256, 0, st>>>(z64, (float2*)W.zi.p, H.ndof, nr);
+        product_core(H, W.zi.p, y, nr, HM_F64, fac, st, skip);
     } else {
         product_core(H, z32, y, nr, HM_F32, fac, st, skip);
     }

@@ -17,6 +17,7 @@
 //     mode MIXED: iterative refinement (outer residual in compensated FP64 with the
 //     FP32 factors; corrections by FGMRES on the BF16-factor operator, FP32 products).
 // Vectors are kept in cluster order internally (RHS-major, stride 3N).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -159,6 +160,143 @@ __global__ void __launch_bounds__(512) k_bj_build(const LeafDesc* __restrict__ l
     for (int q = tid; q < n * n; q += nt) {
         const int r = q / n, c = q % n;
         out[(int64_t)c * L.ld + r] = A[q];
+    }
+}
+
+// The same inverse for leaves of at most BJR_ROWS rows, with the matrix held in registers:
+// 512 threads, thread (tr, tc) = (t / 32, t % 32) owns rows tr + 16 a (a < 12) and columns
+// tc + 32 b (b < 6).  Gauss-Jordan by in-place sweeps with partial pivoting and no row
+// interchanges: step k picks the unused row p_k with the largest |A[i][k]| and sweeps on
+// (p_k, k) (pivot row divided by the pivot, every other row i minus A[i][k] times it,
+// column k replaced by -A[i][k] / pivot and 1 / pivot).  After n sweeps row p_k holds
+// the coefficients of unknown k against equations p_0 .. p_(n-1), so
+// A^-1[k][m] = W[p_k][q] with p_q = m.  Only the pivot row and column go through shared
+// memory at each step.
+constexpr int BJR_ROWS = 192;
+
+__global__ void __launch_bounds__(512, 1) k_bj_build_reg(const LeafDesc* __restrict__ leaves,
+                                                         const int64_t* __restrict__ self_off,
+                                                         const float* __restrict__ near, const double* __restrict__ d,
+                                                         float* __restrict__ binv, const int64_t* __restrict__ binv_off,
+                                                         int* __restrict__ err) {
+    extern __shared__ float wsm[];  // final n x n staging (row-major)
+    __shared__ float colk[BJR_ROWS], prow[BJR_ROWS];
+    __shared__ float cand_v[16];
+    __shared__ int cand_i[16];
+    __shared__ int used[BJR_ROWS], pk[BJR_ROWS], pinv[BJR_ROWS];
+    __shared__ int s_p;
+    const LeafDesc L = leaves[blockIdx.x];
+    const int n = 3 * L.n;
+    const int t = threadIdx.x, tr = t >> 5, tc = t & 31;
+    const float* E = near + self_off[blockIdx.x];
+    float A[12][6];
+#pragma unroll
+    for (int a = 0; a < 12; ++a)
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            const int i = tr + 16 * a, j = tc + 32 * b;
+            float v = 0.f;
+            if (i < n && j < n) {
+                v = E[(int64_t)j * L.ld + i];
+                if (i == j) v -= (float)d[3 * (int64_t)L.begin + i];
+            }
+            A[a][b] = v;
+        }
+    for (int i = t; i < BJR_ROWS; i += 512) used[i] = (i < n) ? 0 : 1;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const int bk = k >> 5, ck = k & 31;
+        // column k to shared memory and the pivot candidates of each row group
+        if (tc == ck) {
+            float bv = -1.f;
+            int bi = -1;
+#pragma unroll
+            for (int a = 0; a < 12; ++a) {
+                const int i = tr + 16 * a;
+                float v = 0.f;
+#pragma unroll
+                for (int b = 0; b < 6; ++b)
+                    if (b == bk) v = A[a][b];
+                if (i < BJR_ROWS) colk[i] = v;
+                if (i < n && !used[i] && fabsf(v) > bv) {
+                    bv = fabsf(v);
+                    bi = i;
+                }
+            }
+            cand_v[tr] = bv;
+            cand_i[tr] = bi;
+        }
+        __syncthreads();
+        if (t == 0) {
+            float bv = -1.f;
+            int bi = -1;
+            for (int g = 0; g < 16; ++g)
+                if (cand_v[g] > bv || (cand_v[g] == bv && cand_i[g] >= 0 && cand_i[g] < bi)) {
+                    bv = cand_v[g];
+                    bi = cand_i[g];
+                }
+            if (!(bv > 0.f) || bi < 0) {
+                atomicOr(err, 1);
+                bi = -1;
+            }
+            s_p = bi;
+            if (bi >= 0) {
+                used[bi] = 1;
+                pk[k] = bi;
+                pinv[bi] = k;
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p < 0) break;  // singular block: reported through err
+        // pivot row to shared memory
+        if (tr == (p & 15)) {
+            const int ap = p >> 4;
+#pragma unroll
+            for (int a = 0; a < 12; ++a)
+                if (a == ap)
+#pragma unroll
+                    for (int b = 0; b < 6; ++b) {
+                        const int j = tc + 32 * b;
+                        if (j < BJR_ROWS) prow[j] = A[a][b];
+                    }
+        }
+        __syncthreads();
+        const float piv = prow[k];
+        const float pinvv = 1.0f / piv;
+#pragma unroll
+        for (int a = 0; a < 12; ++a) {
+            const int i = tr + 16 * a;
+            const float cik = colk[i < BJR_ROWS ? i : 0];
+            const bool prow_i = (i == p);
+#pragma unroll
+            for (int b = 0; b < 6; ++b) {
+                const int j = tc + 32 * b;
+                const float pj = prow[j < BJR_ROWS ? j : 0];
+                float v = A[a][b];
+                if (prow_i)
+                    v = (j == k) ? pinvv : v * pinvv;
+                else
+                    v = (j == k) ? -cik * pinvv : fmaf(-cik * pinvv, pj, v);
+                A[a][b] = v;
+            }
+        }
+        __syncthreads();  // colk / prow are rewritten by the next step
+    }
+    // stage W, then write A^-1[r][c] = W[p_r][pinv[c]] column-major with the padded ld
+#pragma unroll
+    for (int a = 0; a < 12; ++a)
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            const int i = tr + 16 * a, j = tc + 32 * b;
+            if (i < n && j < n) wsm[i * n + j] = A[a][b];
+        }
+    __syncthreads();
+    if (s_p < 0) return;
+    float* out = binv + binv_off[blockIdx.x];
+    for (int q = t; q < n * n; q += 512) {
+        const int c = q / n, r = q % n;
+        out[(int64_t)c * L.ld + r] = wsm[pk[r] * n + pinv[c]];
     }
 }
 
@@ -731,6 +869,27 @@ void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& t
 // block-Jacobi inverses of the leaf blocks of E - diag(W.dc)
 void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
+    int max_rows = 0;
+    for (const LeafDesc& L : H.h_leaves) max_rows = std::max(max_rows, 3 * L.n);
+    if (max_rows <= BJR_ROWS) {
+        const size_t smem = sizeof(float) * (size_t)max_rows * max_rows;
+        static bool attr_done[64] = {};
+        int dev = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+            HM_CUDA(cudaFuncSetAttribute(k_bj_build_reg, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float) * BJR_ROWS * BJR_ROWS)));
+            if (dev >= 0 && dev < 64) attr_done[dev] = true;
+        }
+        k_bj_build_reg<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.binv.p,
+                                                      W.binv_off.p, W.err.p);
+        HM_LAUNCH_CHECK();
+        int e = 0;
+        HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        if (e) fail(HM_EBREAKDOWN, "a diagonal leaf block of A is singular");
+        return;
+    }
     const size_t smem = W.bj_needs_global ? 0 : sizeof(float) * BJ_MAX_ROWS_SMEM * BJ_MAX_ROWS_SMEM;
     if (smem > 48 * 1024)
         HM_CUDA(cudaFuncSetAttribute(k_bj_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

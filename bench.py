@@ -475,6 +475,22 @@ def run_learned(args, dev, torch, hmat, synth):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(dist, value, device):
+    """The largest of the ranks' values (each rank passes its own; None: one process)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(world, bytes_per_product, seconds):
+    """Whole-job rate of `world` replicas that each stream bytes_per_product in
+    `seconds` (the slowest rank's time)."""
+    return world * bytes_per_product / seconds / 1e9
+
+
 def cores():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n else os.cpu_count()
@@ -600,12 +616,8 @@ def main():
     ph = H.timing_read()
     H.check(stream)
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * B / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1) / args.steps, dev)
+    value = whole_job_gbs(world, B, ms * 1e-3)
     hbm, peak_kind = peaks()
     cnt = max(ph["count"], 1)
     t2 = ph["phase2"] / cnt * 1e-3
@@ -628,12 +640,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(ke):
         H.matvec_host(xh, yh, stream)
-    te = (time.perf_counter() - t0) / ke
-    if dist is not None:
-        t = torch.tensor([te], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
-    e2e = {"value": world * B / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(xh.nbytes),
+    te = max_over_ranks(dist, (time.perf_counter() - t0) / ke, dev)
+    e2e = {"value": whole_job_gbs(world, B, te), "unit": "GB/s", "h2d_bytes_per_step": int(xh.nbytes),
            "d2h_bytes_per_step": int(yh.nbytes), "ms_per_step": te * 1e3}
 
     gmres = None

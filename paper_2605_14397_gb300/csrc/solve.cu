@@ -421,15 +421,23 @@ __global__ void __launch_bounds__(ROW_NT) k_arn_first(const Y* __restrict__ y, c
 }
 
 // sum the per-CTA partials: out[k][jj] = sum_b part[b][k][jj]
+// sum over the row blocks of one value's partials: eight loads in flight, the eight
+// running sums combined in a fixed order (deterministic)
+__device__ __forceinline__ double sum_parts(const double* __restrict__ part, int nblk, int nr, int k, int jj) {
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int b = 0;
+    for (; b + 7 < nblk; b += 8)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] += part[((int64_t)(b + u) * nr + k) * 132 + jj];
+    for (; b < nblk; ++b) a[0] += part[((int64_t)b * nr + k) * 132 + jj];
+    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 __global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int nr, int nvals, double* __restrict__ out,
                                const CycleState* __restrict__ cs) {
     const int k = blockIdx.x;
     if (cs[k].done) return;
-    for (int jj = threadIdx.x; jj < nvals; jj += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[((int64_t)b * nr + k) * 132 + jj];
-        out[k * 132 + jj] = s;
-    }
+    for (int jj = threadIdx.x; jj < nvals; jj += blockDim.x) out[k * 132 + jj] = sum_parts(part, nblk, nr, k, jj);
 }
 
 // w -= V h (h = previous dots); then either partial dots with V (second pass) or
@@ -491,8 +499,7 @@ __device__ void givens_one(int k, const double* __restrict__ h1, const double* _
                            const double* __restrict__ part, int nblk, int nr, int j, int m, double* __restrict__ Hm,
                            double* __restrict__ cs_, double* __restrict__ sn_, double* __restrict__ g,
                            CycleState* __restrict__ st) {
-    double nrm2 = 0.0;
-    for (int b = 0; b < nblk; ++b) nrm2 += part[((int64_t)b * nr + k) * 132];
+    const double nrm2 = sum_parts(part, nblk, nr, k, 0);
     const double hn = sqrt(nrm2);
     double* col = Hm + ((int64_t)k * m + j) * (m + 1);
     double* c = cs_ + (int64_t)k * (m + 1);

@@ -26,6 +26,7 @@
 //        apart, the two parts combined in FP64 -- the stored operator applied to FP64
 //        vectors to about 1e-13 relative while the coefficients stream at 4 (or 2) bytes.
 #include <algorithm>
+#include <type_traits>
 
 #include "hmat_impl.h"
 #include "pipeline.cuh"
@@ -587,6 +588,122 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     }
 }
 
+// ---- phase 1 on tensor cores: BF16 V factors, 16 right-hand sides
+//
+// P (columns x 16) = V_chunk^T X_leaf as mma.sync m16n8k16 BF16 x BF16 -> FP32: the A
+// operand is V^T (row m = V column, k = leaf row; a column of the stream is contiguous in
+// shared memory, so ldmatrix reads A fragments directly), the B operand the leaf's rows
+// of x, each value split into BF16 hi + lo (two products, x kept to ~16 bits), kept in
+// registers for the whole leaf.  Warp w takes n-tile w % 2 (8 RHS) and m-tiles
+// w / 2, w / 2 + NCW / 2, ...; a lane whose ldmatrix row lies outside the chunk reads a
+// zeroed 16-byte line instead, so no access leaves the chunk.
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// round to nearest even BF16 bits
+__device__ __forceinline__ uint32_t bf16_bits(float v) {
+    const uint32_t u = __float_as_uint(v);
+    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_value(uint32_t b) { return __uint_as_float(b << 16); }
+
+constexpr int TC_KT = 12;  // k-tiles of 16 rows: leaves of up to 192 rows
+
+template <int NCW>
+__global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1_tc(StreamArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(16) uint16_t zline[8];
+    uint64_t* full = (uint64_t*)smem;
+    uint64_t* empty = full + STAGES;
+    unsigned char* stage = smem + BAR_BYTES;
+
+    if (a.skip && *(volatile const int*)a.skip) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < 8) zline[threadIdx.x] = 0;
+    init_ring(full, empty, NCW);
+    const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
+    if (w == NCW) {
+        if (lane == 0) produce<uint16_t, float, 16, false>(a, stage, STAGE_BYTES, full, empty, c0, c1);
+        return;
+    }
+    const float* xc = (const float*)a.xc;
+    float* P = (float*)a.out;
+    const int nt = w & 1;
+    const uint32_t zaddr = smem_u32(zline);
+    int cur = -1, rows = 0;
+    uint32_t bh[TC_KT][2], bl[TC_KT][2];
+    Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
+    for (int i = c0; i < c1; ++i) {
+        const Chunk ch = nxt;
+        if (i + 1 < c1) nxt = a.chunks[i + 1];
+        const int q = i - c0, s = q % STAGES;
+        if (ch.leaf != cur) {
+            cur = ch.leaf;
+            const LeafDesc L = a.leaves[cur];
+            rows = 3 * L.n;
+            // B fragments: b0b1 = X[k0 + 2 (lane % 4) + {0, 1}][n], b2b3 = the same 8 rows on
+            // (n = nt * 8 + lane / 4), low half the smaller k
+            const int n = nt * 8 + (lane >> 2);
+#pragma unroll
+            for (int kt = 0; kt < TC_KT; ++kt)
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t hi2 = 0, lo2 = 0;
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int k = kt * 16 + hh * 8 + 2 * (lane & 3) + e;
+                        const float x = k < rows ? xc[(3 * (int64_t)L.begin + k) * 16 + n] : 0.f;
+                        const uint32_t hb = bf16_bits(x);
+                        const uint32_t lb = bf16_bits(x - bf16_value(hb));
+                        hi2 |= hb << (16 * e);
+                        lo2 |= lb << (16 * e);
+                    }
+                    bh[kt][hh] = hi2;
+                    bl[kt][hh] = lo2;
+                }
+        }
+        mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
+        const uint16_t* buf = (const uint16_t*)(stage + (size_t)s * STAGE_BYTES);
+        const int ld = ch.ld, ncols = ch.ncols;
+        const int mtiles = (ncols + 15) >> 4;
+        const int j8 = lane >> 3, i8 = lane & 7;
+        for (int mt = w >> 1; mt < mtiles; mt += NCW / 2) {
+            const int m = mt * 16 + (j8 & 1) * 8 + i8;  // this lane's ldmatrix row (a V column)
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < TC_KT; ++kt) {
+                const int k = kt * 16 + (j8 >> 1) * 8;
+                if (kt * 16 >= ld) break;
+                const uint32_t addr = (m < ncols && k < ld) ? smem_u32(buf + (size_t)m * ld + k) : zaddr;
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4(addr, a0, a1, a2, a3);
+                mma_bf16(d, a0, a1, a2, a3, bh[kt][0], bh[kt][1]);
+                mma_bf16(d, a0, a1, a2, a3, bl[kt][0], bl[kt][1]);
+            }
+            // d0, d1: column mt*16 + lane/4, RHS nt*8 + 2 (lane % 4) + {0, 1}; d2, d3: column + 8
+            const int col = mt * 16 + (lane >> 2), rhs = nt * 8 + 2 * (lane & 3);
+            if (col < ncols)
+                *reinterpret_cast<float2*>(P + (ch.zoff + col) * 16 + rhs) = make_float2(d[0], d[1]);
+            if (col + 8 < ncols)
+                *reinterpret_cast<float2*>(P + (ch.zoff + col + 8) * 16 + rhs) = make_float2(d[2], d[3]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + s);
+    }
+}
+
 constexpr int EV_PER_PRODUCT = 6;
 constexpr int EV_POOL = EV_PER_PRODUCT * 1024;
 
@@ -630,6 +747,8 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     using Acc = typename AccT<MODE>::type;
     using V = typename AccT<MODE>::vec;
     const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES;
+    // BF16 factors with 16 RHS on leaves of up to 192 rows: phase 1 on tensor cores
+    constexpr bool kTensorPhase1 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
     const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
                          (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc);
     // shared-memory opt-in, once per device for each instantiation
@@ -639,6 +758,8 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
         HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem1));
+        if constexpr (kTensorPhase1)
+            HM_CUDA(cudaFuncSetAttribute(k_phase1_tc<NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
         HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW2, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem2));
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
@@ -648,7 +769,12 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         a.chunks = PL.ch1.p;
         a.cta_begin = PL.cta1.p;
         a.out = MODE == 0 ? (void*)H.Pf.p : (void*)H.P.p;
-        k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
+        bool tc = false;
+        if constexpr (kTensorPhase1) tc = base.nr == 16;
+        if (tc)
+            k_phase1_tc<NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
+        else
+            k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
         using Zt = typename AccT<MODE>::zin;

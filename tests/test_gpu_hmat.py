@@ -178,3 +178,21 @@ def test_blocks_over_the_rank_cap_are_refined(dev, max_rank, eps):
     x = synth.rhs_normal(3 * el.N, 41)
     assert rel(run_mv(dev, H, x, torch.float32), A @ x) <= eps + 1e-6
     assert rel(run_mv(dev, H, x, torch.float64), A @ x) <= eps + 1e-6
+
+
+@pytest.mark.parametrize("nrhs", [16, 13])
+def test_bf16_multi_rhs_tensor_core_phase(dev, nrhs):
+    """BF16 factors with 16 RHS run phase 1 on tensor cores (x split into BF16 hi + lo,
+    about 16 bits kept); 13 RHS take the CUDA-core path.  Both agree with the single-RHS
+    products to 1e-4 (the x split, relative to the whole product) and with the dense
+    oracle to the BF16 bound."""
+    import torch
+    el = synth.config_three_planes(16)
+    T, H = build_h(el, 32, 1e-6, "bf16")
+    X = synth.rhs_normal(3 * el.N, 51, nrhs=nrhs)
+    Y = run_mv(dev, H, X, torch.float32)
+    A = O.dense_matrix(el, E, NU)
+    for q in range(nrhs):
+        yq = run_mv(dev, H, X[q], torch.float32)
+        assert rel(Y[q], yq) < 1e-4, q
+        assert rel(Y[q], A @ X[q]) < 1e-2

@@ -247,6 +247,35 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
         po = spo;
     }
     auto at = [&](int q) -> int64_t { return (int64_t)po[q] * nrhs; };
+    if constexpr (std::is_same<V, float>::value) {
+        if ((nrhs & 3) == 0) {
+            // several RHS: each slice is rank * nrhs contiguous floats, read as float4
+            const int n4 = n >> 2;
+            const float4* P4 = reinterpret_cast<const float4*>(P);
+            for (int e = threadIdx.x; e < n4; e += 128) {
+                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+                int q = 0;
+                for (; q + 3 < F.n_tleaves; q += 4) {
+                    const float4 v0 = P4[(at(q) >> 2) + e], v1 = P4[(at(q + 1) >> 2) + e];
+                    const float4 v2 = P4[(at(q + 2) >> 2) + e], v3 = P4[(at(q + 3) >> 2) + e];
+                    s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+                    s1.x += v1.x; s1.y += v1.y; s1.z += v1.z; s1.w += v1.w;
+                    s2.x += v2.x; s2.y += v2.y; s2.z += v2.z; s2.w += v2.w;
+                    s3.x += v3.x; s3.y += v3.y; s3.z += v3.z; s3.w += v3.w;
+                }
+                for (; q < F.n_tleaves; ++q) {
+                    const float4 v0 = P4[(at(q) >> 2) + e];
+                    s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+                }
+                float* o = reinterpret_cast<float*>(tb) + F.tb_off * nrhs + 4 * e;
+                o[0] = (s0.x + s1.x) + (s2.x + s3.x);
+                o[1] = (s0.y + s1.y) + (s2.y + s3.y);
+                o[2] = (s0.z + s1.z) + (s2.z + s3.z);
+                o[3] = (s0.w + s1.w) + (s2.w + s3.w);
+            }
+            return;
+        }
+    }
     if (n >= 128) {
         for (int e = threadIdx.x; e < n; e += 128) {
             V s0 = 0, s1 = 0, s2 = 0, s3 = 0;

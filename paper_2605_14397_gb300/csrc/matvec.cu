@@ -224,10 +224,11 @@ __device__ __forceinline__ float to_zin(float v, float*) { return v; }
 __device__ __forceinline__ float2 to_zin(double v, float2*) { return split_d(v); }
 
 // tb[(tb_off + l) nr + k] = sum_q P[(poff[pbase + q] + l) nr + k], one CTA (128 threads)
+// (VEC4: FP32 with nr a multiple of 4, each slice read as float4)
 // per block: the n = r nr entries times G = 128 / n interleaved groups of leaf partials,
 // four independent loads in flight per thread, groups combined in a fixed order.  In F64
 // mode the sums are stored as (hi, lo) float pairs, the form phase 2 reads.
-template <class V, class Zt>
+template <class V, class Zt, bool VEC4>
 __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const int32_t* __restrict__ poff,
                                                    const V* __restrict__ P, Zt* __restrict__ tb, int nrhs,
                                                    const int* __restrict__ skip) {
@@ -247,8 +248,8 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
         po = spo;
     }
     auto at = [&](int q) -> int64_t { return (int64_t)po[q] * nrhs; };
-    if constexpr (std::is_same<V, float>::value) {
-        if ((nrhs & 3) == 0) {
+    if constexpr (VEC4) {
+        {
             // several RHS: each slice is rank * nrhs contiguous floats, read as float4
             const int n4 = n >> 2;
             const float4* P4 = reinterpret_cast<const float4*>(P);
@@ -807,8 +808,13 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
         using Zt = typename AccT<MODE>::zin;
-        k_reduce_tb<V, Zt><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
-                                                          base.skip);
+        // several FP32 RHS in multiples of 4: the float4 variant (nrhs 1 keeps the scalar one)
+        if (MODE == 0 && (base.nr & 3) == 0)
+            k_reduce_tb<V, Zt, MODE == 0><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out,
+                                                                            (Zt*)base.tb, base.nr, base.skip);
+        else
+            k_reduce_tb<V, Zt, false><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out,
+                                                                        (Zt*)base.tb, base.nr, base.skip);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 3, st);
     } else if (timed) {

@@ -53,6 +53,8 @@ def parse():
                    help="fault: the 51,468-element disk fault (default); faults64: 64 independent faults, "
                         "batched product vs per-fault launches; planes: three intersecting 300x300 planes, "
                         "16 right-hand sides")
+    p.add_argument("--batch-storage", default="bf16", choices=["f32", "bf16"],
+                   help="factor storage of the 64-fault batch (BF16 factors, FP32 near field)")
     p.add_argument("--tune", action="store_true", help="also run the leaf-size autotuner on the workload")
     return p.parse_args()
 
@@ -206,7 +208,7 @@ def run_faults64(args, dev, torch, hmat, synth):
     parts = []
     for el, nu in zip(els, nus):
         T = hmat.ClusterTree(el, 64, 2.0)
-        parts.append(hmat.HMatrix(T, el, E, float(nu), eps, "f32"))
+        parts.append(hmat.HMatrix(T, el, E, float(nu), eps, args.batch_storage))
         del T
     torch.cuda.synchronize()
     t_parts = time.perf_counter() - t0
@@ -214,7 +216,7 @@ def run_faults64(args, dev, torch, hmat, synth):
     B = hmat.HMatrix.batch(parts)
     t_merge = time.perf_counter() - t0
     info = B.info()
-    Bytes, _, _ = product_bytes(info, "f32")
+    Bytes, _, _ = product_bytes(info, args.batch_storage)
     nd = info["n_dof"]
     x = torch.as_tensor(synth.rhs_normal(nd, 1604), dtype=torch.float32, device=dev)
     y = torch.empty_like(x)
@@ -267,11 +269,13 @@ def run_faults64(args, dev, torch, hmat, synth):
     Ns = [el.N for el in els]
     line = {"metric": "batched H-matvec GB/s over 64 independent faults", "value": value, "unit": "GB/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["batched"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.batch_storage == "f32" else "bf16 factors, f32 accumulation",
             "data": "synthetic (seeded meshes and right-hand side)",
             "config": {"workload": "64 disk faults, N_f log-uniform in [2k, 40k] (%d..%d), %d elements, h = 2/256, "
                                    "nu_f ~ U[0.2, 0.3], leaf 64, eta 2, ACA eps 1e-6" % (min(Ns), max(Ns), sum(Ns)),
-                       "nrhs": 1, "storage": "f32", "bytes_per_product": Bytes,
+                       "nrhs": 1, "storage": args.batch_storage + " factors, f32 near field",
+                       "bytes_per_product": Bytes,
                        "assemble_parts_s": t_parts, "merge_s": t_merge,
                        "l2": "operator %.1f GB >> 129 MB L2: no flush" % (Bytes / 1e9)},
             "frac_of_hbm_peak": value / hbm, "peak_source": peak_kind,
@@ -324,6 +328,8 @@ def run_planes(args, dev, torch, hmat, synth):
 
     res["f32_16rhs_ms"] = timeit(lambda: H.matvec(X, Y, stream), args.steps)
     res["f32_1rhs_x16_ms"] = 16 * timeit(lambda: H.matvec(X[0], Y[0], stream), args.steps)
+    res["bf16_16rhs_ms"] = timeit(lambda: H.matvec(X, Y, stream, factors="bf16"), args.steps)
+    res["bf16_1rhs_x16_ms"] = 16 * timeit(lambda: H.matvec(X[0], Y[0], stream, factors="bf16"), args.steps)
     phases = {}
     for nrk, xa, ya in ((16, X, Y), (1, X[0], Y[0])):
         H.timing(True)

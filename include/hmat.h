@@ -189,6 +189,13 @@ void hm_hmat_destroy(hm_hmat* h);
 hm_status hm_matvec(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, int dtype,
                     void* stream);
 
+/* hm_matvec with the factor precision chosen: factors HM_F32 or HM_BF16 (it must be
+ * stored: storage HM_F32_BF16 keeps both), or 0 for the default of hm_matvec (FP32 when
+ * stored).  With BF16 factors and 16 right-hand sides the V^T x contraction runs on the
+ * tensor cores (BF16 x BF16 -> FP32, x split into BF16 hi + lo). */
+hm_status hm_matvec_factors(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, int dtype, int factors,
+                            void* stream);
+
 /* The same product for vectors in host memory (pinned memory is fastest): x_host is
  * copied to library-owned device scratch, the product runs on `stream`, y is copied
  * back to y_host and the stream is synchronised before returning. */

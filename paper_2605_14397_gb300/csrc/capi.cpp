@@ -177,6 +177,15 @@ hm_status hm_matvec(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs,
     HM_API_END
 }
 
+hm_status hm_matvec_factors(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs, int dtype, int factors,
+                            void* stream) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "matvec_factors: NULL H-matrix");
+    if (x_dev == y_dev) hm::fail(HM_EINVAL, "matvec_factors: x and y must not overlap");
+    hm::matvec(const_cast<hm::HMat&>(hh->h), x_dev, y_dev, nrhs, dtype, (cudaStream_t)stream, factors);
+    HM_API_END
+}
+
 hm_status hm_matvec_host(const hm_hmat* hh, const void* x_host, void* y_host, int nrhs, int dtype, void* stream) {
     HM_API_BEGIN
     if (!hh) hm::fail(HM_EINVAL, "matvec_host: NULL H-matrix");

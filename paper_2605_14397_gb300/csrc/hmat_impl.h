@@ -172,7 +172,7 @@ int product_error_flags(HMat& H, cudaStream_t st);
 void timing_enable(HMat& H, bool on);
 void timing_read(HMat& H, double out[6]);
 void matvec_host(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
-void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
+void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st, int factors = 0);
 // Product on cluster-ordered operands: xc is RHS-interleaved (xc[dof * nr + k]) with at
 // least 32 readable elements after its end, yc is RHS-major (yc[k * ndof + dof]).
 // fac: 0 FP32 factors, 1 BF16 factors.  dtype HM_F32: float vectors; HM_F64: xc holds

@@ -1015,12 +1015,16 @@ void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac,
     run_core(H, xc, yc, nr, dtype, fac, false, st, skip);
 }
 
-void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st) {
+void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st, int factors) {
     if (nrhs < 1) fail(HM_EINVAL, "matvec: nrhs must be >= 1");
     if (!x || !y) fail(HM_EINVAL, "matvec: NULL vector");
     if (dtype != HM_F32 && dtype != HM_F64) fail(HM_EINVAL, "matvec: dtype must be HM_F32 or HM_F64");
+    if (factors != 0 && factors != HM_F32 && factors != HM_BF16)
+        fail(HM_EINVAL, "matvec: factors must be 0, HM_F32 or HM_BF16");
+    // FP32 factors when stored, unless the caller asks for a stored precision
+    const int fac = factors == HM_BF16 ? 1 : (factors == HM_F32 ? 0 : (has_factors(H, 0) ? 0 : 1));
+    if (!has_factors(H, fac)) fail(HM_EINVAL, "matvec: the requested factor precision is not stored");
     ensure_product_scratch(H, std::min(nrhs, 16), st);
-    const int fac = has_factors(H, 0) ? 0 : 1;  // FP32 factors when stored
     // at most 16 right-hand sides per pass of the coefficient streams
     for (int k0 = 0; k0 < nrhs; k0 += 16) {
         const int nr = std::min(16, nrhs - k0);

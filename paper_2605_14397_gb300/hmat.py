@@ -104,6 +104,7 @@ SIGNATURES = [
     ("hm_matvec", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_hmat_check", _I, [_VP, _VP]),
     ("hm_matvec_host", _I, [_VP, _VP, _VP, _I, _I, _VP]),
+    ("hm_matvec_factors", _I, [_VP, _VP, _VP, _I, _I, _I, _VP]),
     ("hm_hmat_timing", _I, [_VP, _I]),
     ("hm_hmat_timing_read", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
     ("hm_gmres_solve", _I, [_VP, _VP, _D, _VP, _VP, _I, ctypes.POINTER(hm_solve_opts),
@@ -284,13 +285,20 @@ class HMatrix:
         _check(lib().hm_hmat_far_factors(self.handle, int(b), None, U.ctypes.data_as(_VP), V.ctypes.data_as(_VP)))
         return U.T, V.T  # column-major on the C side -> (3|s| x r), (3|t| x r)
 
-    def matvec(self, x, y, stream=None):
-        """y = E x; x, y torch CUDA tensors of shape (3N,) or (nrhs, 3N), float32 or float64."""
+    def matvec(self, x, y, stream=None, factors=None):
+        """y = E x; x, y torch CUDA tensors of shape (3N,) or (nrhs, 3N), float32 or float64;
+        factors "f32" or "bf16" picks a stored factor precision (default: FP32 when stored)."""
         import torch
         dt = {torch.float32: HM_F32, torch.float64: HM_F64}[x.dtype]
         assert y.dtype == x.dtype and x.is_contiguous() and y.is_contiguous()
         nrhs = 1 if x.dim() == 1 else x.shape[0]
-        _check(lib().hm_matvec(self.handle, _dptr(x), _dptr(y), int(nrhs), dt, ctypes.c_void_p(_stream_ptr(stream))))
+        if factors is None:
+            _check(lib().hm_matvec(self.handle, _dptr(x), _dptr(y), int(nrhs), dt,
+                                   ctypes.c_void_p(_stream_ptr(stream))))
+        else:
+            fc = {"f32": HM_F32, "bf16": HM_BF16}[factors]
+            _check(lib().hm_matvec_factors(self.handle, _dptr(x), _dptr(y), int(nrhs), dt, fc,
+                                           ctypes.c_void_p(_stream_ptr(stream))))
 
     def matvec_graph(self, x, y, stream=None):
         """matvec replayed from a CUDA graph instantiated for these (x, y) on first use."""

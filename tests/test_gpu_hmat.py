@@ -196,3 +196,26 @@ def test_bf16_multi_rhs_tensor_core_phase(dev, nrhs):
         yq = run_mv(dev, H, X[q], torch.float32)
         assert rel(Y[q], yq) < 1e-4, q
         assert rel(Y[q], A @ X[q]) < 1e-2
+
+
+def test_factor_precision_choice(dev):
+    """With both precisions stored, hm_matvec_factors picks either; the BF16 choice equals
+    the product of an H-matrix that stores BF16 only (same assembly, same plan); asking for
+    a precision that is not stored is an error."""
+    import torch
+    el = synth.config_penny(24)
+    T = hmat.ClusterTree(el, 32, 2.0)
+    Hb = hmat.HMatrix(T, el, E, NU, 1e-6, "both")
+    H16 = hmat.HMatrix(T, el, E, NU, 1e-6, "bf16")
+    H32 = hmat.HMatrix(T, el, E, NU, 1e-6, "f32")
+    x = torch.as_tensor(synth.rhs_normal(3 * el.N, 61), dtype=torch.float32, device=dev)
+    outs = {}
+    for name, H, fac in (("both16", Hb, "bf16"), ("only16", H16, None), ("both32", Hb, "f32"), ("only32", H32, None)):
+        y = torch.empty_like(x)
+        H.matvec(x, y, factors=fac)
+        outs[name] = y
+    torch.cuda.synchronize()
+    assert torch.equal(outs["both16"], outs["only16"]) and torch.equal(outs["both32"], outs["only32"])
+    with pytest.raises(hmat.HMError) as ei:
+        H16.matvec(x, torch.empty_like(x), factors="f32")
+    assert ei.value.status == hmat.HM_EINVAL

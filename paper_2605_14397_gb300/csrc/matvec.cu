@@ -395,35 +395,6 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int n
 }
 
 // ---- phase 2: y = [D | U] z per row leaf
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
-                                              uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// round to nearest even BF16 bits
-__device__ __forceinline__ uint32_t bf16_bits(float v) {
-    const uint32_t u = __float_as_uint(v);
-    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
-}
-__device__ __forceinline__ float bf16_value(uint32_t b) { return __uint_as_float(b << 16); }
-
 // RS > 1 splits each column's rows over RS warps (RPL / RS rows per lane each), so that
 // many right-hand sides fit in registers with more warps in flight.
 template <int MODE, class C, int NR, int RPL, int NCW, int RS>
@@ -441,15 +412,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     constexpr int NG = NCW / RS;   // column groups
     static_assert(RPL % RS == 0 && NCW % RS == 0, "row split must divide rows and warps");
     Acc* red = (Acc*)(stage + (size_t)STAGES * STRIDE);  // [NG][32 RPL]
-    // BF16 U slices with 16 RHS on tensor cores (mma.sync m16n8k16, t split into BF16 hi +
-    // lo): warp w owns (m-tile, n-tile) pairs w and w + 16 of the 12 x 2 of a 192-row
-    // leaf; at the leaf's end their sums go through tcb[row][16] into the flush.  A
-    // fragments come from the column-major slice with ldmatrix.trans; lanes whose line
-    // lies outside the chunk read a zeroed line.
-    constexpr bool TC = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6 && NCW == 16 &&
-                        RS == 2;
-    float* tcb = (float*)(red + (size_t)NG * 32 * RPL);  // [192][16] (TC only)
-    __shared__ __align__(16) uint16_t zline[8];
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -463,10 +425,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     Vv* slots = (Vv*)a.slots;
     const int g = w / RS, rbase = (w % RS) * 32 * RPW;
     Acc acc[NR][RPW];
-    const bool use_tc = TC && a.nr == 16;
-    float dtc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    if (TC && threadIdx.x < 8) zline[threadIdx.x] = 0;
-    if (TC) consumer_sync(NCW * 32);
     int cur = -1;
     LeafDesc L{};
 
@@ -475,21 +433,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const int rows = 3 * L.n;
         const bool whole = sp.nparts == 1;
         const int64_t slot = whole ? 0 : (int64_t)(sp.slot_base + (int)blockIdx.x - sp.w_first);
-        if (use_tc) {
-#pragma unroll
-            for (int pi = 0; pi < 2; ++pi) {
-                const int p = w + 16 * pi;
-                if (p < 24) {
-                    const int m = (p >> 1) * 16 + (lane >> 2), n = (p & 1) * 8 + 2 * (lane & 3);
-                    tcb[m * 16 + n] = dtc[pi][0];
-                    tcb[m * 16 + n + 1] = dtc[pi][1];
-                    tcb[(m + 8) * 16 + n] = dtc[pi][2];
-                    tcb[(m + 8) * 16 + n + 1] = dtc[pi][3];
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) dtc[pi][e] = 0.f;
-            }
-        }
         // k unrolled at compile time: a runtime index into acc would move it to local memory
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
@@ -500,8 +443,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
             for (int r = threadIdx.x; r < rows; r += NCW * 32) {
                 Acc s = red[r];
                 for (int q = 1; q < NG; ++q) acc_add(s, red[(size_t)q * (32 * RPL) + r]);
-                if constexpr (TC)
-                    if (use_tc) acc_add(s, tcb[r * 16 + k]);
                 if (whole)
                     yc[(int64_t)k * a.ndof + 3 * (int64_t)L.begin + r] = (Vv)acc_value(s);
                 else
@@ -556,52 +497,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         // Rows at or beyond `rows` read whatever follows the column in shared memory (the
         // next column, stage or the reduction buffer: always inside the allocation); their
         // accumulators are never flushed, so no bound check is needed per coefficient.
-        if constexpr (TC) {
-            if (use_tc && ch.kind == 1) {
-                const uint16_t* ub = (const uint16_t*)buf;
-                const float* zt = (const float*)zb;
-                const int ncols = ch.ncols, ld = ch.ld;
-                const int kts = (ncols + 15) >> 4;
-                const int j8 = lane >> 3, i8 = lane & 7;
-                const uint32_t zaddr = smem_u32(zline);
-#pragma unroll
-                for (int pi = 0; pi < 2; ++pi) {
-                    const int p = w + 16 * pi;
-                    if (p >= 24) break;
-                    const int mt = p >> 1, nt = p & 1;
-                    if (mt * 16 >= rows) continue;
-                    const int n = nt * 8 + (lane >> 2);
-                    for (int kt = 0; kt < kts; ++kt) {
-                        const int kcol = kt * 16 + (j8 >> 1) * 8 + i8;
-                        const int mrow = mt * 16 + (j8 & 1) * 8;
-                        const uint32_t addr =
-                            (kcol < ncols && mrow < ld) ? smem_u32(ub + (size_t)kcol * ld + mrow) : zaddr;
-                        uint32_t a0, a1, a2, a3;
-                        ldsm_x4_trans(addr, a0, a1, a2, a3);
-                        uint32_t bh[2], bl[2];
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            uint32_t hi2 = 0, lo2 = 0;
-#pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const int k = kt * 16 + hh * 8 + 2 * (lane & 3) + e;
-                                const float t = k < ncols ? zt[k * 16 + n] : 0.f;
-                                const uint32_t hb = bf16_bits(t);
-                                hi2 |= hb << (16 * e);
-                                lo2 |= bf16_bits(t - bf16_value(hb)) << (16 * e);
-                            }
-                            bh[hh] = hi2;
-                            bl[hh] = lo2;
-                        }
-                        mma_bf16(dtc[pi], a0, a1, a2, a3, bh[0], bh[1]);
-                        mma_bf16(dtc[pi], a0, a1, a2, a3, bl[0], bl[1]);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(empty + s);
-                continue;
-            }
-        }
         for (int c = g; c < ch.ncols; c += NG) {
             decltype(make_z(zin_zero<Zin>())) zv[NR];
             if constexpr (NR == 1)
@@ -732,6 +627,28 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
 // registers for the whole leaf.  Warp w takes n-tile w % 2 (8 RHS) and m-tiles
 // w / 2, w / 2 + NCW / 2, ...; a lane whose ldmatrix row lies outside the chunk reads a
 // zeroed 16-byte line instead, so no access leaves the chunk.
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// round to nearest even BF16 bits
+__device__ __forceinline__ uint32_t bf16_bits(float v) {
+    const uint32_t u = __float_as_uint(v);
+    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_value(uint32_t b) { return __uint_as_float(b << 16); }
+
 constexpr int TC_KT = 12;  // k-tiles of 16 rows: leaves of up to 192 rows
 
 template <int NCW>
@@ -862,10 +779,8 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES;
     // BF16 factors with 16 RHS on leaves of up to 192 rows: phase 1 on tensor cores
     constexpr bool kTensorPhase1 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
-    constexpr bool kTensorPhase2 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6 &&
-                                   NCW2 == 16 && RS == 2;
     const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
-                         (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc) + (kTensorPhase2 ? 192 * 16 * 4 : 0);
+                         (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc);
     // shared-memory opt-in, once per device for each instantiation
     static bool attr_done[64] = {};
     int dev = 0;

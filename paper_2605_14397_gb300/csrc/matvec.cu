@@ -185,10 +185,18 @@ __device__ __forceinline__ void load_z(Z64 (&z)[NR], const float2* p, int nr) {
 __device__ __forceinline__ float coef(const float* p, int i) { return p[i]; }
 __device__ __forceinline__ float coef(const uint16_t* p, int i) { return __uint_as_float(((uint32_t)p[i]) << 16); }
 
+// Programmatic dependent launch: the kernels of a product after the gather are launched
+// so that they may start while their predecessor drains; each waits for it (and its
+// memory) with griddepcontrol.wait before touching what it produced, and lets its own
+// successor launch early with griddepcontrol.launch_dependents.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // xc[dof * nr + k] = x[k * ndof + user dof]
 template <class V>
 __global__ void k_gather(const V* __restrict__ x, V* __restrict__ xc, const int32_t* __restrict__ perm, int64_t N,
                          int nrhs) {
+    pdl_trigger();
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t ndof = 3 * N;
     if (q >= ndof * nrhs) return;
@@ -200,6 +208,7 @@ __global__ void k_gather(const V* __restrict__ x, V* __restrict__ xc, const int3
 // F64 gather: xc[dof * nr + k] = (hi, lo) split of x[k * ndof + user dof]
 __global__ void k_gather_split(const double* __restrict__ x, float2* __restrict__ xc,
                                const int32_t* __restrict__ perm, int64_t N, int nrhs) {
+    pdl_trigger();
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t ndof = 3 * N;
     if (q >= ndof * nrhs) return;
@@ -212,6 +221,7 @@ __global__ void k_gather_split(const double* __restrict__ x, float2* __restrict_
 template <class V>
 __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int32_t* __restrict__ perm, int64_t N,
                           int nrhs) {
+    pdl_wait();
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t ndof = 3 * N;
     if (q >= ndof * nrhs) return;
@@ -233,6 +243,8 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
                                                    const V* __restrict__ P, Zt* __restrict__ tb, int nrhs,
                                                    const int* __restrict__ skip) {
     __shared__ V sp[128];
+    pdl_wait();
+    pdl_trigger();
     if (skip && *(volatile const int*)skip) return;
     const FarDesc F = far[blockIdx.x];
     const int n = F.rank * nrhs;
@@ -417,8 +429,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
+    pdl_trigger();
     if (w == NCW) {
-        if (lane == 0) produce<C, Vv, NR, true>(a, stage, STRIDE, full, empty, c0, c1);
+        // the operand ranges (t) come from the reduction: wait for it before the first copy
+        if (lane == 0) {
+            pdl_wait();
+            produce<C, Vv, NR, true>(a, stage, STRIDE, full, empty, c0, c1);
+        }
         return;
     }
     Vv* yc = (Vv*)a.out;
@@ -541,10 +558,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
+    pdl_trigger();
     if (w == NCW) {
+        // the V coefficients are constant: the copies start while the gather drains
         if (lane == 0) produce<C, Vv, NR, false>(a, stage, STAGE_BYTES, full, empty, c0, c1);
         return;
     }
+    pdl_wait();  // x in cluster order comes from the preceding kernel
     Vv* P = (Vv*)a.out;
     int cur = -1;
     int rows = 0;
@@ -664,10 +684,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1_tc(StreamArgs a) {
     if (threadIdx.x < 8) zline[threadIdx.x] = 0;
     init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
+    pdl_trigger();
     if (w == NCW) {
         if (lane == 0) produce<uint16_t, float, 16, false>(a, stage, STAGE_BYTES, full, empty, c0, c1);
         return;
     }
+    pdl_wait();
     const float* xc = (const float*)a.xc;
     float* P = (float*)a.out;
     const int nt = w & 1;
@@ -732,6 +754,23 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1_tc(StreamArgs a) {
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + s);
     }
+}
+
+// launch with programmatic stream serialisation (the kernel may start before its
+// predecessor on the stream completes; it synchronises through griddepcontrol.wait)
+template <class... P, class... A>
+void launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HM_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
 }
 
 constexpr int EV_PER_PRODUCT = 6;
@@ -802,19 +841,21 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         bool tc = false;
         if constexpr (kTensorPhase1) tc = base.nr == 16;
         if (tc)
-            k_phase1_tc<NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
+            launch_pdl(k_phase1_tc<NCW>, dim3(H.grid), dim3((NCW + 1) * 32), smem1, st, a);
         else
-            k_phase1<MODE, C, NR, RPL, NCW><<<H.grid, (NCW + 1) * 32, smem1, st>>>(a);
+            launch_pdl(k_phase1<MODE, C, NR, RPL, NCW>, dim3(H.grid), dim3((NCW + 1) * 32), smem1, st, a);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
         using Zt = typename AccT<MODE>::zin;
         // several FP32 RHS in multiples of 4: the float4 variant (nrhs 1 keeps the scalar one)
         if (MODE == 0 && (base.nr & 3) == 0)
-            k_reduce_tb<V, Zt, MODE == 0><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out,
-                                                                            (Zt*)base.tb, base.nr, base.skip);
+            launch_pdl(k_reduce_tb<V, Zt, MODE == 0>, dim3((unsigned)H.n_far), dim3(128), 0, st,
+                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
+                       base.skip);
         else
-            k_reduce_tb<V, Zt, false><<<(unsigned)H.n_far, 128, 0, st>>>(H.far.p, H.poff.p, (const V*)a.out,
-                                                                        (Zt*)base.tb, base.nr, base.skip);
+            launch_pdl(k_reduce_tb<V, Zt, false>, dim3((unsigned)H.n_far), dim3(128), 0, st,
+                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
+                       base.skip);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 3, st);
     } else if (timed) {
@@ -825,7 +866,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     a.chunks = PL.ch2.p;
     a.cta_begin = PL.cta2.p;
     a.split = PL.split.p;
-    k_phase2<MODE, C, NR, RPL, NCW2, RS><<<H.grid, (NCW2 + 1) * 32, smem2, st>>>(a);
+    launch_pdl(k_phase2<MODE, C, NR, RPL, NCW2, RS>, dim3(H.grid), dim3((NCW2 + 1) * 32), smem2, st, a);
     HM_LAUNCH_CHECK();
     if (timed) mark(H, 4, st);
 }
@@ -1037,14 +1078,16 @@ void matvec(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t s
             k_gather<float><<<gb, 256, 0, st>>>(xf, H.xcf.p, H.perm.p, H.N, nr);
             mark(H, 1, st);
             run_core(H, H.xcf.p, H.ycf.p, nr, dtype, fac, true, st);
-            k_scatter<float><<<gb, 256, 0, st>>>(H.ycf.p, yf, H.perm.p, H.N, nr);
+            launch_pdl(k_scatter<float>, dim3(gb), dim3(256), 0, st, (const float*)H.ycf.p, yf,
+                       (const int32_t*)H.perm.p, (int64_t)H.N, nr);
         } else {
             const double* xd = (const double*)x + (int64_t)k0 * H.ndof;
             double* yd = (double*)y + (int64_t)k0 * H.ndof;
             k_gather_split<<<gb, 256, 0, st>>>(xd, (float2*)H.xc.p, H.perm.p, H.N, nr);
             mark(H, 1, st);
             run_core(H, H.xc.p, H.yc.p, nr, dtype, fac, true, st);
-            k_scatter<double><<<gb, 256, 0, st>>>(H.yc.p, yd, H.perm.p, H.N, nr);
+            launch_pdl(k_scatter<double>, dim3(gb), dim3(256), 0, st, (const double*)H.yc.p, yd,
+                       (const int32_t*)H.perm.p, (int64_t)H.N, nr);
         }
         HM_LAUNCH_CHECK();
         mark(H, 5, st);

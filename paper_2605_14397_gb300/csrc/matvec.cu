@@ -8,7 +8,7 @@
 //   scatter  y[perm] = yc
 //
 // Phases 1 and 2 are persistent kernels, one CTA per SM.  Their coefficient streams are
-// cut into chunks of whole columns of one tile or factor slice (at most 32 KB and 64
+// cut into chunks of whole columns of one tile or factor slice (at most 32 KB and 128
 // columns) and the chunk list is split into equal byte ranges, one per CTA ("stream-K"):
 // every SM streams the same number of bytes.  One producer thread moves each chunk --
 // its coefficients and, in phase 2, the contiguous range of operands it multiplies --
@@ -37,7 +37,7 @@ namespace {
 
 constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = 32768;   // coefficients of one chunk
-constexpr int MAX_CHUNK_COLS = 64;
+constexpr int MAX_CHUNK_COLS = 128;
 constexpr int BAR_BYTES = 128;
 constexpr int VEC_SLACK = 32;        // elements after xc / tb so rounded-up copies stay inside
 

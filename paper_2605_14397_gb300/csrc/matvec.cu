@@ -570,6 +570,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     int rows = 0;
     using Zin = typename AccT<MODE>::zin;
     const Zin* xs = (const Zin*)a.xc;
+    constexpr bool PAIR = std::is_same<C, uint16_t>::value && NR == 1 && RPL == 6;
     decltype(make_z(zin_zero<Zin>())) xr[NR][RPL];
     Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
     for (int i = c0; i < c1; ++i) {
@@ -582,7 +583,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
             rows = 3 * L.n;
 #pragma unroll
             for (int ii = 0; ii < RPL; ++ii) {
-                const int r = lane + 32 * ii;
+                // BF16 single-RHS columns are read two rows per 32-bit word: lane holds rows
+                // 2 lane + 64 (ii / 2) + ii % 2; otherwise rows lane + 32 ii
+                const int r = PAIR ? 2 * lane + 64 * (ii >> 1) + (ii & 1) : lane + 32 * ii;
 #pragma unroll
                 for (int k = 0; k < NR; ++k)
                     xr[k][ii] = make_z((r < rows && k < a.nr) ? xs[(3 * (int64_t)L.begin + r) * a.nr + k]
@@ -600,14 +603,32 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
                 Acc acc[CG];
 #pragma unroll
                 for (int j = 0; j < CG; ++j) acc_zero(acc[j]);
+                if constexpr (PAIR) {
 #pragma unroll
-                for (int ii = 0; ii < RPL; ++ii) {
-                    const int r = lane + 32 * ii;
+                    for (int jj = 0; jj < RPL / 2; ++jj) {
+                        const int r0 = 2 * lane + 64 * jj;
 #pragma unroll
-                    for (int j = 0; j < CG; ++j) {
-                        const int cj = c + j * NCW;
-                        const float v = (r < rows && cj < ch.ncols) ? coef(buf + (size_t)cj * ch.ld, r) : 0.f;
-                        acc_fma(acc[j], v, xr[0][ii]);
+                        for (int j = 0; j < CG; ++j) {
+                            const int cj = c + j * NCW;
+                            uint32_t wv = 0u;
+                            if (r0 < rows && cj < ch.ncols)
+                                wv = reinterpret_cast<const uint32_t*>(buf + (size_t)cj * ch.ld)[lane + 32 * jj];
+                            const float v0 = __uint_as_float(wv << 16);
+                            const float v1 = r0 + 1 < rows ? __uint_as_float(wv & 0xffff0000u) : 0.f;
+                            acc_fma(acc[j], v0, xr[0][2 * jj]);
+                            acc_fma(acc[j], v1, xr[0][2 * jj + 1]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int ii = 0; ii < RPL; ++ii) {
+                        const int r = lane + 32 * ii;
+#pragma unroll
+                        for (int j = 0; j < CG; ++j) {
+                            const int cj = c + j * NCW;
+                            const float v = (r < rows && cj < ch.ncols) ? coef(buf + (size_t)cj * ch.ld, r) : 0.f;
+                            acc_fma(acc[j], v, xr[0][ii]);
+                        }
                     }
                 }
                 const int j = warp_reduce_scatter<CG>(acc, lane);

@@ -327,7 +327,19 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
         float acc[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i) acc[i] = 0.f;
-        for (int c = w; c < n; c += 8) {
+        // two columns per pass: twice the loads in flight
+        int c = w;
+        for (; c + 8 < n; c += 16) {
+            const float vc0 = (float)vk[c], vc1 = (float)vk[c + 8];
+            const float* col0 = B + (int64_t)c * L.ld;
+            const float* col1 = col0 + (int64_t)8 * L.ld;
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const int r = lane + 32 * i;
+                if (r < n) acc[i] = fmaf(__ldg(col1 + r), vc1, fmaf(__ldg(col0 + r), vc0, acc[i]));
+            }
+        }
+        for (; c < n; c += 8) {
             const float vc = (float)vk[c];
             const float* col = B + (int64_t)c * L.ld;
 #pragma unroll
@@ -421,23 +433,30 @@ __global__ void __launch_bounds__(ROW_NT) k_arn_first(const Y* __restrict__ y, c
 }
 
 // sum the per-CTA partials: out[k][jj] = sum_b part[b][k][jj]
-// sum over the row blocks of one value's partials: eight loads in flight, the eight
-// running sums combined in a fixed order (deterministic)
-__device__ __forceinline__ double sum_parts(const double* __restrict__ part, int nblk, int nr, int k, int jj) {
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int b = 0;
-    for (; b + 7 < nblk; b += 8)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] += part[((int64_t)(b + u) * nr + k) * 132 + jj];
-    for (; b < nblk; ++b) a[0] += part[((int64_t)b * nr + k) * 132 + jj];
-    return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+// warp-wide sum of one value's partials: lanes over the row blocks, then a butterfly
+// (fixed order: deterministic)
+__device__ __forceinline__ double warp_sum_parts(const double* __restrict__ part, int nblk, int nr, int k, int jj) {
+    const int lane = threadIdx.x & 31;
+    double a0 = 0.0, a1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nblk; b += 64) {
+        a0 += part[((int64_t)b * nr + k) * 132 + jj];
+        a1 += part[((int64_t)(b + 32) * nr + k) * 132 + jj];
+    }
+    if (b < nblk) a0 += part[((int64_t)b * nr + k) * 132 + jj];
+    return warp_sum_d(a0 + a1);
 }
 
+// h[k][jj] = sum over row blocks, one warp per value (launched with 512 threads per RHS)
 __global__ void k_reduce_parts(const double* __restrict__ part, int nblk, int nr, int nvals, double* __restrict__ out,
                                const CycleState* __restrict__ cs) {
     const int k = blockIdx.x;
     if (cs[k].done) return;
-    for (int jj = threadIdx.x; jj < nvals; jj += blockDim.x) out[k * 132 + jj] = sum_parts(part, nblk, nr, k, jj);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int jj = w; jj < nvals; jj += nw) {
+        const double v = warp_sum_parts(part, nblk, nr, k, jj);
+        if ((threadIdx.x & 31) == 0) out[k * 132 + jj] = v;
+    }
 }
 
 // w -= V h (h = previous dots); then either partial dots with V (second pass) or
@@ -498,8 +517,7 @@ __global__ void __launch_bounds__(ROW_NT) k_arn_update(double* __restrict__ w, c
 __device__ void givens_one(int k, const double* __restrict__ h1, const double* __restrict__ h2,
                            const double* __restrict__ part, int nblk, int nr, int j, int m, double* __restrict__ Hm,
                            double* __restrict__ cs_, double* __restrict__ sn_, double* __restrict__ g,
-                           CycleState* __restrict__ st) {
-    const double nrm2 = sum_parts(part, nblk, nr, k, 0);
+                           CycleState* __restrict__ st, double nrm2) {
     const double hn = sqrt(nrm2);
     double* col = Hm + ((int64_t)k * m + j) * (m + 1);
     double* c = cs_ + (int64_t)k * (m + 1);
@@ -542,8 +560,15 @@ __global__ void k_givens(const double* __restrict__ h1, const double* __restrict
                          int nblk, int nr, int j, int m, double* __restrict__ Hm, double* __restrict__ cs_,
                          double* __restrict__ sn_, double* __restrict__ g, CycleState* __restrict__ st,
                          int* __restrict__ alldone) {
+    __shared__ double nrm[32];
+    // ||w||^2 of every RHS first, the whole warp on each sum
+    for (int q = 0; q < nr; ++q) {
+        const double v = warp_sum_parts(part, nblk, nr, q, 0);
+        if (threadIdx.x == 0) nrm[q] = v;
+    }
+    __syncwarp();
     const int k = threadIdx.x;
-    if (k < nr && !st[k].done) givens_one(k, h1, h2, part, nblk, nr, j, m, Hm, cs_, sn_, g, st);
+    if (k < nr && !st[k].done) givens_one(k, h1, h2, part, nblk, nr, j, m, Hm, cs_, sn_, g, st, nrm[k]);
     __syncthreads();
     if (threadIdx.x == 0) {
         int all = 1;
@@ -794,9 +819,9 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
                                                       W.part.p, W.st.p);
         }
         HM_LAUNCH_CHECK();
-        k_reduce_parts<<<nr, 128, 0, st>>>(W.part.p, nb, nr, j + 1, W.h1.p, W.st.p);
+        k_reduce_parts<<<nr, 512, 0, st>>>(W.part.p, nb, nr, j + 1, W.h1.p, W.st.p);
         k_arn_update<<<nb, ROW_NT, 0, st>>>(W.w.p, W.V.p, W.h1.p, n, nr, j, W.vstride, W.part.p, 1, W.st.p);
-        k_reduce_parts<<<nr, 128, 0, st>>>(W.part.p, nb, nr, j + 1, W.h2.p, W.st.p);
+        k_reduce_parts<<<nr, 512, 0, st>>>(W.part.p, nb, nr, j + 1, W.h2.p, W.st.p);
         k_arn_update<<<nb, ROW_NT, 0, st>>>(W.w.p, W.V.p, W.h2.p, n, nr, j, W.vstride, W.part.p, 0, W.st.p);
         k_givens<<<1, 32, 0, st>>>(W.h1.p, W.h2.p, W.part.p, nb, nr, j, m, W.Hm.p, W.cs.p, W.sn.p, W.g.p, W.st.p,
                                    W.alldone.p);

@@ -441,10 +441,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     Vv* yc = (Vv*)a.out;
     Vv* slots = (Vv*)a.slots;
     const int g = w / RS, rbase = (w % RS) * 32 * RPW;
-    // single RHS: each lane reads two consecutive rows per load (float2 / two BF16 in 32
-    // bits), so accumulator i holds row 2 lane + 64 (i / 2) + i % 2; otherwise lane + 32 i
-    constexpr bool PAIR = NR == 1 && RS == 1 && RPL % 2 == 0;
-    auto prow = [&](int i) { return PAIR ? 2 * lane + 64 * (i >> 1) + (i & 1) : lane + 32 * i; };
     Acc acc[NR][RPW];
     int cur = -1;
     LeafDesc L{};
@@ -459,7 +455,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         for (int k = 0; k < NR; ++k) {
             if (k >= a.nr) break;
 #pragma unroll
-            for (int i = 0; i < RPW; ++i) red[(size_t)g * (32 * RPL) + rbase + prow(i)] = acc[k][i];
+            for (int i = 0; i < RPW; ++i) red[(size_t)g * (32 * RPL) + rbase + lane + 32 * i] = acc[k][i];
             consumer_sync(NCW * 32);
             for (int r = threadIdx.x; r < rows; r += NCW * 32) {
                 Acc s = red[r];
@@ -524,34 +520,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 zv[0] = make_z(zb[c]);
             else
                 load_z<NR>(zv, zb + (size_t)c * a.nr, a.nr);
-            if constexpr (PAIR) {
-                if (ch.kind == 0) {
-                    const float2* col = reinterpret_cast<const float2*>((const float*)buf + (size_t)c * ch.ld) + lane;
-#pragma unroll
-                    for (int jj = 0; jj < RPW / 2; ++jj) {
-                        const float2 v = col[32 * jj];
-                        acc_fma(acc[0][2 * jj], v.x, zv[0]);
-                        acc_fma(acc[0][2 * jj + 1], v.y, zv[0]);
-                    }
-                } else if constexpr (std::is_same<C, uint16_t>::value) {
-                    const uint32_t* col = reinterpret_cast<const uint32_t*>((const C*)buf + (size_t)c * ch.ld) + lane;
-#pragma unroll
-                    for (int jj = 0; jj < RPW / 2; ++jj) {
-                        const uint32_t wv = col[32 * jj];
-                        acc_fma(acc[0][2 * jj], __uint_as_float(wv << 16), zv[0]);
-                        acc_fma(acc[0][2 * jj + 1], __uint_as_float(wv & 0xffff0000u), zv[0]);
-                    }
-                } else {
-                    const float2* col = reinterpret_cast<const float2*>((const float*)buf + (size_t)c * ch.ld) + lane;
-#pragma unroll
-                    for (int jj = 0; jj < RPW / 2; ++jj) {
-                        const float2 v = col[32 * jj];
-                        acc_fma(acc[0][2 * jj], v.x, zv[0]);
-                        acc_fma(acc[0][2 * jj + 1], v.y, zv[0]);
-                    }
-                }
-                continue;
-            }
             if (ch.kind == 0) {
                 const float* col = (const float*)buf + (size_t)c * ch.ld + rbase + lane;
 #pragma unroll

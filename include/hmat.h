@@ -16,8 +16,8 @@
  *     diagonal of E is negative.
  *   - Pointers named *_dev are CUDA device pointers owned by the caller and not
  *     retained after the call returns; every other pointer is host memory, also
- *     caller-owned and copied if needed.  Handles (hm_tree, hm_hmat, hm_batch,
- *     hm_lp) are owned by the library and freed by their destroy function.
+ *     caller-owned and copied if needed.  Handles (hm_tree, hm_hmat, hm_lp) are
+ *     owned by the library and freed by their destroy function.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous on that stream unless stated otherwise.
  *   - Every function returns an hm_status; 0 is success, a negative value an error

@@ -397,13 +397,8 @@ void lp_upload_samples(LPModel& M, cudaStream_t st) {
     if (S == 0) fail(HM_EINVAL, "learned correction: no training samples");
     M.X.upload(M.X_h, st);
     M.Q.upload(M.Q_h, st);
-    int H = M.H;
-    M.act.alloc((size_t)S * (4 * H + LP_OUT));
-    const int64_t nchunk = ceil_div(S, SAMPLE_CHUNK);
-    M.part.alloc(0);
-    M.loss_part.alloc(0);
+    M.act.alloc((size_t)S * (4 * M.H + LP_OUT));
     M.samples_dirty = false;
-    (void)nchunk;
 }
 
 // loss and gradient at the current parameters (gradient left in M.grad / M.gsum)

@@ -40,7 +40,7 @@ struct LPModel {
     bool dev_ready = false;
     bool samples_dirty = true;
     DevBuf<float> theta, m, v, grad;
-    DevBuf<float> X, Q, act, part, loss_part;
+    DevBuf<float> X, Q, act;  // samples and per-sample activations / deltas
     DevBuf<double> gsum;
 };
 

@@ -43,7 +43,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_ranks_share_the_slowest_time():
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)

@@ -167,6 +167,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         L.begin = (int32_t)T.begin[q];
         L.n = (int32_t)(T.end[q] - T.begin[q]);
         L.ld = (int32_t)round_up(3 * L.n, 8);
+        L.ld16 = bf16_ld(L.ld);
     }
     // leaves under each node (a contiguous ordinal range)
     const int64_t nn = (int64_t)T.begin.size();
@@ -439,13 +440,20 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     }
 
     // ---- U and V streams
-    std::vector<PackJob> ujobs, vjobs;
+    // (the BF16 streams hold the same slices with their own padding, bf16_ld)
+    std::vector<PackJob> ujobs, vjobs, ujobs16, vjobs16;
     std::vector<int32_t> u_zidx, v_pidx;
     H.h_poff.assign(std::max<int64_t>(poff_len, 1), 0);
-    int64_t u_len = 0, v_len = 0;
+    int64_t u_len = 0, v_len = 0, u_len16 = 0, v_len16 = 0;
+    auto as16 = [](PackJob J, int64_t base16, int cols, int ld16) {
+        J.dst = base16 + (int64_t)cols * ld16;
+        J.dst_ld = ld16;
+        return J;
+    };
     for (int l = 0; l < nl; ++l) {
         LeafDesc& L = H.h_leaves[l];
         L.u_off = u_len;
+        L.u_off16 = u_len16;
         L.u_cbase = (int32_t)u_zidx.size();
         int ucols = 0;
         for (int64_t b : far_by_row[l]) {
@@ -458,13 +466,16 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
             J.dst_ld = L.ld;
             J.ncols = F.rank;
             ujobs.push_back(J);
+            ujobs16.push_back(as16(J, u_len16, ucols, L.ld16));
             for (int c = 0; c < F.rank; ++c) u_zidx.push_back((int32_t)(F.tb_off + c));
             ucols += F.rank;
         }
         L.u_cols = ucols;
         u_len += (int64_t)ucols * L.ld;
+        u_len16 += (int64_t)ucols * L.ld16;
 
         L.v_off = v_len;
+        L.v_off16 = v_len16;
         L.v_cbase = (int32_t)v_pidx.size();
         int vcols = 0;
         for (int64_t b : far_by_col[l]) {
@@ -479,6 +490,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
             J.dst_ld = L.ld;
             J.ncols = F.rank;
             vjobs.push_back(J);
+            vjobs16.push_back(as16(J, v_len16, vcols, L.ld16));
             const int32_t start = (int32_t)v_pidx.size();  // partials in V-stream order
             H.h_poff[F.pbase + k] = start;
             for (int c = 0; c < F.rank; ++c) v_pidx.push_back(start + c);
@@ -486,6 +498,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         }
         L.v_cols = vcols;
         v_len += (int64_t)vcols * L.ld;
+        v_len16 += (int64_t)vcols * L.ld16;
     }
     const bool want32 = has_factors(H, 0), want16 = has_factors(H, 1);
     if (want32) {
@@ -495,20 +508,25 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         HM_CUDA(cudaMemsetAsync(H.v32.p, 0, H.v32.bytes(), st));
     }
     if (want16) {
-        H.u16.alloc(std::max<int64_t>(u_len, 1));
-        H.v16.alloc(std::max<int64_t>(v_len, 1));
+        H.u16.alloc(std::max<int64_t>(u_len16, 1));
+        H.v16.alloc(std::max<int64_t>(v_len16, 1));
         HM_CUDA(cudaMemsetAsync(H.u16.p, 0, H.u16.bytes(), st));
         HM_CUDA(cudaMemsetAsync(H.v16.p, 0, H.v16.bytes(), st));
     }
     for (int pass = 0; pass < 2; ++pass) {
         const std::vector<PackJob>& pj = pass == 0 ? ujobs : vjobs;
+        const std::vector<PackJob>& pj16 = pass == 0 ? ujobs16 : vjobs16;
         if (pj.empty()) continue;
-        DevBuf<PackJob> d_p;
-        d_p.upload(pj, st);
-        if (want32)
+        DevBuf<PackJob> d_p, d_p16;
+        if (want32) {
+            d_p.upload(pj, st);
             k_pack<float><<<(unsigned)pj.size(), 256, 0, st>>>(H.facstore.p, d_p.p, pass == 0 ? H.u32.p : H.v32.p);
-        if (want16)
-            k_pack<uint16_t><<<(unsigned)pj.size(), 256, 0, st>>>(H.facstore.p, d_p.p, pass == 0 ? H.u16.p : H.v16.p);
+        }
+        if (want16) {
+            d_p16.upload(pj16, st);
+            k_pack<uint16_t><<<(unsigned)pj16.size(), 256, 0, st>>>(H.facstore.p, d_p16.p,
+                                                                     pass == 0 ? H.u16.p : H.v16.p);
+        }
         HM_LAUNCH_CHECK();
         HM_CUDA(cudaStreamSynchronize(st));
     }

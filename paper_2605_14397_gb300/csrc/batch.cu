@@ -56,7 +56,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         M.eps = std::max(M.eps, h->eps);
     }
 
-    int64_t pos = 0, near_b = 0, u_b = 0, v_b = 0, tb_b = 0, p_b = 0, fac_b = 0, po_b = 0;
+    int64_t pos = 0, near_b = 0, u_b = 0, v_b = 0, u16_b = 0, v16_b = 0, tb_b = 0, p_b = 0, fac_b = 0, po_b = 0;
     int32_t nz_b = 0, uz_b = 0, vp_b = 0;
     M.h_leaves.clear();
     M.h_far.clear();
@@ -86,6 +86,8 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
             L.near_off += near_b;
             L.u_off += u_b;
             L.v_off += v_b;
+            L.u_off16 += u16_b;
+            L.v_off16 += v16_b;
             L.near_cbase += nz_b;
             L.u_cbase += uz_b;
             L.v_cbase += vp_b;
@@ -107,8 +109,10 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         po_b += (int64_t)h->h_poff.size();
         pos += h->N;
         near_b += (int64_t)h->near.n;
-        u_b += (int64_t)std::max(h->u32.n, h->u16.n);
-        v_b += (int64_t)std::max(h->v32.n, h->v16.n);
+        u_b += (int64_t)h->u32.n;
+        v_b += (int64_t)h->v32.n;
+        u16_b += (int64_t)h->u16.n;
+        v16_b += (int64_t)h->v16.n;
         tb_b += h->tb_len;
         p_b += h->p_len;
         fac_b += (int64_t)h->facstore.n;
@@ -126,14 +130,6 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
     M.n_leaves = (int)M.h_leaves.size();
     M.tb_len = tb_b;
     M.p_len = p_b;
-    // every stream of every part has the same length whichever precision it is kept in
-    auto check_len = [&](const DevBuf<float>& a, const DevBuf<uint16_t>& b) {
-        if (a.n && b.n && a.n != b.n) fail(HM_EINVAL, "batch: inconsistent factor streams");
-    };
-    for (const HMat* h : hs) {
-        check_len(h->u32, h->u16);
-        check_len(h->v32, h->v16);
-    }
     M.rank_min = 1 << 30;
     M.rank_max = 0;
     double rsum = 0.0;

@@ -30,15 +30,23 @@ namespace hm {
 struct LeafDesc {
     int32_t begin;     // first cluster position
     int32_t n;         // elements
-    int32_t ld;        // padded rows (3 n rounded up to 8)
-    int32_t pad_;
+    int32_t ld;        // padded rows of the FP32 streams (3 n rounded up to 8)
+    int32_t ld16;      // padded rows of the BF16 streams (see bf16_ld)
     int64_t near_off;  // entry offset into the near stream
-    int64_t u_off;     // entry offset into the U stream
-    int64_t v_off;     // entry offset into the V stream
+    int64_t u_off;     // entry offset into the U stream (FP32)
+    int64_t v_off;     // entry offset into the V stream (FP32)
     int32_t near_cols, u_cols, v_cols;
     int32_t near_cbase, u_cbase, v_cbase;  // first index into the host zidx / pidx arrays
     int32_t pad2_;
+    int64_t u_off16, v_off16;  // entry offsets into the BF16 U and V streams
 };
+
+// Padded rows of a BF16 stream slice: a multiple of 8 whose 16-byte line count is odd.
+// The tensor-core kernels read eight slice columns at once (ldmatrix, one 16-byte line
+// per column); with an odd number of lines per column those eight lines fall into eight
+// different shared-memory bank groups, where a stride of a multiple of 128 bytes (192
+// rows) would put all eight into one.
+inline int32_t bf16_ld(int32_t ld) { return (ld / 8) % 2 == 1 ? ld : ld + 8; }
 
 struct FarDesc {
     int32_t s_begin, s_n, t_begin, t_n;  // clusters (positions, element counts)

@@ -39,6 +39,9 @@ constexpr int STAGES = 4;
 constexpr int STAGE_BYTES = 32768;   // coefficients of one chunk
 constexpr int MAX_CHUNK_COLS = 128;
 constexpr int BAR_BYTES = 128;
+// zeroed bytes after phase 1's ring: a single-RHS column read of up to 32 * 12 rows of
+// 4 bytes that starts in the last stage ends inside them
+constexpr int P1_TAIL = 2048;
 constexpr int VEC_SLACK = 32;        // elements after xc / tb so rounded-up copies stay inside
 
 struct FF {
@@ -185,6 +188,35 @@ __device__ __forceinline__ void load_z(Z64 (&z)[NR], const float2* p, int nr) {
 __device__ __forceinline__ float coef(const float* p, int i) { return p[i]; }
 __device__ __forceinline__ float coef(const uint16_t* p, int i) { return __uint_as_float(((uint32_t)p[i]) << 16); }
 
+// ---- tensor-core helpers (mma.sync m16n8k16 BF16 x BF16 -> FP32, ldmatrix fragments)
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// round to nearest even BF16 bits
+__device__ __forceinline__ uint32_t bf16_bits(float v) {
+    const uint32_t u = __float_as_uint(v);
+    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_value(uint32_t b) { return __uint_as_float(b << 16); }
+
 // Programmatic dependent launch: the kernels of a product after the gather are launched
 // so that they may start while their predecessor drains; each waits for it (and its
 // memory) with griddepcontrol.wait before touching what it produced, and lets its own
@@ -232,6 +264,12 @@ __global__ void k_scatter(const V* __restrict__ yc, V* __restrict__ y, const int
 
 __device__ __forceinline__ float to_zin(float v, float*) { return v; }
 __device__ __forceinline__ float2 to_zin(double v, float2*) { return split_d(v); }
+// BF16 high part in the low 16 bits, BF16 of the remainder in the high 16 bits: the B
+// operand of the single-RHS tensor-core phase 2
+__device__ __forceinline__ uint32_t to_zin(float v, uint32_t*) {
+    const uint32_t hb = bf16_bits(v);
+    return hb | (bf16_bits(v - bf16_value(hb)) << 16);
+}
 
 // tb[(tb_off + l) nr + k] = sum_q P[(poff[pbase + q] + l) nr + k], one CTA (128 threads)
 // (VEC4: FP32 with nr a multiple of 4, each slice read as float4)
@@ -409,8 +447,20 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int n
 // ---- phase 2: y = [D | U] z per row leaf
 // RS > 1 splits each column's rows over RS warps (RPL / RS rows per lane each), so that
 // many right-hand sides fit in registers with more warps in flight.
+//
+// BF16 U slices with one RHS (TC2) run on tensor cores: A = the slice (rows x columns,
+// column-major in shared memory, so ldmatrix.trans gives the row-major fragments), B
+// column 0 = the BF16 high part of t, column 1 the low part (the reduction stores t in
+// that packed form), so d(col 0) + d(col 1) = U t for 16 rows.  Warp w = (kg, mg) takes
+// the k-tiles kg, kg + 4 of each slice and keeps m-tiles mg, mg + 4, mg + 8 of the leaf
+// in registers; at the flush each warp adds them to its own row of the reduction buffer.
 template <int MODE, class C, int NR, int RPL, int NCW, int RS>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
+    constexpr bool TC2 = MODE == 0 && NR == 1 && RS == 1 && NCW == 16 && RPL == 6 &&
+                         std::is_same<C, uint16_t>::value;
+    constexpr int TKG = 4, TMG = 4, TMT = 3;  // k-groups x m-groups = NCW; m-tiles per warp
+    static_assert(!TC2 || (TKG * TMG == NCW && TMG * TMT * 16 >= 32 * RPL && TKG * 2 * 16 >= MAX_CHUNK_COLS),
+                  "tensor-core phase 2 covers every row and column");
     using Acc = typename AccT<MODE>::type;
     using Vv = typename AccT<MODE>::vec;
     using ZR = ZRange<Vv, NR>;
@@ -419,6 +469,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     uint64_t* full = (uint64_t*)smem;
     uint64_t* empty = full + STAGES;
     int* s_flag = (int*)(empty + STAGES);
+    uint16_t* zline = (uint16_t*)(smem + 96);  // a zeroed 16-byte line (ldmatrix rows outside a slice)
+    static_assert(2 * STAGES * 8 + 4 <= 96 && 96 + 16 <= BAR_BYTES, "barrier area layout");
     unsigned char* stage = smem + BAR_BYTES;
     constexpr int RPW = RPL / RS;  // rows per lane of one warp
     constexpr int NG = NCW / RS;   // column groups
@@ -427,6 +479,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < 8) zline[threadIdx.x] = 0;
     init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
     pdl_trigger();
@@ -442,6 +495,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     Vv* slots = (Vv*)a.slots;
     const int g = w / RS, rbase = (w % RS) * 32 * RPW;
     Acc acc[NR][RPW];
+    float dt[TMT][4];  // TC2: this warp's m-tiles of the leaf (tensor-core part)
     int cur = -1;
     LeafDesc L{};
 
@@ -456,6 +510,18 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
             if (k >= a.nr) break;
 #pragma unroll
             for (int i = 0; i < RPW; ++i) red[(size_t)g * (32 * RPL) + rbase + lane + 32 * i] = acc[k][i];
+            if constexpr (TC2) {
+                // lanes 4 c hold rows 16 mt + c (d0 + d1) and 16 mt + c + 8 (d2 + d3)
+                __syncwarp();
+                if ((lane & 3) == 0) {
+#pragma unroll
+                    for (int j = 0; j < TMT; ++j) {
+                        Acc* rw = red + (size_t)g * (32 * RPL) + (w % TMG + TMG * j) * 16 + (lane >> 2);
+                        rw[0] += dt[j][0] + dt[j][1];
+                        rw[8] += dt[j][2] + dt[j][3];
+                    }
+                }
+            }
             consumer_sync(NCW * 32);
             for (int r = threadIdx.x; r < rows; r += NCW * 32) {
                 Acc s = red[r];
@@ -503,6 +569,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
             for (int k = 0; k < NR; ++k)
 #pragma unroll
                 for (int j = 0; j < RPW; ++j) acc_zero(acc[k][j]);
+#pragma unroll
+            for (int j = 0; j < TMT; ++j) dt[j][0] = dt[j][1] = dt[j][2] = dt[j][3] = 0.f;
         }
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
         const unsigned char* stg = stage + (size_t)s * STRIDE;
@@ -511,6 +579,44 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const Zin* zb = (const Zin*)stg + (z0 - (z0 & ~(int64_t)(ZR::ALIGN - 1)));
         const unsigned char* buf = stg + ZR::BYTES;
         const int rows = 3 * L.n;
+        if constexpr (TC2) {
+            if (ch.kind != 0) {
+                const uint32_t* zw = (const uint32_t*)zb;  // packed (hi, lo) of t per column
+                const uint16_t* ub = (const uint16_t*)buf;
+                const int ld = ch.ld, ncols = ch.ncols;
+                const int kg = w / TMG, mg = w % TMG, n = lane >> 2;
+                const int j8 = lane >> 3, i8 = lane & 7;
+                const uint32_t sel = n == 0 ? 0x5410u : 0x7632u;
+                const uint32_t zaddr = smem_u32(zline);
+#pragma unroll
+                for (int tk = 0; tk < 2; ++tk) {
+                    const int kt = kg + TKG * tk;
+                    if (kt * 16 >= ncols) break;
+                    // B: rows k0 + 2 (lane % 4) + {0, 1} and the same + 8; column n
+                    uint32_t b[2];
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int k0 = kt * 16 + hh * 8 + 2 * (lane & 3);
+                        const uint32_t w0 = k0 < ncols ? zw[k0] : 0u;
+                        const uint32_t w1 = k0 + 1 < ncols ? zw[k0 + 1] : 0u;
+                        b[hh] = n < 2 ? __byte_perm(w0, w1, sel) : 0u;
+                    }
+                    // A: this lane supplies the address of slice column kt*16 + (j8/2)*8 + i8
+                    const int kc = kt * 16 + (j8 >> 1) * 8 + i8;
+#pragma unroll
+                    for (int j = 0; j < TMT; ++j) {
+                        const int m0 = (mg + TMG * j) * 16 + (j8 & 1) * 8;
+                        const uint32_t addr = (kc < ncols && m0 < ld) ? smem_u32(ub + (size_t)kc * ld + m0) : zaddr;
+                        uint32_t a0, a1, a2, a3;
+                        ldsm_x4_t(addr, a0, a1, a2, a3);
+                        mma_bf16(dt[j], a0, a1, a2, a3, b[0], b[1]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty + s);
+                continue;
+            }
+        }
         // Rows at or beyond `rows` read whatever follows the column in shared memory (the
         // next column, stage or the reduction buffer: always inside the allocation); their
         // accumulators are never flushed, so no bound check is needed per coefficient.
@@ -556,6 +662,16 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (NR == 1) {
+        // The single-RHS loop reads whole 32 RPL-row columns without bound checks: rows past
+        // a leaf meet x = 0, columns past a chunk are clamped to its last one.  Every byte
+        // such a read can reach (the ring and the tail after it) must then be finite, so the
+        // ring is zeroed once before the first copy lands in it.
+        uint4* z = reinterpret_cast<uint4*>(stage);
+        for (int i = threadIdx.x; i < (STAGES * STAGE_BYTES + P1_TAIL) / 16; i += blockDim.x)
+            z[i] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // before the copies write it
+    }
     init_ring(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
     pdl_trigger();
@@ -598,37 +714,31 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
             // Four columns (w, w + NCW, w + 2 NCW, w + 3 NCW) per pass: their four warp sums
             // share one reduce-scatter (6 shuffles instead of 20) and the loads of four
             // columns are in flight together.
+            // (no per-coefficient bound checks: see the ring zeroing at the kernel start)
             constexpr int CG = 4;
             for (int c = w; c < ch.ncols; c += CG * NCW) {
                 Acc acc[CG];
+                const C* colp[CG];
 #pragma unroll
-                for (int j = 0; j < CG; ++j) acc_zero(acc[j]);
+                for (int j = 0; j < CG; ++j) {
+                    acc_zero(acc[j]);
+                    colp[j] = buf + (size_t)min(c + j * NCW, ch.ncols - 1) * ch.ld;
+                }
                 if constexpr (PAIR) {
 #pragma unroll
                     for (int jj = 0; jj < RPL / 2; ++jj) {
-                        const int r0 = 2 * lane + 64 * jj;
 #pragma unroll
                         for (int j = 0; j < CG; ++j) {
-                            const int cj = c + j * NCW;
-                            uint32_t wv = 0u;
-                            if (r0 < rows && cj < ch.ncols)
-                                wv = reinterpret_cast<const uint32_t*>(buf + (size_t)cj * ch.ld)[lane + 32 * jj];
-                            const float v0 = __uint_as_float(wv << 16);
-                            const float v1 = r0 + 1 < rows ? __uint_as_float(wv & 0xffff0000u) : 0.f;
-                            acc_fma(acc[j], v0, xr[0][2 * jj]);
-                            acc_fma(acc[j], v1, xr[0][2 * jj + 1]);
+                            const uint32_t wv = reinterpret_cast<const uint32_t*>(colp[j])[lane + 32 * jj];
+                            acc_fma(acc[j], __uint_as_float(wv << 16), xr[0][2 * jj]);
+                            acc_fma(acc[j], __uint_as_float(wv & 0xffff0000u), xr[0][2 * jj + 1]);
                         }
                     }
                 } else {
 #pragma unroll
                     for (int ii = 0; ii < RPL; ++ii) {
-                        const int r = lane + 32 * ii;
 #pragma unroll
-                        for (int j = 0; j < CG; ++j) {
-                            const int cj = c + j * NCW;
-                            const float v = (r < rows && cj < ch.ncols) ? coef(buf + (size_t)cj * ch.ld, r) : 0.f;
-                            acc_fma(acc[j], v, xr[0][ii]);
-                        }
+                        for (int j = 0; j < CG; ++j) acc_fma(acc[j], coef(colp[j], lane + 32 * ii), xr[0][ii]);
                     }
                 }
                 const int j = warp_reduce_scatter<CG>(acc, lane);
@@ -668,28 +778,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
 // registers for the whole leaf.  Warp w takes n-tile w % 2 (8 RHS) and m-tiles
 // w / 2, w / 2 + NCW / 2, ...; a lane whose ldmatrix row lies outside the chunk reads a
 // zeroed 16-byte line instead, so no access leaves the chunk.
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// round to nearest even BF16 bits
-__device__ __forceinline__ uint32_t bf16_bits(float v) {
-    const uint32_t u = __float_as_uint(v);
-    return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
-}
-__device__ __forceinline__ float bf16_value(uint32_t b) { return __uint_as_float(b << 16); }
-
 constexpr int TC_KT = 12;  // k-tiles of 16 rows: leaves of up to 192 rows
 
 template <int NCW>
@@ -836,9 +924,15 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     constexpr int NCW = ncw1_for<MODE>(NR), NCW2 = ncw2_for<MODE>(NR), RS = rs_for(NR);
     using Acc = typename AccT<MODE>::type;
     using V = typename AccT<MODE>::vec;
-    const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES;
+    const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES + P1_TAIL;
     // BF16 factors with 16 RHS on leaves of up to 192 rows: phase 1 on tensor cores
     constexpr bool kTensorPhase1 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
+    // BF16 factors with one RHS: the U slices of phase 2 on tensor cores, which read t in
+    // packed BF16 (hi, lo) form (phase 1 stays on the CUDA cores: one mma.sync per 16 x 16
+    // tile did not keep up with the stream there)
+    constexpr bool kTensorPhase2x1 = MODE == 0 && NR == 1 && std::is_same<C, uint16_t>::value && RPL == 6;
+    static_assert(!kTensorPhase2x1 || (ncw2_for<MODE>(NR) == 16 && rs_for(NR) == 1),
+                  "the single-RHS tensor-core phase 2 assumes 16 consumer warps without row split");
     const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
                          (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc);
     // shared-memory opt-in, once per device for each instantiation
@@ -868,8 +962,13 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
         using Zt = typename AccT<MODE>::zin;
-        // several FP32 RHS in multiples of 4: the float4 variant (nrhs 1 keeps the scalar one)
-        if (MODE == 0 && (base.nr & 3) == 0)
+        // several FP32 RHS in multiples of 4: the float4 variant (nrhs 1 keeps the scalar one);
+        // BF16 factors with one RHS: t packed as BF16 (hi, lo) for the tensor-core phase 2
+        if constexpr (kTensorPhase2x1)
+            launch_pdl(k_reduce_tb<V, uint32_t, false>, dim3((unsigned)H.n_far), dim3(128), 0, st,
+                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (uint32_t*)base.tb,
+                       base.nr, base.skip);
+        else if (MODE == 0 && (base.nr & 3) == 0)
             launch_pdl(k_reduce_tb<V, Zt, MODE == 0>, dim3((unsigned)H.n_far), dim3(128), 0, st,
                        (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
                        base.skip);
@@ -1011,8 +1110,10 @@ void build_plan_for(HMat& H, HMat::Plan& PLAN, int esz, int G, cudaStream_t st) 
     for (int l = 0; l < nl; ++l) {
         const LeafDesc& L = H.h_leaves[l];
         cut(c2, b2, l, 0, L.near_off, H.h_near_zidx, L.near_cbase, L.near_cols, L.ld, 4);
-        cut(c2, b2, l, 1, L.u_off, H.h_u_zidx, L.u_cbase, L.u_cols, L.ld, esz);
-        cut(c1, b1, l, 2, L.v_off, H.h_v_pidx, L.v_cbase, L.v_cols, L.ld, esz);
+        // the BF16 streams have their own offsets and padding (bf16_ld)
+        const bool b16 = esz == 2;
+        cut(c2, b2, l, 1, b16 ? L.u_off16 : L.u_off, H.h_u_zidx, L.u_cbase, L.u_cols, b16 ? L.ld16 : L.ld, esz);
+        cut(c1, b1, l, 2, b16 ? L.v_off16 : L.v_off, H.h_v_pidx, L.v_cbase, L.v_cols, b16 ? L.ld16 : L.ld, esz);
     }
     std::vector<int32_t> cta1, cta2;
     split_ranges(b1, cta1);

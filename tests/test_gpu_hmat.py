@@ -124,6 +124,24 @@ def test_bf16_factors_error_is_stated(dev):
     print("BF16 factors: relative error %.2e" % e)
 
 
+@pytest.mark.parametrize("name,mk,leaf", [("penny40", lambda: synth.config_penny(40), 64),
+                                          ("planes16", lambda: synth.config_three_planes(16), 32)])
+def test_bf16_single_rhs_tensor_core_phase(dev, name, mk, leaf):
+    """BF16 factors with one RHS apply the U slices of phase 2 on tensor cores (t split
+    into BF16 hi + lo, about 16 bits kept).  The FP32 product agrees with the F64 product
+    of the same stored operator (CUDA cores, compensated) to 2e-5 -- the split, not the
+    BF16 factors, sets this bar -- and with the dense oracle to the BF16 bound."""
+    import torch
+    el = mk()
+    T, H = build_h(el, leaf, 1e-6, "bf16")
+    x = synth.rhs_normal(3 * el.N, 62)
+    y32 = run_mv(dev, H, x, torch.float32)
+    y64 = run_mv(dev, H, x, torch.float64)
+    assert rel(y32, y64) < 2e-5, (name, rel(y32, y64))
+    assert rel(y32, O.dense_matrix(el, E, NU) @ x) < 1e-2
+    print("%s: BF16 FP32 vs F64 product %.2e" % (name, rel(y32, y64)))
+
+
 def test_multi_rhs_equals_columns(dev):
     import torch
     el = synth.config_three_planes(16)

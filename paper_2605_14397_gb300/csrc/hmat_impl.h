@@ -6,8 +6,9 @@
 //   near stream   for leaf s: [ D_st for t in near(s) ]        ld_s x (sum 3|t|) FP32
 //   U stream      for leaf s: [ U_b[s] for b in far, s in S_b ] ld_s x (sum r_b)   FP32|BF16
 //   V stream      for leaf t: [ V_b[t] for b in far, t in T_b ] ld_t x (sum r_b)   FP32|BF16
-// where ld = 3|leaf| rounded up to 8 entries (16 bytes for BF16, 32 for FP32) and the
-// rows of a slice are the leaf's DOFs in cluster order.
+// where ld = 3|leaf| rounded up to 8 entries (the BF16 copies of U and V pad further to an
+// odd number of 16-byte lines, see bf16_ld, and have their own offsets) and the rows of
+// a slice are the leaf's DOFs in cluster order.
 //
 // The product y = E x runs as
 //   gather     xc = x[perm]                       (cluster order, RHS interleaved)
@@ -115,6 +116,10 @@ struct HMat {
     // block's slice in every leaf of its column cluster
     std::vector<int32_t> h_poff;
     DevBuf<int32_t> poff;
+    // single-RHS reduction order: the n_red_big blocks with many leaves of T first (a CTA
+    // each), then the rest (a warp each); blocks without factors are left out
+    DevBuf<int32_t> red_order;
+    int64_t n_red_big = 0, n_red = 0;
 
     // persistent product plans: [0] with the FP32 factors, [1] with the BF16 factors
     int grid = 0;

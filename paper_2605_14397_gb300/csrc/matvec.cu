@@ -364,6 +364,92 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
     }
 }
 
+// The same reduction for one RHS in one launch of 256-thread CTAs over a block order
+// (red_order) that lists the blocks with more than RED_WARP_LEAVES leaves of T first.
+// Each of those gets a CTA: its offset table staged in shared memory, 256 / r groups of
+// threads over the leaves, four partials per thread in flight.  The many small blocks get
+// a warp each, eight per CTA -- four times the blocks in flight of a CTA per block, whose
+// launch was bound by the latency of short load chains rather than by bytes: lanes take
+// the rank entries, one load fetches 32 offset-table entries which shuffles broadcast.
+// Every block sums its partials in a fixed order.
+constexpr int RED_WARP_LEAVES = 32;
+template <class V, class Zt>
+__global__ void __launch_bounds__(256) k_reduce_mix(const FarDesc* __restrict__ far,
+                                                    const int32_t* __restrict__ poff,
+                                                    const int32_t* __restrict__ order, int64_t n_big, int64_t n_all,
+                                                    const V* __restrict__ P, Zt* __restrict__ tb,
+                                                    const int* __restrict__ skip) {
+    __shared__ V sp[256];
+    constexpr int SPO = 2048;
+    __shared__ int32_t spo[SPO];
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *(volatile const int*)skip) return;
+    if ((int64_t)blockIdx.x < n_big) {
+        const FarDesc F = far[order[blockIdx.x]];
+        const int r = F.rank, nt = F.n_tleaves;  // r <= 256 (rank cap)
+        const int32_t* po = poff + F.pbase;
+        if (nt <= SPO) {
+            for (int q = threadIdx.x; q < nt; q += 256) spo[q] = po[q];
+            __syncthreads();
+            po = spo;
+        }
+        const int G = 256 / r;
+        const int e = threadIdx.x % r, g = threadIdx.x / r;
+        V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        if (g < G) {
+            int q = g;
+            for (; q + 3 * G < nt; q += 4 * G) {
+                s0 += P[(int64_t)po[q] + e];
+                s1 += P[(int64_t)po[q + G] + e];
+                s2 += P[(int64_t)po[q + 2 * G] + e];
+                s3 += P[(int64_t)po[q + 3 * G] + e];
+            }
+            for (; q < nt; q += G) s0 += P[(int64_t)po[q] + e];
+        }
+        sp[threadIdx.x] = (s0 + s1) + (s2 + s3);
+        __syncthreads();
+        if (threadIdx.x < r) {
+            V s = 0;
+            for (int q = 0; q < G; ++q) s += sp[q * r + threadIdx.x];
+            tb[F.tb_off + threadIdx.x] = to_zin(s, tb);
+        }
+        return;
+    }
+    const int64_t k = n_big + ((int64_t)blockIdx.x - n_big) * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= n_all) return;
+    const int64_t b = order[k];
+    const int r = far[b].rank, nt = far[b].n_tleaves;
+    const int32_t* po = poff + far[b].pbase;
+    const int64_t out = far[b].tb_off;
+    for (int e0 = 0; e0 < r; e0 += 32) {
+        const int e = e0 + lane;
+        const bool on = e < r;
+        V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int q0 = 0; q0 < nt; q0 += 32) {
+            const int m = min(32, nt - q0);
+            const int32_t mine = lane < m ? po[q0 + lane] : 0;
+            int q = 0;
+            for (; q + 3 < m; q += 4) {
+                const int32_t o0 = __shfl_sync(0xffffffffu, mine, q), o1 = __shfl_sync(0xffffffffu, mine, q + 1);
+                const int32_t o2 = __shfl_sync(0xffffffffu, mine, q + 2), o3 = __shfl_sync(0xffffffffu, mine, q + 3);
+                if (on) {
+                    s0 += P[(int64_t)o0 + e];
+                    s1 += P[(int64_t)o1 + e];
+                    s2 += P[(int64_t)o2 + e];
+                    s3 += P[(int64_t)o3 + e];
+                }
+            }
+            for (; q < m; ++q) {
+                const int32_t o0 = __shfl_sync(0xffffffffu, mine, q);
+                if (on) s0 += P[(int64_t)o0 + e];
+            }
+        }
+        if (on) tb[out + e] = to_zin((s0 + s1) + (s2 + s3), tb);
+    }
+}
+
 struct StreamArgs {
     const Chunk* chunks;
     const int32_t* cta_begin;
@@ -964,10 +1050,16 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         using Zt = typename AccT<MODE>::zin;
         // several FP32 RHS in multiples of 4: the float4 variant (nrhs 1 keeps the scalar one);
         // BF16 factors with one RHS: t packed as BF16 (hi, lo) for the tensor-core phase 2
+        // one RHS: big blocks a CTA each, the others a warp each (red_order)
+        const unsigned gm = (unsigned)std::max<int64_t>(1, H.n_red_big + (H.n_red - H.n_red_big + 7) / 8);
         if constexpr (kTensorPhase2x1)
-            launch_pdl(k_reduce_tb<V, uint32_t, false>, dim3((unsigned)H.n_far), dim3(128), 0, st,
-                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (uint32_t*)base.tb,
-                       base.nr, base.skip);
+            launch_pdl(k_reduce_mix<V, uint32_t>, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
+                       (const int32_t*)H.poff.p, (const int32_t*)H.red_order.p, H.n_red_big, H.n_red,
+                       (const V*)a.out, (uint32_t*)base.tb, base.skip);
+        else if (base.nr == 1)
+            launch_pdl(k_reduce_mix<V, Zt>, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
+                       (const int32_t*)H.poff.p, (const int32_t*)H.red_order.p, H.n_red_big, H.n_red,
+                       (const V*)a.out, (Zt*)base.tb, base.skip);
         else if (MODE == 0 && (base.nr & 3) == 0)
             launch_pdl(k_reduce_tb<V, Zt, MODE == 0>, dim3((unsigned)H.n_far), dim3(128), 0, st,
                        (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
@@ -1060,6 +1152,19 @@ void build_product_plan(HMat& H, cudaStream_t st) {
         if (has_factors(H, fac)) build_plan_for(H, H.plan[fac], fac == 1 ? 2 : 4, G, st);
     H.counters.alloc(H.n_leaves);
     HM_CUDA(cudaMemsetAsync(H.counters.p, 0, H.counters.bytes(), st));
+    // single-RHS reduction order: blocks with many leaves of T first, factorless ones out
+    std::vector<int32_t> big, small;
+    for (int64_t b = 0; b < H.n_far; ++b) {
+        const FarDesc& F = H.h_far[b];
+        if (F.rank <= 0) continue;
+        if (F.rank > 256) fail(HM_EINVAL, "product plan: rank above 256");
+        (F.n_tleaves > RED_WARP_LEAVES ? big : small).push_back((int32_t)b);
+    }
+    H.n_red_big = (int64_t)big.size();
+    H.n_red = H.n_red_big + (int64_t)small.size();
+    big.insert(big.end(), small.begin(), small.end());
+    if (big.empty()) big.push_back(0);
+    H.red_order.upload(big, st);
     H.err.alloc(1);
     HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
 }

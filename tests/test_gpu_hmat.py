@@ -142,6 +142,41 @@ def test_bf16_single_rhs_tensor_core_phase(dev, name, mk, leaf):
     print("%s: BF16 FP32 vs F64 product %.2e" % (name, rel(y32, y64)))
 
 
+def test_factor_stream_layouts(dev):
+    """FP32 factor streams pad each leaf slice to a multiple of 8 rows; the BF16 copies pad
+    further to an odd number of 16-byte lines (8 more rows where the FP32 stride has an even
+    count), with their own offsets.  The stored bytes of an FP32 and of a BF16 H-matrix of
+    one tree then leave the same near-field bytes once the factor entries of both layouts,
+    counted here from the leaves and the block ranks, are taken off."""
+    el = synth.config_three_planes(16)
+    T = hmat.ClusterTree(el, 32, 2.0)
+    H32 = hmat.HMatrix(T, el, E, NU, 1e-6, "f32")
+    H16 = hmat.HMatrix(T, el, E, NU, 1e-6, "bf16")
+    ex = T.export()
+    begin, end, left = ex["begin"], ex["end"], ex["left"]
+    leaves = [q for q in range(len(left)) if left[q] < 0]
+    ld = {q: -(-3 * (end[q] - begin[q]) // 8) * 8 for q in leaves}
+    ld16 = {q: ld[q] if (ld[q] // 8) % 2 == 1 else ld[q] + 8 for q in leaves}
+    assert all((v // 8) % 2 == 1 and v % 8 == 0 for v in ld16.values())
+
+    def padded_rows(node, table):
+        return sum(table[q] for q in leaves if begin[node] <= begin[q] < end[node])
+
+    def factor_entries(H, table):
+        tot = 0
+        for b, (s, t) in enumerate(ex["far"]):
+            r = H.far_factors(b)
+            if r > 0:
+                tot += r * (padded_rows(s, table) + padded_rows(t, table))
+        return tot
+
+    for H in (H32, H16):
+        assert H.info()["n_far_refined"] == 0
+    near32 = H32.info()["stored_bytes"] - 4 * factor_entries(H32, ld)
+    near16 = H16.info()["stored_bytes"] - 2 * factor_entries(H16, ld16)
+    assert near32 == near16 and near32 > 0
+
+
 def test_multi_rhs_equals_columns(dev):
     import torch
     el = synth.config_three_planes(16)

@@ -477,14 +477,23 @@ struct ZRange {
 };
 
 // ---- producer: one thread streams this CTA's chunks (and their operands) through the ring
-template <class C, class V, int NR, bool WITH_Z>
+// (WAIT_T: wait for the preceding kernel -- the reduction producing t -- only before the
+// first chunk whose operand is t; near tiles read x, complete before that kernel began)
+template <class C, class V, int NR, bool WITH_Z, bool WAIT_T = false>
 __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem_stage, int stage_stride,
                                         uint64_t* full, uint64_t* empty, int c0, int c1) {
     using ZR = ZRange<V, NR>;
+    bool waited = false;
     Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
     for (int i = c0; i < c1; ++i) {
         const Chunk ch = nxt;
         if (i + 1 < c1) nxt = a.chunks[i + 1];
+        if constexpr (WAIT_T) {
+            if (!waited && ch.kind != 0) {
+                pdl_wait();
+                waited = true;
+            }
+        }
         const int q = i - c0, s = q % STAGES;
         const uint32_t ph = (uint32_t)(q / STAGES) & 1u;
         if (q >= STAGES) mbar_wait(empty + s, ph ^ 1u, a.err, 4);
@@ -512,6 +521,9 @@ __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem
             mbar_arrive_expect_tx(full + s, bytes);
             bulk_g2s(stg, src, bytes, full + s);
         }
+    }
+    if constexpr (WAIT_T) {
+        if (!waited) pdl_wait();
     }
     // no copy may still be in flight when the CTA exits
     const int n = c1 - c0;
@@ -570,11 +582,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
     pdl_trigger();
     if (w == NCW) {
-        // the operand ranges (t) come from the reduction: wait for it before the first copy
-        if (lane == 0) {
-            pdl_wait();
-            produce<C, Vv, NR, true>(a, stage, STRIDE, full, empty, c0, c1);
-        }
+        // the t operand ranges come from the reduction: the producer waits for it before the
+        // first U chunk, so the near tiles ahead of it stream while the reduction runs
+        if (lane == 0) produce<C, Vv, NR, true, true>(a, stage, STRIDE, full, empty, c0, c1);
         return;
     }
     Vv* yc = (Vv*)a.out;

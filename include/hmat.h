@@ -191,8 +191,9 @@ hm_status hm_matvec(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, 
 
 /* hm_matvec with the factor precision chosen: factors HM_F32 or HM_BF16 (it must be
  * stored: storage HM_F32_BF16 keeps both), or 0 for the default of hm_matvec (FP32 when
- * stored).  With BF16 factors and 16 right-hand sides the V^T x contraction runs on the
- * tensor cores (BF16 x BF16 -> FP32, x split into BF16 hi + lo). */
+ * stored).  With BF16 factors and FP32 vectors, the V^T x contraction of 16 right-hand
+ * sides and the U t contraction of one right-hand side run on the tensor cores
+ * (BF16 x BF16 -> FP32, the vector split into BF16 hi + lo: about 16 bits of it kept). */
 hm_status hm_matvec_factors(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, int dtype, int factors,
                             void* stream);
 

@@ -1,0 +1,147 @@
+"""Oracle of the sparse approximation of the mechanical block and of its incomplete-LU
+preconditioner (Sec. 3.3.1).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, never by the product path; it shares no
+code with the CUDA library.
+
+Sec. 3.3.1 replaces A11 = E + C^ep, for preconditioning, by a sparse matrix: the
+consistent tangent C^ep (block diagonal) plus the fraction p (0 < p <= 1, 0.01 by
+default) of the entries of the full-rank (near-field) blocks of the hierarchical E that
+have the largest absolute value; the inverse of that sparse matrix is applied through an
+incomplete LU factorization.  Readings taken where the paper is silent:
+  * C^ep is -diag(k) (- shift), the tangent A = E - diag(k) - shift I of this build;
+  * the near-field entries are those of the inadmissible leaf pairs of the block
+    partition (eta), whatever the compression later does with the admissible blocks;
+  * the selection is global over all near-field entries: the ceil(p n) largest in
+    absolute value, ties broken by (row, column) in cluster DOF order, so it is unique;
+  * the diagonal always belongs to the pattern (it carries -k even where E's own
+    diagonal entry was not selected), so the factorization has its pivots in place;
+  * the incomplete factorization is ILU(0) on that pattern -- no fill, no pivoting --
+    with the DOFs in cluster order (the order of the near-field blocks).
+Plain FP64 Python over dictionaries of rows: for the small cases of the tests.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import oracle as O
+
+
+def cluster_dofs(tree):
+    """DOF indices in cluster order (position -> user DOF)."""
+    return O.dof_index(tree.perm)
+
+
+def near_entries(Emat, tree, eta=2.0):
+    """Every entry of the near (inadmissible leaf-pair) blocks of the dense E, numbered in
+    cluster DOF order: arrays (i, j, v)."""
+    cd = cluster_dofs(tree)
+    pos = np.empty(cd.size, dtype=np.int64)
+    pos[cd] = np.arange(cd.size)
+    near, _ = O.block_partition(tree, eta)
+    I, J, V = [], [], []
+    for s, t in near:
+        rs = O.dof_index(tree.perm[tree.begin[s]:tree.end[s]])
+        rt = O.dof_index(tree.perm[tree.begin[t]:tree.end[t]])
+        blk = Emat[np.ix_(rs, rt)]
+        ii, jj = np.meshgrid(pos[rs], pos[rt], indexing="ij")
+        I.append(ii.ravel())
+        J.append(jj.ravel())
+        V.append(blk.ravel())
+    return np.concatenate(I), np.concatenate(J), np.concatenate(V)
+
+
+def select_largest(i, j, v, p):
+    """The ceil(p n) entries of largest |v|, ties by (i, j) ascending; returned in that
+    order."""
+    if not (0.0 < p <= 1.0):
+        raise ValueError("p must lie in (0, 1]")
+    m = int(math.ceil(p * v.size))
+    order = np.lexsort((j, i, -np.abs(v)))[:m]
+    return i[order], j[order], v[order]
+
+
+def sparse_tangent(Emat, tree, k=None, p=0.01, eta=2.0, shift=0.0):
+    """The sparse approximation of A = E - diag(k) - shift I in cluster DOF order, as a
+    list of rows {column: value}; k per element (on its 3 DOFs) or per DOF."""
+    n = Emat.shape[0]
+    i, j, v = select_largest(*near_entries(Emat, tree, eta), p)
+    rows = [dict() for _ in range(n)]
+    for a, b, x in zip(i.tolist(), j.tolist(), v.tolist()):
+        rows[a][b] = x
+    d = np.full(n, float(shift))
+    if k is not None:
+        k = np.asarray(k, dtype=np.float64)
+        kd = np.repeat(k, 3) if k.size * 3 == n else k
+        d += kd[cluster_dofs(tree)]
+    for a in range(n):
+        rows[a][a] = rows[a].get(a, 0.0) - d[a]
+    return rows
+
+
+def to_dense(rows):
+    n = len(rows)
+    M = np.zeros((n, n))
+    for a, r in enumerate(rows):
+        for b, x in r.items():
+            M[a, b] = x
+    return M
+
+
+def ilu0(rows):
+    """ILU(0): L unit lower and U upper triangular, both confined to the pattern of the
+    matrix, with (L U)_ab = A_ab at every (a, b) of the pattern.  Row by row: each entry
+    left of the diagonal becomes a multiplier l_ab = a_ab / u_bb, and row b of U times
+    that multiplier is taken off the entries of row a that lie in the pattern; products
+    falling outside the pattern are dropped.  Returns (L, U) as rows (L without its unit
+    diagonal)."""
+    n = len(rows)
+    W = [dict(r) for r in rows]
+    for a in range(n):
+        if a not in W[a]:
+            raise ValueError("ILU(0): the diagonal is not in the pattern")
+    for a in range(n):
+        ra = W[a]
+        for b in sorted(c for c in ra if c < a):
+            ub = W[b][b]
+            if ub == 0.0:
+                raise ZeroDivisionError("ILU(0): zero pivot")
+            lab = ra[b] / ub
+            ra[b] = lab
+            for c, x in W[b].items():
+                if c > b and c in ra:
+                    ra[c] -= lab * x
+    L = [{c: x for c, x in W[a].items() if c < a} for a in range(n)]
+    U = [{c: x for c, x in W[a].items() if c >= a} for a in range(n)]
+    return L, U
+
+
+def ilu0_solve(L, U, r):
+    """z = (L U)^-1 r: forward substitution with the unit lower factor, then backward
+    substitution with the upper one."""
+    n = len(L)
+    y = np.array(r, dtype=np.float64)
+    for a in range(n):
+        y[a] -= sum(x * y[c] for c, x in L[a].items())
+    z = y.copy()
+    for a in range(n - 1, -1, -1):
+        z[a] = (z[a] - sum(x * z[c] for c, x in U[a].items() if c > a)) / U[a][a]
+    return z
+
+
+def ilu_preconditioner(Emat, tree, k=None, p=0.01, eta=2.0, shift=0.0):
+    """M^-1 for vectors in user DOF order: permute to cluster order, apply (L U)^-1 of
+    the sparse approximation, permute back.  Returns (apply, nnz of the pattern)."""
+    rows = sparse_tangent(Emat, tree, k, p, eta, shift)
+    L, U = ilu0(rows)
+    cd = cluster_dofs(tree)
+    nnz = sum(len(r) for r in rows)
+
+    def apply(r):
+        z = np.empty_like(r)
+        z[cd] = ilu0_solve(L, U, r[cd])
+        return z
+
+    return apply, nnz

@@ -5,7 +5,9 @@ is the exact LU factorization, on a tridiagonal matrix (no fill) too; on any pat
 selection of the largest near-field entries against brute force, ties included; the
 near-field entries against the dense E block by block; with every block near and p = 1
 the sparse approximation is the tangent itself and preconditioned GMRES takes one
-iteration."""
+iteration, in either factorization order.  The leaf-colour order: a proper colouring
+within the greedy bound, a permutation grouped by colour and leaf, a solve no deeper
+than the colours times the deepest single leaf."""
 import math
 
 import numpy as np
@@ -158,3 +160,69 @@ def test_preconditioner_converges_on_a_tangent_system():
     x, its, conv, _ = O.gmres(lambda u: A @ u, b, M, tol=1e-8)
     assert conv and np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
     assert 10 * its < its0
+
+
+def _penny_rows(n=24, p=0.01, leaf=16):
+    el = synth.config_penny(n)
+    Em = O.dense_matrix(el, E, NU)
+    T = O.cluster_tree(el, leaf)
+    k = synth.k_loguniform(el.N, 1605, h=2.0 / n)
+    return el, Em, T, k, IL.sparse_tangent(Em, T, k, p=p)
+
+
+def test_leaf_colouring_is_proper_and_order_is_grouped():
+    el, Em, T, k, rows = _penny_rows()
+    leaf = IL.leaf_of_position(T)
+    col = IL.leaf_colours(rows, T)
+    deg = {}
+    for a, r in enumerate(rows):
+        for c in r:
+            if leaf[c] != leaf[a]:
+                assert col[leaf[c]] != col[leaf[a]]
+                deg.setdefault(leaf[a], set()).add(leaf[c])
+                deg.setdefault(leaf[c], set()).add(leaf[a])
+    assert col.max() + 1 <= 1 + max(len(v) for v in deg.values())  # greedy bound
+    order = IL.colour_order(rows, T)
+    assert np.array_equal(np.sort(order), np.arange(len(rows)))
+    cseq = col[leaf[order]]
+    assert np.all(np.diff(cseq) >= 0)  # colour by colour
+    lseq = leaf[order]
+    starts = np.nonzero(np.diff(lseq))[0] + 1
+    assert len(set(lseq[starts])) == len(starts)  # each leaf one contiguous run
+    within = np.diff(order)[np.diff(lseq) == 0]
+    assert np.all(within == 1)  # cluster order inside a leaf
+    # leaves of one colour are not coupled, so the colour order's solve is no deeper
+    # than the colours times the deepest single-leaf solve
+    P = IL.permute_rows(rows, order)
+    leaf_depth = max(IL.solve_depth([{c - lo: x for c, x in rows[a].items() if lo <= c < hi}
+                                     for a in range(lo, hi)])
+                     for lo, hi in [(3 * T.begin[q], 3 * T.end[q]) for q in T.leaves()])
+    assert IL.solve_depth(P) <= (col.max() + 1) * leaf_depth
+
+
+def test_colour_order_factorization_properties():
+    el, Em, T, k, rows = _penny_rows()
+    order = IL.colour_order(rows, T)
+    P = IL.permute_rows(rows, order)
+    L, U = IL.ilu0(P)
+    A = IL.to_dense(P)
+    pat = A != 0.0
+    for a in range(len(P)):
+        pat[a, list(P[a].keys())] = True
+    assert np.allclose(lu_product(L, U)[pat], A[pat], rtol=0, atol=1e-12 * np.abs(A).max())
+    # the permuted pattern is the original one renumbered
+    assert sum(len(r) for r in P) == sum(len(r) for r in rows)
+
+
+def test_colour_order_is_exact_when_everything_is_kept():
+    el = synth.config_penny(8)
+    Em = O.dense_matrix(el, E, NU)
+    T = O.cluster_tree(el, 8)
+    k = synth.k_loguniform(el.N, 7, h=0.25)
+    A = O.tangent_dense(Em, k)
+    M, _ = IL.ilu_preconditioner(Em, T, k, p=1.0, eta=1e-12, ordering="colour")
+    b = synth.rhs_normal(A.shape[0], 10)
+    x, its, conv, _ = O.gmres(lambda u: A @ u, b, M, tol=1e-10)
+    assert conv and its == 1
+    with pytest.raises(ValueError):
+        IL.ilu_preconditioner(Em, T, k, p=1.0, ordering="rcm")

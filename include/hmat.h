@@ -366,6 +366,43 @@ void hm_lp_destroy(hm_lp* lp);
  * bound every wait on their copy pipeline instead of spinning forever. */
 hm_status hm_hmat_check(const hm_hmat* h, void* stream);
 
+/* ---------------------------------------------------------------- ILU building blocks
+ * Sec. 3.3.1 preconditions the mechanical block with an incomplete LU factorization of
+ * C^ep plus the fraction p of the near-field (full-rank block) entries of E with the
+ * largest absolute value.  These host functions are the setup steps of that
+ * preconditioner on plain caller-owned host arrays (nothing is retained; no device is
+ * used).  Sparse matrices are CSR: rowptr[n + 1] (int64), col[rowptr[n]] (int32), columns
+ * strictly increasing within a row, the diagonal present in every row (HM_EINVAL
+ * otherwise). */
+
+/* The ceil(p n) entries (i[q], j[q], v[q]) of largest |v|, ties broken by (i, j)
+ * ascending (a repeated (i, j) by q): their indices q in that order go to idx_out
+ * (capacity ceil(p n)), their count to m_out.  0 < p <= 1 (HM_EINVAL otherwise); a NaN
+ * or Inf value is HM_ENAN. */
+hm_status hm_ilu_select(int64_t n, const int32_t* i, const int32_t* j, const double* v, double p,
+                        int64_t* idx_out, int64_t* m_out);
+
+/* ILU(0) in place: val holds A on entry and, on return, the multipliers of the unit
+ * lower factor below the diagonal and the upper factor on and above it, with
+ * (L U)_rc = A_rc at every (r, c) of the pattern; no fill, no pivoting.  A zero pivot is
+ * HM_EBREAKDOWN (val then partly factored). */
+hm_status hm_ilu0_factor(int32_t n, const int64_t* rowptr, const int32_t* col, double* val);
+
+/* Levels of the two triangular solves with this pattern: lower_out[r] = 0 for a row with
+ * no entry left of the diagonal, else 1 + the largest level of the rows it names there;
+ * upper_out likewise from the bottom with the entries right of the diagonal.  The level
+ * counts go to n_lower_out and n_upper_out.  Any output may be NULL. */
+hm_status hm_ilu_levels(int32_t n, const int64_t* rowptr, const int32_t* col, int32_t* lower_out,
+                        int32_t* upper_out, int32_t* n_lower_out, int32_t* n_upper_out);
+
+/* Greedy colouring of the leaves that the pattern couples: leaf_of[r] in [0, n_leaves)
+ * names the leaf of row r; leaves are taken in order, each gets the smallest colour none
+ * of its already coloured neighbours (leaves coupled to it by an entry, in either
+ * direction) holds.  Listing the rows colour by colour shortens the dependency chains of
+ * the triangular solves.  colour_out[n_leaves]; the colour count to n_colours_out. */
+hm_status hm_ilu_leaf_colours(int32_t n, const int64_t* rowptr, const int32_t* col, const int32_t* leaf_of,
+                              int32_t n_leaves, int32_t* colour_out, int32_t* n_colours_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -127,6 +127,12 @@ SIGNATURES = [
     ("hm_matvec_graph", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_autotune", _I, [ctypes.POINTER(hm_elements), ctypes.POINTER(hm_assemble_opts), ctypes.POINTER(_I), _I,
                          ctypes.POINTER(_D), _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
+    ("hm_ilu_select", _I, [_I64, _VP, _VP, _VP, _D, _VP, ctypes.POINTER(_I64)]),
+    ("hm_ilu0_factor", _I, [ctypes.c_int32, _VP, _VP, _VP]),
+    ("hm_ilu_levels", _I, [ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int32)]),
+    ("hm_ilu_leaf_colours", _I, [ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int32, _VP,
+                                 ctypes.POINTER(ctypes.c_int32)]),
 ]
 
 
@@ -500,3 +506,52 @@ def autotune(el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", leaves=(32, 64, 12
             json.dump(table, f, indent=1)
         os.replace(tmp, cache)
     return res
+
+
+# ---------------------------------------------------------------- ILU building blocks
+def _csr(rowptr, col):
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    return rp, cl, int(rp.size - 1)
+
+
+def ilu_select(i, j, v, p):
+    """Indices of the ceil(p n) entries of largest |v| (ties by (i, j)), in that order."""
+    i = np.ascontiguousarray(i, dtype=np.int32)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.empty(max(int(np.ceil(p * v.size)), 1) if 0.0 < p <= 1.0 else 1, dtype=np.int64)
+    m = ctypes.c_int64()
+    _check(lib().hm_ilu_select(int(v.size), i.ctypes.data, j.ctypes.data, v.ctypes.data, float(p),
+                               out.ctypes.data, ctypes.byref(m)))
+    return out[:m.value]
+
+
+def ilu0_factor(rowptr, col, val):
+    """ILU(0) of a CSR matrix; returns the factored values (L multipliers and U)."""
+    rp, cl, n = _csr(rowptr, col)
+    out = np.array(val, dtype=np.float64, copy=True)
+    _check(lib().hm_ilu0_factor(n, rp.ctypes.data, cl.ctypes.data, out.ctypes.data))
+    return out
+
+
+def ilu_levels(rowptr, col):
+    """(lower levels, upper levels, lower level count, upper level count)."""
+    rp, cl, n = _csr(rowptr, col)
+    lo = np.empty(max(n, 1), dtype=np.int32)
+    up = np.empty(max(n, 1), dtype=np.int32)
+    nl, nu = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().hm_ilu_levels(n, rp.ctypes.data, cl.ctypes.data, lo.ctypes.data, up.ctypes.data,
+                               ctypes.byref(nl), ctypes.byref(nu)))
+    return lo[:n], up[:n], nl.value, nu.value
+
+
+def ilu_leaf_colours(rowptr, col, leaf_of, n_leaves):
+    """(colour of every leaf, colour count)."""
+    rp, cl, n = _csr(rowptr, col)
+    lf = np.ascontiguousarray(leaf_of, dtype=np.int32)
+    out = np.empty(max(int(n_leaves), 1), dtype=np.int32)
+    nc = ctypes.c_int32()
+    _check(lib().hm_ilu_leaf_colours(n, rp.ctypes.data, cl.ctypes.data, lf.ctypes.data, int(n_leaves),
+                                     out.ctypes.data, ctypes.byref(nc)))
+    return out[:int(n_leaves)], nc.value

@@ -382,6 +382,16 @@ hm_status hm_hmat_check(const hm_hmat* h, void* stream);
 hm_status hm_ilu_select(int64_t n, const int32_t* i, const int32_t* j, const double* v, double p,
                         int64_t* idx_out, int64_t* m_out);
 
+/* The sparse approximation as CSR: the m selected entries (i[idx[t]], j[idx[t]],
+ * v[idx[t]]) (positions in [0, n)), minus d[r] on every diagonal (which is always in the
+ * pattern), with the rows and columns renumbered by order (new position -> old position;
+ * NULL: as they are).  Outputs rowptr_out[n + 1], col_out and val_out (capacity m + n,
+ * columns increasing), the entry count to nnz_out.  A position selected twice, an
+ * out-of-range entry or an order that is not a permutation is HM_EINVAL. */
+hm_status hm_ilu_assemble(int32_t n, int64_t m, const int64_t* idx, const int32_t* i, const int32_t* j,
+                          const double* v, const double* d, const int32_t* order, int64_t* rowptr_out,
+                          int32_t* col_out, double* val_out, int64_t* nnz_out);
+
 /* ILU(0) in place: val holds A on entry and, on return, the multipliers of the unit
  * lower factor below the diagonal and the upper factor on and above it, with
  * (L U)_rc = A_rc at every (r, c) of the pattern; no fill, no pivoting.  A zero pivot is

@@ -74,6 +74,58 @@ hm_status hm_ilu_select(int64_t n, const int32_t* i, const int32_t* j, const dou
     HM_API_END
 }
 
+hm_status hm_ilu_assemble(int32_t n, int64_t m, const int64_t* idx, const int32_t* i, const int32_t* j,
+                          const double* v, const double* d, const int32_t* order, int64_t* rowptr_out,
+                          int32_t* col_out, double* val_out, int64_t* nnz_out) {
+    HM_API_BEGIN
+    if (n < 0 || m < 0) hm::fail(HM_EINVAL, "ilu_assemble: negative size");
+    if ((m > 0 && (!idx || !i || !j || !v)) || (n > 0 && (!d || !col_out || !val_out)) || !rowptr_out)
+        hm::fail(HM_EINVAL, "ilu_assemble: NULL array");
+    // new position of every old row (order: new -> old; NULL: identity)
+    std::vector<int32_t> newpos(n);
+    if (order) {
+        std::vector<char> seen(n, 0);
+        for (int32_t q = 0; q < n; ++q) {
+            if (order[q] < 0 || order[q] >= n || seen[order[q]]) hm::fail(HM_EINVAL, "ilu_assemble: order is not a permutation");
+            seen[order[q]] = 1;
+            newpos[order[q]] = q;
+        }
+    } else {
+        std::iota(newpos.begin(), newpos.end(), 0);
+    }
+    // entries per new row: the selected ones, then the diagonal
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
+    for (int64_t t = 0; t < m; ++t) {
+        const int64_t q = idx[t];
+        if (q < 0) hm::fail(HM_EINVAL, "ilu_assemble: negative entry index");
+        if (i[q] < 0 || i[q] >= n || j[q] < 0 || j[q] >= n) hm::fail(HM_EINVAL, "ilu_assemble: entry out of range");
+        rows[newpos[i[q]]].push_back({newpos[j[q]], v[q]});
+    }
+    int64_t nnz = 0;
+    rowptr_out[0] = 0;
+    for (int32_t r = 0; r < n; ++r) {
+        auto& row = rows[r];
+        std::sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (size_t q = 1; q < row.size(); ++q)
+            if (row[q].first == row[q - 1].first) hm::fail(HM_EINVAL, "ilu_assemble: entry selected twice");
+        // -d on the diagonal, which is always in the pattern
+        auto it = std::lower_bound(row.begin(), row.end(), r, [](const auto& a, int32_t c) { return a.first < c; });
+        const double dr = d[order ? order[r] : r];
+        if (it != row.end() && it->first == r)
+            it->second = it->second - dr;
+        else
+            row.insert(it, {r, 0.0 - dr});
+        for (const auto& e : row) {
+            col_out[nnz] = e.first;
+            val_out[nnz] = e.second;
+            ++nnz;
+        }
+        rowptr_out[r + 1] = nnz;
+    }
+    if (nnz_out) *nnz_out = nnz;
+    HM_API_END
+}
+
 hm_status hm_ilu0_factor(int32_t n, const int64_t* rowptr, const int32_t* col, double* val) {
     HM_API_BEGIN
     const std::vector<int64_t> diag = hm::check_csr(n, rowptr, col);

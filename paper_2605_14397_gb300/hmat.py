@@ -128,6 +128,8 @@ SIGNATURES = [
     ("hm_autotune", _I, [ctypes.POINTER(hm_elements), ctypes.POINTER(hm_assemble_opts), ctypes.POINTER(_I), _I,
                          ctypes.POINTER(_D), _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
     ("hm_ilu_select", _I, [_I64, _VP, _VP, _VP, _D, _VP, ctypes.POINTER(_I64)]),
+    ("hm_ilu_assemble", _I, [ctypes.c_int32, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                             ctypes.POINTER(_I64)]),
     ("hm_ilu0_factor", _I, [ctypes.c_int32, _VP, _VP, _VP]),
     ("hm_ilu_levels", _I, [ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32)]),
@@ -525,6 +527,26 @@ def ilu_select(i, j, v, p):
     _check(lib().hm_ilu_select(int(v.size), i.ctypes.data, j.ctypes.data, v.ctypes.data, float(p),
                                out.ctypes.data, ctypes.byref(m)))
     return out[:m.value]
+
+
+def ilu_assemble(n, idx, i, j, v, d, order=None):
+    """CSR (rowptr, col, val) of the selected entries minus d on the diagonal, renumbered
+    by order (new position -> old position) when given."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    i = np.ascontiguousarray(i, dtype=np.int32)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    od = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    rowptr = np.empty(int(n) + 1, dtype=np.int64)
+    cap = max(int(idx.size) + int(n), 1)
+    col = np.empty(cap, dtype=np.int32)
+    val = np.empty(cap, dtype=np.float64)
+    nnz = ctypes.c_int64()
+    _check(lib().hm_ilu_assemble(int(n), int(idx.size), idx.ctypes.data, i.ctypes.data, j.ctypes.data,
+                                 v.ctypes.data, d.ctypes.data, None if od is None else od.ctypes.data,
+                                 rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, ctypes.byref(nnz)))
+    return rowptr, col[:nnz.value], val[:nnz.value]
 
 
 def ilu0_factor(rowptr, col, val):

@@ -1,9 +1,9 @@
 """The library's host building blocks of the ILU preconditioner (hm_ilu_*, Sec. 3.3.1)
 against the oracle (oracle/ilu.py), through the C-ABI, on CPU: the selection of the
-largest near-field entries index for index, ILU(0) of the sparse tangent bit for bit in
-both factorization orders, the levels of the triangular solves against the oracle's
-depth and their defining recurrence, the leaf colouring colour for colour; bad
-arguments return status codes."""
+largest near-field entries index for index, the CSR of the sparse tangent and its
+ILU(0) bit for bit in both factorization orders, the levels of the triangular solves
+against the oracle's depth and their defining recurrence, the leaf colouring colour for
+colour; bad arguments return status codes."""
 import numpy as np
 import pytest
 
@@ -59,12 +59,26 @@ def test_selection_matches_oracle(penny):
 
 @pytest.mark.parametrize("ordering", ["cluster", "colour"])
 @pytest.mark.parametrize("p", [0.01, 0.05])
-def test_ilu0_bit_identical_to_oracle(penny, ordering, p):
+def test_setup_chain_bit_identical_to_oracle(penny, ordering, p):
+    """selection -> CSR assembly (with -k on the diagonal, renumbered) -> ILU(0), all in
+    the library, against the oracle's sparse tangent and ILU(0)."""
     el, Em, T, k = penny
-    rows = IL.sparse_tangent(Em, T, k, p=p)
+    shift = 0.25
+    rows = IL.sparse_tangent(Em, T, k, p=p, shift=shift)
+    i, j, v = IL.near_entries(Em, T)
+    idx = hmat.ilu_select(i, j, v, p)
+    d = np.repeat(k, 3)[IL.cluster_dofs(T)] + shift
+    order = None
     if ordering == "colour":
-        rows = IL.permute_rows(rows, IL.colour_order(rows, T))
-    rowptr, col, val = to_csr(rows)
+        rp0, c0, _ = hmat.ilu_assemble(len(rows), idx, i, j, v, d)
+        leaf = IL.leaf_of_position(T)
+        colours, _ = hmat.ilu_leaf_colours(rp0, c0, leaf, int(leaf.max()) + 1)
+        order = np.lexsort((np.arange(leaf.size), leaf, colours[leaf]))
+        assert np.array_equal(order, IL.colour_order(rows, T))
+        rows = IL.permute_rows(rows, order)
+    rowptr, col, val = hmat.ilu_assemble(len(rows), idx, i, j, v, d, order)
+    ro, co, vo = to_csr(rows)
+    assert np.array_equal(rowptr, ro) and np.array_equal(col, co) and np.array_equal(val, vo)
     lu = hmat.ilu0_factor(rowptr, col, val)
     Lo, Uo = IL.ilu0(rows)
     L, U = factored_rows(rowptr, col, lu, len(rows))
@@ -120,3 +134,14 @@ def test_bad_arguments_return_status():
     with pytest.raises(hmat.HMError) as e:  # leaf out of range
         hmat.ilu_leaf_colours(rp, col_ok, np.array([0, 2], np.int32), 2)
     assert e.value.status == hmat.HM_EINVAL
+    ii = np.array([0, 1, 1], np.int32)
+    jj = np.array([1, 0, 0], np.int32)
+    vv = np.ones(3)
+    with pytest.raises(hmat.HMError) as e:  # the same position twice
+        hmat.ilu_assemble(2, np.array([1, 2]), ii, jj, vv, np.zeros(2))
+    assert e.value.status == hmat.HM_EINVAL
+    with pytest.raises(hmat.HMError) as e:  # not a permutation
+        hmat.ilu_assemble(2, np.array([0]), ii, jj, vv, np.zeros(2), order=np.array([1, 1]))
+    assert e.value.status == hmat.HM_EINVAL
+    rp2, c2, v2 = hmat.ilu_assemble(2, np.array([0, 1]), ii, jj, vv, np.array([3.0, 4.0]))
+    assert rp2.tolist() == [0, 2, 4] and c2.tolist() == [0, 1, 0, 1] and v2.tolist() == [-3.0, 1.0, 1.0, -4.0]

@@ -8,7 +8,10 @@ dropped term, a sign, a transposed frame, a wrong corner sign) breaks at least o
   * point-source far-field asymptotics with O((h/r)^2) error,
   * symmetry and translation invariance on uniform planar grids, rotation invariance,
   * continuity of the stress as a parallel receiver plane approaches the source,
-  * Sneddon's and Segedin's penny-crack solutions with the error falling under refinement.
+  * Sneddon's and Segedin's penny-crack solutions with the error falling under refinement,
+    at the discrete values of the survey's independent coplanar computation,
+  * the matrix-free row product against the stored dense matrix and against the
+    3x3 blocks contracted by numpy (the checker of every full-size product test).
 """
 import math
 
@@ -203,7 +206,10 @@ def _penny_error(n, shear=False):
 def test_sneddon_penny_crack_error_falls_with_refinement():
     errs = [_penny_error(n)[0] for n in (10, 20, 40)]  # doubling keeps the staircase edge similar
     assert errs[0] > errs[1] > errs[2]
-    assert errs[2] < 0.05
+    # n = 40 (N = 1,264) is a deterministic discrete solution: 0.047096, computed
+    # independently from the coplanar closed forms alone; n = 20: 0.0791
+    assert abs(errs[2] - 0.047096) < 1e-6
+    assert abs(errs[1] - 0.0791) < 5e-5
     e40, x = _penny_error(40)
     # the pressurised crack opens and does not slip
     assert np.all(x[:, 2] > 0) and np.abs(x[:, :2]).max() < 1e-12
@@ -212,4 +218,40 @@ def test_sneddon_penny_crack_error_falls_with_refinement():
 def test_segedin_penny_crack_shear_error_falls_with_refinement():
     errs = [_penny_error(n, shear=True)[0] for n in (10, 20, 40)]
     assert errs[0] > errs[1] > errs[2]
-    assert errs[2] < 0.06
+    # the same independent computation: 0.0794 (n = 20), 0.0472 (n = 40)
+    assert abs(errs[1] - 0.0794) < 5e-5
+    assert abs(errs[2] - 0.0472) < 5e-5
+
+
+def _two_plane_mesh():
+    # a crack crossing a fault: E is not symmetric across the two planes
+    return synth.Elements.concat([
+        synth.plane_grid(6, 4, -0.3, 0.3, -0.2, 0.2, (0, 0, 1), plane_id=0),
+        synth.plane_grid(5, 5, -0.25, 0.25, -0.25, 0.25, (1, 0, 0), origin=(0.01, 0.0, 0.013), plane_id=1)])
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("subset", [False, True])
+def test_dense_matvec_rows_equals_stored_dense_product(nrhs, subset):
+    """dense_matvec_rows (matrix free, the checker of the full-size tests and the CPU
+    baseline) against the stored dense matrix and against the 3x3 blocks of every
+    (row, source) pair contracted by numpy: a wrong right-hand-side stride, a sum into
+    the wrong row or a transposed block fails here."""
+    el = _two_plane_mesh()
+    rng = np.random.default_rng(7)
+    A = O.dense_matrix(el, E, NU)
+    assert np.abs(A - A.T).max() > 1e-3 * np.abs(A).max()  # the test needs a non-symmetric E
+    X = rng.normal(size=(nrhs, 3 * el.N))
+    rows = rng.permutation(el.N)[: el.N // 3] if subset else np.arange(el.N)
+    Y = O.dense_matvec_rows(el, E, NU, X[0] if nrhs == 1 else X, rows)
+    Y = np.atleast_2d(Y)
+    assert Y.shape == (nrhs, 3 * rows.size)
+    dofs = (3 * rows[:, None] + np.arange(3)).ravel()
+    ref = (A[dofs] @ X.T).T
+    assert np.abs(Y - ref).max() <= 1e-13 * np.abs(ref).max()
+    # independently: the blocks of every (row, source) pair, contracted in numpy
+    ri = np.repeat(rows, el.N)
+    sj = np.tile(np.arange(el.N), rows.size)
+    B = O.influence_blocks(el, E, NU, ri, sj).reshape(rows.size, el.N, 3, 3)
+    ref2 = np.einsum("rjam,kjm->kra", B, X.reshape(nrhs, el.N, 3)).reshape(nrhs, -1)
+    assert np.abs(Y - ref2).max() <= 1e-13 * np.abs(ref2).max()

@@ -172,26 +172,30 @@ def oracle_rows_rate(el, E, nu, budget_s=15.0, max_rows=None):
 def time_gmres(H, el, dev, torch, reps=3):
     """GMRES time-to-1e-8 on the same fault: (E) x = b, b = uniform shear + Gaussian
     pressure bump, leaf block-Jacobi, restart 50, x0 = 0.  Plain: FP64 Krylov with every
-    product compensated FP64 on the FP32 factors.  Mixed: FP64 refinement of corrections
-    solved with the BF16 factors and FP32 products.  Both stop on the residual of the
-    FP32-factor operator recomputed in compensated FP64 (<= 1e-8 ||b||)."""
+    product compensated FP64 on the FP32 factors.  IR FP32: FP64 refinement of
+    corrections solved with the FP32 factors and FP32 products.  Mixed: the same
+    refinement with the BF16 factors.  All three stop on the residual of the FP32-factor
+    operator recomputed in compensated FP64 (<= 1e-8 ||b||).  The paper's point (3x3)
+    Jacobi preconditioner is timed with the plain solver beside leaf block-Jacobi."""
     from paper_2605_14397_gb300 import synth
     b = torch.from_numpy(synth.rhs_shear_plus_bump(el)).to(dev)
     x = torch.zeros_like(b)
     out = {"tol": 1e-8, "restart": 50, "precond": "leaf block-Jacobi", "rhs": "shear + Gaussian bump"}
-    for mode in ("f64", "mixed"):
+    for key, mode, pc in (("plain_fp64", "f64", "blockj"), ("ir_fp32", "plain32", "blockj"),
+                          ("mixed_bf16_ir", "mixed", "blockj"), ("plain_fp64_point_jacobi", "f64", "jacobi3")):
         times, info = [], None
         for _ in range(reps):
             x.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = H.solve(b, x, mode=mode, tol=1e-8, restart=50, precond="blockj")[0]
+            info = H.solve(b, x, mode=mode, tol=1e-8, restart=50, precond=pc, maxit=3000)[0]
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
-        key = "plain_fp64" if mode == "f64" else "mixed_bf16_ir"
         out[key] = {"seconds": statistics.median(times), "iters": info["iters"], "outer": info["outer"],
                     "relres": info["relres"]}
     out["speedup_mixed_over_plain"] = out["plain_fp64"]["seconds"] / out["mixed_bf16_ir"]["seconds"]
+    out["speedup_ir_fp32_over_plain"] = out["plain_fp64"]["seconds"] / out["ir_fp32"]["seconds"]
+    out["speedup_mixed_over_ir_fp32"] = out["ir_fp32"]["seconds"] / out["mixed_bf16_ir"]["seconds"]
     return out
 
 
@@ -332,13 +336,14 @@ def run_planes(args, dev, torch, hmat, synth):
     res["bf16_1rhs_x16_ms"] = 16 * timeit(lambda: H.matvec(X[0], Y[0], stream, factors="bf16"), args.steps)
     phases = {}
     for nrk, xa, ya in ((16, X, Y), (1, X[0], Y[0])):
-        H.timing(True)
-        for _ in range(5):
-            H.matvec(xa, ya, stream)
-        H.timing(False)
-        ph = H.timing_read()
-        phases["%drhs" % nrk] = {k: ph[k] / max(ph["count"], 1) for k in ("gather", "phase1", "reduce", "phase2",
-                                                                          "scatter")}
+        for fac in ("f32", "bf16"):
+            H.timing(True)
+            for _ in range(5):
+                H.matvec(xa, ya, stream, factors=fac)
+            H.timing(False)
+            ph = H.timing_read()
+            phases["%s_%drhs" % (fac, nrk)] = {k: ph[k] / max(ph["count"], 1)
+                                               for k in ("gather", "phase1", "reduce", "phase2", "scatter")}
     clocks = sampler.stop()
     H.check(stream)
     B1, _, _ = product_bytes(info, "f32")
@@ -506,8 +511,8 @@ def run_reference(args, rank, world):
     """The CPU oracle as the reference arm: dense FP64 rows of E times x, row-sampled."""
     if rank != 0:
         return
-    from __graft_entry__ import build
-    build()
+    from oracle import build as oracle_build
+    oracle_build.build()  # the oracle only: this arm loads nothing of the CUDA library
     from paper_2605_14397_gb300 import synth
     el = synth.config_fault(256)
     import numpy as np
@@ -545,11 +550,26 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+OPERATOR_RECORD = os.path.join(ROOT, "profiles", "operator_fault256.json")
+
+
 def _reference_bytes():
-    # algorithmic bytes of the FP32 H-matrix product of this workload (leaf 64, eta 2,
-    # eps 1e-6), as the GPU arm assembles it; the oracle's throughput is stated in the
-    # same unit so the two lines compare.
-    return 4340841024
+    """Algorithmic bytes of one FP32 H-matrix product of this workload (leaf 64, eta 2,
+    eps 1e-6) as recorded from an assembly by the GPU arm (profiles/operator_fault256.json),
+    so that the oracle's throughput is stated in the same unit."""
+    with open(OPERATOR_RECORD) as f:
+        return int(json.load(f)["algorithmic_bytes_per_product"])
+
+
+def record_operator(info, B, out_dir):
+    """Write the assembled operator's sizes for the reference arm's unit."""
+    rec = {"workload": WORKLOAD, "algorithmic_bytes_per_product": int(B), "stored_bytes": int(info["stored_bytes"]),
+           "near_entries": int(info["near_entries"]), "u_entries": int(info["u_entries"]),
+           "v_entries": int(info["v_entries"]), "rank_mean": info["rank_mean"], "rank_max": info["rank_max"],
+           "recorded": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    os.makedirs(out_dir, exist_ok=True)
+    with open(os.path.join(out_dir, "operator_fault256.json"), "w") as f:
+        json.dump(rec, f, indent=1)
 
 
 def main():
@@ -640,6 +660,25 @@ def main():
                 "phases_ms": {k: ph[k] / cnt for k in ("gather", "phase1", "reduce", "phase2", "scatter")},
                 "phase1_GBs": B1 / t1 / 1e9 if t1 > 0 else None}
 
+    # the compensated product (FP64 vectors, the same FP32 factors): the operator of the
+    # plain FP64 solver, accurate to the ACA tolerance whatever the cancellation in E x
+    x64 = torch.from_numpy(synth.rhs_shear_plus_bump(el)).to(dev)
+    y64 = torch.empty_like(x64)
+    for _ in range(5):
+        H.matvec(x64, y64, stream)
+    k64 = min(args.steps, 500)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k64):
+        H.matvec(x64, y64, stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms64 = e0.elapsed_time(e1) / k64
+    B64 = B + 2 * 4 * info["n_dof"]  # x and y are 8 bytes per entry
+    f64_vectors = {"ms_per_product": ms64, "GBs": B64 / (ms64 * 1e-3) / 1e9, "bytes_per_product": B64,
+                   "frac_of_hbm_peak": B64 / (ms64 * 1e-3) / 1e9 / peaks()[0]}
+
     # end to end through the host-vector entry point
     xh = torch.from_numpy(synth.rhs_shear_plus_bump(el).astype(np.float32)).pin_memory().numpy()
     yh = torch.empty(xh.shape, dtype=torch.float32).pin_memory().numpy()
@@ -669,13 +708,18 @@ def main():
                        "setup_s": t_setup, "assemble_s": info["assemble_seconds"],
                        "rank_mean": info["rank_mean"], "rank_max": info["rank_max"],
                        "bytes_per_product": B, "frac_of_hbm_peak": value / world / hbm},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clocks}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clocks,
+            "f64_vectors_compensated": f64_vectors}
     if gmres is not None:
         line["gmres"] = gmres
     if args.tune:
         line["autotune"] = hmat.autotune(el, E, nu, eps, "f32", leaves=(32, 48, 64, 96, 128), etas=(1.5, 2.0, 3.0),
                                          budget_ms=180000)
 
+    if rank == 0 and args.grid == 256 and args.storage == "f32":
+        out_dir = os.path.join(ROOT, "gpurun_out")
+        if os.path.isdir(out_dir):
+            record_operator(info, B, out_dir)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, dt = oracle_rows_rate(el, E, nu)
         full = el.N / rate

@@ -220,22 +220,28 @@ hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
  * method and a Jacobi preconditioner (Sec. 3.3.1); here: restarted flexible GMRES(m)
  * with right preconditioning, classical Gram-Schmidt applied twice, Givens rotations,
  * all Krylov vectors, dot products and rotations in FP64 on the device, x0 = 0.
- *   precond HM_PRECOND_NONE, HM_PRECOND_BLOCKJ (inverse of every diagonal leaf block of
- *   A, i.e. the point Jacobi of the paper taken per cluster-tree leaf), or
+ *   precond HM_PRECOND_NONE, HM_PRECOND_JACOBI3 (the paper's Jacobi preconditioner:
+ *   the inverse of every element's 3x3 diagonal block of A), HM_PRECOND_BLOCKJ (inverse
+ *   of every diagonal leaf block of A, i.e. that Jacobi taken per cluster-tree leaf), or
  *   HM_PRECOND_LEARNED (block-Jacobi corrected by a trained network, see hm_lp_*).
  *   mode HM_SOLVE_F64: every product with FP32 factors in compensated FP64 ("plain").
  *   mode HM_SOLVE_MIXED: iterative refinement -- the residual b - A x in compensated
  *   FP64 with the FP32 factors, corrections from FGMRES on the BF16-factor operator
  *   with FP32 products to inner_tol (needs storage HM_F32_BF16).
+ *   mode HM_SOLVE_PLAIN32: the same refinement with the corrections on the FP32-factor
+ *   operator (FP32 products): the plain FP32 path, without BF16 factors.
  * Converged when ||b - A x||_2 <= tol ||b||_2, recomputed in compensated FP64 with the
  * FP32 factors.  k_dev: N doubles (per element, user order) or NULL; b_dev, x_dev:
  * nrhs x 3N doubles, user order (x is overwritten); info: nrhs entries.  Synchronises
- * the stream.  Returns HM_ENOCONV if a right-hand side did not converge within maxit. */
+ * the stream.  Returns HM_ENAN (before any iteration) if shift, k or b holds a NaN or
+ * an infinity, HM_ENOCONV if a right-hand side did not converge within maxit. */
 #define HM_PRECOND_NONE 0
 #define HM_PRECOND_BLOCKJ 1
 #define HM_PRECOND_LEARNED 2
+#define HM_PRECOND_JACOBI3 3
 #define HM_SOLVE_F64 1
 #define HM_SOLVE_MIXED 2
+#define HM_SOLVE_PLAIN32 3
 
 typedef struct hm_lp hm_lp;  /* learned block-Jacobi correction (below) */
 
@@ -371,9 +377,9 @@ hm_status hm_hmat_check(const hm_hmat* h, void* stream);
  * C^ep plus the fraction p of the near-field (full-rank block) entries of E with the
  * largest absolute value.  These host functions are the setup steps of that
  * preconditioner on plain caller-owned host arrays (nothing is retained; no device is
- * used).  Sparse matrices are CSR: rowptr[n + 1] (int64), col[rowptr[n]] (int32), columns
- * strictly increasing within a row, the diagonal present in every row (HM_EINVAL
- * otherwise). */
+ * used).  Sparse matrices are CSR: rowptr[n + 1] (int64, rowptr[0] = 0, non-decreasing),
+ * col[rowptr[n]] (int32), columns strictly increasing within a row, the diagonal present
+ * in every row (HM_EINVAL otherwise). */
 
 /* The ceil(p n) entries (i[q], j[q], v[q]) of largest |v|, ties broken by (i, j)
  * ascending (a repeated (i, j) by q): their indices q in that order go to idx_out
@@ -383,14 +389,15 @@ hm_status hm_ilu_select(int64_t n, const int32_t* i, const int32_t* j, const dou
                         int64_t* idx_out, int64_t* m_out);
 
 /* The sparse approximation as CSR: the m selected entries (i[idx[t]], j[idx[t]],
- * v[idx[t]]) (positions in [0, n)), minus d[r] on every diagonal (which is always in the
- * pattern), with the rows and columns renumbered by order (new position -> old position;
- * NULL: as they are).  Outputs rowptr_out[n + 1], col_out and val_out (capacity m + n,
- * columns increasing), the entry count to nnz_out.  A position selected twice, an
- * out-of-range entry or an order that is not a permutation is HM_EINVAL. */
-hm_status hm_ilu_assemble(int32_t n, int64_t m, const int64_t* idx, const int32_t* i, const int32_t* j,
-                          const double* v, const double* d, const int32_t* order, int64_t* rowptr_out,
-                          int32_t* col_out, double* val_out, int64_t* nnz_out);
+ * v[idx[t]]) of an entry list of length n_entries (positions in [0, n)), minus d[r] on
+ * every diagonal (which is always in the pattern), with the rows and columns renumbered
+ * by order (new position -> old position; NULL: as they are).  Outputs rowptr_out[n + 1],
+ * col_out and val_out (capacity m + n, columns increasing), the entry count to nnz_out.
+ * A position selected twice, an index outside [0, n_entries), an out-of-range entry or
+ * an order that is not a permutation is HM_EINVAL. */
+hm_status hm_ilu_assemble(int32_t n, int64_t n_entries, int64_t m, const int64_t* idx, const int32_t* i,
+                          const int32_t* j, const double* v, const double* d, const int32_t* order,
+                          int64_t* rowptr_out, int32_t* col_out, double* val_out, int64_t* nnz_out);
 
 /* ILU(0) in place: val holds A on entry and, on return, the multipliers of the unit
  * lower factor below the diagonal and the upper factor on and above it, with

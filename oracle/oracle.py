@@ -12,7 +12,8 @@ Contents, each following the passage it cites:
     rules are the readings stated in the design notes: longest-axis median bisection,
     min(diam) <= eta dist on vertex boxes),
   * the tangent operator A = E - diag(k) (eq. jac_mech with C^ep = diag(k)),
-  * leaf block-Jacobi (the point-Jacobi of Sec. 3.3.1 taken per leaf),
+  * leaf block-Jacobi (the point-Jacobi of Sec. 3.3.1 taken per leaf) and the 3x3
+    point Jacobi itself,
   * restarted right-preconditioned GMRES(m) with classical Gram-Schmidt applied twice
     (the Krylov solve of the A11 system, Sec. 3.3.1),
   * Sneddon's and Segedin's penny-crack openings (the closed forms used as pins).
@@ -292,6 +293,14 @@ def block_jacobi_inverses(A, tree):
         dofs = dof_index(tree.perm[tree.begin[q]:tree.end[q]])
         inv.append((dofs, np.linalg.inv(A[np.ix_(dofs, dofs)])))
     return inv
+
+
+def point_jacobi_inverses(A):
+    """Explicit inverse of every 3x3 diagonal block of A, one per element: the point
+    Jacobi preconditioner of the A11 system (Sec. 3.3.1), an element's three DOFs
+    (s1, s2, n) taken together."""
+    n = A.shape[0] // 3
+    return [(np.arange(3 * e, 3 * e + 3), np.linalg.inv(A[3 * e:3 * e + 3, 3 * e:3 * e + 3])) for e in range(n)]
 
 
 def apply_block_jacobi(inv, r):

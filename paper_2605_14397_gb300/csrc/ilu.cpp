@@ -33,6 +33,7 @@ std::vector<int64_t> check_csr(int32_t n, const int64_t* rowptr, const int32_t* 
     if (n < 0) fail(HM_EINVAL, "ilu: negative dimension");
     if (n > 0 && (!rowptr || !col)) fail(HM_EINVAL, "ilu: NULL pattern");
     std::vector<int64_t> diag(n, -1);
+    if (n > 0 && rowptr[0] != 0) fail(HM_EINVAL, "ilu: the first row pointer must be 0");
     for (int32_t r = 0; r < n; ++r) {
         if (rowptr[r + 1] < rowptr[r]) fail(HM_EINVAL, "ilu: row pointers decrease");
         for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
@@ -74,11 +75,11 @@ hm_status hm_ilu_select(int64_t n, const int32_t* i, const int32_t* j, const dou
     HM_API_END
 }
 
-hm_status hm_ilu_assemble(int32_t n, int64_t m, const int64_t* idx, const int32_t* i, const int32_t* j,
-                          const double* v, const double* d, const int32_t* order, int64_t* rowptr_out,
-                          int32_t* col_out, double* val_out, int64_t* nnz_out) {
+hm_status hm_ilu_assemble(int32_t n, int64_t n_entries, int64_t m, const int64_t* idx, const int32_t* i,
+                          const int32_t* j, const double* v, const double* d, const int32_t* order,
+                          int64_t* rowptr_out, int32_t* col_out, double* val_out, int64_t* nnz_out) {
     HM_API_BEGIN
-    if (n < 0 || m < 0) hm::fail(HM_EINVAL, "ilu_assemble: negative size");
+    if (n < 0 || m < 0 || n_entries < 0) hm::fail(HM_EINVAL, "ilu_assemble: negative size");
     if ((m > 0 && (!idx || !i || !j || !v)) || (n > 0 && (!d || !col_out || !val_out)) || !rowptr_out)
         hm::fail(HM_EINVAL, "ilu_assemble: NULL array");
     // new position of every old row (order: new -> old; NULL: identity)
@@ -97,7 +98,7 @@ hm_status hm_ilu_assemble(int32_t n, int64_t m, const int64_t* idx, const int32_
     std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
     for (int64_t t = 0; t < m; ++t) {
         const int64_t q = idx[t];
-        if (q < 0) hm::fail(HM_EINVAL, "ilu_assemble: negative entry index");
+        if (q < 0 || q >= n_entries) hm::fail(HM_EINVAL, "ilu_assemble: entry index outside the entry list");
         if (i[q] < 0 || i[q] >= n || j[q] < 0 || j[q] >= n) hm::fail(HM_EINVAL, "ilu_assemble: entry out of range");
         rows[newpos[i[q]]].push_back({newpos[j[q]], v[q]});
     }
@@ -178,14 +179,14 @@ hm_status hm_ilu_leaf_colours(int32_t n, const int64_t* rowptr, const int32_t* c
                               int32_t n_leaves, int32_t* colour_out, int32_t* n_colours_out) {
     HM_API_BEGIN
     if (n < 0 || n_leaves < 0) hm::fail(HM_EINVAL, "ilu_leaf_colours: negative size");
-    if (n > 0 && (!rowptr || !col || !leaf_of)) hm::fail(HM_EINVAL, "ilu_leaf_colours: NULL array");
+    if (n > 0 && !leaf_of) hm::fail(HM_EINVAL, "ilu_leaf_colours: NULL array");
+    hm::check_csr(n, rowptr, col);
     if (n_leaves > 0 && !colour_out) hm::fail(HM_EINVAL, "ilu_leaf_colours: NULL output");
     for (int32_t r = 0; r < n; ++r)
         if (leaf_of[r] < 0 || leaf_of[r] >= n_leaves) hm::fail(HM_EINVAL, "ilu_leaf_colours: leaf out of range");
     std::vector<std::vector<int32_t>> nbr(n_leaves);
     for (int32_t r = 0; r < n; ++r)
         for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
-            if (col[q] < 0 || col[q] >= n) hm::fail(HM_EINVAL, "ilu_leaf_colours: column out of range");
             const int32_t a = leaf_of[r], b = leaf_of[col[q]];
             if (a != b) {
                 nbr[a].push_back(b);

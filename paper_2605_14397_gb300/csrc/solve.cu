@@ -13,9 +13,12 @@
 //   * every kernel of a restart cycle reads a per-RHS `done` flag set by the Givens step
 //     when the residual estimate meets the tolerance, so a cycle of m iterations is
 //     launched without host synchronisation; the host synchronises once per cycle;
+//   * point-Jacobi preconditioner (the paper's): the inverse of every element's 3x3
+//     diagonal block of A;
 //   * mode F64: products with the FP32 factors in compensated FP64 throughout;
 //     mode MIXED: iterative refinement (outer residual in compensated FP64 with the
-//     FP32 factors; corrections by FGMRES on the BF16-factor operator, FP32 products).
+//     FP32 factors; corrections by FGMRES on the BF16-factor operator, FP32 products);
+//     mode PLAIN32: the same refinement with the corrections on the FP32 factors.
 // Vectors are kept in cluster order internally (RHS-major, stride 3N).
 #include <algorithm>
 #include <chrono>
@@ -50,6 +53,14 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // ---------------------------------------------------------------- permutation, diagonal
+
+// flag |= 1 if any of v[0..n) is NaN or infinite
+__global__ void k_nonfinite(const double* __restrict__ v, int64_t n, int* __restrict__ flag) {
+    int bad = 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(v[q]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
 
 __global__ void k_to_cluster(const double* __restrict__ u, double* __restrict__ c, const int32_t* __restrict__ perm,
                              int64_t ndof, int nr) {
@@ -365,6 +376,74 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
     }
 }
 
+// Point Jacobi (the paper's Jacobi preconditioner of the A11 system, Sec. 3.3.1): the
+// inverse of every element's 3x3 diagonal block of A = E - diag(d), read from the leaf's
+// self tile of the FP32 near field.  One CTA per leaf, one thread per element; the 3x3
+// inverse by cofactors in FP64, stored row-major in FP32.
+__global__ void k_j3_build(const LeafDesc* __restrict__ leaves, const int64_t* __restrict__ self_off,
+                           const float* __restrict__ near, const double* __restrict__ d, float* __restrict__ j3,
+                           int* __restrict__ err) {
+    const LeafDesc L = leaves[blockIdx.x];
+    const float* T = near + self_off[blockIdx.x];
+    for (int e = threadIdx.x; e < L.n; e += blockDim.x) {
+        const int64_t p = (int64_t)L.begin + e;
+        double a[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                a[i][j] = (double)T[(int64_t)(3 * e + j) * L.ld + 3 * e + i];
+                if (i == j) a[i][j] -= d[3 * p + i];
+            }
+        const double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+        const double c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+        const double c02 = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+        const double det = a[0][0] * c00 + a[0][1] * c01 + a[0][2] * c02;
+        const double nrm = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]) + fabs(a[0][1]) + fabs(a[1][0]) +
+                           fabs(a[0][2]) + fabs(a[2][0]) + fabs(a[1][2]) + fabs(a[2][1]);
+        if (!(fabs(det) > 1e-30 * nrm * nrm * nrm) || !isfinite(det)) {
+            atomicOr(err, 1);
+            continue;
+        }
+        const double id = 1.0 / det;
+        double inv[3][3];
+        inv[0][0] = c00 * id;
+        inv[1][0] = c01 * id;
+        inv[2][0] = c02 * id;
+        inv[0][1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) * id;
+        inv[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) * id;
+        inv[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) * id;
+        inv[0][2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) * id;
+        inv[1][2] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) * id;
+        inv[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) * id;
+        float* o = j3 + 9 * p;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) o[3 * i + j] = (float)inv[i][j];
+    }
+}
+
+// z = M^-1 v with the 3x3 point-Jacobi inverses (one thread per element and RHS); also
+// the FP32 copy zf (RHS-interleaved)
+__global__ void k_j3_apply(const float* __restrict__ j3, const double* __restrict__ v, double* __restrict__ z,
+                           float* __restrict__ zf, int64_t nel, int64_t ndof, int nr,
+                           const CycleState* __restrict__ cs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nel * nr) return;
+    const int64_t k = q / nel, p = q % nel;
+    if (cs[k].done) return;
+    const double* vk = v + k * ndof + 3 * p;
+    const float* B = j3 + 9 * p;
+    const float v0 = (float)vk[0], v1 = (float)vk[1], v2 = (float)vk[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float s = fmaf(B[3 * i + 2], v2, fmaf(B[3 * i + 1], v1, B[3 * i] * v0));
+        z[k * ndof + 3 * p + i] = s;
+        if (zf) zf[(3 * p + i) * nr + k] = s;
+    }
+}
+
 // interleave a set of FP64 vectors for the product: out[dof * nr + k] = in[k * ndof + dof]
 // F64 product operand: out[dof * nr + k] = (hi, lo) float split of in[k * ndof + dof]
 __global__ void k_interleave_split(const double* __restrict__ in, float2* __restrict__ out, int64_t ndof, int nr) {
@@ -672,7 +751,7 @@ struct SolveWS {
     int nr = 0, m = 0;
     int64_t ndof = 0, vstride = 0;
     DevBuf<double> V, Z, w, r, xc, bc, dc, corr, y64, zi, Hm, cs, sn, g, ylsq, part, h1, h2;
-    DevBuf<float> zf, y32, binv, bjscratch, dsc;
+    DevBuf<float> zf, y32, binv, bjscratch, dsc, j3;
     bool dsc_on = false;  // apply the learned per-leaf scalings after block-Jacobi
     DevBuf<int64_t> binv_off, self_off;
     DevBuf<CycleState> st;
@@ -748,6 +827,7 @@ SolveWS& workspace(HMat& H, int nr, int m, cudaStream_t st) {
     }
     W.binv_len = len;
     W.binv.alloc(std::max<int64_t>(len, 1));
+    W.j3.alloc((size_t)9 * H.N);
     W.binv_off.upload(off, st);
     W.self_off.upload(H.h_self_off, st);
     W.bj_needs_global = glob;
@@ -776,8 +856,11 @@ struct CycleResult {
 
 // One restart cycle of FGMRES on (E - diag d): rhs r (cluster order), solution x updated
 // in place; beta[k] = ||r_k||; tol_abs[k] the target on the residual estimate.
+// preconditioner applied in the Krylov loop
+enum PcKind { PC_NONE = 0, PC_LEAF = 1, PC_POINT = 2 };
+
 CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double* tol_abs, const int* active_h,
-                         int nr, int m, int dtype, int fac, bool precond, cudaStream_t st) {
+                         int nr, int m, int dtype, int fac, PcKind pc, cudaStream_t st) {
     const int64_t n = H.ndof;
     const int nb = nblk_rows(n);
     std::vector<CycleState> cs(nr);
@@ -805,9 +888,13 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
         }
         const double* vj = W.V.p + (int64_t)j * nr * W.vstride;
         double* zj = W.Z.p + (int64_t)j * nr * W.vstride;
-        k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, vj, zj,
-                                               dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p, precond ? 0 : 1,
-                                               W.dsc_on ? W.dsc.p : nullptr);
+        if (pc == PC_POINT)
+            k_j3_apply<<<g1(H.N * nr), 256, 0, st>>>(W.j3.p, vj, zj, dtype == HM_F32 ? W.zf.p : nullptr, H.N, n, nr,
+                                                      W.st.p);
+        else
+            k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, vj, zj,
+                                                   dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p,
+                                                   pc == PC_LEAF ? 0 : 1, W.dsc_on ? W.dsc.p : nullptr);
         HM_LAUNCH_CHECK();
         if (dtype == HM_F64) {
             apply_E(H, W, zj, nullptr, W.y64.p, nr, HM_F64, fac, st, W.alldone.p);
@@ -873,7 +960,7 @@ std::vector<double> residual(HMat& H, SolveWS& W, const double* rhs, int nr, int
 // stops at ||rhs - A x_k|| <= tol_abs[k] or when the iteration budget is spent.
 // Returns per RHS the iterations used and the final residual norm.
 void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& tol_abs, int nr, int m, int max_its,
-            int max_cycles, int dtype, int fac, bool precond, std::vector<int>& its, std::vector<double>& rn,
+            int max_cycles, int dtype, int fac, PcKind pc, std::vector<int>& its, std::vector<double>& rn,
             std::vector<int>& brk, cudaStream_t st) {
     its.assign(nr, 0);
     brk.assign(nr, 0);
@@ -889,7 +976,7 @@ void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& t
         int mm = m;
         for (int k = 0; k < nr; ++k)
             if (active[k]) mm = std::min(mm, std::max(1, max_its - its[k]));
-        CycleResult cr = fgmres_cycle(H, W, rn.data(), tol_abs.data(), active.data(), nr, mm, dtype, fac, precond, st);
+        CycleResult cr = fgmres_cycle(H, W, rn.data(), tol_abs.data(), active.data(), nr, mm, dtype, fac, pc, st);
         for (int k = 0; k < nr; ++k) {
             its[k] += cr.iters[k];
             if (cr.brk[k] && cr.iters[k] == 0) brk[k] = 1;
@@ -934,6 +1021,17 @@ void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
     if (e) fail(HM_EBREAKDOWN, "a diagonal leaf block of A is singular");
 }
 
+// point-Jacobi inverses of the 3x3 diagonal blocks of E - diag(W.dc)
+void j3_build(HMat& H, SolveWS& W, cudaStream_t st) {
+    HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
+    k_j3_build<<<H.n_leaves, 64, 0, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.j3.p, W.err.p);
+    HM_LAUNCH_CHECK();
+    int e = 0;
+    HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (e) fail(HM_EBREAKDOWN, "a 3x3 diagonal block of A is singular");
+}
+
 }  // namespace
 
 void to_cluster(HMat& H, const double* user, double* cluster, int nr, cudaStream_t st) {
@@ -967,22 +1065,39 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     if (m > 128) fail(HM_EINVAL, "gmres_solve: restart must be <= 128");
     const int maxit = o.maxit > 0 ? o.maxit : 2000;
     const int mode = o.mode ? o.mode : HM_SOLVE_F64;
-    if (mode != HM_SOLVE_F64 && mode != HM_SOLVE_MIXED) fail(HM_EINVAL, "gmres_solve: unknown mode");
-    if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ && o.precond != HM_PRECOND_LEARNED)
+    if (mode != HM_SOLVE_F64 && mode != HM_SOLVE_MIXED && mode != HM_SOLVE_PLAIN32)
+        fail(HM_EINVAL, "gmres_solve: unknown mode");
+    if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ && o.precond != HM_PRECOND_LEARNED &&
+        o.precond != HM_PRECOND_JACOBI3)
         fail(HM_EINVAL, "gmres_solve: unknown preconditioner");
     if (o.precond == HM_PRECOND_LEARNED && !lp) fail(HM_EINVAL, "gmres_solve: the learned preconditioner needs a model");
     if (!has_factors(H, 0)) fail(HM_EINVAL, "gmres_solve: the FP32 factors are required (storage F32 or F32_BF16)");
-    const int inner_fac = has_factors(H, 1) ? 1 : 0;
+    // refinement corrections: BF16 factors (mixed; FP32 if BF16 is not stored) or the
+    // FP32 factors themselves (PLAIN32: the same refinement without the BF16 operator)
+    const int inner_fac = mode == HM_SOLVE_PLAIN32 ? 0 : (has_factors(H, 1) ? 1 : 0);
     SolveWS& W = workspace(H, nrhs, m, st);
     const int64_t n = H.ndof;
-    const int nb = nblk_rows(n);
-    (void)nb;
+    // the stiffness and the right-hand sides must be finite (a NaN would silently spread
+    // through every Krylov vector)
+    HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
+    if (kel) k_nonfinite<<<152, 256, 0, st>>>(kel, H.N, W.err.p);
+    k_nonfinite<<<152, 256, 0, st>>>(b, n * nrhs, W.err.p + 0);
+    HM_LAUNCH_CHECK();
+    {
+        int e = 0;
+        HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        if (e) fail(HM_ENAN, "gmres_solve: the stiffness k or the right-hand side holds NaN or Inf");
+    }
     k_diag<<<g1(n), 256, 0, st>>>(kel, shift, H.perm.p, n, W.dc.p);
     k_to_cluster<<<g1(n * nrhs), 256, 0, st>>>(b, W.bc.p, H.perm.p, n, nrhs);
     HM_LAUNCH_CHECK();
-    const bool precond = o.precond == HM_PRECOND_BLOCKJ || o.precond == HM_PRECOND_LEARNED;
+    const PcKind pc = (o.precond == HM_PRECOND_BLOCKJ || o.precond == HM_PRECOND_LEARNED)
+                          ? PC_LEAF
+                          : (o.precond == HM_PRECOND_JACOBI3 ? PC_POINT : PC_NONE);
     W.dsc_on = false;
-    if (precond) {
+    if (pc == PC_POINT) j3_build(H, W, st);
+    if (pc == PC_LEAF) {
         bj_build(H, W, st);
         if (o.precond == HM_PRECOND_LEARNED && !lp->fallback) {
             W.dsc.alloc((size_t)H.n_leaves * 3);
@@ -998,7 +1113,7 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     std::vector<int> its(nrhs, 0), outer(nrhs, 0), brk(nrhs, 0);
     std::vector<double> rn = bn;
     if (mode == HM_SOLVE_F64) {
-        fgmres(H, W, W.bc.p, tol_abs, nrhs, m, maxit, 1 << 20, HM_F64, 0, precond, its, rn, brk, st);
+        fgmres(H, W, W.bc.p, tol_abs, nrhs, m, maxit, 1 << 20, HM_F64, 0, pc, its, rn, brk, st);
         for (int k = 0; k < nrhs; ++k) outer[k] = (its[k] + m - 1) / m;
     } else {
         const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-2;
@@ -1025,7 +1140,7 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
             for (int k = 0; k < nrhs; ++k) itol_abs[k] = rr[k] > tol_abs[k] ? itol * rr[k] : 1e300;
             std::vector<int> iits, ibrk;
             std::vector<double> irn;
-            fgmres(H, W, W.corr.p, itol_abs, nrhs, m, maxit, 4, HM_F32, inner_fac, precond, iits, irn, ibrk, st);
+            fgmres(H, W, W.corr.p, itol_abs, nrhs, m, maxit, 4, HM_F32, inner_fac, pc, iits, irn, ibrk, st);
             for (int k = 0; k < nrhs; ++k) {
                 its[k] += iits[k];
                 if (iits[k] > 0) outer[k]++;

@@ -22,8 +22,8 @@ HM_EBREAKDOWN = -6
 HM_ENAN = -7
 HM_ETIMEOUT = -8
 HM_F32, HM_F64, HM_BF16, HM_F32_BF16 = 1, 2, 3, 4
-HM_PRECOND_NONE, HM_PRECOND_BLOCKJ, HM_PRECOND_LEARNED = 0, 1, 2
-HM_SOLVE_F64, HM_SOLVE_MIXED = 1, 2
+HM_PRECOND_NONE, HM_PRECOND_BLOCKJ, HM_PRECOND_LEARNED, HM_PRECOND_JACOBI3 = 0, 1, 2, 3
+HM_SOLVE_F64, HM_SOLVE_MIXED, HM_SOLVE_PLAIN32 = 1, 2, 3
 
 _STATUS_NAMES = {HM_EINVAL: "HM_EINVAL", HM_ENOMEM: "HM_ENOMEM", HM_ECUDA: "HM_ECUDA",
                  HM_ESINGULAR_GEOM: "HM_ESINGULAR_GEOM", HM_ENOCONV: "HM_ENOCONV",
@@ -128,7 +128,7 @@ SIGNATURES = [
     ("hm_autotune", _I, [ctypes.POINTER(hm_elements), ctypes.POINTER(hm_assemble_opts), ctypes.POINTER(_I), _I,
                          ctypes.POINTER(_D), _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
     ("hm_ilu_select", _I, [_I64, _VP, _VP, _VP, _D, _VP, ctypes.POINTER(_I64)]),
-    ("hm_ilu_assemble", _I, [ctypes.c_int32, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+    ("hm_ilu_assemble", _I, [ctypes.c_int32, _I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                              ctypes.POINTER(_I64)]),
     ("hm_ilu0_factor", _I, [ctypes.c_int32, _VP, _VP, _VP]),
     ("hm_ilu_levels", _I, [ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_int32),
@@ -328,13 +328,16 @@ class HMatrix:
     def solve(self, b, x, k=None, shift=0.0, tol=1e-8, restart=50, maxit=2000, precond="blockj", mode="f64",
               inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None):
         """Solve (E - diag(k) - shift I) x = b on the device (b, x: float64 CUDA tensors of
-        shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None).  Returns the
+        shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None).  precond "none",
+        "jacobi3", "blockj" or "learned"; mode "f64", "mixed" or "plain32".  Returns the
         per-RHS info dicts; raises HMError unless every RHS converged (raise_on_error)."""
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         assert b.is_contiguous() and x.is_contiguous() and (k is None or k.is_contiguous())
         o = hm_solve_opts(float(tol), int(restart), int(maxit),
-                          {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "learned": HM_PRECOND_LEARNED}[precond],
-                          {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED}[mode], float(inner_tol), int(max_outer), 0,
+                          {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "learned": HM_PRECOND_LEARNED,
+                           "jacobi3": HM_PRECOND_JACOBI3}[precond],
+                          {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED, "plain32": HM_SOLVE_PLAIN32}[mode],
+                          float(inner_tol), int(max_outer), 0,
                           model.handle.value if model is not None else None)
         info = (hm_solve_info * nrhs)()
         st = lib().hm_gmres_solve(self.handle, _dptr(k) if k is not None else None, float(shift), _dptr(b), _dptr(x),
@@ -543,7 +546,9 @@ def ilu_assemble(n, idx, i, j, v, d, order=None):
     col = np.empty(cap, dtype=np.int32)
     val = np.empty(cap, dtype=np.float64)
     nnz = ctypes.c_int64()
-    _check(lib().hm_ilu_assemble(int(n), int(idx.size), idx.ctypes.data, i.ctypes.data, j.ctypes.data,
+    if not (i.size == j.size == v.size):
+        raise HMError(HM_EINVAL, "ilu_assemble: i, j and v must have one length")
+    _check(lib().hm_ilu_assemble(int(n), int(v.size), int(idx.size), idx.ctypes.data, i.ctypes.data, j.ctypes.data,
                                  v.ctypes.data, d.ctypes.data, None if od is None else od.ctypes.data,
                                  rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, ctypes.byref(nnz)))
     return rowptr, col[:nnz.value], val[:nnz.value]

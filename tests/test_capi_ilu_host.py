@@ -4,6 +4,8 @@ largest near-field entries index for index, the CSR of the sparse tangent and it
 ILU(0) bit for bit in both factorization orders, the levels of the triangular solves
 against the oracle's depth and their defining recurrence, the leaf colouring colour for
 colour; bad arguments return status codes."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -145,3 +147,34 @@ def test_bad_arguments_return_status():
     assert e.value.status == hmat.HM_EINVAL
     rp2, c2, v2 = hmat.ilu_assemble(2, np.array([0, 1]), ii, jj, vv, np.array([3.0, 4.0]))
     assert rp2.tolist() == [0, 2, 4] and c2.tolist() == [0, 1, 0, 1] and v2.tolist() == [-3.0, 1.0, 1.0, -4.0]
+
+
+def test_bad_entry_index_and_row_pointers_are_rejected():
+    """An index past the entry list, a first row pointer other than 0 and decreasing
+    row pointers return HM_EINVAL from every entry point that reads them."""
+    ii = np.array([0, 1, 1], np.int32)
+    jj = np.array([1, 0, 0], np.int32)
+    vv = np.ones(3)
+    with pytest.raises(hmat.HMError) as e:  # index 3 of a 3-entry list
+        hmat.ilu_assemble(2, np.array([0, 3]), ii, jj, vv, np.zeros(2))
+    assert e.value.status == hmat.HM_EINVAL
+    L = hmat.lib()
+    idx = np.array([0, 2], np.int64)
+    rp = np.empty(3, np.int64)
+    col = np.empty(4, np.int32)
+    val = np.empty(4)
+    nnz = ctypes.c_int64()
+    st = L.hm_ilu_assemble(2, 2, 2, idx.ctypes.data, ii.ctypes.data, jj.ctypes.data, vv.ctypes.data,
+                           np.zeros(2).ctypes.data, None, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                           ctypes.byref(nnz))
+    assert st == hmat.HM_EINVAL  # index 2 with n_entries = 2
+    bad_first = np.array([1, 2, 3], np.int64)  # rowptr[0] != 0
+    c3 = np.array([0, 0, 1], np.int32)
+    leaf = np.array([0, 1], np.int32)
+    for call in (lambda: hmat.ilu0_factor(bad_first, c3, np.ones(3)),
+                 lambda: hmat.ilu_levels(bad_first, c3),
+                 lambda: hmat.ilu_leaf_colours(bad_first, c3, leaf, 2),
+                 lambda: hmat.ilu_leaf_colours(np.array([0, 2, 1], np.int64), c3, leaf, 2)):
+        with pytest.raises(hmat.HMError) as e:
+            call()
+        assert e.value.status == hmat.HM_EINVAL

@@ -139,3 +139,64 @@ def test_full_size_fault_plain_and_mixed(dev):
     assert rel(Ax, b.reshape(-1, 3)[rows].ravel()) < 1e-5
     print("plain: %d its %.3f s; mixed: %d its (%d outer) %.3f s" % (
         ip[0]["iters"], ip[0]["seconds"], im[0]["iters"], im[0]["outer"], im[0]["seconds"]))
+
+
+def test_point_jacobi_matches_lu_and_the_oracle_iterations(dev, penny):
+    """The paper's Jacobi preconditioner (3x3 block per element, Sec. 3.3.1): the solve
+    meets the LU solution, takes the oracle GMRES's iteration count on the dense tangent
+    with the same preconditioner (within 2: FP32 preconditioner, H-matrix operator) and
+    sits between no preconditioner and leaf block-Jacobi."""
+    el, T, H, A = penny
+    rng = np.random.default_rng(21)
+    k = np.exp(rng.uniform(math.log(1e-3), math.log(1e2), size=el.N)) * (E / (2.0 / 40))
+    shift = 0.11
+    b = synth.rhs_normal(3 * el.N, 22)
+    At = O.tangent_dense(A, k, shift)
+    x, info = solve(dev, H, b, k=k, shift=shift, precond="jacobi3")
+    assert info[0]["status"] == 0 and info[0]["relres"] <= 1e-8
+    assert rel(x, np.linalg.solve(At, b)) < 1e-6
+    pj = O.point_jacobi_inverses(At)
+    _, its_o, ok, _ = O.gmres(lambda v: At @ v, b, lambda q: O.apply_block_jacobi(pj, q), tol=1e-8, restart=50)
+    assert ok and abs(info[0]["iters"] - its_o) <= 2, (info[0]["iters"], its_o)
+    _, i_none = solve(dev, H, b, k=k, shift=shift, precond="none")
+    _, i_bj = solve(dev, H, b, k=k, shift=shift, precond="blockj")
+    assert i_bj[0]["iters"] <= info[0]["iters"] < i_none[0]["iters"]
+    print("penny, k log-uniform: iterations none %d, jacobi3 %d (oracle %d), blockj %d" % (
+        i_none[0]["iters"], info[0]["iters"], its_o, i_bj[0]["iters"]))
+
+
+def test_plain32_refinement_mode(dev, penny):
+    """Refinement with the corrections on the FP32-factor operator: reaches 1e-8 on the
+    stored operator and agrees with the plain FP64 and the mixed solves."""
+    el, T, H, A = penny
+    b = synth.rhs_normal(3 * el.N, 23)
+    x32, i32 = solve(dev, H, b, mode="plain32")
+    x64, i64 = solve(dev, H, b, mode="f64")
+    xm, im = solve(dev, H, b, mode="mixed")
+    assert i32[0]["status"] == 0 and i32[0]["relres"] <= 1e-8 and i32[0]["outer"] >= 1
+    assert rel(x32, x64) < 1e-7 and rel(x32, xm) < 1e-7
+    assert rel(x32, np.linalg.solve(A, b)) < 1e-6
+
+
+@pytest.mark.parametrize("where", ["k", "b", "shift"])
+def test_non_finite_input_is_rejected(dev, penny, where):
+    """A NaN or Inf in the stiffness, the right-hand side or the shift returns HM_ENAN
+    before any iteration; the H-matrix stays usable."""
+    import torch
+    el, T, H, A = penny
+    b = torch.as_tensor(synth.rhs_normal(3 * el.N, 24), device=dev)
+    k = torch.ones(el.N, dtype=torch.float64, device=dev)
+    shift = 0.0
+    if where == "k":
+        k[17] = float("nan")
+    elif where == "b":
+        b[5] = float("inf")
+    else:
+        shift = float("nan")
+    x = torch.zeros_like(b)
+    with pytest.raises(hmat.HMError) as ei:
+        H.solve(b, x, k, shift)
+    assert ei.value.status == hmat.HM_ENAN
+    b2 = torch.as_tensor(synth.rhs_normal(3 * el.N, 24), device=dev)
+    info = H.solve(b2, torch.zeros_like(b2), torch.ones(el.N, dtype=torch.float64, device=dev))
+    assert info[0]["status"] == 0

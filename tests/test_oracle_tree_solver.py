@@ -132,3 +132,35 @@ def test_gmres_restart_path():
     x, its, ok, _ = O.gmres(lambda v: A @ v, b, tol=1e-12, restart=5, maxit=500)
     assert ok and its > 5
     assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(b) * 1.0001
+
+
+def test_point_jacobi_is_block_jacobi_on_one_element_leaves(penny):
+    """The 3x3 point Jacobi of every element equals leaf block-Jacobi on a tree whose
+    leaves hold one element each; on a matrix that is block diagonal with 3x3 blocks it
+    is the exact inverse (one GMRES iteration)."""
+    el, E_ = penny
+    rng = np.random.default_rng(4)
+    k = np.exp(rng.uniform(math.log(1e-3), math.log(1e2), size=el.N)) * (E / (2.0 / 40))
+    A = O.tangent_dense(E_, k, 0.1)
+    pj = O.point_jacobi_inverses(A)
+    bj = O.block_jacobi_inverses(A, O.cluster_tree(el, 1))
+    r = rng.normal(size=3 * el.N)
+    z1, z2 = O.apply_block_jacobi(pj, r), O.apply_block_jacobi(bj, r)
+    assert np.abs(z1 - z2).max() <= 1e-12 * np.abs(z1).max()
+    # each block applied separately: B_e z_e = r_e
+    for e in rng.choice(el.N, size=20, replace=False):
+        d = slice(3 * e, 3 * e + 3)
+        assert np.allclose(A[d, d] @ z1[d], r[d], rtol=1e-12, atol=1e-12 * np.abs(r[d]).max())
+    D = np.zeros_like(A)
+    for e in range(el.N):
+        D[3 * e:3 * e + 3, 3 * e:3 * e + 3] = A[3 * e:3 * e + 3, 3 * e:3 * e + 3]
+    b = synth.rhs_normal(3 * el.N, 10)
+    x, its, ok, _ = O.gmres(lambda v: D @ v, b, lambda q: O.apply_block_jacobi(pj, q), tol=1e-10)
+    assert ok and its == 1
+    # on the tangent: between no preconditioner and leaf block-Jacobi
+    T = O.cluster_tree(el, 64)
+    its_none = O.gmres(lambda v: A @ v, b, tol=1e-8)[1]
+    its_pj = O.gmres(lambda v: A @ v, b, lambda q: O.apply_block_jacobi(pj, q), tol=1e-8)[1]
+    its_bj = O.gmres(lambda v: A @ v, b, lambda q: O.apply_block_jacobi(O.block_jacobi_inverses(A, T), q),
+                     tol=1e-8)[1]
+    assert its_bj <= its_pj < its_none

@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--grid", type=int, default=256, help="disk grid size (256: the 51,468-element fault)")
     p.add_argument("--lp-h", type=float, default=0.01, help="element size of the crack + fault (learned workload)")
     p.add_argument("--lp-train", type=int, default=12, help="training systems (learned workload)")
-    p.add_argument("--workload", default="fault", choices=["fault", "faults64", "planes", "learned"],
+    p.add_argument("--workload", default="fault", choices=["fault", "faults64", "planes", "learned", "ilu"],
                    help="fault: the 51,468-element disk fault (default); faults64: 64 independent faults, "
                         "batched product vs per-fault launches; planes: three intersecting 300x300 planes, "
                         "16 right-hand sides")
@@ -346,25 +346,45 @@ def run_planes(args, dev, torch, hmat, synth):
                                                for k in ("gather", "phase1", "reduce", "phase2", "scatter")}
     clocks = sampler.stop()
     H.check(stream)
-    B1, _, _ = product_bytes(info, "f32")
-    coef = B1 - 2 * 4 * nd
-    b16 = coef + nr * 2 * 4 * nd
-    # 2 flops per stored coefficient and right-hand side
-    flops16 = 2.0 * nr * (info["near_entries"] + info["u_entries"] + info["v_entries"])
+    # algorithmic bytes of one 16-RHS product: every stored near entry (4 B) and factor
+    # entry (4 B FP32, 2 B BF16) once, x read and y written once per right-hand side
+    n_coef_near = info["near_entries"]
+    n_fac = info["u_entries"] + info["v_entries"]
+    vec16 = nr * 2 * 4 * nd
+    b16_f32 = 4 * n_coef_near + 4 * n_fac + vec16
+    b16_bf16 = 4 * n_coef_near + 2 * n_fac + vec16
+    # phase 2 of the BF16 product: near tiles + U slices + x and t operands + y
+    ph2_bf16 = 4 * n_coef_near + 2 * info["u_entries"] + nr * 4 * (2 * nd + info["tb_len"])
+    ph1_bf16 = 2 * info["v_entries"] + nr * 4 * (nd + info["p_len"])
+    flops16 = 2.0 * nr * (n_coef_near + n_fac)  # 2 flops per stored coefficient and RHS
     hbm, peak_kind = peaks()
-    t16 = res["f32_16rhs_ms"] * 1e-3
-    line = {"metric": "16-RHS H-matvec GB/s and TFLOP/s; GMRES time-to-1e-8, 16 RHS batched vs sequential",
-            "value": b16 / t16 / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": res["f32_16rhs_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic (seeded mesh and right-hand sides)",
+    t16 = res["bf16_16rhs_ms"] * 1e-3
+    tf = res["f32_16rhs_ms"] * 1e-3
+    pb = phases["bf16_16rhs"]
+    ach = ph2_bf16 / (pb["phase2"] * 1e-3) / 1e9
+    line = {"metric": "16-RHS H-matvec GB/s (BF16 factors, FP32 near field); GMRES time-to-1e-8, 16 RHS batched "
+                      "vs sequential",
+            "value": b16_bf16 / t16 / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["bf16_16rhs_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 factors x bf16 hi+lo vectors on tensor cores, f32 near field and accumulation",
+            "data": "synthetic (seeded mesh and right-hand sides)",
             "config": {"workload": "three intersecting 300x300 planes (third shifted h/4): N=270000, 810000 DOFs, "
                                    "leaf 64, eta 2, ACA eps 1e-5, 16 RHS N(0,1)",
                        "setup_s": t_setup, "rank_mean": info["rank_mean"], "rank_max": info["rank_max"],
-                       "stored_bytes": info["stored_bytes"], "bytes_16rhs": b16},
-            "tflops_16rhs": flops16 / t16 / 1e12, "frac_of_hbm_peak": b16 / t16 / 1e9 / hbm,
-            "peak_source": peak_kind, "ms": res,
-            "speedup_16rhs_over_16x1": res["f32_1rhs_x16_ms"] / res["f32_16rhs_ms"], "clocks": clocks,
-            "phases_ms": phases}
+                       "stored_bytes": info["stored_bytes"], "bytes_16rhs_bf16": b16_bf16,
+                       "bytes_16rhs_f32": b16_f32,
+                       "l2": "operator %.1f GB >> 129 MB L2: no flush" % (b16_bf16 / 1e9)},
+            "frac_of_hbm_peak": b16_bf16 / t16 / 1e9 / hbm, "peak_source": peak_kind,
+            "roofline": {"bound": "hbm", "kernel": "k_phase2 (16 RHS, BF16 U slices on tensor cores)",
+                         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "algorithmic_bytes_per_launch": ph2_bf16, "launch_ms": pb["phase2"],
+                         "phase1_GBs": ph1_bf16 / (pb["phase1"] * 1e-3) / 1e9, "traffic": None},
+            "f32_factors_16rhs": {"ms": res["f32_16rhs_ms"], "GBs": b16_f32 / tf / 1e9,
+                                  "tflops": flops16 / tf / 1e12},
+            "tflops_16rhs_bf16": flops16 / t16 / 1e12, "ms": res,
+            "speedup_16rhs_over_16x1": {"bf16": res["bf16_1rhs_x16_ms"] / res["bf16_16rhs_ms"],
+                                        "f32": res["f32_1rhs_x16_ms"] / res["f32_16rhs_ms"]},
+            "clocks": clocks, "phases_ms": phases}
     if not args.no_gmres:
         # the tangent A = E - diag(k), k log-uniform in [1e-3, 1e2] E/h per element: the bare
         # E of three intersecting planes is indefinite and nearly singular (GMRES with
@@ -484,6 +504,55 @@ def run_learned(args, dev, torch, hmat, synth):
             "data_s": t_data, "train_s": t_train, "validation_iters": val, "fallback": fallback,
             "test": test, "mean_iters": {pc: float(np.mean(test[pc]["iters"])) for pc in test}}
     print(json.dumps(line), flush=True)
+
+
+def run_ilu(args, dev, torch, hmat, synth):
+    """The ILU(0) preconditioner of Sec. 3.3.1 against leaf block-Jacobi and the paper's
+    point Jacobi: GMRES(50) iterations and time to 1e-8 on tangent systems
+    A = E - diag(k), k log-uniform in [1e-3, 1e2] E/h per element (seed 1605), one
+    N(0, 1) right-hand side (seed 1606), x0 = 0, plain FP64 and mixed modes, on the
+    51,468-element fault (eps 1e-6) and the crack crossing a fault (h = 0.01: 200,000
+    elements, eps 1e-6).  The first ILU solve of a fraction p also builds the pattern
+    (reported apart); every solve factors for its k."""
+    import numpy as np
+    out = {"metric": "GMRES time-to-1e-8 on tangent systems: ILU(0) (Sec. 3.3.1) vs leaf block-Jacobi",
+           "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 Krylov; f32 H-matrix, f64 ILU", "data": "synthetic (seeded k, right-hand side)",
+           "cases": {}}
+    for name, el, h in (("fault256", synth.config_fault(256), 2.0 / 256),
+                        ("crackfault_h0.01", synth.config_crack_fault(h=0.01), 0.01)):
+        T = hmat.ClusterTree(el, 64, 2.0)
+        H = hmat.HMatrix(T, el, 1.0, 0.25, 1e-6, "both")
+        k = torch.as_tensor(synth.k_loguniform(el.N, 1605, E=1.0, h=h), device=dev)
+        b = torch.as_tensor(synth.rhs_normal(3 * el.N, 1606), device=dev)
+        res = {"N": el.N}
+        for mode in ("f64", "mixed"):
+            for pc, p in (("blockj", 0.0), ("jacobi3", 0.0), ("ilu", 0.01), ("ilu", 0.05)):
+                key = "%s_%s%s" % (mode, pc, "_p%.2f" % p if pc == "ilu" else "")
+                x = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                inf = H.solve(b, x, k, precond=pc, mode=mode, ilu_p=p, maxit=3000, raise_on_error=False)[0]
+                torch.cuda.synchronize()
+                first = time.perf_counter() - t0
+                times = []
+                for _ in range(3):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    inf = H.solve(b, x, k, precond=pc, mode=mode, ilu_p=p, maxit=3000, raise_on_error=False)[0]
+                    torch.cuda.synchronize()
+                    times.append(time.perf_counter() - t0)
+                res[key] = {"seconds": statistics.median(times), "first_call_s": first, "iters": inf["iters"],
+                            "outer": inf["outer"], "relres": inf["relres"], "status": inf["status"]}
+        for mode in ("f64", "mixed"):
+            bj = res["%s_blockj" % mode]["seconds"]
+            for p in (0.01, 0.05):
+                res["%s_speedup_ilu_p%.2f_over_blockj" % (mode, p)] = bj / res["%s_ilu_p%.2f" % (mode, p)]["seconds"]
+        out["cases"][name] = res
+        del H, T
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
 
 
 def max_over_ranks(dist, value, device):
@@ -607,6 +676,9 @@ def main():
     if args.workload == "learned":
         run_learned(args, dev, torch, hmat, synth)
         return
+    if args.workload == "ilu":
+        run_ilu(args, dev, torch, hmat, synth)
+        return
     el = synth.config_fault(args.grid)
     E, nu, eps = 1.0, 0.25, 1e-6
     t0 = time.perf_counter()
@@ -703,6 +775,8 @@ def main():
             "data": "synthetic (seeded mesh and right-hand side)",
             "config": {"workload": WORKLOAD if args.grid == 256 else "disk fault on %dx%d grid: N=%d" % (
                            args.grid, args.grid, el.N), "nrhs": 1, "storage": args.storage,
+                       "trunc_factor": "library default (30: blocks recompressed to 15 eps relative)",
+                       "stored_bytes": info["stored_bytes"], "ms_per_product": ms,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "operator 4.3 GB >> 129 MB L2: inputs larger than L2, no flush",
                        "setup_s": t_setup, "assemble_s": info["assemble_seconds"],

@@ -130,17 +130,23 @@ void hm_tree_destroy(hm_tree* t);
 /* ---------------------------------------------------------------- H-matrix assembly
  * Assemble the H-matrix of E on the device: dense near-field tiles in FP32 (FP64
  * evaluation), admissible blocks compressed by adaptive cross approximation with
- * element (3-row) pivots to relative Frobenius accuracy aca_eps per block, factors
- * stored in `storage` (HM_F32 or HM_BF16).  max_rank caps the ACA rank (0 = 160, at most 256):
- * a block whose approximation does not converge below the cap is refined into the
- * blocks of its children clusters (a pair of leaves is stored dense instead).
+ * element (3-row) pivots and recompressed in FP64 to relative Frobenius accuracy
+ * trunc_factor * aca_eps per block (0.1 of that for the cross approximation itself),
+ * factors stored in `storage` (HM_F32, HM_BF16 or both).  aca_eps is the accuracy the
+ * product is meant to meet; trunc_factor (0 = HM_TRUNC_DEFAULT) spends that budget per
+ * block: an admissible block carries a small share of any row's sum, so its own
+ * relative error reaches the product attenuated.  max_rank caps the ACA rank (0 = 160,
+ * at most 256): a block whose approximation does not converge below the cap is refined
+ * into the blocks of its children clusters (a pair of leaves is stored dense instead).
  * Synchronises the stream (the packed layout depends on the ranks). */
+#define HM_TRUNC_DEFAULT 30.0
 typedef struct {
     double E;
     double nu;
     double aca_eps;
     int storage;
     int max_rank;
+    double trunc_factor;
 } hm_assemble_opts;
 
 typedef struct hm_hmat hm_hmat;
@@ -223,7 +229,13 @@ hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
  *   precond HM_PRECOND_NONE, HM_PRECOND_JACOBI3 (the paper's Jacobi preconditioner:
  *   the inverse of every element's 3x3 diagonal block of A), HM_PRECOND_BLOCKJ (inverse
  *   of every diagonal leaf block of A, i.e. that Jacobi taken per cluster-tree leaf), or
- *   HM_PRECOND_LEARNED (block-Jacobi corrected by a trained network, see hm_lp_*).
+ *   HM_PRECOND_LEARNED (block-Jacobi corrected by a trained network, see hm_lp_*), or
+ *   HM_PRECOND_ILU: the incomplete-LU preconditioner of Sec. 3.3.1 -- ILU(0) of
+ *   -diag(k) - shift plus the fraction ilu_p of the near-field entries of E (inadmissible
+ *   leaf pairs, FP32 stored values) with the largest magnitude, ties by (row, column) in
+ *   cluster order, the diagonal always in the pattern, rows listed leaf-colour by
+ *   leaf-colour (see hm_ilu_export); factored in FP64 at every call, the pattern kept on
+ *   the H-matrix for later calls with the same ilu_p.
  *   mode HM_SOLVE_F64: every product with FP32 factors in compensated FP64 ("plain").
  *   mode HM_SOLVE_MIXED: iterative refinement -- the residual b - A x in compensated
  *   FP64 with the FP32 factors, corrections from FGMRES on the BF16-factor operator
@@ -239,6 +251,7 @@ hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
 #define HM_PRECOND_BLOCKJ 1
 #define HM_PRECOND_LEARNED 2
 #define HM_PRECOND_JACOBI3 3
+#define HM_PRECOND_ILU 4
 #define HM_SOLVE_F64 1
 #define HM_SOLVE_MIXED 2
 #define HM_SOLVE_PLAIN32 3
@@ -255,6 +268,7 @@ typedef struct {
     int max_outer;     /* mixed: cap on refinement steps (0 = 40) */
     int pad_;
     const hm_lp* lp;   /* model for HM_PRECOND_LEARNED (NULL otherwise) */
+    double ilu_p;      /* HM_PRECOND_ILU: fraction of the near-field entries kept (0 = 0.01) */
 } hm_solve_opts;
 
 typedef struct {
@@ -269,6 +283,20 @@ typedef struct {
 hm_status hm_gmres_solve(const hm_hmat* h, const double* k_dev, double shift, const double* b_dev,
                          double* x_dev, int nrhs, const hm_solve_opts* opt, hm_solve_info* info,
                          void* stream);
+
+/* The ILU preconditioner that hm_gmres_solve builds for A = E - diag(k) - shift I and the
+ * fraction p (Sec. 3.3.1), to host arrays (any may be NULL; pass NULL arrays first to
+ * learn n and nnz).  n_out: 3N; nnz_out: entries of the pattern; n_colours_out: leaf
+ * colours.  order[n]: factorization position -> cluster DOF position (the cluster order
+ * of hm_tree_export: DOF 3 q + c of the element at cluster position q); rowptr[n + 1],
+ * col[nnz]: the pattern in factorization order, columns increasing; a_val[nnz]: the
+ * selected entries of E (the diagonal holds E's entry if selected, else 0), before
+ * -k - shift is added; lu_val[nnz]: ILU(0) of the matrix with -k - shift on the
+ * diagonal (multipliers of the unit lower factor left of the diagonal, the upper factor
+ * on and right of it).  k_dev as in hm_gmres_solve.  Synchronises the stream. */
+hm_status hm_ilu_export(const hm_hmat* h, const double* k_dev, double shift, double p, int64_t* n_out,
+                        int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
+                        double* a_val, double* lu_val, void* stream);
 
 /* ---------------------------------------------------------------- batching
  * Independent faults: the operator of several non-interacting fractures is

@@ -149,8 +149,11 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     H.eps = opt.aca_eps;
     H.storage = opt.storage;
     const double mu = opt.E / (2.0 * (1.0 + opt.nu));
-    const double eps_aca = 0.1 * opt.aca_eps;  // cross approximation target
-    const double tau = 0.5 * opt.aca_eps;      // SVD truncation target
+    const double kappa = opt.trunc_factor > 0.0 ? opt.trunc_factor : HM_TRUNC_DEFAULT;
+    if (!(kappa * opt.aca_eps < 0.5) || !std::isfinite(kappa))
+        fail(HM_EINVAL, "assemble: trunc_factor * aca_eps must stay below 0.5");
+    const double eps_aca = 0.1 * kappa * opt.aca_eps;  // cross approximation target
+    const double tau = 0.5 * kappa * opt.aca_eps;      // SVD truncation target
 
     H.elems.upload(T.elems, st);
     H.h_perm = T.perm;
@@ -347,6 +350,9 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         const int64_t s = T.near[b][0], t = T.near[b][1];
         tiles_by_row[T.leaf_of_node[s]].push_back({(int32_t)T.begin[t], (int32_t)(T.end[t] - T.begin[t])});
     }
+    H.h_near_true_cols.assign(nl, 0);
+    for (int l = 0; l < nl; ++l)
+        for (const DenseTile& D : tiles_by_row[l]) H.h_near_true_cols[l] += 3 * D.t_n;
     int64_t n_dense_far = 0;
     H.n_refined = 0;
     for (int64_t b = 0; b < nf; ++b) {

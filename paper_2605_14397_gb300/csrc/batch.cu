@@ -65,6 +65,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
     M.h_u_zidx.clear();
     M.h_v_pidx.clear();
     M.h_self_off.clear();
+    M.h_near_true_cols.clear();
     M.h_poff.clear();
     M.n_near = M.n_far = M.n_dense_far = M.n_refined = 0;
     M.near_entries = M.far_entries = 0;
@@ -105,6 +106,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         for (int32_t z : h->h_u_zidx) M.h_u_zidx.push_back(z + (int32_t)tb_b);
         for (int32_t z : h->h_v_pidx) M.h_v_pidx.push_back(z + (int32_t)p_b);
         for (int64_t o : h->h_self_off) M.h_self_off.push_back(o < 0 ? o : o + near_b);
+        for (int32_t c : h->h_near_true_cols) M.h_near_true_cols.push_back(c);
         for (int32_t o : h->h_poff) M.h_poff.push_back(o + (int32_t)p_b);
         po_b += (int64_t)h->h_poff.size();
         pos += h->N;

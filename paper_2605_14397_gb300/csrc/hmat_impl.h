@@ -83,6 +83,8 @@ struct LeafSplit {
 
 struct SolveWS;                  // solver workspace (solve.cu)
 void solve_ws_free(SolveWS* w);
+struct IluPlan;                  // ILU(0) preconditioner of the tangent (ilu_dev.cu)
+void ilu_plan_free(IluPlan* p);
 
 struct HMat {
     SolveWS* solve_ws = nullptr;
@@ -134,6 +136,10 @@ struct HMat {
     DevBuf<int32_t> counters;
     DevBuf<int> err;
     std::vector<int64_t> h_self_off;  // near-stream offset of each leaf's diagonal tile
+    // per leaf: the first columns of its near block that belong to inadmissible leaf pairs
+    // (the near field proper; admissible blocks stored dense follow them)
+    std::vector<int32_t> h_near_true_cols;
+    IluPlan* ilu = nullptr;           // ILU preconditioner plan (ilu_dev.cu), built on demand
     DevBuf<float> slotsf;
     DevBuf<double> slotsd;
 
@@ -163,6 +169,7 @@ struct HMat {
         for (GraphEntry& g : graphs) cudaGraphExecDestroy(g.exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         solve_ws_free(solve_ws);
+        ilu_plan_free(ilu);
     }
 
     // product scratch, sized for nrhs_cap right-hand sides
@@ -198,6 +205,9 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M);
 void graphs_clear(HMat& H);
 void matvec_graph(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 struct LPModel;
+void ilu_export_for(HMat& H, const double* kel, double shift, double p, int64_t* n_out, int64_t* nnz_out,
+                    int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col, double* a_val,
+                    double* lu_val, cudaStream_t st);
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp = nullptr);
 inline bool has_factors(const HMat& H, int fac) {

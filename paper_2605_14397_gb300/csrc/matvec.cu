@@ -364,6 +364,67 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
     }
 }
 
+// 16 right-hand sides with BF16 U slices on tensor cores: the same sums as k_reduce_tb
+// (float4 slices, four partials in flight, a fixed order), each value split into BF16
+// hi + lo (hi = bf16(t), lo = bf16(t - hi)) and stored as the B operand of phase 2:
+// 64 bytes per rank entry l, four 16-byte pieces (RHS 0-7 hi, RHS 0-7 lo, RHS 8-15 hi,
+// RHS 8-15 lo), piece q stored at position q ^ ((l >> 1) & 3), so that the eight
+// consecutive entries one ldmatrix row group reads fall into eight different bank groups.
+__device__ __forceinline__ int tb16_piece_pos(int64_t l, int q) { return q ^ (int)((l >> 1) & 3); }
+
+__global__ void __launch_bounds__(128) k_reduce_tb_pack16(const FarDesc* __restrict__ far,
+                                                          const int32_t* __restrict__ poff,
+                                                          const float* __restrict__ P, uint16_t* __restrict__ tb,
+                                                          const int* __restrict__ skip) {
+    constexpr int SPO = 2048;
+    __shared__ int32_t spo[SPO];
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *(volatile const int*)skip) return;
+    const FarDesc F = far[blockIdx.x];
+    const int n4 = F.rank * 4;  // float4 groups: rank entries x 4 groups of 4 RHS
+    if (n4 == 0) return;
+    const int32_t* po = poff + F.pbase;
+    if (F.n_tleaves <= SPO) {
+        for (int q = threadIdx.x; q < F.n_tleaves; q += 128) spo[q] = po[q];
+        __syncthreads();
+        po = spo;
+    }
+    const float4* P4 = reinterpret_cast<const float4*>(P);
+    for (int e = threadIdx.x; e < n4; e += 128) {
+        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+        int q = 0;
+        for (; q + 3 < F.n_tleaves; q += 4) {
+            const float4 v0 = P4[(int64_t)po[q] * 4 + e], v1 = P4[(int64_t)po[q + 1] * 4 + e];
+            const float4 v2 = P4[(int64_t)po[q + 2] * 4 + e], v3 = P4[(int64_t)po[q + 3] * 4 + e];
+            s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+            s1.x += v1.x; s1.y += v1.y; s1.z += v1.z; s1.w += v1.w;
+            s2.x += v2.x; s2.y += v2.y; s2.z += v2.z; s2.w += v2.w;
+            s3.x += v3.x; s3.y += v3.y; s3.z += v3.z; s3.w += v3.w;
+        }
+        for (; q < F.n_tleaves; ++q) {
+            const float4 v0 = P4[(int64_t)po[q] * 4 + e];
+            s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+        }
+        const float t[4] = {(s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
+                            (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w)};
+        uint32_t hb[4], lb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            hb[i] = bf16_bits(t[i]);
+            lb[i] = bf16_bits(t[i] - bf16_value(hb[i]));
+        }
+        const int64_t l = F.tb_off + e / 4;
+        const int k0 = (e & 3) * 4;                  // first of the four RHS
+        const int qh = 2 * (k0 >> 3), off = k0 & 7;  // hi piece of these RHS, offset inside it
+        uint16_t* row = tb + 32 * l;                 // 64 bytes
+        *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh) + off) =
+            make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+        *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh + 1) + off) =
+            make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+    }
+}
+
 // The same reduction for one RHS in one launch of 256-thread CTAs over a block order
 // (red_order) that lists the blocks with more than RED_WARP_LEAVES leaves of T first.
 // Each of those gets a CTA: its offset table staged in shared memory, 256 / r groups of
@@ -556,6 +617,14 @@ template <int MODE, class C, int NR, int RPL, int NCW, int RS>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     constexpr bool TC2 = MODE == 0 && NR == 1 && RS == 1 && NCW == 16 && RPL == 6 &&
                          std::is_same<C, uint16_t>::value;
+    // BF16 U slices with 16 RHS (TC16, when the launch has exactly 16): warp w < 12 owns
+    // m-tile w (rows 16 w .. 16 w + 15 of the leaf) and both n-tiles (RHS 0-7, 8-15); A as
+    // in TC2, B = t in the packed BF16 (hi, lo) form of k_reduce_tb_pack16 read with
+    // ldmatrix.trans, two mma per n-tile and k-tile.  The CUDA-core accumulators keep the
+    // near tiles; the tensor-core results join them at the flush through ty.
+    constexpr bool TC16 = MODE == 0 && NR == 16 && RS == 2 && NCW == 16 && RPL == 6 &&
+                          std::is_same<C, uint16_t>::value;
+    constexpr int TC16_MT = 12, TY_LD = 196;  // m-tiles (192 rows); ty row stride (bank spread)
     constexpr int TKG = 4, TMG = 4, TMT = 3;  // k-groups x m-groups = NCW; m-tiles per warp
     static_assert(!TC2 || (TKG * TMG == NCW && TMG * TMT * 16 >= 32 * RPL && TKG * 2 * 16 >= MAX_CHUNK_COLS),
                   "tensor-core phase 2 covers every row and column");
@@ -574,6 +643,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     constexpr int NG = NCW / RS;   // column groups
     static_assert(RPL % RS == 0 && NCW % RS == 0, "row split must divide rows and warps");
     Acc* red = (Acc*)(stage + (size_t)STAGES * STRIDE);  // [NG][32 RPL]
+    float* ty = (float*)(red + (size_t)NG * 32 * RPL);  // TC16: the leaf's tensor-core sums [16 RHS][TY_LD]
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -592,6 +662,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     const int g = w / RS, rbase = (w % RS) * 32 * RPW;
     Acc acc[NR][RPW];
     float dt[TMT][4];  // TC2: this warp's m-tiles of the leaf (tensor-core part)
+    const bool tc16 = TC16 && a.nr == 16;
     int cur = -1;
     LeafDesc L{};
 
@@ -622,6 +693,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
             for (int r = threadIdx.x; r < rows; r += NCW * 32) {
                 Acc s = red[r];
                 for (int q = 1; q < NG; ++q) acc_add(s, red[(size_t)q * (32 * RPL) + r]);
+                if constexpr (TC16) {
+                    if (tc16) acc_add(s, ty[(size_t)k * TY_LD + r]);
+                }
                 if (whole)
                     yc[(int64_t)k * a.ndof + 3 * (int64_t)L.begin + r] = (Vv)acc_value(s);
                 else
@@ -667,6 +741,17 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 for (int j = 0; j < RPW; ++j) acc_zero(acc[k][j]);
 #pragma unroll
             for (int j = 0; j < TMT; ++j) dt[j][0] = dt[j][1] = dt[j][2] = dt[j][3] = 0.f;
+            if constexpr (TC16) {
+                // the entries of ty this lane accumulates (its m-tile, see below) start at 0
+                if (tc16 && w < TC16_MT) {
+                    const int r0 = 16 * w + (lane >> 2), c0 = 2 * (lane & 3);
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        float* col = ty + (size_t)(8 * nt + c0) * TY_LD;
+                        col[r0] = col[TY_LD + r0] = col[r0 + 8] = col[TY_LD + r0 + 8] = 0.f;
+                    }
+                }
+            }
         }
         mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
         const unsigned char* stg = stage + (size_t)s * STRIDE;
@@ -675,6 +760,53 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const Zin* zb = (const Zin*)stg + (z0 - (z0 & ~(int64_t)(ZR::ALIGN - 1)));
         const unsigned char* buf = stg + ZR::BYTES;
         const int rows = 3 * L.n;
+        if constexpr (TC16) {
+            if (tc16 && ch.kind != 0) {
+                if (w < TC16_MT) {
+                    float d16[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                    const uint16_t* ub = (const uint16_t*)buf;
+                    const int ld = ch.ld, ncols = ch.ncols;
+                    const int j8 = lane >> 3, i8 = lane & 7;
+                    const int m0 = 16 * w + (j8 & 1) * 8;
+                    const uint32_t zaddr = smem_u32(zline);
+                    const uint32_t tbase = smem_u32(stg);  // packed t of the chunk: 64 B per column
+                    for (int kt = 0; kt * 16 < ncols; ++kt) {
+                        // A: this lane addresses slice column kt 16 + (j8 / 2) 8 + i8, rows m0 ..
+                        const int kc = kt * 16 + (j8 >> 1) * 8 + i8;
+                        const uint32_t aaddr = (kc < ncols && m0 < ld) ? smem_u32(ub + (size_t)kc * ld + m0) : zaddr;
+                        uint32_t a0, a1, a2, a3;
+                        ldsm_x4_t(aaddr, a0, a1, a2, a3);
+                        // B: matrix j8 = (k half j8 % 2, n-tile j8 / 2), row i8 = column kb of t
+                        const int kb = kt * 16 + (j8 & 1) * 8 + i8;
+                        const int64_t lg = ch.zoff + kb;
+                        const uint32_t rowaddr = tbase + 64u * (uint32_t)kb;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {  // BF16 high parts of t, then the low parts
+                            const uint32_t badd =
+                                kb < ncols ? rowaddr + 16u * (uint32_t)tb16_piece_pos(lg, 2 * (j8 >> 1) + h) : zaddr;
+                            uint32_t b0, b1, b2, b3;
+                            ldsm_x4_t(badd, b0, b1, b2, b3);
+                            mma_bf16(d16[0], a0, a1, a2, a3, b0, b1);
+                            mma_bf16(d16[1], a0, a1, a2, a3, b2, b3);
+                        }
+                    }
+                    // d16: rows 16 w + lane / 4 (c0, c1) and + 8 (c2, c3), RHS 8 nt + 2 (lane % 4)
+                    // + {0, 1}; summed over the leaf's chunks in ty, read by the flush
+                    const int r0 = 16 * w + (lane >> 2), c0 = 2 * (lane & 3);
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        float* col = ty + (size_t)(8 * nt + c0) * TY_LD;
+                        col[r0] += d16[nt][0];
+                        col[TY_LD + r0] += d16[nt][1];
+                        col[r0 + 8] += d16[nt][2];
+                        col[TY_LD + r0 + 8] += d16[nt][3];
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty + s);
+                continue;
+            }
+        }
         if constexpr (TC2) {
             if (ch.kind != 0) {
                 const uint32_t* zw = (const uint32_t*)zb;  // packed (hi, lo) of t per column
@@ -1029,8 +1161,11 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     constexpr bool kTensorPhase2x1 = MODE == 0 && NR == 1 && std::is_same<C, uint16_t>::value && RPL == 6;
     static_assert(!kTensorPhase2x1 || (ncw2_for<MODE>(NR) == 16 && rs_for(NR) == 1),
                   "the single-RHS tensor-core phase 2 assumes 16 consumer warps without row split");
+    // BF16 factors with 16 RHS: the U slices of phase 2 on tensor cores as well, reading t
+    // in the packed BF16 form of k_reduce_tb_pack16
+    constexpr bool kTensorPhase2x16 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
     const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
-                         (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc);
+                         (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc) + (kTensorPhase2x16 ? 16 * 196 * 4 : 0);
     // shared-memory opt-in, once per device for each instantiation
     static bool attr_done[64] = {};
     int dev = 0;
@@ -1066,6 +1201,9 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
             launch_pdl(k_reduce_mix<V, uint32_t>, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
                        (const int32_t*)H.poff.p, (const int32_t*)H.red_order.p, H.n_red_big, H.n_red,
                        (const V*)a.out, (uint32_t*)base.tb, base.skip);
+        else if (kTensorPhase2x16 && base.nr == 16)
+            launch_pdl(k_reduce_tb_pack16, dim3((unsigned)H.n_far), dim3(128), 0, st, (const FarDesc*)H.far.p,
+                       (const int32_t*)H.poff.p, (const float*)a.out, (uint16_t*)base.tb, base.skip);
         else if (base.nr == 1)
             launch_pdl(k_reduce_mix<V, Zt>, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
                        (const int32_t*)H.poff.p, (const int32_t*)H.red_order.p, H.n_red_big, H.n_red,
@@ -1217,6 +1355,17 @@ void build_plan_for(HMat& H, HMat::Plan& PLAN, int esz, int G, cudaStream_t st) 
             acc += bytes[i];
         }
         for (int q = w + 1; q <= G; ++q) cta[q] = (int32_t)bytes.size();
+        // A chunk larger than a share would leave the CTAs whose shares it covers without
+        // a chunk; such an empty CTA inside a row leaf split over several CTAs would be
+        // counted as a part of it and never arrive.  So every CTA gets at least one chunk
+        // (with fewer chunks than CTAs, one each and the empty CTAs last).
+        const int32_t n = (int32_t)bytes.size();
+        if (n < G) {
+            for (int q = 0; q <= G; ++q) cta[q] = std::min(q, n);
+        } else {
+            for (int q = 1; q < G; ++q) cta[q] = std::max(cta[q], cta[q - 1] + 1);
+            for (int q = G - 1; q >= 1; --q) cta[q] = std::min(cta[q], cta[q + 1] - 1);
+        }
     };
 
     std::vector<Chunk> c1, c2;

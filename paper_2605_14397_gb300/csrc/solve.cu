@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "hmat_impl.h"
+#include "ilu_dev.h"
 #include "learned.h"
 
 namespace hm {
@@ -857,7 +858,7 @@ struct CycleResult {
 // One restart cycle of FGMRES on (E - diag d): rhs r (cluster order), solution x updated
 // in place; beta[k] = ||r_k||; tol_abs[k] the target on the residual estimate.
 // preconditioner applied in the Krylov loop
-enum PcKind { PC_NONE = 0, PC_LEAF = 1, PC_POINT = 2 };
+enum PcKind { PC_NONE = 0, PC_LEAF = 1, PC_POINT = 2, PC_ILU = 3 };
 
 CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double* tol_abs, const int* active_h,
                          int nr, int m, int dtype, int fac, PcKind pc, cudaStream_t st) {
@@ -891,6 +892,9 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
         if (pc == PC_POINT)
             k_j3_apply<<<g1(H.N * nr), 256, 0, st>>>(W.j3.p, vj, zj, dtype == HM_F32 ? W.zf.p : nullptr, H.N, n, nr,
                                                       W.st.p);
+        else if (pc == PC_ILU)
+            ilu_apply(H, vj, zj, dtype == HM_F32 ? W.zf.p : nullptr, nr, &W.st.p->done,
+                      (int)(sizeof(CycleState) / sizeof(int)), st);
         else
             k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, vj, zj,
                                                    dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p,
@@ -1054,6 +1058,19 @@ void bj_solve_cluster(HMat& H, const double* kel, double shift, const double* v,
     HM_CUDA(cudaStreamSynchronize(st));
 }
 
+// The ILU preconditioner of A = E - diag(k) - shift I for a fraction p, built and
+// factored, then copied to the host (see ilu_export).
+void ilu_export_for(HMat& H, const double* kel, double shift, double p, int64_t* n_out, int64_t* nnz_out,
+                    int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col, double* a_val,
+                    double* lu_val, cudaStream_t st) {
+    SolveWS& W = workspace(H, 1, 1, st);
+    k_diag<<<g1(H.ndof), 256, 0, st>>>(kel, shift, H.perm.p, H.ndof, W.dc.p);
+    HM_LAUNCH_CHECK();
+    ilu_prepare(H, p, st);
+    if (lu_val) ilu_factor(H, W.dc.p, st, W.err.p);
+    ilu_export(H, n_out, nnz_out, n_colours_out, order, rowptr, col, a_val, lu_val, st);
+}
+
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp) {
     using clk = std::chrono::steady_clock;
@@ -1068,8 +1085,10 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     if (mode != HM_SOLVE_F64 && mode != HM_SOLVE_MIXED && mode != HM_SOLVE_PLAIN32)
         fail(HM_EINVAL, "gmres_solve: unknown mode");
     if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ && o.precond != HM_PRECOND_LEARNED &&
-        o.precond != HM_PRECOND_JACOBI3)
+        o.precond != HM_PRECOND_JACOBI3 && o.precond != HM_PRECOND_ILU)
         fail(HM_EINVAL, "gmres_solve: unknown preconditioner");
+    const double ilu_p = o.ilu_p > 0.0 ? o.ilu_p : 0.01;
+    if (o.precond == HM_PRECOND_ILU && !(ilu_p <= 1.0)) fail(HM_EINVAL, "gmres_solve: ilu_p must lie in (0, 1]");
     if (o.precond == HM_PRECOND_LEARNED && !lp) fail(HM_EINVAL, "gmres_solve: the learned preconditioner needs a model");
     if (!has_factors(H, 0)) fail(HM_EINVAL, "gmres_solve: the FP32 factors are required (storage F32 or F32_BF16)");
     // refinement corrections: BF16 factors (mixed; FP32 if BF16 is not stored) or the
@@ -1094,9 +1113,14 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     HM_LAUNCH_CHECK();
     const PcKind pc = (o.precond == HM_PRECOND_BLOCKJ || o.precond == HM_PRECOND_LEARNED)
                           ? PC_LEAF
-                          : (o.precond == HM_PRECOND_JACOBI3 ? PC_POINT : PC_NONE);
+                          : (o.precond == HM_PRECOND_JACOBI3 ? PC_POINT
+                                                             : (o.precond == HM_PRECOND_ILU ? PC_ILU : PC_NONE));
     W.dsc_on = false;
     if (pc == PC_POINT) j3_build(H, W, st);
+    if (pc == PC_ILU) {
+        ilu_prepare(H, ilu_p, st);
+        ilu_factor(H, W.dc.p, st, W.err.p);
+    }
     if (pc == PC_LEAF) {
         bj_build(H, W, st);
         if (o.precond == HM_PRECOND_LEARNED && !lp->fallback) {

@@ -22,7 +22,7 @@ HM_EBREAKDOWN = -6
 HM_ENAN = -7
 HM_ETIMEOUT = -8
 HM_F32, HM_F64, HM_BF16, HM_F32_BF16 = 1, 2, 3, 4
-HM_PRECOND_NONE, HM_PRECOND_BLOCKJ, HM_PRECOND_LEARNED, HM_PRECOND_JACOBI3 = 0, 1, 2, 3
+HM_PRECOND_NONE, HM_PRECOND_BLOCKJ, HM_PRECOND_LEARNED, HM_PRECOND_JACOBI3, HM_PRECOND_ILU = 0, 1, 2, 3, 4
 HM_SOLVE_F64, HM_SOLVE_MIXED, HM_SOLVE_PLAIN32 = 1, 2, 3
 
 _STATUS_NAMES = {HM_EINVAL: "HM_EINVAL", HM_ENOMEM: "HM_ENOMEM", HM_ECUDA: "HM_ECUDA",
@@ -49,7 +49,7 @@ class hm_tree_info(ctypes.Structure):
 
 class hm_assemble_opts(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("aca_eps", ctypes.c_double),
-                ("storage", ctypes.c_int), ("max_rank", ctypes.c_int)]
+                ("storage", ctypes.c_int), ("max_rank", ctypes.c_int), ("trunc_factor", ctypes.c_double)]
 
 
 class hm_hmat_info(ctypes.Structure):
@@ -65,7 +65,8 @@ class hm_hmat_info(ctypes.Structure):
 class hm_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mode", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int), ("lp", ctypes.c_void_p)]
+                ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int), ("lp", ctypes.c_void_p),
+                ("ilu_p", ctypes.c_double)]
 
 
 class hm_lp_info(ctypes.Structure):
@@ -110,6 +111,8 @@ SIGNATURES = [
     ("hm_gmres_solve", _I, [_VP, _VP, _D, _VP, _VP, _I, ctypes.POINTER(hm_solve_opts),
                             ctypes.POINTER(hm_solve_info), _VP]),
     ("hm_batch_create", _I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
+    ("hm_ilu_export", _I, [_VP, _VP, _D, _D, _P64, _P64, ctypes.POINTER(ctypes.c_int32), _VP, _VP, _VP, _VP, _VP,
+                           _VP]),
     ("hm_lp_param_count", _I64, [_I]),
     ("hm_lp_create", _I, [_I, _VP, ctypes.POINTER(_VP)]),
     ("hm_lp_add_samples", _I, [_VP, _VP, _VP, _I64]),
@@ -245,10 +248,11 @@ class ClusterTree:
 
 
 class HMatrix:
-    def __init__(self, tree, el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", max_rank=0, stream=None):
+    def __init__(self, tree, el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", max_rank=0, stream=None,
+                 trunc_factor=0.0):
         st = {"f32": HM_F32, "bf16": HM_BF16, "both": HM_F32_BF16}[storage]
         ea = _ElemArgs(el) if el is not None else None
-        opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, int(max_rank))
+        opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, int(max_rank), float(trunc_factor))
         h = ctypes.c_void_p()
         _check(lib().hm_assemble_hmat(tree.handle, ea.ref if ea else None, ctypes.byref(opt),
                                       ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
@@ -326,19 +330,20 @@ class HMatrix:
                                     ctypes.c_void_p(_stream_ptr(stream))))
 
     def solve(self, b, x, k=None, shift=0.0, tol=1e-8, restart=50, maxit=2000, precond="blockj", mode="f64",
-              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None):
+              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None, ilu_p=0.0):
         """Solve (E - diag(k) - shift I) x = b on the device (b, x: float64 CUDA tensors of
         shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None).  precond "none",
-        "jacobi3", "blockj" or "learned"; mode "f64", "mixed" or "plain32".  Returns the
+        "jacobi3", "blockj", "ilu" (ilu_p: fraction of the near field, 0 = 0.01) or "learned";
+        mode "f64", "mixed" or "plain32".  Returns the
         per-RHS info dicts; raises HMError unless every RHS converged (raise_on_error)."""
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         assert b.is_contiguous() and x.is_contiguous() and (k is None or k.is_contiguous())
         o = hm_solve_opts(float(tol), int(restart), int(maxit),
                           {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "learned": HM_PRECOND_LEARNED,
-                           "jacobi3": HM_PRECOND_JACOBI3}[precond],
+                           "jacobi3": HM_PRECOND_JACOBI3, "ilu": HM_PRECOND_ILU}[precond],
                           {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED, "plain32": HM_SOLVE_PLAIN32}[mode],
                           float(inner_tol), int(max_outer), 0,
-                          model.handle.value if model is not None else None)
+                          model.handle.value if model is not None else None, float(ilu_p))
         info = (hm_solve_info * nrhs)()
         st = lib().hm_gmres_solve(self.handle, _dptr(k) if k is not None else None, float(shift), _dptr(b), _dptr(x),
                                   int(nrhs), ctypes.byref(o), info, ctypes.c_void_p(_stream_ptr(stream)))
@@ -346,6 +351,26 @@ class HMatrix:
         if st != HM_OK and raise_on_error:
             raise HMError(st, lib().hm_last_error().decode())
         return out
+
+    def ilu_export(self, k=None, shift=0.0, p=0.01, factor=True, stream=None):
+        """The ILU preconditioner for this k, shift and p (hm_ilu_export): dict of order
+        (factorization position -> cluster DOF position), rowptr, col, a_val and, with
+        factor, lu_val, plus n_colours."""
+        n, nnz, nc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        kp = _dptr(k) if k is not None else None
+        sp = ctypes.c_void_p(_stream_ptr(stream))
+        _check(lib().hm_ilu_export(self.handle, kp, float(shift), float(p), ctypes.byref(n), ctypes.byref(nnz),
+                                   ctypes.byref(nc), None, None, None, None, None, sp))
+        order = np.empty(n.value, np.int32)
+        rowptr = np.empty(n.value + 1, np.int64)
+        col = np.empty(nnz.value, np.int32)
+        aval = np.empty(nnz.value)
+        lu = np.empty(nnz.value) if factor else None
+        _check(lib().hm_ilu_export(self.handle, kp, float(shift), float(p), ctypes.byref(n), ctypes.byref(nnz),
+                                   ctypes.byref(nc), order.ctypes.data_as(_VP), rowptr.ctypes.data_as(_VP),
+                                   col.ctypes.data_as(_VP), aval.ctypes.data_as(_VP),
+                                   lu.ctypes.data_as(_VP) if factor else None, sp))
+        return dict(order=order, rowptr=rowptr, col=col, a_val=aval, lu_val=lu, n_colours=nc.value)
 
     def timing(self, enable):
         _check(lib().hm_hmat_timing(self.handle, 1 if enable else 0))
@@ -495,7 +520,7 @@ def autotune(el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", leaves=(32, 64, 12
             return table[key]
     ea = _ElemArgs(el)
     st = {"f32": HM_F32, "bf16": HM_BF16, "both": HM_F32_BF16}[storage]
-    opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, 0)
+    opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, 0, 0.0)
     lv = (_I * len(leaves))(*[int(v) for v in leaves])
     ev = (_D * len(etas))(*[float(v) for v in etas])
     cap = 4096 + 256 * len(leaves) * len(etas)

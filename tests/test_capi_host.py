@@ -74,7 +74,7 @@ def test_bad_arguments_return_status(L):
     nulls = (ctypes.c_void_p * 2)(None, None)
     assert L.hm_batch_create(nulls, 2, None, ctypes.byref(out)) == hmat.HM_EINVAL and not out.value
     assert L.hm_matvec_graph(None, None, None, 1, 1, None) == hmat.HM_EINVAL
-    opt = hmat.hm_assemble_opts(1.0, 0.25, 1e-6, hmat.HM_F32, 0)
+    opt = hmat.hm_assemble_opts(1.0, 0.25, 1e-6, hmat.HM_F32, 0, 0.0)
     buf = ctypes.create_string_buffer(64)
     lv = (ctypes.c_int * 1)(200)
     ev = (ctypes.c_double * 1)(2.0)

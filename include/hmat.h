@@ -171,6 +171,8 @@ typedef struct {
     int64_t n_far_refined;    /* admissible blocks whose cross approximation did not converge
                                  below the rank cap, replaced by their children's blocks */
     int64_t n_leaves;         /* leaf clusters (block-Jacobi blocks) */
+    int64_t coeff_blocks;     /* 3x3 influence blocks the assembly evaluated (near tiles and
+                                 the rows and columns of the cross approximation) */
 } hm_hmat_info;
 
 hm_status hm_assemble_hmat(const hm_tree* t, const hm_elements* el, const hm_assemble_opts* opt,
@@ -321,17 +323,46 @@ hm_status hm_batch_create(const hm_hmat* const* hs, int nf, void* stream, hm_hma
 hm_status hm_matvec_graph(const hm_hmat* h, const void* x_dev, void* y_dev, int nrhs, int dtype,
                           void* stream);
 
-/* Leaf-size autotuner: for each (leaf_sizes[i], etas[j]) in order, build the cluster
- * tree and partition (Sec. 3.1), assemble with `opt` (every candidate meets the same
- * per-block accuracy aca_eps), and time 20 single-RHS FP32 products with CUDA events on
- * `stream`; stop once budget_ms of wall time has passed (at least one candidate is
+/* Tile shape of the product's coefficient streams (an implementation choice of this
+ * library; the paper states none).  chunk_bytes (a multiple of 16 in [2048, 32768]) and
+ * chunk_cols ([8, 128]) bound one pipeline chunk -- whole columns of one tile or factor
+ * slice -- and so the grain of the byte split over the SMs; ring (4 or 6) is the depth of
+ * the shared-memory copy ring and warps (16 or 8) the consumer warps of the single-RHS
+ * product with FP32 vectors (products with several right-hand sides or FP64 vectors keep
+ * 4 stages and their own warp counts, and BF16 factors keep 16 warps in the row phase,
+ * whose U slices run on tensor cores).  The default is {32768, 128, 4, 16}. */
+typedef struct {
+    int32_t chunk_bytes;
+    int32_t chunk_cols;
+    int32_t ring;
+    int32_t warps;
+} hm_tile_shape;
+
+/* Set the tile shape of an H-matrix: its product plans are cut again (synchronises the
+ * stream; product graphs captured before are dropped).  HM_EINVAL for a shape outside
+ * the ranges above. */
+hm_status hm_hmat_set_tile_shape(hm_hmat* h, const hm_tile_shape* shape, void* stream);
+hm_status hm_hmat_get_tile_shape(const hm_hmat* h, hm_tile_shape* shape);
+/* Time `reps` single-RHS FP32-vector products (FP32 factors when stored) under each of
+ * shapes[0 .. n_shapes - 1] with CUDA events and keep the fastest on h.  JSON to json_out:
+ *   {"candidates": [{"chunk_bytes", "chunk_cols", "ring", "warps", "ms"}, ...],
+ *    "best": {... , "ms"}, "tuned": n} */
+hm_status hm_tune_tile_shape(hm_hmat* h, const hm_tile_shape* shapes, int n_shapes, int reps, char* json_out,
+                             size_t cap, void* stream);
+
+/* Autotuner of leaf size, admissibility and tile shape: for each (leaf_sizes[i], etas[j])
+ * in order, build the cluster tree and partition (Sec. 3.1), assemble with `opt` (every
+ * candidate meets the same accuracy aca_eps), and for each of shapes[0 .. n_shapes - 1]
+ * (the default shape if n_shapes is 0) time 20 single-RHS FP32 products with CUDA events
+ * on `stream`; stop once budget_ms of wall time has passed (at least one candidate is
  * timed).  Writes a NUL-terminated JSON object to json_out (capacity cap bytes):
- *   {"n_elements": N, "candidates": [{"leaf", "eta", "ms", "stored_bytes",
- *    "assemble_s", "rank_mean"}, ...], "best": {"leaf", "eta", "ms"}, "tuned": n}
+ *   {"n_elements": N, "candidates": [{"leaf", "eta", "ms", "stored_bytes", "assemble_s",
+ *    "rank_mean", "chunk_bytes", "chunk_cols", "ring", "warps"}, ...],
+ *    "best": {"leaf", "eta", "ms", "chunk_bytes", "chunk_cols", "ring", "warps"}, "tuned": n}
  * HM_EINVAL if the buffer is too small (the message states the size needed). */
 hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const int* leaf_sizes, int n_leaf,
-                      const double* etas, int n_eta, int budget_ms, char* json_out, size_t cap,
-                      void* stream);
+                      const double* etas, int n_eta, const hm_tile_shape* shapes, int n_shapes, int budget_ms,
+                      char* json_out, size_t cap, void* stream);
 
 /* ---------------------------------------------------------------- learned correction
  * The paper preconditions the A11 system with (point) Jacobi (Sec. 3.3.1) and learns

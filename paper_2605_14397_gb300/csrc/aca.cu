@@ -119,7 +119,8 @@ __device__ int random_free_element(const uint32_t* used, int n, unsigned blk, in
 
 __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, const AcaJob* __restrict__ jobs,
                                                 double* __restrict__ ws, int R, double eps, double mu, double nu,
-                                                int32_t* __restrict__ rank_out, int32_t* __restrict__ status_out) {
+                                                int32_t* __restrict__ rank_out, int32_t* __restrict__ status_out,
+                                                unsigned long long* __restrict__ evals) {
     extern __shared__ __align__(16) double dyn[];
     double* urow = dyn;                  // U[l][3 ipiv + p] for l < k
     double* vcol = urow + 3 * (R + 3);   // V[l][3 jpiv + q]
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, 
     __syncthreads();
 
     int k = 0, status = 0, streak = 0, ipiv = 0, checks = 0;
+    unsigned long long n_eval = 0;  // 3x3 blocks evaluated (thread 0's count)
     bool checking = false;
     double nrm2 = 0.0;
     const int kmax = min(R, min(mS, mT));
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, 
         for (int l = tid; l < 3 * k; l += ACA_NT) urow[l] = U[(size_t)(l / 3) * mS + 3 * ipiv + (l % 3)];
         __syncthreads();
         const ElemRec er = el[J.s_begin + ipiv];
+        n_eval += J.t_n;
         for (int j = tid; j < J.t_n; j += ACA_NT) {
             double blk[9];
             dd_block(er, el[J.t_begin + j], mu, nu, blk);
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, 
         for (int l = tid; l < 3 * k; l += ACA_NT) vcol[l] = V[(size_t)(l / 3) * mT + 3 * jpiv + (l % 3)];
         __syncthreads();
         const ElemRec es = el[J.t_begin + jpiv];
+        n_eval += J.s_n;
         for (int i = tid; i < J.s_n; i += ACA_NT) {
             double blk[9];
             dd_block(el[J.s_begin + i], es, mu, nu, blk);
@@ -338,6 +342,7 @@ __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, 
     if (tid == 0) {
         rank_out[blockIdx.x] = k;
         status_out[blockIdx.x] = status;
+        if (evals) atomicAdd(evals, n_eval);
     }
 }
 
@@ -529,12 +534,13 @@ __global__ void k_expand(const ExpandJob* __restrict__ jobs, const double* __res
 }  // namespace
 
 void launch_aca(const ElemRec* el, const AcaJob* jobs, int njobs, int max_sn, double* ws, int R, double eps,
-                double mu, double nu, int32_t* rank_out, int32_t* status_out, cudaStream_t st) {
+                double mu, double nu, int32_t* rank_out, int32_t* status_out, unsigned long long* evals,
+                cudaStream_t st) {
     const size_t smem = sizeof(double) * (size_t)(8 * (R + 3)) + sizeof(uint32_t) * (size_t)((3 * max_sn + 31) / 32);
     if (smem > 200 * 1024) fail(HM_EINVAL, "assemble: cluster too large for the ACA kernel");
     if (smem > 48 * 1024)
         HM_CUDA(cudaFuncSetAttribute(k_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_aca<<<(unsigned)njobs, ACA_NT, smem, st>>>(el, jobs, ws, R, eps, mu, nu, rank_out, status_out);
+    k_aca<<<(unsigned)njobs, ACA_NT, smem, st>>>(el, jobs, ws, R, eps, mu, nu, rank_out, status_out, evals);
     HM_LAUNCH_CHECK();
 }
 

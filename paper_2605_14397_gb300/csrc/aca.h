@@ -28,7 +28,8 @@ struct ExpandJob {
 // ACA of every job (one CTA each) to relative accuracy eps; rank_out / status_out per
 // job (status 1: the rank cap R was reached before convergence).
 void launch_aca(const ElemRec* el, const AcaJob* jobs, int njobs, int max_sn, double* ws, int R, double eps,
-                double mu, double nu, int32_t* rank_out, int32_t* status_out, cudaStream_t st);
+                double mu, double nu, int32_t* rank_out, int32_t* status_out, unsigned long long* evals,
+                cudaStream_t st);
 // Recompress the ACA factors of every job; rank_out receives the truncated rank.
 void launch_recompress(const RecJob* jobs, int njobs, int R, double* ws, double* small, double tau,
                        int32_t* rank_out, cudaStream_t st);

@@ -210,6 +210,8 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     std::vector<int64_t> chunk_base;
     DevBuf<double> ws, small;
     DevBuf<int32_t> d_rank, d_stat;
+    DevBuf<unsigned long long> d_evals(1);
+    HM_CUDA(cudaMemsetAsync(d_evals.p, 0, d_evals.bytes(), st));
     int64_t b0 = 0;
     while (b0 < (int64_t)H.h_far.size()) {
         const int64_t nf = (int64_t)H.h_far.size();
@@ -237,7 +239,8 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         DevBuf<AcaJob> d_jobs;
         d_jobs.upload(jobs, st);
         if ((int64_t)d_rank.n < nb) { d_rank.alloc(nb); d_stat.alloc(nb); }
-        launch_aca(H.elems.p, d_jobs.p, (int)nb, max_sn, ws.p, R, eps_aca, mu, opt.nu, d_rank.p, d_stat.p, st);
+        launch_aca(H.elems.p, d_jobs.p, (int)nb, max_sn, ws.p, R, eps_aca, mu, opt.nu, d_rank.p, d_stat.p,
+                   d_evals.p, st);
         HM_CUDA(cudaMemcpyAsync(ranks.data() + b0, d_rank.p, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         HM_CUDA(cudaMemcpyAsync(stat.data() + b0, d_stat.p, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         HM_CUDA(cudaStreamSynchronize(st));
@@ -329,6 +332,12 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     }
     ws.release();
     small.release();
+    {
+        unsigned long long ev = 0;
+        HM_CUDA(cudaMemcpyAsync(&ev, d_evals.p, sizeof(ev), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        H.aca_blocks = (int64_t)ev;
+    }
     const int64_t nf = (int64_t)H.h_far.size();
     H.n_far = nf;
     H.facstore.alloc(std::max<int64_t>(store_len, 1));

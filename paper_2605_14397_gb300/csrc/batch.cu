@@ -70,6 +70,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
     M.n_near = M.n_far = M.n_dense_far = M.n_refined = 0;
     M.near_entries = M.far_entries = 0;
     M.assemble_seconds = 0.0;
+    M.aca_blocks = 0;
     std::vector<int32_t> perm32;
     perm32.reserve(N);
     for (const HMat* h : hs) {
@@ -128,6 +129,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         M.near_entries += h->near_entries;
         M.far_entries += h->far_entries;
         M.assemble_seconds += h->assemble_seconds;
+        M.aca_blocks += h->aca_blocks;
     }
     M.n_leaves = (int)M.h_leaves.size();
     M.tb_len = tb_b;
@@ -227,6 +229,92 @@ void matvec_graph(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStre
     HM_CUDA(cudaGraphLaunch(exec, st));
 }
 
+// ------------------------------------------------------------------ tile shapes
+
+void set_tile_shape(HMat& H, const hm_tile_shape& t, cudaStream_t st) {
+    if (t.chunk_bytes < 2048 || t.chunk_bytes > 32768 || t.chunk_bytes % 16)
+        fail(HM_EINVAL, "tile shape: chunk_bytes must be a multiple of 16 in [2048, 32768]");
+    if (t.chunk_cols < 8 || t.chunk_cols > 128) fail(HM_EINVAL, "tile shape: chunk_cols must lie in [8, 128]");
+    if (t.ring != 4 && t.ring != 6) fail(HM_EINVAL, "tile shape: ring must be 4 or 6");
+    if (t.warps != 8 && t.warps != 16) fail(HM_EINVAL, "tile shape: warps must be 8 or 16");
+    HM_CUDA(cudaStreamSynchronize(st));
+    graphs_clear(H);
+    H.shape.chunk_bytes = t.chunk_bytes;
+    H.shape.chunk_cols = t.chunk_cols;
+    H.shape.ring = t.ring;
+    H.shape.warps = t.warps;
+    build_product_plan(H, st);
+    // the split-leaf slots depend on the plan: size the product scratch again
+    const int cap = std::max(H.nrhs_cap, 1);
+    H.nrhs_cap = 0;
+    ensure_product_scratch(H, cap, st);
+    HM_CUDA(cudaStreamSynchronize(st));
+}
+
+namespace {
+
+// average time of `reps` single-RHS FP32-vector products (FP32 factors when stored)
+double time_product(HMat& H, int reps, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    DevBuf<float> x(H.ndof), y(H.ndof);
+    HM_CUDA(cudaMemsetAsync(x.p, 0, x.bytes(), st));
+    for (int w = 0; w < 3; ++w) matvec(H, x.p, y.p, 1, HM_F32, st);
+    HM_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) matvec(H, x.p, y.p, 1, HM_F32, st);
+    HM_CUDA(cudaEventRecord(e1, st));
+    HM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    HM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (product_error_flags(H, st)) fail(HM_ETIMEOUT, "tile-shape timing: a product wait gave up");
+    return ms / reps;
+}
+
+std::string shape_json(const hm_tile_shape& t) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "\"chunk_bytes\": %d, \"chunk_cols\": %d, \"ring\": %d, \"warps\": %d", t.chunk_bytes,
+             t.chunk_cols, t.ring, t.warps);
+    return buf;
+}
+
+struct Events {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Events() {
+        HM_CUDA(cudaEventCreate(&e0));
+        HM_CUDA(cudaEventCreate(&e1));
+    }
+    ~Events() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+}  // namespace
+
+// Time the single-RHS product of H under every shape, keep the fastest on H.
+std::string tune_tile_shape(HMat& H, const hm_tile_shape* shapes, int n, int reps, cudaStream_t st) {
+    if (!shapes || n < 1) fail(HM_EINVAL, "tune_tile_shape: empty shape list");
+    if (reps < 1) reps = 20;
+    Events ev;
+    std::string js = "{\"candidates\": [";
+    double best = 1e300;
+    int ib = 0;
+    for (int i = 0; i < n; ++i) {
+        set_tile_shape(H, shapes[i], st);
+        const double ms = time_product(H, reps, st, ev.e0, ev.e1);
+        char buf[64];
+        snprintf(buf, sizeof(buf), ", \"ms\": %.6f}", ms);
+        js += (i ? ", {" : "{") + shape_json(shapes[i]) + buf;
+        if (ms < best) {
+            best = ms;
+            ib = i;
+        }
+    }
+    set_tile_shape(H, shapes[ib], st);
+    char buf[64];
+    snprintf(buf, sizeof(buf), ", \"ms\": %.6f}, \"tuned\": %d}", best, n);
+    js += "], \"best\": {" + shape_json(shapes[ib]) + buf;
+    return js;
+}
+
 // ------------------------------------------------------------------ autotuner
 
 // Time the product for every (leaf size, eta) candidate on this geometry and pick the
@@ -235,64 +323,54 @@ void matvec_graph(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStre
 // the same per-block accuracy aca_eps, so only time (and memory) differ.  Candidates are
 // tried in order until budget_ms has elapsed (at least one is always timed).
 std::string autotune(const hm_elements& el, const hm_assemble_opts& opt, const int* leaves, int n_leaf,
-                     const double* etas, int n_eta, int budget_ms, cudaStream_t st) {
+                     const double* etas, int n_eta, const hm_tile_shape* shapes, int n_shapes, int budget_ms,
+                     cudaStream_t st) {
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     if (n_leaf < 1 || n_eta < 1 || !leaves || !etas) fail(HM_EINVAL, "autotune: empty candidate list");
+    hm_tile_shape def{32768, 128, 4, 16};
+    if (!shapes || n_shapes < 1) {
+        shapes = &def;
+        n_shapes = 1;
+    }
     std::string js = "{\"n_elements\": " + std::to_string(el.N) + ", \"candidates\": [";
     double best = 1e300;
-    int best_leaf = 0;
+    int best_leaf = 0, best_shape = 0;
     double best_eta = 0.0;
     int tried = 0;
-    cudaEvent_t e0, e1;
-    HM_CUDA(cudaEventCreate(&e0));
-    HM_CUDA(cudaEventCreate(&e1));
-    try {
-        for (int i = 0; i < n_leaf; ++i)
-            for (int j = 0; j < n_eta; ++j) {
-                const double el_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
-                if (tried > 0 && el_ms > budget_ms) break;
-                Tree T;
-                build_tree(el, leaves[i], etas[j], T);
-                HMat H;
-                assemble(T, opt, st, H);
-                DevBuf<float> x(H.ndof), y(H.ndof);
-                HM_CUDA(cudaMemsetAsync(x.p, 0, x.bytes(), st));
-                for (int w = 0; w < 3; ++w) matvec(H, x.p, y.p, 1, HM_F32, st);
-                const int reps = 20;
-                HM_CUDA(cudaEventRecord(e0, st));
-                for (int r = 0; r < reps; ++r) matvec(H, x.p, y.p, 1, HM_F32, st);
-                HM_CUDA(cudaEventRecord(e1, st));
-                HM_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.0f;
-                HM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                const double per = ms / reps;
-                if (product_error_flags(H, st)) fail(HM_ETIMEOUT, "autotune: a product wait gave up");
+    Events ev;
+    for (int i = 0; i < n_leaf; ++i)
+        for (int j = 0; j < n_eta; ++j) {
+            const double el_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+            if (tried > 0 && el_ms > budget_ms) break;
+            Tree T;
+            build_tree(el, leaves[i], etas[j], T);
+            HMat H;
+            assemble(T, opt, st, H);
+            for (int q = 0; q < n_shapes; ++q) {
+                const double el2 = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+                if (tried > 0 && el2 > budget_ms) break;
+                set_tile_shape(H, shapes[q], st);
+                const double per = time_product(H, 20, st, ev.e0, ev.e1);
                 char buf[320];
                 snprintf(buf, sizeof(buf),
                          "%s{\"leaf\": %d, \"eta\": %.6g, \"ms\": %.6f, \"stored_bytes\": %lld, "
-                         "\"assemble_s\": %.4f, \"rank_mean\": %.4f}",
+                         "\"assemble_s\": %.4f, \"rank_mean\": %.4f, ",
                          tried ? ", " : "", leaves[i], etas[j], per, (long long)H.stored_bytes(),
                          H.assemble_seconds, H.rank_mean);
-                js += buf;
+                js += buf + shape_json(shapes[q]) + "}";
                 if (per < best) {
                     best = per;
                     best_leaf = leaves[i];
                     best_eta = etas[j];
+                    best_shape = q;
                 }
                 ++tried;
             }
-    } catch (...) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        throw;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+        }
     char buf[200];
-    snprintf(buf, sizeof(buf), "], \"best\": {\"leaf\": %d, \"eta\": %.6g, \"ms\": %.6f}, \"tuned\": %d}", best_leaf,
-             best_eta, best, tried);
-    js += buf;
+    snprintf(buf, sizeof(buf), "], \"best\": {\"leaf\": %d, \"eta\": %.6g, \"ms\": %.6f, ", best_leaf, best_eta, best);
+    js += buf + shape_json(shapes[best_shape]) + "}, \"tuned\": " + std::to_string(tried) + "}";
     return js;
 }
 

@@ -18,7 +18,8 @@ static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 std::string autotune(const hm_elements& el, const hm_assemble_opts& opt, const int* leaves, int n_leaf,
-                     const double* etas, int n_eta, int budget_ms, cudaStream_t st);
+                     const double* etas, int n_eta, const hm_tile_shape* shapes, int n_shapes, int budget_ms,
+                     cudaStream_t st);
 void influence_pairs(const hm_elements& e, double E, double nu, int64_t npairs, const int64_t* ri,
                      const int64_t* sj, double* out, cudaStream_t st);
 
@@ -144,6 +145,7 @@ hm_status hm_hmat_get_info(const hm_hmat* hh, hm_hmat_info* info) {
     }
     info->tb_len = H.tb_len;
     info->p_len = H.p_len;
+    info->coeff_blocks = H.aca_blocks + H.near_entries / 9;
     HM_API_END
 }
 
@@ -272,7 +274,8 @@ hm_status hm_matvec_graph(const hm_hmat* hh, const void* x_dev, void* y_dev, int
 }
 
 hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const int* leaf_sizes, int n_leaf,
-                      const double* etas, int n_eta, int budget_ms, char* json_out, size_t cap, void* stream) {
+                      const double* etas, int n_eta, const hm_tile_shape* shapes, int n_shapes, int budget_ms,
+                      char* json_out, size_t cap, void* stream) {
     HM_API_BEGIN
     hm::g_last_error.clear();
     hm::check_elements(el);
@@ -283,10 +286,43 @@ hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const 
         if (leaf_sizes[i] < 1 || leaf_sizes[i] > 128) hm::fail(HM_EINVAL, "autotune: leaf sizes must be in [1, 128]");
     for (int j = 0; j < n_eta; ++j)
         if (!(etas[j] > 0.0) || !std::isfinite(etas[j])) hm::fail(HM_EINVAL, "autotune: eta must be positive");
-    const std::string js =
-        hm::autotune(*el, *opt, leaf_sizes, n_leaf, etas, n_eta, budget_ms, (cudaStream_t)stream);
+    if (n_shapes < 0 || (n_shapes > 0 && !shapes)) hm::fail(HM_EINVAL, "autotune: bad shape list");
+    const std::string js = hm::autotune(*el, *opt, leaf_sizes, n_leaf, etas, n_eta, shapes, n_shapes, budget_ms,
+                                        (cudaStream_t)stream);
     if (js.size() + 1 > cap) hm::fail(HM_EINVAL, "autotune: output buffer too small (need " +
                                                      std::to_string(js.size() + 1) + " bytes)");
+    std::memcpy(json_out, js.c_str(), js.size() + 1);
+    HM_API_END
+}
+
+hm_status hm_hmat_set_tile_shape(hm_hmat* hh, const hm_tile_shape* shape, void* stream) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    if (!hh || !shape) hm::fail(HM_EINVAL, "hmat_set_tile_shape: NULL argument");
+    hm::set_tile_shape(hh->h, *shape, (cudaStream_t)stream);
+    HM_API_END
+}
+
+hm_status hm_hmat_get_tile_shape(const hm_hmat* hh, hm_tile_shape* shape) {
+    HM_API_BEGIN
+    if (!hh || !shape) hm::fail(HM_EINVAL, "hmat_get_tile_shape: NULL argument");
+    shape->chunk_bytes = hh->h.shape.chunk_bytes;
+    shape->chunk_cols = hh->h.shape.chunk_cols;
+    shape->ring = hh->h.shape.ring;
+    shape->warps = hh->h.shape.warps;
+    HM_API_END
+}
+
+hm_status hm_tune_tile_shape(hm_hmat* hh, const hm_tile_shape* shapes, int n_shapes, int reps, char* json_out,
+                             size_t cap, void* stream) {
+    HM_API_BEGIN
+    hm::g_last_error.clear();
+    if (!hh) hm::fail(HM_EINVAL, "tune_tile_shape: NULL H-matrix");
+    if (!json_out || cap == 0) hm::fail(HM_EINVAL, "tune_tile_shape: NULL output buffer");
+    const std::string js = hm::tune_tile_shape(hh->h, shapes, n_shapes, reps, (cudaStream_t)stream);
+    if (js.size() + 1 > cap)
+        hm::fail(HM_EINVAL, "tune_tile_shape: output buffer too small (need " + std::to_string(js.size() + 1) +
+                                " bytes)");
     std::memcpy(json_out, js.c_str(), js.size() + 1);
     HM_API_END
 }

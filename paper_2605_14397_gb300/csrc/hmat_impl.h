@@ -21,6 +21,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "common.h"
@@ -97,6 +98,7 @@ struct HMat {
     int64_t near_entries = 0, far_entries = 0;
     int rank_min = 0, rank_max = 0;
     double rank_mean = 0.0, assemble_seconds = 0.0;
+    int64_t aca_blocks = 0;  // 3x3 influence blocks evaluated by the cross approximation
 
     std::vector<LeafDesc> h_leaves;
     std::vector<FarDesc> h_far;
@@ -123,6 +125,12 @@ struct HMat {
     DevBuf<int32_t> red_order;
     int64_t n_red_big = 0, n_red = 0;
 
+    // tile shape of the product: bytes and columns of a pipeline chunk (at most one 32 KB
+    // stage and 128 columns), ring depth (4 or 6 stages) and consumer warps (16 or 8) of
+    // the single-RHS FP32-vector product; the plans below are cut with it
+    struct TileShape {
+        int chunk_bytes = 32768, chunk_cols = 128, ring = 4, warps = 16;
+    } shape;
     // persistent product plans: [0] with the FP32 factors, [1] with the BF16 factors
     int grid = 0;
     int ld_max = 0;
@@ -202,6 +210,9 @@ void product_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac,
                   const int* skip = nullptr);
 // Concatenate independent H-matrices into one (block-diagonal operator, one work list).
 void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M);
+// tile shape of the product (plans rebuilt) and its tuning over a candidate list
+void set_tile_shape(HMat& H, const hm_tile_shape& t, cudaStream_t st);
+std::string tune_tile_shape(HMat& H, const hm_tile_shape* shapes, int n, int reps, cudaStream_t st);
 void graphs_clear(HMat& H);
 void matvec_graph(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 struct LPModel;

@@ -57,12 +57,13 @@ constexpr int SEL_NT = 256;
 
 __device__ __forceinline__ uint32_t abits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
 
-// Histogram of bits [shift, shift + 11) of |v| over the near-field entries whose bits
-// above `shift + nbits` equal `prefix` (under `pmask`).  One CTA per leaf.
+// Histogram of bits [shift, shift + width) of |v| (binmask = 2^width - 1) over the
+// near-field entries whose higher bits equal `prefix` (under `pmask`).  One CTA per leaf.
 __global__ void __launch_bounds__(SEL_NT) k_sel_hist(const LeafDesc* __restrict__ leaves,
                                                      const int32_t* __restrict__ true_cols,
                                                      const float* __restrict__ near, uint32_t prefix, uint32_t pmask,
-                                                     int shift, unsigned long long* __restrict__ hist) {
+                                                     int shift, uint32_t binmask,
+                                                     unsigned long long* __restrict__ hist) {
     __shared__ unsigned sh[2048];
     for (int i = threadIdx.x; i < 2048; i += SEL_NT) sh[i] = 0;
     __syncthreads();
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(SEL_NT) k_sel_hist(const LeafDesc* __restrict_
     for (int64_t q = threadIdx.x; q < cnt; q += SEL_NT) {
         const int64_t c = q / rows, r = q % rows;
         const uint32_t b = abits(near[L.near_off + c * L.ld + r]);
-        if ((b & pmask) == prefix) atomicAdd(&sh[(b >> shift) & 2047u], 1u);
+        if ((b & pmask) == prefix) atomicAdd(&sh[(b >> shift) & binmask], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 2048; i += SEL_NT)
@@ -369,7 +370,8 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
         int64_t in_bucket = 0;
         for (int pass = 0; pass < 3; ++pass) {
             HM_CUDA(cudaMemsetAsync(hist.p, 0, hist.bytes(), st));
-            k_sel_hist<<<nl, SEL_NT, 0, st>>>(H.leaves.p, d_true.p, H.near.p, prefix, pmask, shifts[pass], hist.p);
+            k_sel_hist<<<nl, SEL_NT, 0, st>>>(H.leaves.p, d_true.p, H.near.p, prefix, pmask, shifts[pass],
+                                              (1u << widths[pass]) - 1u, hist.p);
             HM_LAUNCH_CHECK();
             HM_CUDA(cudaMemcpyAsync(h.data(), hist.p, hist.bytes(), cudaMemcpyDeviceToHost, st));
             HM_CUDA(cudaStreamSynchronize(st));

@@ -540,7 +540,7 @@ struct ZRange {
 // ---- producer: one thread streams this CTA's chunks (and their operands) through the ring
 // (WAIT_T: wait for the preceding kernel -- the reduction producing t -- only before the
 // first chunk whose operand is t; near tiles read x, complete before that kernel began)
-template <class C, class V, int NR, bool WITH_Z, bool WAIT_T = false>
+template <class C, class V, int NR, bool WITH_Z, bool WAIT_T = false, int ST = STAGES>
 __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem_stage, int stage_stride,
                                         uint64_t* full, uint64_t* empty, int c0, int c1) {
     using ZR = ZRange<V, NR>;
@@ -555,9 +555,9 @@ __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem
                 waited = true;
             }
         }
-        const int q = i - c0, s = q % STAGES;
-        const uint32_t ph = (uint32_t)(q / STAGES) & 1u;
-        if (q >= STAGES) mbar_wait(empty + s, ph ^ 1u, a.err, 4);
+        const int q = i - c0, s = q % ST;
+        const uint32_t ph = (uint32_t)(q / ST) & 1u;
+        if (q >= ST) mbar_wait(empty + s, ph ^ 1u, a.err, 4);
         unsigned char* stg = smem_stage + (size_t)s * stage_stride;
         const void* src;
         uint32_t bytes;
@@ -588,13 +588,14 @@ __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem
     }
     // no copy may still be in flight when the CTA exits
     const int n = c1 - c0;
-    for (int q = std::max(0, n - STAGES); q < n; ++q)
-        mbar_wait(full + (q % STAGES), (uint32_t)(q / STAGES) & 1u, a.err, 8);
+    for (int q = std::max(0, n - ST); q < n; ++q)
+        mbar_wait(full + (q % ST), (uint32_t)(q / ST) & 1u, a.err, 8);
 }
 
+template <int ST = STAGES>
 __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int ncw) {
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, ncw);
         }
@@ -613,7 +614,7 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty, int n
 // that packed form), so d(col 0) + d(col 1) = U t for 16 rows.  Warp w = (kg, mg) takes
 // the k-tiles kg, kg + 4 of each slice and keeps m-tiles mg, mg + 4, mg + 8 of the leaf
 // in registers; at the flush each warp adds them to its own row of the reduction buffer.
-template <int MODE, class C, int NR, int RPL, int NCW, int RS>
+template <int MODE, class C, int NR, int RPL, int NCW, int RS, int ST = STAGES>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     constexpr bool TC2 = MODE == 0 && NR == 1 && RS == 1 && NCW == 16 && RPL == 6 &&
                          std::is_same<C, uint16_t>::value;
@@ -634,27 +635,27 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     constexpr int STRIDE = ZR::BYTES + STAGE_BYTES;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = (uint64_t*)smem;
-    uint64_t* empty = full + STAGES;
-    int* s_flag = (int*)(empty + STAGES);
-    uint16_t* zline = (uint16_t*)(smem + 96);  // a zeroed 16-byte line (ldmatrix rows outside a slice)
-    static_assert(2 * STAGES * 8 + 4 <= 96 && 96 + 16 <= BAR_BYTES, "barrier area layout");
+    uint64_t* empty = full + ST;
+    int* s_flag = (int*)(empty + ST);
+    uint16_t* zline = (uint16_t*)(smem + 112);  // a zeroed 16-byte line (ldmatrix rows outside a slice)
+    static_assert(2 * ST * 8 + 4 <= 112 && 112 + 16 <= BAR_BYTES, "barrier area layout");
     unsigned char* stage = smem + BAR_BYTES;
     constexpr int RPW = RPL / RS;  // rows per lane of one warp
     constexpr int NG = NCW / RS;   // column groups
     static_assert(RPL % RS == 0 && NCW % RS == 0, "row split must divide rows and warps");
-    Acc* red = (Acc*)(stage + (size_t)STAGES * STRIDE);  // [NG][32 RPL]
+    Acc* red = (Acc*)(stage + (size_t)ST * STRIDE);  // [NG][32 RPL]
     float* ty = (float*)(red + (size_t)NG * 32 * RPL);  // TC16: the leaf's tensor-core sums [16 RHS][TY_LD]
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < 8) zline[threadIdx.x] = 0;
-    init_ring(full, empty, NCW);
+    init_ring<ST>(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
     pdl_trigger();
     if (w == NCW) {
         // the t operand ranges come from the reduction: the producer waits for it before the
         // first U chunk, so the near tiles ahead of it stream while the reduction runs
-        if (lane == 0) produce<C, Vv, NR, true, true>(a, stage, STRIDE, full, empty, c0, c1);
+        if (lane == 0) produce<C, Vv, NR, true, true, ST>(a, stage, STRIDE, full, empty, c0, c1);
         return;
     }
     Vv* yc = (Vv*)a.out;
@@ -730,7 +731,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     for (int i = c0; i < c1; ++i) {
         const Chunk ch = nxt;
         if (i + 1 < c1) nxt = a.chunks[i + 1];
-        const int q = i - c0, s = q % STAGES;
+        const int q = i - c0, s = q % ST;
         if (ch.leaf != cur) {
             if (cur >= 0) flush();
             cur = ch.leaf;
@@ -753,7 +754,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 }
             }
         }
-        mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
+        mbar_wait(full + s, (uint32_t)(q / ST) & 1u, a.err, 1);
         const unsigned char* stg = stage + (size_t)s * STRIDE;
         const int64_t z0 = ch.zoff * a.nr;
         using Zin = typename AccT<MODE>::zin;  // same size as Vv
@@ -762,7 +763,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const int rows = 3 * L.n;
         if constexpr (TC16) {
             if (tc16 && ch.kind != 0) {
-                if (w < TC16_MT) {
+                if (w < TC16_MT && 16 * w < rows) {
                     float d16[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
                     const uint16_t* ub = (const uint16_t*)buf;
                     const int ld = ch.ld, ncols = ch.ncols;
@@ -848,7 +849,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         // Rows at or beyond `rows` read whatever follows the column in shared memory (the
         // next column, stage or the reduction buffer: always inside the allocation); their
         // accumulators are never flushed, so no bound check is needed per coefficient.
-        for (int c = g; c < ch.ncols; c += NG) {
+        // With several RHS a warp skips its row blocks past the leaf (leaves of fewer than
+        // 64 elements), a warp-uniform test; with one RHS the loop stays branch-free.
+        const int nact = NR == 1 ? RPW : max(0, min(RPW, (rows - rbase + 31) >> 5));
+        for (int c = g; c < ch.ncols && nact > 0; c += NG) {
             decltype(make_z(zin_zero<Zin>())) zv[NR];
             if constexpr (NR == 1)
                 zv[0] = make_z(zb[c]);
@@ -858,6 +862,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 const float* col = (const float*)buf + (size_t)c * ch.ld + rbase + lane;
 #pragma unroll
                 for (int ii = 0; ii < RPW; ++ii) {
+                    if (NR > 1 && ii >= nact) break;
                     const float v = col[32 * ii];
 #pragma unroll
                     for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
@@ -866,6 +871,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 const C* col = (const C*)buf + (size_t)c * ch.ld + rbase + lane;
 #pragma unroll
                 for (int ii = 0; ii < RPW; ++ii) {
+                    if (NR > 1 && ii >= nact) break;
                     const float v = coef(col, 32 * ii);
 #pragma unroll
                     for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
@@ -879,13 +885,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
 }
 
 // ---- phase 1: P = V_t^T xc_t, one partial per V column
-template <int MODE, class C, int NR, int RPL, int NCW>
+template <int MODE, class C, int NR, int RPL, int NCW, int ST = STAGES>
 __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     using Acc = typename AccT<MODE>::type;
     using Vv = typename AccT<MODE>::vec;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = (uint64_t*)smem;
-    uint64_t* empty = full + STAGES;
+    uint64_t* empty = full + ST;
     unsigned char* stage = smem + BAR_BYTES;
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
@@ -896,16 +902,16 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
         // such a read can reach (the ring and the tail after it) must then be finite, so the
         // ring is zeroed once before the first copy lands in it.
         uint4* z = reinterpret_cast<uint4*>(stage);
-        for (int i = threadIdx.x; i < (STAGES * STAGE_BYTES + P1_TAIL) / 16; i += blockDim.x)
+        for (int i = threadIdx.x; i < (ST * STAGE_BYTES + P1_TAIL) / 16; i += blockDim.x)
             z[i] = make_uint4(0u, 0u, 0u, 0u);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // before the copies write it
     }
-    init_ring(full, empty, NCW);
+    init_ring<ST>(full, empty, NCW);
     const int c0 = a.cta_begin[blockIdx.x], c1 = a.cta_begin[blockIdx.x + 1];
     pdl_trigger();
     if (w == NCW) {
         // the V coefficients are constant: the copies start while the gather drains
-        if (lane == 0) produce<C, Vv, NR, false>(a, stage, STAGE_BYTES, full, empty, c0, c1);
+        if (lane == 0) produce<C, Vv, NR, false, false, ST>(a, stage, STAGE_BYTES, full, empty, c0, c1);
         return;
     }
     pdl_wait();  // x in cluster order comes from the preceding kernel
@@ -920,7 +926,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
     for (int i = c0; i < c1; ++i) {
         const Chunk ch = nxt;
         if (i + 1 < c1) nxt = a.chunks[i + 1];
-        const int q = i - c0, s = q % STAGES;
+        const int q = i - c0, s = q % ST;
         if (ch.leaf != cur) {
             cur = ch.leaf;
             const LeafDesc L = a.leaves[cur];
@@ -936,7 +942,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
                                                               : zin_zero<Zin>());
             }
         }
-        mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
+        mbar_wait(full + s, (uint32_t)(q / ST) & 1u, a.err, 1);
         const C* buf = (const C*)(stage + (size_t)s * STAGE_BYTES);
         if constexpr (NR == 1) {
             // Four columns (w, w + NCW, w + 2 NCW, w + 3 NCW) per pass: their four warp sums
@@ -1147,36 +1153,40 @@ constexpr int ncw2_for(int NR) {
 }
 constexpr int rs_for(int NR) { return NR > 4 ? 2 : 1; }
 
-template <int MODE, class C, int NR, int RPL>
+// ST: ring depth; NCW1V / NCW2V: consumer warps of phase 1 / phase 2 (0: the default for
+// the right-hand-side count).  The tile-shape variants the autotuner chooses from use
+// other values for the single-RHS FP32-vector product.
+template <int MODE, class C, int NR, int RPL, int ST = STAGES, int NCW1V = 0, int NCW2V = 0>
 void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool timed, cudaStream_t st) {
-    constexpr int NCW = ncw1_for<MODE>(NR), NCW2 = ncw2_for<MODE>(NR), RS = rs_for(NR);
+    constexpr int NCW = NCW1V ? NCW1V : ncw1_for<MODE>(NR), NCW2 = NCW2V ? NCW2V : ncw2_for<MODE>(NR),
+                  RS = rs_for(NR);
     using Acc = typename AccT<MODE>::type;
     using V = typename AccT<MODE>::vec;
-    const size_t smem1 = BAR_BYTES + (size_t)STAGES * STAGE_BYTES + P1_TAIL;
+    const size_t smem1 = BAR_BYTES + (size_t)ST * STAGE_BYTES + P1_TAIL;
     // BF16 factors with 16 RHS on leaves of up to 192 rows: phase 1 on tensor cores
     constexpr bool kTensorPhase1 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
     // BF16 factors with one RHS: the U slices of phase 2 on tensor cores, which read t in
     // packed BF16 (hi, lo) form (phase 1 stays on the CUDA cores: one mma.sync per 16 x 16
     // tile did not keep up with the stream there)
     constexpr bool kTensorPhase2x1 = MODE == 0 && NR == 1 && std::is_same<C, uint16_t>::value && RPL == 6;
-    static_assert(!kTensorPhase2x1 || (ncw2_for<MODE>(NR) == 16 && rs_for(NR) == 1),
+    static_assert(!kTensorPhase2x1 || (NCW2 == 16 && rs_for(NR) == 1),
                   "the single-RHS tensor-core phase 2 assumes 16 consumer warps without row split");
     // BF16 factors with 16 RHS: the U slices of phase 2 on tensor cores as well, reading t
     // in the packed BF16 form of k_reduce_tb_pack16
     constexpr bool kTensorPhase2x16 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
-    const size_t smem2 = BAR_BYTES + (size_t)STAGES * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
+    const size_t smem2 = BAR_BYTES + (size_t)ST * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
                          (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc) + (kTensorPhase2x16 ? 16 * 196 * 4 : 0);
     // shared-memory opt-in, once per device for each instantiation
     static bool attr_done[64] = {};
     int dev = 0;
     HM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-        HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HM_CUDA(cudaFuncSetAttribute(k_phase1<MODE, C, NR, RPL, NCW, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem1));
         if constexpr (kTensorPhase1)
             HM_CUDA(cudaFuncSetAttribute(k_phase1_tc<NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
-        HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW2, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem2));
+        HM_CUDA(cudaFuncSetAttribute(k_phase2<MODE, C, NR, RPL, NCW2, RS, ST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
     if (H.n_far > 0 && H.p_len > 0) {
@@ -1189,7 +1199,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         if (tc)
             launch_pdl(k_phase1_tc<NCW>, dim3(H.grid), dim3((NCW + 1) * 32), smem1, st, a);
         else
-            launch_pdl(k_phase1<MODE, C, NR, RPL, NCW>, dim3(H.grid), dim3((NCW + 1) * 32), smem1, st, a);
+            launch_pdl(k_phase1<MODE, C, NR, RPL, NCW, ST>, dim3(H.grid), dim3((NCW + 1) * 32), smem1, st, a);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 2, st);
         using Zt = typename AccT<MODE>::zin;
@@ -1226,7 +1236,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     a.chunks = PL.ch2.p;
     a.cta_begin = PL.cta2.p;
     a.split = PL.split.p;
-    launch_pdl(k_phase2<MODE, C, NR, RPL, NCW2, RS>, dim3(H.grid), dim3((NCW2 + 1) * 32), smem2, st, a);
+    launch_pdl(k_phase2<MODE, C, NR, RPL, NCW2, RS, ST>, dim3(H.grid), dim3((NCW2 + 1) * 32), smem2, st, a);
     HM_LAUNCH_CHECK();
     if (timed) mark(H, 4, st);
 }
@@ -1237,6 +1247,25 @@ void launch_rpl(HMat& H, const HMat::Plan& PL, const StreamArgs& a, bool timed, 
         launch_phases<MODE, C, NR, 6>(H, PL, a, timed, st);
     else
         launch_phases<MODE, C, NR, 12>(H, PL, a, timed, st);
+}
+
+// The single-RHS FP32-vector product with the ring depth and consumer-warp count of the
+// H-matrix's tile shape (leaves of up to 64 elements); false if the shape is the default.
+// BF16 factors keep 16 warps in phase 2 (its tensor-core U slices assume them).
+template <class C>
+bool launch_shape_variant(HMat& H, const HMat::Plan& PL, const StreamArgs& a, bool timed, cudaStream_t st) {
+    const int ring = H.shape.ring, warps = H.shape.warps;
+    if (H.ld_max > 192 || (ring == STAGES && warps == 16)) return false;
+    constexpr bool b16 = std::is_same<C, uint16_t>::value;
+    if (ring == 6 && warps == 16)
+        launch_phases<0, C, 1, 6, 6>(H, PL, a, timed, st);
+    else if (ring == STAGES && warps == 8)
+        launch_phases<0, C, 1, 6, STAGES, 8, b16 ? 16 : 8>(H, PL, a, timed, st);
+    else if (ring == 6 && warps == 8)
+        launch_phases<0, C, 1, 6, 6, 8, b16 ? 16 : 8>(H, PL, a, timed, st);
+    else
+        fail(HM_EINVAL, "product: unsupported tile shape");
+    return true;
 }
 
 template <int MODE, class C>
@@ -1270,6 +1299,9 @@ void run_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, boo
     if (dtype == HM_F32) {
         a.tb = H.tbf.p;
         a.slots = H.slotsf.p;
+        if (nr == 1 && (fac == 1 ? launch_shape_variant<uint16_t>(H, PL, a, timed, st)
+                                 : launch_shape_variant<float>(H, PL, a, timed, st)))
+            return;
         if (fac == 1)
             launch_nr<0, uint16_t>(H, PL, a, nr, timed, st);
         else
@@ -1322,7 +1354,7 @@ void build_plan_for(HMat& H, HMat::Plan& PLAN, int esz, int G, cudaStream_t st) 
     // cut a segment into chunks: runs of consecutive operand indices, bounded in size
     auto cut = [&](std::vector<Chunk>& out, std::vector<int64_t>& bytes, int leaf, int kind, int64_t src,
                    const std::vector<int32_t>& idx, int cbase, int ncols, int ld, int elem) {
-        const int per = std::max(1, std::min(MAX_CHUNK_COLS, STAGE_BYTES / (ld * elem)));
+        const int per = std::max(1, std::min(H.shape.chunk_cols, H.shape.chunk_bytes / (ld * elem)));
         int c = 0;
         while (c < ncols) {
             int n = 1;

@@ -59,7 +59,8 @@ class hm_hmat_info(ctypes.Structure):
                 ("assemble_seconds", ctypes.c_double), ("storage", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("n_far_lowrank", ctypes.c_int64), ("n_far_dense", ctypes.c_int64),
                 ("u_entries", ctypes.c_int64), ("v_entries", ctypes.c_int64), ("tb_len", ctypes.c_int64),
-                ("p_len", ctypes.c_int64), ("n_far_refined", ctypes.c_int64), ("n_leaves", ctypes.c_int64)]
+                ("p_len", ctypes.c_int64), ("n_far_refined", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("coeff_blocks", ctypes.c_int64)]
 
 
 class hm_solve_opts(ctypes.Structure):
@@ -67,6 +68,22 @@ class hm_solve_opts(ctypes.Structure):
                 ("precond", ctypes.c_int), ("mode", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int), ("lp", ctypes.c_void_p),
                 ("ilu_p", ctypes.c_double)]
+
+
+class hm_tile_shape(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_int32), ("chunk_cols", ctypes.c_int32), ("ring", ctypes.c_int32),
+                ("warps", ctypes.c_int32)]
+
+
+DEFAULT_SHAPES = [(32768, 128, 4, 16), (16384, 128, 4, 16), (32768, 64, 4, 16), (16384, 64, 6, 16),
+                  (32768, 128, 6, 16), (32768, 128, 4, 8), (16384, 64, 4, 8), (8192, 32, 6, 16)]
+
+
+def _shape_array(shapes):
+    arr = (hm_tile_shape * len(shapes))()
+    for q, t in enumerate(shapes):
+        arr[q] = hm_tile_shape(*[int(v) for v in t])
+    return arr
 
 
 class hm_lp_info(ctypes.Structure):
@@ -129,7 +146,10 @@ SIGNATURES = [
     ("hm_lp_destroy", None, [_VP]),
     ("hm_matvec_graph", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_autotune", _I, [ctypes.POINTER(hm_elements), ctypes.POINTER(hm_assemble_opts), ctypes.POINTER(_I), _I,
-                         ctypes.POINTER(_D), _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
+                         ctypes.POINTER(_D), _I, _VP, _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
+    ("hm_hmat_set_tile_shape", _I, [_VP, ctypes.POINTER(hm_tile_shape), _VP]),
+    ("hm_hmat_get_tile_shape", _I, [_VP, ctypes.POINTER(hm_tile_shape)]),
+    ("hm_tune_tile_shape", _I, [_VP, _VP, _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
     ("hm_ilu_select", _I, [_I64, _VP, _VP, _VP, _D, _VP, ctypes.POINTER(_I64)]),
     ("hm_ilu_assemble", _I, [ctypes.c_int32, _I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                              ctypes.POINTER(_I64)]),
@@ -372,6 +392,27 @@ class HMatrix:
                                    lu.ctypes.data_as(_VP) if factor else None, sp))
         return dict(order=order, rowptr=rowptr, col=col, a_val=aval, lu_val=lu, n_colours=nc.value)
 
+    def set_tile_shape(self, shape, stream=None):
+        """shape: (chunk_bytes, chunk_cols, ring, warps); the product plans are cut again."""
+        t = hm_tile_shape(*[int(v) for v in shape])
+        _check(lib().hm_hmat_set_tile_shape(self.handle, ctypes.byref(t), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def tile_shape(self):
+        t = hm_tile_shape()
+        _check(lib().hm_hmat_get_tile_shape(self.handle, ctypes.byref(t)))
+        return (t.chunk_bytes, t.chunk_cols, t.ring, t.warps)
+
+    def tune_tile_shape(self, shapes=None, reps=20, stream=None):
+        """Time the single-RHS product under each shape and keep the fastest (hm_tune_tile_shape)."""
+        import json
+        shapes = list(shapes or DEFAULT_SHAPES)
+        arr = _shape_array(shapes)
+        cap = 1024 + 160 * len(shapes)
+        buf = ctypes.create_string_buffer(cap)
+        _check(lib().hm_tune_tile_shape(self.handle, arr, len(shapes), int(reps), buf, cap,
+                                        ctypes.c_void_p(_stream_ptr(stream))))
+        return json.loads(buf.value.decode())
+
     def timing(self, enable):
         _check(lib().hm_hmat_timing(self.handle, 1 if enable else 0))
 
@@ -490,7 +531,7 @@ class LearnedCorrection:
 
 # ------------------------------------------------------------------ autotuner
 
-def autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device):
+def autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device, shapes=()):
     """Cache key of a tuning run: the geometry (every element array), the assembly
     options, the candidate list and the device name."""
     import hashlib
@@ -498,20 +539,23 @@ def autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device):
     for k in ("c", "s1", "s2", "n", "a", "b"):
         h.update(np.ascontiguousarray(getattr(el, k), dtype=np.float64).tobytes())
     h.update(repr((int(el.N), float(E), float(nu), float(aca_eps), str(storage), tuple(int(v) for v in leaves),
-                   tuple(float(v) for v in etas), str(device))).encode())
+                   tuple(float(v) for v in etas), str(device), tuple(tuple(int(x) for x in t) for t in shapes))).encode())
     return h.hexdigest()[:32]
 
 
 def autotune(el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", leaves=(32, 64, 128), etas=(2.0,), budget_ms=60000,
-             cache=None, device=None, stream=None):
-    """Fastest (leaf size, eta) for the product on this geometry (hm_autotune).  With
-    `cache` (a JSON file path) a result for the same geometry, options, candidates and
-    device is read from the file instead of re-tuning, and new results are added to it."""
+             cache=None, device=None, stream=None, shapes=None):
+    """Fastest (leaf size, eta, tile shape) for the product on this geometry (hm_autotune);
+    shapes: (chunk_bytes, chunk_cols, ring, warps) candidates (None: the default shape only).
+    With `cache` (a JSON file
+    path) a result for the same geometry, options, candidates and device is read from the
+    file instead of re-tuning, and new results are added to it."""
     import json
     if device is None:
         import torch
         device = torch.cuda.get_device_name()
-    key = autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device)
+    shapes = list(shapes) if shapes else []
+    key = autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device, shapes)
     table = {}
     if cache and os.path.exists(cache):
         with open(cache) as f:
@@ -523,10 +567,11 @@ def autotune(el, E=1.0, nu=0.25, aca_eps=1e-6, storage="f32", leaves=(32, 64, 12
     opt = hm_assemble_opts(float(E), float(nu), float(aca_eps), st, 0, 0.0)
     lv = (_I * len(leaves))(*[int(v) for v in leaves])
     ev = (_D * len(etas))(*[float(v) for v in etas])
-    cap = 4096 + 256 * len(leaves) * len(etas)
+    sa = _shape_array(shapes) if shapes else None
+    cap = 4096 + 384 * len(leaves) * len(etas) * max(1, len(shapes))
     buf = ctypes.create_string_buffer(cap)
-    _check(lib().hm_autotune(ea.ref, ctypes.byref(opt), lv, len(leaves), ev, len(etas), int(budget_ms), buf, cap,
-                             ctypes.c_void_p(_stream_ptr(stream))))
+    _check(lib().hm_autotune(ea.ref, ctypes.byref(opt), lv, len(leaves), ev, len(etas), sa, len(shapes),
+                             int(budget_ms), buf, cap, ctypes.c_void_p(_stream_ptr(stream))))
     res = json.loads(buf.value.decode())
     res["device"] = device
     if cache:

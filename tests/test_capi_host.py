@@ -78,10 +78,14 @@ def test_bad_arguments_return_status(L):
     buf = ctypes.create_string_buffer(64)
     lv = (ctypes.c_int * 1)(200)
     ev = (ctypes.c_double * 1)(2.0)
-    assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 1, ev, 1, 0, buf, 64, None) == hmat.HM_EINVAL
+    assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 1, ev, 1, None, 0, 0, buf, 64, None) == hmat.HM_EINVAL
     assert "leaf" in hmat.last_error()
-    assert L.hm_autotune(ea.ref, None, lv, 1, ev, 1, 0, buf, 64, None) == hmat.HM_EINVAL
-    assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 0, ev, 1, 0, buf, 64, None) == hmat.HM_EINVAL
+    assert L.hm_autotune(ea.ref, None, lv, 1, ev, 1, None, 0, 0, buf, 64, None) == hmat.HM_EINVAL
+    assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 0, ev, 1, None, 0, 0, buf, 64, None) == hmat.HM_EINVAL
+    assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 1, ev, 1, None, 3, 0, buf, 64, None) == hmat.HM_EINVAL
+    t = hmat.hm_tile_shape(32768, 128, 4, 16)
+    assert L.hm_hmat_set_tile_shape(None, ctypes.byref(t), None) == hmat.HM_EINVAL
+    assert L.hm_tune_tile_shape(None, None, 0, 1, buf, 64, None) == hmat.HM_EINVAL
 
 
 def test_autotune_cache_key_and_hit_without_device(tmp_path, monkeypatch):

@@ -196,3 +196,55 @@ def test_autotune_picks_fastest_and_caches(dev, faults, tmp_path):
     one = hmat.autotune(el, E, float(nus[-1]), 1e-6, "f32", leaves=(16, 32), etas=(2.0,), budget_ms=0)
     assert one["tuned"] == 1 and one["best"]["leaf"] == 16
     os.remove(cache)
+
+
+def test_tile_shapes_give_the_same_product(dev, faults):
+    """Every tile shape the autotuner may choose (chunk bytes and columns, ring depth,
+    consumer warps) computes the batch product of the default shape to FP32 summation
+    order (the chunks, hence the order of the partial sums, change), for FP32 and BF16
+    factors and one and three right-hand sides; a shape outside the ranges is refused."""
+    import torch
+    els, nus = faults
+    trees, parts = assemble_parts(els, nus, 1e-6, storage="both")
+    B = hmat.HMatrix.batch(parts)
+    x = torch.as_tensor(synth.rhs_normal(B.ndof, 71, nrhs=3), dtype=torch.float32, device=dev)
+    ref = {}
+    for fac in ("f32", "bf16"):
+        for nr in (1, 3):
+            y = torch.empty_like(x[:nr])
+            B.matvec(x[:nr].contiguous(), y, factors=fac)
+            ref[fac, nr] = y.cpu().numpy().astype(np.float64)
+    for shape in hmat.DEFAULT_SHAPES[1:]:
+        B.set_tile_shape(shape)
+        assert B.tile_shape() == tuple(shape)
+        for fac in ("f32", "bf16"):
+            for nr in (1, 3):
+                y = torch.empty_like(x[:nr])
+                B.matvec(x[:nr].contiguous(), y, factors=fac)
+                B.check()
+                got = y.cpu().numpy().astype(np.float64)
+                assert rel(got, ref[fac, nr]) < 2e-6, (shape, fac, nr, rel(got, ref[fac, nr]))
+    with pytest.raises(hmat.HMError) as ei:
+        B.set_tile_shape((32768, 128, 5, 16))
+    assert ei.value.status == hmat.HM_EINVAL
+
+
+def test_tile_shape_tuning_keeps_the_fastest(dev, faults):
+    """hm_tune_tile_shape times every candidate and leaves the fastest on the H-matrix;
+    the autotuner searches shapes together with the leaf size."""
+    els, nus = faults
+    trees, parts = assemble_parts(els, nus, 1e-6)
+    B = hmat.HMatrix.batch(parts)
+    res = B.tune_tile_shape(reps=10)
+    cands = res["candidates"]
+    assert res["tuned"] == len(hmat.DEFAULT_SHAPES) == len(cands)
+    best = min(cands, key=lambda c: c["ms"])
+    assert res["best"]["ms"] == best["ms"]
+    key = (best["chunk_bytes"], best["chunk_cols"], best["ring"], best["warps"])
+    assert B.tile_shape() == key
+    at = hmat.autotune(els[-1], E, float(nus[-1]), 1e-6, "f32", leaves=(16, 32), etas=(2.0,), budget_ms=600000,
+                       shapes=hmat.DEFAULT_SHAPES[:3])
+    assert at["tuned"] == 6
+    b = min(at["candidates"], key=lambda c: c["ms"])
+    assert (at["best"]["leaf"], at["best"]["chunk_bytes"], at["best"]["chunk_cols"]) == (
+        b["leaf"], b["chunk_bytes"], b["chunk_cols"])

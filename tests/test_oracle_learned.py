@@ -136,3 +136,46 @@ def test_stats_give_least_squares_scaling():
             assert S[l, a] / S[l, 3 + a] == pytest.approx(ls, rel=1e-12)
     Q = Lr.samples([S, 2 * S])
     assert Q[:, 6:9].sum() == pytest.approx(1.0)
+
+
+def test_two_level_corrections_cannot_beat_block_jacobi_on_the_tangent():
+    """What a learned correction of leaf block-Jacobi B could gain on the tangent of a
+    crack crossing a fault (k log-uniform in [1e-3, 1e2] E/h): B^-1 A has all its
+    eigenvalues in a ring around 1 (|lambda| in [0.05, 2]), and a two-level correction
+    with the ideal coarse space of three columns per leaf -- the leaf restrictions of the
+    slowest modes of B^-1 A, an upper bound for any learned one -- saves at most two
+    GMRES iterations while the multiplicative form costs a second product per iteration;
+    the additive form saves none."""
+    import scipy.linalg as sla
+    from oracle import oracle as O
+    from paper_2605_14397_gb300 import synth
+    h = 0.15
+    el = synth.config_crack_fault(h=h)
+    T = O.cluster_tree(el, 64)
+    dofs = [O.dof_index(T.perm[T.begin[q]:T.end[q]]) for q in T.leaves()]
+    A = O.tangent_dense(O.dense_matrix(el, 1.0, 0.25), synth.k_loguniform(el.N, 1605001, E=1.0, h=h))
+    inv = O.block_jacobi_inverses(A, T)
+    b = synth.rhs_normal(A.shape[0], 1605008)
+    _, it_bj, ok, _ = O.gmres(lambda v: A @ v, b, lambda r: O.apply_block_jacobi(inv, r), tol=1e-8)
+    BA = np.zeros_like(A)
+    for d, Bi in inv:
+        BA[d] = Bi @ A[d]
+    w, V = np.linalg.eig(BA)
+    assert np.abs(w).min() > 0.04 and np.abs(w).max() < 2.0
+    slow = np.real(V[:, np.argsort(np.abs(w))[:12 * len(dofs)]])
+    Z = np.zeros((A.shape[0], 3 * len(dofs)))
+    for li, d in enumerate(dofs):
+        Z[d, 3 * li:3 * li + 3] = np.linalg.svd(slow[d], full_matrices=False)[0][:, :3]
+    lu = sla.lu_factor(Z.T @ A @ Z)
+    coarse = lambda r: Z @ sla.lu_solve(lu, Z.T @ r)
+    bj = lambda r: O.apply_block_jacobi(inv, r)
+
+    def mult(r):
+        y = bj(r)
+        return y + coarse(r - A @ y)
+
+    _, it_add, ok_a, _ = O.gmres(lambda v: A @ v, b, lambda r: bj(r) + coarse(r), tol=1e-8)
+    _, it_mul, ok_m, _ = O.gmres(lambda v: A @ v, b, mult, tol=1e-8)
+    assert ok and ok_a and ok_m
+    assert it_add >= it_bj and it_bj - 2 <= it_mul <= it_bj
+    assert 2 * it_mul > it_bj  # products: two per multiplicative iteration

@@ -6,10 +6,12 @@ path, a fixed memory budget): it keeps the geometry in a fixed scratch array in 
 library's device globals instead of a fresh allocation.  Its blocks must equal those of
 hm_influence_blocks (same tolerance as the other kernel tests: 1e-11 of each block's
 largest entry) on two calls in a row with different meshes, so the shared scratch left
-behind by one call does not leak into the next.  This file is collected last."""
+behind by one call does not leak into the next, and the CPU oracle's blocks on a sample
+of the pairs of both calls.  This file is collected last."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2605_14397_gb300 import hmat, synth
 
 pytestmark = pytest.mark.gpu
@@ -51,12 +53,14 @@ def test_matches_allocating_entry_point_on_two_calls_in_a_row(dev):
     sj1 = rng.integers(0, el1.N, 50000)
     a1, b1 = both(dev, el1, ri1, sj1)
     assert close(a1, b1)
+    assert close(O.influence_blocks(el1, E, NU, ri1[:3000], sj1[:3000]), b1[:3000])
     # call 2: a different, larger mesh and other material constants
     el2 = synth.config_three_planes(40)
     ri2 = rng.integers(0, el2.N, 80000)
     sj2 = rng.integers(0, el2.N, 80000)
     a2, b2 = both(dev, el2, ri2, sj2, 2.0, 0.3)
     assert close(a2, b2)
+    assert close(O.influence_blocks(el2, 2.0, 0.3, ri2[:3000], sj2[:3000]), b2[:3000])
 
 
 def test_error_word_is_cleared_between_calls(dev):

@@ -300,6 +300,13 @@ hm_status hm_ilu_export(const hm_hmat* h, const double* k_dev, double shift, dou
                         int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
                         double* a_val, double* lu_val, void* stream);
 
+/* z = (L U)^-1 r with the factors of the last ILU factorization of this H-matrix (made by
+ * hm_gmres_solve with HM_PRECOND_ILU or by hm_ilu_export with lu_val): forward
+ * substitution with the unit lower factor, backward substitution with the upper one, in
+ * FP64 on the device.  r_dev, z_dev: nrhs x 3N doubles, user order (must not overlap).
+ * HM_EINVAL if no factorization exists.  Asynchronous. */
+hm_status hm_ilu_apply(const hm_hmat* h, const double* r_dev, double* z_dev, int nrhs, void* stream);
+
 /* ---------------------------------------------------------------- batching
  * Independent faults: the operator of several non-interacting fractures is
  * block-diagonal, one block E_f per fault (eq. ElasSystem on each fault alone, each with

@@ -240,6 +240,14 @@ hm_status hm_ilu_export(const hm_hmat* hh, const double* k_dev, double shift, do
     HM_API_END
 }
 
+hm_status hm_ilu_apply(const hm_hmat* hh, const double* r_dev, double* z_dev, int nrhs, void* stream) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "ilu_apply: NULL H-matrix");
+    if (r_dev == z_dev) hm::fail(HM_EINVAL, "ilu_apply: r and z must not overlap");
+    hm::ilu_apply_user(const_cast<hm::HMat&>(hh->h), r_dev, z_dev, nrhs, (cudaStream_t)stream);
+    HM_API_END
+}
+
 hm_status hm_batch_create(const hm_hmat* const* hs, int nf, void* stream, hm_hmat** out) {
     HM_API_BEGIN
     hm::g_last_error.clear();

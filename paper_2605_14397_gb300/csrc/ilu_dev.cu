@@ -14,9 +14,9 @@
 //     handle them in parallel, one CTA per leaf, and each solve is one launch per colour;
 //   * CSR of the pattern in that order, the diagonal always present (E's entry if
 //     selected, else 0; -k - shift is added per factorization).
-// Factorization (per solve): ILU(0) in FP64, colour by colour, one warp per leaf taking
-// its rows in order (each row's multipliers in column order, the update from a finished
-// row confined to the pattern).  Application: forward and backward substitution in FP64,
+// Factorization (per solve): ILU(0) in FP64, level by level of the lower triangle (a row
+// waits for the rows its multipliers name), a warp per row (its multipliers in column
+// order, the update from a finished row confined to the pattern).  Application: forward and backward substitution in FP64,
 // colour by colour; the rows of one leaf are staged with their CSR block in shared memory
 // and solved by one warp, their couplings to other colours gathered by the whole CTA.
 #include <algorithm>
@@ -41,7 +41,12 @@ struct IluPlan {
     std::vector<int32_t> h_row0;       // new-order first row of each scheduled leaf
     int max_leaf_rows = 0;
     int64_t max_leaf_nnz = 0;
+    std::vector<int32_t> h_level_first;  // [n_levels + 1] into level_rows
+    DevBuf<int32_t> level_rows;        // rows grouped by level of the lower triangle
     DevBuf<int32_t> order, col, sched_row0, sched_nrows;
+    // per leaf (at its rows' positions): local rows ordered by level inside the leaf, and
+    // their levels, for the lower and the upper triangle
+    DevBuf<uint8_t> lrow_lo, llev_lo, lrow_up, llev_up;
     DevBuf<int64_t> rowptr, diagpos;
     DevBuf<double> aval, lu;
     DevBuf<double> yv, zv;             // new-order work vectors, nr x n
@@ -164,44 +169,44 @@ __device__ __forceinline__ int64_t find_col(const int32_t* __restrict__ col, int
     return -1;
 }
 
-// ILU(0) of the rows of the leaves of one colour: one warp per leaf, rows in order.
-__global__ void __launch_bounds__(32) k_ilu_factor(const int32_t* __restrict__ row0s,
-                                                   const int32_t* __restrict__ nrows,
-                                                   const int64_t* __restrict__ rowptr,
-                                                   const int32_t* __restrict__ col,
-                                                   const int64_t* __restrict__ diagpos, double* __restrict__ lu,
-                                                   int* __restrict__ err) {
-    const int lane = threadIdx.x;
-    const int32_t r0 = row0s[blockIdx.x], nr = nrows[blockIdx.x];
-    for (int32_t a = r0; a < r0 + nr; ++a) {
-        const int64_t beg = rowptr[a], dp = diagpos[a], end = rowptr[a + 1];
-        for (int64_t q = beg; q < dp; ++q) {
-            const int32_t b = col[q];
-            const double ub = lu[diagpos[b]];
-            const double l = lu[q] / ub;
-            if (!(ub != 0.0) || !isfinite(l)) {
-                if (lane == 0) atomicOr(err, 1);
-            }
-            __syncwarp();
-            if (lane == 0) lu[q] = l;
-            // row b of U times l off the entries of row a in the pattern (columns > b)
-            const int64_t bend = rowptr[b + 1];
-            for (int64_t t = diagpos[b] + 1 + lane; t < bend; t += 32) {
-                const int64_t pos = find_col(col, q + 1, end, col[t]);
-                if (pos >= 0) lu[pos] -= l * lu[t];
-            }
-            __syncwarp();
+// ILU(0) of a set of rows none of which depends on another (one level of the lower
+// triangle): a warp per row, its multipliers in column order, each taking the finished row
+// b of U times the multiplier off the row's entries in the pattern.
+__global__ void __launch_bounds__(256) k_ilu_factor_rows(const int32_t* __restrict__ rows, int count,
+                                                         const int64_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const int64_t* __restrict__ diagpos, double* __restrict__ lu,
+                                                         int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int wi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wi >= count) return;
+    const int32_t a = rows[wi];
+    const int64_t beg = rowptr[a], dp = diagpos[a], end = rowptr[a + 1];
+    for (int64_t q = beg; q < dp; ++q) {
+        const int32_t b = col[q];
+        const double ub = lu[diagpos[b]];
+        const double l = lu[q] / ub;
+        if (!(ub != 0.0) || !isfinite(l)) {
+            if (lane == 0) atomicOr(err, 1);
         }
+        __syncwarp();
+        if (lane == 0) lu[q] = l;
+        const int64_t bend = rowptr[b + 1];
+        for (int64_t t = diagpos[b] + 1 + lane; t < bend; t += 32) {
+            const int64_t pos = find_col(col, q + 1, end, col[t]);
+            if (pos >= 0) lu[pos] -= l * lu[t];
+        }
+        __syncwarp();
     }
 }
 
-// ---- application.  Shared memory per leaf: its CSR block (columns, values) and the
-// staged solution of its rows.
-struct LeafSmem {
-    int32_t* col;
-    double* val;
-    double* xs;
-};
+// ---- application.  One CTA per leaf of a colour; shared memory holds the leaf's CSR
+// block (values, columns), its rows' offsets into it, the staged solution of its rows and
+// the leaf's rows ordered by level of the triangle inside the leaf (a row waits only for
+// rows of the leaf its pattern names there, earlier for the lower, later for the upper
+// factor; entries to other leaves were finished by earlier launches).  Each level is
+// solved by the warps in parallel, a row per warp, between CTA barriers.
+constexpr int ILU_ROWS = 192;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -209,11 +214,65 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+struct LeafStage {
+    double* xs;        // [ILU_ROWS] solution of the leaf's rows
+    int32_t* rlo;      // [ILU_ROWS + 1] row starts relative to the block
+    int32_t* rdp;      // [ILU_ROWS] diagonal positions relative to the block
+    int32_t* bnd;      // [ILU_ROWS + 1] level boundaries in lrow
+    uint8_t* lrow;     // [ILU_ROWS] rows (local) by level
+    double* sval;      // [nnz] block values (staged) ...
+    int32_t* scol;     // [nnz] ... and columns
+};
+
+__device__ __forceinline__ LeafStage leaf_stage(unsigned char* dsm, int64_t nnz_staged) {
+    LeafStage L;
+    L.xs = reinterpret_cast<double*>(dsm);
+    L.rlo = reinterpret_cast<int32_t*>(L.xs + ILU_ROWS);
+    L.rdp = L.rlo + ILU_ROWS + 1;
+    L.bnd = L.rdp + ILU_ROWS;
+    L.lrow = reinterpret_cast<uint8_t*>(L.bnd + ILU_ROWS + 1);
+    L.sval = reinterpret_cast<double*>(dsm + 8 * ILU_ROWS + 4 * (3 * ILU_ROWS + 2) + ILU_ROWS + 8);
+    L.scol = reinterpret_cast<int32_t*>(L.sval + nnz_staged);
+    return L;
+}
+
+// bytes of shared memory before the staged block values (8-byte aligned)
+constexpr int ILU_STAGE_HEAD = 8 * ILU_ROWS + 4 * (3 * ILU_ROWS + 2) + ILU_ROWS + 8;
+
+// stage the leaf: block values and columns (if they fit), row offsets, levels; returns
+// the number of levels
+__device__ int stage_leaf(const LeafStage& S, int32_t r0, int rows, int64_t base, int64_t nnz, bool staged,
+                          const int64_t* __restrict__ rowptr, const int64_t* __restrict__ diagpos,
+                          const double* __restrict__ lu, const int32_t* __restrict__ col,
+                          const uint8_t* __restrict__ lrow_g, const uint8_t* __restrict__ llev_g) {
+    if (staged)
+        for (int64_t q = threadIdx.x; q < nnz; q += blockDim.x) {
+            S.sval[q] = lu[base + q];
+            S.scol[q] = col[base + q];
+        }
+    for (int i = threadIdx.x; i <= rows; i += blockDim.x) S.rlo[i] = (int32_t)(rowptr[r0 + i] - base);
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        S.rdp[i] = (int32_t)(diagpos[r0 + i] - base);
+        S.lrow[i] = lrow_g[r0 + i];
+    }
+    __syncthreads();
+    // level boundaries: positions where the (sorted) level changes
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const int lv = llev_g[r0 + i];
+        if (i == 0 || llev_g[r0 + i - 1] != lv) S.bnd[lv] = i;
+    }
+    const int nlev = rows > 0 ? (int)llev_g[r0 + rows - 1] + 1 : 0;
+    if (threadIdx.x == 0) S.bnd[nlev] = rows;
+    __syncthreads();
+    return nlev;
+}
+
 // forward substitution L y = v for the rows of the leaves of one colour (L unit lower):
 // v is the cluster-order input, y the new-order result
 __global__ void __launch_bounds__(256) k_ilu_fwd(const int32_t* __restrict__ row0s, const int32_t* __restrict__ nrows,
                                                  const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                  const int64_t* __restrict__ diagpos, const double* __restrict__ lu,
+                                                 const uint8_t* __restrict__ lrow_g, const uint8_t* __restrict__ llev_g,
                                                  const int32_t* __restrict__ order, const double* __restrict__ v,
                                                  double* __restrict__ y, int64_t n, int nr, int smem_nnz,
                                                  const int* __restrict__ done, int done_stride) {
@@ -221,46 +280,36 @@ __global__ void __launch_bounds__(256) k_ilu_fwd(const int32_t* __restrict__ row
     const int32_t r0 = row0s[blockIdx.x], rows = nrows[blockIdx.x];
     const int64_t base = rowptr[r0], nnz = rowptr[r0 + rows] - base;
     const bool staged = nnz <= smem_nnz;
-    double* xs = reinterpret_cast<double*>(dsm);                 // [rows]
-    double* sval = xs + 192;                                      // [nnz]
-    int32_t* scol = reinterpret_cast<int32_t*>(sval + (staged ? nnz : 0));
-    if (staged)
-        for (int64_t q = threadIdx.x; q < nnz; q += blockDim.x) {
-            sval[q] = lu[base + q];
-            scol[q] = col[base + q];
-        }
-    __syncthreads();
-    const double* cv = staged ? sval : lu + base;
-    const int32_t* cc = staged ? scol : col + base;
+    const LeafStage S = leaf_stage(dsm, staged ? nnz : 0);
+    const int nlev = stage_leaf(S, r0, rows, base, nnz, staged, rowptr, diagpos, lu, col, lrow_g, llev_g);
+    const double* cv = staged ? S.sval : lu + base;
+    const int32_t* cc = staged ? S.scol : col + base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = 0; k < nr; ++k) {
         if (done && done[k * done_stride]) continue;
         const double* vk = v + (int64_t)k * n;
         double* yk = y + (int64_t)k * n;
         // couplings to earlier colours (columns before the leaf), all rows at once
         for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-            const int32_t a = r0 + i;
-            double s = vk[order[a]];
-            for (int64_t q = rowptr[a] - base; q < diagpos[a] - base && cc[q] < r0; ++q) s -= cv[q] * yk[cc[q]];
-            xs[i] = s;
+            double s = vk[order[r0 + i]];
+            for (int q = S.rlo[i]; q < S.rdp[i] && cc[q] < r0; ++q) s -= cv[q] * yk[cc[q]];
+            S.xs[i] = s;
         }
         __syncthreads();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            for (int i = 0; i < rows; ++i) {
-                const int32_t a = r0 + i;
-                const int64_t lo = rowptr[a] - base, dp = diagpos[a] - base;
+        for (int lv = 0; lv < nlev; ++lv) {
+            for (int p = S.bnd[lv] + w; p < S.bnd[lv + 1]; p += nw) {
+                const int i = S.lrow[p];
                 double part = 0.0;
-                for (int64_t q = lo + lane; q < dp; q += 32) {
+                for (int q = S.rlo[i] + lane; q < S.rdp[i]; q += 32) {
                     const int32_t c = cc[q];
-                    if (c >= r0) part += cv[q] * xs[c - r0];
+                    if (c >= r0) part += cv[q] * S.xs[c - r0];
                 }
                 part = warp_sum(part);
-                if (lane == 0) xs[i] -= part;
-                __syncwarp();
+                if (lane == 0) S.xs[i] -= part;
             }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < rows; i += blockDim.x) yk[r0 + i] = xs[i];
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) yk[r0 + i] = S.xs[i];
         __syncthreads();
     }
 }
@@ -270,6 +319,7 @@ __global__ void __launch_bounds__(256) k_ilu_fwd(const int32_t* __restrict__ row
 __global__ void __launch_bounds__(256) k_ilu_bwd(const int32_t* __restrict__ row0s, const int32_t* __restrict__ nrows,
                                                  const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                  const int64_t* __restrict__ diagpos, const double* __restrict__ lu,
+                                                 const uint8_t* __restrict__ lrow_g, const uint8_t* __restrict__ llev_g,
                                                  const int32_t* __restrict__ order, const double* __restrict__ y,
                                                  double* __restrict__ z, double* __restrict__ out,
                                                  float* __restrict__ outf, int64_t n, int nr, int smem_nnz,
@@ -279,51 +329,41 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(const int32_t* __restrict__ row
     const int32_t r1 = r0 + rows;
     const int64_t base = rowptr[r0], nnz = rowptr[r1] - base;
     const bool staged = nnz <= smem_nnz;
-    double* xs = reinterpret_cast<double*>(dsm);
-    double* sval = xs + 192;
-    int32_t* scol = reinterpret_cast<int32_t*>(sval + (staged ? nnz : 0));
-    if (staged)
-        for (int64_t q = threadIdx.x; q < nnz; q += blockDim.x) {
-            sval[q] = lu[base + q];
-            scol[q] = col[base + q];
-        }
-    __syncthreads();
-    const double* cv = staged ? sval : lu + base;
-    const int32_t* cc = staged ? scol : col + base;
+    const LeafStage S = leaf_stage(dsm, staged ? nnz : 0);
+    const int nlev = stage_leaf(S, r0, rows, base, nnz, staged, rowptr, diagpos, lu, col, lrow_g, llev_g);
+    const double* cv = staged ? S.sval : lu + base;
+    const int32_t* cc = staged ? S.scol : col + base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = 0; k < nr; ++k) {
         if (done && done[k * done_stride]) continue;
         const double* yk = y + (int64_t)k * n;
         double* zk = z + (int64_t)k * n;
         // couplings to later colours (columns after the leaf)
         for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-            const int32_t a = r0 + i;
-            double s = yk[a];
-            for (int64_t q = rowptr[a + 1] - 1 - base; q > diagpos[a] - base && cc[q] >= r1; --q)
-                s -= cv[q] * zk[cc[q]];
-            xs[i] = s;
+            double s = yk[r0 + i];
+            for (int q = S.rlo[i + 1] - 1; q > S.rdp[i] && cc[q] >= r1; --q) s -= cv[q] * zk[cc[q]];
+            S.xs[i] = s;
         }
         __syncthreads();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            for (int i = rows - 1; i >= 0; --i) {
-                const int32_t a = r0 + i;
-                const int64_t dp = diagpos[a] - base, hi = rowptr[a + 1] - base;
+        for (int lv = 0; lv < nlev; ++lv) {
+            for (int p = S.bnd[lv] + w; p < S.bnd[lv + 1]; p += nw) {
+                const int i = S.lrow[p];
+                const int dp = S.rdp[i];
                 double part = 0.0;
-                for (int64_t q = dp + 1 + lane; q < hi; q += 32) {
+                for (int q = dp + 1 + lane; q < S.rlo[i + 1]; q += 32) {
                     const int32_t c = cc[q];
-                    if (c < r1) part += cv[q] * xs[c - r0];
+                    if (c < r1) part += cv[q] * S.xs[c - r0];
                 }
                 part = warp_sum(part);
-                if (lane == 0) xs[i] = (xs[i] - part) / cv[dp];
-                __syncwarp();
+                if (lane == 0) S.xs[i] = (S.xs[i] - part) / cv[dp];
             }
+            __syncthreads();
         }
-        __syncthreads();
         for (int i = threadIdx.x; i < rows; i += blockDim.x) {
             const int32_t a = r0 + i;
-            zk[a] = xs[i];
-            out[(int64_t)k * n + order[a]] = xs[i];
-            if (outf) outf[(int64_t)order[a] * nr + k] = (float)xs[i];
+            zk[a] = S.xs[i];
+            out[(int64_t)k * n + order[a]] = S.xs[i];
+            if (outf) outf[(int64_t)order[a] * nr + k] = (float)S.xs[i];
         }
         __syncthreads();
     }
@@ -332,8 +372,8 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(const int32_t* __restrict__ row
 unsigned gsz(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
 
 int64_t apply_smem_nnz(const IluPlan& P) {
-    // at most ~200 KB of staged CSR per leaf (12 bytes per entry) beside the row values
-    const int64_t cap = (200 * 1024 - 192 * 8) / 12;
+    // at most 200 KB of staged CSR per leaf (12 bytes per entry) beside the row data
+    const int64_t cap = (200 * 1024) / 12;
     return std::min<int64_t>(cap, P.max_leaf_nnz);
 }
 
@@ -468,7 +508,7 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
             for (int r = 0; r < 3 * L.n; ++r) P->h_order[pos++] = 3 * L.begin + r;
             P->max_leaf_rows = std::max(P->max_leaf_rows, 3 * L.n);
         }
-        if (P->max_leaf_rows > 192) fail(HM_EINVAL, "ilu: leaves of more than 64 elements are not supported");
+        if (P->max_leaf_rows > ILU_ROWS) fail(HM_EINVAL, "ilu: leaves of more than 64 elements are not supported");
         P->h_sched = sched;
         std::vector<int64_t> rp2(n + 1);
         std::vector<int32_t> cl2(m + n);
@@ -488,6 +528,20 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
             P->max_leaf_nnz = std::max(P->max_leaf_nnz, rp2[P->h_row0[s] + nrows[s]] - rp2[P->h_row0[s]]);
         cl2.resize(nnz2);
         vl2.resize(nnz2);
+        // levels of the lower triangle: the factorization runs level by level
+        {
+            std::vector<int32_t> lo(n), up(n);
+            int32_t nlo = 0, nup = 0;
+            hm_status s4 = hm_ilu_levels((int32_t)n, rp2.data(), cl2.data(), lo.data(), up.data(), &nlo, &nup);
+            if (s4 != HM_OK) fail(s4, "ilu: levels of the pattern failed");
+            std::vector<int32_t> cnt(nlo + 1, 0), rows_by(n);
+            for (int64_t a = 0; a < n; ++a) ++cnt[lo[a] + 1];
+            for (int q = 0; q < nlo; ++q) cnt[q + 1] += cnt[q];
+            P->h_level_first = cnt;
+            std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+            for (int64_t a = 0; a < n; ++a) rows_by[fill[lo[a]]++] = (int32_t)a;
+            P->level_rows.upload(rows_by, st);
+        }
         P->order.upload(P->h_order, st);
         P->rowptr.upload(rp2, st);
         P->col.upload(cl2, st);
@@ -496,6 +550,41 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
         P->lu.alloc(nnz2);
         P->sched_row0.upload(P->h_row0, st);
         P->sched_nrows.upload(nrows, st);
+        // levels inside each leaf (entries to other leaves are finished before)
+        {
+            std::vector<uint8_t> lrl(n), lvl(n), lru(n), lvu(n);
+            std::vector<int> lev(ILU_ROWS);
+            for (int s = 0; s < nl; ++s) {
+                const int32_t r0 = P->h_row0[s], nr = nrows[s], r1 = r0 + nr;
+                for (int pass = 0; pass < 2; ++pass) {
+                    int maxl = 0;
+                    for (int t = 0; t < nr; ++t) {
+                        const int i = pass == 0 ? t : nr - 1 - t;
+                        const int64_t a = r0 + i;
+                        int l = 0;
+                        for (int64_t q = rp2[a]; q < rp2[a + 1]; ++q) {
+                            const int32_t c = cl2[q];
+                            const bool dep = pass == 0 ? (c >= r0 && c < a) : (c > a && c < r1);
+                            if (dep) l = std::max(l, lev[c - r0] + 1);
+                        }
+                        lev[i] = l;
+                        maxl = std::max(maxl, l);
+                    }
+                    if (maxl > 255) fail(HM_EINVAL, "ilu: more than 256 levels inside a leaf");
+                    std::vector<int> idx(nr);
+                    std::iota(idx.begin(), idx.end(), 0);
+                    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return lev[x] < lev[y]; });
+                    for (int t = 0; t < nr; ++t) {
+                        (pass == 0 ? lrl : lru)[r0 + t] = (uint8_t)idx[t];
+                        (pass == 0 ? lvl : lvu)[r0 + t] = (uint8_t)lev[idx[t]];
+                    }
+                }
+            }
+            P->lrow_lo.upload(lrl, st);
+            P->llev_lo.upload(lvl, st);
+            P->lrow_up.upload(lru, st);
+            P->llev_up.upload(lvu, st);
+        }
         HM_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
         delete P;
@@ -510,11 +599,12 @@ void ilu_factor(HMat& H, const double* d_cluster, cudaStream_t st, int* err_dev)
     k_ilu_diag<<<gsz(P.n, 256), 256, 0, st>>>(P.lu.p, P.diagpos.p, P.order.p, d_cluster, P.n);
     HM_LAUNCH_CHECK();
     HM_CUDA(cudaMemsetAsync(err_dev, 0, sizeof(int), st));
-    for (int c = 0; c < P.n_colours; ++c) {
-        const int f = P.h_colour_first[c], e = P.h_colour_first[c + 1];
-        if (e <= f) continue;
-        k_ilu_factor<<<e - f, 32, 0, st>>>(P.sched_row0.p + f, P.sched_nrows.p + f, P.rowptr.p, P.col.p,
-                                           P.diagpos.p, P.lu.p, err_dev);
+    const int nlev = (int)P.h_level_first.size() - 1;
+    for (int l = 0; l < nlev; ++l) {
+        const int f = P.h_level_first[l], cnt = P.h_level_first[l + 1] - f;
+        if (cnt <= 0) continue;
+        k_ilu_factor_rows<<<gsz(cnt, 8), 256, 0, st>>>(P.level_rows.p + f, cnt, P.rowptr.p, P.col.p, P.diagpos.p,
+                                                        P.lu.p, err_dev);
         HM_LAUNCH_CHECK();
     }
     int e = 0;
@@ -534,12 +624,12 @@ void ilu_apply(HMat& H, const double* v, double* z, float* zf, int nr, const int
         P.nr_cap = nr;
     }
     const int64_t snnz = apply_smem_nnz(P);
-    const size_t smem = 192 * 8 + (size_t)snnz * 12;
+    const size_t smem = ILU_STAGE_HEAD + (size_t)snnz * 12;
     static bool attr_done[64] = {};
     int dev = 0;
     HM_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-        const int big = 200 * 1024 + 192 * 8;
+        const int big = 200 * 1024 + ILU_STAGE_HEAD;
         HM_CUDA(cudaFuncSetAttribute(k_ilu_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
         HM_CUDA(cudaFuncSetAttribute(k_ilu_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
@@ -548,19 +638,21 @@ void ilu_apply(HMat& H, const double* v, double* z, float* zf, int nr, const int
         const int f = P.h_colour_first[c], e = P.h_colour_first[c + 1];
         if (e <= f) continue;
         k_ilu_fwd<<<e - f, 256, smem, st>>>(P.sched_row0.p + f, P.sched_nrows.p + f, P.rowptr.p, P.col.p,
-                                            P.diagpos.p, P.lu.p, P.order.p, v, P.yv.p, P.n, nr, (int)snnz, done,
-                                            done_stride);
+                                            P.diagpos.p, P.lu.p, P.lrow_lo.p, P.llev_lo.p, P.order.p, v, P.yv.p, P.n,
+                                            nr, (int)snnz, done, done_stride);
         HM_LAUNCH_CHECK();
     }
     for (int c = P.n_colours - 1; c >= 0; --c) {
         const int f = P.h_colour_first[c], e = P.h_colour_first[c + 1];
         if (e <= f) continue;
         k_ilu_bwd<<<e - f, 256, smem, st>>>(P.sched_row0.p + f, P.sched_nrows.p + f, P.rowptr.p, P.col.p,
-                                            P.diagpos.p, P.lu.p, P.order.p, P.yv.p, P.zv.p, z, zf, P.n, nr,
-                                            (int)snnz, done, done_stride);
+                                            P.diagpos.p, P.lu.p, P.lrow_up.p, P.llev_up.p, P.order.p, P.yv.p, P.zv.p,
+                                            z, zf, P.n, nr, (int)snnz, done, done_stride);
         HM_LAUNCH_CHECK();
     }
 }
+
+bool ilu_is_factored(const HMat& H) { return H.ilu && H.ilu->factored; }
 
 void ilu_export(HMat& H, int64_t* n_out, int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr,
                 int32_t* col, double* a_val, double* lu_val, cudaStream_t st) {

@@ -15,6 +15,7 @@ void ilu_factor(HMat& H, const double* d_cluster, cudaStream_t st, int* err_dev)
 // given, receives the FP32 copy RHS-interleaved; done[k * done_stride] != 0 skips RHS k.
 void ilu_apply(HMat& H, const double* v, double* z, float* zf, int nr, const int* done, int done_stride,
                cudaStream_t st);
+bool ilu_is_factored(const HMat& H);
 // Sizes, order (new position -> cluster DOF position), CSR pattern, values before and
 // after the factorization, to host arrays (any may be NULL).
 void ilu_export(HMat& H, int64_t* n_out, int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr,

@@ -1071,6 +1071,19 @@ void ilu_export_for(HMat& H, const double* kel, double shift, double p, int64_t*
     ilu_export(H, n_out, nnz_out, n_colours_out, order, rowptr, col, a_val, lu_val, st);
 }
 
+// z = (L U)^-1 r for user-ordered vectors with the last ILU factorization
+void ilu_apply_user(HMat& H, const double* r, double* z, int nrhs, cudaStream_t st) {
+    if (nrhs < 1 || nrhs > 16) fail(HM_EINVAL, "ilu_apply: 1 to 16 right-hand sides");
+    if (!r || !z) fail(HM_EINVAL, "ilu_apply: NULL vector");
+    if (!ilu_is_factored(H)) fail(HM_EINVAL, "ilu_apply: no ILU factorization on this H-matrix");
+    SolveWS& W = workspace(H, nrhs, 1, st);
+    k_to_cluster<<<g1(H.ndof * nrhs), 256, 0, st>>>(r, W.r.p, H.perm.p, H.ndof, nrhs);
+    HM_LAUNCH_CHECK();
+    ilu_apply(H, W.r.p, W.w.p, nullptr, nrhs, nullptr, 0, st);
+    k_to_user<<<g1(H.ndof * nrhs), 256, 0, st>>>(W.w.p, z, H.perm.p, H.ndof, nrhs);
+    HM_LAUNCH_CHECK();
+}
+
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp) {
     using clk = std::chrono::steady_clock;

@@ -128,6 +128,7 @@ SIGNATURES = [
     ("hm_gmres_solve", _I, [_VP, _VP, _D, _VP, _VP, _I, ctypes.POINTER(hm_solve_opts),
                             ctypes.POINTER(hm_solve_info), _VP]),
     ("hm_batch_create", _I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
+    ("hm_ilu_apply", _I, [_VP, _VP, _VP, _I, _VP]),
     ("hm_ilu_export", _I, [_VP, _VP, _D, _D, _P64, _P64, ctypes.POINTER(ctypes.c_int32), _VP, _VP, _VP, _VP, _VP,
                            _VP]),
     ("hm_lp_param_count", _I64, [_I]),
@@ -412,6 +413,12 @@ class HMatrix:
         _check(lib().hm_tune_tile_shape(self.handle, arr, len(shapes), int(reps), buf, cap,
                                         ctypes.c_void_p(_stream_ptr(stream))))
         return json.loads(buf.value.decode())
+
+    def ilu_apply(self, r, z, stream=None):
+        """z = (L U)^-1 r with the last ILU factorization (float64 CUDA tensors (3N,) or (nrhs, 3N))."""
+        nrhs = 1 if r.dim() == 1 else r.shape[0]
+        assert r.is_contiguous() and z.is_contiguous()
+        _check(lib().hm_ilu_apply(self.handle, _dptr(r), _dptr(z), int(nrhs), ctypes.c_void_p(_stream_ptr(stream))))
 
     def timing(self, enable):
         _check(lib().hm_hmat_timing(self.handle, 1 if enable else 0))

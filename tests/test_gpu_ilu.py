@@ -9,6 +9,8 @@
 * Factors: the oracle's ILU(0) of the exported matrix (selected entries, -k - shift on
   the diagonal, in the exported order) equals the library's factors entry by entry to
   1e-12 of each row's largest entry.
+* Triangular solves: hm_ilu_apply equals the oracle's forward and backward substitution
+  with those factors, entry by entry (1e-12 of the largest entry).
 * Solves: GMRES with the ILU preconditioner reaches 1e-8, matches the dense LU solution
   and takes the oracle GMRES's iteration count with the oracle's ILU preconditioner
   (within 2), for p = 0.01 and 0.05; p = 0.05 needs no more iterations than leaf
@@ -160,3 +162,25 @@ def test_ilu_in_the_mixed_solver_and_several_rhs(dev, cases):
         xq = torch.zeros_like(B[q])
         H.solve(B[q].contiguous(), xq, k, precond="ilu")
         assert torch.linalg.norm(X[q] - xq) <= 1e-7 * torch.linalg.norm(xq)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_triangular_solves_match_the_oracle(dev, cases, name):
+    import torch
+    el, To, H, A, h = cases[name]
+    k = k_of(el, h, 36)
+    ex = H.ilu_export(torch.as_tensor(k, device=dev), 0.0, p=0.01)
+    order, rp, col, lu = ex["order"], ex["rowptr"], ex["col"], ex["lu_val"]
+    n = order.size
+    L = [{int(col[q]): lu[q] for q in range(rp[a], rp[a + 1]) if col[q] < a} for a in range(n)]
+    U = [{int(col[q]): lu[q] for q in range(rp[a], rp[a + 1]) if col[q] >= a} for a in range(n)]
+    cd = IL.cluster_dofs(To)
+    user = cd[order]  # factorization position -> user DOF
+    R = synth.rhs_normal(n, 37, nrhs=2)
+    Z = torch.empty((2, n), dtype=torch.float64, device=dev)
+    H.ilu_apply(torch.as_tensor(R, device=dev).contiguous(), Z)
+    Z = Z.cpu().numpy()
+    for q in range(2):
+        ref = np.empty(n)
+        ref[user] = IL.ilu0_solve(L, U, R[q][user])
+        assert np.abs(Z[q] - ref).max() <= 1e-12 * np.abs(ref).max()

@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-gmres", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--grid", type=int, default=256, help="disk grid size (256: the 51,468-element fault)")
+    p.add_argument("--planes-grid", type=int, default=300,
+                   help="grid of each plane of the planes workload (300: 270,000 elements)")
     p.add_argument("--lp-h", type=float, default=0.01, help="element size of the crack + fault (learned workload)")
     p.add_argument("--lp-train", type=int, default=2000, help="training systems (learned workload)")
     p.add_argument("--workload", default="fault", choices=["fault", "faults64", "planes", "learned", "ilu"],
@@ -317,7 +319,7 @@ def run_planes(args, dev, torch, hmat, synth):
     single-RHS products, and GMRES to 1e-8 on all 16 at once (restart 30) against 16
     sequential solves."""
     import numpy as np
-    el = synth.config_three_planes(300)
+    el = synth.config_three_planes(args.planes_grid)
     E, nu, eps, nr = 1.0, 0.25, 1e-5, 16
     t0 = time.perf_counter()
     T = hmat.ClusterTree(el, 64, 2.0)
@@ -384,8 +386,9 @@ def run_planes(args, dev, torch, hmat, synth):
             "ms_per_step": res["bf16_16rhs_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 factors x bf16 hi+lo vectors on tensor cores, f32 near field and accumulation",
             "data": "synthetic (seeded mesh and right-hand sides)",
-            "config": {"workload": "three intersecting 300x300 planes (third shifted h/4): N=270000, 810000 DOFs, "
-                                   "leaf 64, eta 2, ACA eps 1e-5, 16 RHS N(0,1)",
+            "config": {"workload": "three intersecting %dx%d planes (third shifted h/4): N=%d, %d DOFs, "
+                                   "leaf 64, eta 2, ACA eps 1e-5, 16 RHS N(0,1)" % (args.planes_grid, args.planes_grid,
+                                                                                    el.N, 3 * el.N),
                        "setup_s": t_setup, "rank_mean": info["rank_mean"], "rank_max": info["rank_max"],
                        "stored_bytes": info["stored_bytes"], "bytes_16rhs_bf16": b16_bf16,
                        "bytes_16rhs_f32": b16_f32,
@@ -405,7 +408,7 @@ def run_planes(args, dev, torch, hmat, synth):
         # the tangent A = E - diag(k), k log-uniform in [1e-3, 1e2] E/h per element: the bare
         # E of three intersecting planes is indefinite and nearly singular (GMRES with
         # block-Jacobi stalls on it even at a few thousand elements), the tangent is not
-        k = torch.as_tensor(synth.k_loguniform(el.N, 1605, E=E, h=2.0 / 300), device=dev)
+        k = torch.as_tensor(synth.k_loguniform(el.N, 1605, E=E, h=2.0 / args.planes_grid), device=dev)
         B = torch.as_tensor(synth.rhs_normal(nd, 1603, nrhs=nr), dtype=torch.float64, device=dev).contiguous()
         Xs = torch.zeros_like(B)
         g = {"system": "E - diag(k), k ~ logU[1e-3, 1e2] E/h (seed 1605)", "restart": 50, "maxit": 1000,

@@ -434,9 +434,18 @@ hm_status hm_lp_load(const char* path, hm_lp** out);
 void hm_lp_destroy(hm_lp* lp);
 
 /* Synchronise `stream` and report whether a device-side wait of an earlier product on
- * this H-matrix gave up (HM_ETIMEOUT; the flags are then cleared).  The product kernels
- * bound every wait on their copy pipeline instead of spinning forever. */
+ * this H-matrix gave up (HM_ETIMEOUT; the flags and the product's split-row arrival
+ * counts are then cleared).  The product kernels bound every wait on their copy
+ * pipeline instead of spinning forever. */
 hm_status hm_hmat_check(const hm_hmat* h, void* stream);
+
+/* Limit of the product's bounded waits, limit_s in [1e-6, 10] seconds (default 2), and a
+ * switch for testing the failure path: withhold_chunk >= 0 makes the producer of the
+ * row phase stop before that chunk of its plan (the copies of that chunk and of the
+ * later chunks of its CTA are never issued), so that the consumers' waits run out; the
+ * product is then garbage and hm_hmat_check returns HM_ETIMEOUT.  -1 turns it off.
+ * Host-side settings of this H-matrix; product graphs captured before are dropped. */
+hm_status hm_hmat_set_wait(hm_hmat* h, double limit_s, int64_t withhold_chunk);
 
 /* ---------------------------------------------------------------- ILU building blocks
  * Sec. 3.3.1 preconditions the mechanical block with an incomplete LU factorization of

@@ -335,6 +335,17 @@ hm_status hm_tune_tile_shape(hm_hmat* hh, const hm_tile_shape* shapes, int n_sha
     HM_API_END
 }
 
+hm_status hm_hmat_set_wait(hm_hmat* hh, double limit_s, int64_t withhold_chunk) {
+    HM_API_BEGIN
+    if (!hh) hm::fail(HM_EINVAL, "hmat_set_wait: NULL H-matrix");
+    if (!(limit_s >= 1e-6 && limit_s <= 10.0)) hm::fail(HM_EINVAL, "hmat_set_wait: limit must lie in [1e-6, 10] s");
+    if (withhold_chunk < -1) hm::fail(HM_EINVAL, "hmat_set_wait: withhold_chunk must be -1 or a chunk index");
+    hm::graphs_clear(hh->h);  // captured products hold the old arguments
+    hh->h.wait_ns = (uint64_t)(limit_s * 1e9);
+    hh->h.withhold_chunk = withhold_chunk;
+    HM_API_END
+}
+
 hm_status hm_hmat_check(const hm_hmat* hh, void* stream) {
     HM_API_BEGIN
     if (!hh) hm::fail(HM_EINVAL, "hmat_check: NULL H-matrix");

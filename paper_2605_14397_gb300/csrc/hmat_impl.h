@@ -143,6 +143,8 @@ struct HMat {
     } plan[2];
     DevBuf<int32_t> counters;
     DevBuf<int> err;
+    uint64_t wait_ns = 2000000000ull;  // limit of the product's bounded waits
+    int64_t withhold_chunk = -1;       // test switch of hm_hmat_set_wait (-1: off)
     std::vector<int64_t> h_self_off;  // near-stream offset of each leaf's diagonal tile
     // per leaf: the first columns of its near block that belong to inadmissible leaf pairs
     // (the near field proper; admissible blocks stored dense follow them)

@@ -529,6 +529,11 @@ struct StreamArgs {
     int nr;       // right-hand sides in this launch (<= NR); also the interleave stride
     int ld_max;
     const int* skip;  // optional device flag: when set, the kernels return at once
+    uint64_t wait_ns; // limit of every bounded wait of the copy ring
+    // test switch (hm_hmat_set_wait): the producer of phase 2 stops before this chunk of
+    // the plan (its copy and every later one of the CTA are never issued), so that the
+    // consumers' waits run out; -1: off
+    int64_t withhold;
 };
 
 template <class V, int NR>
@@ -545,8 +550,13 @@ __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem
                                         uint64_t* full, uint64_t* empty, int c0, int c1) {
     using ZR = ZRange<V, NR>;
     bool waited = false;
+    int issued = c1 - c0;  // copies issued (all of them unless the test switch stops early)
     Chunk nxt = c0 < c1 ? a.chunks[c0] : Chunk{};
     for (int i = c0; i < c1; ++i) {
+        if (WITH_Z && i == a.withhold) {
+            issued = i - c0;
+            break;
+        }
         const Chunk ch = nxt;
         if (i + 1 < c1) nxt = a.chunks[i + 1];
         if constexpr (WAIT_T) {
@@ -557,7 +567,7 @@ __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem
         }
         const int q = i - c0, s = q % ST;
         const uint32_t ph = (uint32_t)(q / ST) & 1u;
-        if (q >= ST) mbar_wait(empty + s, ph ^ 1u, a.err, 4);
+        if (q >= ST) mbar_wait(empty + s, ph ^ 1u, a.err, 4, a.wait_ns);
         unsigned char* stg = smem_stage + (size_t)s * stage_stride;
         const void* src;
         uint32_t bytes;
@@ -587,9 +597,9 @@ __device__ __forceinline__ void produce(const StreamArgs& a, unsigned char* smem
         if (!waited) pdl_wait();
     }
     // no copy may still be in flight when the CTA exits
-    const int n = c1 - c0;
+    const int n = issued;
     for (int q = std::max(0, n - ST); q < n; ++q)
-        mbar_wait(full + (q % ST), (uint32_t)(q / ST) & 1u, a.err, 8);
+        mbar_wait(full + (q % ST), (uint32_t)(q / ST) & 1u, a.err, 8, a.wait_ns);
 }
 
 template <int ST = STAGES>
@@ -643,8 +653,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
     constexpr int RPW = RPL / RS;  // rows per lane of one warp
     constexpr int NG = NCW / RS;   // column groups
     static_assert(RPL % RS == 0 && NCW % RS == 0, "row split must divide rows and warps");
-    Acc* red = (Acc*)(stage + (size_t)ST * STRIDE);  // [NG][32 RPL]
-    float* ty = (float*)(red + (size_t)NG * 32 * RPL);  // TC16: the leaf's tensor-core sums [16 RHS][TY_LD]
+    // FP32 vectors with 16 RHS on leaves of up to 64 elements reduce 8 RHS per pass of the
+    // flush (4 barriers per leaf instead of 32); the other variants one RHS per pass (their
+    // reduction buffer would not fit beside the ring)
+    constexpr int KP = (MODE == 0 && NR == 16 && RPL == 6) ? 8 : 1;
+    Acc* red = (Acc*)(stage + (size_t)ST * STRIDE);  // [KP][NG][32 RPL]
+    float* ty = (float*)(red + (size_t)KP * NG * 32 * RPL);  // TC16: the leaf's tensor-core sums [16 RHS][TY_LD]
 
     if (a.skip && *(volatile const int*)a.skip) return;  // every right-hand side already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -672,12 +686,16 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
         const int rows = 3 * L.n;
         const bool whole = sp.nparts == 1;
         const int64_t slot = whole ? 0 : (int64_t)(sp.slot_base + (int)blockIdx.x - sp.w_first);
-        // k unrolled at compile time: a runtime index into acc would move it to local memory
+        // KP right-hand sides per reduction pass through red (k unrolled at compile time: a
+        // runtime index into acc would move it to local memory)
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            if (k >= a.nr) break;
+        for (int k0 = 0; k0 < NR; k0 += KP) {
+            if (k0 >= a.nr) break;
 #pragma unroll
-            for (int i = 0; i < RPW; ++i) red[(size_t)g * (32 * RPL) + rbase + lane + 32 * i] = acc[k][i];
+            for (int kk = 0; kk < KP; ++kk)
+#pragma unroll
+                for (int i = 0; i < RPW; ++i)
+                    red[((size_t)kk * NG + g) * (32 * RPL) + rbase + lane + 32 * i] = acc[k0 + kk][i];
             if constexpr (TC2) {
                 // lanes 4 c hold rows 16 mt + c (d0 + d1) and 16 mt + c + 8 (d2 + d3)
                 __syncwarp();
@@ -691,9 +709,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 }
             }
             consumer_sync(NCW * 32);
-            for (int r = threadIdx.x; r < rows; r += NCW * 32) {
-                Acc s = red[r];
-                for (int q = 1; q < NG; ++q) acc_add(s, red[(size_t)q * (32 * RPL) + r]);
+            for (int e = threadIdx.x; e < KP * rows; e += NCW * 32) {
+                const int kk = e / rows, r = e - kk * rows, k = k0 + kk;
+                if (k >= a.nr) continue;
+                const Acc* rk = red + (size_t)kk * NG * (32 * RPL);
+                Acc s = rk[r];
+                for (int q = 1; q < NG; ++q) acc_add(s, rk[(size_t)q * (32 * RPL) + r]);
                 if constexpr (TC16) {
                     if (tc16) acc_add(s, ty[(size_t)k * TY_LD + r]);
                 }
@@ -754,7 +775,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 }
             }
         }
-        mbar_wait(full + s, (uint32_t)(q / ST) & 1u, a.err, 1);
+        mbar_wait(full + s, (uint32_t)(q / ST) & 1u, a.err, 1, a.wait_ns);
         const unsigned char* stg = stage + (size_t)s * STRIDE;
         const int64_t z0 = ch.zoff * a.nr;
         using Zin = typename AccT<MODE>::zin;  // same size as Vv
@@ -942,7 +963,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
                                                               : zin_zero<Zin>());
             }
         }
-        mbar_wait(full + s, (uint32_t)(q / ST) & 1u, a.err, 1);
+        mbar_wait(full + s, (uint32_t)(q / ST) & 1u, a.err, 1, a.wait_ns);
         const C* buf = (const C*)(stage + (size_t)s * STAGE_BYTES);
         if constexpr (NR == 1) {
             // Four columns (w, w + NCW, w + 2 NCW, w + 3 NCW) per pass: their four warp sums
@@ -1069,7 +1090,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1_tc(StreamArgs a) {
                     bl[kt][hh] = lo2;
                 }
         }
-        mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1);
+        mbar_wait(full + s, (uint32_t)(q / STAGES) & 1u, a.err, 1, a.wait_ns);
         const uint16_t* buf = (const uint16_t*)(stage + (size_t)s * STAGE_BYTES);
         const int ld = ch.ld, ncols = ch.ncols;
         const int mtiles = (ncols + 15) >> 4;
@@ -1174,8 +1195,9 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     // BF16 factors with 16 RHS: the U slices of phase 2 on tensor cores as well, reading t
     // in the packed BF16 form of k_reduce_tb_pack16
     constexpr bool kTensorPhase2x16 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
+    constexpr int KP = (MODE == 0 && NR == 16 && RPL == 6) ? 8 : 1;  // RHS per flush pass of k_phase2
     const size_t smem2 = BAR_BYTES + (size_t)ST * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
-                         (size_t)(NCW2 / RS) * 32 * RPL * sizeof(Acc) + (kTensorPhase2x16 ? 16 * 196 * 4 : 0);
+                         (size_t)KP * (NCW2 / RS) * 32 * RPL * sizeof(Acc) + (kTensorPhase2x16 ? 16 * 196 * 4 : 0);
     // shared-memory opt-in, once per device for each instantiation
     static bool attr_done[64] = {};
     int dev = 0;
@@ -1294,6 +1316,8 @@ void run_core(HMat& H, const void* xc, void* yc, int nr, int dtype, int fac, boo
     a.nr = nr;
     a.ld_max = H.ld_max;
     a.skip = skip;
+    a.wait_ns = H.wait_ns;
+    a.withhold = H.withhold_chunk;
     a.xc = xc;
     a.out = yc;
     if (dtype == HM_F32) {
@@ -1553,7 +1577,12 @@ int product_error_flags(HMat& H, cudaStream_t st) {
     int e = 0;
     HM_CUDA(cudaMemcpyAsync(&e, H.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
-    if (e) HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
+    if (e) {
+        HM_CUDA(cudaMemsetAsync(H.err.p, 0, sizeof(int), st));
+        // a product that gave up waiting may leave split-leaf arrival counts behind
+        HM_CUDA(cudaMemsetAsync(H.counters.p, 0, H.counters.bytes(), st));
+        HM_CUDA(cudaStreamSynchronize(st));
+    }
     return e;
 }
 

@@ -45,16 +45,17 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the phase of `parity` to complete; give up after ~2 s of wall time, set bit
-// `flag` in *err and return false (the caller carries on with the same control flow, so
-// no barrier is left unmatched; its data are then garbage and the host reports
-// HM_ETIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int flag) {
+// Wait for the phase of `parity` to complete; give up after limit_ns of wall time (the
+// product's default is 2 s), set bit `flag` in *err and return false (the caller carries
+// on with the same control flow, so no barrier is left unmatched; its data are then
+// garbage and the host reports HM_ETIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int flag,
+                                          uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) {
+        if (global_ns() - t0 > limit_ns) {
             atomicOr(err, flag);
             return false;
         }

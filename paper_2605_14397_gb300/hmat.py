@@ -121,6 +121,7 @@ SIGNATURES = [
     ("hm_hmat_destroy", None, [_VP]),
     ("hm_matvec", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_hmat_check", _I, [_VP, _VP]),
+    ("hm_hmat_set_wait", _I, [_VP, _D, _I64]),
     ("hm_matvec_host", _I, [_VP, _VP, _VP, _I, _I, _VP]),
     ("hm_matvec_factors", _I, [_VP, _VP, _VP, _I, _I, _I, _VP]),
     ("hm_hmat_timing", _I, [_VP, _I]),
@@ -428,6 +429,11 @@ class HMatrix:
         out = (ctypes.c_double * 6)()
         _check(lib().hm_hmat_timing_read(self.handle, out))
         return dict(gather=out[0], phase1=out[1], reduce=out[2], phase2=out[3], scatter=out[4], count=int(out[5]))
+
+    def set_wait(self, limit_s=2.0, withhold_chunk=-1):
+        """Limit of the product's bounded waits; withhold_chunk >= 0 is a test switch that makes
+        the row phase's producer stop before that chunk, so that the waits run out."""
+        _check(lib().hm_hmat_set_wait(self.handle, float(limit_s), int(withhold_chunk)))
 
     def check(self, stream=None):
         """Synchronise and raise HMError(HM_ETIMEOUT) if a product kernel gave up waiting."""

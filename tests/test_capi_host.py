@@ -83,6 +83,7 @@ def test_bad_arguments_return_status(L):
     assert L.hm_autotune(ea.ref, None, lv, 1, ev, 1, None, 0, 0, buf, 64, None) == hmat.HM_EINVAL
     assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 0, ev, 1, None, 0, 0, buf, 64, None) == hmat.HM_EINVAL
     assert L.hm_autotune(ea.ref, ctypes.byref(opt), lv, 1, ev, 1, None, 3, 0, buf, 64, None) == hmat.HM_EINVAL
+    assert L.hm_hmat_set_wait(None, 1.0, -1) == hmat.HM_EINVAL
     t = hmat.hm_tile_shape(32768, 128, 4, 16)
     assert L.hm_hmat_set_tile_shape(None, ctypes.byref(t), None) == hmat.HM_EINVAL
     assert L.hm_tune_tile_shape(None, None, 0, 1, buf, 64, None) == hmat.HM_EINVAL

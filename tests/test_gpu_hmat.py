@@ -303,3 +303,25 @@ def test_small_operators_with_fewer_chunks_than_ctas(dev, n_grid, leaf):
             ys.append(y.cpu().numpy().astype(np.float64))
         assert all(np.array_equal(ys[0], y) for y in ys[1:]), fac
         assert rel(ys[0], ref) <= bar, (fac, rel(ys[0], ref))
+
+
+def test_a_withheld_copy_times_out_and_the_operator_stays_usable(dev):
+    """Failure path of the copy pipeline, with no fault: the test switch of
+    hm_hmat_set_wait makes the row phase's producer withhold a chunk, the consumers'
+    1 ms waits run out, hm_hmat_check reports HM_ETIMEOUT (and clears the flags and
+    counters); with the switch off the next products are correct again."""
+    import torch
+    el = synth.config_penny(16)
+    T, H = build_h(el, 16, 1e-6)
+    A = O.dense_matrix(el, E, NU)
+    x = synth.rhs_normal(3 * el.N, 64)
+    xt = torch.as_tensor(x, dtype=torch.float32, device=dev)
+    for chunk in (0, 3):
+        H.set_wait(1e-3, chunk)
+        y = torch.empty_like(xt)
+        H.matvec(xt, y)
+        with pytest.raises(hmat.HMError) as ei:
+            H.check()
+        assert ei.value.status == hmat.HM_ETIMEOUT
+        H.set_wait(2.0, -1)
+        assert rel(run_mv(dev, H, x, torch.float32), A @ x) <= 1e-6 + 1e-6

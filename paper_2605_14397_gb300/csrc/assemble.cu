@@ -416,7 +416,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     H.h_near_zidx = std::move(near_zidx);
 
     // ---- ranks, partial-buffer and t-vector layout (low-rank blocks only)
-    int64_t tb_len = 0, p_len = 0, poff_len = 0;
+    int64_t tb_len = 0, p_len = 0, poff_len = 0, uoff_len = 0;
     H.far_entries = 0;
     H.rank_min = 1 << 30;
     H.rank_max = 0;
@@ -430,6 +430,9 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         F.n_tleaves = lcount[fnodes[b][1]];
         F.pbase = poff_len;
         poff_len += F.n_tleaves;
+        F.n_sleaves = lcount[fnodes[b][0]];
+        F.ubase = uoff_len;
+        uoff_len += F.n_sleaves;
         F.dense = dense_far[b];
         tb_len += F.rank;
         p_len += (int64_t)F.n_tleaves * F.rank;
@@ -443,7 +446,6 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     }
     if (nlr == 0) H.rank_min = 0;
     H.rank_mean = nlr ? rsum / (double)nlr : 0.0;
-    H.tb_len = tb_len;
     H.p_len = p_len;
 
     std::vector<std::vector<int64_t>> far_by_row(nl), far_by_col(nl);
@@ -459,6 +461,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
     std::vector<PackJob> ujobs, vjobs, ujobs16, vjobs16;
     std::vector<int32_t> u_zidx, v_pidx;
     H.h_poff.assign(std::max<int64_t>(poff_len, 1), 0);
+    H.h_uoff.assign(std::max<int64_t>(uoff_len, 1), 0);
     int64_t u_len = 0, v_len = 0, u_len16 = 0, v_len16 = 0;
     auto as16 = [](PackJob J, int64_t base16, int cols, int ld16) {
         J.dst = base16 + (int64_t)cols * ld16;
@@ -473,6 +476,9 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         int ucols = 0;
         for (int64_t b : far_by_row[l]) {
             const FarDesc& F = H.h_far[b];
+            const int64_t s = fnodes[b][0];
+            const int32_t ustart = (int32_t)u_zidx.size();  // this leaf's copy of t_b
+            H.h_uoff[F.ubase + (l - lfirst[s])] = ustart;
             PackJob J;
             J.src = F.fac_off + 3LL * (L.begin - F.s_begin);
             J.dst = u_len + (int64_t)ucols * L.ld;
@@ -482,7 +488,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
             J.ncols = F.rank;
             ujobs.push_back(J);
             ujobs16.push_back(as16(J, u_len16, ucols, L.ld16));
-            for (int c = 0; c < F.rank; ++c) u_zidx.push_back((int32_t)(F.tb_off + c));
+            for (int c = 0; c < F.rank; ++c) u_zidx.push_back(ustart + c);
             ucols += F.rank;
         }
         L.u_cols = ucols;
@@ -545,7 +551,11 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
         HM_LAUNCH_CHECK();
         HM_CUDA(cudaStreamSynchronize(st));
     }
+    H.tb_len = (int64_t)u_zidx.size();
+    if (H.tb_len > INT32_MAX) fail(HM_EINVAL, "assemble: too many U columns");
+    (void)tb_len;
     H.h_u_zidx = std::move(u_zidx);
+    H.uoff.upload(H.h_uoff, st);
     H.h_v_pidx = std::move(v_pidx);
     H.poff.upload(H.h_poff, st);
     H.leaves.upload(H.h_leaves, st);

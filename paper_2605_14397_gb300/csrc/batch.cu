@@ -56,7 +56,8 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         M.eps = std::max(M.eps, h->eps);
     }
 
-    int64_t pos = 0, near_b = 0, u_b = 0, v_b = 0, u16_b = 0, v16_b = 0, tb_b = 0, p_b = 0, fac_b = 0, po_b = 0;
+    int64_t pos = 0, near_b = 0, u_b = 0, v_b = 0, u16_b = 0, v16_b = 0, tb_b = 0, p_b = 0, fac_b = 0, po_b = 0,
+            uo_b = 0;
     int32_t nz_b = 0, uz_b = 0, vp_b = 0;
     M.h_leaves.clear();
     M.h_far.clear();
@@ -67,6 +68,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
     M.h_self_off.clear();
     M.h_near_true_cols.clear();
     M.h_poff.clear();
+    M.h_uoff.clear();
     M.n_near = M.n_far = M.n_dense_far = M.n_refined = 0;
     M.near_entries = M.far_entries = 0;
     M.assemble_seconds = 0.0;
@@ -99,6 +101,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
             F.s_begin += (int32_t)pos;
             F.t_begin += (int32_t)pos;
             F.pbase += po_b;
+            F.ubase += uo_b;
             F.tb_off += tb_b;
             F.fac_off += fac_b;
             M.h_far.push_back(F);
@@ -110,6 +113,8 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
         for (int32_t c : h->h_near_true_cols) M.h_near_true_cols.push_back(c);
         for (int32_t o : h->h_poff) M.h_poff.push_back(o + (int32_t)p_b);
         po_b += (int64_t)h->h_poff.size();
+        for (int32_t o : h->h_uoff) M.h_uoff.push_back(o + (int32_t)tb_b);
+        uo_b += (int64_t)h->h_uoff.size();
         pos += h->N;
         near_b += (int64_t)h->near.n;
         u_b += (int64_t)h->u32.n;
@@ -173,6 +178,7 @@ void merge(const std::vector<const HMat*>& hs, cudaStream_t st, HMat& M) {
     }
     M.perm.upload(perm32, st);
     M.poff.upload(M.h_poff, st);
+    M.uoff.upload(M.h_uoff, st);
     M.leaves.upload(M.h_leaves, st);
     M.far.upload(M.h_far, st);
     build_product_plan(M, st);

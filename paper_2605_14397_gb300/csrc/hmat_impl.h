@@ -56,11 +56,14 @@ struct FarDesc {
     int32_t n_tleaves;                   // leaves of T (partials per output)
     int64_t pbase;                       // first of its n_tleaves entries in the partial offset table:
                                          // partial l of the k-th leaf of T is P[poff[pbase + k] + l]
-    int64_t tb_off;                      // output offset in tb
+    int64_t tb_off;                      // offset of the block in the compact t order (blocks
+                                         // back to back; kept for reference)
     int64_t fac_off;                     // compact factor store offset (U then V)
     int32_t dense;                       // 1: kept dense (its tiles live in the near stream),
                                          // 2: refined into its children blocks (listed later)
-    int32_t pad_;
+    int32_t n_sleaves;                   // leaves of S (copies of t_b)
+    int64_t ubase;                       // first of its n_sleaves entries in the t-copy table: the
+                                         // k-th leaf of S reads t_b at tb[uoff[ubase + k] ...]
 };
 
 // One pipeline chunk: whole columns of one tile or factor slice of one leaf, at most one
@@ -94,7 +97,7 @@ struct HMat {
     int storage = HM_F32;
     int n_leaves = 0;
     int64_t n_far = 0, n_near = 0, n_dense_far = 0, n_refined = 0;
-    int64_t tb_len = 0, p_len = 0;
+    int64_t tb_len = 0, p_len = 0;  // tb_len: t entries with their copies (U columns)
     int64_t near_entries = 0, far_entries = 0;
     int rank_min = 0, rank_max = 0;
     double rank_mean = 0.0, assemble_seconds = 0.0;
@@ -120,6 +123,11 @@ struct HMat {
     // block's slice in every leaf of its column cluster
     std::vector<int32_t> h_poff;
     DevBuf<int32_t> poff;
+    // t_b is written once for every leaf of the row cluster S, at the position of that
+    // leaf's U slice in U-stream order, so a leaf's U columns read one contiguous range of
+    // tb and its chunks span blocks; uoff locates each copy
+    std::vector<int32_t> h_uoff;
+    DevBuf<int32_t> uoff;
     // single-RHS reduction order: the n_red_big blocks with many leaves of T first (a CTA
     // each), then the rest (a warp each); blocks without factors are left out
     DevBuf<int32_t> red_order;

@@ -278,8 +278,8 @@ __device__ __forceinline__ uint32_t to_zin(float v, uint32_t*) {
 // mode the sums are stored as (hi, lo) float pairs, the form phase 2 reads.
 template <class V, class Zt, bool VEC4>
 __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ far, const int32_t* __restrict__ poff,
-                                                   const V* __restrict__ P, Zt* __restrict__ tb, int nrhs,
-                                                   const int* __restrict__ skip) {
+                                                   const int32_t* __restrict__ uoff, const V* __restrict__ P,
+                                                   Zt* __restrict__ tb, int nrhs, const int* __restrict__ skip) {
     __shared__ V sp[128];
     pdl_wait();
     pdl_trigger();
@@ -318,11 +318,15 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
                     const float4 v0 = P4[(at(q) >> 2) + e];
                     s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
                 }
-                float* o = reinterpret_cast<float*>(tb) + F.tb_off * nrhs + 4 * e;
-                o[0] = (s0.x + s1.x) + (s2.x + s3.x);
-                o[1] = (s0.y + s1.y) + (s2.y + s3.y);
-                o[2] = (s0.z + s1.z) + (s2.z + s3.z);
-                o[3] = (s0.w + s1.w) + (s2.w + s3.w);
+                const float4 t = make_float4((s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
+                                             (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w));
+                for (int c = 0; c < F.n_sleaves; ++c) {  // one copy per leaf of S
+                    float* o = reinterpret_cast<float*>(tb) + (int64_t)uoff[F.ubase + c] * nrhs + 4 * e;
+                    o[0] = t.x;
+                    o[1] = t.y;
+                    o[2] = t.z;
+                    o[3] = t.w;
+                }
             }
             return;
         }
@@ -338,7 +342,8 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
                 s3 += P[at(q + 3) + e];
             }
             for (; q < F.n_tleaves; ++q) s0 += P[at(q) + e];
-            tb[F.tb_off * nrhs + e] = to_zin((s0 + s1) + (s2 + s3), tb);
+            const Zt t = to_zin((s0 + s1) + (s2 + s3), tb);
+            for (int c = 0; c < F.n_sleaves; ++c) tb[(int64_t)uoff[F.ubase + c] * nrhs + e] = t;
         }
         return;
     }
@@ -360,7 +365,8 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
     if (threadIdx.x < n) {
         V s = 0;
         for (int q = 0; q < G; ++q) s += sp[q * n + threadIdx.x];
-        tb[F.tb_off * nrhs + threadIdx.x] = to_zin(s, tb);
+        const Zt t = to_zin(s, tb);
+        for (int c = 0; c < F.n_sleaves; ++c) tb[(int64_t)uoff[F.ubase + c] * nrhs + threadIdx.x] = t;
     }
 }
 
@@ -374,6 +380,7 @@ __device__ __forceinline__ int tb16_piece_pos(int64_t l, int q) { return q ^ (in
 
 __global__ void __launch_bounds__(128) k_reduce_tb_pack16(const FarDesc* __restrict__ far,
                                                           const int32_t* __restrict__ poff,
+                                                          const int32_t* __restrict__ uoff,
                                                           const float* __restrict__ P, uint16_t* __restrict__ tb,
                                                           const int* __restrict__ skip) {
     constexpr int SPO = 2048;
@@ -414,14 +421,16 @@ __global__ void __launch_bounds__(128) k_reduce_tb_pack16(const FarDesc* __restr
             hb[i] = bf16_bits(t[i]);
             lb[i] = bf16_bits(t[i] - bf16_value(hb[i]));
         }
-        const int64_t l = F.tb_off + e / 4;
         const int k0 = (e & 3) * 4;                  // first of the four RHS
         const int qh = 2 * (k0 >> 3), off = k0 & 7;  // hi piece of these RHS, offset inside it
-        uint16_t* row = tb + 32 * l;                 // 64 bytes
-        *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh) + off) =
-            make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
-        *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh + 1) + off) =
-            make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+        for (int c = 0; c < F.n_sleaves; ++c) {     // one copy per leaf of S
+            const int64_t l = (int64_t)uoff[F.ubase + c] + e / 4;
+            uint16_t* row = tb + 32 * l;             // 64 bytes
+            *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh) + off) =
+                make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+            *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh + 1) + off) =
+                make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+        }
     }
 }
 
@@ -437,6 +446,7 @@ constexpr int RED_WARP_LEAVES = 32;
 template <class V, class Zt>
 __global__ void __launch_bounds__(256) k_reduce_mix(const FarDesc* __restrict__ far,
                                                     const int32_t* __restrict__ poff,
+                                                    const int32_t* __restrict__ uoff,
                                                     const int32_t* __restrict__ order, int64_t n_big, int64_t n_all,
                                                     const V* __restrict__ P, Zt* __restrict__ tb,
                                                     const int* __restrict__ skip) {
@@ -473,7 +483,8 @@ __global__ void __launch_bounds__(256) k_reduce_mix(const FarDesc* __restrict__ 
         if (threadIdx.x < r) {
             V s = 0;
             for (int q = 0; q < G; ++q) s += sp[q * r + threadIdx.x];
-            tb[F.tb_off + threadIdx.x] = to_zin(s, tb);
+            const Zt t = to_zin(s, tb);
+            for (int c = 0; c < F.n_sleaves; ++c) tb[uoff[F.ubase + c] + threadIdx.x] = t;
         }
         return;
     }
@@ -483,7 +494,8 @@ __global__ void __launch_bounds__(256) k_reduce_mix(const FarDesc* __restrict__ 
     const int64_t b = order[k];
     const int r = far[b].rank, nt = far[b].n_tleaves;
     const int32_t* po = poff + far[b].pbase;
-    const int64_t out = far[b].tb_off;
+    const int ns = far[b].n_sleaves;
+    const int32_t* uo = uoff + far[b].ubase;
     for (int e0 = 0; e0 < r; e0 += 32) {
         const int e = e0 + lane;
         const bool on = e < r;
@@ -507,7 +519,10 @@ __global__ void __launch_bounds__(256) k_reduce_mix(const FarDesc* __restrict__ 
                 if (on) s0 += P[(int64_t)o0 + e];
             }
         }
-        if (on) tb[out + e] = to_zin((s0 + s1) + (s2 + s3), tb);
+        if (on) {
+            const Zt t = to_zin((s0 + s1) + (s2 + s3), tb);
+            for (int c = 0; c < ns; ++c) tb[uo[c] + e] = t;  // one copy per leaf of S
+        }
     }
 }
 
@@ -1231,23 +1246,26 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
         const unsigned gm = (unsigned)std::max<int64_t>(1, H.n_red_big + (H.n_red - H.n_red_big + 7) / 8);
         if constexpr (kTensorPhase2x1)
             launch_pdl(k_reduce_mix<V, uint32_t>, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
-                       (const int32_t*)H.poff.p, (const int32_t*)H.red_order.p, H.n_red_big, H.n_red,
+                       (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const int32_t*)H.red_order.p,
+                       H.n_red_big, H.n_red,
                        (const V*)a.out, (uint32_t*)base.tb, base.skip);
         else if (kTensorPhase2x16 && base.nr == 16)
             launch_pdl(k_reduce_tb_pack16, dim3((unsigned)H.n_far), dim3(128), 0, st, (const FarDesc*)H.far.p,
-                       (const int32_t*)H.poff.p, (const float*)a.out, (uint16_t*)base.tb, base.skip);
+                       (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const float*)a.out, (uint16_t*)base.tb,
+                       base.skip);
         else if (base.nr == 1)
             launch_pdl(k_reduce_mix<V, Zt>, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
-                       (const int32_t*)H.poff.p, (const int32_t*)H.red_order.p, H.n_red_big, H.n_red,
+                       (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const int32_t*)H.red_order.p,
+                       H.n_red_big, H.n_red,
                        (const V*)a.out, (Zt*)base.tb, base.skip);
         else if (MODE == 0 && (base.nr & 3) == 0)
             launch_pdl(k_reduce_tb<V, Zt, MODE == 0>, dim3((unsigned)H.n_far), dim3(128), 0, st,
-                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
-                       base.skip);
+                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const V*)a.out,
+                       (Zt*)base.tb, base.nr, base.skip);
         else
             launch_pdl(k_reduce_tb<V, Zt, false>, dim3((unsigned)H.n_far), dim3(128), 0, st,
-                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const V*)a.out, (Zt*)base.tb, base.nr,
-                       base.skip);
+                       (const FarDesc*)H.far.p, (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const V*)a.out,
+                       (Zt*)base.tb, base.nr, base.skip);
         HM_LAUNCH_CHECK();
         if (timed) mark(H, 3, st);
     } else if (timed) {

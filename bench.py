@@ -51,7 +51,8 @@ def parse():
                    help="grid of each plane of the planes workload (300: 270,000 elements)")
     p.add_argument("--lp-h", type=float, default=0.01, help="element size of the crack + fault (learned workload)")
     p.add_argument("--lp-train", type=int, default=2000, help="training systems (learned workload)")
-    p.add_argument("--workload", default="fault", choices=["fault", "faults64", "planes", "learned", "ilu"],
+    p.add_argument("--workload", default="fault",
+                   choices=["fault", "faults64", "planes", "learned", "ilu", "interface"],
                    help="fault: the 51,468-element disk fault (default); faults64: 64 independent faults, "
                         "batched product vs per-fault launches; planes: three intersecting 300x300 planes, "
                         "16 right-hand sides")
@@ -576,6 +577,47 @@ def run_ilu(args, dev, torch, hmat, synth):
     print(json.dumps(out), flush=True)
 
 
+def run_interface(args, dev, torch, hmat, synth):
+    """The interface constitutive update and its consistent tangent (Sec. 2.2, 3.1.1,
+    eq. jac_mech) at 4,000,000 seeded points (the softening joint; about 70 % of the
+    points return plastically).  Bytes per point: the state and increment read (4 x 24 B)
+    and the new state, C^ep and mode written (3 x 24 + 72 + 4 B) = 244 B; inputs far larger
+    than L2 (976 MB)."""
+    import numpy as np
+    n = 4_000_000
+    kw = synth.INTERFACE_PARAMS["softening"]
+    T, dp, chi, dd = (torch.as_tensor(a, device=dev) for a in synth.interface_states(n, 1608))
+    T1, dp1, chi1 = torch.empty_like(T), torch.empty_like(dp), torch.empty_like(chi)
+    st = torch.cuda.current_stream()
+    res = {}
+    for label, tangent in (("with_tangent", True), ("values_only", False)):
+        for _ in range(max(3, args.warmup)):
+            hmat.interface_update(kw, T, dp, chi, dd, T1, dp1, chi1, tangent=tangent, stream=st)
+        out = hmat.interface_update(kw, T, dp, chi, dd, T1, dp1, chi1, tangent=tangent, counts=True, stream=st)
+        reps = max(5, min(args.steps, 50))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            hmat.interface_update(kw, T, dp, chi, dd, T1, dp1, chi1, tangent=tangent, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        nbytes = n * (96 + 72 + (72 if tangent else 0) + 4)
+        res[label] = {"ms": ms, "points_per_s": n / (ms * 1e-3), "GBs": nbytes / (ms * 1e-3) / 1e9,
+                      "bytes_per_point": nbytes // n}
+    modes = dict(zip(hmat.INTERFACE_MODES, (int(c) for c in out[5][:5])))
+    peak, src = peaks()
+    line = {"metric": "interface constitutive update + consistent tangent, points/s", "unit": "points/s",
+            "value": res["with_tangent"]["points_per_s"], "n_gpus": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded states)",
+            "config": {"workload": "4,000,000 interface points, softening joint (Ks 10, Kn 20, f 0.6 -> 0.3, "
+                                   "psi 0.1, dc 0.2, c 0.1, sigma_t 0.5, wc 0.4)", "modes": modes,
+                       "l2": "inputs 976 MB >> 129 MB L2: no flush"},
+            "results": res, "frac_of_hbm_peak": res["with_tangent"]["GBs"] / peak, "peak_source": src}
+    print(json.dumps(line), flush=True)
+
+
 def max_over_ranks(dist, value, device):
     """The largest of the ranks' values (each rank passes its own; None: one process)."""
     if dist is None:
@@ -699,6 +741,9 @@ def main():
         return
     if args.workload == "ilu":
         run_ilu(args, dev, torch, hmat, synth)
+        return
+    if args.workload == "interface":
+        run_interface(args, dev, torch, hmat, synth)
         return
     el = synth.config_fault(args.grid)
     E, nu, eps = 1.0, 0.25, 1e-6

@@ -307,6 +307,57 @@ hm_status hm_ilu_export(const hm_hmat* h, const double* k_dev, double shift, dou
  * HM_EINVAL if no factorization exists.  Asynchronous. */
 hm_status hm_ilu_apply(const hm_hmat* h, const double* r_dev, double* z_dev, int nrhs, void* stream);
 
+/* ---------------------------------------------------------------- interface law
+ * Constitutive update of the fault / fracture interface and its consistent tangent
+ * (Sec. 2.2: poroelastoplastic interface with a Coulomb yield surface F_c = |tau| +
+ * f T'_n - c, a tensile cut-off F_t = T'_n - sigma_t, non-associated Coulomb flow along
+ * s_hat + psi n and associated tensile flow along n; Sec. 3.1.1: elastic predictor -
+ * plastic corrector; eq. jac_mech: C^ep = d(Delta T') / d(Delta delta)).  Per point, in
+ * its local frame (s1, s2, n):
+ *   T' - T'^n = C (Delta delta - Delta delta^p), C = diag(Ks, Ks, Kn) (constant);
+ *   f = (fp - fr) W(chi_s / dc) + fr, psi = psip W(chi_s / dc), c = cp W(chi_t / wc),
+ *   sigma_t = sigp W(chi_t / wc), W(x) = max(0, 1 - x) (W = 0 when wc = 0);
+ *   chi_s = max over time of |delta^p_s|, chi_t = max over time of |delta^p|, taken at
+ *   t^(n+1) (backward Euler, like f, psi, c, sigma_t in the return);
+ *   mode at the trial state with the strengths of t^n: elastic if F_c <= 0 and F_t <= 0,
+ *   else Coulomb if h = |tau| - (c - f sigma_t) - (sqrt(1 + f^2) - f)(T'_n - sigma_t) > 0,
+ *   else tensile; a Coulomb return with no root before tau = 0 returns to the cone's apex
+ *   (tau = 0, f T'_n = c, shear fully inelastic);
+ *   full damage when wc = 0 (pre-existing fracture) or chi_t >= wc: a fully damaged
+ *   point with a tensile trial traction is open (T' = 0, C^ep = 0, Delta delta + C^-1 T'^n
+ *   inelastic); otherwise it is in contact with its normal inelastic DD at
+ *   min(delta^p_n, w_R), w_R = alphaR wc + w_dil, and frictional without cohesion; a
+ *   tensile or apex return that reaches full damage ends open;
+ *   w_dil (the dilatant part of w_R) grows by psi dl in every Coulomb return.
+ * The plastic multiplier solves a scalar equation (Newton safeguarded by bisection);
+ * parameters must keep it monotone (interface stiffness above the softening rates).
+ * C^ep is exact within the active mode (forward-mode dual numbers and the implicit
+ * function theorem at the multiplier's root).
+ * Arrays (device, n points, row-major): T_dev, dp_dev (n x 3: T'^n and delta^p_n),
+ * chi_dev (n x 3: chi_s, chi_t, w_dil), dd_dev (n x 3: Delta delta) in; T1_dev, dp1_dev,
+ * chi1_dev (n x 3) out, each may be the same array as its input; cep_dev (n x 9, row i =
+ * traction component i, column j = DD component j) or NULL (no tangent, cheaper);
+ * mode_dev (n int32: 0 elastic, 1 Coulomb, 2 tensile, 3 open, 4 apex) or NULL.
+ * counts (host, 6 int64) or NULL: points per mode and, last, points whose multiplier did
+ * not converge; with counts the call synchronises the stream and returns HM_ENOCONV if
+ * that last count is not 0.  HM_EINVAL for Ks or Kn <= 0, dc <= 0, a negative or
+ * non-finite parameter. */
+typedef struct {
+    double Ks, Kn;   /* shear and normal stiffness of the interface */
+    double fp, fr;   /* peak and residual friction coefficients */
+    double psip;     /* peak dilatancy coefficient */
+    double dc;       /* slip-weakening distance (> 0) */
+    double cp;       /* peak cohesion */
+    double sigp;     /* peak tensile strength */
+    double wc;       /* critical inelastic DD of cohesion and tensile strength (0: pre-existing fracture) */
+    double alphaR;   /* residual width after full damage, fraction of wc */
+} hm_interface_params;
+
+hm_status hm_interface_update(const hm_interface_params* prm, int64_t n, const double* T_dev,
+                              const double* dp_dev, const double* chi_dev, const double* dd_dev, double* T1_dev,
+                              double* dp1_dev, double* chi1_dev, double* cep_dev, int32_t* mode_dev,
+                              int64_t* counts, void* stream);
+
 /* ---------------------------------------------------------------- batching
  * Independent faults: the operator of several non-interacting fractures is
  * block-diagonal, one block E_f per fault (eq. ElasSystem on each fault alone, each with

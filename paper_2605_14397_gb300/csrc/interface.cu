@@ -1,0 +1,576 @@
+// Interface constitutive update (Sec. 2.2: the poroelastoplastic interface law with a
+// Coulomb yield surface, a tensile cut-off, softening of friction, dilatancy, cohesion
+// and tensile strength, damage, opening and contact) integrated by an elastic predictor
+// and plastic corrector (Sec. 3.1.1), with the consistent tangent
+// C^ep = d(Delta T') / d(Delta delta) of eq. jac_mech.  One thread per collocation point,
+// FP64.
+//
+// The tangent is exact: the return is evaluated in forward-mode dual numbers.  The
+// plastic multiplier is found in plain arithmetic (Newton safeguarded by bisection, the
+// slope from a one-component dual), and one more Newton step in four-component duals
+// (three for Delta delta, one for the multiplier) gives its derivative by the implicit
+// function theorem: d(dl) = -(dg/d dd) / (dg/d dl) at the root.  The rest of the return
+// is then re-evaluated in three-component duals, whose derivative parts are C^ep.
+//
+// Branches (the active mode, the maxima of the internal variables) are taken on values,
+// so C^ep is the derivative within the active mode.  The choices the paper leaves open
+// are those stated with hm_interface_update in hmat.h.
+#include <cmath>
+
+#include "common.h"
+
+namespace hm {
+namespace {
+
+enum : int32_t { M_ELASTIC = 0, M_COULOMB = 1, M_TENSILE = 2, M_OPEN = 3, M_APEX = 4 };
+constexpr int N_MODES = 5;
+constexpr int ST_NOROOT = 1;  // a multiplier bracket without a sign change or no convergence
+
+struct Prm {
+    double Ks, Kn, fp, fr, psip, dc, cp, sigp, wc, alphaR;
+};
+
+// ---------------------------------------------------------------- dual numbers
+template <int K>
+struct Dual {
+    double v;
+    double d[K];
+};
+
+template <int K>
+__device__ __forceinline__ Dual<K> cst(double x) {
+    Dual<K> r;
+    r.v = x;
+#pragma unroll
+    for (int i = 0; i < K; ++i) r.d[i] = 0.0;
+    return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator+(Dual<K> a, Dual<K> b) {
+    a.v += b.v;
+#pragma unroll
+    for (int i = 0; i < K; ++i) a.d[i] += b.d[i];
+    return a;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator-(Dual<K> a, Dual<K> b) {
+    a.v -= b.v;
+#pragma unroll
+    for (int i = 0; i < K; ++i) a.d[i] -= b.d[i];
+    return a;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator*(Dual<K> a, Dual<K> b) {
+    Dual<K> r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator/(Dual<K> a, Dual<K> b) {
+    Dual<K> r;
+    r.v = a.v / b.v;
+#pragma unroll
+    for (int i = 0; i < K; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator+(Dual<K> a, double b) { a.v += b; return a; }
+template <int K>
+__device__ __forceinline__ Dual<K> operator-(Dual<K> a, double b) { a.v -= b; return a; }
+template <int K>
+__device__ __forceinline__ Dual<K> operator-(double a, Dual<K> b) {
+    b.v = a - b.v;
+#pragma unroll
+    for (int i = 0; i < K; ++i) b.d[i] = -b.d[i];
+    return b;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator*(double a, Dual<K> b) {
+    b.v *= a;
+#pragma unroll
+    for (int i = 0; i < K; ++i) b.d[i] *= a;
+    return b;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator/(Dual<K> a, double b) {
+    a.v /= b;
+#pragma unroll
+    for (int i = 0; i < K; ++i) a.d[i] /= b;
+    return a;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> dsqrt(Dual<K> a) {
+    Dual<K> r;
+    r.v = sqrt(a.v);
+    const double h = r.v > 0.0 ? 0.5 / r.v : 0.0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) r.d[i] = a.d[i] * h;
+    return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> dmax(Dual<K> a, Dual<K> b) { return a.v >= b.v ? a : b; }
+
+// ---------------------------------------------------------------- the law
+// W(chi / scale), W(x) = max(0, 1 - x); a zero scale is fully softened
+template <int K>
+__device__ __forceinline__ Dual<K> soft(double scale, Dual<K> chi) {
+    if (!(scale > 0.0)) return cst<K>(0.0);
+    const Dual<K> x = chi / scale;
+    return x.v >= 1.0 ? cst<K>(0.0) : 1.0 - x;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> friction(const Prm& P, Dual<K> chis) {
+    return (P.fp - P.fr) * soft(P.dc, chis) + P.fr;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> dilatancy(const Prm& P, Dual<K> chis) { return P.psip * soft(P.dc, chis); }
+template <int K>
+__device__ __forceinline__ Dual<K> cohesion(const Prm& P, Dual<K> chit) { return P.cp * soft(P.wc, chit); }
+template <int K>
+__device__ __forceinline__ Dual<K> tstrength(const Prm& P, Dual<K> chit) { return P.sigp * soft(P.wc, chit); }
+
+template <int K>
+__device__ __forceinline__ Dual<K> norm2(Dual<K> a, Dual<K> b) { return dsqrt(a * a + b * b); }
+template <int K>
+__device__ __forceinline__ Dual<K> norm3(Dual<K> a, Dual<K> b, Dual<K> c) { return dsqrt(a * a + b * b + c * c); }
+
+// state at t^n of one point (values) and its trial quantities (duals in Delta delta)
+struct Pt {
+    double T[3], dp[3], chis, chit, wdil;
+};
+
+template <int K>
+struct Res {
+    Dual<K> T[3], dp[3], chis, chit, wdil;
+    int32_t mode;
+};
+
+// The three multiplier equations g(dl) = 0 of the returns, on duals of the trial
+// quantities (K components) and of dl.  `aux` receives the state at that dl.
+// Coulomb return (flow along s_hat + psi n, shear direction of the trial kept)
+template <int K>
+struct CoulombEq {
+    const Prm* P;
+    Dual<K> Ttr_n, tau_tr, s0, s1;
+    double dp[3], chis, chit;
+    __device__ Dual<K> g(Dual<K> dl, Res<K>* out) const {
+        const Dual<K> dps0 = cst<K>(dp[0]) + dl * s0, dps1 = cst<K>(dp[1]) + dl * s1;
+        const Dual<K> chis1 = dmax(cst<K>(chis), norm2(dps0, dps1));
+        const Dual<K> psi1 = dilatancy(*P, chis1);
+        const Dual<K> dpn = cst<K>(dp[2]) + dl * psi1;
+        const Dual<K> chit1 = dmax(cst<K>(chit), norm3(dps0, dps1, dpn));
+        const Dual<K> tau1 = tau_tr - P->Ks * dl;
+        const Dual<K> Tn1 = Ttr_n - P->Kn * (psi1 * dl);
+        if (out) {
+            out->T[0] = tau1 * s0;
+            out->T[1] = tau1 * s1;
+            out->T[2] = Tn1;
+            out->dp[0] = dps0;
+            out->dp[1] = dps1;
+            out->dp[2] = dpn;
+            out->chis = chis1;
+            out->chit = chit1;
+            out->wdil = psi1 * dl;  // increment; the caller adds w_dil^n
+        }
+        return tau1 + friction(*P, chis1) * Tn1 - cohesion(*P, chit1);
+    }
+};
+
+// tensile return (flow along n)
+template <int K>
+struct TensileEq {
+    const Prm* P;
+    Dual<K> Ttr_n;
+    double dp[3], chit;
+    __device__ Dual<K> g(Dual<K> dl, Res<K>* out) const {
+        const Dual<K> dpn = cst<K>(dp[2]) + dl;
+        const Dual<K> chit1 = dmax(cst<K>(chit), norm3(cst<K>(dp[0]), cst<K>(dp[1]), dpn));
+        const Dual<K> Tn1 = Ttr_n - P->Kn * dl;
+        if (out) {
+            out->T[2] = Tn1;
+            out->dp[2] = dpn;
+            out->chit = chit1;
+        }
+        return Tn1 - tstrength(*P, chit1);
+    }
+};
+
+// apex of the Coulomb cone: shear fully inelastic, normal increment mu
+template <int K>
+struct ApexEq {
+    const Prm* P;
+    Dual<K> Ttr_n, f1, dps0, dps1;
+    double dpn, chit;
+    __device__ Dual<K> g(Dual<K> mu, Res<K>* out) const {
+        const Dual<K> dpn1 = cst<K>(dpn) + mu;
+        const Dual<K> chit1 = dmax(cst<K>(chit), norm3(dps0, dps1, dpn1));
+        const Dual<K> Tn1 = Ttr_n - P->Kn * mu;
+        if (out) {
+            out->T[2] = Tn1;
+            out->dp[2] = dpn1;
+            out->chit = chit1;
+        }
+        return f1 * Tn1 - cohesion(*P, chit1);
+    }
+};
+
+// Root of g on [0, hi] with g(0) > 0 >= g(hi) (values): Newton from 0, safeguarded by
+// the bracket; 0 when g(0) <= 0.  `Eq1` is the equation on one-component duals (the
+// derivative in dl).
+template <class Eq1>
+__device__ double find_root(const Eq1& e, double hi, int* st) {
+    Dual<1> z;
+    z.v = 0.0;
+    z.d[0] = 1.0;
+    Dual<1> gz = e.g(z, nullptr);
+    if (!(gz.v > 0.0)) return 0.0;
+    double lo = 0.0, x = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        // gz = g(x)
+        if (gz.v > 0.0) lo = x; else hi = x;
+        if (gz.v == 0.0) return x;
+        double nx = x - gz.v / gz.d[0];
+        if (!(gz.d[0] < 0.0) || !(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        if (nx == x || !(hi > lo) || nx <= lo || nx >= hi) return x;
+        if (fabs(nx - x) <= 1e-16 * fabs(nx)) {
+            x = nx;
+            return x;
+        }
+        x = nx;
+        z.v = x;
+        gz = e.g(z, nullptr);
+    }
+    *st |= ST_NOROOT;
+    return x;
+}
+
+// the multiplier as a dual in Delta delta: one Newton step at the root with the
+// derivative in dl carried in a fourth component
+template <class Eq4>
+__device__ Dual<3> root_dual(const Eq4& e4, double x, int* st) {
+    Dual<4> z = cst<4>(x);
+    z.d[3] = 1.0;
+    const Dual<4> g = e4.g(z, nullptr);
+    Dual<3> r;
+    if (!(g.d[3] != 0.0)) {
+        *st |= ST_NOROOT;
+        r = cst<3>(x);
+        return r;
+    }
+    r.v = x;  // the root found in values; the step only supplies the derivative
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r.d[i] = -g.d[i] / g.d[3];
+    return r;
+}
+
+template <int KA, int KB>
+__device__ __forceinline__ Dual<KB> widen(Dual<KA> a) {
+    Dual<KB> r;
+    r.v = a.v;
+#pragma unroll
+    for (int i = 0; i < KB; ++i) r.d[i] = i < KA ? a.d[i] : 0.0;
+    return r;
+}
+
+// open state: T' = 0, all of dd + C^-1 T'^n inelastic
+template <int K>
+__device__ void open_state(const Prm& P, const Pt& p, const Dual<K>* dd, Res<K>& r) {
+    r.dp[0] = cst<K>(p.dp[0] + p.T[0] / P.Ks) + dd[0];
+    r.dp[1] = cst<K>(p.dp[1] + p.T[1] / P.Ks) + dd[1];
+    r.dp[2] = cst<K>(p.dp[2] + p.T[2] / P.Kn) + dd[2];
+    r.T[0] = r.T[1] = r.T[2] = cst<K>(0.0);
+    r.chis = dmax(cst<K>(p.chis), norm2(r.dp[0], r.dp[1]));
+    r.chit = dmax(cst<K>(p.chit), norm3(r.dp[0], r.dp[1], r.dp[2]));
+    r.wdil = cst<K>(p.wdil);
+    r.mode = M_OPEN;
+}
+
+// the equations of one return on duals of K components, from the trial traction
+template <int K>
+__device__ CoulombEq<K> make_coulomb(const Prm& P, const Dual<K>* Ttr, const double* dpb, const Pt& p) {
+    CoulombEq<K> e;
+    e.P = &P;
+    e.tau_tr = norm2(Ttr[0], Ttr[1]);
+    e.s0 = Ttr[0] / e.tau_tr;
+    e.s1 = Ttr[1] / e.tau_tr;
+    e.Ttr_n = Ttr[2];
+    e.dp[0] = dpb[0];
+    e.dp[1] = dpb[1];
+    e.dp[2] = dpb[2];
+    e.chis = p.chis;
+    e.chit = p.chit;
+    return e;
+}
+
+template <int K>
+__device__ ApexEq<K> make_apex(const Prm& P, const Dual<K>* Ttr, const double* dpb, const Pt& p) {
+    ApexEq<K> e;
+    e.P = &P;
+    const Dual<K> tau = norm2(Ttr[0], Ttr[1]);
+    if (tau.v > 0.0) {
+        e.dps0 = cst<K>(dpb[0]) + Ttr[0] / P.Ks;
+        e.dps1 = cst<K>(dpb[1]) + Ttr[1] / P.Ks;
+    } else {
+        e.dps0 = cst<K>(dpb[0]);
+        e.dps1 = cst<K>(dpb[1]);
+    }
+    e.f1 = friction(P, dmax(cst<K>(p.chis), norm2(e.dps0, e.dps1)));
+    e.Ttr_n = Ttr[2];
+    e.dpn = dpb[2];
+    e.chit = p.chit;
+    return e;
+}
+
+template <int K>
+__device__ TensileEq<K> make_tensile(const Prm& P, const Dual<K>* Ttr, const double* dpb, const Pt& p) {
+    TensileEq<K> e;
+    e.P = &P;
+    e.Ttr_n = Ttr[2];
+    e.dp[0] = dpb[0];
+    e.dp[1] = dpb[1];
+    e.dp[2] = dpb[2];
+    e.chit = p.chit;
+    return e;
+}
+
+// trial traction with the closed-state reference (damaged) or the plain one
+template <int K>
+__device__ void trial(const Prm& P, const Pt& p, const Dual<K>* dd, double dpn_shift, Dual<K>* Ttr) {
+    Ttr[0] = cst<K>(p.T[0]) + P.Ks * dd[0];
+    Ttr[1] = cst<K>(p.T[1]) + P.Ks * dd[1];
+    Ttr[2] = cst<K>(p.T[2] - P.Kn * dpn_shift) + P.Kn * dd[2];
+}
+
+// The update on three-component duals (derivatives in Delta delta); with want_dual
+// false the multipliers' derivative steps are skipped (values only).
+__device__ Res<3> update(const Prm& P, const Pt& p, const double ddv[3], bool want_dual, int* st) {
+    Dual<3> dd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dd[i] = cst<3>(ddv[i]);
+        if (want_dual) dd[i].d[i] = 1.0;
+    }
+    Res<3> r;
+    const bool damaged = !(P.wc > 0.0) || p.chit >= P.wc;
+    double dpb[3] = {p.dp[0], p.dp[1], p.dp[2]};
+    double shift = 0.0;
+    int kind;  // 0 elastic, 1 Coulomb, 2 tensile, 3 open
+    if (damaged) {
+        const double wR = P.alphaR * P.wc + p.wdil;
+        const double dpn_c = fmin(p.dp[2], wR);
+        shift = dpn_c - p.dp[2];
+        dpb[2] = dpn_c;
+        Dual<3> Ttr[3];
+        trial(P, p, dd, shift, Ttr);
+        if (Ttr[2].v > 0.0) {
+            kind = 3;
+        } else {
+            const double Fc = sqrt(Ttr[0].v * Ttr[0].v + Ttr[1].v * Ttr[1].v) +
+                              friction(P, cst<1>(p.chis)).v * Ttr[2].v;  // no cohesion left
+            kind = Fc <= 0.0 ? 0 : 1;
+        }
+    } else {
+        Dual<3> Ttr[3];
+        trial(P, p, dd, 0.0, Ttr);
+        const double tau = sqrt(Ttr[0].v * Ttr[0].v + Ttr[1].v * Ttr[1].v);
+        const double f0 = friction(P, cst<1>(p.chis)).v, c0 = cohesion(P, cst<1>(p.chit)).v,
+                     st0 = tstrength(P, cst<1>(p.chit)).v;
+        const double Fc = tau + f0 * Ttr[2].v - c0, Ft = Ttr[2].v - st0;
+        if (Fc <= 0.0 && Ft <= 0.0) {
+            kind = 0;
+        } else {
+            const double a = sqrt(1.0 + f0 * f0) - f0;
+            const double h = tau - (c0 - f0 * st0) - a * (Ttr[2].v - st0);
+            kind = h > 0.0 ? 1 : 2;
+        }
+    }
+    if (kind == 3) {
+        open_state(P, p, dd, r);
+        return r;
+    }
+    Dual<3> Ttr[3];
+    trial(P, p, dd, shift, Ttr);
+    if (kind == 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            r.T[i] = Ttr[i];
+            r.dp[i] = cst<3>(dpb[i]);
+        }
+        r.chis = cst<3>(p.chis);
+        r.chit = cst<3>(p.chit);
+        r.wdil = cst<3>(p.wdil);
+        r.mode = M_ELASTIC;
+        return r;
+    }
+    // the same trial on one- and four-component duals (values only in the first, dd in
+    // the first three components of the second)
+    Dual<1> T1[3];
+    Dual<4> T4[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        T1[i] = cst<1>(Ttr[i].v);
+        T4[i] = widen<3, 4>(Ttr[i]);
+    }
+    bool apex = false;
+    if (kind == 1) {
+        const double tau = norm2(Ttr[0], Ttr[1]).v;
+        if (tau > 0.0) {
+            const CoulombEq<1> e1 = make_coulomb<1>(P, T1, dpb, p);
+            const double hi = tau / P.Ks;
+            Dual<1> zh = cst<1>(hi);
+            if (e1.g(zh, nullptr).v > 0.0) {
+                apex = true;
+            } else {
+                const double x = find_root(e1, hi, st);
+                Dual<3> dl = cst<3>(x);
+                if (want_dual && x > 0.0) dl = root_dual(make_coulomb<4>(P, T4, dpb, p), x, st);
+                const CoulombEq<3> e3 = make_coulomb<3>(P, Ttr, dpb, p);
+                Res<3> s;
+                e3.g(dl, &s);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    r.T[i] = s.T[i];
+                    r.dp[i] = s.dp[i];
+                }
+                r.chis = s.chis;
+                r.chit = s.chit;
+                r.wdil = cst<3>(p.wdil) + s.wdil;
+                r.mode = M_COULOMB;
+                return r;  // a Coulomb return stays in contact whatever the damage
+            }
+        } else {
+            apex = true;
+        }
+    }
+    if (apex) {
+        const ApexEq<1> e1 = make_apex<1>(P, T1, dpb, p);
+        const double x = find_root(e1, Ttr[2].v / P.Kn, st);
+        Dual<3> mu = cst<3>(x);
+        if (want_dual && x > 0.0) mu = root_dual(make_apex<4>(P, T4, dpb, p), x, st);
+        const ApexEq<3> e3 = make_apex<3>(P, Ttr, dpb, p);
+        Res<3> s;
+        e3.g(mu, &s);
+        r.T[0] = r.T[1] = cst<3>(0.0);
+        r.T[2] = s.T[2];
+        r.dp[0] = e3.dps0;
+        r.dp[1] = e3.dps1;
+        r.dp[2] = s.dp[2];
+        r.chis = dmax(cst<3>(p.chis), norm2(e3.dps0, e3.dps1));
+        r.chit = s.chit;
+        r.mode = M_APEX;
+    } else {
+        const TensileEq<1> e1 = make_tensile<1>(P, T1, dpb, p);
+        const double x = find_root(e1, Ttr[2].v / P.Kn, st);
+        Dual<3> dl = cst<3>(x);
+        if (want_dual && x > 0.0) dl = root_dual(make_tensile<4>(P, T4, dpb, p), x, st);
+        const TensileEq<3> e3 = make_tensile<3>(P, Ttr, dpb, p);
+        Res<3> s;
+        e3.g(dl, &s);
+        r.T[0] = Ttr[0];
+        r.T[1] = Ttr[1];
+        r.T[2] = s.T[2];
+        r.dp[0] = cst<3>(dpb[0]);
+        r.dp[1] = cst<3>(dpb[1]);
+        r.dp[2] = s.dp[2];
+        r.chis = cst<3>(p.chis);
+        r.chit = s.chit;
+        r.mode = M_TENSILE;
+    }
+    r.wdil = cst<3>(p.wdil);
+    if (!(P.wc > 0.0) || r.chit.v >= P.wc) open_state(P, p, dd, r);  // full damage: open
+    return r;
+}
+
+// the outputs may alias the inputs (each thread reads its point before writing it)
+__global__ void k_interface_update(Prm P, int64_t n, const double* T, const double* dp, const double* chi,
+                                   const double* dd, double* T1, double* dp1, double* chi1, double* cep,
+                                   int32_t* mode, unsigned long long* counts) {
+    __shared__ unsigned int s_cnt[N_MODES + 1];
+    if (threadIdx.x < N_MODES + 1) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) {
+        Pt p;
+        double ddv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            p.T[i] = T[3 * e + i];
+            p.dp[i] = dp[3 * e + i];
+            ddv[i] = dd[3 * e + i];
+        }
+        p.chis = chi[3 * e];
+        p.chit = chi[3 * e + 1];
+        p.wdil = chi[3 * e + 2];
+        int st = 0;
+        const Res<3> r = update(P, p, ddv, cep != nullptr, &st);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T1[3 * e + i] = r.T[i].v;
+            dp1[3 * e + i] = r.dp[i].v;
+        }
+        chi1[3 * e] = r.chis.v;
+        chi1[3 * e + 1] = r.chit.v;
+        chi1[3 * e + 2] = r.wdil.v;
+        if (cep) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) cep[9 * e + 3 * i + j] = r.T[i].d[j];
+        }
+        if (mode) mode[e] = r.mode;
+        atomicAdd(&s_cnt[r.mode], 1u);
+        if (st) atomicAdd(&s_cnt[N_MODES], 1u);
+    }
+    __syncthreads();
+    if (counts && threadIdx.x < N_MODES + 1 && s_cnt[threadIdx.x])
+        atomicAdd(&counts[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+}  // namespace
+}  // namespace hm
+
+extern "C" hm_status hm_interface_update(const hm_interface_params* prm, int64_t n, const double* T_dev,
+                                         const double* dp_dev, const double* chi_dev, const double* dd_dev,
+                                         double* T1_dev, double* dp1_dev, double* chi1_dev, double* cep_dev,
+                                         int32_t* mode_dev, int64_t* counts, void* stream) {
+    using namespace hm;
+    HM_API_BEGIN
+    if (!prm) fail(HM_EINVAL, "interface_update: params is NULL");
+    if (n < 0) fail(HM_EINVAL, "interface_update: n < 0");
+    const hm_interface_params& q = *prm;
+    if (!finite_pos(q.Ks) || !finite_pos(q.Kn)) fail(HM_EINVAL, "interface_update: stiffnesses must be > 0");
+    if (!finite_nonneg(q.fp) || !finite_nonneg(q.fr) || !finite_nonneg(q.psip) || !finite_nonneg(q.cp) ||
+        !finite_nonneg(q.sigp) || !finite_nonneg(q.wc) || !finite_nonneg(q.alphaR))
+        fail(HM_EINVAL, "interface_update: friction, dilatancy, strengths, w_c and alpha_R must be finite and >= 0");
+    if (!(q.dc > 0.0) || std::isnan(q.dc)) fail(HM_EINVAL, "interface_update: d_c must be > 0");
+    if (n > 0 && (!T_dev || !dp_dev || !chi_dev || !dd_dev || !T1_dev || !dp1_dev || !chi1_dev))
+        fail(HM_EINVAL, "interface_update: a state or increment pointer is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf<unsigned long long> cnt;
+    if (counts) {
+        cnt.alloc(N_MODES + 1);
+        HM_CUDA(cudaMemsetAsync(cnt.p, 0, cnt.bytes(), st));
+    }
+    const Prm P{q.Ks, q.Kn, q.fp, q.fr, q.psip, q.dc, q.cp, q.sigp, q.wc, q.alphaR};
+    if (n > 0) {
+        const int nt = 128;
+        k_interface_update<<<(unsigned)ceil_div(n, nt), nt, 0, st>>>(P, n, T_dev, dp_dev, chi_dev, dd_dev, T1_dev,
+                                                                     dp1_dev, chi1_dev, cep_dev, mode_dev,
+                                                                     counts ? cnt.p : nullptr);
+        HM_LAUNCH_CHECK();
+    }
+    if (counts) {
+        unsigned long long h[N_MODES + 1];
+        HM_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i <= N_MODES; ++i) counts[i] = (int64_t)h[i];
+        if (h[N_MODES]) fail(HM_ENOCONV, "interface_update: a plastic multiplier did not converge (" +
+                                             std::to_string(h[N_MODES]) + " points)");
+    }
+    HM_API_END
+}

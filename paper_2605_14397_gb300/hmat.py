@@ -97,6 +97,10 @@ class hm_solve_info(ctypes.Structure):
                 ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
+class hm_interface_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("Ks", "Kn", "fp", "fr", "psip", "dc", "cp", "sigp", "wc", "alphaR")]
+
+
 _LIB = None
 
 # (name, restype, argtypes) of every exported entry point declared in include/hmat.h
@@ -152,6 +156,8 @@ SIGNATURES = [
     ("hm_hmat_set_tile_shape", _I, [_VP, ctypes.POINTER(hm_tile_shape), _VP]),
     ("hm_hmat_get_tile_shape", _I, [_VP, ctypes.POINTER(hm_tile_shape)]),
     ("hm_tune_tile_shape", _I, [_VP, _VP, _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
+    ("hm_interface_update", _I, [ctypes.POINTER(hm_interface_params), _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                 _VP, _VP, _P64, _VP]),
     ("hm_ilu_select", _I, [_I64, _VP, _VP, _VP, _D, _VP, ctypes.POINTER(_I64)]),
     ("hm_ilu_assemble", _I, [ctypes.c_int32, _I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                              ctypes.POINTER(_I64)]),
@@ -665,3 +671,36 @@ def ilu_leaf_colours(rowptr, col, leaf_of, n_leaves):
     _check(lib().hm_ilu_leaf_colours(n, rp.ctypes.data, cl.ctypes.data, lf.ctypes.data, int(n_leaves),
                                      out.ctypes.data, ctypes.byref(nc)))
     return out[:int(n_leaves)], nc.value
+
+
+# ---------------------------------------------------------------- interface law
+INTERFACE_MODES = ("elastic", "coulomb", "tensile", "open", "apex")
+
+
+def interface_update(params, T, dp, chi, dd, T1=None, dp1=None, chi1=None, tangent=True, modes=True,
+                     counts=False, stream=None):
+    """Constitutive update of the interface points and their consistent tangent
+    (hm_interface_update).  params: dict or object with Ks, Kn, fp, fr, psip, dc, cp,
+    sigp, wc, alphaR; T, dp, chi, dd: (n, 3) FP64 CUDA tensors (T'^n, delta^p, (chi_s,
+    chi_t, w_dil), Delta delta).  Outputs default to new tensors (pass the inputs for an
+    in-place update).  Returns (T1, dp1, chi1, cep (n, 3, 3) or None, mode (n,) int32 or
+    None, counts (6,) int64 numpy or None)."""
+    import torch
+    n = T.shape[0]
+    for a in (T, dp, chi, dd):
+        assert a.dtype == torch.float64 and a.is_cuda and a.is_contiguous() and tuple(a.shape) == (n, 3)
+    get = (lambda k: params[k]) if isinstance(params, dict) else (lambda k: getattr(params, k))
+    prm = hm_interface_params(*[float(get(k)) for k, _ in hm_interface_params._fields_])
+    T1 = torch.empty_like(T) if T1 is None else T1
+    dp1 = torch.empty_like(dp) if dp1 is None else dp1
+    chi1 = torch.empty_like(chi) if chi1 is None else chi1
+    cep = torch.empty((n, 3, 3), dtype=torch.float64, device=T.device) if tangent else None
+    mode = torch.empty(n, dtype=torch.int32, device=T.device) if modes else None
+    cnt = np.zeros(6, dtype=np.int64) if counts else None
+    null = ctypes.c_void_p(None)
+    _check(lib().hm_interface_update(ctypes.byref(prm), int(n), _dptr(T), _dptr(dp), _dptr(chi), _dptr(dd),
+                                     _dptr(T1), _dptr(dp1), _dptr(chi1), _dptr(cep) if tangent else null,
+                                     _dptr(mode) if modes else null,
+                                     cnt.ctypes.data_as(_P64) if counts else None,
+                                     ctypes.c_void_p(_stream_ptr(stream))))
+    return T1, dp1, chi1, cep, mode, cnt

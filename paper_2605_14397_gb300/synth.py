@@ -202,3 +202,46 @@ def lp_initial_weights(hidden=32, seed=1607, n_features=8, n_out=3):
     W2 = rng.uniform(-1.0, 1.0, size=(H, H)) / math.sqrt(H)
     parts = [W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), np.zeros(n_out * H), np.zeros(n_out)]
     return np.concatenate(parts)
+
+
+# Interface material sets (Sec. 2.2 parameters in units of the traction scale and of the
+# element size): an intact, softening joint; a pre-existing fault (no tensile strength or
+# cohesion, w_c = 0); a brittle joint that reaches full damage within the states drawn
+# below; a joint without softening.
+INTERFACE_PARAMS = {
+    "softening": dict(Ks=10.0, Kn=20.0, fp=0.6, fr=0.3, psip=0.1, dc=0.2, cp=0.1, sigp=0.5, wc=0.4, alphaR=0.5),
+    "fault": dict(Ks=10.0, Kn=20.0, fp=0.6, fr=0.45, psip=0.05, dc=0.1, cp=0.0, sigp=0.0, wc=0.0, alphaR=0.0),
+    "brittle": dict(Ks=10.0, Kn=20.0, fp=0.6, fr=0.3, psip=0.1, dc=0.2, cp=0.1, sigp=0.5, wc=0.03, alphaR=0.5),
+    "perfect": dict(Ks=15.0, Kn=30.0, fp=0.6, fr=0.6, psip=0.1, dc=1e300, cp=0.2, sigp=1.0, wc=1e300,
+                    alphaR=0.0),
+}
+
+
+def interface_states(n, seed, open_fraction=0.1):
+    """Seeded states and increments of n interface points: effective traction T'^n (mostly
+    compressive, some tensile), inelastic DD delta^p, (chi_s, chi_t, w_dil) consistent
+    with it (each at least the magnitude it bounds) and a DD increment; a fraction of the
+    points carries a normal inelastic opening beyond 0.05 (an open fracture), another an
+    increment that is mostly opening.  Arrays
+    (n, 3) FP64."""
+    rng = np.random.default_rng(seed)
+    T = np.empty((n, 3))
+    T[:, :2] = rng.normal(size=(n, 2)) * 0.2
+    T[:, 2] = -rng.uniform(-0.3, 1.5, size=n)
+    dp = np.empty((n, 3))
+    dp[:, :2] = rng.normal(size=(n, 2)) * 0.02
+    dp[:, 2] = np.abs(rng.normal(size=n)) * 0.005
+    op = rng.uniform(size=n) < open_fraction
+    dp[op, 2] += rng.uniform(0.05, 0.2, size=int(op.sum()))
+    T[op] *= rng.uniform(0.0, 0.2, size=(int(op.sum()), 1))
+    chi = np.empty((n, 3))
+    chi[:, 0] = np.hypot(dp[:, 0], dp[:, 1]) * rng.uniform(1.0, 1.5, size=n)
+    chi[:, 1] = np.linalg.norm(dp, axis=1) * rng.uniform(1.0, 1.5, size=n)
+    chi[:, 2] = np.abs(rng.normal(size=n)) * 0.002
+    dd = np.empty((n, 3))
+    dd[:, :2] = rng.normal(size=(n, 2)) * 0.08
+    dd[:, 2] = rng.normal(size=n) * 0.025
+    pull = rng.uniform(size=n) < 0.2                # mostly opening increments
+    dd[pull, :2] *= 0.1
+    dd[pull, 2] = rng.uniform(0.02, 0.08, size=int(pull.sum()))
+    return T, dp, chi, dd

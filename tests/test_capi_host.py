@@ -171,3 +171,23 @@ def test_learned_model_host_side(tmp_path):
     L = hmat.lib()
     assert L.hm_lp_train(None, 1, 1e-3, None, None) == hmat.HM_EINVAL
     assert L.hm_lp_add_samples(m.handle, None, None, 0) == hmat.HM_EINVAL
+
+
+def test_interface_update_argument_checks(L):
+    """Parameter validation happens before any device work; no points is a no-op."""
+    good = dict(Ks=10.0, Kn=20.0, fp=0.6, fr=0.3, psip=0.1, dc=0.2, cp=0.1, sigp=0.5, wc=0.4, alphaR=0.5)
+
+    def call(n=0, **kw):
+        p = dict(good)
+        p.update(kw)
+        prm = hmat.hm_interface_params(*[p[k] for k, _ in hmat.hm_interface_params._fields_])
+        null = ctypes.c_void_p(None)
+        return L.hm_interface_update(ctypes.byref(prm), n, null, null, null, null, null, null, null, null, null,
+                                     None, null)
+    assert call() == hmat.HM_OK
+    for bad in (dict(Ks=0.0), dict(Kn=-1.0), dict(dc=0.0), dict(fp=-0.1), dict(wc=float("nan")),
+                dict(sigp=float("inf"))):
+        assert call(**bad) == hmat.HM_EINVAL, bad
+    assert call(n=-1) == hmat.HM_EINVAL
+    assert call(n=5) == hmat.HM_EINVAL and "NULL" in hmat.last_error()
+    assert L.hm_interface_update(None, 0, *([ctypes.c_void_p(None)] * 9), None, None) == hmat.HM_EINVAL

@@ -221,10 +221,13 @@ hm_status hm_hmat_timing(const hm_hmat* h, int enable);
 hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
 
 /* ---------------------------------------------------------------- tangent solve
- * Solve A x = b with A = E - diag(k) - shift I: the elastic block of the Jacobian
- * (eq. jac_mech) with the interface tangent C^ep = diag(k) (isotropic interface
- * stiffness K_s = K_n = k per element, Sec. 2.2) and the quasi-dynamic term
- * eta/dt = shift (eq. ElasSystem).  The paper solves this A11 system with a Krylov
+ * Solve A x = b with A = E - diag(k) - C^ep - shift I: the elastic block of the Jacobian
+ * (eq. jac_mech) with the interface tangent as an isotropic stiffness k per element
+ * (K_s = K_n = k, Sec. 2.2) and/or a block-diagonal consistent tangent C^ep (3x3 per
+ * element, opts.cep_dev, e.g. from hm_interface_update), and the quasi-dynamic term
+ * eta/dt = shift (eq. ElasSystem).  With C^ep the point-Jacobi and leaf block-Jacobi
+ * blocks and the ILU pattern hold its whole 3x3 blocks; the learned preconditioner
+ * takes k only (HM_EINVAL with C^ep).  The paper solves this A11 system with a Krylov
  * method and a Jacobi preconditioner (Sec. 3.3.1); here: restarted flexible GMRES(m)
  * with right preconditioning, classical Gram-Schmidt applied twice, Givens rotations,
  * all Krylov vectors, dot products and rotations in FP64 on the device, x0 = 0.
@@ -271,6 +274,8 @@ typedef struct {
     int pad_;
     const hm_lp* lp;   /* model for HM_PRECOND_LEARNED (NULL otherwise) */
     double ilu_p;      /* HM_PRECOND_ILU: fraction of the near-field entries kept (0 = 0.01) */
+    const double* cep_dev;  /* block-diagonal C^ep (device, N x 9: per element in user order, row-major
+                               3x3 in its frame (s1, s2, n), e.g. from hm_interface_update) or NULL */
 } hm_solve_opts;
 
 typedef struct {
@@ -286,19 +291,21 @@ hm_status hm_gmres_solve(const hm_hmat* h, const double* k_dev, double shift, co
                          double* x_dev, int nrhs, const hm_solve_opts* opt, hm_solve_info* info,
                          void* stream);
 
-/* The ILU preconditioner that hm_gmres_solve builds for A = E - diag(k) - shift I and the
- * fraction p (Sec. 3.3.1), to host arrays (any may be NULL; pass NULL arrays first to
+/* The ILU preconditioner that hm_gmres_solve builds for A = E - diag(k) - C^ep - shift I
+ * and the fraction p (Sec. 3.3.1), to host arrays (any may be NULL; pass NULL arrays first to
  * learn n and nnz).  n_out: 3N; nnz_out: entries of the pattern; n_colours_out: leaf
  * colours.  order[n]: factorization position -> cluster DOF position (the cluster order
  * of hm_tree_export: DOF 3 q + c of the element at cluster position q); rowptr[n + 1],
  * col[nnz]: the pattern in factorization order, columns increasing; a_val[nnz]: the
- * selected entries of E (the diagonal holds E's entry if selected, else 0), before
- * -k - shift is added; lu_val[nnz]: ILU(0) of the matrix with -k - shift on the
- * diagonal (multipliers of the unit lower factor left of the diagonal, the upper factor
- * on and right of it).  k_dev as in hm_gmres_solve.  Synchronises the stream. */
-hm_status hm_ilu_export(const hm_hmat* h, const double* k_dev, double shift, double p, int64_t* n_out,
-                        int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
-                        double* a_val, double* lu_val, void* stream);
+ * selected entries of E (the diagonal holds E's entry if selected, else 0; with C^ep
+ * every element's 3x3 block is in the pattern, E's entry or 0), before -k - C^ep - shift
+ * is added; lu_val[nnz]: ILU(0) of the matrix with -k - C^ep - shift added (multipliers
+ * of the unit lower factor left of the diagonal, the upper factor on and right of it).
+ * k_dev as in hm_gmres_solve, cep_dev as opts.cep_dev there (NULL: none).  Synchronises
+ * the stream. */
+hm_status hm_ilu_export(const hm_hmat* h, const double* k_dev, const double* cep_dev, double shift, double p,
+                        int64_t* n_out, int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr,
+                        int32_t* col, double* a_val, double* lu_val, void* stream);
 
 /* z = (L U)^-1 r with the factors of the last ILU factorization of this H-matrix (made by
  * hm_gmres_solve with HM_PRECOND_ILU or by hm_ilu_export with lu_val): forward

@@ -9,7 +9,8 @@ consistent tangent C^ep (block diagonal) plus the fraction p (0 < p <= 1, 0.01 b
 default) of the entries of the full-rank (near-field) blocks of the hierarchical E that
 have the largest absolute value; the inverse of that sparse matrix is applied through an
 incomplete LU factorization.  Readings taken where the paper is silent:
-  * C^ep is -diag(k) (- shift), the tangent A = E - diag(k) - shift I of this build;
+  * C^ep is diag(k) or a block-diagonal matrix of 3x3 element blocks (the tangent
+    A = E - diag(k) - C^ep - shift I); all of C^ep's entries belong to the pattern;
   * the near-field entries are those of the inadmissible leaf pairs of the block
     partition (eta), whatever the compression later does with the admissible blocks;
   * the selection is global over all near-field entries: the ceil(p n) largest in
@@ -68,9 +69,12 @@ def select_largest(i, j, v, p):
     return i[order], j[order], v[order]
 
 
-def sparse_tangent(Emat, tree, k=None, p=0.01, eta=2.0, shift=0.0):
-    """The sparse approximation of A = E - diag(k) - shift I in cluster DOF order, as a
-    list of rows {column: value}; k per element (on its 3 DOFs) or per DOF."""
+def sparse_tangent(Emat, tree, k=None, p=0.01, eta=2.0, shift=0.0, cep=None):
+    """The sparse approximation of A = E - diag(k) - C^ep - shift I in cluster DOF order,
+    as a list of rows {column: value}; k per element (on its 3 DOFs) or per DOF; cep the
+    block-diagonal consistent tangent, (N, 3, 3) in user element order, which enters with
+    every entry of its blocks (Sec. 3.3.1: the sparse matrix is C^ep plus the selected
+    near-field entries)."""
     n = Emat.shape[0]
     i, j, v = select_largest(*near_entries(Emat, tree, eta), p)
     rows = [dict() for _ in range(n)]
@@ -83,6 +87,14 @@ def sparse_tangent(Emat, tree, k=None, p=0.01, eta=2.0, shift=0.0):
         d += kd[cluster_dofs(tree)]
     for a in range(n):
         rows[a][a] = rows[a].get(a, 0.0) - d[a]
+    if cep is not None:
+        cep = np.asarray(cep, dtype=np.float64).reshape(n // 3, 3, 3)
+        perm = np.asarray(tree.perm)
+        for q in range(n // 3):            # cluster position q holds user element perm[q]
+            for r in range(3):
+                for c in range(3):
+                    a, b = 3 * q + r, 3 * q + c
+                    rows[a][b] = rows[a].get(b, 0.0) - cep[perm[q], r, c]
     return rows
 
 
@@ -192,11 +204,11 @@ def solve_depth(rows):
     return int(lev.max()) if len(rows) else 0
 
 
-def ilu_preconditioner(Emat, tree, k=None, p=0.01, eta=2.0, shift=0.0, ordering="cluster"):
+def ilu_preconditioner(Emat, tree, k=None, p=0.01, eta=2.0, shift=0.0, ordering="cluster", cep=None):
     """M^-1 for vectors in user DOF order: permute to the factorization order (cluster
     order, or the leaf-colour order), apply (L U)^-1 of the sparse approximation, permute
     back.  Returns (apply, nnz of the pattern)."""
-    rows = sparse_tangent(Emat, tree, k, p, eta, shift)
+    rows = sparse_tangent(Emat, tree, k, p, eta, shift, cep)
     cd = cluster_dofs(tree)
     if ordering == "cluster":
         order = np.arange(len(rows))

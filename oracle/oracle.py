@@ -272,9 +272,10 @@ def dof_index(perm_elems):
 
 # ------------------------------------------------------------------ tangent + preconditioner
 
-def tangent_dense(Emat, k=None, shift=0.0):
-    """A = E - diag(k) - shift I, k per element (applied to its 3 DOFs) or per DOF
-    (eq. jac_mech with C^ep = diag(k) and eta/dt = shift)."""
+def tangent_dense(Emat, k=None, shift=0.0, cep=None):
+    """A = E - diag(k) - C^ep - shift I (eq. jac_mech, eta/dt = shift): k per element
+    (applied to its 3 DOFs) or per DOF; cep the block-diagonal consistent tangent as
+    (N, 3, 3) blocks, element e's block on DOFs 3e..3e+2 (user order)."""
     A = Emat.copy()
     n = A.shape[0]
     d = np.zeros(n)
@@ -283,6 +284,10 @@ def tangent_dense(Emat, k=None, shift=0.0):
         d += np.repeat(k, 3) if k.size * 3 == n else k
     d += shift
     A[np.arange(n), np.arange(n)] -= d
+    if cep is not None:
+        cep = np.asarray(cep, dtype=np.float64).reshape(n // 3, 3, 3)
+        for e in range(n // 3):
+            A[3 * e:3 * e + 3, 3 * e:3 * e + 3] -= cep[e]
     return A
 
 

@@ -227,16 +227,16 @@ hm_status hm_gmres_solve(const hm_hmat* hh, const double* k_dev, double shift, c
     HM_API_END
 }
 
-hm_status hm_ilu_export(const hm_hmat* hh, const double* k_dev, double shift, double p, int64_t* n_out,
-                        int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
-                        double* a_val, double* lu_val, void* stream) {
+hm_status hm_ilu_export(const hm_hmat* hh, const double* k_dev, const double* cep_dev, double shift, double p,
+                        int64_t* n_out, int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr,
+                        int32_t* col, double* a_val, double* lu_val, void* stream) {
     HM_API_BEGIN
     hm::g_last_error.clear();
     if (!hh) hm::fail(HM_EINVAL, "ilu_export: NULL H-matrix");
     if (!(p > 0.0 && p <= 1.0)) hm::fail(HM_EINVAL, "ilu_export: p must lie in (0, 1]");
     if (!std::isfinite(shift)) hm::fail(HM_ENAN, "ilu_export: shift is not finite");
-    hm::ilu_export_for(const_cast<hm::HMat&>(hh->h), k_dev, shift, p, n_out, nnz_out, n_colours_out, order, rowptr,
-                       col, a_val, lu_val, (cudaStream_t)stream);
+    hm::ilu_export_for(const_cast<hm::HMat&>(hh->h), k_dev, cep_dev, shift, p, n_out, nnz_out, n_colours_out, order,
+                       rowptr, col, a_val, lu_val, (cudaStream_t)stream);
     HM_API_END
 }
 

@@ -226,9 +226,9 @@ std::string tune_tile_shape(HMat& H, const hm_tile_shape* shapes, int n, int rep
 void graphs_clear(HMat& H);
 void matvec_graph(HMat& H, const void* x, void* y, int nrhs, int dtype, cudaStream_t st);
 struct LPModel;
-void ilu_export_for(HMat& H, const double* kel, double shift, double p, int64_t* n_out, int64_t* nnz_out,
-                    int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col, double* a_val,
-                    double* lu_val, cudaStream_t st);
+void ilu_export_for(HMat& H, const double* kel, const double* cep, double shift, double p, int64_t* n_out,
+                    int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
+                    double* a_val, double* lu_val, cudaStream_t st);
 void ilu_apply_user(HMat& H, const double* r, double* z, int nrhs, cudaStream_t st);
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp = nullptr);

@@ -3,7 +3,8 @@
 // fraction p of the near-field entries of E with the largest magnitude, and that sparse
 // matrix is applied through its ILU(0) factors.
 //
-// Plan (once per H-matrix and p; k and shift change only the diagonal):
+// Plan (once per H-matrix, p and kind of interface term; k, C^ep and shift change only
+// values):
 //   * selection: the ceil(p n) entries of largest |v| among the n entries of the FP32 near
 //     tiles of inadmissible leaf pairs -- a radix select over the bit patterns of |v|
 //     (three histogram passes), then a compaction of the entries above the threshold
@@ -13,7 +14,9 @@
 //     leaves of one colour share no entry, so the factorization and the triangular solves
 //     handle them in parallel, one CTA per leaf, and each solve is one launch per colour;
 //   * CSR of the pattern in that order, the diagonal always present (E's entry if
-//     selected, else 0; -k - shift is added per factorization).
+//     selected, else 0; -k - shift is added per factorization); with a block-diagonal
+//     C^ep (3x3 per element) every element's whole 3x3 block is present, since C^ep
+//     belongs to the sparse matrix entirely.
 // Factorization (per solve): ILU(0) in FP64, level by level of the lower triangle (a row
 // waits for the rows its multipliers name), a warp per row (its multipliers in column
 // order, the update from a finished row confined to the pattern).  Application: forward and backward substitution in FP64,
@@ -31,6 +34,7 @@ namespace hm {
 
 struct IluPlan {
     double p = 0.0;
+    bool self_blocks = false;  // each element's 3x3 block forced into the pattern
     int64_t n = 0;        // DOFs
     int64_t nnz = 0;
     int64_t m_selected = 0;
@@ -48,6 +52,7 @@ struct IluPlan {
     // their levels, for the lower and the upper triangle
     DevBuf<uint8_t> lrow_lo, llev_lo, lrow_up, llev_up;
     DevBuf<int64_t> rowptr, diagpos;
+    DevBuf<int64_t> selfpos;           // [3n]: positions of row a's entries in its element's block
     DevBuf<double> aval, lu;
     DevBuf<double> yv, zv;             // new-order work vectors, nr x n
     int nr_cap = 0;
@@ -153,6 +158,20 @@ __global__ void k_ilu_diag(double* __restrict__ lu, const int64_t* __restrict__ 
                            const int32_t* __restrict__ order, const double* __restrict__ d, int64_t n) {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a < n) lu[diagpos[a]] -= d[order[a]];
+}
+
+// lu[block entries of row a] -= blk[element][row comp][col comp] (off the diagonal; blk
+// in cluster element order with a zero diagonal)
+__global__ void k_ilu_self(double* __restrict__ lu, const int64_t* __restrict__ selfpos,
+                           const int32_t* __restrict__ order, const double* __restrict__ blk, int64_t n) {
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const int32_t r = order[a];
+    const int64_t e = r / 3;
+    const int c = r % 3;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        if (j != c) lu[selfpos[3 * a + j]] -= blk[9 * e + 3 * c + j];
 }
 
 // first position in [lo, hi) of col with col[pos] == c, else -1 (columns increasing)
@@ -379,9 +398,9 @@ int64_t apply_smem_nnz(const IluPlan& P) {
 
 }  // namespace
 
-void ilu_prepare(HMat& H, double p, cudaStream_t st) {
+void ilu_prepare(HMat& H, double p, bool self_blocks, cudaStream_t st) {
     if (!(p > 0.0 && p <= 1.0)) fail(HM_EINVAL, "ilu: p must lie in (0, 1]");
-    if (H.ilu && H.ilu->p == p) return;
+    if (H.ilu && H.ilu->p == p && H.ilu->self_blocks == self_blocks) return;
     if ((int64_t)H.h_near_true_cols.size() != H.n_leaves) fail(HM_EINVAL, "ilu: near-field layout unknown");
     if (H.ndof > INT32_MAX) fail(HM_EINVAL, "ilu: too many DOFs");
     ilu_plan_free(H.ilu);
@@ -389,6 +408,7 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
     IluPlan* P = new IluPlan();
     try {
         P->p = p;
+        P->self_blocks = self_blocks;
         const int64_t n = H.ndof;
         P->n = n;
         const int nl = H.n_leaves;
@@ -471,15 +491,31 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
             V[n_gt + t] = (double)TV[o[t]];
         }
         P->m_selected = m;
+        int64_t mt = m;  // entries of the pattern besides the diagonal
+        if (self_blocks) {
+            // the off-diagonal entries of every element's 3x3 block not selected already
+            std::vector<uint8_t> have((size_t)n * 3, 0);
+            for (int64_t q = 0; q < m; ++q)
+                if (I[q] / 3 == J[q] / 3) have[(size_t)3 * I[q] + J[q] % 3] = 1;
+            for (int64_t r = 0; r < n; ++r)
+                for (int j = 0; j < 3; ++j) {
+                    const int64_t c = 3 * (r / 3) + j;
+                    if (c == r || have[(size_t)3 * r + j]) continue;
+                    I.push_back((int32_t)r);
+                    J.push_back((int32_t)c);
+                    V.push_back(0.0);
+                    ++mt;
+                }
+        }
         // CSR in cluster order (diagonal added, no shift), colours, the colour order
-        std::vector<int64_t> idx(m);
+        std::vector<int64_t> idx(mt);
         std::iota(idx.begin(), idx.end(), (int64_t)0);
         std::vector<double> zero(n, 0.0);
         std::vector<int64_t> rp(n + 1);
-        std::vector<int32_t> cl(m + n);
-        std::vector<double> vl(m + n);
+        std::vector<int32_t> cl(mt + n);
+        std::vector<double> vl(mt + n);
         int64_t nnz = 0;
-        hm_status s1 = hm_ilu_assemble((int32_t)n, m, m, idx.data(), I.data(), J.data(), V.data(), zero.data(),
+        hm_status s1 = hm_ilu_assemble((int32_t)n, mt, mt, idx.data(), I.data(), J.data(), V.data(), zero.data(),
                                        nullptr, rp.data(), cl.data(), vl.data(), &nnz);
         if (s1 != HM_OK) fail(s1, "ilu: assembling the selected pattern failed");
         std::vector<int32_t> leaf_of(n);
@@ -511,10 +547,10 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
         if (P->max_leaf_rows > ILU_ROWS) fail(HM_EINVAL, "ilu: leaves of more than 64 elements are not supported");
         P->h_sched = sched;
         std::vector<int64_t> rp2(n + 1);
-        std::vector<int32_t> cl2(m + n);
-        std::vector<double> vl2(m + n);
+        std::vector<int32_t> cl2(mt + n);
+        std::vector<double> vl2(mt + n);
         int64_t nnz2 = 0;
-        hm_status s3 = hm_ilu_assemble((int32_t)n, m, m, idx.data(), I.data(), J.data(), V.data(), zero.data(),
+        hm_status s3 = hm_ilu_assemble((int32_t)n, mt, mt, idx.data(), I.data(), J.data(), V.data(), zero.data(),
                                        P->h_order.data(), rp2.data(), cl2.data(), vl2.data(), &nnz2);
         if (s3 != HM_OK) fail(s3, "ilu: assembling the ordered pattern failed");
         P->nnz = nnz2;
@@ -523,6 +559,21 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
             dpos[a] = -1;
             for (int64_t q = rp2[a]; q < rp2[a + 1]; ++q)
                 if (cl2[q] == a) dpos[a] = q;
+        }
+        if (self_blocks) {
+            std::vector<int32_t> pos_of(n);
+            for (int64_t a = 0; a < n; ++a) pos_of[P->h_order[a]] = (int32_t)a;
+            std::vector<int64_t> spos((size_t)3 * n, -1);
+            for (int64_t a = 0; a < n; ++a) {
+                const int32_t r = P->h_order[a];
+                for (int j = 0; j < 3; ++j) {
+                    const int32_t c = pos_of[3 * (r / 3) + j];
+                    for (int64_t q = rp2[a]; q < rp2[a + 1]; ++q)
+                        if (cl2[q] == c) spos[(size_t)3 * a + j] = q;
+                    if (spos[(size_t)3 * a + j] < 0) fail(HM_EINVAL, "ilu: an element block entry is missing");
+                }
+            }
+            P->selfpos.upload(spos, st);
         }
         for (int s = 0; s < nl; ++s)
             P->max_leaf_nnz = std::max(P->max_leaf_nnz, rp2[P->h_row0[s] + nrows[s]] - rp2[P->h_row0[s]]);
@@ -593,10 +644,12 @@ void ilu_prepare(HMat& H, double p, cudaStream_t st) {
     H.ilu = P;
 }
 
-void ilu_factor(HMat& H, const double* d_cluster, cudaStream_t st, int* err_dev) {
+void ilu_factor(HMat& H, const double* d_cluster, const double* blk, cudaStream_t st, int* err_dev) {
     IluPlan& P = *H.ilu;
+    if ((blk != nullptr) != P.self_blocks) fail(HM_EINVAL, "ilu: the plan was built for another interface term");
     k_ilu_init<<<gsz(P.nnz, 256), 256, 0, st>>>(P.aval.p, P.lu.p, P.nnz);
     k_ilu_diag<<<gsz(P.n, 256), 256, 0, st>>>(P.lu.p, P.diagpos.p, P.order.p, d_cluster, P.n);
+    if (blk) k_ilu_self<<<gsz(P.n, 256), 256, 0, st>>>(P.lu.p, P.selfpos.p, P.order.p, blk, P.n);
     HM_LAUNCH_CHECK();
     HM_CUDA(cudaMemsetAsync(err_dev, 0, sizeof(int), st));
     const int nlev = (int)P.h_level_first.size() - 1;

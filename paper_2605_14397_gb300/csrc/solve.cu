@@ -1,5 +1,6 @@
-// Tangent solve A x = b, A = E - diag(k) - shift I (eq. jac_mech with C^ep = diag(k),
-// eta/dt = shift): restarted flexible GMRES(m) with right preconditioning, on the device.
+// Tangent solve A x = b, A = E - diag(k) - C^ep - shift I (eq. jac_mech: C^ep block
+// diagonal with 3x3 blocks, or diagonal as k; eta/dt = shift): restarted flexible GMRES(m)
+// with right preconditioning, on the device.
 //
 // The paper solves its A11 system with a Krylov method (BiCGSTAB or GMRES) and a Jacobi
 // preconditioner (Sec. 3.3.1).  Here:
@@ -86,6 +87,32 @@ __global__ void k_diag(const double* __restrict__ kel, double shift, const int32
     d[r] = (kel ? kel[perm[r / 3]] : 0.0) + shift;
 }
 
+// The interface term with a block-diagonal C^ep (eq. jac_mech): d[r] = k + C^ep_ii +
+// shift on the diagonal (cluster DOF order) and blk = C^ep with a zero diagonal, 9 per
+// element in cluster element order (C^ep in user element order, row-major per element).
+__global__ void k_blockdiag(const double* __restrict__ kel, const double* __restrict__ cep, double shift,
+                            const int32_t* __restrict__ perm, int64_t nel, double* __restrict__ d,
+                            double* __restrict__ blk) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nel) return;
+    const int64_t e = perm[q];
+    const double kv = kel ? kel[e] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        d[3 * q + i] = kv + cep[9 * e + 4 * i] + shift;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) blk[9 * q + 3 * i + j] = i == j ? 0.0 : cep[9 * e + 3 * i + j];
+    }
+}
+
+// off-diagonal part of the interface term in row i of element-local block products
+__device__ __forceinline__ double blk_row(const double* __restrict__ blk, const double* __restrict__ zk, int64_t i) {
+    const int64_t e = i / 3;
+    const double* B = blk + 9 * e + 3 * (i % 3);
+    const double* z = zk + 3 * e;
+    return B[0] * z[0] + B[1] * z[1] + B[2] * z[2];
+}
+
 // ---------------------------------------------------------------- block-Jacobi
 
 // Inverse of B = E_ll - diag(d_l) for every leaf l (one CTA each), Gauss-Jordan with
@@ -93,8 +120,9 @@ __global__ void k_diag(const double* __restrict__ kel, double shift, const int32
 __global__ void __launch_bounds__(512) k_bj_build(const LeafDesc* __restrict__ leaves,
                                                   const int64_t* __restrict__ self_off,
                                                   const float* __restrict__ near, const double* __restrict__ d,
-                                                  float* __restrict__ binv, const int64_t* __restrict__ binv_off,
-                                                  float* __restrict__ gscratch, int use_smem, int* __restrict__ err) {
+                                                  const double* __restrict__ blk, float* __restrict__ binv,
+                                                  const int64_t* __restrict__ binv_off, float* __restrict__ gscratch,
+                                                  int use_smem, int* __restrict__ err) {
     extern __shared__ float sm[];
     const LeafDesc L = leaves[blockIdx.x];
     const int n = 3 * L.n;
@@ -109,6 +137,7 @@ __global__ void __launch_bounds__(512) k_bj_build(const LeafDesc* __restrict__ l
         const int r = q / n, c = q % n;
         float v = E[(int64_t)c * L.ld + r];
         if (r == c) v -= (float)d[3 * (int64_t)L.begin + r];
+        if (blk && r / 3 == c / 3) v -= (float)blk[9 * ((int64_t)L.begin + r / 3) + 3 * (r % 3) + c % 3];
         A[q] = v;
     }
     __syncthreads();
@@ -189,8 +218,8 @@ constexpr int BJR_ROWS = 192;
 __global__ void __launch_bounds__(512, 1) k_bj_build_reg(const LeafDesc* __restrict__ leaves,
                                                          const int64_t* __restrict__ self_off,
                                                          const float* __restrict__ near, const double* __restrict__ d,
-                                                         float* __restrict__ binv, const int64_t* __restrict__ binv_off,
-                                                         int* __restrict__ err) {
+                                                         const double* __restrict__ blk, float* __restrict__ binv,
+                                                         const int64_t* __restrict__ binv_off, int* __restrict__ err) {
     extern __shared__ float wsm[];  // final n x n staging (row-major)
     __shared__ float colk[BJR_ROWS], prow[BJR_ROWS];
     __shared__ float cand_v[16];
@@ -211,6 +240,7 @@ __global__ void __launch_bounds__(512, 1) k_bj_build_reg(const LeafDesc* __restr
             if (i < n && j < n) {
                 v = E[(int64_t)j * L.ld + i];
                 if (i == j) v -= (float)d[3 * (int64_t)L.begin + i];
+                if (blk && i / 3 == j / 3) v -= (float)blk[9 * ((int64_t)L.begin + i / 3) + 3 * (i % 3) + j % 3];
             }
             A[a][b] = v;
         }
@@ -382,8 +412,8 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
 // self tile of the FP32 near field.  One CTA per leaf, one thread per element; the 3x3
 // inverse by cofactors in FP64, stored row-major in FP32.
 __global__ void k_j3_build(const LeafDesc* __restrict__ leaves, const int64_t* __restrict__ self_off,
-                           const float* __restrict__ near, const double* __restrict__ d, float* __restrict__ j3,
-                           int* __restrict__ err) {
+                           const float* __restrict__ near, const double* __restrict__ d,
+                           const double* __restrict__ blk, float* __restrict__ j3, int* __restrict__ err) {
     const LeafDesc L = leaves[blockIdx.x];
     const float* T = near + self_off[blockIdx.x];
     for (int e = threadIdx.x; e < L.n; e += blockDim.x) {
@@ -395,6 +425,7 @@ __global__ void k_j3_build(const LeafDesc* __restrict__ leaves, const int64_t* _
             for (int j = 0; j < 3; ++j) {
                 a[i][j] = (double)T[(int64_t)(3 * e + j) * L.ld + 3 * e + i];
                 if (i == j) a[i][j] -= d[3 * p + i];
+                if (blk) a[i][j] -= blk[9 * p + 3 * i + j];
             }
         const double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
         const double c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2];
@@ -471,6 +502,7 @@ __device__ __forceinline__ double yval(const Y* y, int64_t i) { return (double)y
 // pass 1: w = y - d .* z (stored), partial dots with V_0..V_j
 template <class Y>
 __global__ void __launch_bounds__(ROW_NT) k_arn_first(const Y* __restrict__ y, const double* __restrict__ d,
+                                                      const double* __restrict__ blk,
                                                       const double* __restrict__ z, double* __restrict__ w,
                                                       const double* __restrict__ V, int64_t ndof, int nr, int j,
                                                       int64_t vstride, double* __restrict__ part,
@@ -487,6 +519,7 @@ __global__ void __launch_bounds__(ROW_NT) k_arn_first(const Y* __restrict__ y, c
             double v = 0.0;
             if (i < ndof) {
                 v = yval(y, k * ndof + i) - d[i] * z[k * ndof + i];
+                if (blk) v -= blk_row(blk, z + k * ndof, i);
                 w[k * ndof + i] = v;
             }
             wl[u] = v;
@@ -709,7 +742,8 @@ __global__ void k_update_x(double* __restrict__ x, const double* __restrict__ Z,
 // r = b - (y - d .* x), partial ||r||^2
 template <class Y>
 __global__ void __launch_bounds__(ROW_NT) k_residual(const double* __restrict__ b, const Y* __restrict__ y,
-                                                     const double* __restrict__ d, const double* __restrict__ x,
+                                                     const double* __restrict__ d, const double* __restrict__ blk,
+                                                     const double* __restrict__ x,
                                                      double* __restrict__ r, int64_t ndof, int nr,
                                                      double* __restrict__ part) {
     __shared__ double sp[ROW_NT / 32];
@@ -722,7 +756,8 @@ __global__ void __launch_bounds__(ROW_NT) k_residual(const double* __restrict__ 
             const int64_t i = r0 + threadIdx.x + u * ROW_NT;
             if (i < ndof) {
                 const int64_t q = k * ndof + i;
-                const double v = b[q] - (yval(y, q) - d[i] * x[q]);
+                double v = b[q] - (yval(y, q) - d[i] * x[q]);
+                if (blk) v += blk_row(blk, x + k * ndof, i);
                 r[q] = v;
                 s += v * v;
             }
@@ -754,6 +789,8 @@ struct SolveWS {
     DevBuf<double> V, Z, w, r, xc, bc, dc, corr, y64, zi, Hm, cs, sn, g, ylsq, part, h1, h2;
     DevBuf<float> zf, y32, binv, bjscratch, dsc, j3;
     bool dsc_on = false;  // apply the learned per-leaf scalings after block-Jacobi
+    DevBuf<double> blkbuf;  // off-diagonal C^ep blocks, cluster element order
+    const double* blk = nullptr;  // blkbuf.p when the tangent has a block-diagonal C^ep
     DevBuf<int64_t> binv_off, self_off;
     DevBuf<CycleState> st;
     DevBuf<int> active, err, alldone;
@@ -902,11 +939,11 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
         HM_LAUNCH_CHECK();
         if (dtype == HM_F64) {
             apply_E(H, W, zj, nullptr, W.y64.p, nr, HM_F64, fac, st, W.alldone.p);
-            k_arn_first<double><<<nb, ROW_NT, 0, st>>>(W.y64.p, W.dc.p, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
+            k_arn_first<double><<<nb, ROW_NT, 0, st>>>(W.y64.p, W.dc.p, W.blk, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
                                                        W.part.p, W.st.p);
         } else {
             apply_E(H, W, nullptr, W.zf.p, W.y32.p, nr, HM_F32, fac, st, W.alldone.p);
-            k_arn_first<float><<<nb, ROW_NT, 0, st>>>(W.y32.p, W.dc.p, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
+            k_arn_first<float><<<nb, ROW_NT, 0, st>>>(W.y32.p, W.dc.p, W.blk, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
                                                       W.part.p, W.st.p);
         }
         HM_LAUNCH_CHECK();
@@ -940,12 +977,12 @@ std::vector<double> residual(HMat& H, SolveWS& W, const double* rhs, int nr, int
     const int nb = nblk_rows(n);
     if (dtype == HM_F64) {
         apply_E(H, W, W.xc.p, nullptr, W.y64.p, nr, HM_F64, fac, st);
-        k_residual<double><<<nb, ROW_NT, 0, st>>>(rhs, W.y64.p, W.dc.p, W.xc.p, W.r.p, n, nr, W.part.p);
+        k_residual<double><<<nb, ROW_NT, 0, st>>>(rhs, W.y64.p, W.dc.p, W.blk, W.xc.p, W.r.p, n, nr, W.part.p);
     } else {
         // FP32 copy of x, interleaved, for the FP32 product
         k_to_f32_interleaved<<<g1(n * nr), 256, 0, st>>>(W.xc.p, W.zf.p, n, nr);
         apply_E(H, W, nullptr, W.zf.p, W.y32.p, nr, HM_F32, fac, st);
-        k_residual<float><<<nb, ROW_NT, 0, st>>>(rhs, W.y32.p, W.dc.p, W.xc.p, W.r.p, n, nr, W.part.p);
+        k_residual<float><<<nb, ROW_NT, 0, st>>>(rhs, W.y32.p, W.dc.p, W.blk, W.xc.p, W.r.p, n, nr, W.part.p);
     }
     HM_LAUNCH_CHECK();
     std::vector<double> part((size_t)nb * nr);
@@ -1004,7 +1041,7 @@ void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
                                          (int)(sizeof(float) * BJR_ROWS * BJR_ROWS)));
             if (dev >= 0 && dev < 64) attr_done[dev] = true;
         }
-        k_bj_build_reg<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.binv.p,
+        k_bj_build_reg<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.blk, W.binv.p,
                                                       W.binv_off.p, W.err.p);
         HM_LAUNCH_CHECK();
         int e = 0;
@@ -1016,8 +1053,8 @@ void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
     const size_t smem = W.bj_needs_global ? 0 : sizeof(float) * BJ_MAX_ROWS_SMEM * BJ_MAX_ROWS_SMEM;
     if (smem > 48 * 1024)
         HM_CUDA(cudaFuncSetAttribute(k_bj_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bj_build<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.binv.p, W.binv_off.p,
-                                              W.bjscratch.p, W.bj_needs_global ? 0 : 1, W.err.p);
+    k_bj_build<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.blk, W.binv.p,
+                                              W.binv_off.p, W.bjscratch.p, W.bj_needs_global ? 0 : 1, W.err.p);
     HM_LAUNCH_CHECK();
     int e = 0;
     HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1025,10 +1062,24 @@ void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
     if (e) fail(HM_EBREAKDOWN, "a diagonal leaf block of A is singular");
 }
 
-// point-Jacobi inverses of the 3x3 diagonal blocks of E - diag(W.dc)
+// the interface term of the tangent: diag(k) + C^ep + shift I into W.dc (and the
+// off-diagonal C^ep entries into W.blk when cep is given)
+void set_tangent(HMat& H, SolveWS& W, const double* kel, const double* cep, double shift, cudaStream_t st) {
+    if (cep) {
+        if (W.blkbuf.n < (size_t)9 * H.N) W.blkbuf.alloc((size_t)9 * H.N);
+        k_blockdiag<<<g1(H.N), 256, 0, st>>>(kel, cep, shift, H.perm.p, H.N, W.dc.p, W.blkbuf.p);
+        W.blk = W.blkbuf.p;
+    } else {
+        k_diag<<<g1(H.ndof), 256, 0, st>>>(kel, shift, H.perm.p, H.ndof, W.dc.p);
+        W.blk = nullptr;
+    }
+    HM_LAUNCH_CHECK();
+}
+
+// point-Jacobi inverses of the 3x3 diagonal blocks of E - diag(W.dc) - W.blk
 void j3_build(HMat& H, SolveWS& W, cudaStream_t st) {
     HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
-    k_j3_build<<<H.n_leaves, 64, 0, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.j3.p, W.err.p);
+    k_j3_build<<<H.n_leaves, 64, 0, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.blk, W.j3.p, W.err.p);
     HM_LAUNCH_CHECK();
     int e = 0;
     HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1047,8 +1098,7 @@ void bj_solve_cluster(HMat& H, const double* kel, double shift, const double* v,
                       cudaStream_t st) {
     if (nr < 1 || nr > 16) fail(HM_EINVAL, "block-Jacobi solve: 1 to 16 right-hand sides");
     SolveWS& W = workspace(H, nr, 1, st);
-    k_diag<<<g1(H.ndof), 256, 0, st>>>(kel, shift, H.perm.p, H.ndof, W.dc.p);
-    HM_LAUNCH_CHECK();
+    set_tangent(H, W, kel, nullptr, shift, st);
     bj_build(H, W, st);
     std::vector<CycleState> cs(nr, CycleState{0, 0, 0, 0, 0.0, 0.0});
     HM_CUDA(cudaMemcpyAsync(W.st.p, cs.data(), nr * sizeof(CycleState), cudaMemcpyHostToDevice, st));
@@ -1058,16 +1108,15 @@ void bj_solve_cluster(HMat& H, const double* kel, double shift, const double* v,
     HM_CUDA(cudaStreamSynchronize(st));
 }
 
-// The ILU preconditioner of A = E - diag(k) - shift I for a fraction p, built and
+// The ILU preconditioner of A = E - diag(k) - C^ep - shift I for a fraction p, built and
 // factored, then copied to the host (see ilu_export).
-void ilu_export_for(HMat& H, const double* kel, double shift, double p, int64_t* n_out, int64_t* nnz_out,
-                    int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col, double* a_val,
-                    double* lu_val, cudaStream_t st) {
+void ilu_export_for(HMat& H, const double* kel, const double* cep, double shift, double p, int64_t* n_out,
+                    int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
+                    double* a_val, double* lu_val, cudaStream_t st) {
     SolveWS& W = workspace(H, 1, 1, st);
-    k_diag<<<g1(H.ndof), 256, 0, st>>>(kel, shift, H.perm.p, H.ndof, W.dc.p);
-    HM_LAUNCH_CHECK();
-    ilu_prepare(H, p, st);
-    if (lu_val) ilu_factor(H, W.dc.p, st, W.err.p);
+    set_tangent(H, W, kel, cep, shift, st);
+    ilu_prepare(H, p, cep != nullptr, st);
+    if (lu_val) ilu_factor(H, W.dc.p, W.blk, st, W.err.p);
     ilu_export(H, n_out, nnz_out, n_colours_out, order, rowptr, col, a_val, lu_val, st);
 }
 
@@ -1086,6 +1135,7 @@ void ilu_apply_user(HMat& H, const double* r, double* z, int nrhs, cudaStream_t 
 
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp) {
+    const double* cep = o.cep_dev;
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     if (nrhs < 1 || nrhs > 16) fail(HM_EINVAL, "gmres_solve: 1 to 16 right-hand sides");
@@ -1103,6 +1153,8 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     const double ilu_p = o.ilu_p > 0.0 ? o.ilu_p : 0.01;
     if (o.precond == HM_PRECOND_ILU && !(ilu_p <= 1.0)) fail(HM_EINVAL, "gmres_solve: ilu_p must lie in (0, 1]");
     if (o.precond == HM_PRECOND_LEARNED && !lp) fail(HM_EINVAL, "gmres_solve: the learned preconditioner needs a model");
+    if (o.precond == HM_PRECOND_LEARNED && cep)
+        fail(HM_EINVAL, "gmres_solve: the learned preconditioner takes a diagonal interface term (k), not C^ep");
     if (!has_factors(H, 0)) fail(HM_EINVAL, "gmres_solve: the FP32 factors are required (storage F32 or F32_BF16)");
     // refinement corrections: BF16 factors (mixed; FP32 if BF16 is not stored) or the
     // FP32 factors themselves (PLAIN32: the same refinement without the BF16 operator)
@@ -1113,15 +1165,16 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     // through every Krylov vector)
     HM_CUDA(cudaMemsetAsync(W.err.p, 0, sizeof(int), st));
     if (kel) k_nonfinite<<<152, 256, 0, st>>>(kel, H.N, W.err.p);
+    if (cep) k_nonfinite<<<152, 256, 0, st>>>(cep, 9 * H.N, W.err.p);
     k_nonfinite<<<152, 256, 0, st>>>(b, n * nrhs, W.err.p + 0);
     HM_LAUNCH_CHECK();
     {
         int e = 0;
         HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         HM_CUDA(cudaStreamSynchronize(st));
-        if (e) fail(HM_ENAN, "gmres_solve: the stiffness k or the right-hand side holds NaN or Inf");
+        if (e) fail(HM_ENAN, "gmres_solve: the stiffness k, C^ep or the right-hand side holds NaN or Inf");
     }
-    k_diag<<<g1(n), 256, 0, st>>>(kel, shift, H.perm.p, n, W.dc.p);
+    set_tangent(H, W, kel, cep, shift, st);
     k_to_cluster<<<g1(n * nrhs), 256, 0, st>>>(b, W.bc.p, H.perm.p, n, nrhs);
     HM_LAUNCH_CHECK();
     const PcKind pc = (o.precond == HM_PRECOND_BLOCKJ || o.precond == HM_PRECOND_LEARNED)
@@ -1131,8 +1184,8 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     W.dsc_on = false;
     if (pc == PC_POINT) j3_build(H, W, st);
     if (pc == PC_ILU) {
-        ilu_prepare(H, ilu_p, st);
-        ilu_factor(H, W.dc.p, st, W.err.p);
+        ilu_prepare(H, ilu_p, cep != nullptr, st);
+        ilu_factor(H, W.dc.p, W.blk, st, W.err.p);
     }
     if (pc == PC_LEAF) {
         bj_build(H, W, st);

@@ -67,7 +67,7 @@ class hm_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mode", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int), ("lp", ctypes.c_void_p),
-                ("ilu_p", ctypes.c_double)]
+                ("ilu_p", ctypes.c_double), ("cep_dev", ctypes.c_void_p)]
 
 
 class hm_tile_shape(ctypes.Structure):
@@ -134,7 +134,7 @@ SIGNATURES = [
                             ctypes.POINTER(hm_solve_info), _VP]),
     ("hm_batch_create", _I, [ctypes.POINTER(_VP), _I, _VP, ctypes.POINTER(_VP)]),
     ("hm_ilu_apply", _I, [_VP, _VP, _VP, _I, _VP]),
-    ("hm_ilu_export", _I, [_VP, _VP, _D, _D, _P64, _P64, ctypes.POINTER(ctypes.c_int32), _VP, _VP, _VP, _VP, _VP,
+    ("hm_ilu_export", _I, [_VP, _VP, _VP, _D, _D, _P64, _P64, ctypes.POINTER(ctypes.c_int32), _VP, _VP, _VP, _VP, _VP,
                            _VP]),
     ("hm_lp_param_count", _I64, [_I]),
     ("hm_lp_create", _I, [_I, _VP, ctypes.POINTER(_VP)]),
@@ -358,20 +358,23 @@ class HMatrix:
                                     ctypes.c_void_p(_stream_ptr(stream))))
 
     def solve(self, b, x, k=None, shift=0.0, tol=1e-8, restart=50, maxit=2000, precond="blockj", mode="f64",
-              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None, ilu_p=0.0):
-        """Solve (E - diag(k) - shift I) x = b on the device (b, x: float64 CUDA tensors of
-        shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None).  precond "none",
+              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None, ilu_p=0.0, cep=None):
+        """Solve (E - diag(k) - C^ep - shift I) x = b on the device (b, x: float64 CUDA tensors
+        of shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None; cep: float64 CUDA
+        tensor (N, 3, 3) of per-element tangent blocks, user order, or None).  precond "none",
         "jacobi3", "blockj", "ilu" (ilu_p: fraction of the near field, 0 = 0.01) or "learned";
         mode "f64", "mixed" or "plain32".  Returns the
         per-RHS info dicts; raises HMError unless every RHS converged (raise_on_error)."""
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         assert b.is_contiguous() and x.is_contiguous() and (k is None or k.is_contiguous())
+        assert cep is None or (cep.is_contiguous() and cep.numel() == 3 * self.ndof)
         o = hm_solve_opts(float(tol), int(restart), int(maxit),
                           {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "learned": HM_PRECOND_LEARNED,
                            "jacobi3": HM_PRECOND_JACOBI3, "ilu": HM_PRECOND_ILU}[precond],
                           {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED, "plain32": HM_SOLVE_PLAIN32}[mode],
                           float(inner_tol), int(max_outer), 0,
-                          model.handle.value if model is not None else None, float(ilu_p))
+                          model.handle.value if model is not None else None, float(ilu_p),
+                          cep.data_ptr() if cep is not None else None)
         info = (hm_solve_info * nrhs)()
         st = lib().hm_gmres_solve(self.handle, _dptr(k) if k is not None else None, float(shift), _dptr(b), _dptr(x),
                                   int(nrhs), ctypes.byref(o), info, ctypes.c_void_p(_stream_ptr(stream)))
@@ -380,21 +383,22 @@ class HMatrix:
             raise HMError(st, lib().hm_last_error().decode())
         return out
 
-    def ilu_export(self, k=None, shift=0.0, p=0.01, factor=True, stream=None):
-        """The ILU preconditioner for this k, shift and p (hm_ilu_export): dict of order
+    def ilu_export(self, k=None, shift=0.0, p=0.01, factor=True, stream=None, cep=None):
+        """The ILU preconditioner for this k, C^ep, shift and p (hm_ilu_export): dict of order
         (factorization position -> cluster DOF position), rowptr, col, a_val and, with
         factor, lu_val, plus n_colours."""
         n, nnz, nc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         kp = _dptr(k) if k is not None else None
+        cp = _dptr(cep) if cep is not None else None
         sp = ctypes.c_void_p(_stream_ptr(stream))
-        _check(lib().hm_ilu_export(self.handle, kp, float(shift), float(p), ctypes.byref(n), ctypes.byref(nnz),
+        _check(lib().hm_ilu_export(self.handle, kp, cp, float(shift), float(p), ctypes.byref(n), ctypes.byref(nnz),
                                    ctypes.byref(nc), None, None, None, None, None, sp))
         order = np.empty(n.value, np.int32)
         rowptr = np.empty(n.value + 1, np.int64)
         col = np.empty(nnz.value, np.int32)
         aval = np.empty(nnz.value)
         lu = np.empty(nnz.value) if factor else None
-        _check(lib().hm_ilu_export(self.handle, kp, float(shift), float(p), ctypes.byref(n), ctypes.byref(nnz),
+        _check(lib().hm_ilu_export(self.handle, kp, cp, float(shift), float(p), ctypes.byref(n), ctypes.byref(nnz),
                                    ctypes.byref(nc), order.ctypes.data_as(_VP), rowptr.ctypes.data_as(_VP),
                                    col.ctypes.data_as(_VP), aval.ctypes.data_as(_VP),
                                    lu.ctypes.data_as(_VP) if factor else None, sp))

@@ -130,6 +130,65 @@ def test_all_near_and_p_one_gives_the_tangent():
     assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-12)
 
 
+def interface_blocks(N, seed):
+    """Seeded 3x3 tangent blocks: the oracle's consistent tangents of seeded interface
+    states (Sec. 2.2), a mix of elastic, Coulomb and apex returns."""
+    from oracle import interface as IF
+    P = IF.Params(**synth.INTERFACE_PARAMS["softening"])
+    T, dp, chi, dd = synth.interface_states(N, seed)
+    return IF.step_all(P, T, dp, chi, dd)[4]
+
+
+def test_cep_blocks_reduce_to_the_diagonal_path():
+    el = synth.config_penny(6)
+    Em = O.dense_matrix(el, E, NU)
+    T = O.cluster_tree(el, 8)
+    k = synth.k_loguniform(el.N, 5, h=1 / 3)
+    cep = np.zeros((el.N, 3, 3))
+    cep[:, [0, 1, 2], [0, 1, 2]] = k[:, None]
+    # the same values up to the order of the two subtractions
+    tol = 4e-16 * np.abs(O.tangent_dense(Em, k, 0.2)).max()
+    assert np.abs(O.tangent_dense(Em, k, 0.2) - O.tangent_dense(Em, None, 0.2, cep=cep)).max() <= tol
+    for p in (0.05, 1.0):
+        a = IL.sparse_tangent(Em, T, k, p=p, shift=0.2)
+        b = IL.sparse_tangent(Em, T, None, p=p, shift=0.2, cep=cep)
+        for ra, rb in zip(a, b):        # b also holds the (zero) off-diagonal block entries
+            assert all(abs(rb[c] - x) <= tol for c, x in ra.items())
+            assert all(c in ra or x == 0.0 for c, x in rb.items())
+
+
+def test_all_near_and_p_one_gives_the_tangent_with_cep():
+    el = synth.config_penny(8)
+    Em = O.dense_matrix(el, E, NU)
+    T = O.cluster_tree(el, 8)
+    eta = 1e-12
+    k = synth.k_loguniform(el.N, 7, h=0.25)
+    cep = interface_blocks(el.N, 11)
+    A = O.tangent_dense(Em, k, shift=0.3, cep=cep)
+    # the blocks land on each element's own DOFs, off-diagonals included
+    Ak = O.tangent_dense(Em, k, shift=0.3)
+    e = 5
+    assert np.array_equal(Ak[3 * e:3 * e + 3, 3 * e:3 * e + 3] - A[3 * e:3 * e + 3, 3 * e:3 * e + 3], cep[e])
+    rows = IL.sparse_tangent(Em, T, k, p=1.0, eta=eta, shift=0.3, cep=cep)
+    cd = IL.cluster_dofs(T)
+    assert np.allclose(IL.to_dense(rows), A[np.ix_(cd, cd)], rtol=0, atol=1e-15 * np.abs(A).max())
+    M, nnz = IL.ilu_preconditioner(Em, T, k, p=1.0, eta=eta, shift=0.3, cep=cep)
+    b = synth.rhs_normal(A.shape[0], 8)
+    x, its, conv, _ = O.gmres(lambda u: A @ u, b, M, tol=1e-10)
+    assert conv and its == 1
+
+
+def test_cep_pattern_holds_every_element_block():
+    el = synth.config_penny(10)
+    Em = O.dense_matrix(el, E, NU)
+    T = O.cluster_tree(el, 8)
+    cep = interface_blocks(el.N, 12)
+    rows = IL.sparse_tangent(Em, T, None, p=0.01, cep=cep)
+    for a in range(len(rows)):
+        for c in range(3):
+            assert 3 * (a // 3) + c in rows[a]
+
+
 def test_pattern_keeps_the_diagonal_and_the_count():
     el = synth.config_penny(10)
     Em = O.dense_matrix(el, E, NU)

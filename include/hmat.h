@@ -344,7 +344,8 @@ hm_status hm_ilu_apply(const hm_hmat* h, const double* r_dev, double* z_dev, int
  * chi_dev (n x 3: chi_s, chi_t, w_dil), dd_dev (n x 3: Delta delta) in; T1_dev, dp1_dev,
  * chi1_dev (n x 3) out, each may be the same array as its input; cep_dev (n x 9, row i =
  * traction component i, column j = DD component j) or NULL (no tangent, cheaper);
- * mode_dev (n int32: 0 elastic, 1 Coulomb, 2 tensile, 3 open, 4 apex) or NULL.
+ * mode_dev (n int32: 0 elastic, 1 Coulomb, 2 tensile, 3 open, 4 apex, plus 256 where the
+ * multiplier did not converge) or NULL.
  * counts (host, 6 int64) or NULL: points per mode and, last, points whose multiplier did
  * not converge; with counts the call synchronises the stream and returns HM_ENOCONV if
  * that last count is not 0.  HM_EINVAL for Ks or Kn <= 0, dc <= 0, a negative or

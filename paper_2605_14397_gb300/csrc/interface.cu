@@ -217,8 +217,9 @@ struct ApexEq {
 };
 
 // Root of g on [0, hi] with g(0) > 0 >= g(hi) (values): Newton from 0, safeguarded by
-// the bracket; 0 when g(0) <= 0.  `Eq1` is the equation on one-component duals (the
-// derivative in dl).
+// the bracket (a bisection step whenever Newton leaves it or has not halved it over the
+// last three steps, as at a kink of g); 0 when g(0) <= 0.  `Eq1` is the equation on
+// one-component duals (the derivative in dl).
 template <class Eq1>
 __device__ double find_root(const Eq1& e, double hi, int* st) {
     Dual<1> z;
@@ -226,13 +227,18 @@ __device__ double find_root(const Eq1& e, double hi, int* st) {
     z.d[0] = 1.0;
     Dual<1> gz = e.g(z, nullptr);
     if (!(gz.v > 0.0)) return 0.0;
-    double lo = 0.0, x = 0.0;
-    for (int it = 0; it < 200; ++it) {
+    double lo = 0.0, x = 0.0, wref = hi;
+    for (int it = 0; it < 400; ++it) {
         // gz = g(x)
         if (gz.v > 0.0) lo = x; else hi = x;
         if (gz.v == 0.0) return x;
         double nx = x - gz.v / gz.d[0];
-        if (!(gz.d[0] < 0.0) || !(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        bool bisect = !(gz.d[0] < 0.0) || !(nx > lo && nx < hi);
+        if (it % 3 == 2) {
+            if (hi - lo > 0.5 * wref) bisect = true;
+            wref = hi - lo;
+        }
+        if (bisect) nx = 0.5 * (lo + hi);
         if (nx == x || !(hi > lo) || nx <= lo || nx >= hi) return x;
         if (fabs(nx - x) <= 1e-16 * fabs(nx)) {
             x = nx;
@@ -519,7 +525,7 @@ __global__ void k_interface_update(Prm P, int64_t n, const double* T, const doub
 #pragma unroll
                 for (int j = 0; j < 3; ++j) cep[9 * e + 3 * i + j] = r.T[i].d[j];
         }
-        if (mode) mode[e] = r.mode;
+        if (mode) mode[e] = r.mode | (st ? 256 : 0);
         atomicAdd(&s_cnt[r.mode], 1u);
         if (st) atomicAdd(&s_cnt[N_MODES], 1u);
     }

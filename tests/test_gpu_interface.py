@@ -64,8 +64,12 @@ def test_invariants_at_two_million_points(dev):
     n = 2_000_000
     T, dp, chi, dd = synth.interface_states(n, 43)
     Td, dpd, chid, ddd = to_dev(dev, T, dp, chi, dd)
-    T1, dp1, chi1, cep, mode, cnt = hmat.interface_update(kw, Td, dpd, chid, ddd, counts=True)
-    assert cnt[:5].sum() == n and cnt[5] == 0 and (cnt[:5] > 0).sum() >= 4
+    T1, dp1, chi1, cep, mode, cnt = hmat.interface_update(kw, Td, dpd, chid, ddd, counts=False)
+    cnt = np.bincount(mode.cpu().numpy() & 255, minlength=5)
+    bad = np.flatnonzero(mode.cpu().numpy() >= 256)
+    assert bad.size == 0, [(int(e), T[e].tolist(), dp[e].tolist(), chi[e].tolist(), dd[e].tolist())
+                           for e in bad[:3]]
+    assert cnt.sum() == n and (cnt > 0).sum() >= 4
     K = torch.tensor([kw["Ks"], kw["Ks"], kw["Kn"]], dtype=torch.float64, device=dev)
     m = mode.long()
     notopen = m != I.OPEN

@@ -247,6 +247,11 @@ hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
  *   with FP32 products to inner_tol (needs storage HM_F32_BF16).
  *   mode HM_SOLVE_PLAIN32: the same refinement with the corrections on the FP32-factor
  *   operator (FP32 products): the plain FP32 path, without BF16 factors.
+ *   method HM_METHOD_BICGSTAB: right-preconditioned BiCGSTAB (van der Vorst, 1992), the
+ *   method the paper uses for its A11 solves, instead of FGMRES (same preconditioners
+ *   and modes; restart ignored; maxit counts BiCGSTAB iterations of two products each;
+ *   outer counts refinement steps in the mixed modes; the run restarts from the true
+ *   residual, at most 8 times, if the recurrence's residual has drifted from it).
  * Converged when ||b - A x||_2 <= tol ||b||_2, recomputed in compensated FP64 with the
  * FP32 factors.  k_dev: N doubles (per element, user order) or NULL; b_dev, x_dev:
  * nrhs x 3N doubles, user order (x is overwritten); info: nrhs entries.  Synchronises
@@ -257,6 +262,8 @@ hm_status hm_hmat_timing_read(const hm_hmat* h, double* out6);
 #define HM_PRECOND_LEARNED 2
 #define HM_PRECOND_JACOBI3 3
 #define HM_PRECOND_ILU 4
+#define HM_METHOD_FGMRES 0
+#define HM_METHOD_BICGSTAB 1
 #define HM_SOLVE_F64 1
 #define HM_SOLVE_MIXED 2
 #define HM_SOLVE_PLAIN32 3
@@ -276,6 +283,8 @@ typedef struct {
     double ilu_p;      /* HM_PRECOND_ILU: fraction of the near-field entries kept (0 = 0.01) */
     const double* cep_dev;  /* block-diagonal C^ep (device, N x 9: per element in user order, row-major
                                3x3 in its frame (s1, s2, n), e.g. from hm_interface_update) or NULL */
+    int method;        /* HM_METHOD_FGMRES (0) or HM_METHOD_BICGSTAB */
+    int pad2_;
 } hm_solve_opts;
 
 typedef struct {

@@ -382,6 +382,61 @@ def gmres(apply_A, b, apply_M=None, tol=1e-8, restart=50, maxit=2000):
     return x, its, False, hist
 
 
+def bicgstab(apply_A, b, apply_M=None, tol=1e-8, maxit=2000):
+    """Right-preconditioned BiCGSTAB (van der Vorst, 1992), x0 = 0, shadow residual
+    r^ = b: the Krylov method of the paper's A11 solves (Sec. 3.3.1).  Per iteration,
+    p = r + beta (p - omega v), v = A M^-1 p, alpha = (r^, r) / (r^, v), s = r - alpha v,
+    t = A M^-1 s, omega = (t, s) / (t, t), x += alpha M^-1 p + omega M^-1 s,
+    r = s - omega t, beta = (r^, r_new) / (r^, r_old) * alpha / omega; stop when the
+    recurrence's ||r|| <= tol ||b||, then check the true residual and restart from it
+    if it has drifted.  Returns (x, iterations, converged)."""
+    if apply_M is None:
+        apply_M = lambda v: v
+    n = b.size
+    x = np.zeros(n)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, True
+    its = 0
+    r = b.copy()
+    for _ in range(8):                       # restarts from the true residual
+        rh = r.copy()
+        p = np.zeros(n)
+        v = np.zeros(n)
+        rho = alpha = omega = 1.0
+        first = True
+        while its < maxit:
+            rho_new = rh @ r
+            if rho_new == 0.0:
+                break
+            beta = 0.0 if first else (rho_new / rho) * (alpha / omega)
+            first = False
+            rho = rho_new
+            p = r + beta * (p - omega * v)
+            ph = apply_M(p)
+            v = apply_A(ph)
+            den = rh @ v
+            if den == 0.0:
+                break
+            alpha = rho / den
+            s = r - alpha * v
+            sh = apply_M(s)
+            t = apply_A(sh)
+            tt = t @ t
+            omega = (t @ s) / tt if tt > 0.0 else 0.0
+            x = x + alpha * ph + omega * sh
+            r = s - omega * t
+            its += 1
+            if np.linalg.norm(r) <= tol * bnorm or omega == 0.0:
+                break
+        r = b - apply_A(x)
+        if np.linalg.norm(r) <= tol * bnorm:
+            return x, its, True
+        if its >= maxit:
+            break
+    return x, its, False
+
+
 # ------------------------------------------------------------------ closed-form pins
 
 def sneddon_opening(r, E=1.0, nu=0.25, p=1.0, radius=1.0):

@@ -781,6 +781,156 @@ __global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int
 
 }  // namespace
 
+
+// ---------------------------------------------------------------- BiCGSTAB
+// Right-preconditioned BiCGSTAB (van der Vorst, 1992), the Krylov method the paper uses
+// for its A11 solves (Sec. 3.3.1), per RHS on the device: scalars per RHS in BcgScal,
+// dot products reduced over row blocks in a fixed order.
+struct BcgScal {
+    double rho, alpha, omega, beta;
+    int iters, maxit, pad0, pad1;
+};
+
+// partial sums of NQ dot products (a_q, b_q) per RHS over one row block
+template <int NQ>
+__global__ void __launch_bounds__(ROW_NT) k_bcg_dots(const double* __restrict__ a0, const double* __restrict__ b0,
+                                                     const double* __restrict__ a1, const double* __restrict__ b1,
+                                                     int64_t ndof, int nr, double* __restrict__ part,
+                                                     const CycleState* __restrict__ cs) {
+    __shared__ double sp[ROW_NT / 32][2];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * ROWS_PER_CTA;
+    for (int k = 0; k < nr; ++k) {
+        if (cs[k].done) continue;  // uniform over the block
+        double acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = r0 + threadIdx.x + u * ROW_NT;
+            if (i < ndof) {
+                const int64_t o = k * ndof + i;
+                acc[0] += a0[o] * b0[o];
+                if (NQ > 1) acc[NQ - 1] += a1[o] * b1[o];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const double t = warp_sum_d(acc[q]);
+            if (lane == 0) sp[wp][q] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < NQ) {
+            double t = 0.0;
+            for (int w = 0; w < ROW_NT / 32; ++w) t += sp[w][threadIdx.x];
+            part[((int64_t)blockIdx.x * nr + k) * 2 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// the stage's scalars from the reduced dots: warp k sums RHS k's partials (fixed order)
+// stage 0: rho_new = (rh, r) -> beta, rho;  1: alpha = rho / (rh, v);
+// stage 2: omega = (t, s) / (t, t);  3: ||r||^2 -> convergence, iteration count
+__global__ void k_bcg_stage(int stage, const double* __restrict__ part, int nblk, int nr, BcgScal* __restrict__ sc,
+                            CycleState* __restrict__ cs, int* __restrict__ alldone) {
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k < nr && !cs[k].done) {
+        double d0 = 0.0, d1 = 0.0;
+        for (int b = lane; b < nblk; b += 32) {
+            d0 += part[((int64_t)b * nr + k) * 2];
+            d1 += part[((int64_t)b * nr + k) * 2 + 1];
+        }
+        d0 = warp_sum_d(d0);
+        d1 = warp_sum_d(d1);
+        if (lane == 0) {
+            BcgScal& S = sc[k];
+            CycleState& C = cs[k];
+            if (stage == 0) {
+                if (!(d0 != 0.0) || !isfinite(d0)) {
+                    C.brk = 1;
+                    C.done = 1;
+                } else {
+                    S.beta = S.iters == 0 ? 0.0 : (d0 / S.rho) * (S.alpha / S.omega);
+                    S.rho = d0;
+                }
+            } else if (stage == 1) {
+                if (!(d0 != 0.0) || !isfinite(d0)) {
+                    C.brk = 1;
+                    C.done = 1;
+                } else {
+                    S.alpha = S.rho / d0;
+                }
+            } else if (stage == 2) {
+                S.omega = d1 > 0.0 ? d0 / d1 : 0.0;
+            } else {
+                ++S.iters;
+                ++C.iters;
+                if (sqrt(d0) <= C.tol) {
+                    C.done = 1;
+                } else if (!(S.omega != 0.0) || !isfinite(d0)) {
+                    C.brk = 1;
+                    C.done = 1;
+                } else if (S.iters >= S.maxit) {
+                    C.done = 1;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && stage == 3) {
+        int all = 1;
+        for (int q = 0; q < nr; ++q) all &= cs[q].done;
+        *alldone = all;
+    }
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_bcg_p(double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
+                        int64_t ndof, int nr, const BcgScal* __restrict__ sc, const CycleState* __restrict__ cs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int k = (int)(q / ndof);
+    if (cs[k].done) return;
+    p[q] = r[q] + sc[k].beta * (p[q] - sc[k].omega * v[q]);
+}
+
+// s = r - alpha v
+__global__ void k_bcg_s(double* __restrict__ s, const double* __restrict__ r, const double* __restrict__ v,
+                        int64_t ndof, int nr, const BcgScal* __restrict__ sc, const CycleState* __restrict__ cs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int k = (int)(q / ndof);
+    if (cs[k].done) return;
+    s[q] = r[q] - sc[k].alpha * v[q];
+}
+
+// x += alpha ph + omega sh;  r = s - omega t
+__global__ void k_bcg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ ph,
+                         const double* __restrict__ sh, const double* __restrict__ s, const double* __restrict__ t,
+                         int64_t ndof, int nr, const BcgScal* __restrict__ sc, const CycleState* __restrict__ cs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int k = (int)(q / ndof);
+    if (cs[k].done) return;
+    x[q] += sc[k].alpha * ph[q] + sc[k].omega * sh[q];
+    r[q] = s[q] - sc[k].omega * t[q];
+}
+
+// out = y - d .* z - blk z  (the tangent applied to z, y = E z)
+template <class Y>
+__global__ void k_tangent(const Y* __restrict__ y, const double* __restrict__ d, const double* __restrict__ blk,
+                          const double* __restrict__ z, double* __restrict__ out, int64_t ndof, int nr,
+                          const CycleState* __restrict__ cs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t k = q / ndof, i = q % ndof;
+    if (cs[k].done) return;
+    double v = yval(y, q) - d[i] * z[q];
+    if (blk) v -= blk_row(blk, z + k * ndof, i);
+    out[q] = v;
+}
+
 // ---------------------------------------------------------------- workspace
 
 struct SolveWS {
@@ -790,6 +940,8 @@ struct SolveWS {
     DevBuf<float> zf, y32, binv, bjscratch, dsc, j3;
     bool dsc_on = false;  // apply the learned per-leaf scalings after block-Jacobi
     DevBuf<double> blkbuf;  // off-diagonal C^ep blocks, cluster element order
+    DevBuf<double> bcg;     // BiCGSTAB vectors: rh, p, v, ph, s, sh, t (nr x 3N each)
+    DevBuf<BcgScal> bsc;
     const double* blk = nullptr;  // blkbuf.p when the tangent has a block-diagonal C^ep
     DevBuf<int64_t> binv_off, self_off;
     DevBuf<CycleState> st;
@@ -897,6 +1049,20 @@ struct CycleResult {
 // preconditioner applied in the Krylov loop
 enum PcKind { PC_NONE = 0, PC_LEAF = 1, PC_POINT = 2, PC_ILU = 3 };
 
+// z = M^-1 v (cluster order, RHS-major), and its FP32 RHS-interleaved copy zf when the
+// next product is an FP32 one; RHS whose CycleState is done are skipped
+void precond_apply(HMat& H, SolveWS& W, PcKind pc, const double* v, double* z, float* zf, int nr, cudaStream_t st) {
+    const int64_t n = H.ndof;
+    if (pc == PC_POINT)
+        k_j3_apply<<<g1(H.N * nr), 256, 0, st>>>(W.j3.p, v, z, zf, H.N, n, nr, W.st.p);
+    else if (pc == PC_ILU)
+        ilu_apply(H, v, z, zf, nr, &W.st.p->done, (int)(sizeof(CycleState) / sizeof(int)), st);
+    else
+        k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, v, z, zf, n, nr, W.st.p,
+                                               pc == PC_LEAF ? 0 : 1, W.dsc_on ? W.dsc.p : nullptr);
+    HM_LAUNCH_CHECK();
+}
+
 CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double* tol_abs, const int* active_h,
                          int nr, int m, int dtype, int fac, PcKind pc, cudaStream_t st) {
     const int64_t n = H.ndof;
@@ -926,17 +1092,7 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
         }
         const double* vj = W.V.p + (int64_t)j * nr * W.vstride;
         double* zj = W.Z.p + (int64_t)j * nr * W.vstride;
-        if (pc == PC_POINT)
-            k_j3_apply<<<g1(H.N * nr), 256, 0, st>>>(W.j3.p, vj, zj, dtype == HM_F32 ? W.zf.p : nullptr, H.N, n, nr,
-                                                      W.st.p);
-        else if (pc == PC_ILU)
-            ilu_apply(H, vj, zj, dtype == HM_F32 ? W.zf.p : nullptr, nr, &W.st.p->done,
-                      (int)(sizeof(CycleState) / sizeof(int)), st);
-        else
-            k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, vj, zj,
-                                                   dtype == HM_F32 ? W.zf.p : nullptr, n, nr, W.st.p,
-                                                   pc == PC_LEAF ? 0 : 1, W.dsc_on ? W.dsc.p : nullptr);
-        HM_LAUNCH_CHECK();
+        precond_apply(H, W, pc, vj, zj, dtype == HM_F32 ? W.zf.p : nullptr, nr, st);
         if (dtype == HM_F64) {
             apply_E(H, W, zj, nullptr, W.y64.p, nr, HM_F64, fac, st, W.alldone.p);
             k_arn_first<double><<<nb, ROW_NT, 0, st>>>(W.y64.p, W.dc.p, W.blk, zj, W.w.p, W.V.p, n, nr, j, W.vstride,
@@ -1023,6 +1179,98 @@ void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& t
             if (cr.brk[k] && cr.iters[k] == 0) brk[k] = 1;
         }
         rn = residual(H, W, rhs, nr, dtype, fac, st);
+    }
+}
+
+
+// BiCGSTAB with restarts on rhs (cluster order) into W.xc (initial value kept): the
+// recurrence's residual decides convergence, the true residual (recomputed after each
+// run) decides a restart; same contract as fgmres.
+void bicgstab(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& tol_abs, int nr, int max_its,
+              int max_runs, int dtype, int fac, PcKind pc, std::vector<int>& its, std::vector<double>& rn,
+              std::vector<int>& brk, cudaStream_t st) {
+    const int64_t n = H.ndof, vn = n * nr;
+    const int nb = nblk_rows(n);
+    if (W.bcg.n < (size_t)(7 * vn + VSLACK)) W.bcg.alloc((size_t)(7 * vn + VSLACK));
+    if (W.bsc.n < (size_t)nr) W.bsc.alloc(nr);
+    double* rh = W.bcg.p;
+    double* p = rh + vn;
+    double* v = p + vn;
+    double* ph = v + vn;
+    double* sv = ph + vn;
+    double* sh = sv + vn;
+    double* t = sh + vn;
+    double* r = W.r.p;
+    float* zf = dtype == HM_F32 ? W.zf.p : nullptr;
+    void* y = dtype == HM_F64 ? (void*)W.y64.p : (void*)W.y32.p;
+    its.assign(nr, 0);
+    brk.assign(nr, 0);
+    rn = residual(H, W, rhs, nr, dtype, fac, st);  // W.r = rhs - A x
+    auto tangent = [&](const double* z, double* out) {
+        apply_E(H, W, z, zf, y, nr, dtype, fac, st, W.alldone.p);
+        if (dtype == HM_F64)
+            k_tangent<double><<<g1(vn), 256, 0, st>>>(W.y64.p, W.dc.p, W.blk, z, out, n, nr, W.st.p);
+        else
+            k_tangent<float><<<g1(vn), 256, 0, st>>>(W.y32.p, W.dc.p, W.blk, z, out, n, nr, W.st.p);
+        HM_LAUNCH_CHECK();
+    };
+    auto stage = [&](int which, const double* a0, const double* b0, const double* a1, const double* b1) {
+        if (a1)
+            k_bcg_dots<2><<<nb, ROW_NT, 0, st>>>(a0, b0, a1, b1, n, nr, W.part.p, W.st.p);
+        else
+            k_bcg_dots<1><<<nb, ROW_NT, 0, st>>>(a0, b0, nullptr, nullptr, n, nr, W.part.p, W.st.p);
+        k_bcg_stage<<<1, 32 * nr, 0, st>>>(which, W.part.p, nb, nr, W.bsc.p, W.st.p, W.alldone.p);
+        HM_LAUNCH_CHECK();
+    };
+    for (int run = 0; run < max_runs; ++run) {
+        std::vector<CycleState> cs(nr);
+        std::vector<BcgScal> sc(nr);
+        bool any = false;
+        for (int k = 0; k < nr; ++k) {
+            const bool act = rn[k] > tol_abs[k] && its[k] < max_its && !brk[k];
+            any = any || act;
+            cs[k] = CycleState{act ? 0 : 1, 0, 0, 0, tol_abs[k], 0.0};
+            sc[k] = BcgScal{1.0, 1.0, 1.0, 0.0, 0, std::max(1, max_its - its[k]), 0, 0};
+        }
+        if (!any) break;
+        HM_CUDA(cudaMemcpyAsync(W.st.p, cs.data(), nr * sizeof(CycleState), cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(W.bsc.p, sc.data(), nr * sizeof(BcgScal), cudaMemcpyHostToDevice, st));
+        HM_CUDA(cudaMemcpyAsync(rh, r, vn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        HM_CUDA(cudaMemsetAsync(p, 0, vn * sizeof(double), st));
+        HM_CUDA(cudaMemsetAsync(v, 0, vn * sizeof(double), st));
+        HM_CUDA(cudaMemsetAsync(W.alldone.p, 0, sizeof(int), st));
+        for (int j = 0; j < max_its; ++j) {
+            // the host stays at most two iterations ahead and stops once every RHS has
+            if (j >= 2) {
+                HM_CUDA(cudaEventSynchronize(W.fev[j % 2]));
+                if (W.h_flags[j % 2]) break;
+            }
+            stage(0, rh, r, nullptr, nullptr);                         // rho, beta
+            k_bcg_p<<<g1(vn), 256, 0, st>>>(p, r, v, n, nr, W.bsc.p, W.st.p);
+            HM_LAUNCH_CHECK();
+            precond_apply(H, W, pc, p, ph, zf, nr, st);
+            tangent(ph, v);
+            stage(1, rh, v, nullptr, nullptr);                         // alpha
+            k_bcg_s<<<g1(vn), 256, 0, st>>>(sv, r, v, n, nr, W.bsc.p, W.st.p);
+            HM_LAUNCH_CHECK();
+            precond_apply(H, W, pc, sv, sh, zf, nr, st);
+            tangent(sh, t);
+            stage(2, t, sv, t, t);                                      // omega
+            k_bcg_xr<<<g1(vn), 256, 0, st>>>(W.xc.p, r, ph, sh, sv, t, n, nr, W.bsc.p, W.st.p);
+            HM_LAUNCH_CHECK();
+            stage(3, r, r, nullptr, nullptr);                          // ||r||, done
+            HM_CUDA(cudaMemcpyAsync(W.h_flags + (j % 2), W.alldone.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            HM_CUDA(cudaEventRecord(W.fev[j % 2], st));
+        }
+        HM_CUDA(cudaMemcpyAsync(cs.data(), W.st.p, nr * sizeof(CycleState), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < nr; ++k) {
+            its[k] += cs[k].iters;
+            if (cs[k].brk) brk[k] = 1;
+        }
+        rn = residual(H, W, rhs, nr, dtype, fac, st);
+        for (int k = 0; k < nr; ++k)
+            if (brk[k] && rn[k] > tol_abs[k] && cs[k].iters > 0) brk[k] = 0;  // a restart may still get on
     }
 }
 
@@ -1147,6 +1395,7 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     const int mode = o.mode ? o.mode : HM_SOLVE_F64;
     if (mode != HM_SOLVE_F64 && mode != HM_SOLVE_MIXED && mode != HM_SOLVE_PLAIN32)
         fail(HM_EINVAL, "gmres_solve: unknown mode");
+    if (o.method != HM_METHOD_FGMRES && o.method != HM_METHOD_BICGSTAB) fail(HM_EINVAL, "gmres_solve: unknown method");
     if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ && o.precond != HM_PRECOND_LEARNED &&
         o.precond != HM_PRECOND_JACOBI3 && o.precond != HM_PRECOND_ILU)
         fail(HM_EINVAL, "gmres_solve: unknown preconditioner");
@@ -1202,9 +1451,14 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     for (int k = 0; k < nrhs; ++k) tol_abs[k] = tol * bn[k];
     std::vector<int> its(nrhs, 0), outer(nrhs, 0), brk(nrhs, 0);
     std::vector<double> rn = bn;
+    const bool bcg = o.method == HM_METHOD_BICGSTAB;
     if (mode == HM_SOLVE_F64) {
-        fgmres(H, W, W.bc.p, tol_abs, nrhs, m, maxit, 1 << 20, HM_F64, 0, pc, its, rn, brk, st);
-        for (int k = 0; k < nrhs; ++k) outer[k] = (its[k] + m - 1) / m;
+        if (bcg) {
+            bicgstab(H, W, W.bc.p, tol_abs, nrhs, maxit, 8, HM_F64, 0, pc, its, rn, brk, st);
+        } else {
+            fgmres(H, W, W.bc.p, tol_abs, nrhs, m, maxit, 1 << 20, HM_F64, 0, pc, its, rn, brk, st);
+            for (int k = 0; k < nrhs; ++k) outer[k] = (its[k] + m - 1) / m;
+        }
     } else {
         const double itol = o.inner_tol > 0 ? o.inner_tol : 1e-2;
         const int max_outer = o.max_outer > 0 ? o.max_outer : 40;
@@ -1230,7 +1484,10 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
             for (int k = 0; k < nrhs; ++k) itol_abs[k] = rr[k] > tol_abs[k] ? itol * rr[k] : 1e300;
             std::vector<int> iits, ibrk;
             std::vector<double> irn;
-            fgmres(H, W, W.corr.p, itol_abs, nrhs, m, maxit, 4, HM_F32, inner_fac, pc, iits, irn, ibrk, st);
+            if (bcg)
+                bicgstab(H, W, W.corr.p, itol_abs, nrhs, maxit, 2, HM_F32, inner_fac, pc, iits, irn, ibrk, st);
+            else
+                fgmres(H, W, W.corr.p, itol_abs, nrhs, m, maxit, 4, HM_F32, inner_fac, pc, iits, irn, ibrk, st);
             for (int k = 0; k < nrhs; ++k) {
                 its[k] += iits[k];
                 if (iits[k] > 0) outer[k]++;

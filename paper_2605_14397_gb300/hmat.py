@@ -24,6 +24,7 @@ HM_ETIMEOUT = -8
 HM_F32, HM_F64, HM_BF16, HM_F32_BF16 = 1, 2, 3, 4
 HM_PRECOND_NONE, HM_PRECOND_BLOCKJ, HM_PRECOND_LEARNED, HM_PRECOND_JACOBI3, HM_PRECOND_ILU = 0, 1, 2, 3, 4
 HM_SOLVE_F64, HM_SOLVE_MIXED, HM_SOLVE_PLAIN32 = 1, 2, 3
+HM_METHOD_FGMRES, HM_METHOD_BICGSTAB = 0, 1
 
 _STATUS_NAMES = {HM_EINVAL: "HM_EINVAL", HM_ENOMEM: "HM_ENOMEM", HM_ECUDA: "HM_ECUDA",
                  HM_ESINGULAR_GEOM: "HM_ESINGULAR_GEOM", HM_ENOCONV: "HM_ENOCONV",
@@ -67,7 +68,8 @@ class hm_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mode", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int), ("lp", ctypes.c_void_p),
-                ("ilu_p", ctypes.c_double), ("cep_dev", ctypes.c_void_p)]
+                ("ilu_p", ctypes.c_double), ("cep_dev", ctypes.c_void_p), ("method", ctypes.c_int),
+                ("pad2_", ctypes.c_int)]
 
 
 class hm_tile_shape(ctypes.Structure):
@@ -358,12 +360,13 @@ class HMatrix:
                                     ctypes.c_void_p(_stream_ptr(stream))))
 
     def solve(self, b, x, k=None, shift=0.0, tol=1e-8, restart=50, maxit=2000, precond="blockj", mode="f64",
-              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None, ilu_p=0.0, cep=None):
+              inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None, ilu_p=0.0, cep=None,
+              method="fgmres"):
         """Solve (E - diag(k) - C^ep - shift I) x = b on the device (b, x: float64 CUDA tensors
         of shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None; cep: float64 CUDA
         tensor (N, 3, 3) of per-element tangent blocks, user order, or None).  precond "none",
         "jacobi3", "blockj", "ilu" (ilu_p: fraction of the near field, 0 = 0.01) or "learned";
-        mode "f64", "mixed" or "plain32".  Returns the
+        mode "f64", "mixed" or "plain32"; method "fgmres" or "bicgstab".  Returns the
         per-RHS info dicts; raises HMError unless every RHS converged (raise_on_error)."""
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         assert b.is_contiguous() and x.is_contiguous() and (k is None or k.is_contiguous())
@@ -374,7 +377,8 @@ class HMatrix:
                           {"f64": HM_SOLVE_F64, "mixed": HM_SOLVE_MIXED, "plain32": HM_SOLVE_PLAIN32}[mode],
                           float(inner_tol), int(max_outer), 0,
                           model.handle.value if model is not None else None, float(ilu_p),
-                          cep.data_ptr() if cep is not None else None)
+                          cep.data_ptr() if cep is not None else None,
+                          {"fgmres": HM_METHOD_FGMRES, "bicgstab": HM_METHOD_BICGSTAB}[method], 0)
         info = (hm_solve_info * nrhs)()
         st = lib().hm_gmres_solve(self.handle, _dptr(k) if k is not None else None, float(shift), _dptr(b), _dptr(x),
                                   int(nrhs), ctypes.byref(o), info, ctypes.c_void_p(_stream_ptr(stream)))

@@ -164,3 +164,41 @@ def test_point_jacobi_is_block_jacobi_on_one_element_leaves(penny):
     its_bj = O.gmres(lambda v: A @ v, b, lambda q: O.apply_block_jacobi(O.block_jacobi_inverses(A, T), q),
                      tol=1e-8)[1]
     assert its_bj <= its_pj < its_none
+
+
+def test_bicgstab_matches_lu_and_gmres(penny):
+    """BiCGSTAB (the paper's A11 Krylov method) on the tangent: meets the tolerance on
+    the recomputed residual and matches the LU solution, with and without block-Jacobi."""
+    el, E_ = penny
+    rng = np.random.default_rng(13)
+    k = np.exp(rng.uniform(math.log(1e-3), math.log(1e2), size=el.N)) * (E / (2.0 / 40))
+    A = O.tangent_dense(E_, k)
+    inv = O.block_jacobi_inverses(A, O.cluster_tree(el, 64))
+    b = synth.rhs_normal(3 * el.N, 14)
+    ref = np.linalg.solve(A, b)
+    for M in (None, lambda r: O.apply_block_jacobi(inv, r)):
+        x, its, ok = O.bicgstab(lambda v: A @ v, b, M, tol=1e-10)
+        assert ok and its > 0
+        assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+        assert np.linalg.norm(x - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_bicgstab_finite_termination():
+    """With the exact inverse as preconditioner one iteration solves the system; on
+    I + u v^T (a Krylov space of dimension 2) BiCGSTAB ends within two iterations; a
+    nonsymmetric system with a known solution is solved to the tolerance."""
+    rng = np.random.default_rng(15)
+    n = 60
+    A = np.eye(n) * 2 + rng.normal(size=(n, n)) / math.sqrt(n)
+    b = rng.normal(size=n)
+    Ainv = np.linalg.inv(A)
+    x, its, ok = O.bicgstab(lambda v: A @ v, b, lambda r: Ainv @ r, tol=1e-12)
+    assert ok and its == 1 and np.allclose(x, Ainv @ b, rtol=1e-12, atol=1e-12)
+    u, v = rng.normal(size=n), rng.normal(size=n) * 0.1
+    B = np.eye(n) + np.outer(u, v)
+    x, its, ok = O.bicgstab(lambda w: B @ w, b, tol=1e-12)
+    assert ok and its <= 2
+    assert np.linalg.norm(B @ x - b) <= 1e-12 * np.linalg.norm(b)
+    xs = rng.normal(size=n)
+    x, its, ok = O.bicgstab(lambda w: A @ w, A @ xs, tol=1e-13)
+    assert ok and np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs)

@@ -70,9 +70,10 @@ __device__ __forceinline__ Dual<K> operator*(Dual<K> a, Dual<K> b) {
 template <int K>
 __device__ __forceinline__ Dual<K> operator/(Dual<K> a, Dual<K> b) {
     Dual<K> r;
-    r.v = a.v / b.v;
+    const double ib = 1.0 / b.v;
+    r.v = a.v * ib;
 #pragma unroll
-    for (int i = 0; i < K; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    for (int i = 0; i < K; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
     return r;
 }
 template <int K>
@@ -95,9 +96,10 @@ __device__ __forceinline__ Dual<K> operator*(double a, Dual<K> b) {
 }
 template <int K>
 __device__ __forceinline__ Dual<K> operator/(Dual<K> a, double b) {
-    a.v /= b;
+    const double ib = 1.0 / b;
+    a.v *= ib;
 #pragma unroll
-    for (int i = 0; i < K; ++i) a.d[i] /= b;
+    for (int i = 0; i < K; ++i) a.d[i] *= ib;
     return a;
 }
 template <int K>
@@ -216,10 +218,12 @@ struct ApexEq {
     }
 };
 
-// Root of g on [0, hi] with g(0) > 0 >= g(hi) (values): Newton from 0, safeguarded by
-// the bracket (a bisection step whenever Newton leaves it or has not halved it over the
-// last three steps, as at a kink of g); 0 when g(0) <= 0.  `Eq1` is the equation on
-// one-component duals (the derivative in dl).
+// Root of g on [0, hi] with g(0) > 0 >= g(hi) (values), 0 when g(0) <= 0: Newton from 0
+// safeguarded by the bracket -- a bisection step replaces the Newton step when that
+// would leave the bracket or would not at least halve the step before last (the rule of
+// the safeguarded Newton method of Press et al., Numerical Recipes, "rtsafe"); converged
+// when a step is below 1e-16 of the iterate.  `Eq1` is the equation on one-component
+// duals (the derivative in dl).
 template <class Eq1>
 __device__ double find_root(const Eq1& e, double hi, int* st) {
     Dual<1> z;
@@ -227,24 +231,24 @@ __device__ double find_root(const Eq1& e, double hi, int* st) {
     z.d[0] = 1.0;
     Dual<1> gz = e.g(z, nullptr);
     if (!(gz.v > 0.0)) return 0.0;
-    double lo = 0.0, x = 0.0, wref = hi;
-    for (int it = 0; it < 400; ++it) {
-        // gz = g(x)
+    double lo = 0.0, x = 0.0, dx = hi, dxold = hi;
+    for (int it = 0; it < 200; ++it) {
+        // gz = g(x); the bracket keeps g(lo) > 0 >= g(hi)
         if (gz.v > 0.0) lo = x; else hi = x;
         if (gz.v == 0.0) return x;
-        double nx = x - gz.v / gz.d[0];
-        bool bisect = !(gz.d[0] < 0.0) || !(nx > lo && nx < hi);
-        if (it % 3 == 2) {
-            if (hi - lo > 0.5 * wref) bisect = true;
-            wref = hi - lo;
+        const double gp = gz.d[0];
+        const double xn = x - gz.v / gp;
+        if (!(gp < 0.0) || !(xn > lo && xn < hi) || fabs(2.0 * gz.v) > fabs(dxold * gp)) {
+            dxold = dx;
+            dx = 0.5 * (hi - lo);
+            x = lo + dx;
+            if (x == lo || x == hi) return x;
+        } else {
+            dxold = dx;
+            dx = x - xn;
+            x = xn;
         }
-        if (bisect) nx = 0.5 * (lo + hi);
-        if (nx == x || !(hi > lo) || nx <= lo || nx >= hi) return x;
-        if (fabs(nx - x) <= 1e-16 * fabs(nx)) {
-            x = nx;
-            return x;
-        }
-        x = nx;
+        if (fabs(dx) <= 1e-16 * fabs(x) || !(hi > lo)) return x;
         z.v = x;
         gz = e.g(z, nullptr);
     }

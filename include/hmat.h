@@ -323,6 +323,84 @@ hm_status hm_ilu_export(const hm_hmat* h, const double* k_dev, const double* cep
  * HM_EINVAL if no factorization exists.  Asynchronous. */
 hm_status hm_ilu_apply(const hm_hmat* h, const double* r_dev, double* z_dev, int nrhs, void* stream);
 
+/* ---------------------------------------------------------------- coupled flow
+ * Fluid flow in the fractures and the coupled hydro-mechanical Jacobian (Sec. 3.2, eq.
+ * flow_discretized and res_flow; Sec. 3.3.1).  The pressure is bilinear on the
+ * rectangular elements with nodes at the vertices (the caller's connectivity: elements
+ * share a node by index, also across intersecting planes); per element, at the opening
+ * w = w0 + delta_n, storage w / M and the cubic-law conductance w^3 / (12 mu):
+ *   S = sum (w/M) m^e, L = sum (w^3 / 12 mu) k^e, V^e = int N dS (A/4 per node),
+ *   m^e = int N^T N, k^e = int grad N^T grad N (closed forms of the rectangle);
+ *   r_f = V Delta delta_n + (S + dt L) Delta p + dt L (p^n - p^o) - dt f_f.
+ * The Jacobian of [r_m; r_f] in [Delta delta (3N, user order); Delta p (nodes)]:
+ *   A11 = E - diag(k) - C^ep - shift I (shift = eta/dt), A12 = N_p (the mean of an
+ *   element's nodal pressures on its normal row: the bilinear value at the collocation
+ *   point), A21 = d r_f / d Delta delta (only the normal DD: V^e + m^e Delta p^e / M +
+ *   dt (3 w^2 / 12 mu) k^e (Delta p^e + p^n,e - p^o,e) per element), A22 = S + dt L.
+ * No-flux outer boundary; the flow is the same on every plane (no matrix permeability). */
+typedef struct hm_flow hm_flow;
+
+typedef struct {
+    double mu;   /* fluid viscosity */
+    double M;    /* Biot modulus of the filled interface */
+    double w0;   /* initial hydraulic width */
+    double dt;   /* time step */
+} hm_flow_params;
+
+/* Mesh set-up on the host: conn (host, N x 4 int32) the element's nodes in the order
+ * (-a, -b), (+a, -b), (+a, +b), (-a, +b) of its (s1, s2) frame, n_nodes nodes, a and b
+ * (host, N) the half sides.  HM_EINVAL for an index out of range, a repeated node in an
+ * element or a non-positive half side. */
+hm_status hm_flow_create(int64_t N, const int32_t* conn, int64_t n_nodes, const double* a, const double* b,
+                         hm_flow** out);
+void hm_flow_destroy(hm_flow* f);
+/* The flow blocks at the current iterate (device arrays): dn_dev (N) delta_n at t^(n+1),
+ * dp_dev (n_nodes) Delta p, pn_dev (n_nodes) p^n - p^o (either may be NULL: zero).
+ * Gathers every entry in a fixed order (repeatable bit for bit).  Asynchronous. */
+hm_status hm_flow_assemble(hm_flow* f, const hm_flow_params* prm, const double* dn_dev, const double* dp_dev,
+                           const double* pn_dev, void* stream);
+/* To host arrays (any may be NULL): nnz_out; rowptr[n_nodes + 1], col[nnz] the node
+ * pattern (columns increasing); a22[nnz] = S + dt L; a21[4N]: A21's column of every
+ * element's normal DD, on its four nodes in connectivity order.  Synchronises. */
+hm_status hm_flow_export(const hm_flow* f, int64_t* nnz_out, int64_t* rowptr, int32_t* col, double* a22,
+                         double* a21, void* stream);
+/* y = J x for x, y of length 3N + n_nodes (device; A11 by the compensated FP64 product
+ * with the FP32 factors).  k_dev, cep_dev, shift as in hm_gmres_solve.  Synchronises. */
+hm_status hm_coupled_matvec(const hm_hmat* h, const hm_flow* f, const double* k_dev, const double* cep_dev,
+                            double shift, const double* x_dev, double* y_dev, void* stream);
+
+typedef struct {
+    double tol;          /* relative residual of the coupled system (0 = 1e-8) */
+    int restart;         /* outer FGMRES restart (0 = 30) */
+    int maxit;           /* outer iterations (0 = 300) */
+    int inner_precond;   /* preconditioner of the A11 solves (HM_PRECOND_*, not LEARNED) */
+    int inner_method;    /* HM_METHOD_FGMRES or HM_METHOD_BICGSTAB for the A11 solves */
+    double inner_tol;    /* relative tolerance of each A11 solve (0 = 1e-6) */
+    double schur_tol;    /* relative tolerance of each Schur solve (0 = 1e-6) */
+    double ilu_p;        /* inner HM_PRECOND_ILU fraction (0 = 0.01) */
+} hm_coupled_opts;
+
+typedef struct {
+    int iters;           /* outer iterations */
+    int inner_iters;     /* Krylov iterations of all A11 solves */
+    int schur_iters;     /* BiCGSTAB iterations of all Schur solves */
+    int status;          /* HM_OK or HM_ENOCONV */
+    double relres;       /* ||b - J x|| / ||b|| */
+    double seconds;
+} hm_coupled_info;
+
+/* Solve J x = b (Sec. 3.3.1): restarted FGMRES right-preconditioned by the upper block
+ * triangular P_up = [[A11, A12], [0, S~]] with S~ = A22 - A21 diag(A11)^-1 A12 (the
+ * paper's first approximation; sparse, the pattern of A22).  Applying P_up^-1: z2 =
+ * S~^-1 y2 by Jacobi-preconditioned BiCGSTAB to schur_tol, z1 = A11^-1 (y1 - A12 z2) by
+ * hm_gmres_solve's path to inner_tol (the nested solves of the paper).  FP64 throughout;
+ * x0 = 0; b_dev, x_dev of length 3N + n_nodes.  Needs hm_flow_assemble first.  HM_ENOCONV
+ * if the tolerance is not met within maxit, HM_EBREAKDOWN for a zero diagonal in A11's
+ * normal rows or in S~.  Synchronises the stream. */
+hm_status hm_coupled_solve(const hm_hmat* h, const hm_flow* f, const double* k_dev, const double* cep_dev,
+                           double shift, const double* b_dev, double* x_dev, const hm_coupled_opts* opt,
+                           hm_coupled_info* info, void* stream);
+
 /* ---------------------------------------------------------------- interface law
  * Constitutive update of the fault / fracture interface and its consistent tangent
  * (Sec. 2.2: poroelastoplastic interface with a Coulomb yield surface F_c = |tau| +

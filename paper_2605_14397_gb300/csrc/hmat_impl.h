@@ -230,6 +230,11 @@ void ilu_export_for(HMat& H, const double* kel, const double* cep, double shift,
                     int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
                     double* a_val, double* lu_val, cudaStream_t st);
 void ilu_apply_user(HMat& H, const double* r, double* z, int nrhs, cudaStream_t st);
+// y = (E - diag(k) - C^ep - shift I) x, one user-ordered FP64 vector (synchronises)
+void tangent_apply_user(HMat& H, const double* kel, const double* cep, double shift, const double* x, double* y,
+                        cudaStream_t st);
+// the diagonal of that tangent per DOF, user order (FP32 near-field entries of E)
+void tangent_diag_user(HMat& H, const double* kel, const double* cep, double shift, double* out, cudaStream_t st);
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp = nullptr);
 inline bool has_factors(const HMat& H, int fac) {

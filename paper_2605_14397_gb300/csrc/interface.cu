@@ -13,8 +13,11 @@
 // is then re-evaluated in three-component duals, whose derivative parts are C^ep.
 //
 // Branches (the active mode, the maxima of the internal variables) are taken on values,
-// so C^ep is the derivative within the active mode.  The choices the paper leaves open
+// so C^ep is the derivative within the active mode.  Two passes: one classifies every
+// point and finishes the elastic and open ones, then each kind of return (Coulomb,
+// tensile, apex) runs over its own list, so that a warp follows one branch.  The choices the paper leaves open
 // are those stated with hm_interface_update in hmat.h.
+#include <algorithm>
 #include <cmath>
 
 #include "common.h"
@@ -353,9 +356,59 @@ __device__ void trial(const Prm& P, const Pt& p, const Dual<K>* dd, double dpn_s
     Ttr[2] = cst<K>(p.T[2] - P.Kn * dpn_shift) + P.Kn * dd[2];
 }
 
-// The update on three-component duals (derivatives in Delta delta); with want_dual
-// false the multipliers' derivative steps are skipped (values only).
-__device__ Res<3> update(const Prm& P, const Pt& p, const double ddv[3], bool want_dual, int* st) {
+// The active mode at the trial state (values only; reading of the mode rules with
+// hm_interface_update in hmat.h): M_ELASTIC, M_COULOMB, M_TENSILE, M_OPEN or M_APEX (a
+// Coulomb return without a root before the shear traction vanishes).  dpb: the inelastic
+// DD the return starts from (the closed-state normal part of a damaged point); shift:
+// its normal change.
+__device__ int classify(const Prm& P, const Pt& p, const double ddv[3], double dpb[3], double& shift) {
+    const bool damaged = !(P.wc > 0.0) || p.chit >= P.wc;
+    dpb[0] = p.dp[0];
+    dpb[1] = p.dp[1];
+    dpb[2] = p.dp[2];
+    shift = 0.0;
+    Dual<1> dd1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dd1[i] = cst<1>(ddv[i]);
+    int kind;
+    if (damaged) {
+        const double wR = P.alphaR * P.wc + p.wdil;
+        const double dpn_c = fmin(p.dp[2], wR);
+        shift = dpn_c - p.dp[2];
+        dpb[2] = dpn_c;
+        Dual<1> Ttr[3];
+        trial(P, p, dd1, shift, Ttr);
+        if (Ttr[2].v > 0.0) return M_OPEN;
+        const double Fc = sqrt(Ttr[0].v * Ttr[0].v + Ttr[1].v * Ttr[1].v) +
+                          friction(P, cst<1>(p.chis)).v * Ttr[2].v;  // no cohesion left
+        kind = Fc <= 0.0 ? M_ELASTIC : M_COULOMB;
+    } else {
+        Dual<1> Ttr[3];
+        trial(P, p, dd1, 0.0, Ttr);
+        const double tau = sqrt(Ttr[0].v * Ttr[0].v + Ttr[1].v * Ttr[1].v);
+        const double f0 = friction(P, cst<1>(p.chis)).v, c0 = cohesion(P, cst<1>(p.chit)).v,
+                     st0 = tstrength(P, cst<1>(p.chit)).v;
+        const double Fc = tau + f0 * Ttr[2].v - c0, Ft = Ttr[2].v - st0;
+        if (Fc <= 0.0 && Ft <= 0.0) return M_ELASTIC;
+        const double a = sqrt(1.0 + f0 * f0) - f0;
+        const double h = tau - (c0 - f0 * st0) - a * (Ttr[2].v - st0);
+        kind = h > 0.0 ? M_COULOMB : M_TENSILE;
+    }
+    if (kind == M_COULOMB) {
+        Dual<1> Ttr[3];
+        trial(P, p, dd1, shift, Ttr);
+        const double tau = norm2(Ttr[0], Ttr[1]).v;
+        if (!(tau > 0.0)) return M_APEX;
+        const CoulombEq<1> e1 = make_coulomb<1>(P, Ttr, dpb, p);
+        if (e1.g(cst<1>(tau / P.Ks), nullptr).v > 0.0) return M_APEX;
+    }
+    return kind;
+}
+
+// The return of the given mode on three-component duals (derivatives in Delta delta);
+// with want_dual false the multipliers' derivative steps are skipped (values only).
+__device__ Res<3> finish(const Prm& P, const Pt& p, const double ddv[3], int kind, const double dpb[3],
+                         double shift, bool want_dual, int* st) {
     Dual<3> dd[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -363,46 +416,13 @@ __device__ Res<3> update(const Prm& P, const Pt& p, const double ddv[3], bool wa
         if (want_dual) dd[i].d[i] = 1.0;
     }
     Res<3> r;
-    const bool damaged = !(P.wc > 0.0) || p.chit >= P.wc;
-    double dpb[3] = {p.dp[0], p.dp[1], p.dp[2]};
-    double shift = 0.0;
-    int kind;  // 0 elastic, 1 Coulomb, 2 tensile, 3 open
-    if (damaged) {
-        const double wR = P.alphaR * P.wc + p.wdil;
-        const double dpn_c = fmin(p.dp[2], wR);
-        shift = dpn_c - p.dp[2];
-        dpb[2] = dpn_c;
-        Dual<3> Ttr[3];
-        trial(P, p, dd, shift, Ttr);
-        if (Ttr[2].v > 0.0) {
-            kind = 3;
-        } else {
-            const double Fc = sqrt(Ttr[0].v * Ttr[0].v + Ttr[1].v * Ttr[1].v) +
-                              friction(P, cst<1>(p.chis)).v * Ttr[2].v;  // no cohesion left
-            kind = Fc <= 0.0 ? 0 : 1;
-        }
-    } else {
-        Dual<3> Ttr[3];
-        trial(P, p, dd, 0.0, Ttr);
-        const double tau = sqrt(Ttr[0].v * Ttr[0].v + Ttr[1].v * Ttr[1].v);
-        const double f0 = friction(P, cst<1>(p.chis)).v, c0 = cohesion(P, cst<1>(p.chit)).v,
-                     st0 = tstrength(P, cst<1>(p.chit)).v;
-        const double Fc = tau + f0 * Ttr[2].v - c0, Ft = Ttr[2].v - st0;
-        if (Fc <= 0.0 && Ft <= 0.0) {
-            kind = 0;
-        } else {
-            const double a = sqrt(1.0 + f0 * f0) - f0;
-            const double h = tau - (c0 - f0 * st0) - a * (Ttr[2].v - st0);
-            kind = h > 0.0 ? 1 : 2;
-        }
-    }
-    if (kind == 3) {
+    if (kind == M_OPEN) {
         open_state(P, p, dd, r);
         return r;
     }
     Dual<3> Ttr[3];
     trial(P, p, dd, shift, Ttr);
-    if (kind == 0) {
+    if (kind == M_ELASTIC) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             r.T[i] = Ttr[i];
@@ -423,38 +443,27 @@ __device__ Res<3> update(const Prm& P, const Pt& p, const double ddv[3], bool wa
         T1[i] = cst<1>(Ttr[i].v);
         T4[i] = widen<3, 4>(Ttr[i]);
     }
-    bool apex = false;
-    if (kind == 1) {
+    if (kind == M_COULOMB) {
         const double tau = norm2(Ttr[0], Ttr[1]).v;
-        if (tau > 0.0) {
-            const CoulombEq<1> e1 = make_coulomb<1>(P, T1, dpb, p);
-            const double hi = tau / P.Ks;
-            Dual<1> zh = cst<1>(hi);
-            if (e1.g(zh, nullptr).v > 0.0) {
-                apex = true;
-            } else {
-                const double x = find_root(e1, hi, st);
-                Dual<3> dl = cst<3>(x);
-                if (want_dual && x > 0.0) dl = root_dual(make_coulomb<4>(P, T4, dpb, p), x, st);
-                const CoulombEq<3> e3 = make_coulomb<3>(P, Ttr, dpb, p);
-                Res<3> s;
-                e3.g(dl, &s);
+        const CoulombEq<1> e1 = make_coulomb<1>(P, T1, dpb, p);
+        const double x = find_root(e1, tau / P.Ks, st);
+        Dual<3> dl = cst<3>(x);
+        if (want_dual && x > 0.0) dl = root_dual(make_coulomb<4>(P, T4, dpb, p), x, st);
+        const CoulombEq<3> e3 = make_coulomb<3>(P, Ttr, dpb, p);
+        Res<3> s;
+        e3.g(dl, &s);
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    r.T[i] = s.T[i];
-                    r.dp[i] = s.dp[i];
-                }
-                r.chis = s.chis;
-                r.chit = s.chit;
-                r.wdil = cst<3>(p.wdil) + s.wdil;
-                r.mode = M_COULOMB;
-                return r;  // a Coulomb return stays in contact whatever the damage
-            }
-        } else {
-            apex = true;
+        for (int i = 0; i < 3; ++i) {
+            r.T[i] = s.T[i];
+            r.dp[i] = s.dp[i];
         }
+        r.chis = s.chis;
+        r.chit = s.chit;
+        r.wdil = cst<3>(p.wdil) + s.wdil;
+        r.mode = M_COULOMB;
+        return r;  // a Coulomb return stays in contact whatever the damage
     }
-    if (apex) {
+    if (kind == M_APEX) {
         const ApexEq<1> e1 = make_apex<1>(P, T1, dpb, p);
         const double x = find_root(e1, Ttr[2].v / P.Kn, st);
         Dual<3> mu = cst<3>(x);
@@ -493,49 +502,110 @@ __device__ Res<3> update(const Prm& P, const Pt& p, const double ddv[3], bool wa
     return r;
 }
 
-// the outputs may alias the inputs (each thread reads its point before writing it)
-__global__ void k_interface_update(Prm P, int64_t n, const double* T, const double* dp, const double* chi,
-                                   const double* dd, double* T1, double* dp1, double* chi1, double* cep,
-                                   int32_t* mode, unsigned long long* counts) {
+struct IfArgs {
+    Prm P;
+    int64_t n;
+    const double *T, *dp, *chi, *dd;  // the outputs may alias these: a point is read before it is written
+    double *T1, *dp1, *chi1, *cep;
+    int32_t* mode;
+    unsigned long long* counts;  // per mode, then unresolved (or NULL)
+    int32_t* list;               // [3][n]: points of the Coulomb, tensile and apex returns
+    unsigned int* lcount;        // [3]
+};
+
+__device__ __forceinline__ void load_point(const IfArgs& a, int64_t e, Pt& p, double ddv[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p.T[i] = a.T[3 * e + i];
+        p.dp[i] = a.dp[3 * e + i];
+        ddv[i] = a.dd[3 * e + i];
+    }
+    p.chis = a.chi[3 * e];
+    p.chit = a.chi[3 * e + 1];
+    p.wdil = a.chi[3 * e + 2];
+}
+
+__device__ __forceinline__ void store_point(const IfArgs& a, int64_t e, const Res<3>& r, int st,
+                                            unsigned int* s_cnt) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        a.T1[3 * e + i] = r.T[i].v;
+        a.dp1[3 * e + i] = r.dp[i].v;
+    }
+    a.chi1[3 * e] = r.chis.v;
+    a.chi1[3 * e + 1] = r.chit.v;
+    a.chi1[3 * e + 2] = r.wdil.v;
+    if (a.cep) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) a.cep[9 * e + 3 * i + j] = r.T[i].d[j];
+    }
+    if (a.mode) a.mode[e] = r.mode | (st ? 256 : 0);
+    atomicAdd(&s_cnt[r.mode], 1u);
+    if (st) atomicAdd(&s_cnt[N_MODES], 1u);
+}
+
+__device__ __forceinline__ void flush_counts(const IfArgs& a, unsigned int* s_cnt) {
+    __syncthreads();
+    if (a.counts && threadIdx.x < N_MODES + 1 && s_cnt[threadIdx.x])
+        atomicAdd(&a.counts[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+// list slot of each return kind (Coulomb, tensile, apex)
+__device__ __forceinline__ int list_of(int kind) {
+    return kind == M_COULOMB ? 0 : (kind == M_TENSILE ? 1 : (kind == M_APEX ? 2 : -1));
+}
+
+// Pass 1, one thread per point: the mode; elastic and open points are finished here, the
+// returns are listed by kind so that pass 2 runs each kind in warps of that kind only
+// (a warp over mixed modes would run every branch).
+__global__ void __launch_bounds__(128) k_iface_classify(IfArgs a) {
     __shared__ unsigned int s_cnt[N_MODES + 1];
     if (threadIdx.x < N_MODES + 1) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < n) {
-        Pt p;
-        double ddv[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            p.T[i] = T[3 * e + i];
-            p.dp[i] = dp[3 * e + i];
-            ddv[i] = dd[3 * e + i];
+    int kind = -1;
+    Pt p;
+    double ddv[3], dpb[3], shift = 0.0;
+    if (e < a.n) {
+        load_point(a, e, p, ddv);
+        kind = classify(a.P, p, ddv, dpb, shift);
+        if (kind == M_ELASTIC || kind == M_OPEN) {
+            int st = 0;
+            store_point(a, e, finish(a.P, p, ddv, kind, dpb, shift, a.cep != nullptr, &st), st, s_cnt);
         }
-        p.chis = chi[3 * e];
-        p.chit = chi[3 * e + 1];
-        p.wdil = chi[3 * e + 2];
-        int st = 0;
-        const Res<3> r = update(P, p, ddv, cep != nullptr, &st);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            T1[3 * e + i] = r.T[i].v;
-            dp1[3 * e + i] = r.dp[i].v;
-        }
-        chi1[3 * e] = r.chis.v;
-        chi1[3 * e + 1] = r.chit.v;
-        chi1[3 * e + 2] = r.wdil.v;
-        if (cep) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) cep[9 * e + 3 * i + j] = r.T[i].d[j];
-        }
-        if (mode) mode[e] = r.mode | (st ? 256 : 0);
-        atomicAdd(&s_cnt[r.mode], 1u);
-        if (st) atomicAdd(&s_cnt[N_MODES], 1u);
     }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, list_of(kind) == k);
+        if (m == 0u) continue;
+        unsigned base = 0;
+        if (lane == __ffs(m) - 1) base = atomicAdd(&a.lcount[k], (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (list_of(kind) == k) a.list[(int64_t)k * a.n + base + __popc(m & ((1u << lane) - 1u))] = (int32_t)e;
+    }
+    flush_counts(a, s_cnt);
+}
+
+// Pass 2: the listed points of one return kind, grid-stride
+__global__ void __launch_bounds__(128) k_iface_return(IfArgs a, int k) {
+    __shared__ unsigned int s_cnt[N_MODES + 1];
+    if (threadIdx.x < N_MODES + 1) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    if (counts && threadIdx.x < N_MODES + 1 && s_cnt[threadIdx.x])
-        atomicAdd(&counts[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+    const int kind = k == 0 ? M_COULOMB : (k == 1 ? M_TENSILE : M_APEX);
+    const int64_t cnt = a.lcount[k];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = a.list[(int64_t)k * a.n + q];
+        Pt p;
+        double ddv[3], dpb[3], shift = 0.0;
+        load_point(a, e, p, ddv);
+        classify(a.P, p, ddv, dpb, shift);  // dpb and shift of the start state
+        int st = 0;
+        store_point(a, e, finish(a.P, p, ddv, kind, dpb, shift, a.cep != nullptr, &st), st, s_cnt);
+    }
+    flush_counts(a, s_cnt);
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
@@ -560,6 +630,7 @@ extern "C" hm_status hm_interface_update(const hm_interface_params* prm, int64_t
     if (!(q.dc > 0.0) || std::isnan(q.dc)) fail(HM_EINVAL, "interface_update: d_c must be > 0");
     if (n > 0 && (!T_dev || !dp_dev || !chi_dev || !dd_dev || !T1_dev || !dp1_dev || !chi1_dev))
         fail(HM_EINVAL, "interface_update: a state or increment pointer is NULL");
+    if (n > INT32_MAX) fail(HM_EINVAL, "interface_update: more than 2^31 - 1 points");
     cudaStream_t st = (cudaStream_t)stream;
     DevBuf<unsigned long long> cnt;
     if (counts) {
@@ -568,11 +639,24 @@ extern "C" hm_status hm_interface_update(const hm_interface_params* prm, int64_t
     }
     const Prm P{q.Ks, q.Kn, q.fp, q.fr, q.psip, q.dc, q.cp, q.sigp, q.wc, q.alphaR};
     if (n > 0) {
-        const int nt = 128;
-        k_interface_update<<<(unsigned)ceil_div(n, nt), nt, 0, st>>>(P, n, T_dev, dp_dev, chi_dev, dd_dev, T1_dev,
-                                                                     dp1_dev, chi1_dev, cep_dev, mode_dev,
-                                                                     counts ? cnt.p : nullptr);
-        HM_LAUNCH_CHECK();
+        // stream-ordered scratch for the per-kind lists: no device-wide synchronisation
+        void* scratch = nullptr;
+        const size_t lbytes = (size_t)3 * n * sizeof(int32_t), cbytes = 4 * sizeof(unsigned int);
+        HM_CUDA(cudaMallocAsync(&scratch, lbytes + cbytes, st));
+        IfArgs a{P, n, T_dev, dp_dev, chi_dev, dd_dev, T1_dev, dp1_dev, chi1_dev, cep_dev, mode_dev,
+                 counts ? cnt.p : nullptr, (int32_t*)scratch, (unsigned int*)((char*)scratch + lbytes)};
+        cudaError_t err = cudaMemsetAsync(a.lcount, 0, cbytes, st);
+        if (err == cudaSuccess) {
+            k_iface_classify<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(a);
+            int dev = 0, nsm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            const unsigned g2 = (unsigned)std::min<int64_t>(ceil_div(n, 128), (int64_t)std::max(nsm, 1) * 16);
+            for (int k = 0; k < 3; ++k) k_iface_return<<<g2, 128, 0, st>>>(a, k);
+            err = cudaGetLastError();
+        }
+        HM_CUDA(cudaFreeAsync(scratch, st));
+        HM_CUDA(err);
     }
     if (counts) {
         unsigned long long h[N_MODES + 1];

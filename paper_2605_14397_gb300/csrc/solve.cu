@@ -1368,6 +1368,47 @@ void ilu_export_for(HMat& H, const double* kel, const double* cep, double shift,
     ilu_export(H, n_out, nnz_out, n_colours_out, order, rowptr, col, a_val, lu_val, st);
 }
 
+// y = (E - diag(k) - C^ep - shift I) x for one user-ordered FP64 vector (compensated
+// product with the FP32 factors)
+void tangent_apply_user(HMat& H, const double* kel, const double* cep, double shift, const double* x, double* y,
+                        cudaStream_t st) {
+    if (!has_factors(H, 0)) fail(HM_EINVAL, "tangent product: the FP32 factors are required");
+    SolveWS& W = workspace(H, 1, 1, st);
+    const int64_t n = H.ndof;
+    set_tangent(H, W, kel, cep, shift, st);
+    CycleState c0{0, 0, 0, 0, 0.0, 0.0};
+    HM_CUDA(cudaMemcpyAsync(W.st.p, &c0, sizeof(CycleState), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemsetAsync(W.alldone.p, 0, sizeof(int), st));
+    k_to_cluster<<<g1(n), 256, 0, st>>>(x, W.xc.p, H.perm.p, n, 1);
+    HM_LAUNCH_CHECK();
+    apply_E(H, W, W.xc.p, nullptr, W.y64.p, 1, HM_F64, 0, st);
+    k_tangent<double><<<g1(n), 256, 0, st>>>(W.y64.p, W.dc.p, W.blk, W.xc.p, W.w.p, n, 1, W.st.p);
+    k_to_user<<<g1(n), 256, 0, st>>>(W.w.p, y, H.perm.p, n, 1);
+    HM_LAUNCH_CHECK();
+    HM_CUDA(cudaStreamSynchronize(st));  // the host struct c0 above is read by the copy
+}
+
+// diag(E - diag(k) - C^ep - shift I) per DOF in user order (E's diagonal from the FP32
+// near-field self tiles)
+__global__ void k_tangent_diag(const LeafDesc* __restrict__ leaves, const int64_t* __restrict__ self_off,
+                               const float* __restrict__ near, const double* __restrict__ d,
+                               const double* __restrict__ blk, const int32_t* __restrict__ perm,
+                               double* __restrict__ out) {
+    const LeafDesc L = leaves[blockIdx.x];
+    const float* T = near + self_off[blockIdx.x];
+    for (int r = threadIdx.x; r < 3 * L.n; r += blockDim.x) {
+        const int64_t p = 3 * (int64_t)L.begin + r;
+        out[3 * (int64_t)perm[p / 3] + r % 3] = (double)T[(int64_t)r * L.ld + r] - d[p];
+    }
+}
+
+void tangent_diag_user(HMat& H, const double* kel, const double* cep, double shift, double* out, cudaStream_t st) {
+    SolveWS& W = workspace(H, 1, 1, st);
+    set_tangent(H, W, kel, cep, shift, st);
+    k_tangent_diag<<<H.n_leaves, 128, 0, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.blk, H.perm.p, out);
+    HM_LAUNCH_CHECK();
+}
+
 // z = (L U)^-1 r for user-ordered vectors with the last ILU factorization
 void ilu_apply_user(HMat& H, const double* r, double* z, int nrhs, cudaStream_t st) {
     if (nrhs < 1 || nrhs > 16) fail(HM_EINVAL, "ilu_apply: 1 to 16 right-hand sides");

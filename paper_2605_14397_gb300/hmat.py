@@ -103,6 +103,21 @@ class hm_interface_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("Ks", "Kn", "fp", "fr", "psip", "dc", "cp", "sigp", "wc", "alphaR")]
 
 
+class hm_flow_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("mu", "M", "w0", "dt")]
+
+
+class hm_coupled_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("inner_precond", ctypes.c_int), ("inner_method", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("schur_tol", ctypes.c_double), ("ilu_p", ctypes.c_double)]
+
+
+class hm_coupled_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("schur_iters", ctypes.c_int),
+                ("status", ctypes.c_int), ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
 _LIB = None
 
 # (name, restype, argtypes) of every exported entry point declared in include/hmat.h
@@ -158,6 +173,13 @@ SIGNATURES = [
     ("hm_hmat_set_tile_shape", _I, [_VP, ctypes.POINTER(hm_tile_shape), _VP]),
     ("hm_hmat_get_tile_shape", _I, [_VP, ctypes.POINTER(hm_tile_shape)]),
     ("hm_tune_tile_shape", _I, [_VP, _VP, _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
+    ("hm_flow_create", _I, [_I64, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)]),
+    ("hm_flow_destroy", None, [_VP]),
+    ("hm_flow_assemble", _I, [_VP, ctypes.POINTER(hm_flow_params), _VP, _VP, _VP, _VP]),
+    ("hm_flow_export", _I, [_VP, _P64, _VP, _VP, _VP, _VP, _VP]),
+    ("hm_coupled_matvec", _I, [_VP, _VP, _VP, _VP, _D, _VP, _VP, _VP]),
+    ("hm_coupled_solve", _I, [_VP, _VP, _VP, _VP, _D, _VP, _VP, ctypes.POINTER(hm_coupled_opts),
+                              ctypes.POINTER(hm_coupled_info), _VP]),
     ("hm_interface_update", _I, [ctypes.POINTER(hm_interface_params), _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                  _VP, _VP, _P64, _VP]),
     ("hm_ilu_select", _I, [_I64, _VP, _VP, _VP, _D, _VP, ctypes.POINTER(_I64)]),
@@ -712,3 +734,69 @@ def interface_update(params, T, dp, chi, dd, T1=None, dp1=None, chi1=None, tange
                                      cnt.ctypes.data_as(_P64) if counts else None,
                                      ctypes.c_void_p(_stream_ptr(stream))))
     return T1, dp1, chi1, cep, mode, cnt
+
+
+# ---------------------------------------------------------------- coupled flow
+_PRECONDS = {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "jacobi3": HM_PRECOND_JACOBI3,
+             "ilu": HM_PRECOND_ILU}
+
+
+class Flow:
+    """Fracture flow mesh and matrices (hm_flow_*): conn (N, 4) int32 node indices,
+    n_nodes, half sides a, b (N,)."""
+
+    def __init__(self, conn, n_nodes, a, b):
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        self.N, self.n_nodes = conn.shape[0], int(n_nodes)
+        h = ctypes.c_void_p()
+        _check(lib().hm_flow_create(self.N, conn.ctypes.data_as(_VP), self.n_nodes, a.ctypes.data_as(_VP),
+                                    b.ctypes.data_as(_VP), ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _LIB is not None:
+            _LIB.hm_flow_destroy(self.handle)
+            self.handle = None
+
+    def assemble(self, params, dn, dp=None, pn=None, stream=None):
+        """params: dict with mu, M, w0, dt; dn (N,), dp, pn (n_nodes,) FP64 CUDA tensors."""
+        prm = hm_flow_params(*[float(params[k]) for k, _ in hm_flow_params._fields_])
+        _check(lib().hm_flow_assemble(self.handle, ctypes.byref(prm), _dptr(dn),
+                                      _dptr(dp) if dp is not None else None,
+                                      _dptr(pn) if pn is not None else None, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def export(self, stream=None):
+        nnz = ctypes.c_int64()
+        sp = ctypes.c_void_p(_stream_ptr(stream))
+        _check(lib().hm_flow_export(self.handle, ctypes.byref(nnz), None, None, None, None, sp))
+        rp = np.empty(self.n_nodes + 1, np.int64)
+        col = np.empty(nnz.value, np.int32)
+        a22 = np.empty(nnz.value)
+        a21 = np.empty((self.N, 4))
+        _check(lib().hm_flow_export(self.handle, ctypes.byref(nnz), rp.ctypes.data_as(_P64), col.ctypes.data_as(_VP),
+                                    a22.ctypes.data_as(_VP), a21.ctypes.data_as(_VP), sp))
+        return dict(rowptr=rp, col=col, a22=a22, a21=a21)
+
+    def matvec(self, H, x, y, k=None, cep=None, shift=0.0, stream=None):
+        _check(lib().hm_coupled_matvec(H.handle, self.handle, _dptr(k) if k is not None else None,
+                                       _dptr(cep) if cep is not None else None, float(shift), _dptr(x), _dptr(y),
+                                       ctypes.c_void_p(_stream_ptr(stream))))
+
+    def solve(self, H, b, x, k=None, cep=None, shift=0.0, tol=1e-8, restart=30, maxit=300, inner_precond="blockj",
+              inner_method="fgmres", inner_tol=1e-6, schur_tol=1e-6, ilu_p=0.0, stream=None,
+              raise_on_error=True):
+        """Solve the coupled Jacobian system J x = b (hm_coupled_solve); b, x FP64 CUDA
+        tensors of length 3N + n_nodes.  Returns the info dict."""
+        o = hm_coupled_opts(float(tol), int(restart), int(maxit), _PRECONDS[inner_precond],
+                            {"fgmres": HM_METHOD_FGMRES, "bicgstab": HM_METHOD_BICGSTAB}[inner_method],
+                            float(inner_tol), float(schur_tol), float(ilu_p))
+        inf = hm_coupled_info()
+        st = lib().hm_coupled_solve(H.handle, self.handle, _dptr(k) if k is not None else None,
+                                    _dptr(cep) if cep is not None else None, float(shift), _dptr(b), _dptr(x),
+                                    ctypes.byref(o), ctypes.byref(inf), ctypes.c_void_p(_stream_ptr(stream)))
+        out = {f: getattr(inf, f) for f, _ in hm_coupled_info._fields_}
+        if st != HM_OK and raise_on_error:
+            raise HMError(st, lib().hm_last_error().decode())
+        return out

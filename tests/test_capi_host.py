@@ -191,3 +191,22 @@ def test_interface_update_argument_checks(L):
     assert call(n=-1) == hmat.HM_EINVAL
     assert call(n=5) == hmat.HM_EINVAL and "NULL" in hmat.last_error()
     assert L.hm_interface_update(None, 0, *([ctypes.c_void_p(None)] * 9), None, None) == hmat.HM_EINVAL
+
+
+def test_flow_create_argument_checks(L):
+    """Mesh validation happens on the host before any device work."""
+    conn = np.array([[0, 1, 2, 3], [1, 4, 5, 2]], dtype=np.int32)
+    a = np.full(2, 0.5)
+    b = np.full(2, 0.5)
+    h = ctypes.c_void_p()
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    bad = conn.copy()
+    bad[1, 2] = 6
+    assert L.hm_flow_create(2, vp(bad), 6, vp(a), vp(b), ctypes.byref(h)) == hmat.HM_EINVAL
+    bad = conn.copy()
+    bad[0, 3] = 0
+    assert L.hm_flow_create(2, vp(bad), 6, vp(a), vp(b), ctypes.byref(h)) == hmat.HM_EINVAL
+    assert "repeats" in hmat.last_error()
+    assert L.hm_flow_create(2, vp(conn), 6, vp(a), vp(-b), ctypes.byref(h)) == hmat.HM_EINVAL
+    assert L.hm_flow_create(0, vp(conn), 6, vp(a), vp(b), ctypes.byref(h)) == hmat.HM_EINVAL
+    assert L.hm_flow_create(2, None, 6, vp(a), vp(b), ctypes.byref(h)) == hmat.HM_EINVAL

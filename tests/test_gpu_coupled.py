@@ -115,7 +115,11 @@ def test_coupled_solve_matches_lu(dev, case, inner):
     xl = np.linalg.solve(J, b)
     xs = x.cpu().numpy()
     assert np.linalg.norm(xs - xl) <= 1e-5 * np.linalg.norm(xl)
-    assert np.linalg.norm(b - J @ xs) <= 1e-6 * np.linalg.norm(b)
+    # the oracle's Jacobian differs from the library's by the FP32 storage of E's
+    # near-field entries and the compression (eps 1e-8): a bound on |A11| |x1|
+    n1 = 3 * case["el"].N
+    a11x = np.abs(J[:n1, :n1]) @ np.abs(xs[:n1])
+    assert np.linalg.norm(b - J @ xs) <= 1e-8 * np.linalg.norm(b) + 2e-7 * np.linalg.norm(a11x)
     print("%s: %d outer, %d inner, %d Schur iterations" % (inner, info["iters"], info["inner_iters"],
                                                            info["schur_iters"]))
 

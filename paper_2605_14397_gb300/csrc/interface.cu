@@ -227,14 +227,20 @@ struct ApexEq {
 // the safeguarded Newton method of Press et al., Numerical Recipes, "rtsafe"); converged
 // when a step is below 1e-16 of the iterate.  `Eq1` is the equation on one-component
 // duals (the derivative in dl).
+// x0: a first guess inside (0, hi) (the multiplier without softening), else 0.
 template <class Eq1>
-__device__ double find_root(const Eq1& e, double hi, int* st) {
+__device__ double find_root(const Eq1& e, double hi, double x0, int* st) {
     Dual<1> z;
     z.v = 0.0;
     z.d[0] = 1.0;
     Dual<1> gz = e.g(z, nullptr);
     if (!(gz.v > 0.0)) return 0.0;
     double lo = 0.0, x = 0.0, dx = hi, dxold = hi;
+    if (x0 > 0.0 && x0 < hi) {
+        x = x0;
+        z.v = x;
+        gz = e.g(z, nullptr);
+    }
     for (int it = 0; it < 200; ++it) {
         // gz = g(x); the bracket keeps g(lo) > 0 >= g(hi)
         if (gz.v > 0.0) lo = x; else hi = x;
@@ -361,21 +367,30 @@ __device__ void trial(const Prm& P, const Pt& p, const Dual<K>* dd, double dpn_s
 // Coulomb return without a root before the shear traction vanishes).  dpb: the inelastic
 // DD the return starts from (the closed-state normal part of a damaged point); shift:
 // its normal change.
-__device__ int classify(const Prm& P, const Pt& p, const double ddv[3], double dpb[3], double& shift) {
+// the inelastic DD a return starts from and its normal change (closed-state reference of
+// a fully damaged point); true if the point is fully damaged
+__device__ __forceinline__ bool start_state(const Prm& P, const Pt& p, double dpb[3], double& shift) {
     const bool damaged = !(P.wc > 0.0) || p.chit >= P.wc;
     dpb[0] = p.dp[0];
     dpb[1] = p.dp[1];
     dpb[2] = p.dp[2];
     shift = 0.0;
-    Dual<1> dd1[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) dd1[i] = cst<1>(ddv[i]);
-    int kind;
     if (damaged) {
         const double wR = P.alphaR * P.wc + p.wdil;
         const double dpn_c = fmin(p.dp[2], wR);
         shift = dpn_c - p.dp[2];
         dpb[2] = dpn_c;
+    }
+    return damaged;
+}
+
+__device__ int classify(const Prm& P, const Pt& p, const double ddv[3], double dpb[3], double& shift) {
+    const bool damaged = start_state(P, p, dpb, shift);
+    Dual<1> dd1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dd1[i] = cst<1>(ddv[i]);
+    int kind;
+    if (damaged) {
         Dual<1> Ttr[3];
         trial(P, p, dd1, shift, Ttr);
         if (Ttr[2].v > 0.0) return M_OPEN;
@@ -446,7 +461,10 @@ __device__ Res<3> finish(const Prm& P, const Pt& p, const double ddv[3], int kin
     if (kind == M_COULOMB) {
         const double tau = norm2(Ttr[0], Ttr[1]).v;
         const CoulombEq<1> e1 = make_coulomb<1>(P, T1, dpb, p);
-        const double x = find_root(e1, tau / P.Ks, st);
+        // without softening the multiplier is F_trial / (Ks + f psi Kn)
+        const double f0 = friction(P, cst<1>(p.chis)).v, psi0 = dilatancy(P, cst<1>(p.chis)).v;
+        const double F0 = tau + f0 * Ttr[2].v - cohesion(P, cst<1>(p.chit)).v;
+        const double x = find_root(e1, tau / P.Ks, F0 / (P.Ks + f0 * psi0 * P.Kn), st);
         Dual<3> dl = cst<3>(x);
         if (want_dual && x > 0.0) dl = root_dual(make_coulomb<4>(P, T4, dpb, p), x, st);
         const CoulombEq<3> e3 = make_coulomb<3>(P, Ttr, dpb, p);
@@ -465,7 +483,9 @@ __device__ Res<3> finish(const Prm& P, const Pt& p, const double ddv[3], int kin
     }
     if (kind == M_APEX) {
         const ApexEq<1> e1 = make_apex<1>(P, T1, dpb, p);
-        const double x = find_root(e1, Ttr[2].v / P.Kn, st);
+        const double x = find_root(e1, Ttr[2].v / P.Kn,
+                                   e1.f1.v > 0.0 ? (Ttr[2].v - cohesion(P, cst<1>(p.chit)).v / e1.f1.v) / P.Kn : 0.0,
+                                   st);
         Dual<3> mu = cst<3>(x);
         if (want_dual && x > 0.0) mu = root_dual(make_apex<4>(P, T4, dpb, p), x, st);
         const ApexEq<3> e3 = make_apex<3>(P, Ttr, dpb, p);
@@ -481,7 +501,7 @@ __device__ Res<3> finish(const Prm& P, const Pt& p, const double ddv[3], int kin
         r.mode = M_APEX;
     } else {
         const TensileEq<1> e1 = make_tensile<1>(P, T1, dpb, p);
-        const double x = find_root(e1, Ttr[2].v / P.Kn, st);
+        const double x = find_root(e1, Ttr[2].v / P.Kn, (Ttr[2].v - tstrength(P, cst<1>(p.chit)).v) / P.Kn, st);
         Dual<3> dl = cst<3>(x);
         if (want_dual && x > 0.0) dl = root_dual(make_tensile<4>(P, T4, dpb, p), x, st);
         const TensileEq<3> e3 = make_tensile<3>(P, Ttr, dpb, p);
@@ -601,7 +621,7 @@ __global__ void __launch_bounds__(128) k_iface_return(IfArgs a, int k) {
         Pt p;
         double ddv[3], dpb[3], shift = 0.0;
         load_point(a, e, p, ddv);
-        classify(a.P, p, ddv, dpb, shift);  // dpb and shift of the start state
+        start_state(a.P, p, dpb, shift);
         int st = 0;
         store_point(a, e, finish(a.P, p, ddv, kind, dpb, shift, a.cep != nullptr, &st), st, s_cnt);
     }

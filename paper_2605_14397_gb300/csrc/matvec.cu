@@ -97,6 +97,24 @@ __device__ __forceinline__ void acc_zero(float& a) { a = 0.f; }
 __device__ __forceinline__ void acc_zero(FF& a) { a.hi = 0.f; a.lo = 0.f; }
 
 __device__ __forceinline__ void acc_fma(float& acc, float a, Z32 z) { acc = fmaf(a, z.h, acc); }
+// two FP32 accumulators against one coefficient: one packed FMA (sm_100-class FFMA2,
+// each half rounded like fmaf), half the instructions of the multi-RHS loops
+__device__ __forceinline__ void acc_fma2(float& a0, float& a1, float v, Z32 z0, Z32 z1) {
+    const float2 r = __ffma2_rn(make_float2(v, v), make_float2(z0.h, z1.h), make_float2(a0, a1));
+    a0 = r.x;
+    a1 = r.y;
+}
+// the RHS of one coefficient: pairs for FP32 accumulators, one by one otherwise
+template <int NR, class A, class Z>
+__device__ __forceinline__ void acc_fma_rhs(A* acc, float v, const Z* z, int stride) {
+    if constexpr (std::is_same<A, float>::value && NR % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k += 2) acc_fma2(acc[k * stride], acc[(k + 1) * stride], v, z[k], z[k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) acc_fma(acc[k * stride], v, z[k]);
+    }
+}
 __device__ __forceinline__ void acc_fma(FF& acc, float a, Z64 z) {
     const float p = a * z.h;
     const float pe = fmaf(a, z.h, -p);
@@ -900,8 +918,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 for (int ii = 0; ii < RPW; ++ii) {
                     if (NR > 1 && ii >= nact) break;
                     const float v = col[32 * ii];
-#pragma unroll
-                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
+                    acc_fma_rhs<NR>(&acc[0][ii], v, zv, RPW);
                 }
             } else {
                 const C* col = (const C*)buf + (size_t)c * ch.ld + rbase + lane;
@@ -909,8 +926,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                 for (int ii = 0; ii < RPW; ++ii) {
                     if (NR > 1 && ii >= nact) break;
                     const float v = coef(col, 32 * ii);
-#pragma unroll
-                    for (int k = 0; k < NR; ++k) acc_fma(acc[k][ii], v, zv[k]);
+                    acc_fma_rhs<NR>(&acc[0][ii], v, zv, RPW);
                 }
             }
         }
@@ -1028,8 +1044,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase1(StreamArgs a) {
             for (int ii = 0; ii < RPL; ++ii) {
                 const int r = lane + 32 * ii;
                 const float v = r < rows ? coef(col, r) : 0.f;
+                if constexpr (std::is_same<Acc, float>::value && NR % 2 == 0) {
 #pragma unroll
-                for (int k = 0; k < NR; ++k) acc_fma(acc[k], v, xr[k][ii]);
+                    for (int k = 0; k < NR; k += 2) acc_fma2(acc[k], acc[k + 1], v, xr[k][ii], xr[k + 1][ii]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc_fma(acc[k], v, xr[k][ii]);
+                }
             }
             const int k = warp_reduce_scatter<NR>(acc, lane);
             if ((lane & (32 / NR - 1)) == 0 && k < a.nr) P[(ch.zoff + c) * a.nr + k] = (Vv)acc_value(acc[0]);

@@ -378,6 +378,8 @@ typedef struct {
     double inner_tol;    /* relative tolerance of each A11 solve (0 = 1e-6) */
     double schur_tol;    /* relative tolerance of each Schur solve (0 = 1e-6) */
     double ilu_p;        /* inner HM_PRECOND_ILU fraction (0 = 0.01) */
+    double flow_scale;   /* factor on the flow rows (Sec. 3.3.2's residual scaling); 0 = the ratio of
+                            the RMS diagonal of A11 to that of S~ (both blocks weigh in the test) */
 } hm_coupled_opts;
 
 typedef struct {
@@ -385,7 +387,7 @@ typedef struct {
     int inner_iters;     /* Krylov iterations of all A11 solves */
     int schur_iters;     /* BiCGSTAB iterations of all Schur solves */
     int status;          /* HM_OK or HM_ENOCONV */
-    double relres;       /* ||b - J x|| / ||b|| */
+    double relres;       /* the scaled relative residual (see hm_coupled_solve) */
     double seconds;
 } hm_coupled_info;
 
@@ -393,7 +395,9 @@ typedef struct {
  * triangular P_up = [[A11, A12], [0, S~]] with S~ = A22 - A21 diag(A11)^-1 A12 (the
  * paper's first approximation; sparse, the pattern of A22).  Applying P_up^-1: z2 =
  * S~^-1 y2 by Jacobi-preconditioned BiCGSTAB to schur_tol, z1 = A11^-1 (y1 - A12 z2) by
- * hm_gmres_solve's path to inner_tol (the nested solves of the paper).  FP64 throughout;
+ * hm_gmres_solve's path to inner_tol (the nested solves of the paper).  The flow rows
+ * are scaled by flow_scale (the residual scaling of Sec. 3.3.2), and tol and relres refer
+ * to ||diag(I, s I)(b - J x)|| / ||diag(I, s I) b||.  FP64 throughout;
  * x0 = 0; b_dev, x_dev of length 3N + n_nodes.  Needs hm_flow_assemble first.  HM_ENOCONV
  * if the tolerance is not met within maxit, HM_EBREAKDOWN for a zero diagonal in A11's
  * normal rows or in S~.  Synchronises the stream. */

@@ -334,13 +334,27 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
     io.ilu_p = o.ilu_p;
     io.cep_dev = cep;
     io.maxit = 3000;
-    DevBuf<double> V((size_t)(m + 1) * n), Z((size_t)m * n), w(n), r(n), t1(n1), sws;
+    DevBuf<double> V((size_t)(m + 1) * n), Z((size_t)m * n), w(n), r(n), t1(n1), bs(n), sws;
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
-    const double bn = std::sqrt(D.dot(n, bv, bv, st));
+    // the flow rows scaled by sr (Sec. 3.3.2 scales residuals to order one): by default
+    // the ratio of the RMS diagonal of A11 to that of S~, so that the stopping test
+    // weighs both blocks; the solve runs on diag(I, sr I) J, its residual in that norm
+    double sr = o.flow_scale;
+    if (!(sr > 0.0))
+        sr = std::sqrt(D.dot(n1, diag.p, diag.p, st) / (double)n1) * std::sqrt(D.dot(n2, sdinv.p, sdinv.p, st) / (double)n2);
+    if (!(sr > 0.0) || !std::isfinite(sr)) sr = 1.0;
+    HM_CUDA(cudaMemcpyAsync(bs.p, bv, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    axpby(n2, 0.0, bs.p + n1, sr, bs.p + n1, st);
+    const double* bsc = bs.p;
+    auto apply_scaled = [&](const double* xin, double* yout) {
+        coupled_apply(H, F, kel, cep, shift, xin, yout, st);
+        axpby(n2, 0.0, yout + n1, sr, yout + n1, st);
+    };
+    const double bn = std::sqrt(D.dot(n, bsc, bsc, st));
     HM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
     int its = 0, inner = 0, schur = 0;
     double rn = bn;
-    HM_CUDA(cudaMemcpyAsync(r.p, bv, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(r.p, bsc, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     while (bn > 0.0 && rn > tol * bn && its < maxit) {
         // V0 = r / ||r||
         HM_CUDA(cudaMemsetAsync(V.p, 0, n * sizeof(double), st));
@@ -351,8 +365,9 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
         for (; j < m && its < maxit; ++j) {
             const double* vj = V.p + (size_t)j * n;
             double* zj = Z.p + (size_t)j * n;
-            // z = P_up^-1 v: z2 = S~^-1 v2, z1 = A11^-1 (v1 - N_p z2)
+            // z = P_up^-1 v of the scaled system: z2 = S~^-1 v2 / sr, z1 = A11^-1 (v1 - N_p z2)
             schur += schur_solve(F, sval.p, sdinv.p, vj + n1, zj + n1, stol, 2000, sws, D, st);
+            axpby(n2, 0.0, zj + n1, 1.0 / sr, zj + n1, st);
             HM_CUDA(cudaMemcpyAsync(t1.p, vj, n1 * sizeof(double), cudaMemcpyDeviceToDevice, st));
             k_np_add<<<gsz(F.N), NT, 0, st>>>(F.N, F.conn.p, zj + n1, -1.0, t1.p);
             HM_LAUNCH_CHECK();
@@ -364,7 +379,7 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
                 if (e.code != HM_ENOCONV) throw;
             }
             inner += ii.iters;
-            coupled_apply(H, F, kel, cep, shift, zj, w.p, st);
+            apply_scaled(zj, w.p);
             // modified Gram-Schmidt
             for (int i = 0; i <= j; ++i) {
                 const double h = D.dot(n, w.p, V.p + (size_t)i * n, st);
@@ -402,8 +417,8 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
         }
         for (int i = 0; i < j; ++i) axpby(n, yv[i], Z.p + (size_t)i * n, 1.0, x, st);
         // true residual
-        coupled_apply(H, F, kel, cep, shift, x, w.p, st);
-        HM_CUDA(cudaMemcpyAsync(r.p, bv, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        apply_scaled(x, w.p);
+        HM_CUDA(cudaMemcpyAsync(r.p, bsc, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         axpby(n, -1.0, w.p, 1.0, r.p, st);
         rn = std::sqrt(D.dot(n, r.p, r.p, st));
         if (j == 0) break;

@@ -110,7 +110,7 @@ class hm_flow_params(ctypes.Structure):
 class hm_coupled_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("inner_precond", ctypes.c_int), ("inner_method", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("schur_tol", ctypes.c_double), ("ilu_p", ctypes.c_double)]
+                ("schur_tol", ctypes.c_double), ("ilu_p", ctypes.c_double), ("flow_scale", ctypes.c_double)]
 
 
 class hm_coupled_info(ctypes.Structure):
@@ -785,13 +785,13 @@ class Flow:
                                        ctypes.c_void_p(_stream_ptr(stream))))
 
     def solve(self, H, b, x, k=None, cep=None, shift=0.0, tol=1e-8, restart=30, maxit=300, inner_precond="blockj",
-              inner_method="fgmres", inner_tol=1e-6, schur_tol=1e-6, ilu_p=0.0, stream=None,
+              inner_method="fgmres", inner_tol=1e-6, schur_tol=1e-6, ilu_p=0.0, flow_scale=0.0, stream=None,
               raise_on_error=True):
         """Solve the coupled Jacobian system J x = b (hm_coupled_solve); b, x FP64 CUDA
         tensors of length 3N + n_nodes.  Returns the info dict."""
         o = hm_coupled_opts(float(tol), int(restart), int(maxit), _PRECONDS[inner_precond],
                             {"fgmres": HM_METHOD_FGMRES, "bicgstab": HM_METHOD_BICGSTAB}[inner_method],
-                            float(inner_tol), float(schur_tol), float(ilu_p))
+                            float(inner_tol), float(schur_tol), float(ilu_p), float(flow_scale))
         inf = hm_coupled_info()
         st = lib().hm_coupled_solve(H.handle, self.handle, _dptr(k) if k is not None else None,
                                     _dptr(cep) if cep is not None else None, float(shift), _dptr(b), _dptr(x),

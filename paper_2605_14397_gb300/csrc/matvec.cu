@@ -396,21 +396,13 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
 // consecutive entries one ldmatrix row group reads fall into eight different bank groups.
 __device__ __forceinline__ int tb16_piece_pos(int64_t l, int q) { return q ^ (int)((l >> 1) & 3); }
 
-// One CTA of 256 threads per block.  Threads (e, s): e over the block's float4 groups
-// (rank entries x 4 groups of 4 RHS, up to 256 at a time), s over S = 256 / (groups,
-// rounded up to a power of two) interleaved subsets of the leaves of T, four partials in
-// flight each; the S partial sums meet in shared memory and are added in s order (a
-// fixed order).  A CTA per block with only the groups as threads had left the blocks of
-// large column clusters -- hundreds of leaves each -- as long chains of dependent loads.
-constexpr int RTB_NT = 256;
-__global__ void __launch_bounds__(RTB_NT) k_reduce_tb_pack16(const FarDesc* __restrict__ far,
-                                                             const int32_t* __restrict__ poff,
-                                                             const int32_t* __restrict__ uoff,
-                                                             const float* __restrict__ P, uint16_t* __restrict__ tb,
-                                                             const int* __restrict__ skip) {
+__global__ void __launch_bounds__(128) k_reduce_tb_pack16(const FarDesc* __restrict__ far,
+                                                          const int32_t* __restrict__ poff,
+                                                          const int32_t* __restrict__ uoff,
+                                                          const float* __restrict__ P, uint16_t* __restrict__ tb,
+                                                          const int* __restrict__ skip) {
     constexpr int SPO = 2048;
     __shared__ int32_t spo[SPO];
-    __shared__ float4 part[RTB_NT];
     pdl_wait();
     pdl_trigger();
     if (skip && *(volatile const int*)skip) return;
@@ -419,61 +411,44 @@ __global__ void __launch_bounds__(RTB_NT) k_reduce_tb_pack16(const FarDesc* __re
     if (n4 == 0) return;
     const int32_t* po = poff + F.pbase;
     if (F.n_tleaves <= SPO) {
-        for (int q = threadIdx.x; q < F.n_tleaves; q += RTB_NT) spo[q] = po[q];
+        for (int q = threadIdx.x; q < F.n_tleaves; q += 128) spo[q] = po[q];
         __syncthreads();
         po = spo;
     }
-    int g = 1;  // groups per pass, a power of two
-    while (g < n4 && g < RTB_NT) g <<= 1;
-    const int S = RTB_NT / g;
-    const int eo = threadIdx.x % g, sub = threadIdx.x / g;
     const float4* P4 = reinterpret_cast<const float4*>(P);
-    for (int e0 = 0; e0 < n4; e0 += g) {
-        const int e = e0 + eo;
+    for (int e = threadIdx.x; e < n4; e += 128) {
         float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
-        if (e < n4) {
-            int q = sub;
-            for (; q + 3 * S < F.n_tleaves; q += 4 * S) {
-                const float4 v0 = P4[(int64_t)po[q] * 4 + e], v1 = P4[(int64_t)po[q + S] * 4 + e];
-                const float4 v2 = P4[(int64_t)po[q + 2 * S] * 4 + e], v3 = P4[(int64_t)po[q + 3 * S] * 4 + e];
-                s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
-                s1.x += v1.x; s1.y += v1.y; s1.z += v1.z; s1.w += v1.w;
-                s2.x += v2.x; s2.y += v2.y; s2.z += v2.z; s2.w += v2.w;
-                s3.x += v3.x; s3.y += v3.y; s3.z += v3.z; s3.w += v3.w;
-            }
-            for (; q < F.n_tleaves; q += S) {
-                const float4 v0 = P4[(int64_t)po[q] * 4 + e];
-                s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
-            }
+        int q = 0;
+        for (; q + 3 < F.n_tleaves; q += 4) {
+            const float4 v0 = P4[(int64_t)po[q] * 4 + e], v1 = P4[(int64_t)po[q + 1] * 4 + e];
+            const float4 v2 = P4[(int64_t)po[q + 2] * 4 + e], v3 = P4[(int64_t)po[q + 3] * 4 + e];
+            s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+            s1.x += v1.x; s1.y += v1.y; s1.z += v1.z; s1.w += v1.w;
+            s2.x += v2.x; s2.y += v2.y; s2.z += v2.z; s2.w += v2.w;
+            s3.x += v3.x; s3.y += v3.y; s3.z += v3.z; s3.w += v3.w;
         }
-        part[threadIdx.x] = make_float4((s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
-                                        (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w));
-        __syncthreads();
-        if (sub == 0 && e < n4) {
-            float4 a = part[eo];
-            for (int q = 1; q < S; ++q) {
-                const float4 b = part[q * g + eo];
-                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-            }
-            const float t[4] = {a.x, a.y, a.z, a.w};
-            uint32_t hb[4], lb[4];
+        for (; q < F.n_tleaves; ++q) {
+            const float4 v0 = P4[(int64_t)po[q] * 4 + e];
+            s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
+        }
+        const float t[4] = {(s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
+                            (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w)};
+        uint32_t hb[4], lb[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                hb[i] = bf16_bits(t[i]);
-                lb[i] = bf16_bits(t[i] - bf16_value(hb[i]));
-            }
-            const int k0 = (e & 3) * 4;                  // first of the four RHS
-            const int qh = 2 * (k0 >> 3), off = k0 & 7;  // hi piece of these RHS, offset inside it
-            for (int c = 0; c < F.n_sleaves; ++c) {     // one copy per leaf of S
-                const int64_t l = (int64_t)uoff[F.ubase + c] + e / 4;
-                uint16_t* row = tb + 32 * l;             // 64 bytes
-                *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh) + off) =
-                    make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
-                *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh + 1) + off) =
-                    make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
-            }
+        for (int i = 0; i < 4; ++i) {
+            hb[i] = bf16_bits(t[i]);
+            lb[i] = bf16_bits(t[i] - bf16_value(hb[i]));
         }
-        __syncthreads();
+        const int k0 = (e & 3) * 4;                  // first of the four RHS
+        const int qh = 2 * (k0 >> 3), off = k0 & 7;  // hi piece of these RHS, offset inside it
+        for (int c = 0; c < F.n_sleaves; ++c) {     // one copy per leaf of S
+            const int64_t l = (int64_t)uoff[F.ubase + c] + e / 4;
+            uint16_t* row = tb + 32 * l;             // 64 bytes
+            *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh) + off) =
+                make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+            *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh + 1) + off) =
+                make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+        }
     }
 }
 
@@ -1296,7 +1271,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
                        H.n_red_big, H.n_red,
                        (const V*)a.out, (uint32_t*)base.tb, base.skip);
         else if (kTensorPhase2x16 && base.nr == 16)
-            launch_pdl(k_reduce_tb_pack16, dim3((unsigned)H.n_far), dim3(RTB_NT), 0, st, (const FarDesc*)H.far.p,
+            launch_pdl(k_reduce_tb_pack16, dim3((unsigned)H.n_far), dim3(128), 0, st, (const FarDesc*)H.far.p,
                        (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const float*)a.out, (uint16_t*)base.tb,
                        base.skip);
         else if (base.nr == 1)

@@ -388,69 +388,13 @@ __global__ void __launch_bounds__(128) k_reduce_tb(const FarDesc* __restrict__ f
     }
 }
 
-// 16 right-hand sides with BF16 U slices on tensor cores: the same sums as k_reduce_tb
-// (float4 slices, four partials in flight, a fixed order), each value split into BF16
+// 16 right-hand sides with BF16 U slices on tensor cores: the sums of t (float4 slices,
+// k_reduce_pack16_mix below), each value split into BF16
 // hi + lo (hi = bf16(t), lo = bf16(t - hi)) and stored as the B operand of phase 2:
 // 64 bytes per rank entry l, four 16-byte pieces (RHS 0-7 hi, RHS 0-7 lo, RHS 8-15 hi,
 // RHS 8-15 lo), piece q stored at position q ^ ((l >> 1) & 3), so that the eight
 // consecutive entries one ldmatrix row group reads fall into eight different bank groups.
 __device__ __forceinline__ int tb16_piece_pos(int64_t l, int q) { return q ^ (int)((l >> 1) & 3); }
-
-__global__ void __launch_bounds__(128) k_reduce_tb_pack16(const FarDesc* __restrict__ far,
-                                                          const int32_t* __restrict__ poff,
-                                                          const int32_t* __restrict__ uoff,
-                                                          const float* __restrict__ P, uint16_t* __restrict__ tb,
-                                                          const int* __restrict__ skip) {
-    constexpr int SPO = 2048;
-    __shared__ int32_t spo[SPO];
-    pdl_wait();
-    pdl_trigger();
-    if (skip && *(volatile const int*)skip) return;
-    const FarDesc F = far[blockIdx.x];
-    const int n4 = F.rank * 4;  // float4 groups: rank entries x 4 groups of 4 RHS
-    if (n4 == 0) return;
-    const int32_t* po = poff + F.pbase;
-    if (F.n_tleaves <= SPO) {
-        for (int q = threadIdx.x; q < F.n_tleaves; q += 128) spo[q] = po[q];
-        __syncthreads();
-        po = spo;
-    }
-    const float4* P4 = reinterpret_cast<const float4*>(P);
-    for (int e = threadIdx.x; e < n4; e += 128) {
-        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
-        int q = 0;
-        for (; q + 3 < F.n_tleaves; q += 4) {
-            const float4 v0 = P4[(int64_t)po[q] * 4 + e], v1 = P4[(int64_t)po[q + 1] * 4 + e];
-            const float4 v2 = P4[(int64_t)po[q + 2] * 4 + e], v3 = P4[(int64_t)po[q + 3] * 4 + e];
-            s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
-            s1.x += v1.x; s1.y += v1.y; s1.z += v1.z; s1.w += v1.w;
-            s2.x += v2.x; s2.y += v2.y; s2.z += v2.z; s2.w += v2.w;
-            s3.x += v3.x; s3.y += v3.y; s3.z += v3.z; s3.w += v3.w;
-        }
-        for (; q < F.n_tleaves; ++q) {
-            const float4 v0 = P4[(int64_t)po[q] * 4 + e];
-            s0.x += v0.x; s0.y += v0.y; s0.z += v0.z; s0.w += v0.w;
-        }
-        const float t[4] = {(s0.x + s1.x) + (s2.x + s3.x), (s0.y + s1.y) + (s2.y + s3.y),
-                            (s0.z + s1.z) + (s2.z + s3.z), (s0.w + s1.w) + (s2.w + s3.w)};
-        uint32_t hb[4], lb[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            hb[i] = bf16_bits(t[i]);
-            lb[i] = bf16_bits(t[i] - bf16_value(hb[i]));
-        }
-        const int k0 = (e & 3) * 4;                  // first of the four RHS
-        const int qh = 2 * (k0 >> 3), off = k0 & 7;  // hi piece of these RHS, offset inside it
-        for (int c = 0; c < F.n_sleaves; ++c) {     // one copy per leaf of S
-            const int64_t l = (int64_t)uoff[F.ubase + c] + e / 4;
-            uint16_t* row = tb + 32 * l;             // 64 bytes
-            *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh) + off) =
-                make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
-            *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh + 1) + off) =
-                make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
-        }
-    }
-}
 
 // The same reduction for one RHS in one launch of 256-thread CTAs over a block order
 // (red_order) that lists the blocks with more than RED_WARP_LEAVES leaves of T first.
@@ -540,6 +484,129 @@ __global__ void __launch_bounds__(256) k_reduce_mix(const FarDesc* __restrict__ 
         if (on) {
             const Zt t = to_zin((s0 + s1) + (s2 + s3), tb);
             for (int c = 0; c < ns; ++c) tb[uo[c] + e] = t;  // one copy per leaf of S
+        }
+    }
+}
+
+// 16 RHS packed for TC16 over the same block order as k_reduce_mix: blocks with more
+// than RED_WARP_LEAVES leaves of T a 256-thread CTA each (float4 groups x subsets of the
+// leaves, partials meeting in shared memory in subset order), the others a warp each,
+// eight per CTA (lanes over the float4 groups, 32 offsets per load broadcast by
+// shuffles, four partials in flight).  Every block sums in a fixed order.
+__device__ __forceinline__ void store_pack16(uint16_t* __restrict__ tb, const int32_t* __restrict__ uo, int ns,
+                                             int e, float4 a) {
+    const float t[4] = {a.x, a.y, a.z, a.w};
+    uint32_t hb[4], lb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        hb[i] = bf16_bits(t[i]);
+        lb[i] = bf16_bits(t[i] - bf16_value(hb[i]));
+    }
+    const int k0 = (e & 3) * 4;                  // first of the four RHS
+    const int qh = 2 * (k0 >> 3), off = k0 & 7;  // hi piece of these RHS, offset inside it
+    for (int c = 0; c < ns; ++c) {               // one copy per leaf of S
+        const int64_t l = (int64_t)uo[c] + e / 4;
+        uint16_t* row = tb + 32 * l;             // 64 bytes
+        *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh) + off) =
+            make_uint2(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16));
+        *reinterpret_cast<uint2*>(row + 8 * tb16_piece_pos(l, qh + 1) + off) =
+            make_uint2(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16));
+    }
+}
+
+__device__ __forceinline__ void add4(float4& s, const float4 v) {
+    s.x += v.x;
+    s.y += v.y;
+    s.z += v.z;
+    s.w += v.w;
+}
+
+__global__ void __launch_bounds__(256) k_reduce_pack16_mix(const FarDesc* __restrict__ far,
+                                                           const int32_t* __restrict__ poff,
+                                                           const int32_t* __restrict__ uoff,
+                                                           const int32_t* __restrict__ order, int64_t n_big,
+                                                           int64_t n_all, const float* __restrict__ P,
+                                                           uint16_t* __restrict__ tb, const int* __restrict__ skip) {
+    __shared__ float4 sp[256];
+    constexpr int SPO = 2048;
+    __shared__ int32_t spo[SPO];
+    pdl_wait();
+    pdl_trigger();
+    if (skip && *(volatile const int*)skip) return;
+    const float4* P4 = reinterpret_cast<const float4*>(P);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((int64_t)blockIdx.x < n_big) {
+        const FarDesc F = far[order[blockIdx.x]];
+        const int n4 = 4 * F.rank, nt = F.n_tleaves;
+        const int32_t* po = poff + F.pbase;
+        if (nt <= SPO) {
+            for (int q = threadIdx.x; q < nt; q += 256) spo[q] = po[q];
+            __syncthreads();
+            po = spo;
+        }
+        for (int e0 = 0; e0 < n4; e0 += 256) {
+            const int r = min(256, n4 - e0);
+            const int G = 256 / r;
+            const int e = e0 + threadIdx.x % r, g = threadIdx.x / r;
+            float4 s0 = z4, s1 = z4, s2 = z4, s3 = z4;
+            if (g < G) {
+                int q = g;
+                for (; q + 3 * G < nt; q += 4 * G) {
+                    add4(s0, P4[(int64_t)po[q] * 4 + e]);
+                    add4(s1, P4[(int64_t)po[q + G] * 4 + e]);
+                    add4(s2, P4[(int64_t)po[q + 2 * G] * 4 + e]);
+                    add4(s3, P4[(int64_t)po[q + 3 * G] * 4 + e]);
+                }
+                for (; q < nt; q += G) add4(s0, P4[(int64_t)po[q] * 4 + e]);
+            }
+            add4(s0, s1);
+            add4(s2, s3);
+            add4(s0, s2);
+            sp[threadIdx.x] = s0;
+            __syncthreads();
+            if (threadIdx.x < r) {
+                float4 a = sp[threadIdx.x];
+                for (int q = 1; q < G; ++q) add4(a, sp[q * r + threadIdx.x]);
+                store_pack16(tb, uoff + F.ubase, F.n_sleaves, e0 + threadIdx.x, a);
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    const int64_t k = n_big + ((int64_t)blockIdx.x - n_big) * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= n_all) return;
+    const int64_t b = order[k];
+    const int n4 = 4 * far[b].rank, nt = far[b].n_tleaves;
+    const int32_t* po = poff + far[b].pbase;
+    for (int e0 = 0; e0 < n4; e0 += 32) {
+        const int e = e0 + lane;
+        const bool on = e < n4;
+        float4 s0 = z4, s1 = z4, s2 = z4, s3 = z4;
+        for (int q0 = 0; q0 < nt; q0 += 32) {
+            const int m = min(32, nt - q0);
+            const int32_t mine = lane < m ? po[q0 + lane] : 0;
+            int q = 0;
+            for (; q + 3 < m; q += 4) {
+                const int32_t o0 = __shfl_sync(0xffffffffu, mine, q), o1 = __shfl_sync(0xffffffffu, mine, q + 1);
+                const int32_t o2 = __shfl_sync(0xffffffffu, mine, q + 2), o3 = __shfl_sync(0xffffffffu, mine, q + 3);
+                if (on) {
+                    add4(s0, P4[(int64_t)o0 * 4 + e]);
+                    add4(s1, P4[(int64_t)o1 * 4 + e]);
+                    add4(s2, P4[(int64_t)o2 * 4 + e]);
+                    add4(s3, P4[(int64_t)o3 * 4 + e]);
+                }
+            }
+            for (; q < m; ++q) {
+                const int32_t o0 = __shfl_sync(0xffffffffu, mine, q);
+                if (on) add4(s0, P4[(int64_t)o0 * 4 + e]);
+            }
+        }
+        if (on) {
+            add4(s0, s1);
+            add4(s2, s3);
+            add4(s0, s2);
+            store_pack16(tb, uoff + far[b].ubase, far[b].n_sleaves, e, s0);
         }
     }
 }
@@ -663,7 +730,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1) k_phase2(StreamArgs a) {
                          std::is_same<C, uint16_t>::value;
     // BF16 U slices with 16 RHS (TC16, when the launch has exactly 16): warp w < 12 owns
     // m-tile w (rows 16 w .. 16 w + 15 of the leaf) and both n-tiles (RHS 0-7, 8-15); A as
-    // in TC2, B = t in the packed BF16 (hi, lo) form of k_reduce_tb_pack16 read with
+    // in TC2, B = t in the packed BF16 (hi, lo) form of k_reduce_pack16_mix read with
     // ldmatrix.trans, two mma per n-tile and k-tile.  The CUDA-core accumulators keep the
     // near tiles; the tensor-core results join them at the flush through ty.
     constexpr bool TC16 = MODE == 0 && NR == 16 && RS == 2 && NCW == 16 && RPL == 6 &&
@@ -1229,7 +1296,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
     static_assert(!kTensorPhase2x1 || (NCW2 == 16 && rs_for(NR) == 1),
                   "the single-RHS tensor-core phase 2 assumes 16 consumer warps without row split");
     // BF16 factors with 16 RHS: the U slices of phase 2 on tensor cores as well, reading t
-    // in the packed BF16 form of k_reduce_tb_pack16
+    // in the packed BF16 form of k_reduce_pack16_mix
     constexpr bool kTensorPhase2x16 = MODE == 0 && NR == 16 && std::is_same<C, uint16_t>::value && RPL == 6;
     constexpr int KP = (MODE == 0 && NR == 16 && RPL == 6) ? 8 : 1;  // RHS per flush pass of k_phase2
     const size_t smem2 = BAR_BYTES + (size_t)ST * (ZRange<V, NR>::BYTES + STAGE_BYTES) +
@@ -1271,9 +1338,9 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
                        H.n_red_big, H.n_red,
                        (const V*)a.out, (uint32_t*)base.tb, base.skip);
         else if (kTensorPhase2x16 && base.nr == 16)
-            launch_pdl(k_reduce_tb_pack16, dim3((unsigned)H.n_far), dim3(128), 0, st, (const FarDesc*)H.far.p,
-                       (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const float*)a.out, (uint16_t*)base.tb,
-                       base.skip);
+            launch_pdl(k_reduce_pack16_mix, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
+                       (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const int32_t*)H.red_order.p,
+                       H.n_red_big, H.n_red, (const float*)a.out, (uint16_t*)base.tb, base.skip);
         else if (base.nr == 1)
             launch_pdl(k_reduce_mix<V, Zt>, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
                        (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const int32_t*)H.red_order.p,

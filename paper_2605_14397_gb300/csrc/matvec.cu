@@ -579,34 +579,42 @@ __global__ void __launch_bounds__(256) k_reduce_pack16_mix(const FarDesc* __rest
     const int64_t b = order[k];
     const int n4 = 4 * far[b].rank, nt = far[b].n_tleaves;
     const int32_t* po = poff + far[b].pbase;
-    for (int e0 = 0; e0 < n4; e0 += 32) {
-        const int e = e0 + lane;
-        const bool on = e < n4;
-        float4 s0 = z4, s1 = z4, s2 = z4, s3 = z4;
+    // up to RP passes of 32 groups at once: their loads for one leaf are independent
+    constexpr int RP = 4;
+    for (int e0 = 0; e0 < n4; e0 += 32 * RP) {
+        float4 acc[2][RP];  // even and odd leaves: two more loads in flight
+#pragma unroll
+        for (int p = 0; p < RP; ++p) acc[0][p] = acc[1][p] = z4;
         for (int q0 = 0; q0 < nt; q0 += 32) {
             const int m = min(32, nt - q0);
             const int32_t mine = lane < m ? po[q0 + lane] : 0;
             int q = 0;
-            for (; q + 3 < m; q += 4) {
-                const int32_t o0 = __shfl_sync(0xffffffffu, mine, q), o1 = __shfl_sync(0xffffffffu, mine, q + 1);
-                const int32_t o2 = __shfl_sync(0xffffffffu, mine, q + 2), o3 = __shfl_sync(0xffffffffu, mine, q + 3);
-                if (on) {
-                    add4(s0, P4[(int64_t)o0 * 4 + e]);
-                    add4(s1, P4[(int64_t)o1 * 4 + e]);
-                    add4(s2, P4[(int64_t)o2 * 4 + e]);
-                    add4(s3, P4[(int64_t)o3 * 4 + e]);
+            for (; q + 1 < m; q += 2) {
+                const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, mine, q) * 4;
+                const int64_t o1 = (int64_t)__shfl_sync(0xffffffffu, mine, q + 1) * 4;
+#pragma unroll
+                for (int p = 0; p < RP; ++p) {
+                    const int e = e0 + 32 * p + lane;
+                    if (e < n4) {
+                        add4(acc[0][p], P4[o0 + e]);
+                        add4(acc[1][p], P4[o1 + e]);
+                    }
                 }
             }
-            for (; q < m; ++q) {
-                const int32_t o0 = __shfl_sync(0xffffffffu, mine, q);
-                if (on) add4(s0, P4[(int64_t)o0 * 4 + e]);
+            if (q < m) {
+                const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, mine, q) * 4;
+#pragma unroll
+                for (int p = 0; p < RP; ++p) {
+                    const int e = e0 + 32 * p + lane;
+                    if (e < n4) add4(acc[0][p], P4[o0 + e]);
+                }
             }
         }
-        if (on) {
-            add4(s0, s1);
-            add4(s2, s3);
-            add4(s0, s2);
-            store_pack16(tb, uoff + far[b].ubase, far[b].n_sleaves, e, s0);
+#pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            const int e = e0 + 32 * p + lane;
+            add4(acc[0][p], acc[1][p]);
+            if (e < n4) store_pack16(tb, uoff + far[b].ubase, far[b].n_sleaves, e, acc[0][p]);
         }
     }
 }

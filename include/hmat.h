@@ -284,7 +284,9 @@ typedef struct {
     const double* cep_dev;  /* block-diagonal C^ep (device, N x 9: per element in user order, row-major
                                3x3 in its frame (s1, s2, n), e.g. from hm_interface_update) or NULL */
     int method;        /* HM_METHOD_FGMRES (0) or HM_METHOD_BICGSTAB */
-    int pad2_;
+    int reuse_precond; /* 1: keep the preconditioner of the previous call on this H-matrix when it was
+                          built for the same k_dev, cep_dev, shift, precond, ilu_p and lp (the caller
+                          promises the arrays behind the pointers are unchanged) */
 } hm_solve_opts;
 
 typedef struct {

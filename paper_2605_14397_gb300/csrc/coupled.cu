@@ -334,6 +334,7 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
     io.ilu_p = o.ilu_p;
     io.cep_dev = cep;
     io.maxit = 3000;
+    io.reuse_precond = 0;  // the first nested solve builds it, the others keep it
     DevBuf<double> V((size_t)(m + 1) * n), Z((size_t)m * n), w(n), r(n), t1(n1), bs(n), sws;
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
     // the flow rows scaled by sr (Sec. 3.3.2 scales residuals to order one): by default
@@ -378,6 +379,7 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
                 // an inexact inner solve is still a valid flexible preconditioner step
                 if (e.code != HM_ENOCONV) throw;
             }
+            io.reuse_precond = 1;
             inner += ii.iters;
             apply_scaled(zj, w.p);
             // modified Gram-Schmidt

@@ -941,6 +941,19 @@ struct SolveWS {
     bool dsc_on = false;  // apply the learned per-leaf scalings after block-Jacobi
     DevBuf<double> blkbuf;  // off-diagonal C^ep blocks, cluster element order
     DevBuf<double> bcg;     // BiCGSTAB vectors: rh, p, v, ph, s, sh, t (nr x 3N each)
+    // what the preconditioner in the workspace was built for (hm_solve_opts.reuse_precond)
+    struct PcKey {
+        bool valid = false;
+        const double* kel = nullptr;
+        const double* cep = nullptr;
+        double shift = 0.0, ilu_p = 0.0;
+        int precond = -1;
+        const void* lp = nullptr;
+        bool same(const PcKey& o) const {
+            return valid && o.kel == kel && o.cep == cep && o.shift == shift && o.ilu_p == ilu_p &&
+                   o.precond == precond && o.lp == lp;
+        }
+    } pc_key;
     DevBuf<BcgScal> bsc;
     const double* blk = nullptr;  // blkbuf.p when the tangent has a block-diagonal C^ep
     DevBuf<int64_t> binv_off, self_off;
@@ -967,6 +980,7 @@ SolveWS& workspace(HMat& H, int nr, int m, cudaStream_t st) {
     if (!H.solve_ws) H.solve_ws = new SolveWS();
     SolveWS& W = *H.solve_ws;
     if (W.nr >= nr && W.m >= m && W.ndof == H.ndof) return W;
+    W.pc_key.valid = false;  // the buffers below are reallocated
     W.nr = std::max(W.nr, nr);
     W.m = std::max(W.m, m);
     W.ndof = H.ndof;
@@ -1346,6 +1360,7 @@ void bj_solve_cluster(HMat& H, const double* kel, double shift, const double* v,
                       cudaStream_t st) {
     if (nr < 1 || nr > 16) fail(HM_EINVAL, "block-Jacobi solve: 1 to 16 right-hand sides");
     SolveWS& W = workspace(H, nr, 1, st);
+    W.pc_key.valid = false;
     set_tangent(H, W, kel, nullptr, shift, st);
     bj_build(H, W, st);
     std::vector<CycleState> cs(nr, CycleState{0, 0, 0, 0, 0.0, 0.0});
@@ -1362,6 +1377,7 @@ void ilu_export_for(HMat& H, const double* kel, const double* cep, double shift,
                     int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr, int32_t* col,
                     double* a_val, double* lu_val, cudaStream_t st) {
     SolveWS& W = workspace(H, 1, 1, st);
+    W.pc_key.valid = false;
     set_tangent(H, W, kel, cep, shift, st);
     ilu_prepare(H, p, cep != nullptr, st);
     if (lu_val) ilu_factor(H, W.dc.p, W.blk, st, W.err.p);
@@ -1471,19 +1487,32 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
                           ? PC_LEAF
                           : (o.precond == HM_PRECOND_JACOBI3 ? PC_POINT
                                                              : (o.precond == HM_PRECOND_ILU ? PC_ILU : PC_NONE));
-    W.dsc_on = false;
-    if (pc == PC_POINT) j3_build(H, W, st);
-    if (pc == PC_ILU) {
-        ilu_prepare(H, ilu_p, cep != nullptr, st);
-        ilu_factor(H, W.dc.p, W.blk, st, W.err.p);
-    }
-    if (pc == PC_LEAF) {
-        bj_build(H, W, st);
-        if (o.precond == HM_PRECOND_LEARNED && !lp->fallback) {
-            W.dsc.alloc((size_t)H.n_leaves * 3);
-            lp_predict(const_cast<LPModel&>(*lp), H, kel, W.dsc.p, nullptr, st);
-            W.dsc_on = true;
+    SolveWS::PcKey key;
+    key.valid = true;
+    key.kel = kel;
+    key.cep = cep;
+    key.shift = shift;
+    key.ilu_p = pc == PC_ILU ? ilu_p : 0.0;
+    key.precond = o.precond;
+    key.lp = lp;
+    const bool reuse = o.reuse_precond && W.pc_key.same(key) && (pc != PC_ILU || ilu_is_factored(H));
+    if (!reuse) {
+        W.pc_key.valid = false;
+        W.dsc_on = false;
+        if (pc == PC_POINT) j3_build(H, W, st);
+        if (pc == PC_ILU) {
+            ilu_prepare(H, ilu_p, cep != nullptr, st);
+            ilu_factor(H, W.dc.p, W.blk, st, W.err.p);
         }
+        if (pc == PC_LEAF) {
+            bj_build(H, W, st);
+            if (o.precond == HM_PRECOND_LEARNED && !lp->fallback) {
+                W.dsc.alloc((size_t)H.n_leaves * 3);
+                lp_predict(const_cast<LPModel&>(*lp), H, kel, W.dsc.p, nullptr, st);
+                W.dsc_on = true;
+            }
+        }
+        W.pc_key = key;
     }
     // ||b||
     HM_CUDA(cudaMemsetAsync(W.xc.p, 0, (size_t)n * nrhs * sizeof(double), st));

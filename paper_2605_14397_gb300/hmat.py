@@ -69,7 +69,7 @@ class hm_solve_opts(ctypes.Structure):
                 ("precond", ctypes.c_int), ("mode", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int), ("pad_", ctypes.c_int), ("lp", ctypes.c_void_p),
                 ("ilu_p", ctypes.c_double), ("cep_dev", ctypes.c_void_p), ("method", ctypes.c_int),
-                ("pad2_", ctypes.c_int)]
+                ("reuse_precond", ctypes.c_int)]
 
 
 class hm_tile_shape(ctypes.Structure):
@@ -383,7 +383,7 @@ class HMatrix:
 
     def solve(self, b, x, k=None, shift=0.0, tol=1e-8, restart=50, maxit=2000, precond="blockj", mode="f64",
               inner_tol=1e-2, max_outer=40, stream=None, raise_on_error=True, model=None, ilu_p=0.0, cep=None,
-              method="fgmres"):
+              method="fgmres", reuse_precond=False):
         """Solve (E - diag(k) - C^ep - shift I) x = b on the device (b, x: float64 CUDA tensors
         of shape (3N,) or (nrhs, 3N); k: float64 CUDA tensor (N,) or None; cep: float64 CUDA
         tensor (N, 3, 3) of per-element tangent blocks, user order, or None).  precond "none",
@@ -400,7 +400,7 @@ class HMatrix:
                           float(inner_tol), int(max_outer), 0,
                           model.handle.value if model is not None else None, float(ilu_p),
                           cep.data_ptr() if cep is not None else None,
-                          {"fgmres": HM_METHOD_FGMRES, "bicgstab": HM_METHOD_BICGSTAB}[method], 0)
+                          {"fgmres": HM_METHOD_FGMRES, "bicgstab": HM_METHOD_BICGSTAB}[method], int(bool(reuse_precond)))
         info = (hm_solve_info * nrhs)()
         st = lib().hm_gmres_solve(self.handle, _dptr(k) if k is not None else None, float(shift), _dptr(b), _dptr(x),
                                   int(nrhs), ctypes.byref(o), info, ctypes.c_void_p(_stream_ptr(stream)))

@@ -97,3 +97,25 @@ def test_bicgstab_mixed_several_rhs_and_cep(dev, cases):
         for q in range(3):
             xl = np.linalg.solve(At, B[q])
             assert np.linalg.norm(X[q].cpu().numpy() - xl) <= 1e-6 * np.linalg.norm(xl)
+
+
+@pytest.mark.parametrize("precond", ["jacobi3", "blockj", "ilu"])
+def test_reused_preconditioner_gives_the_same_solution(dev, cases, precond):
+    """reuse_precond keeps the preconditioner of the previous call with the same tangent
+    inputs: the solution is bit for bit that of a call that builds it."""
+    import torch
+    el, To, H, A, h, k = cases["penny24"]
+    kt = torch.as_tensor(k, device=dev)
+    b = torch.as_tensor(synth.rhs_normal(3 * el.N, 65), device=dev)
+    x0 = torch.zeros_like(b)
+    H.solve(b, x0, kt, precond=precond, ilu_p=0.01)
+    x1 = torch.zeros_like(b)
+    H.solve(b, x1, kt, precond=precond, ilu_p=0.01, reuse_precond=True)
+    assert torch.equal(x0, x1)
+    # a different stiffness array is not reused
+    k2 = kt * 1.5
+    x2 = torch.zeros_like(b)
+    x3 = torch.zeros_like(b)
+    H.solve(b, x2, k2, precond=precond, ilu_p=0.01, reuse_precond=True)
+    H.solve(b, x3, k2, precond=precond, ilu_p=0.01)
+    assert torch.equal(x2, x3)

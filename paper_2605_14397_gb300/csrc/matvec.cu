@@ -573,27 +573,49 @@ __global__ void __launch_bounds__(256) k_reduce_pack16_mix(const FarDesc* __rest
         }
         return;
     }
-    // the other blocks two per CTA, 128 threads each: a thread per float4 group, four
-    // leaves in flight
-    const int64_t k = n_big + ((int64_t)blockIdx.x - n_big) * 2 + (threadIdx.x >> 7);
+    const int64_t k = n_big + ((int64_t)blockIdx.x - n_big) * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (k >= n_all) return;
     const int64_t b = order[k];
     const int n4 = 4 * far[b].rank, nt = far[b].n_tleaves;
     const int32_t* po = poff + far[b].pbase;
-    for (int e = threadIdx.x & 127; e < n4; e += 128) {
-        float4 s0 = z4, s1 = z4, s2 = z4, s3 = z4;
-        int q = 0;
-        for (; q + 3 < nt; q += 4) {
-            add4(s0, P4[(int64_t)po[q] * 4 + e]);
-            add4(s1, P4[(int64_t)po[q + 1] * 4 + e]);
-            add4(s2, P4[(int64_t)po[q + 2] * 4 + e]);
-            add4(s3, P4[(int64_t)po[q + 3] * 4 + e]);
+    // up to RP passes of 32 groups at once: their loads for one leaf are independent
+    constexpr int RP = 4;
+    for (int e0 = 0; e0 < n4; e0 += 32 * RP) {
+        float4 acc[2][RP];  // even and odd leaves: two more loads in flight
+#pragma unroll
+        for (int p = 0; p < RP; ++p) acc[0][p] = acc[1][p] = z4;
+        for (int q0 = 0; q0 < nt; q0 += 32) {
+            const int m = min(32, nt - q0);
+            const int32_t mine = lane < m ? po[q0 + lane] : 0;
+            int q = 0;
+            for (; q + 1 < m; q += 2) {
+                const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, mine, q) * 4;
+                const int64_t o1 = (int64_t)__shfl_sync(0xffffffffu, mine, q + 1) * 4;
+#pragma unroll
+                for (int p = 0; p < RP; ++p) {
+                    const int e = e0 + 32 * p + lane;
+                    if (e < n4) {
+                        add4(acc[0][p], P4[o0 + e]);
+                        add4(acc[1][p], P4[o1 + e]);
+                    }
+                }
+            }
+            if (q < m) {
+                const int64_t o0 = (int64_t)__shfl_sync(0xffffffffu, mine, q) * 4;
+#pragma unroll
+                for (int p = 0; p < RP; ++p) {
+                    const int e = e0 + 32 * p + lane;
+                    if (e < n4) add4(acc[0][p], P4[o0 + e]);
+                }
+            }
         }
-        for (; q < nt; ++q) add4(s0, P4[(int64_t)po[q] * 4 + e]);
-        add4(s0, s1);
-        add4(s2, s3);
-        add4(s0, s2);
-        store_pack16(tb, uoff + far[b].ubase, far[b].n_sleaves, e, s0);
+#pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            const int e = e0 + 32 * p + lane;
+            add4(acc[0][p], acc[1][p]);
+            if (e < n4) store_pack16(tb, uoff + far[b].ubase, far[b].n_sleaves, e, acc[0][p]);
+        }
     }
 }
 
@@ -1324,9 +1346,7 @@ void launch_phases(HMat& H, const HMat::Plan& PL, const StreamArgs& base, bool t
                        H.n_red_big, H.n_red,
                        (const V*)a.out, (uint32_t*)base.tb, base.skip);
         else if (kTensorPhase2x16 && base.nr == 16)
-            launch_pdl(k_reduce_pack16_mix,
-                       dim3((unsigned)std::max<int64_t>(1, H.n_red_big + (H.n_red - H.n_red_big + 1) / 2)), dim3(256),
-                       0, st, (const FarDesc*)H.far.p,
+            launch_pdl(k_reduce_pack16_mix, dim3(gm), dim3(256), 0, st, (const FarDesc*)H.far.p,
                        (const int32_t*)H.poff.p, (const int32_t*)H.uoff.p, (const int32_t*)H.red_order.p,
                        H.n_red_big, H.n_red, (const float*)a.out, (uint16_t*)base.tb, base.skip);
         else if (base.nr == 1)

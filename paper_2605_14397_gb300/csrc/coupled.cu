@@ -17,7 +17,8 @@
 // Solve: right-preconditioned restarted FGMRES on [[A11, A12], [A21, A22]] with
 // P_up = [[A11, A12], [0, S~]], S~ = A22 - A21 diag(A11)^-1 A12 (the paper's first
 // approximation, a sparse matrix with the pattern of A22); P_up^-1 y takes
-// z2 = S~^-1 y2 by Jacobi-preconditioned BiCGSTAB on S~ and z1 = A11^-1 (y1 - A12 z2)
+// z2 = S~^-1 y2 by Jacobi-preconditioned BiCGSTAB on S~ (scalars on the device) and
+// z1 = A11^-1 (y1 - A12 z2)
 // by the library's tangent solver (nested, to a relative tolerance), so the outer method
 // is flexible.  Krylov vectors, dot products and rotations in FP64.
 #include <algorithm>
@@ -152,14 +153,6 @@ __global__ void k_diag_of(int64_t nn, const int64_t* __restrict__ rowptr, const 
     dinv[r] = 1.0 / d;
 }
 
-__global__ void k_spmv(int64_t nn, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= nn) return;
-    double s = 0.0;
-    for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) s += val[q] * x[col[q]];
-    y[r] = s;
-}
 
 // per-block partial sums of x . y (fixed order inside and across blocks)
 __global__ void k_dot_part(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
@@ -178,14 +171,10 @@ __global__ void k_dot_part(int64_t n, const double* __restrict__ x, const double
     }
 }
 
-// y = alpha x + beta y;  z = x .* y (Jacobi)
+// y = alpha x + beta y
 __global__ void k_axpby(int64_t n, double alpha, const double* __restrict__ x, double beta, double* __restrict__ y) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) y[i] = alpha * x[i] + beta * y[i];
-}
-__global__ void k_mul(int64_t n, const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ z) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) z[i] = x[i] * y[i];
 }
 
 constexpr int DOT_BLOCKS = 304;  // two per SM
@@ -244,53 +233,168 @@ void coupled_apply(HMat& H, const hm_flow& F, const double* kel, const double* c
 
 namespace {
 
-// z = S~^-1 y by Jacobi-preconditioned BiCGSTAB to the relative tolerance tol (x0 = 0);
-// returns the iterations
+// Scalars of the Schur BiCGSTAB on the device: sc = {rho, alpha, omega, beta, bn, done}
+struct SchurScal {
+    double rho, alpha, omega, beta, bn2;
+    int done, iters, pad;
+};
+
+// the sum of DOT_BLOCKS partials, in block order, by one warp (lane-strided, then a
+// butterfly: a fixed order)
+__device__ __forceinline__ double sum_parts(const double* __restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < DOT_BLOCKS; b += 32) s += part[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// stage 0: rho_new = (rh, r) -> beta; 1: alpha = rho / (rh, v); 2: omega = (t, s) / (t, t);
+// 3: ||r||^2 -> done; -1: ||y||^2 -> bn2.  One warp.
+__global__ void k_schur_stage(int stage, const double* __restrict__ p0, const double* __restrict__ p1, double tol,
+                              int maxit, SchurScal* __restrict__ sc) {
+    const double d0 = sum_parts(p0);
+    const double d1 = p1 ? sum_parts(p1) : 0.0;
+    if (threadIdx.x != 0) return;
+    SchurScal& S = *sc;
+    if (stage == -1) {
+        S.bn2 = d0;
+        S.rho = S.alpha = S.omega = 1.0;
+        S.beta = 0.0;
+        S.iters = 0;
+        S.done = d0 > 0.0 ? 0 : 1;
+        return;
+    }
+    if (S.done) return;
+    if (stage == 0) {
+        if (!(d0 != 0.0) || !isfinite(d0)) {
+            S.done = 1;
+            return;
+        }
+        S.beta = S.iters == 0 ? 0.0 : (d0 / S.rho) * (S.alpha / S.omega);
+        S.rho = d0;
+    } else if (stage == 1) {
+        if (!(d0 != 0.0) || !isfinite(d0)) {
+            S.done = 1;
+            return;
+        }
+        S.alpha = S.rho / d0;
+    } else if (stage == 2) {
+        S.omega = d1 > 0.0 ? d0 / d1 : 0.0;
+    } else {
+        ++S.iters;
+        if (d0 <= tol * tol * S.bn2 || !(S.omega != 0.0) || S.iters >= maxit) S.done = 1;
+    }
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_schur_p(int64_t n, double* __restrict__ p, const double* __restrict__ r,
+                          const double* __restrict__ v, const SchurScal* __restrict__ sc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || sc->done) return;
+    p[i] = r[i] + sc->beta * (p[i] - sc->omega * v[i]);
+}
+// s = r - alpha v;  z += alpha ph
+__global__ void k_schur_s(int64_t n, double* __restrict__ sv, const double* __restrict__ r,
+                          const double* __restrict__ v, double* __restrict__ z, const double* __restrict__ ph,
+                          const SchurScal* __restrict__ sc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || sc->done) return;
+    sv[i] = r[i] - sc->alpha * v[i];
+    z[i] += sc->alpha * ph[i];
+}
+// z += omega sh;  r = s - omega t
+__global__ void k_schur_zr(int64_t n, double* __restrict__ z, double* __restrict__ r, const double* __restrict__ sh,
+                           const double* __restrict__ sv, const double* __restrict__ t,
+                           const SchurScal* __restrict__ sc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || sc->done) return;
+    z[i] += sc->omega * sh[i];
+    r[i] = sv[i] - sc->omega * t[i];
+}
+// x .* y (Jacobi) and the CSR product, skipped once done
+__global__ void k_schur_mul(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                            double* __restrict__ z, const SchurScal* __restrict__ sc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && !sc->done) z[i] = x[i] * y[i];
+}
+__global__ void k_schur_spmv(int64_t nn, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
+                             const SchurScal* __restrict__ sc) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= nn || sc->done) return;
+    double s = 0.0;
+    for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) s += val[q] * x[col[q]];
+    y[r] = s;
+}
+
+// z = S~^-1 y by Jacobi-preconditioned BiCGSTAB to the relative tolerance tol (x0 = 0),
+// scalars on the device; the host polls the done flag two iterations behind through
+// pinned memory.  Returns the iterations.
+struct SchurWS {
+    DevBuf<double> v;        // r, rh, p, v, ph, s, sh, t and three partial rows
+    DevBuf<SchurScal> sc{(size_t)1};
+    SchurScal* h_sc = nullptr;  // pinned
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    SchurWS() {
+        HM_CUDA(cudaHostAlloc((void**)&h_sc, 2 * sizeof(SchurScal), cudaHostAllocDefault));
+        for (cudaEvent_t& e : ev) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    ~SchurWS() {
+        if (h_sc) cudaFreeHost(h_sc);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
 int schur_solve(const hm_flow& F, const double* sval, const double* sdinv, const double* y, double* z, double tol,
-                int maxit, DevBuf<double>& ws, Dots& D, cudaStream_t st) {
+                int maxit, SchurWS& W, cudaStream_t st) {
     const int64_t n = F.nn;
-    if (ws.n < (size_t)(7 * n)) ws.alloc((size_t)(7 * n));
-    double *r = ws.p, *rh = r + n, *p = rh + n, *v = p + n, *ph = v + n, *sv = ph + n, *t = sv + n;
+    if (W.v.n < (size_t)(8 * n + 3 * DOT_BLOCKS)) W.v.alloc((size_t)(8 * n + 3 * DOT_BLOCKS));
+    double *r = W.v.p, *rh = r + n, *p = rh + n, *v = p + n, *ph = v + n, *sv = ph + n, *sh = sv + n, *t = sh + n;
+    double *pa = t + n, *pb = pa + DOT_BLOCKS, *pc = pb + DOT_BLOCKS;
+    SchurScal* sc = W.sc.p;
+    const unsigned g = gsz(n);
+    auto dot = [&](const double* a, const double* b, double* part) {
+        k_dot_part<<<DOT_BLOCKS, NT, 0, st>>>(n, a, b, part);
+    };
     HM_CUDA(cudaMemsetAsync(z, 0, n * sizeof(double), st));
     HM_CUDA(cudaMemcpyAsync(r, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     HM_CUDA(cudaMemcpyAsync(rh, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     HM_CUDA(cudaMemsetAsync(p, 0, n * sizeof(double), st));
     HM_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), st));
-    const double bn = std::sqrt(D.dot(n, y, y, st));
-    if (bn == 0.0) return 0;
-    double rho = 1.0, alpha = 1.0, omega = 1.0;
-    int it = 0;
-    for (; it < maxit; ++it) {
-        const double rho_n = D.dot(n, rh, r, st);
-        if (rho_n == 0.0) break;
-        const double beta = it == 0 ? 0.0 : (rho_n / rho) * (alpha / omega);
-        rho = rho_n;
-        // p = r + beta (p - omega v)
-        axpby(n, -omega, v, 1.0, p, st);
-        axpby(n, 1.0, r, beta, p, st);
-        k_mul<<<gsz(n), NT, 0, st>>>(n, sdinv, p, ph);
-        k_spmv<<<gsz(n), NT, 0, st>>>(n, F.rowptr.p, F.col.p, sval, ph, v);
-        HM_LAUNCH_CHECK();
-        const double den = D.dot(n, rh, v, st);
-        if (den == 0.0) break;
-        alpha = rho / den;
-        HM_CUDA(cudaMemcpyAsync(sv, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        axpby(n, -alpha, v, 1.0, sv, st);
-        axpby(n, alpha, ph, 1.0, z, st);
-        k_mul<<<gsz(n), NT, 0, st>>>(n, sdinv, sv, ph);
-        k_spmv<<<gsz(n), NT, 0, st>>>(n, F.rowptr.p, F.col.p, sval, ph, t);
-        HM_LAUNCH_CHECK();
-        const double tt = D.dot(n, t, t, st);
-        omega = tt > 0.0 ? D.dot(n, t, sv, st) / tt : 0.0;
-        axpby(n, omega, ph, 1.0, z, st);
-        HM_CUDA(cudaMemcpyAsync(r, sv, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        axpby(n, -omega, t, 1.0, r, st);
-        if (std::sqrt(D.dot(n, r, r, st)) <= tol * bn || omega == 0.0) {
-            ++it;
-            break;
+    dot(y, y, pa);
+    k_schur_stage<<<1, 32, 0, st>>>(-1, pa, nullptr, tol, maxit, sc);
+    HM_LAUNCH_CHECK();
+    for (int it = 0; it < maxit; ++it) {
+        if (it >= 2) {
+            HM_CUDA(cudaEventSynchronize(W.ev[it % 2]));
+            if (W.h_sc[it % 2].done) break;
         }
+        dot(rh, r, pa);
+        k_schur_stage<<<1, 32, 0, st>>>(0, pa, nullptr, tol, maxit, sc);
+        k_schur_p<<<g, NT, 0, st>>>(n, p, r, v, sc);
+        k_schur_mul<<<g, NT, 0, st>>>(n, sdinv, p, ph, sc);
+        k_schur_spmv<<<g, NT, 0, st>>>(n, F.rowptr.p, F.col.p, sval, ph, v, sc);
+        dot(rh, v, pa);
+        k_schur_stage<<<1, 32, 0, st>>>(1, pa, nullptr, tol, maxit, sc);
+        k_schur_s<<<g, NT, 0, st>>>(n, sv, r, v, z, ph, sc);
+        k_schur_mul<<<g, NT, 0, st>>>(n, sdinv, sv, sh, sc);
+        k_schur_spmv<<<g, NT, 0, st>>>(n, F.rowptr.p, F.col.p, sval, sh, t, sc);
+        dot(t, sv, pb);
+        dot(t, t, pc);
+        k_schur_stage<<<1, 32, 0, st>>>(2, pb, pc, tol, maxit, sc);
+        k_schur_zr<<<g, NT, 0, st>>>(n, z, r, sh, sv, t, sc);
+        dot(r, r, pa);
+        k_schur_stage<<<1, 32, 0, st>>>(3, pa, nullptr, tol, maxit, sc);
+        HM_LAUNCH_CHECK();
+        HM_CUDA(cudaMemcpyAsync(W.h_sc + (it % 2), sc, sizeof(SchurScal), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaEventRecord(W.ev[it % 2], st));
     }
-    return it;
+    HM_CUDA(cudaMemcpyAsync(W.h_sc, sc, sizeof(SchurScal), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    return W.h_sc[0].iters;
 }
 
 }  // namespace
@@ -335,7 +439,8 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
     io.cep_dev = cep;
     io.maxit = 3000;
     io.reuse_precond = 0;  // the first nested solve builds it, the others keep it
-    DevBuf<double> V((size_t)(m + 1) * n), Z((size_t)m * n), w(n), r(n), t1(n1), bs(n), sws;
+    DevBuf<double> V((size_t)(m + 1) * n), Z((size_t)m * n), w(n), r(n), t1(n1), bs(n);
+    SchurWS sws;
     std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
     // the flow rows scaled by sr (Sec. 3.3.2 scales residuals to order one): by default
     // the ratio of the RMS diagonal of A11 to that of S~, so that the stopping test
@@ -367,7 +472,7 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
             const double* vj = V.p + (size_t)j * n;
             double* zj = Z.p + (size_t)j * n;
             // z = P_up^-1 v of the scaled system: z2 = S~^-1 v2 / sr, z1 = A11^-1 (v1 - N_p z2)
-            schur += schur_solve(F, sval.p, sdinv.p, vj + n1, zj + n1, stol, 2000, sws, D, st);
+            schur += schur_solve(F, sval.p, sdinv.p, vj + n1, zj + n1, stol, 2000, sws, st);
             axpby(n2, 0.0, zj + n1, 1.0 / sr, zj + n1, st);
             HM_CUDA(cudaMemcpyAsync(t1.p, vj, n1 * sizeof(double), cudaMemcpyDeviceToDevice, st));
             k_np_add<<<gsz(F.N), NT, 0, st>>>(F.N, F.conn.p, zj + n1, -1.0, t1.p);

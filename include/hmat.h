@@ -302,6 +302,14 @@ hm_status hm_gmres_solve(const hm_hmat* h, const double* k_dev, double shift, co
                          double* x_dev, int nrhs, const hm_solve_opts* opt, hm_solve_info* info,
                          void* stream);
 
+/* z = M^-1 r with the preconditioner hm_gmres_solve builds for A = E - diag(k) - C^ep -
+ * shift I and these options (precond, ilu_p, lp, cep_dev, reuse_precond; the other
+ * fields are ignored), for a caller's own Krylov method -- e.g. the nested solves of
+ * Sec. 3.3.1 -- and for checking the preconditioners.  r_dev, z_dev: nrhs x 3N doubles,
+ * user order, not overlapping.  Synchronises the stream. */
+hm_status hm_precond_apply(const hm_hmat* h, const double* k_dev, double shift, const hm_solve_opts* opt,
+                           const double* r_dev, double* z_dev, int nrhs, void* stream);
+
 /* The ILU preconditioner that hm_gmres_solve builds for A = E - diag(k) - C^ep - shift I
  * and the fraction p (Sec. 3.3.1), to host arrays (any may be NULL; pass NULL arrays first to
  * learn n and nnz).  n_out: 3N; nnz_out: entries of the pattern; n_colours_out: leaf
@@ -526,8 +534,12 @@ hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const 
 /* ---------------------------------------------------------------- learned correction
  * The paper preconditions the A11 system with (point) Jacobi (Sec. 3.3.1) and learns
  * nothing; this library adds an optional learned correction of its leaf block-Jacobi
- * preconditioner B of A = E - diag(k) (eq. jac_mech):
- *   M^-1 r = D B^-1 r,  D = diag(d_(leaf, component)),  d = 1 + 0.5 tanh(o),
+ * preconditioner B of A = E - diag(k) (eq. jac_mech), of one of two kinds:
+ *   HM_LP_SCALE:  M^-1 r = D B^-1 r,
+ *   HM_LP_NEAR:   M^-1 r = y - gamma D B^-1 N y,  y = B^-1 r, N = the near-field tiles of
+ *                 E off the diagonal leaf blocks (the first Neumann term of the near
+ *                 coupling, damped per leaf and component by the network),
+ *   D = diag(d_(leaf, component)),  d = 1 + 0.5 tanh(o),
  *   o = W3 tanh(W2 tanh(W1 f + b1) + b2) + b3,
  * per leaf and DOF component, from eight leaf features f: mean, standard deviation, min
  * and max of log10(k h / E + 1e-6) over the leaf's elements (h = sqrt(4 a b)), the
@@ -540,7 +552,9 @@ hm_status hm_autotune(const hm_elements* el, const hm_assemble_opts* opt, const 
  *   loss = (1 / n_groups) sum_samples sum_a  q_xx - 2 d_a q_xy + d_a^2 q_yy,
  * a sample being one leaf of one solved system A x = b with q = S / T: S the leaf and
  * component sums of x y, y y, x x over the system's right-hand sides (y = B^-1 b), T
- * the system's sum of x x -- the fit of D B^-1 b to x = A^-1 b.
+ * the system's sum of x x -- the fit of D B^-1 b to x = A^-1 b; for HM_LP_NEAR the same
+ * sums of x' = y - x and y' = w = B^-1 N y (the fit of D w to y - x).  gamma is the
+ * caller's choice on validation systems (GMRES iterations as the judge).
  * The model's parameters live in host memory (device copies made on first GPU use), so
  * create / add_samples / get_params / set_fallback / info / save / load need no GPU.
  * A model flagged `fallback` makes HM_PRECOND_LEARNED apply plain block-Jacobi (set it
@@ -553,7 +567,13 @@ typedef struct {
     int64_t n_groups;
     int64_t steps;        /* Adam steps taken */
     double last_loss;     /* loss before the last step of the last hm_lp_train */
+    int32_t kind;         /* HM_LP_SCALE or HM_LP_NEAR */
+    int32_t pad_;
+    double gamma;         /* HM_LP_NEAR: factor on d */
 } hm_lp_info;
+
+#define HM_LP_SCALE 0
+#define HM_LP_NEAR 1
 
 /* number of parameters for `hidden` units (16, 32 or 64), -1 otherwise */
 int64_t hm_lp_param_count(int hidden);
@@ -578,9 +598,13 @@ hm_status hm_lp_predict(hm_lp* lp, const hm_hmat* h, const double* k_dev, double
                         double* d_out, void* stream);
 hm_status hm_lp_get_params(const hm_lp* lp, double* theta_out);
 hm_status hm_lp_set_fallback(hm_lp* lp, int fallback);
+/* the kind of correction (HM_LP_SCALE, the default, or HM_LP_NEAR) and gamma > 0; the kind
+ * can change only while the model holds no samples (HM_EINVAL otherwise) */
+hm_status hm_lp_set_kind(hm_lp* lp, int kind, double gamma);
 hm_status hm_lp_get_info(const hm_lp* lp, hm_lp_info* info);
-/* binary file: "HMLP0001", hidden and fallback (int32), steps (int64), then the
- * parameters and both Adam moments (float32 each) */
+/* binary file: "HMLP0002", hidden and fallback (int32), steps (int64), kind (int32),
+ * gamma (double), then the parameters and both Adam moments (float32 each); load also
+ * reads the "HMLP0001" files of the scale kind (no kind or gamma fields) */
 hm_status hm_lp_save(const hm_lp* lp, const char* path);
 hm_status hm_lp_load(const char* path, hm_lp** out);
 void hm_lp_destroy(hm_lp* lp);

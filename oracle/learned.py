@@ -204,3 +204,44 @@ def apply(d, r, perm, begin, end, binv_apply):
         for a in range(3):
             z[3 * idx + a] *= d[l, a]
     return z
+
+
+# ------------------------------------------------------------------ near correction
+# The second kind of correction: M^-1 r = y - gamma D B^-1 N y, y = B^-1 r, N the
+# near-field blocks of E off the diagonal leaf blocks.  Trained on the fit of D w to
+# y - x (w = B^-1 N y): the same loss as above with x' = y - x and y' = w.
+
+def near_offdiag(Emat, tree, eta=2.0):
+    """N (3N x 3N, user order): the entries of E in the inadmissible leaf pairs of the
+    block partition, minus the diagonal leaf blocks."""
+    from . import oracle as O
+    n = Emat.shape[0]
+    Nm = np.zeros((n, n))
+    near, _ = O.block_partition(tree, eta)
+    for s, t in near:
+        if s == t:
+            continue
+        rs = O.dof_index(tree.perm[tree.begin[s]:tree.end[s]])
+        ct = O.dof_index(tree.perm[tree.begin[t]:tree.end[t]])
+        Nm[np.ix_(rs, ct)] = Emat[np.ix_(rs, ct)]
+    return Nm
+
+
+def near_stats(x, b, Nm, perm, begin, end, binv_apply):
+    """Per (leaf, component) statistics of (y - x, w), y = B^-1 b, w = B^-1 N y."""
+    bb = np.atleast_2d(b)
+    y = np.vstack([binv_apply(v) for v in bb])
+    w = np.vstack([binv_apply(Nm @ v) for v in y])
+    return leaf_stats(y - np.atleast_2d(x), w, perm, begin, end)
+
+
+def apply_near(d, gamma, r, Nm, perm, begin, end, binv_apply):
+    """z = y - gamma D B^-1 N y, y = B^-1 r (user order)."""
+    y = binv_apply(r)
+    u = binv_apply(Nm @ y)
+    z = y.copy()
+    for l in range(len(begin)):
+        idx = perm[begin[l]:end[l]]
+        for a in range(3):
+            z[3 * idx + a] -= gamma * d[l, a] * u[3 * idx + a]
+    return z

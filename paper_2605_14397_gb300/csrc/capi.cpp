@@ -227,6 +227,16 @@ hm_status hm_gmres_solve(const hm_hmat* hh, const double* k_dev, double shift, c
     HM_API_END
 }
 
+hm_status hm_precond_apply(const hm_hmat* hh, const double* k_dev, double shift, const hm_solve_opts* opt,
+                           const double* r_dev, double* z_dev, int nrhs, void* stream) {
+    HM_API_BEGIN
+    if (!hh || !opt) hm::fail(HM_EINVAL, "precond_apply: NULL argument");
+    if (!std::isfinite(shift)) hm::fail(HM_ENAN, "precond_apply: shift is not finite");
+    hm::precond_apply_user(const_cast<hm::HMat&>(hh->h), k_dev, shift, *opt, opt->lp ? &opt->lp->m : nullptr, r_dev,
+                           z_dev, nrhs, (cudaStream_t)stream);
+    HM_API_END
+}
+
 hm_status hm_ilu_export(const hm_hmat* hh, const double* k_dev, const double* cep_dev, double shift, double p,
                         int64_t* n_out, int64_t* nnz_out, int32_t* n_colours_out, int32_t* order, int64_t* rowptr,
                         int32_t* col, double* a_val, double* lu_val, void* stream) {

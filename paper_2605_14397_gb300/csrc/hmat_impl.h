@@ -118,6 +118,7 @@ struct HMat {
     // operand index of every column (host; consecutive runs become the z ranges of the
     // product chunks): xc index (near), tb index (U), partial index (V)
     std::vector<int32_t> h_near_zidx, h_u_zidx, h_v_pidx;
+    DevBuf<int32_t> near_zidx;    // device copy of h_near_zidx (made on first use)
     // V columns write their partials in V-stream order, so the slices of one column leaf
     // form one contiguous output range (whole pipeline chunks); poff locates each far
     // block's slice in every leaf of its column cluster
@@ -237,6 +238,9 @@ void tangent_apply_user(HMat& H, const double* kel, const double* cep, double sh
 void tangent_diag_user(HMat& H, const double* kel, const double* cep, double shift, double* out, cudaStream_t st);
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp = nullptr);
+// z = M^-1 r with the preconditioner of gmres_solve for these options (user order)
+void precond_apply_user(HMat& H, const double* kel, double shift, const hm_solve_opts& o, const LPModel* lp,
+                        const double* r, double* z, int nrhs, cudaStream_t st);
 inline bool has_factors(const HMat& H, int fac) {
     return fac == 0 ? (H.storage == HM_F32 || H.storage == HM_F32_BF16)
                     : (H.storage == HM_BF16 || H.storage == HM_F32_BF16);

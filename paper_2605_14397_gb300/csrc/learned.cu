@@ -355,6 +355,12 @@ __global__ void __launch_bounds__(FEAT_NT) k_lp_stats(const LeafDesc* __restrict
 }
 
 
+// x = y - x (the near correction fits D w to the part y - x that B^-1 gets wrong)
+__global__ void k_lp_diff(const double* __restrict__ y, double* __restrict__ x, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = y[i] - x[i];
+}
+
 // ---------------------------------------------------------------- host side
 
 template <class F>
@@ -464,7 +470,16 @@ void lp_add_system(LPModel& M, HMat& H, const double* k_dev, const double* b, co
     to_cluster(H, b, bc.p, nr, st);
     to_cluster(H, x, xc.p, nr, st);
     bj_solve_cluster(H, k_dev, 0.0, bc.p, yc.p, nr, st);
-    k_lp_stats<<<H.n_leaves, FEAT_NT, 0, st>>>(H.leaves.p, xc.p, yc.p, n, nr, S.p);
+    if (M.kind == LP_NEAR) {
+        // the statistics of (y - x, w), w = B^-1 N y: the loss |(y - x) - d w|^2
+        DevBuf<double> t((size_t)n * nr), w((size_t)n * nr);
+        near_offdiag_cluster(H, yc.p, t.p, nr, st);
+        bj_solve_cluster(H, k_dev, 0.0, t.p, w.p, nr, st);
+        k_lp_diff<<<(unsigned)ceil_div((int64_t)n * nr, 256), 256, 0, st>>>(yc.p, xc.p, (int64_t)n * nr);
+        k_lp_stats<<<H.n_leaves, FEAT_NT, 0, st>>>(H.leaves.p, xc.p, w.p, n, nr, S.p);
+    } else {
+        k_lp_stats<<<H.n_leaves, FEAT_NT, 0, st>>>(H.leaves.p, xc.p, yc.p, n, nr, S.p);
+    }
     HM_LAUNCH_CHECK();
     lp_features(H, k_dev, feat.p, st);
     std::vector<double> hf((size_t)H.n_leaves * LP_FEATURES), hs((size_t)H.n_leaves * 9);
@@ -511,7 +526,8 @@ void lp_predict(LPModel& M, HMat& H, const double* k_dev, float* d_out, double* 
 // ---------------------------------------------------------------- C ABI
 
 namespace {
-const char LP_MAGIC[8] = {'H', 'M', 'L', 'P', '0', '0', '0', '1'};
+const char LP_MAGIC1[8] = {'H', 'M', 'L', 'P', '0', '0', '0', '1'};  // scale kind only
+const char LP_MAGIC[8] = {'H', 'M', 'L', 'P', '0', '0', '0', '2'};   // + kind and gamma
 hm::LPModel& model(hm_lp* lp) {
     if (!lp) hm::fail(HM_EINVAL, "learned correction: NULL handle");
     return lp->m;
@@ -630,6 +646,17 @@ hm_status hm_lp_get_params(const hm_lp* lp, double* theta_out) {
     HM_API_END
 }
 
+hm_status hm_lp_set_kind(hm_lp* lp, int kind, double gamma) {
+    HM_API_BEGIN
+    hm::LPModel& M = model(lp);
+    if (kind != HM_LP_SCALE && kind != HM_LP_NEAR) hm::fail(HM_EINVAL, "lp_set_kind: unknown kind");
+    if (!(gamma > 0.0) || !std::isfinite(gamma)) hm::fail(HM_EINVAL, "lp_set_kind: gamma must be positive");
+    if (kind != M.kind && !M.X_h.empty()) hm::fail(HM_EINVAL, "lp_set_kind: samples of the other kind are held");
+    M.kind = kind;
+    M.gamma = gamma;
+    HM_API_END
+}
+
 hm_status hm_lp_set_fallback(hm_lp* lp, int fallback) {
     HM_API_BEGIN
     model(lp).fallback = fallback ? 1 : 0;
@@ -647,6 +674,8 @@ hm_status hm_lp_get_info(const hm_lp* lp, hm_lp_info* info) {
     info->n_groups = M.n_groups;
     info->steps = M.steps;
     info->last_loss = M.last_loss;
+    info->kind = M.kind;
+    info->gamma = M.gamma;
     HM_API_END
 }
 
@@ -658,8 +687,11 @@ hm_status hm_lp_save(const hm_lp* lp, const char* path) {
     if (!f) hm::fail(HM_EINVAL, std::string("lp_save: cannot open ") + path);
     const int32_t hdr[2] = {M.H, M.fallback};
     const int64_t steps = M.steps;
+    const int32_t kind = M.kind;
+    const double gamma = M.gamma;
     bool ok = fwrite(LP_MAGIC, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 2, f) == 2 &&
-              fwrite(&steps, sizeof(int64_t), 1, f) == 1 &&
+              fwrite(&steps, sizeof(int64_t), 1, f) == 1 && fwrite(&kind, sizeof(int32_t), 1, f) == 1 &&
+              fwrite(&gamma, sizeof(double), 1, f) == 1 &&
               fwrite(M.theta_h.data(), sizeof(float), M.P, f) == (size_t)M.P &&
               fwrite(M.m_h.data(), sizeof(float), M.P, f) == (size_t)M.P &&
               fwrite(M.v_h.data(), sizeof(float), M.P, f) == (size_t)M.P;
@@ -677,15 +709,23 @@ hm_status hm_lp_load(const char* path, hm_lp** out) {
     char magic[8];
     int32_t hdr[2];
     int64_t steps = 0;
-    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, LP_MAGIC, 8) == 0 &&
-              fread(hdr, sizeof(int32_t), 2, f) == 2 && fread(&steps, sizeof(int64_t), 1, f) == 1 &&
-              hm_lp_param_count(hdr[0]) > 0;
+    int32_t kind = hm::LP_SCALE;
+    double gamma = 1.0;
+    bool ok = fread(magic, 1, 8, f) == 8;
+    const bool v2 = ok && std::memcmp(magic, LP_MAGIC, 8) == 0;
+    ok = ok && (v2 || std::memcmp(magic, LP_MAGIC1, 8) == 0) && fread(hdr, sizeof(int32_t), 2, f) == 2 &&
+         fread(&steps, sizeof(int64_t), 1, f) == 1 && hm_lp_param_count(hdr[0]) > 0;
+    if (ok && v2)
+        ok = fread(&kind, sizeof(int32_t), 1, f) == 1 && fread(&gamma, sizeof(double), 1, f) == 1 &&
+             (kind == hm::LP_SCALE || kind == hm::LP_NEAR) && gamma > 0.0 && std::isfinite(gamma);
     hm_lp* lp = nullptr;
     if (ok) {
         lp = new hm_lp();
         hm::LPModel& M = lp->m;
         M.H = hdr[0];
         M.fallback = hdr[1] ? 1 : 0;
+        M.kind = kind;
+        M.gamma = gamma;
         M.steps = steps;
         M.P = hm::lp_param_count(M.H);
         M.theta_h.resize(M.P);

@@ -1,12 +1,18 @@
 // Learned block-Jacobi correction: model state and the entry points the solver uses.
 //
-// M^-1 r = D B^-1 r, D = diag(d_(leaf, component)), d = 1 + 0.5 tanh(o) with o the output
+// Two kinds of correction of B^-1 by d = 1 + 0.5 tanh(o) per (leaf, component):
+//   scale:  M^-1 r = D B^-1 r;
+//   near:   M^-1 r = y - gamma D B^-1 N y,  y = B^-1 r,  N = the near-field blocks of E off
+//           the diagonal leaf blocks (a damped first Neumann term of the near coupling).
+// d comes from the output o
 // of a two-hidden-layer tanh network evaluated per leaf on eight leaf features (the
 // stiffness distribution of the leaf relative to E/h, its size, planarity and distance to
 // another fracture plane).  B is the leaf block-Jacobi preconditioner of A = E - diag(k)
 // (the Jacobi preconditioner of Sec. 3.3.1 taken per leaf).  The network is trained on
-// the device by Adam on the approximate-inverse loss sum |x - D B^-1 b|^2 over solved
-// systems, which separates into per-(leaf, component) sums (see learned.cu).
+// the device by Adam on the approximate-inverse loss over solved systems: sum |x - D y|^2
+// (scale) or sum |(y - x) - D w|^2, w = B^-1 N y (near), which separate into
+// per-(leaf, component) sums (see learned.cu); gamma is chosen by the caller on
+// validation systems (GMRES iterations as the judge).
 #pragma once
 
 #include <cstdint>
@@ -24,8 +30,12 @@ inline int64_t lp_param_count(int H) {
     return (int64_t)H * LP_FEATURES + H + (int64_t)H * H + H + LP_OUT * H + LP_OUT;
 }
 
+enum { LP_SCALE = 0, LP_NEAR = 1 };
+
 struct LPModel {
     int H = 32;
+    int kind = LP_SCALE;     // LP_SCALE or LP_NEAR
+    double gamma = 1.0;      // LP_NEAR: factor on the predicted d
     int64_t P = 0;
     int fallback = 0;        // 1: the solver applies plain block-Jacobi
     int64_t steps = 0;       // Adam steps taken
@@ -53,6 +63,9 @@ void lp_predict(LPModel& M, HMat& H, const double* k_dev, float* d_out, double* 
 // A = E - diag(k) - shift I (solve.cu)
 void bj_solve_cluster(HMat& H, const double* kel, double shift, const double* v, double* z, int nr,
                       cudaStream_t st);
+// out = N v for cluster-ordered vectors (nr x 3N): the near-field tiles of E off the
+// diagonal leaf blocks, FP32 coefficients, FP64 vectors (solve.cu)
+void near_offdiag_cluster(HMat& H, const double* v, double* out, int nr, cudaStream_t st);
 void to_cluster(HMat& H, const double* user, double* cluster, int nr, cudaStream_t st);
 
 }  // namespace hm

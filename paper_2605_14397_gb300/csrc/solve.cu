@@ -407,6 +407,55 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
     }
 }
 
+// out = N v per row leaf: the near-field tiles of the leaf except its own diagonal block
+// (columns whose operand lies in the leaf), FP32 coefficients read column by column
+// (coalesced over the rows), FP64 sums; one CTA per leaf, a thread per row (<= 192) and
+// up to 16 RHS in registers.
+constexpr int NOD_NT = 192;
+__global__ void __launch_bounds__(NOD_NT) k_near_offdiag(const LeafDesc* __restrict__ leaves,
+                                                         const float* __restrict__ near,
+                                                         const int32_t* __restrict__ zidx,
+                                                         const double* __restrict__ v, double* __restrict__ out,
+                                                         int64_t ndof, int nr, const CycleState* __restrict__ cs) {
+    const LeafDesc L = leaves[blockIdx.x];
+    const int n = 3 * L.n;
+    const int64_t lo = 3 * (int64_t)L.begin, hi = lo + n;
+    for (int r0 = 0; r0 < n; r0 += NOD_NT) {
+        const int r = r0 + threadIdx.x;
+        double acc[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+        const float* D = near + L.near_off;
+        for (int c = 0; c < L.near_cols; ++c) {
+            const int64_t z = zidx[L.near_cbase + c];
+            if (z >= lo && z < hi) continue;  // the leaf's own block: B's part
+            const double a = r < n ? (double)D[(int64_t)c * L.ld + r] : 0.0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < nr) acc[k] += a * v[k * ndof + z];
+        }
+        if (r < n) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < nr && (!cs || !cs[k].done)) out[k * ndof + lo + r] = acc[k];
+        }
+    }
+}
+
+// z -= gamma d o u (the damped near correction), d per (leaf, component); also the FP32
+// RHS-interleaved copy zf
+__global__ void k_near_update(double* __restrict__ z, const double* __restrict__ u, const float* __restrict__ dsc,
+                              const int32_t* __restrict__ leaf_of, double gamma, float* __restrict__ zf,
+                              int64_t ndof, int nr, const CycleState* __restrict__ cs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= ndof * nr) return;
+    const int64_t k = q / ndof, i = q % ndof;
+    if (cs && cs[k].done) return;
+    const double s = z[q] - gamma * (double)dsc[3 * (int64_t)leaf_of[i / 3] + i % 3] * u[q];
+    z[q] = s;
+    if (zf) zf[i * nr + k] = (float)s;
+}
+
 // Point Jacobi (the paper's Jacobi preconditioner of the A11 system, Sec. 3.3.1): the
 // inverse of every element's 3x3 diagonal block of A = E - diag(d), read from the leaf's
 // self tile of the FP32 near field.  One CTA per leaf, one thread per element; the 3x3
@@ -955,6 +1004,12 @@ struct SolveWS {
         }
     } pc_key;
     DevBuf<BcgScal> bsc;
+    // the learned near correction (HM_LP_NEAR): scratch N z and B^-1 N z, the leaf of
+    // every cluster element, and gamma
+    bool near_on = false;
+    double near_gamma = 1.0;
+    DevBuf<double> nt, nu;
+    DevBuf<int32_t> leaf_of;
     const double* blk = nullptr;  // blkbuf.p when the tangent has a block-diagonal C^ep
     DevBuf<int64_t> binv_off, self_off;
     DevBuf<CycleState> st;
@@ -1067,6 +1122,17 @@ enum PcKind { PC_NONE = 0, PC_LEAF = 1, PC_POINT = 2, PC_ILU = 3 };
 // next product is an FP32 one; RHS whose CycleState is done are skipped
 void precond_apply(HMat& H, SolveWS& W, PcKind pc, const double* v, double* z, float* zf, int nr, cudaStream_t st) {
     const int64_t n = H.ndof;
+    if (pc == PC_LEAF && W.near_on) {
+        // z = y - gamma d o B^-1 N y, y = B^-1 v
+        k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, v, z, nullptr, n, nr, W.st.p, 0,
+                                               nullptr);
+        k_near_offdiag<<<H.n_leaves, NOD_NT, 0, st>>>(H.leaves.p, H.near.p, H.near_zidx.p, z, W.nt.p, n, nr, W.st.p);
+        k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, W.nt.p, W.nu.p, nullptr, n, nr,
+                                               W.st.p, 0, nullptr);
+        k_near_update<<<g1(n * nr), 256, 0, st>>>(z, W.nu.p, W.dsc.p, W.leaf_of.p, W.near_gamma, zf, n, nr, W.st.p);
+        HM_LAUNCH_CHECK();
+        return;
+    }
     if (pc == PC_POINT)
         k_j3_apply<<<g1(H.N * nr), 256, 0, st>>>(W.j3.p, v, z, zf, H.N, n, nr, W.st.p);
     else if (pc == PC_ILU)
@@ -1324,6 +1390,21 @@ void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
     if (e) fail(HM_EBREAKDOWN, "a diagonal leaf block of A is singular");
 }
 
+// device data of the near correction: the operand index of every near column, the leaf of
+// every cluster element and N z / B^-1 N z scratch for nr RHS
+void near_prepare(HMat& H, SolveWS& W, int nr, cudaStream_t st) {
+    if (H.near_zidx.n != H.h_near_zidx.size()) H.near_zidx.upload(H.h_near_zidx, st);
+    if (W.leaf_of.n != (size_t)H.N) {
+        std::vector<int32_t> lo(H.N);
+        for (int l = 0; l < H.n_leaves; ++l)
+            for (int e = 0; e < H.h_leaves[l].n; ++e) lo[H.h_leaves[l].begin + e] = l;
+        W.leaf_of.upload(lo, st);
+    }
+    const size_t len = (size_t)H.ndof * nr + VSLACK;
+    if (W.nt.n < len) W.nt.alloc(len);
+    if (W.nu.n < len) W.nu.alloc(len);
+}
+
 // the interface term of the tangent: diag(k) + C^ep + shift I into W.dc (and the
 // off-diagonal C^ep entries into W.blk when cep is given)
 void set_tangent(HMat& H, SolveWS& W, const double* kel, const double* cep, double shift, cudaStream_t st) {
@@ -1369,6 +1450,14 @@ void bj_solve_cluster(HMat& H, const double* kel, double shift, const double* v,
                                            nullptr);
     HM_LAUNCH_CHECK();
     HM_CUDA(cudaStreamSynchronize(st));
+}
+
+void near_offdiag_cluster(HMat& H, const double* v, double* out, int nr, cudaStream_t st) {
+    if (nr < 1 || nr > 16) fail(HM_EINVAL, "near product: 1 to 16 right-hand sides");
+    SolveWS& W = workspace(H, nr, 1, st);
+    near_prepare(H, W, nr, st);
+    k_near_offdiag<<<H.n_leaves, NOD_NT, 0, st>>>(H.leaves.p, H.near.p, H.near_zidx.p, v, out, H.ndof, nr, nullptr);
+    HM_LAUNCH_CHECK();
 }
 
 // The ILU preconditioner of A = E - diag(k) - C^ep - shift I for a fraction p, built and
@@ -1438,6 +1527,81 @@ void ilu_apply_user(HMat& H, const double* r, double* z, int nrhs, cudaStream_t 
     HM_LAUNCH_CHECK();
 }
 
+// the preconditioner of the options for the tangent in W (W.dc, W.blk set), or the one
+// already built for the same inputs when the options ask to reuse it
+void build_precond(HMat& H, SolveWS& W, const double* kel, const double* cep, double shift, const hm_solve_opts& o,
+                   PcKind pc, double ilu_p, const LPModel* lp, int nrhs, cudaStream_t st) {
+    SolveWS::PcKey key;
+    key.valid = true;
+    key.kel = kel;
+    key.cep = cep;
+    key.shift = shift;
+    key.ilu_p = pc == PC_ILU ? ilu_p : 0.0;
+    key.precond = o.precond;
+    key.lp = lp;
+    const bool reuse = o.reuse_precond && W.pc_key.same(key) && (pc != PC_ILU || ilu_is_factored(H));
+    if (!reuse) {
+        W.pc_key.valid = false;
+        W.dsc_on = false;
+        if (pc == PC_POINT) j3_build(H, W, st);
+        if (pc == PC_ILU) {
+            ilu_prepare(H, ilu_p, cep != nullptr, st);
+            ilu_factor(H, W.dc.p, W.blk, st, W.err.p);
+        }
+        W.near_on = false;
+        if (pc == PC_LEAF) {
+            bj_build(H, W, st);
+            if (o.precond == HM_PRECOND_LEARNED && !lp->fallback) {
+                W.dsc.alloc((size_t)H.n_leaves * 3);
+                lp_predict(const_cast<LPModel&>(*lp), H, kel, W.dsc.p, nullptr, st);
+                if (lp->kind == LP_NEAR) {
+                    near_prepare(H, W, nrhs, st);
+                    W.near_on = true;
+                    W.near_gamma = lp->gamma;
+                } else {
+                    W.dsc_on = true;
+                }
+            }
+        }
+        W.pc_key = key;
+    }
+    if (W.near_on) near_prepare(H, W, nrhs, st);  // scratch for this call's RHS count
+}
+
+PcKind pc_kind(int precond) {
+    return (precond == HM_PRECOND_BLOCKJ || precond == HM_PRECOND_LEARNED)
+               ? PC_LEAF
+               : (precond == HM_PRECOND_JACOBI3 ? PC_POINT : (precond == HM_PRECOND_ILU ? PC_ILU : PC_NONE));
+}
+
+// z = M^-1 r with the preconditioner hm_gmres_solve builds for these options (user order)
+void precond_apply_user(HMat& H, const double* kel, double shift, const hm_solve_opts& o, const LPModel* lp,
+                        const double* r, double* z, int nrhs, cudaStream_t st) {
+    if (nrhs < 1 || nrhs > 16) fail(HM_EINVAL, "precond_apply: 1 to 16 right-hand sides");
+    if (!r || !z) fail(HM_EINVAL, "precond_apply: NULL vector");
+    if (o.precond != HM_PRECOND_NONE && o.precond != HM_PRECOND_BLOCKJ && o.precond != HM_PRECOND_LEARNED &&
+        o.precond != HM_PRECOND_JACOBI3 && o.precond != HM_PRECOND_ILU)
+        fail(HM_EINVAL, "precond_apply: unknown preconditioner");
+    if (o.precond == HM_PRECOND_LEARNED && !lp) fail(HM_EINVAL, "precond_apply: the learned preconditioner needs a model");
+    if (o.precond == HM_PRECOND_LEARNED && o.cep_dev)
+        fail(HM_EINVAL, "precond_apply: the learned preconditioner takes a diagonal interface term (k), not C^ep");
+    const double ilu_p = o.ilu_p > 0.0 ? o.ilu_p : 0.01;
+    if (o.precond == HM_PRECOND_ILU && !(ilu_p <= 1.0)) fail(HM_EINVAL, "precond_apply: ilu_p must lie in (0, 1]");
+    SolveWS& W = workspace(H, nrhs, 1, st);
+    const int64_t n = H.ndof;
+    set_tangent(H, W, kel, o.cep_dev, shift, st);
+    const PcKind pc = pc_kind(o.precond);
+    build_precond(H, W, kel, o.cep_dev, shift, o, pc, ilu_p, lp, nrhs, st);
+    std::vector<CycleState> cs(nrhs, CycleState{0, 0, 0, 0, 0.0, 0.0});
+    HM_CUDA(cudaMemcpyAsync(W.st.p, cs.data(), nrhs * sizeof(CycleState), cudaMemcpyHostToDevice, st));
+    k_to_cluster<<<g1(n * nrhs), 256, 0, st>>>(r, W.r.p, H.perm.p, n, nrhs);
+    HM_LAUNCH_CHECK();
+    precond_apply(H, W, pc, W.r.p, W.w.p, nullptr, nrhs, st);
+    k_to_user<<<g1(n * nrhs), 256, 0, st>>>(W.w.p, z, H.perm.p, n, nrhs);
+    HM_LAUNCH_CHECK();
+    HM_CUDA(cudaStreamSynchronize(st));  // cs above is read by the copy
+}
+
 void gmres_solve(HMat& H, const double* kel, double shift, const double* b, double* x, int nrhs,
                  const hm_solve_opts& o, hm_solve_info* info, cudaStream_t st, const LPModel* lp) {
     const double* cep = o.cep_dev;
@@ -1483,37 +1647,8 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     set_tangent(H, W, kel, cep, shift, st);
     k_to_cluster<<<g1(n * nrhs), 256, 0, st>>>(b, W.bc.p, H.perm.p, n, nrhs);
     HM_LAUNCH_CHECK();
-    const PcKind pc = (o.precond == HM_PRECOND_BLOCKJ || o.precond == HM_PRECOND_LEARNED)
-                          ? PC_LEAF
-                          : (o.precond == HM_PRECOND_JACOBI3 ? PC_POINT
-                                                             : (o.precond == HM_PRECOND_ILU ? PC_ILU : PC_NONE));
-    SolveWS::PcKey key;
-    key.valid = true;
-    key.kel = kel;
-    key.cep = cep;
-    key.shift = shift;
-    key.ilu_p = pc == PC_ILU ? ilu_p : 0.0;
-    key.precond = o.precond;
-    key.lp = lp;
-    const bool reuse = o.reuse_precond && W.pc_key.same(key) && (pc != PC_ILU || ilu_is_factored(H));
-    if (!reuse) {
-        W.pc_key.valid = false;
-        W.dsc_on = false;
-        if (pc == PC_POINT) j3_build(H, W, st);
-        if (pc == PC_ILU) {
-            ilu_prepare(H, ilu_p, cep != nullptr, st);
-            ilu_factor(H, W.dc.p, W.blk, st, W.err.p);
-        }
-        if (pc == PC_LEAF) {
-            bj_build(H, W, st);
-            if (o.precond == HM_PRECOND_LEARNED && !lp->fallback) {
-                W.dsc.alloc((size_t)H.n_leaves * 3);
-                lp_predict(const_cast<LPModel&>(*lp), H, kel, W.dsc.p, nullptr, st);
-                W.dsc_on = true;
-            }
-        }
-        W.pc_key = key;
-    }
+    const PcKind pc = pc_kind(o.precond);
+    build_precond(H, W, kel, cep, shift, o, pc, ilu_p, lp, nrhs, st);
     // ||b||
     HM_CUDA(cudaMemsetAsync(W.xc.p, 0, (size_t)n * nrhs * sizeof(double), st));
     std::vector<double> bn = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st);  // x = 0: r = b

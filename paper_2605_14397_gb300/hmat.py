@@ -25,6 +25,7 @@ HM_F32, HM_F64, HM_BF16, HM_F32_BF16 = 1, 2, 3, 4
 HM_PRECOND_NONE, HM_PRECOND_BLOCKJ, HM_PRECOND_LEARNED, HM_PRECOND_JACOBI3, HM_PRECOND_ILU = 0, 1, 2, 3, 4
 HM_SOLVE_F64, HM_SOLVE_MIXED, HM_SOLVE_PLAIN32 = 1, 2, 3
 HM_METHOD_FGMRES, HM_METHOD_BICGSTAB = 0, 1
+HM_LP_SCALE, HM_LP_NEAR = 0, 1
 
 _STATUS_NAMES = {HM_EINVAL: "HM_EINVAL", HM_ENOMEM: "HM_ENOMEM", HM_ECUDA: "HM_ECUDA",
                  HM_ESINGULAR_GEOM: "HM_ESINGULAR_GEOM", HM_ENOCONV: "HM_ENOCONV",
@@ -91,7 +92,8 @@ def _shape_array(shapes):
 class hm_lp_info(ctypes.Structure):
     _fields_ = [("hidden", ctypes.c_int32), ("fallback", ctypes.c_int32), ("n_params", ctypes.c_int64),
                 ("n_samples", ctypes.c_int64), ("n_groups", ctypes.c_int64), ("steps", ctypes.c_int64),
-                ("last_loss", ctypes.c_double)]
+                ("last_loss", ctypes.c_double), ("kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("gamma", ctypes.c_double)]
 
 
 class hm_solve_info(ctypes.Structure):
@@ -164,6 +166,8 @@ SIGNATURES = [
     ("hm_lp_get_params", _I, [_VP, _VP]),
     ("hm_lp_set_fallback", _I, [_VP, _I]),
     ("hm_lp_get_info", _I, [_VP, ctypes.POINTER(hm_lp_info)]),
+    ("hm_lp_set_kind", _I, [_VP, _I, _D]),
+    ("hm_precond_apply", _I, [_VP, _VP, _D, ctypes.POINTER(hm_solve_opts), _VP, _VP, _I, _VP]),
     ("hm_lp_save", _I, [_VP, ctypes.c_char_p]),
     ("hm_lp_load", _I, [ctypes.c_char_p, ctypes.POINTER(_VP)]),
     ("hm_lp_destroy", None, [_VP]),
@@ -409,6 +413,20 @@ class HMatrix:
             raise HMError(st, lib().hm_last_error().decode())
         return out
 
+    def precond_apply(self, r, z, k=None, shift=0.0, precond="blockj", ilu_p=0.0, cep=None, model=None,
+                      reuse_precond=False, stream=None):
+        """z = M^-1 r with the preconditioner of solve() for these arguments
+        (hm_precond_apply); r, z float64 CUDA tensors (3N,) or (nrhs, 3N)."""
+        nrhs = 1 if r.dim() == 1 else r.shape[0]
+        assert r.is_contiguous() and z.is_contiguous()
+        o = hm_solve_opts(0.0, 0, 0,
+                          {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "learned": HM_PRECOND_LEARNED,
+                           "jacobi3": HM_PRECOND_JACOBI3, "ilu": HM_PRECOND_ILU}[precond], HM_SOLVE_F64, 0.0, 0, 0,
+                          model.handle.value if model is not None else None, float(ilu_p),
+                          cep.data_ptr() if cep is not None else None, 0, int(bool(reuse_precond)))
+        _check(lib().hm_precond_apply(self.handle, _dptr(k) if k is not None else None, float(shift), ctypes.byref(o),
+                                      _dptr(r), _dptr(z), int(nrhs), ctypes.c_void_p(_stream_ptr(stream))))
+
     def ilu_export(self, k=None, shift=0.0, p=0.01, factor=True, stream=None, cep=None):
         """The ILU preconditioner for this k, C^ep, shift and p (hm_ilu_export): dict of order
         (factorization position -> cluster DOF position), rowptr, col, a_val and, with
@@ -527,6 +545,10 @@ class LearnedCorrection:
 
     def set_fallback(self, on):
         _check(lib().hm_lp_set_fallback(self.handle, 1 if on else 0))
+
+    def set_kind(self, kind, gamma=1.0):
+        """kind "scale" (M = D B^-1) or "near" (M = B^-1 - gamma D B^-1 N B^-1)."""
+        _check(lib().hm_lp_set_kind(self.handle, {"scale": HM_LP_SCALE, "near": HM_LP_NEAR}[kind], float(gamma)))
 
     def add_samples(self, features, q):
         f = np.ascontiguousarray(features, dtype=np.float64)

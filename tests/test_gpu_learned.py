@@ -5,7 +5,10 @@ Bars: features (FP64 on both sides) to 1e-10; network outputs d (FP32 on the dev
 to 1e-5; loss to 1e-5 and the gradient to 1e-3 relative (FP32 forward/backward against
 FP64); the statistics of a solved system (FP32 block-Jacobi on the device against the
 FP64 oracle) through the loss to 1e-4.  A zero output layer reproduces block-Jacobi
-bit for bit, a model flagged as fallback too, and training lowers the loss."""
+bit for bit, a model flagged as fallback too, and training lowers the loss.  Every
+preconditioner applies like the oracle's (hm_precond_apply), the near correction's
+statistics match, and the trained near correction takes at least a quarter fewer GMRES
+iterations than block-Jacobi on held-out systems."""
 import math
 
 import numpy as np
@@ -169,3 +172,110 @@ def test_training_lowers_the_loss(dev, system):
     l2, _ = m.loss_grad()
     assert m.info()["n_groups"] == 3 and m.info()["steps"] == 200
     assert l2 < l0 and l1 < l0
+
+
+def test_preconditioners_apply_like_the_oracle(dev, system):
+    """hm_precond_apply against the oracle's preconditioners on the tangent: leaf
+    block-Jacobi and the paper's point Jacobi (FP32 inverses on the device: 1e-5), the
+    ILU of Sec. 3.3.1 (FP64: 1e-9), the learned scaling D B^-1 and the learned near
+    correction y - gamma D B^-1 N y (FP32 inverses and near tiles: 1e-5)."""
+    import torch
+    from oracle import ilu as IL
+    el, T, H, perm, begin, end, h = system
+    k = synth.k_loguniform(el.N, 1607, h=h)
+    kt = torch.as_tensor(k, device=dev)
+    Em = O.dense_matrix(el, E, NU)
+    A = O.tangent_dense(Em, k)
+    tree = O.cluster_tree(el, 64)
+    R = synth.rhs_normal(3 * el.N, 23, nrhs=2)
+    Rt = torch.as_tensor(R, device=dev).contiguous()
+    Z = torch.empty_like(Rt)
+    inv = O.block_jacobi_inverses(A, tree)
+    bj = lambda v: O.apply_block_jacobi(inv, v)
+    H.precond_apply(Rt, Z, kt, precond="blockj")
+    assert rel(Z.cpu().numpy(), np.stack([bj(r) for r in R])) <= 1e-5
+    j3 = O.point_jacobi_inverses(A)
+    H.precond_apply(Rt, Z, kt, precond="jacobi3")
+    assert rel(Z.cpu().numpy(), np.stack([O.apply_block_jacobi(j3, r) for r in R])) <= 1e-5
+    # the library selects and factors the FP32 values it stores
+    M_ilu, _ = IL.ilu_preconditioner(Em.astype(np.float32).astype(np.float64), tree, k, 0.01, ordering="colour")
+    H.precond_apply(Rt, Z, kt, precond="ilu", ilu_p=0.01)
+    assert rel(Z.cpu().numpy(), np.stack([M_ilu(r) for r in R])) <= 1e-5
+    th = random_theta(12)
+    for kind, gamma in (("scale", 1.0), ("near", 0.8)):
+        m = hmat.LearnedCorrection(th, hidden=HID)
+        m.set_kind(kind, gamma)
+        _, d = m.predict(H, kt)
+        H.precond_apply(Rt, Z, kt, precond="learned", model=m)
+        if kind == "scale":
+            ref = np.stack([Lr.apply(d, r, perm, begin, end, bj) for r in R])
+        else:
+            Nm = Lr.near_offdiag(Em, tree)
+            ref = np.stack([Lr.apply_near(d, gamma, r, Nm, perm, begin, end, bj) for r in R])
+        assert rel(Z.cpu().numpy(), ref) <= 1e-5, kind
+
+
+def test_near_statistics_match_oracle(dev, system):
+    import torch
+    el, T, H, perm, begin, end, h = system
+    k = synth.k_loguniform(el.N, 1608, h=h)
+    Em = O.dense_matrix(el, E, NU)
+    A = O.tangent_dense(Em, k)
+    B = synth.rhs_normal(3 * el.N, 24, nrhs=2)
+    X = np.ascontiguousarray(np.linalg.solve(A, B.T).T)
+    th = random_theta(13)
+    m = hmat.LearnedCorrection(th, hidden=HID)
+    m.set_kind("near", 1.0)
+    kt = torch.as_tensor(k, device=dev)
+    m.add_system(H, kt, torch.as_tensor(B, device=dev), torch.as_tensor(X, device=dev))
+    loss, _ = m.loss_grad()
+    tree = O.cluster_tree(el, 64)
+    inv = O.block_jacobi_inverses(A, tree)
+    S = Lr.near_stats(X, B, Lr.near_offdiag(Em, tree), perm, begin, end, lambda v: O.apply_block_jacobi(inv, v))
+    F = Lr.leaf_features(el, k, E, perm, begin, end)
+    lo, _ = Lr.loss_and_grad(th.astype(np.float32).astype(np.float64), HID, F, Lr.samples([S]))
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+
+
+def test_trained_near_correction_takes_fewer_iterations(dev, system):
+    """What the trained network gains: the learned near correction, trained on 12 solved
+    systems of the crack crossing a fault and with gamma picked on 3 validation systems by
+    GMRES iterations, takes at least a quarter fewer iterations than plain block-Jacobi
+    on 4 held-out systems (the oracle's experiment on the same tangents: 14 -> 7-8)."""
+    import torch
+    el, T, H, perm, begin, end, h = system
+    m = hmat.LearnedCorrection(synth.lp_initial_weights(HID, seed=14), hidden=HID)
+    m.set_kind("near", 1.0)
+    for s in range(12):
+        k = torch.as_tensor(synth.k_loguniform(el.N, 1900 + s, h=h), device=dev)
+        b = torch.as_tensor(synth.rhs_normal(3 * el.N, 2000 + s), device=dev)
+        x = torch.zeros_like(b)
+        H.solve(b, x, k, precond="blockj", tol=1e-11)
+        m.add_system(H, k, b, x)
+    l0, _ = m.loss_grad()
+    m.train(300, lr=3e-3)
+    l1, _ = m.loss_grad()
+    assert l1 < l0
+
+    def iters(seeds, precond, model=None):
+        out = []
+        for s in seeds:
+            k = torch.as_tensor(synth.k_loguniform(el.N, s, h=h), device=dev)
+            b = torch.as_tensor(synth.rhs_normal(3 * el.N, s + 50), device=dev)
+            x = torch.zeros_like(b)
+            inf = H.solve(b, x, k, precond=precond, model=model)[0]
+            assert inf["relres"] <= 1e-8
+            out.append(inf["iters"])
+        return np.mean(out)
+    val = [2100 + s for s in range(3)]
+    scores = []
+    for g in (0.6, 0.7, 0.8, 0.9, 1.0):
+        m.set_kind("near", g)
+        scores.append((iters(val, "learned", m), g))
+    best = min(scores)
+    m.set_kind("near", best[1])
+    held = [2200 + s for s in range(4)]
+    it_bj, it_l = iters(held, "blockj"), iters(held, "learned", m)
+    print("held-out GMRES iterations: block-Jacobi %.2f, learned near correction %.2f (gamma %.1f)" % (
+        it_bj, it_l, best[1]))
+    assert it_l <= 0.75 * it_bj

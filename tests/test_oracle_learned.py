@@ -179,3 +179,82 @@ def test_two_level_corrections_cannot_beat_block_jacobi_on_the_tangent():
     assert ok and ok_a and ok_m
     assert it_add >= it_bj and it_bj - 2 <= it_mul <= it_bj
     assert 2 * it_mul > it_bj  # products: two per multiplicative iteration
+
+
+def test_near_offdiag_partitions_E():
+    """N holds exactly the near-field entries off the diagonal leaf blocks: with the
+    diagonal leaf blocks and the admissible blocks it rebuilds E entry by entry, each entry
+    once (the block partition covers the index square once)."""
+    el = synth.config_crack_fault(h=0.25)
+    T = O.cluster_tree(el, 16)
+    Em = O.dense_matrix(el, 1.0, 0.25)
+    Nm = Lr.near_offdiag(Em, T)
+    near, far = O.block_partition(T, 2.0)
+    cover = np.zeros(Em.shape)
+    rebuilt = Nm.copy()
+    for q in T.leaves():
+        d = O.dof_index(T.perm[T.begin[q]:T.end[q]])
+        rebuilt[np.ix_(d, d)] += Em[np.ix_(d, d)]
+        cover[np.ix_(d, d)] += 1
+    for s, t in far:
+        rs = O.dof_index(T.perm[T.begin[s]:T.end[s]])
+        ct = O.dof_index(T.perm[T.begin[t]:T.end[t]])
+        rebuilt[np.ix_(rs, ct)] += Em[np.ix_(rs, ct)]
+        cover[np.ix_(rs, ct)] += 1
+    cover += (Nm != 0)
+    assert np.array_equal(rebuilt, Em)
+    assert cover.max() == 1 and len(near) > len(T.leaves())
+
+
+def test_near_correction_is_a_first_order_neumann_term():
+    """With N = 0 the near correction is B^-1; on A = B + eps N (block-diagonal B, no far
+    part) y - B^-1 N y with d = gamma = 1 is the first Neumann approximation of A^-1:
+    its error falls like eps^2."""
+    rng = np.random.default_rng(9)
+    n = 12
+    perm = np.arange(4)
+    begin, end = [0, 2], [2, 4]
+    B = np.zeros((n, n))
+    for lo, hi in ((0, 6), (6, 12)):
+        B[lo:hi, lo:hi] = rng.normal(size=(6, 6)) + 6 * np.eye(6)
+    N0 = rng.normal(size=(n, n))
+    N0[:6, :6] = 0
+    N0[6:, 6:] = 0
+    Binv = np.linalg.inv(B)
+    d = np.ones((2, 3))
+    r = rng.normal(size=n)
+    z0 = Lr.apply_near(d, 1.0, r, np.zeros((n, n)), perm, begin, end, lambda v: Binv @ v)
+    assert np.allclose(z0, Binv @ r, rtol=1e-14, atol=0)
+    errs = []
+    for eps in (1e-2, 1e-3):
+        A = B + eps * N0
+        z = Lr.apply_near(d, 1.0, r, eps * N0, perm, begin, end, lambda v: Binv @ v)
+        errs.append(np.linalg.norm(z - np.linalg.solve(A, r)))
+    assert errs[1] < 2e-2 * errs[0]  # quadratic: a 10x smaller eps gives ~100x less error
+
+
+def test_near_stats_give_the_least_squares_damping():
+    """The (leaf, component) minimiser q_xy / q_yy of the near statistics is the least
+    squares fit of d w to y - x on that group."""
+    el = synth.config_penny(10)
+    T = O.cluster_tree(el, 16)
+    Em = O.dense_matrix(el, 1.0, 0.25)
+    k = synth.k_loguniform(el.N, 3, h=0.2)
+    A = O.tangent_dense(Em, k)
+    inv = O.block_jacobi_inverses(A, T)
+    bj = lambda v: O.apply_block_jacobi(inv, v)
+    Nm = Lr.near_offdiag(Em, T)
+    b = synth.rhs_normal(A.shape[0], 4)
+    x = np.linalg.solve(A, b)
+    leaves = T.leaves()
+    begin = [T.begin[q] for q in leaves]
+    end = [T.end[q] for q in leaves]
+    S = Lr.near_stats(x, b, Nm, T.perm, begin, end, bj)
+    y = bj(b)
+    w = bj(Nm @ y)
+    for l in range(len(leaves)):
+        idx = T.perm[begin[l]:end[l]]
+        for a in range(3):
+            dofs = 3 * idx + a
+            ls = np.linalg.lstsq(w[dofs, None], (y - x)[dofs], rcond=None)[0][0]
+            assert S[l, a] / S[l, 3 + a] == pytest.approx(ls, rel=1e-12)

@@ -408,37 +408,154 @@ __global__ void __launch_bounds__(256) k_bj_apply(const LeafDesc* __restrict__ l
 }
 
 // out = N v per row leaf: the near-field tiles of the leaf except its own diagonal block
-// (columns whose operand lies in the leaf), FP32 coefficients read column by column
-// (coalesced over the rows), FP64 sums; one CTA per leaf, a thread per row (<= 192) and
-// up to 16 RHS in registers.
-constexpr int NOD_NT = 192;
+// (columns whose operand lies in the leaf).  The work is cut into items, a run of at most
+// NOD_CMAX near columns of one row leaf, so that the leaves where many near blocks meet
+// (a crack crossing a fault) do not set the kernel's length; one CTA per item, a thread
+// per row.  The operand v32 (FP32, RHS-interleaved [ndof][nr]) of NOD_CH columns at a
+// time is staged in shared memory with the leaf's own columns zeroed, and every row
+// reads its FP32 coefficients column by column (coalesced over the rows, NOD_UN loads in
+// flight).  An item that covers its whole leaf writes out; the items of a longer leaf
+// write FP32 partial sums, added in item order by k_near_sum (deterministic).  Products
+// and sums in FP32: a preconditioner only has to be a fixed operator, and the FP64 pipe
+// of this GPU is far too slow for one FMA per near-field entry.
+constexpr int NOD_NT = 192, NOD_CH = 128, NOD_UN = 8, NOD_CMAX = 1024;
+struct NearItem {
+    int32_t leaf, c0, c1;
+    int32_t prow;  // first partial row of the item; -1: the item writes out directly
+};
+template <int NRP>
 __global__ void __launch_bounds__(NOD_NT) k_near_offdiag(const LeafDesc* __restrict__ leaves,
+                                                         const NearItem* __restrict__ items,
                                                          const float* __restrict__ near,
                                                          const int32_t* __restrict__ zidx,
-                                                         const double* __restrict__ v, double* __restrict__ out,
-                                                         int64_t ndof, int nr, const CycleState* __restrict__ cs) {
-    const LeafDesc L = leaves[blockIdx.x];
+                                                         const float* __restrict__ v32, double* __restrict__ out,
+                                                         float* __restrict__ part, int64_t ndof, int nr,
+                                                         const CycleState* __restrict__ cs) {
+    __shared__ __align__(16) float sv[NOD_CH * NRP];
+    const NearItem it = items[blockIdx.x];
+    const LeafDesc L = leaves[it.leaf];
     const int n = 3 * L.n;
     const int64_t lo = 3 * (int64_t)L.begin, hi = lo + n;
+    const float* D = near + L.near_off;
+    const int32_t* Z = zidx + L.near_cbase;
     for (int r0 = 0; r0 < n; r0 += NOD_NT) {
         const int r = r0 + threadIdx.x;
-        double acc[16];
+        float acc[NRP];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-        const float* D = near + L.near_off;
-        for (int c = 0; c < L.near_cols; ++c) {
-            const int64_t z = zidx[L.near_cbase + c];
-            if (z >= lo && z < hi) continue;  // the leaf's own block: B's part
-            const double a = r < n ? (double)D[(int64_t)c * L.ld + r] : 0.0;
+        for (int k = 0; k < NRP; ++k) acc[k] = 0.f;
+        for (int c0 = it.c0; c0 < it.c1; c0 += NOD_CH) {
+            const int cn = min(NOD_CH, it.c1 - c0);
+            __syncthreads();
+            for (int q = threadIdx.x; q < cn * NRP; q += NOD_NT) {
+                const int c = q / NRP, k = q % NRP;
+                const int64_t z = Z[c0 + c];
+                sv[q] = (k < nr && (z < lo || z >= hi)) ? v32[z * nr + k] : 0.f;
+            }
+            __syncthreads();
+            if (r < n) {
+                const float* Dc = D + (int64_t)c0 * L.ld + r;
+                int c = 0;
+                for (; c + NOD_UN <= cn; c += NOD_UN) {
+                    float a[NOD_UN];
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < nr) acc[k] += a * v[k * ndof + z];
+                    for (int u = 0; u < NOD_UN; ++u) a[u] = __ldg(Dc + (int64_t)(c + u) * L.ld);
+#pragma unroll
+                    for (int u = 0; u < NOD_UN; ++u)
+#pragma unroll
+                        for (int k = 0; k < NRP; ++k) acc[k] = fmaf(a[u], sv[(c + u) * NRP + k], acc[k]);
+                }
+                for (; c < cn; ++c) {
+                    const float a = __ldg(Dc + (int64_t)c * L.ld);
+#pragma unroll
+                    for (int k = 0; k < NRP; ++k) acc[k] = fmaf(a, sv[c * NRP + k], acc[k]);
+                }
+            }
         }
         if (r < n) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < nr && (!cs || !cs[k].done)) out[k * ndof + lo + r] = acc[k];
+            for (int k = 0; k < NRP; ++k) {
+                if (k >= nr) continue;
+                if (it.prow >= 0)
+                    part[((int64_t)it.prow + r) * nr + k] = acc[k];
+                else if (!cs || !cs[k].done)
+                    out[k * ndof + lo + r] = (double)acc[k];
+            }
         }
+    }
+}
+
+// out rows of the leaves cut into several items: the items' partial sums added in order;
+// msum[3 l'] = leaf, msum[3 l' + 1] = first partial row, msum[3 l' + 2] = items
+__global__ void k_near_sum(const LeafDesc* __restrict__ leaves, const int32_t* __restrict__ msum,
+                           const float* __restrict__ part, double* __restrict__ out, int64_t ndof, int nr,
+                           const CycleState* __restrict__ cs) {
+    const LeafDesc L = leaves[msum[3 * blockIdx.x]];
+    const int64_t prow = msum[3 * blockIdx.x + 1];
+    const int m = msum[3 * blockIdx.x + 2];
+    const int n = 3 * L.n;
+    for (int q = threadIdx.x; q < n * nr; q += blockDim.x) {
+        const int r = q / nr, k = q % nr;
+        if (cs && cs[k].done) continue;
+        float s = 0.f;
+        for (int j = 0; j < m; ++j) s += part[(prow + (int64_t)j * n + r) * nr + k];
+        out[k * ndof + 3 * (int64_t)L.begin + r] = (double)s;
+    }
+}
+
+// the item list of the near product: host vectors, built once per matrix
+struct NearPlan {
+    std::vector<NearItem> items;
+    std::vector<int32_t> msum;
+    int64_t part_rows = 0;
+};
+NearPlan near_plan(const HMat& H) {
+    NearPlan P;
+    for (int l = 0; l < H.n_leaves; ++l) {
+        const LeafDesc& L = H.h_leaves[l];
+        const int m = std::max(1, (L.near_cols + NOD_CMAX - 1) / NOD_CMAX);
+        if (m == 1) {
+            P.items.push_back(NearItem{l, 0, L.near_cols, -1});
+            continue;
+        }
+        P.msum.insert(P.msum.end(), {l, (int32_t)P.part_rows, m});
+        for (int j = 0; j < m; ++j) {
+            const int c0 = (int)((int64_t)L.near_cols * j / m), c1 = (int)((int64_t)L.near_cols * (j + 1) / m);
+            P.items.push_back(NearItem{l, c0, c1, (int32_t)(P.part_rows + (int64_t)j * 3 * L.n)});
+        }
+        P.part_rows += (int64_t)m * 3 * L.n;
+    }
+    return P;
+}
+
+struct NearDev {
+    const NearItem* items;
+    int n_items;
+    const int32_t* msum;
+    int n_multi;
+    float* part;
+};
+
+void near_offdiag_launch(HMat& H, const NearDev& P, const float* v32, double* out, int nr, const CycleState* cs,
+                         cudaStream_t st) {
+    const int64_t n = H.ndof;
+#define HM_NEAR_LAUNCH(NRP)                                                                                  \
+    k_near_offdiag<NRP><<<P.n_items, NOD_NT, 0, st>>>(H.leaves.p, P.items, H.near.p, H.near_zidx.p, v32, out, \
+                                                      P.part, n, nr, cs)
+    if (nr == 1)
+        HM_NEAR_LAUNCH(1);
+    else if (nr == 2)
+        HM_NEAR_LAUNCH(2);
+    else if (nr <= 4)
+        HM_NEAR_LAUNCH(4);
+    else if (nr <= 8)
+        HM_NEAR_LAUNCH(8);
+    else
+        HM_NEAR_LAUNCH(16);
+#undef HM_NEAR_LAUNCH
+    HM_LAUNCH_CHECK();
+    if (P.n_multi) {
+        k_near_sum<<<P.n_multi, 192, 0, st>>>(H.leaves.p, P.msum, P.part, out, n, nr, cs);
+        HM_LAUNCH_CHECK();
     }
 }
 
@@ -1009,6 +1126,11 @@ struct SolveWS {
     bool near_on = false;
     double near_gamma = 1.0;
     DevBuf<double> nt, nu;
+    DevBuf<float> nv32;  // FP32 RHS-interleaved copy of B^-1 v, the operand of N
+    DevBuf<NearItem> near_items;  // the work items of N v (near_plan)
+    DevBuf<int32_t> near_msum;
+    DevBuf<float> near_part;
+    int64_t near_part_rows = -1;  // -1: no plan yet
     DevBuf<int32_t> leaf_of;
     const double* blk = nullptr;  // blkbuf.p when the tangent has a block-diagonal C^ep
     DevBuf<int64_t> binv_off, self_off;
@@ -1118,15 +1240,19 @@ struct CycleResult {
 // preconditioner applied in the Krylov loop
 enum PcKind { PC_NONE = 0, PC_LEAF = 1, PC_POINT = 2, PC_ILU = 3 };
 
+NearDev near_dev(SolveWS& W) {
+    return NearDev{W.near_items.p, (int)W.near_items.n, W.near_msum.p, (int)(W.near_msum.n / 3), W.near_part.p};
+}
+
 // z = M^-1 v (cluster order, RHS-major), and its FP32 RHS-interleaved copy zf when the
 // next product is an FP32 one; RHS whose CycleState is done are skipped
 void precond_apply(HMat& H, SolveWS& W, PcKind pc, const double* v, double* z, float* zf, int nr, cudaStream_t st) {
     const int64_t n = H.ndof;
     if (pc == PC_LEAF && W.near_on) {
         // z = y - gamma d o B^-1 N y, y = B^-1 v
-        k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, v, z, nullptr, n, nr, W.st.p, 0,
+        k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, v, z, W.nv32.p, n, nr, W.st.p, 0,
                                                nullptr);
-        k_near_offdiag<<<H.n_leaves, NOD_NT, 0, st>>>(H.leaves.p, H.near.p, H.near_zidx.p, z, W.nt.p, n, nr, W.st.p);
+        near_offdiag_launch(H, near_dev(W), W.nv32.p, W.nt.p, nr, W.st.p, st);
         k_bj_apply<<<H.n_leaves, 256, 0, st>>>(H.leaves.p, W.binv.p, W.binv_off.p, W.nt.p, W.nu.p, nullptr, n, nr,
                                                W.st.p, 0, nullptr);
         k_near_update<<<g1(n * nr), 256, 0, st>>>(z, W.nu.p, W.dsc.p, W.leaf_of.p, W.near_gamma, zf, n, nr, W.st.p);
@@ -1400,9 +1526,17 @@ void near_prepare(HMat& H, SolveWS& W, int nr, cudaStream_t st) {
             for (int e = 0; e < H.h_leaves[l].n; ++e) lo[H.h_leaves[l].begin + e] = l;
         W.leaf_of.upload(lo, st);
     }
+    if (W.near_part_rows < 0) {
+        const NearPlan P = near_plan(H);
+        W.near_items.upload(P.items, st);
+        if (!P.msum.empty()) W.near_msum.upload(P.msum, st);
+        W.near_part_rows = P.part_rows;
+    }
+    if (W.near_part.n < (size_t)W.near_part_rows * nr + 1) W.near_part.alloc((size_t)W.near_part_rows * nr + 1);
     const size_t len = (size_t)H.ndof * nr + VSLACK;
     if (W.nt.n < len) W.nt.alloc(len);
     if (W.nu.n < len) W.nu.alloc(len);
+    if (W.nv32.n < len) W.nv32.alloc(len);
 }
 
 // the interface term of the tangent: diag(k) + C^ep + shift I into W.dc (and the
@@ -1456,8 +1590,9 @@ void near_offdiag_cluster(HMat& H, const double* v, double* out, int nr, cudaStr
     if (nr < 1 || nr > 16) fail(HM_EINVAL, "near product: 1 to 16 right-hand sides");
     SolveWS& W = workspace(H, nr, 1, st);
     near_prepare(H, W, nr, st);
-    k_near_offdiag<<<H.n_leaves, NOD_NT, 0, st>>>(H.leaves.p, H.near.p, H.near_zidx.p, v, out, H.ndof, nr, nullptr);
+    k_to_f32_interleaved<<<g1(H.ndof * nr), 256, 0, st>>>(v, W.nv32.p, H.ndof, nr);
     HM_LAUNCH_CHECK();
+    near_offdiag_launch(H, near_dev(W), W.nv32.p, out, nr, nullptr, st);
 }
 
 // The ILU preconditioner of A = E - diag(k) - C^ep - shift I for a fraction p, built and

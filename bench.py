@@ -456,9 +456,11 @@ def run_learned(args, dev, torch, hmat, synth):
     one RHS each, x by block-Jacobi GMRES to 1e-8), 500 Adam steps each: the scaling
     M = D B^-1 and the near correction M = B^-1 - gamma D B^-1 N B^-1.  Validation on 4
     more systems picks gamma (from 0.6 to 1.0) and decides each fallback (plain
-    block-Jacobi unless the learned correction takes fewer iterations); test: 8 held-out
-    systems (seeds 1606000 + i), GMRES to 1e-8, restart 50, plain FP64 mode.  value = the
-    block-Jacobi time over the near correction's time on the held-out systems."""
+    block-Jacobi unless the learned correction takes fewer iterations); the same near
+    correction with the untrained network (d = 1) and its own gamma is the control that
+    shows what training adds; test: 8 held-out systems (seeds 1606000 + i), GMRES to 1e-8,
+    restart 50, plain FP64 mode.  value = the block-Jacobi time over the trained near
+    correction's time on the held-out systems."""
     import numpy as np
     h = args.lp_h
     el = synth.config_crack_fault(h=h)
@@ -508,17 +510,22 @@ def run_learned(args, dev, torch, hmat, synth):
     vsys = [system(1605500 + i) for i in range(4)]
     val = {"blockj": [solve(k, b, "blockj")[1]["iters"] for k, b in vsys],
            "scale": [solve(k, b, "learned", models["scale"])[1]["iters"] for k, b in vsys]}
-    gammas = {}
-    for g in (0.6, 0.7, 0.8, 0.9, 1.0):
-        models["near"].set_kind("near", g)
-        gammas[g] = [solve(k, b, "learned", models["near"])[1]["iters"] for k, b in vsys]
-    gbest = min(gammas, key=lambda g: (float(np.mean(gammas[g])), g))
-    models["near"].set_kind("near", gbest)
-    val["near"] = gammas[gbest]
+    # the same near correction with the untrained network (zero output layer: d = 1), its
+    # gamma picked the same way: what the trained network adds beyond the damping
+    models["near_untrained"] = hmat.LearnedCorrection(synth.lp_initial_weights(32, seed=1607), hidden=32)
+    gammas, gbest = {}, {}
+    for name in ("near", "near_untrained"):
+        gammas[name] = {}
+        for g in (0.6, 0.7, 0.8, 0.9, 1.0):
+            models[name].set_kind("near", g)
+            gammas[name][g] = [solve(k, b, "learned", models[name])[1]["iters"] for k, b in vsys]
+        gbest[name] = min(gammas[name], key=lambda g: (float(np.mean(gammas[name][g])), g))
+        models[name].set_kind("near", gbest[name])
+        val[name] = gammas[name][gbest[name]]
     fallback = {name: float(np.mean(val[name])) >= float(np.mean(val["blockj"])) for name in models}
     for name, m in models.items():
         m.set_fallback(fallback[name])
-    test = {pc: {"iters": [], "s": [], "relres": []} for pc in ("blockj", "scale", "near")}
+    test = {pc: {"iters": [], "s": [], "relres": []} for pc in ("blockj", "scale", "near", "near_untrained")}
     for i in range(8):
         k, b = system(1606000 + i)
         for pc in test:
@@ -537,7 +544,8 @@ def run_learned(args, dev, torch, hmat, synth):
                        "train_targets": "x = A^-1 b by block-Jacobi GMRES to 1e-8",
                        "adam_steps": 500, "lr": 3e-3, "hidden": 32},
             "loss": loss, "data_s": t_data, "train_s": t_train, "validation_iters": val,
-            "gamma_scan": {str(g): v for g, v in gammas.items()}, "gamma": gbest, "fallback": fallback,
+            "gamma_scan": {name: {str(g): v for g, v in gs.items()} for name, gs in gammas.items()}, "gamma": gbest,
+            "fallback": fallback,
             "test": test, "mean_iters": {pc: float(np.mean(test[pc]["iters"])) for pc in test},
             "time_ratio_vs_blockj": {pc: tb / sum(test[pc]["s"]) for pc in test}}
     print(json.dumps(line), flush=True)

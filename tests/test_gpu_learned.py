@@ -238,10 +238,13 @@ def test_near_statistics_match_oracle(dev, system):
 
 
 def test_trained_near_correction_takes_fewer_iterations(dev, system):
-    """What the trained network gains: the learned near correction, trained on 12 solved
-    systems of the crack crossing a fault and with gamma picked on 3 validation systems by
-    GMRES iterations, takes at least a quarter fewer iterations than plain block-Jacobi
-    on 4 held-out systems (the oracle's experiment on the same tangents: 14 -> 7-8)."""
+    """The learned near correction, trained on 12 solved systems of the crack crossing a
+    fault and with gamma picked on 3 validation systems by GMRES iterations, takes at
+    least a quarter fewer iterations than plain block-Jacobi on 4 held-out systems (the
+    oracle's experiment on the same tangents: 14 -> 7-8).  The control, the untrained
+    network (d = 1) with its own gamma picked the same way, is within one iteration of
+    the trained one: the gain is the damped near correction's, and the oracle's
+    per-system optimum of the per-leaf scaling does no better than a constant."""
     import torch
     el, T, H, perm, begin, end, h = system
     m = hmat.LearnedCorrection(synth.lp_initial_weights(HID, seed=14), hidden=HID)
@@ -268,14 +271,21 @@ def test_trained_near_correction_takes_fewer_iterations(dev, system):
             out.append(inf["iters"])
         return np.mean(out)
     val = [2100 + s for s in range(3)]
-    scores = []
-    for g in (0.6, 0.7, 0.8, 0.9, 1.0):
-        m.set_kind("near", g)
-        scores.append((iters(val, "learned", m), g))
-    best = min(scores)
-    m.set_kind("near", best[1])
+
+    def pick(model):
+        scores = []
+        for g in (0.6, 0.7, 0.8, 0.9, 1.0):
+            model.set_kind("near", g)
+            scores.append((iters(val, "learned", model), g))
+        best = min(scores)
+        model.set_kind("near", best[1])
+        return best[1]
+    g_l = pick(m)
+    u = hmat.LearnedCorrection(synth.lp_initial_weights(HID, seed=14), hidden=HID)
+    g_u = pick(u)
     held = [2200 + s for s in range(4)]
-    it_bj, it_l = iters(held, "blockj"), iters(held, "learned", m)
-    print("held-out GMRES iterations: block-Jacobi %.2f, learned near correction %.2f (gamma %.1f)" % (
-        it_bj, it_l, best[1]))
+    it_bj, it_l, it_u = iters(held, "blockj"), iters(held, "learned", m), iters(held, "learned", u)
+    print("held-out GMRES iterations: block-Jacobi %.2f, learned near correction %.2f (gamma %.1f), "
+          "untrained %.2f (gamma %.1f)" % (it_bj, it_l, g_l, it_u, g_u))
     assert it_l <= 0.75 * it_bj
+    assert abs(it_l - it_u) <= 1.0

@@ -258,3 +258,53 @@ def test_near_stats_give_the_least_squares_damping():
             dofs = 3 * idx + a
             ls = np.linalg.lstsq(w[dofs, None], (y - x)[dofs], rcond=None)[0][0]
             assert S[l, a] / S[l, 3 + a] == pytest.approx(ls, rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", [1606000, 1606001])
+def test_per_leaf_scaling_of_the_near_correction_has_no_headroom(seed):
+    """What the network of the near correction M = B^-1 - gamma D B^-1 N B^-1 can add
+    beyond a constant damping, on the tangent of a crack crossing a fault (h = 0.15,
+    16 leaves, k log-uniform): the damped correction with D = I cuts GMRES iterations by
+    a third against block-Jacobi for the best gamma in 0.6..1.0, and the per-(leaf,
+    component) scaling that minimises sum ||r - A M r||^2 over 8 probe vectors r -- the
+    optimum of a loss that sees the spectrum of A M, fitted on the very system it is
+    tested on -- saves at most one iteration more."""
+    h = 0.15
+    el = synth.config_crack_fault(h=h)
+    Em = O.dense_matrix(el, 1.0, 0.25)
+    T = O.cluster_tree(el, 64)
+    perm, begin, end = _tree_arrays(el, 64)
+    Nm = Lr.near_offdiag(Em, T)
+    nl, n = len(begin), 3 * el.N
+    A = O.tangent_dense(Em, synth.k_loguniform(el.N, seed, E=1.0, h=h))
+    inv = O.block_jacobi_inverses(A, T)
+    bj = lambda v: O.apply_block_jacobi(inv, v)
+    b = synth.rhs_normal(n, seed)
+
+    def iters(M):
+        _, it, ok, _ = O.gmres(lambda v: A @ v, b, M, tol=1e-8, restart=50)
+        assert ok
+        return it
+    it_bj = iters(bj)
+    it_d1 = min(iters(lambda r, g=g: Lr.apply_near(np.ones((nl, 3)), g, r, Nm, perm, begin, end, bj))
+                for g in (0.6, 0.7, 0.8, 0.9, 1.0))
+    assert it_d1 <= 0.7 * it_bj
+    # A M r = A y - sum_(l, a) d_(l, a) A (u restricted to leaf l, component a)
+    rng = np.random.default_rng(5)
+    rows, rhs = [], []
+    for _ in range(8):
+        r = rng.normal(size=n)
+        y = bj(r)
+        u = bj(Nm @ y)
+        cols = []
+        for l in range(nl):
+            for a in range(3):
+                q = 3 * perm[begin[l]:end[l]] + a
+                v = np.zeros(n)
+                v[q] = u[q]
+                cols.append(A @ v)
+        rows.append(np.stack(cols, 1))
+        rhs.append(A @ y - r)
+    d = np.linalg.lstsq(np.vstack(rows), np.concatenate(rhs), rcond=None)[0].reshape(nl, 3)
+    it_opt = iters(lambda r: Lr.apply_near(d, 1.0, r, Nm, perm, begin, end, bj))
+    assert it_opt >= it_d1 - 1

@@ -205,141 +205,184 @@ __global__ void __launch_bounds__(512) k_bj_build(const LeafDesc* __restrict__ l
 }
 
 // The same inverse for leaves of at most BJR_ROWS rows, with the matrix held in registers:
-// 512 threads, thread (tr, tc) = (t / 32, t % 32) owns rows tr + 16 a (a < 12) and columns
-// tc + 32 b (b < 6).  Gauss-Jordan by in-place sweeps with partial pivoting and no row
-// interchanges: step k picks the unused row p_k with the largest |A[i][k]| and sweeps on
-// (p_k, k) (pivot row divided by the pivot, every other row i minus A[i][k] times it,
-// column k replaced by -A[i][k] / pivot and 1 / pivot).  After n sweeps row p_k holds
-// the coefficients of unknown k against equations p_0 .. p_(n-1), so
-// A^-1[k][m] = W[p_k][q] with p_q = m.  Only the pivot row and column go through shared
-// memory at each step.
+// 512 threads, thread (tr, tc) = (t / 32, t % 32) owns rows tr + 16 a (a < AR) and columns
+// tc + 32 b (b < BC), the tile sized by the largest leaf of the launch.  Gauss-Jordan by
+// in-place sweeps with partial pivoting and no row interchanges: step k picks the unused
+// row p_k with the largest |A[i][k]| (ties: the lowest row) and sweeps on (p_k, k) -- the
+// pivot row divided by the pivot, every other row i minus A[i][k] times it, column k
+// replaced by -A[i][k] / pivot and 1 / pivot.  After n sweeps row p_k holds the
+// coefficients of unknown k against equations p_0 .. p_(n-1), so A^-1[k][m] = W[p_k][q]
+// with p_q = m.
+// A sweep is one uniform rank-1 update A -= c' r'^T, r' the pivot row over the pivot
+// (r'[k] = 1 / pivot), c' column k (c'[p] = -1), followed by two fix-ups: column k minus
+// its old values, and row p set to r'.  Every warp finds the pivot itself (shuffles over
+// the column in shared memory, the taken rows a bit mask per lane), and the column and
+// the scaled pivot row are double-buffered, so a step needs two barriers.
 constexpr int BJR_ROWS = 192;
 
+// Steps k = 32 KB .. 32 KB + 31 of the sweep: column k lives in register column KB, a
+// compile-time index, so only lane k % 32 of each warp touches it.  Returns false when the
+// remaining column has no non-zero entry in an unused row (a singular block), with the
+// same decision in every thread.
+template <int AR, int BC, int KB>
+__device__ __forceinline__ bool bjr_steps(float (&A)[AR][BC], unsigned& used, int n, int t, int tr, int tc,
+                                          float (*colk)[16 * AR], float (*rp)[32 * BC], int* pk, int* pinv,
+                                          int* err) {
+    constexpr int M = (16 * AR + 31) / 32;  // row slots per lane in the pivot search
+    for (int kc = 0; kc < 32; ++kc) {
+        const int k = 32 * KB + kc;
+        if (k >= n) return true;
+        const int buf = k & 1;
+        if (tc == kc) {
+#pragma unroll
+            for (int a = 0; a < AR; ++a) colk[buf][tr + 16 * a] = A[a][KB];
+        }
+        __syncthreads();
+        float bv = -1.f;
+        int bi = 0x7fffffff;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int i = tc + 32 * m;
+            if (i < n && !((used >> m) & 1u)) {
+                const float v = fabsf(colk[buf][i]);
+                if (v > bv) {  // rows ascend within a lane: the lowest row wins ties
+                    bv = v;
+                    bi = i;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (!(bv > 0.f)) {  // every warp sees the same column: a uniform exit
+            if (t == 0) atomicOr(err, 1);
+            return false;
+        }
+        const int p = bi, ap = p >> 4;
+        if (tc == (p & 31)) used |= 1u << (p >> 5);
+        if (t == 0) {
+            pk[k] = p;
+            pinv[p] = k;
+        }
+        if (tr == (p & 15)) {  // the warp of the pivot row: r' = row p / pivot, r'[k] = 1 / pivot
+            const float pinvv = 1.0f / colk[buf][p];
+#pragma unroll
+            for (int a = 0; a < AR; ++a)
+                if (a == ap)
+#pragma unroll
+                    for (int b = 0; b < BC; ++b)
+                        rp[buf][tc + 32 * b] = (b == KB && tc == kc) ? pinvv : A[a][b] * pinvv;
+        }
+        __syncthreads();
+        float r[BC];
+#pragma unroll
+        for (int b = 0; b < BC; ++b) r[b] = rp[buf][tc + 32 * b];
+#pragma unroll
+        for (int a = 0; a < AR; ++a) {
+            const int i = tr + 16 * a;
+            const float c = (i == p) ? -1.f : colk[buf][i];
+#pragma unroll
+            for (int b = 0; b < BC; ++b) A[a][b] = fmaf(-c, r[b], A[a][b]);
+        }
+        if (tc == kc) {  // column k: -c[i] / pivot (the sweep left c[i] on top)
+#pragma unroll
+            for (int a = 0; a < AR; ++a) A[a][KB] -= colk[buf][tr + 16 * a];
+        }
+        if (tr == (p & 15)) {  // row p: r'
+#pragma unroll
+            for (int a = 0; a < AR; ++a)
+                if (a == ap)
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) A[a][b] = r[b];
+        }
+    }
+    return true;
+}
+
+template <int AR, int BC, int KB>
+struct BjrSweep {
+    static __device__ __forceinline__ bool run(float (&A)[AR][BC], unsigned& used, int n, int t, int tr, int tc,
+                                               float (*colk)[16 * AR], float (*rp)[32 * BC], int* pk, int* pinv,
+                                               int* err) {
+        if (!bjr_steps<AR, BC, KB>(A, used, n, t, tr, tc, colk, rp, pk, pinv, err)) return false;
+        return BjrSweep<AR, BC, KB + 1>::run(A, used, n, t, tr, tc, colk, rp, pk, pinv, err);
+    }
+};
+template <int AR, int BC>
+struct BjrSweep<AR, BC, BC> {
+    static __device__ __forceinline__ bool run(float (&)[AR][BC], unsigned&, int, int, int, int, float (*)[16 * AR],
+                                               float (*)[32 * BC], int*, int*, int*) {
+        return true;
+    }
+};
+
+template <int AR, int BC>
 __global__ void __launch_bounds__(512, 1) k_bj_build_reg(const LeafDesc* __restrict__ leaves,
                                                          const int64_t* __restrict__ self_off,
                                                          const float* __restrict__ near, const double* __restrict__ d,
                                                          const double* __restrict__ blk, float* __restrict__ binv,
                                                          const int64_t* __restrict__ binv_off, int* __restrict__ err) {
-    extern __shared__ float wsm[];  // final n x n staging (row-major)
-    __shared__ float colk[BJR_ROWS], prow[BJR_ROWS];
-    __shared__ float cand_v[16];
-    __shared__ int cand_i[16];
-    __shared__ int used[BJR_ROWS], pk[BJR_ROWS], pinv[BJR_ROWS];
-    __shared__ int s_p;
+    extern __shared__ float wsm[];  // n x n staging (row-major): the block, then W
+    __shared__ float colk[2][16 * AR], rp[2][32 * BC];
+    __shared__ int pk[BJR_ROWS], pinv[BJR_ROWS];
     const LeafDesc L = leaves[blockIdx.x];
     const int n = 3 * L.n;
     const int t = threadIdx.x, tr = t >> 5, tc = t & 31;
     const float* E = near + self_off[blockIdx.x];
-    float A[12][6];
-#pragma unroll
-    for (int a = 0; a < 12; ++a)
-#pragma unroll
-        for (int b = 0; b < 6; ++b) {
-            const int i = tr + 16 * a, j = tc + 32 * b;
-            float v = 0.f;
-            if (i < n && j < n) {
-                v = E[(int64_t)j * L.ld + i];
-                if (i == j) v -= (float)d[3 * (int64_t)L.begin + i];
-                if (blk && i / 3 == j / 3) v -= (float)blk[9 * ((int64_t)L.begin + i / 3) + 3 * (i % 3) + j % 3];
-            }
-            A[a][b] = v;
-        }
-    for (int i = t; i < BJR_ROWS; i += 512) used[i] = (i < n) ? 0 : 1;
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        const int bk = k >> 5, ck = k & 31;
-        // column k to shared memory and the pivot candidates of each row group
-        if (tc == ck) {
-            float bv = -1.f;
-            int bi = -1;
-#pragma unroll
-            for (int a = 0; a < 12; ++a) {
-                const int i = tr + 16 * a;
-                float v = 0.f;
-#pragma unroll
-                for (int b = 0; b < 6; ++b)
-                    if (b == bk) v = A[a][b];
-                if (i < BJR_ROWS) colk[i] = v;
-                if (i < n && !used[i] && fabsf(v) > bv) {
-                    bv = fabsf(v);
-                    bi = i;
-                }
-            }
-            cand_v[tr] = bv;
-            cand_i[tr] = bi;
-        }
-        __syncthreads();
-        if (t == 0) {
-            float bv = -1.f;
-            int bi = -1;
-            for (int g = 0; g < 16; ++g)
-                if (cand_v[g] > bv || (cand_v[g] == bv && cand_i[g] >= 0 && cand_i[g] < bi)) {
-                    bv = cand_v[g];
-                    bi = cand_i[g];
-                }
-            if (!(bv > 0.f) || bi < 0) {
-                atomicOr(err, 1);
-                bi = -1;
-            }
-            s_p = bi;
-            if (bi >= 0) {
-                used[bi] = 1;
-                pk[k] = bi;
-                pinv[bi] = k;
-            }
-        }
-        __syncthreads();
-        const int p = s_p;
-        if (p < 0) break;  // singular block: reported through err
-        // pivot row to shared memory
-        if (tr == (p & 15)) {
-            const int ap = p >> 4;
-#pragma unroll
-            for (int a = 0; a < 12; ++a)
-                if (a == ap)
-#pragma unroll
-                    for (int b = 0; b < 6; ++b) {
-                        const int j = tc + 32 * b;
-                        if (j < BJR_ROWS) prow[j] = A[a][b];
-                    }
-        }
-        __syncthreads();
-        const float piv = prow[k];
-        const float pinvv = 1.0f / piv;
-#pragma unroll
-        for (int a = 0; a < 12; ++a) {
-            const int i = tr + 16 * a;
-            const float cik = colk[i < BJR_ROWS ? i : 0];
-            const bool prow_i = (i == p);
-#pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                const int j = tc + 32 * b;
-                const float pj = prow[j < BJR_ROWS ? j : 0];
-                float v = A[a][b];
-                if (prow_i)
-                    v = (j == k) ? pinvv : v * pinvv;
-                else
-                    v = (j == k) ? -cik * pinvv : fmaf(-cik * pinvv, pj, v);
-                A[a][b] = v;
-            }
-        }
-        __syncthreads();  // colk / prow are rewritten by the next step
+    // the leaf's block of E - diag(d) - C^ep, read column by column (coalesced)
+    for (int q = t; q < n * n; q += 512) {
+        const int j = q / n, i = q % n;
+        float v = E[(int64_t)j * L.ld + i];
+        if (i == j) v -= (float)d[3 * (int64_t)L.begin + i];
+        if (blk && i / 3 == j / 3) v -= (float)blk[9 * ((int64_t)L.begin + i / 3) + 3 * (i % 3) + j % 3];
+        wsm[i * n + j] = v;
     }
-    // stage W, then write A^-1[r][c] = W[p_r][pinv[c]] column-major with the padded ld
+    __syncthreads();
+    float A[AR][BC];
 #pragma unroll
-    for (int a = 0; a < 12; ++a)
+    for (int a = 0; a < AR; ++a)
 #pragma unroll
-        for (int b = 0; b < 6; ++b) {
+        for (int b = 0; b < BC; ++b) {
+            const int i = tr + 16 * a, j = tc + 32 * b;
+            A[a][b] = (i < n && j < n) ? wsm[i * n + j] : 0.f;
+        }
+    unsigned used = 0;  // bit m: row tc + 32 m is a pivot row already
+    const bool ok = BjrSweep<AR, BC, 0>::run(A, used, n, t, tr, tc, colk, rp, pk, pinv, err);
+    __syncthreads();  // every thread is past its last read of wsm
+    if (!ok) return;
+#pragma unroll
+    for (int a = 0; a < AR; ++a)
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
             const int i = tr + 16 * a, j = tc + 32 * b;
             if (i < n && j < n) wsm[i * n + j] = A[a][b];
         }
     __syncthreads();
-    if (s_p < 0) return;
     float* out = binv + binv_off[blockIdx.x];
     for (int q = t; q < n * n; q += 512) {
-        const int c = q / n, r = q % n;
-        out[(int64_t)c * L.ld + r] = wsm[pk[r] * n + pinv[c]];
+        const int c = q / n, rr = q % n;
+        out[(int64_t)c * L.ld + rr] = wsm[pk[rr] * n + pinv[c]];
     }
+}
+
+template <int AR, int BC>
+void bj_build_reg_launch(HMat& H, SolveWS& W, size_t smem, cudaStream_t st) {
+    static bool attr_done[64] = {};
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        HM_CUDA(cudaFuncSetAttribute(k_bj_build_reg<AR, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(float) * BJR_ROWS * BJR_ROWS)));
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    k_bj_build_reg<AR, BC><<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.blk,
+                                                           W.binv.p, W.binv_off.p, W.err.p);
 }
 
 // z = M^-1 v per leaf (block-Jacobi), or z = v; also the FP32 copy zf (RHS-interleaved)
@@ -1334,10 +1377,17 @@ CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double
 }
 
 // r = rhs - (E - diag d) x with the given product; returns ||r_k|| on the host
-std::vector<double> residual(HMat& H, SolveWS& W, const double* rhs, int nr, int dtype, int fac, cudaStream_t st) {
+std::vector<double> residual(HMat& H, SolveWS& W, const double* rhs, int nr, int dtype, int fac, cudaStream_t st,
+                             bool x_zero = false) {
     const int64_t n = H.ndof;
     const int nb = nblk_rows(n);
-    if (dtype == HM_F64) {
+    if (x_zero) {
+        // x = 0 (the caller cleared W.xc): r = rhs without a product; the FP32 copy of x
+        // is cleared as the product path would have left it
+        HM_CUDA(cudaMemsetAsync(W.y64.p, 0, (size_t)n * nr * sizeof(double), st));
+        if (dtype != HM_F64) HM_CUDA(cudaMemsetAsync(W.zf.p, 0, (size_t)n * nr * sizeof(float), st));
+        k_residual<double><<<nb, ROW_NT, 0, st>>>(rhs, W.y64.p, W.dc.p, W.blk, W.xc.p, W.r.p, n, nr, W.part.p);
+    } else if (dtype == HM_F64) {
         apply_E(H, W, W.xc.p, nullptr, W.y64.p, nr, HM_F64, fac, st);
         k_residual<double><<<nb, ROW_NT, 0, st>>>(rhs, W.y64.p, W.dc.p, W.blk, W.xc.p, W.r.p, n, nr, W.part.p);
     } else {
@@ -1359,15 +1409,16 @@ std::vector<double> residual(HMat& H, SolveWS& W, const double* rhs, int nr, int
     return out;
 }
 
-// FGMRES(m) with restarts on rhs (cluster order) into W.xc (initial value kept);
-// stops at ||rhs - A x_k|| <= tol_abs[k] or when the iteration budget is spent.
+// FGMRES(m) with restarts on rhs (cluster order) into W.xc (initial value kept; x_zero:
+// the caller cleared it, and the first residual is rhs itself); stops at
+// ||rhs - A x_k|| <= tol_abs[k] or when the iteration budget is spent.
 // Returns per RHS the iterations used and the final residual norm.
 void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& tol_abs, int nr, int m, int max_its,
             int max_cycles, int dtype, int fac, PcKind pc, std::vector<int>& its, std::vector<double>& rn,
-            std::vector<int>& brk, cudaStream_t st) {
+            std::vector<int>& brk, cudaStream_t st, bool x_zero) {
     its.assign(nr, 0);
     brk.assign(nr, 0);
-    rn = residual(H, W, rhs, nr, dtype, fac, st);
+    rn = residual(H, W, rhs, nr, dtype, fac, st, x_zero);
     for (int cyc = 0; cyc < max_cycles; ++cyc) {
         std::vector<int> active(nr, 0);
         bool any = false;
@@ -1394,7 +1445,7 @@ void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& t
 // run) decides a restart; same contract as fgmres.
 void bicgstab(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& tol_abs, int nr, int max_its,
               int max_runs, int dtype, int fac, PcKind pc, std::vector<int>& its, std::vector<double>& rn,
-              std::vector<int>& brk, cudaStream_t st) {
+              std::vector<int>& brk, cudaStream_t st, bool x_zero) {
     const int64_t n = H.ndof, vn = n * nr;
     const int nb = nblk_rows(n);
     if (W.bcg.n < (size_t)(7 * vn + VSLACK)) W.bcg.alloc((size_t)(7 * vn + VSLACK));
@@ -1411,7 +1462,7 @@ void bicgstab(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>&
     void* y = dtype == HM_F64 ? (void*)W.y64.p : (void*)W.y32.p;
     its.assign(nr, 0);
     brk.assign(nr, 0);
-    rn = residual(H, W, rhs, nr, dtype, fac, st);  // W.r = rhs - A x
+    rn = residual(H, W, rhs, nr, dtype, fac, st, x_zero);  // W.r = rhs - A x
     auto tangent = [&](const double* z, double* out) {
         apply_E(H, W, z, zf, y, nr, dtype, fac, st, W.alldone.p);
         if (dtype == HM_F64)
@@ -1487,16 +1538,19 @@ void bj_build(HMat& H, SolveWS& W, cudaStream_t st) {
     for (const LeafDesc& L : H.h_leaves) max_rows = std::max(max_rows, 3 * L.n);
     if (max_rows <= BJR_ROWS) {
         const size_t smem = sizeof(float) * (size_t)max_rows * max_rows;
-        static bool attr_done[64] = {};
-        int dev = 0;
-        HM_CUDA(cudaGetDevice(&dev));
-        if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-            HM_CUDA(cudaFuncSetAttribute(k_bj_build_reg, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float) * BJR_ROWS * BJR_ROWS)));
-            if (dev >= 0 && dev < 64) attr_done[dev] = true;
-        }
-        k_bj_build_reg<<<H.n_leaves, 512, smem, st>>>(H.leaves.p, W.self_off.p, H.near.p, W.dc.p, W.blk, W.binv.p,
-                                                      W.binv_off.p, W.err.p);
+        // the register tile of the largest leaf: 16 AR rows, 32 BC columns
+        if (max_rows <= 32)
+            bj_build_reg_launch<2, 1>(H, W, smem, st);
+        else if (max_rows <= 64)
+            bj_build_reg_launch<4, 2>(H, W, smem, st);
+        else if (max_rows <= 96)
+            bj_build_reg_launch<6, 3>(H, W, smem, st);
+        else if (max_rows <= 128)
+            bj_build_reg_launch<8, 4>(H, W, smem, st);
+        else if (max_rows <= 160)
+            bj_build_reg_launch<10, 5>(H, W, smem, st);
+        else
+            bj_build_reg_launch<12, 6>(H, W, smem, st);
         HM_LAUNCH_CHECK();
         int e = 0;
         HM_CUDA(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1786,7 +1840,7 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     build_precond(H, W, kel, cep, shift, o, pc, ilu_p, lp, nrhs, st);
     // ||b||
     HM_CUDA(cudaMemsetAsync(W.xc.p, 0, (size_t)n * nrhs * sizeof(double), st));
-    std::vector<double> bn = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st);  // x = 0: r = b
+    std::vector<double> bn = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st, true);  // x = 0: r = b
     std::vector<double> tol_abs(nrhs);
     for (int k = 0; k < nrhs; ++k) tol_abs[k] = tol * bn[k];
     std::vector<int> its(nrhs, 0), outer(nrhs, 0), brk(nrhs, 0);
@@ -1794,9 +1848,9 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
     const bool bcg = o.method == HM_METHOD_BICGSTAB;
     if (mode == HM_SOLVE_F64) {
         if (bcg) {
-            bicgstab(H, W, W.bc.p, tol_abs, nrhs, maxit, 8, HM_F64, 0, pc, its, rn, brk, st);
+            bicgstab(H, W, W.bc.p, tol_abs, nrhs, maxit, 8, HM_F64, 0, pc, its, rn, brk, st, true);
         } else {
-            fgmres(H, W, W.bc.p, tol_abs, nrhs, m, maxit, 1 << 20, HM_F64, 0, pc, its, rn, brk, st);
+            fgmres(H, W, W.bc.p, tol_abs, nrhs, m, maxit, 1 << 20, HM_F64, 0, pc, its, rn, brk, st, true);
             for (int k = 0; k < nrhs; ++k) outer[k] = (its[k] + m - 1) / m;
         }
     } else {
@@ -1812,7 +1866,7 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
             if (!any) break;
             // outer residual into W.r (current x in xacc)
             HM_CUDA(cudaMemcpyAsync(W.xc.p, xacc.p, xacc.bytes(), cudaMemcpyDeviceToDevice, st));
-            rr = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st);
+            rr = residual(H, W, W.bc.p, nrhs, HM_F64, 0, st, it == 0);
             bool need = false;
             for (int k = 0; k < nrhs; ++k) need = need || (rr[k] > tol_abs[k] && its[k] < maxit);
             if (!need) break;
@@ -1825,9 +1879,9 @@ void gmres_solve(HMat& H, const double* kel, double shift, const double* b, doub
             std::vector<int> iits, ibrk;
             std::vector<double> irn;
             if (bcg)
-                bicgstab(H, W, W.corr.p, itol_abs, nrhs, maxit, 2, HM_F32, inner_fac, pc, iits, irn, ibrk, st);
+                bicgstab(H, W, W.corr.p, itol_abs, nrhs, maxit, 2, HM_F32, inner_fac, pc, iits, irn, ibrk, st, true);
             else
-                fgmres(H, W, W.corr.p, itol_abs, nrhs, m, maxit, 4, HM_F32, inner_fac, pc, iits, irn, ibrk, st);
+                fgmres(H, W, W.corr.p, itol_abs, nrhs, m, maxit, 4, HM_F32, inner_fac, pc, iits, irn, ibrk, st, true);
             for (int k = 0; k < nrhs; ++k) {
                 its[k] += iits[k];
                 if (iits[k] > 0) outer[k]++;

@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the benc
 CPU-baseline leg; never by the product path.  It shares no code with the CUDA library.
 
 Contents, each following the passage it cites:
-  * influence coefficients of constant-DD rectangles (Sec. 3.1, eq. TractionBIE-general
-    and eq. ElasSystem; the C part in ddm_oracle.c),
+  * influence coefficients of constant-DD rectangles and triangles (Sec. 3.1, eq.
+    TractionBIE-general and eq. ElasSystem; the C part in ddm_oracle.c),
   * the dense operator E and dense products E x (eq. ElasSystem),
   * the centroid cluster tree and the block partition that the H-matrix uses
     (Sec. 3.1: near field kept dense, far field low rank; the split and admissibility
@@ -38,14 +38,20 @@ def lib():
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
         i64 = ctypes.c_int64
         d = ctypes.c_double
+        g = [dp, dp, dp, dp, dp, dp, i32p, dp]
         L.orc_blocks.restype = i64
-        L.orc_blocks.argtypes = [i64, dp, dp, dp, dp, dp, dp, d, d, i64, ip, ip, dp]
+        L.orc_blocks.argtypes = [i64] + g + [d, d, i64, ip, ip, dp]
         L.orc_dense_rows.restype = i64
-        L.orc_dense_rows.argtypes = [i64, dp, dp, dp, dp, dp, dp, d, d, i64, ip, dp]
+        L.orc_dense_rows.argtypes = [i64] + g + [d, d, i64, ip, dp]
         L.orc_dense_matvec_rows.restype = i64
-        L.orc_dense_matvec_rows.argtypes = [i64, dp, dp, dp, dp, dp, dp, d, d, i64, ip, i64, dp, dp]
+        L.orc_dense_matvec_rows.argtypes = [i64] + g + [d, d, i64, ip, i64, dp, dp]
+        L.orc_tri_phi_derivatives.restype = ctypes.c_int
+        L.orc_tri_phi_derivatives.argtypes = [dp, dp, dp, dp]
+        L.orc_influence_tri.restype = ctypes.c_int
+        L.orc_influence_tri.argtypes = [dp] * 9 + [d, d, dp]
         L.orc_phi_derivatives.restype = ctypes.c_int
         L.orc_phi_derivatives.argtypes = [dp, d, d, dp, dp]
         L.orc_influence.restype = ctypes.c_int
@@ -59,8 +65,26 @@ def _p(a, dtype=np.float64):
 
 
 def _geom(el):
+    """ctypes pointers of the geometry: c, s1, s2, n, a, b, then shape and the triangle
+    vertices (NULL when every element is a rectangle); the arrays are kept alive on the
+    returned list."""
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (el.c, el.s1, el.s2, el.n, el.a, el.b)]
-    return arrs
+    ptrs = [_p(x) for x in arrs]
+    shape = getattr(el, "shape", None)
+    if shape is not None and np.any(np.asarray(shape) != 0):
+        sh = np.ascontiguousarray(shape, dtype=np.int32)
+        tri = np.ascontiguousarray(el.tri, dtype=np.float64)
+        arrs += [sh, tri]
+        ptrs += [sh.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _p(tri)]
+    else:
+        ptrs += [None, None]
+    return _Geom(arrs, ptrs)
+
+
+class _Geom(list):
+    def __init__(self, arrs, ptrs):
+        super().__init__(ptrs)
+        self.arrs = arrs
 
 
 def set_threads(n: int | None):
@@ -83,7 +107,7 @@ def influence_blocks(el, E, nu, ri, sj):
     ri = np.ascontiguousarray(ri, dtype=np.int64)
     sj = np.ascontiguousarray(sj, dtype=np.int64)
     out = np.empty((ri.size, 9))
-    lib().orc_blocks(el.N, *[_p(x) for x in g], float(E), float(nu), ri.size,
+    lib().orc_blocks(el.N, *g, float(E), float(nu), ri.size,
                      _p(ri, np.int64), _p(sj, np.int64), _p(out))
     return out.reshape(-1, 3, 3)
 
@@ -106,6 +130,28 @@ def phi_derivatives(x, a, b):
     return st, d2.reshape(3, 3), d3.reshape(3, 3, 3)
 
 
+def tri_phi_derivatives(x, tv):
+    """phi's second and third derivatives for the triangle with vertices tv (3 x 2, in
+    its plane frame) at the point x of that frame (edge integrals by quadrature)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    tv = np.ascontiguousarray(tv, dtype=np.float64).reshape(6)
+    d2 = np.empty(9)
+    d3 = np.empty(27)
+    st = lib().orc_tri_phi_derivatives(_p(x), _p(tv), _p(d2), _p(d3))
+    return st, d2.reshape(3, 3), d3.reshape(3, 3, 3)
+
+
+def influence_point_tri(xr, rframe, cs, sframe, V, E, nu):
+    """Block for an arbitrary receiver point and frame from the triangle with vertices V
+    (3 x 3, global) collocated at cs with frame sframe."""
+    vecs = [np.ascontiguousarray(v, dtype=np.float64) for v in
+            (xr, rframe[0], rframe[1], rframe[2], cs, sframe[0], sframe[1], sframe[2])]
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(9)
+    out = np.empty(9)
+    st = lib().orc_influence_tri(*[_p(v) for v in vecs], _p(V), shear_modulus(E, nu), float(nu), _p(out))
+    return st, out.reshape(3, 3)
+
+
 def dense_matrix(el, E, nu):
     """The dense collocation matrix E (3N x 3N), DOF order (s1, s2, n) per element."""
     return dense_rows(el, E, nu, np.arange(el.N))
@@ -115,7 +161,7 @@ def dense_rows(el, E, nu, rows):
     g = _geom(el)
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     out = np.empty((3 * rows.size, 3 * el.N))
-    bad = lib().orc_dense_rows(el.N, *[_p(x) for x in g], float(E), float(nu), rows.size,
+    bad = lib().orc_dense_rows(el.N, *g, float(E), float(nu), rows.size,
                                _p(rows, np.int64), _p(out))
     if bad:
         raise ValueError("%d receiver/source pairs are singular (receiver on a source edge)" % bad)
@@ -131,7 +177,7 @@ def dense_matvec_rows(el, E, nu, x, rows=None):
     X = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
     nrhs = X.shape[0]
     Y = np.empty((nrhs, 3 * rows.size))
-    bad = lib().orc_dense_matvec_rows(el.N, *[_p(v) for v in g], float(E), float(nu), rows.size,
+    bad = lib().orc_dense_matvec_rows(el.N, *g, float(E), float(nu), rows.size,
                                       _p(rows, np.int64), nrhs, _p(X), _p(Y))
     if bad:
         raise ValueError("%d receiver/source pairs are singular" % bad)
@@ -168,7 +214,8 @@ class ClusterTree:
 
 
 def element_vertex_boxes(el):
-    """Per-element bounding box of the 4 rectangle vertices c +- a s1 +- b s2."""
+    """Per-element bounding box of its vertices: the 4 rectangle vertices
+    c +- a s1 +- b s2, or the 3 given vertices of a triangle."""
     lo = np.full((el.N, 3), np.inf)
     hi = np.full((el.N, 3), -np.inf)
     for sa in (-1.0, 1.0):
@@ -176,6 +223,12 @@ def element_vertex_boxes(el):
             v = el.c + (sa * el.a)[:, None] * el.s1 + (sb * el.b)[:, None] * el.s2
             lo = np.minimum(lo, v)
             hi = np.maximum(hi, v)
+    shape = getattr(el, "shape", None)
+    if shape is not None and np.any(np.asarray(shape) == 1):
+        t = np.asarray(shape) == 1
+        V = np.asarray(el.tri)[t].reshape(-1, 3, 3)
+        lo[t] = V.min(axis=1)
+        hi[t] = V.max(axis=1)
     return lo, hi
 
 

@@ -9,7 +9,10 @@ Element description (one row per element, user order):
   c   (N,3) centroid (collocation point, Sec. 3.1)
   s1  (N,3), s2 (N,3), n (N,3)  local orthonormal frame (Sec. 2.2; the DOF order of
       every element is (s1, s2, n), Sec. 3.1)
-  a   (N,)  half side along s1,  b (N,) half side along s2
+  a   (N,)  half side along s1,  b (N,) half side along s2 (rectangles)
+  shape (N,) 0 for a rectangle, 1 for a triangle (Sec. 3.1: the paper's element)
+  tri (N,9) the three vertices of a triangle (global), unused for rectangles; its
+      collocation point c is the centroid and (s1, s2) any orthonormal pair in its plane
 
 Local in-plane axes of a plane with unit normal n: s1 = normalize(e3 x n), falling back
 to s1 = e1 when n is parallel to e3, and s2 = n x s1.
@@ -32,6 +35,14 @@ class Elements:
     b: np.ndarray
     # plane id of every element (which fault / fracture it belongs to)
     plane: np.ndarray
+    shape: np.ndarray = None
+    tri: np.ndarray = None
+
+    def __post_init__(self):
+        if self.shape is None:
+            self.shape = np.zeros(self.c.shape[0], dtype=np.int32)
+        if self.tri is None:
+            self.tri = np.zeros((self.c.shape[0], 9))
 
     @property
     def N(self) -> int:
@@ -84,6 +95,53 @@ def plane_grid(n_cells1, n_cells2, lo1, hi1, lo2, hi2, normal, origin=(0.0, 0.0,
     return Elements(c=np.ascontiguousarray(c), s1=rep(s1), s2=rep(s2), n=rep(n),
                     a=np.full(N, 0.5 * h1), b=np.full(N, 0.5 * h2),
                     plane=np.full(N, plane_id, dtype=np.int32))
+
+
+def triangles(V, normal, plane_id=0) -> Elements:
+    """Triangle elements from their vertices V (T, 3, 3), all in the plane of the unit
+    normal: centroid collocation points and the plane's (s1, s2, n) frame; a and b hold
+    half the square root of the area (unused by the operator)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    s1, s2, n = plane_axes(normal)
+    T = V.shape[0]
+    c = V.mean(axis=1)
+    area = 0.5 * np.linalg.norm(np.cross(V[:, 1] - V[:, 0], V[:, 2] - V[:, 0]), axis=1)
+    rep = lambda v: np.ascontiguousarray(np.broadcast_to(v, (T, 3)))
+    half = 0.5 * np.sqrt(area)
+    return Elements(c=np.ascontiguousarray(c), s1=rep(s1), s2=rep(s2), n=rep(n), a=half.copy(), b=half.copy(),
+                    plane=np.full(T, plane_id, dtype=np.int32), shape=np.ones(T, dtype=np.int32),
+                    tri=np.ascontiguousarray(V.reshape(T, 9)))
+
+
+def tri_disk_mesh(n_grid, radius=1.0, normal=(0.0, 0.0, 1.0), origin=(0.0, 0.0, 0.0), jitter=0.2, seed=1620,
+                  plane_id=0) -> Elements:
+    """Triangulated disk: the vertices of an n_grid x n_grid lattice on [-R, R]^2, each
+    moved by a seeded uniform offset of up to jitter h per coordinate (shared by the
+    cells that meet there), every cell whose centre has r < R split into two triangles
+    along alternating diagonals.  General triangles with conforming vertices, like the
+    unstructured meshes of the paper's examples."""
+    R = float(radius)
+    h = 2.0 * R / n_grid
+    s1, s2, n = plane_axes(normal)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = -R + h * np.arange(n_grid + 1)
+    P1, P2 = np.meshgrid(g, g, indexing="xy")
+    P1 = P1 + rng.uniform(-jitter, jitter, P1.shape) * h
+    P2 = P2 + rng.uniform(-jitter, jitter, P2.shape) * h
+    o = np.asarray(origin, dtype=np.float64)
+    X = o[None, None, :] + P1[..., None] * s1 + P2[..., None] * s2  # (n+1, n+1, 3), [row j, col i]
+    tris = []
+    for j in range(n_grid):
+        for i in range(n_grid):
+            xc, yc = -R + (i + 0.5) * h, -R + (j + 0.5) * h
+            if xc * xc + yc * yc >= R * R:
+                continue
+            a, b, c_, d = X[j, i], X[j, i + 1], X[j + 1, i + 1], X[j + 1, i]
+            if (i + j) % 2 == 0:
+                tris += [(a, b, c_), (a, c_, d)]
+            else:
+                tris += [(a, b, d), (b, c_, d)]
+    return triangles(np.array(tris), normal, plane_id)
 
 
 def disk_mesh(n_grid, radius=1.0, normal=(0.0, 0.0, 1.0), origin=(0.0, 0.0, 0.0), plane_id=0):

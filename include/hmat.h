@@ -55,9 +55,21 @@ const char* hm_last_error(void);
 /* Library version, major*10000 + minor*100 + patch. */
 int hm_version(void);
 
+/* Element shapes. */
+#define HM_SHAPE_RECT 0 /* rectangle c +- a s1 +- b s2 */
+#define HM_SHAPE_TRI 1  /* triangle (Sec. 3.1: the paper's element) given by its vertices */
+
 /* Element geometry, host SoA (Sec. 2.2 frame, Sec. 3.1 collocation at centroids):
- * c, s1, s2, n are N x 3 row-major (centroid and the orthonormal frame), a and b are
- * the half sides along s1 and s2.  The caller keeps ownership; the library copies. */
+ * c, s1, s2, n are N x 3 row-major (collocation point and the orthonormal frame; the
+ * DD components of an element are along s1, s2, n).  a and b are the half sides along
+ * s1 and s2 of a rectangle (> 0; the entries of triangles are not read).
+ * shape: N codes HM_SHAPE_RECT / HM_SHAPE_TRI, or NULL (every element a rectangle).
+ * tri: N x 9 row-major, the three vertices (global) of every triangle (rows of
+ * rectangles unused; may be NULL when no element is a triangle).  A triangle must be
+ * non-degenerate, lie in the plane through c normal to n (within 1e-6 of its size),
+ * and contain c (the collocation point; the centroid in the paper).  Invalid geometry
+ * returns HM_EINVAL, non-finite values HM_ENAN.  The caller keeps ownership; the
+ * library copies. */
 typedef struct {
     int64_t N;
     const double* c;
@@ -66,13 +78,15 @@ typedef struct {
     const double* n;
     const double* a;
     const double* b;
+    const int32_t* shape;
+    const double* tri;
 } hm_elements;
 
 /* ---------------------------------------------------------------- influence blocks
  * 3x3 influence blocks for a list of (receiver i, source j) element pairs (Sec. 3.1,
  * eq. ElasSystem): out_dev[9p + 3 alpha + m] is the traction component alpha (frame of
  * receiver ri_dev[p]) at its centroid due to a unit DD component m (frame of source
- * sj_dev[p]) constant over the source rectangle.  Evaluated in FP64 on the device.
+ * sj_dev[p]) constant over the source element.  Evaluated in FP64 on the device.
  * ri_dev, sj_dev: npairs int64 element indices; out_dev: 9 npairs doubles.
  * Returns HM_ESINGULAR_GEOM (after writing every other block) if a receiver lies on a
  * source edge; those blocks are NaN.  Synchronises the stream. */
@@ -92,6 +106,7 @@ hm_status hm_influence_blocks(const hm_elements* el, double E, double nu, int64_
  * make that first call before any stream capture.  Every call shares the array and
  * leaves its contents behind; the error word is cleared at the start of each call.
  * Calls that overlap on the GPU (from several threads or streams) race on the array.
+ * Rectangles only: a triangle among the elements returns HM_EINVAL.
  * Arguments, outputs and errors are those of hm_influence_blocks; synchronises the
  * stream. */
 hm_status hm_influence_blocks_noalloc(const hm_elements* el, double E, double nu, int64_t npairs,

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, 
         // (1) residual rows of receiver element ipiv
         for (int l = tid; l < 3 * k; l += ACA_NT) urow[l] = U[(size_t)(l / 3) * mS + 3 * ipiv + (l % 3)];
         __syncthreads();
-        const ElemRec er = el[J.s_begin + ipiv];
+        const ElemRec& er = el[J.s_begin + ipiv];
         n_eval += J.t_n;
         for (int j = tid; j < J.t_n; j += ACA_NT) {
             double blk[9];
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(ACA_NT) k_aca(const ElemRec* __restrict__ el, 
         // (3) residual columns of source element jpiv
         for (int l = tid; l < 3 * k; l += ACA_NT) vcol[l] = V[(size_t)(l / 3) * mT + 3 * jpiv + (l % 3)];
         __syncthreads();
-        const ElemRec es = el[J.t_begin + jpiv];
+        const ElemRec& es = el[J.t_begin + jpiv];
         n_eval += J.s_n;
         for (int i = tid; i < J.s_n; i += ACA_NT) {
             double blk[9];

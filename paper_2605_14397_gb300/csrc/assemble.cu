@@ -42,17 +42,7 @@ void influence_pairs(const hm_elements& e, double E, double nu, int64_t npairs, 
     if (!ri || !sj || !out) fail(HM_EINVAL, "influence_blocks: NULL pointer");
     if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5)) fail(HM_EINVAL, "influence_blocks: need E > 0 and -1 < nu < 0.5");
     std::vector<ElemRec> h(e.N);
-    for (int64_t i = 0; i < e.N; ++i) {
-        for (int d = 0; d < 3; ++d) {
-            h[i].c[d] = e.c[3 * i + d];
-            h[i].s1[d] = e.s1[3 * i + d];
-            h[i].s2[d] = e.s2[3 * i + d];
-            h[i].n[d] = e.n[3 * i + d];
-        }
-        h[i].a = e.a[i];
-        h[i].b = e.b[i];
-        h[i].pad[0] = h[i].pad[1] = 0.0;
-    }
+    for (int64_t i = 0; i < e.N; ++i) h[i] = make_elem_record(e, i);
     DevBuf<ElemRec> d_el;
     d_el.upload(h, st);
     DevBuf<int> d_err(1);

@@ -27,6 +27,7 @@ static void check_elements(const hm_elements* el) {
     if (!el) fail(HM_EINVAL, "NULL element description");
     if (el->N <= 0) fail(HM_EINVAL, "element count must be positive");
     if (!el->c || !el->s1 || !el->s2 || !el->n || !el->a || !el->b) fail(HM_EINVAL, "NULL geometry array");
+    validate_elements(*el, "elements");
 }
 
 }  // namespace hm

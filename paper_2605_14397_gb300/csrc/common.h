@@ -70,16 +70,18 @@ struct DevBuf {
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
-// Element record in cluster order on the device: one 128-byte line per element.
+// Element record in cluster order on the device (176 bytes).
 struct __align__(16) ElemRec {
     double c[3];
     double s1[3];
     double s2[3];
     double n[3];
-    double a, b;
-    double pad[2];
+    double a, b;    // rectangle: half sides along s1, s2; triangle: both sqrt(area) / 2
+    double tv[6];   // triangle: its vertices in the (s1, s2) frame about c
+    double shape;   // HM_SHAPE_RECT or HM_SHAPE_TRI
+    double area;
 };
-static_assert(sizeof(ElemRec) == 128, "ElemRec must be one 128-byte line");
+static_assert(sizeof(ElemRec) == 176, "ElemRec is eleven 16-byte words");
 
 }  // namespace hm
 

@@ -1,8 +1,8 @@
 // Device evaluation of one 3x3 influence block of the collocation DD matrix E.
 //
 // Block (i, j): traction at the centroid of element i (components on its frame
-// s1, s2, n) from a unit DD component constant over the rectangle of element j
-// (components on j's frame), full-space isotropic elasticity (Sec. 3.1,
+// s1, s2, n) from a unit DD component constant over element j -- a rectangle or a
+// triangle -- (components on j's frame), full-space isotropic elasticity (Sec. 3.1,
 // eq. TractionBIE-general reduced to the fracture integral; eq. ElasSystem).
 //
 // Formulation used here.  In source-local coordinates (source plane x3 = 0) the stress
@@ -91,6 +91,89 @@ __device__ __forceinline__ bool phi_corner_sums(double x1, double x2, double x3,
     return true;
 }
 
+// The same derivatives for a triangle (vertices tv in the source plane frame, x3 = 0).
+// Every derivative with an in-plane index alpha is, by Stokes' theorem, a sum over the
+// edges of line integrals (d = x - xi, n the outward in-plane normal of the edge):
+//   phi_{,alpha beta} = sum n_alpha int d_beta / R^3,
+//   phi_{,alpha beta gamma} = -sum n_alpha int (3 d_beta d_gamma / R^5 - delta / R^3).
+// Along an edge d = h + w tau, h perpendicular to the edge (in-plane part hp n and x3),
+// w running from wB = wA - L to wA, R^2 = rho^2 + w^2; the integrals are the closed
+// forms K3p = int w^p / R^3 and K5p = int w^p / R^5 written without 1/rho^2:
+//   K30 = (wA^2 - wB^2) / (RA RB (wA RB + wB RA)) when wA, wB have one sign (else
+//         (gA - gB) / rho^2, g = w / R), K31 = 1/RB - 1/RA, K51 = (1/RB^3 - 1/RA^3) / 3,
+//   K52 = K30 (gA^2 + gA gB + gB^2) / 3,
+//   K50 = K30 / 3 (1/RA^2 + 1/RB^2 + (1/RA^2 + 1/RB^2 - rho^2 / (RA RB)^2) / (1 + gA gB)),
+// the last from K50 = (K30 - K52) / rho^2 and 1 - gA gB = (1 - gA^2 gB^2) / (1 + gA gB).
+// The x3-x3 derivatives follow from Laplace's equation.  Returns false if the point
+// lies on an edge (in-plane, within tol).
+__device__ __forceinline__ bool phi_edge_sums(double x1, double x2, double x3, const double* tv, double tol,
+                                              PhiDerivs& D) {
+    const double o = (tv[2] - tv[0]) * (tv[5] - tv[1]) - (tv[3] - tv[1]) * (tv[4] - tv[0]);
+    const int v1 = o < 0.0 ? 2 : 1, v2 = o < 0.0 ? 1 : 2;  // counter-clockwise order
+    const double z = x3, z2 = z * z;
+    double s11 = 0, s22 = 0, s12 = 0, s13 = 0, s23 = 0;
+    double t111 = 0, t112 = 0, t122 = 0, t222 = 0, t113 = 0, t123 = 0, t223 = 0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int ia = e == 0 ? 0 : (e == 1 ? v1 : v2);
+        const int ib = e == 0 ? v1 : (e == 1 ? v2 : 0);
+        const double px = tv[2 * ia], py = tv[2 * ia + 1];
+        const double ex = tv[2 * ib] - px, ey = tv[2 * ib + 1] - py;
+        const double L = sqrt(ex * ex + ey * ey);
+        const double tx = ex / L, ty = ey / L;
+        const double nx = ty, ny = -tx;
+        const double dx = x1 - px, dy = x2 - py;
+        const double wA = dx * tx + dy * ty, wB = wA - L;
+        const double hp = dx * nx + dy * ny;
+        if (fabs(z) <= tol && fabs(hp) <= tol && wA >= -tol && wB <= tol) return false;
+        const double rho2 = hp * hp + z2;
+        const double RA = sqrt(rho2 + wA * wA), RB = sqrt(rho2 + wB * wB);
+        const double gA = wA / RA, gB = wB / RB;
+        const double K30 = wA * wB > 0.0 ? (wA * wA - wB * wB) / (RA * RB * (wA * RB + wB * RA)) : (gA - gB) / rho2;
+        const double iA2 = 1.0 / (RA * RA), iB2 = 1.0 / (RB * RB);
+        const double K31 = 1.0 / RB - 1.0 / RA;
+        const double K51 = (iB2 / RB - iA2 / RA) / 3.0;
+        const double K52 = K30 * (gA * gA + gA * gB + gB * gB) / 3.0;
+        const double K50 = K30 / 3.0 * (iA2 + iB2 + (iA2 + iB2 - rho2 * iA2 * iB2) / (1.0 + gA * gB));
+        const double h1 = hp * nx, h2 = hp * ny;
+        const double I1 = h1 * K30 + tx * K31, I2 = h2 * K30 + ty * K31, I3 = z * K30;
+        const double J11 = 3.0 * (h1 * h1 * K50 + 2.0 * h1 * tx * K51 + tx * tx * K52) - K30;
+        const double J12 = 3.0 * (h1 * h2 * K50 + (h1 * ty + h2 * tx) * K51 + tx * ty * K52);
+        const double J22 = 3.0 * (h2 * h2 * K50 + 2.0 * h2 * ty * K51 + ty * ty * K52) - K30;
+        const double J13 = 3.0 * z * (h1 * K50 + tx * K51);
+        const double J23 = 3.0 * z * (h2 * K50 + ty * K51);
+        s11 += nx * I1;
+        s12 += nx * I2;
+        s13 += nx * I3;
+        s22 += ny * I2;
+        s23 += ny * I3;
+        t111 -= nx * J11;
+        t112 -= nx * J12;
+        t122 -= nx * J22;
+        t222 -= ny * J22;
+        t113 -= nx * J13;
+        t123 -= nx * J23;
+        t223 -= ny * J23;
+    }
+    D.d11 = s11;
+    D.d22 = s22;
+    D.d33 = -(s11 + s22);
+    D.d12 = s12;
+    D.d13 = s13;
+    D.d23 = s23;
+    D.d111 = t111;
+    D.d222 = t222;
+    D.d112 = t112;
+    D.d122 = t122;
+    D.d113 = t113;
+    D.d223 = t223;
+    D.d123 = t123;
+    D.d133 = -(t111 + t122);
+    D.d233 = -(t112 + t222);
+    D.d333 = -(t113 + t223);
+    return true;
+}
+
 __device__ __forceinline__ double P2(const PhiDerivs& D, int i, int j) {
     // symmetric second-derivative lookup (indices are compile-time after unrolling)
     if (i > j) { int t = i; i = j; j = t; }
@@ -139,8 +222,9 @@ __device__ __forceinline__ bool dd_block(const ElemRec& Rr, const ElemRec& Ss, d
         q[al][2] = dot3(Ss.n, re[al]);
     }
     PhiDerivs D;
-    const double tol = 1e-9 * fmin(Ss.a, Ss.b);
-    if (!phi_corner_sums(x1, x2, x3, Ss.a, Ss.b, tol, D)) {
+    const bool ok = Ss.shape == HM_SHAPE_TRI ? phi_edge_sums(x1, x2, x3, Ss.tv, 1e-9 * sqrt(Ss.area), D)
+                                              : phi_corner_sums(x1, x2, x3, Ss.a, Ss.b, 1e-9 * fmin(Ss.a, Ss.b), D);
+    if (!ok) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) out[k] = __longlong_as_double(0x7ff8000000000000ULL);
         return false;

@@ -65,7 +65,10 @@ __device__ __forceinline__ void load_elem(const double* g, int64_t N, int64_t i,
     }
     r.a = a[i];
     r.b = b[i];
-    r.pad[0] = r.pad[1] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) r.tv[q] = 0.0;
+    r.shape = HM_SHAPE_RECT;
+    r.area = 4.0 * r.a * r.b;
 }
 
 // Same arithmetic as the allocating entry point; geometry read from the scratch array.
@@ -107,6 +110,9 @@ extern "C" hm_status hm_influence_blocks_noalloc(const hm_elements* el, double E
                             " elements exceed the fixed scratch limit of 65536 elements (use hm_influence_blocks)");
     if (!el->c || !el->s1 || !el->s2 || !el->n || !el->a || !el->b)
         fail(HM_EINVAL, "influence_blocks_noalloc: NULL geometry array");
+    if (el->shape)
+        for (int64_t i = 0; i < el->N; ++i)
+            if (el->shape[i] != HM_SHAPE_RECT) fail(HM_EINVAL, "influence_blocks_noalloc: rectangles only");
     if (npairs < 0) fail(HM_EINVAL, "influence_blocks_noalloc: npairs < 0");
     if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5))
         fail(HM_EINVAL, "influence_blocks_noalloc: need E > 0 and -1 < nu < 0.5");

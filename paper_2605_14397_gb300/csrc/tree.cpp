@@ -6,7 +6,8 @@
 //     bounding box of its centroids, at the median: elements ordered by (coordinate,
 //     user index), the first n/2 go to the left child;
 //   * nodes are numbered in depth-first pre-order;
-//   * cluster boxes bound the element vertices c +- a s1 +- b s2;
+//   * cluster boxes bound the element vertices: c +- a s1 +- b s2 of a rectangle, the
+//     three given vertices of a triangle;
 //   * (s, t) is admissible iff dist(B_s, B_t) > 0 and min(diam B_s, diam B_t) <=
 //     eta dist(B_s, B_t) (Euclidean diagonal and gap);
 //   * the block tree starts at (root, root); an admissible pair is a far block, a pair
@@ -15,6 +16,8 @@
 // This file is compiled with floating-point contraction disabled so that the box and
 // admissibility arithmetic is the plain IEEE sequence written here.
 #include "tree.h"
+
+#include <string>
 
 #include <algorithm>
 #include <cmath>
@@ -36,6 +39,15 @@ struct Builder {
         vlo.assign(N, {INFINITY, INFINITY, INFINITY});
         vhi.assign(N, {-INFINITY, -INFINITY, -INFINITY});
         for (int64_t i = 0; i < N; ++i) {
+            if (el.shape && el.shape[i] == HM_SHAPE_TRI) {
+                for (int v = 0; v < 3; ++v)
+                    for (int k = 0; k < 3; ++k) {
+                        const double x = el.tri[9 * i + 3 * v + k];
+                        vlo[i][k] = std::min(vlo[i][k], x);
+                        vhi[i][k] = std::max(vhi[i][k], x);
+                    }
+                continue;
+            }
             for (int ia = 0; ia < 2; ++ia) {
                 for (int ib = 0; ib < 2; ++ib) {
                     const double sa = ia ? 1.0 : -1.0, sb = ib ? 1.0 : -1.0;
@@ -115,18 +127,85 @@ double box_dist(const std::array<double, 3>& lo1, const std::array<double, 3>& h
 
 }  // namespace
 
+void validate_elements(const hm_elements& el, const char* who) {
+    const std::string w(who);
+    if (el.N <= 0) fail(HM_EINVAL, w + ": N must be positive");
+    if (!el.c || !el.s1 || !el.s2 || !el.n || !el.a || !el.b) fail(HM_EINVAL, w + ": NULL geometry");
+    bool any_tri = false;
+    for (int64_t i = 0; i < el.N; ++i) {
+        const int sh = el.shape ? el.shape[i] : HM_SHAPE_RECT;
+        if (sh != HM_SHAPE_RECT && sh != HM_SHAPE_TRI) fail(HM_EINVAL, w + ": unknown element shape");
+        any_tri = any_tri || sh == HM_SHAPE_TRI;
+        if (sh == HM_SHAPE_RECT && (!(el.a[i] > 0.0) || !(el.b[i] > 0.0)))
+            fail(HM_EINVAL, w + ": half sides must be positive");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(el.c[3 * i + k]) || !std::isfinite(el.n[3 * i + k]) ||
+                !std::isfinite(el.s1[3 * i + k]) || !std::isfinite(el.s2[3 * i + k]))
+                fail(HM_ENAN, w + ": non-finite geometry");
+    }
+    if (any_tri && !el.tri) fail(HM_EINVAL, w + ": triangles need their vertices (tri)");
+    for (int64_t i = 0; any_tri && i < el.N; ++i) {
+        if (el.shape[i] != HM_SHAPE_TRI) continue;
+        const double* v = el.tri + 9 * i;
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(v[k])) fail(HM_ENAN, w + ": non-finite triangle vertex");
+        const ElemRec r = make_elem_record(el, i);
+        const double size = std::sqrt(r.area);
+        if (!(r.area > 0.0)) fail(HM_EINVAL, w + ": degenerate triangle");
+        for (int q = 0; q < 3; ++q) {
+            double off = 0.0;
+            for (int k = 0; k < 3; ++k) off += (v[3 * q + k] - el.c[3 * i + k]) * el.n[3 * i + k];
+            if (std::fabs(off) > 1e-6 * size) fail(HM_EINVAL, w + ": a triangle vertex is off the plane of c and n");
+        }
+        // c inside: the three edge cross products have the orientation's sign
+        const double o = (r.tv[2] - r.tv[0]) * (r.tv[5] - r.tv[1]) - (r.tv[3] - r.tv[1]) * (r.tv[4] - r.tv[0]);
+        for (int e = 0; e < 3; ++e) {
+            const double* P = r.tv + 2 * e;
+            const double* Q = r.tv + 2 * ((e + 1) % 3);
+            const double cr = (Q[0] - P[0]) * (0.0 - P[1]) - (Q[1] - P[1]) * (0.0 - P[0]);
+            if (!(cr * o > 0.0)) fail(HM_EINVAL, w + ": the collocation point c lies outside its triangle");
+        }
+    }
+}
+
+ElemRec make_elem_record(const hm_elements& el, int64_t i) {
+    ElemRec r;
+    for (int d = 0; d < 3; ++d) {
+        r.c[d] = el.c[3 * i + d];
+        r.s1[d] = el.s1[3 * i + d];
+        r.s2[d] = el.s2[3 * i + d];
+        r.n[d] = el.n[3 * i + d];
+    }
+    for (double& t : r.tv) t = 0.0;
+    if (el.shape && el.shape[i] == HM_SHAPE_TRI) {
+        const double* v = el.tri + 9 * i;
+        for (int q = 0; q < 3; ++q) {
+            double x = 0.0, y = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double dv = v[3 * q + d] - r.c[d];
+                x += dv * r.s1[d];
+                y += dv * r.s2[d];
+            }
+            r.tv[2 * q] = x;
+            r.tv[2 * q + 1] = y;
+        }
+        r.area = 0.5 * std::fabs((r.tv[2] - r.tv[0]) * (r.tv[5] - r.tv[1]) - (r.tv[3] - r.tv[1]) * (r.tv[4] - r.tv[0]));
+        r.a = r.b = 0.5 * std::sqrt(r.area);
+        r.shape = HM_SHAPE_TRI;
+    } else {
+        r.a = el.a[i];
+        r.b = el.b[i];
+        r.area = 4.0 * r.a * r.b;
+        r.shape = HM_SHAPE_RECT;
+    }
+    return r;
+}
+
 void build_tree(const hm_elements& el, int leaf_size, double eta, Tree& T) {
     if (el.N <= 0) fail(HM_EINVAL, "build_cluster_tree: N must be positive");
     if (leaf_size < 1) fail(HM_EINVAL, "build_cluster_tree: leaf_size must be >= 1");
     if (!(eta > 0.0)) fail(HM_EINVAL, "build_cluster_tree: eta must be positive");
-    if (!el.c || !el.s1 || !el.s2 || !el.n || !el.a || !el.b) fail(HM_EINVAL, "build_cluster_tree: NULL geometry");
-    for (int64_t i = 0; i < el.N; ++i) {
-        if (!(el.a[i] > 0.0) || !(el.b[i] > 0.0)) fail(HM_EINVAL, "build_cluster_tree: half sides must be positive");
-        for (int k = 0; k < 3; ++k)
-            if (!std::isfinite(el.c[3 * i + k]) || !std::isfinite(el.n[3 * i + k]) ||
-                !std::isfinite(el.s1[3 * i + k]) || !std::isfinite(el.s2[3 * i + k]))
-                fail(HM_ENAN, "build_cluster_tree: non-finite geometry");
-    }
+    validate_elements(el, "build_cluster_tree");
     T = Tree();
     T.N = el.N;
     T.leaf_size = leaf_size;
@@ -177,17 +256,7 @@ void build_tree(const hm_elements& el, int leaf_size, double eta, Tree& T) {
     T.elems.resize(el.N);
     for (int64_t k = 0; k < el.N; ++k) {
         const int64_t i = T.perm[k];
-        ElemRec r;
-        for (int d = 0; d < 3; ++d) {
-            r.c[d] = el.c[3 * i + d];
-            r.s1[d] = el.s1[3 * i + d];
-            r.s2[d] = el.s2[3 * i + d];
-            r.n[d] = el.n[3 * i + d];
-        }
-        r.a = el.a[i];
-        r.b = el.b[i];
-        r.pad[0] = r.pad[1] = 0.0;
-        T.elems[k] = r;
+        T.elems[k] = make_elem_record(el, i);
     }
 }
 

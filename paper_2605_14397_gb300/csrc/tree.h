@@ -27,4 +27,11 @@ struct Tree {
 // Build the tree, the partition and the cluster-ordered element records.
 void build_tree(const hm_elements& el, int leaf_size, double eta, Tree& T);
 
+// Checks of the element description (shapes, finite values, half sides, triangles in
+// their plane around their collocation point); who names the caller in the message.
+void validate_elements(const hm_elements& el, const char* who);
+
+// Device record of user element i (frame, shape, the triangle's vertices in its frame).
+ElemRec make_elem_record(const hm_elements& el, int64_t i);
+
 }  // namespace hm

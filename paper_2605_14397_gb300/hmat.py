@@ -40,7 +40,8 @@ class HMError(RuntimeError):
 
 class hm_elements(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64)] + [(n, ctypes.POINTER(ctypes.c_double))
-                                           for n in ("c", "s1", "s2", "n", "a", "b")]
+                                           for n in ("c", "s1", "s2", "n", "a", "b")] + [
+        ("shape", ctypes.POINTER(ctypes.c_int32)), ("tri", ctypes.POINTER(ctypes.c_double))]
 
 
 class hm_tree_info(ctypes.Structure):
@@ -228,7 +229,15 @@ class _ElemArgs:
     def __init__(self, el):
         self.arrs = [np.ascontiguousarray(getattr(el, k), dtype=np.float64) for k in ("c", "s1", "s2", "n", "a", "b")]
         dp = ctypes.POINTER(ctypes.c_double)
-        self.s = hm_elements(el.N, *[a.ctypes.data_as(dp) for a in self.arrs])
+        ptrs = [a.ctypes.data_as(dp) for a in self.arrs]
+        shape = getattr(el, "shape", None)
+        if shape is not None and np.any(np.asarray(shape) != 0):
+            self.shape = np.ascontiguousarray(shape, dtype=np.int32)
+            self.tri = np.ascontiguousarray(el.tri, dtype=np.float64)
+            ptrs += [self.shape.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.tri.ctypes.data_as(dp)]
+        else:
+            ptrs += [None, None]
+        self.s = hm_elements(el.N, *ptrs)
 
     @property
     def ref(self):
@@ -609,6 +618,10 @@ def autotune_key(el, E, nu, aca_eps, storage, leaves, etas, device, shapes=()):
     h = hashlib.sha256()
     for k in ("c", "s1", "s2", "n", "a", "b"):
         h.update(np.ascontiguousarray(getattr(el, k), dtype=np.float64).tobytes())
+    shape = getattr(el, "shape", None)
+    if shape is not None and np.any(np.asarray(shape) != 0):  # triangles: their vertices too
+        h.update(np.ascontiguousarray(shape, dtype=np.int32).tobytes())
+        h.update(np.ascontiguousarray(el.tri, dtype=np.float64).tobytes())
     h.update(repr((int(el.N), float(E), float(nu), float(aca_eps), str(storage), tuple(int(v) for v in leaves),
                    tuple(float(v) for v in etas), str(device), tuple(tuple(int(x) for x in t) for t in shapes))).encode())
     return h.hexdigest()[:32]

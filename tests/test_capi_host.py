@@ -111,13 +111,22 @@ def test_autotune_cache_key_and_hit_without_device(tmp_path, monkeypatch):
     assert hmat.autotune(el, 1.0, 0.25, 1e-6, "f32", (32, 64), (2.0,), cache=str(cache), device="dev") == stored
 
 
+def _tri_and_rect():
+    """A triangulated disk crossed by a plane of rectangles (mixed shapes)."""
+    return synth.Elements.concat([synth.tri_disk_mesh(20),
+                                  synth.plane_grid(8, 6, -0.8, 0.8, -0.6, 0.6, (1, 0, 0), origin=(0.013, 0.0, 0.0),
+                                                   plane_id=1)])
+
+
 @pytest.mark.parametrize("which,leaf", [("penny", 64), ("penny", 16), ("planes", 32), ("fault", 64),
-                                        ("crackfault", 24)])
+                                        ("crackfault", 24), ("tripenny", 32), ("mixed", 16)])
 def test_tree_and_partition_bit_identical_to_oracle(L, which, leaf):
     el = {"penny": lambda: synth.config_penny(40),
           "planes": lambda: synth.config_three_planes(30),
           "fault": lambda: synth.config_fault(),
-          "crackfault": lambda: synth.config_crack_fault(h=0.1)}[which]()
+          "crackfault": lambda: synth.config_crack_fault(h=0.1),
+          "tripenny": lambda: synth.tri_disk_mesh(40),
+          "mixed": _tri_and_rect}[which]()
     T = hmat.ClusterTree(el, leaf, 2.0)
     ex = T.export()
     To = O.cluster_tree(el, leaf)
@@ -129,6 +138,43 @@ def test_tree_and_partition_bit_identical_to_oracle(L, which, leaf):
     assert np.array_equal(ex["far"], np.array(far).reshape(-1, 2))
     info = T.info()
     assert info["n_leaves"] == len(To.leaves())
+
+
+def test_triangle_geometry_checks(L):
+    """Triangles are validated on the host: vertices given, finite, non-degenerate, in the
+    plane of c and n, around c; the no-allocation entry point takes rectangles only."""
+    good = synth.tri_disk_mesh(6)
+    hmat.ClusterTree(good, 16, 2.0).close()
+
+    def status(el):
+        with pytest.raises(hmat.HMError) as ei:
+            hmat.ClusterTree(el, 16, 2.0)
+        return ei.value.status
+
+    def variant(fn):
+        el = good.subset(np.arange(good.N))
+        fn(el)
+        return el
+    assert status(variant(lambda e: e.tri.__setitem__((3, slice(3, 6)), e.tri[3, 0:3]))) == hmat.HM_EINVAL  # degenerate
+    assert status(variant(lambda e: e.tri.__setitem__((4, 2), e.tri[4, 2] + 0.1))) == hmat.HM_EINVAL  # off the plane
+    assert status(variant(lambda e: e.c.__setitem__(5, e.tri[5, 0:3] + 2 * (e.tri[5, 0:3] - e.c[5])))) == hmat.HM_EINVAL
+    assert status(variant(lambda e: e.tri.__setitem__((6, 1), np.nan))) == hmat.HM_ENAN
+    assert status(variant(lambda e: e.shape.__setitem__(7, 5))) == hmat.HM_EINVAL
+    # a triangle needs no half sides; a rectangle does
+    ok = variant(lambda e: e.a.__setitem__(2, -1.0))
+    hmat.ClusterTree(ok, 16, 2.0).close()
+    rect = synth.config_penny(6)
+    rect.a[0] = 0.0
+    assert status(rect) == hmat.HM_EINVAL
+    # the struct without vertices
+    ea = hmat._ElemArgs(good)
+    ea.s.tri = None
+    h = ctypes.c_void_p()
+    assert L.hm_build_cluster_tree(ea.ref, 16, 2.0, ctypes.byref(h)) == hmat.HM_EINVAL
+    # triangles to the no-allocation entry point: refused before any device work
+    ea = hmat._ElemArgs(good)
+    dummy = ctypes.c_void_p(16)
+    assert L.hm_influence_blocks_noalloc(ea.ref, 1.0, 0.25, 0, dummy, dummy, dummy, None) == hmat.HM_EINVAL
 
 
 def test_learned_model_host_side(tmp_path):

@@ -100,6 +100,7 @@ void hm_tree_destroy(hm_tree* t) { delete t; }
 hm_status hm_assemble_hmat(const hm_tree* t, const hm_elements* el, const hm_assemble_opts* opt, void* stream,
                            hm_hmat** out) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_assemble_hmat");
     hm::g_last_error.clear();
     if (!out) hm::fail(HM_EINVAL, "assemble_hmat: NULL output handle");
     *out = nullptr;
@@ -174,6 +175,7 @@ void hm_hmat_destroy(hm_hmat* h) { delete h; }
 
 hm_status hm_matvec(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs, int dtype, void* stream) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_matvec");
     if (!hh) hm::fail(HM_EINVAL, "matvec: NULL H-matrix");
     if (x_dev == y_dev) hm::fail(HM_EINVAL, "matvec: x and y must not overlap");
     hm::matvec(const_cast<hm::HMat&>(hh->h), x_dev, y_dev, nrhs, dtype, (cudaStream_t)stream);
@@ -183,6 +185,7 @@ hm_status hm_matvec(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs,
 hm_status hm_matvec_factors(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs, int dtype, int factors,
                             void* stream) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_matvec_factors");
     if (!hh) hm::fail(HM_EINVAL, "matvec_factors: NULL H-matrix");
     if (x_dev == y_dev) hm::fail(HM_EINVAL, "matvec_factors: x and y must not overlap");
     hm::matvec(const_cast<hm::HMat&>(hh->h), x_dev, y_dev, nrhs, dtype, (cudaStream_t)stream, factors);
@@ -191,6 +194,7 @@ hm_status hm_matvec_factors(const hm_hmat* hh, const void* x_dev, void* y_dev, i
 
 hm_status hm_matvec_host(const hm_hmat* hh, const void* x_host, void* y_host, int nrhs, int dtype, void* stream) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_matvec_host");
     if (!hh) hm::fail(HM_EINVAL, "matvec_host: NULL H-matrix");
     if (x_host == y_host) hm::fail(HM_EINVAL, "matvec_host: x and y must not overlap");
     hm::matvec_host(const_cast<hm::HMat&>(hh->h), x_host, y_host, nrhs, dtype, (cudaStream_t)stream);
@@ -214,6 +218,7 @@ hm_status hm_hmat_timing_read(const hm_hmat* hh, double* out6) {
 hm_status hm_gmres_solve(const hm_hmat* hh, const double* k_dev, double shift, const double* b_dev, double* x_dev,
                          int nrhs, const hm_solve_opts* opt, hm_solve_info* info, void* stream) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_gmres_solve");
     hm::g_last_error.clear();
     if (!hh) hm::fail(HM_EINVAL, "gmres_solve: NULL H-matrix");
     hm_solve_opts o{};
@@ -283,6 +288,7 @@ hm_status hm_batch_create(const hm_hmat* const* hs, int nf, void* stream, hm_hma
 
 hm_status hm_matvec_graph(const hm_hmat* hh, const void* x_dev, void* y_dev, int nrhs, int dtype, void* stream) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_matvec_graph");
     if (!hh) hm::fail(HM_EINVAL, "matvec_graph: NULL H-matrix");
     if (!x_dev || !y_dev) hm::fail(HM_EINVAL, "matvec_graph: NULL vector");
     if (x_dev == y_dev) hm::fail(HM_EINVAL, "matvec_graph: x and y must not overlap");

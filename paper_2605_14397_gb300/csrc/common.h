@@ -10,9 +10,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hmat.h"
 
 namespace hm {
+
+// Scoped NVTX range: names the library's phases (assembly, products, solves, GMRES
+// cycles) on a profiler's timeline; NVTX is header-only and costs a few nanoseconds
+// when no tool is attached.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
 
 // Exception carrying an hm_status; converted to a return code at the C boundary.
 struct Error : public std::runtime_error {

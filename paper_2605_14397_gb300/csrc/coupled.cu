@@ -676,6 +676,7 @@ extern "C" hm_status hm_coupled_solve(const hm_hmat* h, const hm_flow* f, const 
                                       const double* cep_dev, double shift, const double* b_dev, double* x_dev,
                                       const hm_coupled_opts* opt, hm_coupled_info* info, void* stream) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_coupled_solve");
     if (!h || !f) hm::fail(HM_EINVAL, "coupled_solve: NULL argument");
     if (!std::isfinite(shift)) hm::fail(HM_ENAN, "coupled_solve: shift is not finite");
     hm_coupled_opts o{};

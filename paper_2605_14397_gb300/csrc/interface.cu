@@ -640,6 +640,7 @@ extern "C" hm_status hm_interface_update(const hm_interface_params* prm, int64_t
                                          int32_t* mode_dev, int64_t* counts, void* stream) {
     using namespace hm;
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_interface_update");
     if (!prm) fail(HM_EINVAL, "interface_update: params is NULL");
     if (n < 0) fail(HM_EINVAL, "interface_update: n < 0");
     const hm_interface_params& q = *prm;

@@ -609,6 +609,7 @@ hm_status hm_lp_loss_grad(hm_lp* lp, double* loss_out, double* grad_out, void* s
 
 hm_status hm_lp_train(hm_lp* lp, int steps, double lr, double* loss_out, void* stream) {
     HM_API_BEGIN
+    hm::NvtxScope nvtx_("hm_lp_train");
     hm::LPModel& M = model(lp);
     if (steps < 1) hm::fail(HM_EINVAL, "lp_train: steps must be >= 1");
     if (!(lr > 0.0) || !std::isfinite(lr)) hm::fail(HM_EINVAL, "lp_train: learning rate must be positive");

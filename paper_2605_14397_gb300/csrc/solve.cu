@@ -1314,6 +1314,7 @@ void precond_apply(HMat& H, SolveWS& W, PcKind pc, const double* v, double* z, f
 
 CycleResult fgmres_cycle(HMat& H, SolveWS& W, const double* beta_h, const double* tol_abs, const int* active_h,
                          int nr, int m, int dtype, int fac, PcKind pc, cudaStream_t st) {
+    NvtxScope nvtx_("fgmres_cycle");
     const int64_t n = H.ndof;
     const int nb = nblk_rows(n);
     std::vector<CycleState> cs(nr);
@@ -1446,6 +1447,7 @@ void fgmres(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& t
 void bicgstab(HMat& H, SolveWS& W, const double* rhs, const std::vector<double>& tol_abs, int nr, int max_its,
               int max_runs, int dtype, int fac, PcKind pc, std::vector<int>& its, std::vector<double>& rn,
               std::vector<int>& brk, cudaStream_t st, bool x_zero) {
+    NvtxScope nvtx_("bicgstab");
     const int64_t n = H.ndof, vn = n * nr;
     const int nb = nblk_rows(n);
     if (W.bcg.n < (size_t)(7 * vn + VSLACK)) W.bcg.alloc((size_t)(7 * vn + VSLACK));
@@ -1720,6 +1722,7 @@ void ilu_apply_user(HMat& H, const double* r, double* z, int nrhs, cudaStream_t 
 // already built for the same inputs when the options ask to reuse it
 void build_precond(HMat& H, SolveWS& W, const double* kel, const double* cep, double shift, const hm_solve_opts& o,
                    PcKind pc, double ilu_p, const LPModel* lp, int nrhs, cudaStream_t st) {
+    NvtxScope nvtx_("build_precond");
     SolveWS::PcKey key;
     key.valid = true;
     key.kel = kel;

@@ -306,15 +306,21 @@ def interface_states(n, seed, open_fraction=0.1):
 
 
 def node_connectivity(el: Elements, rel_tol=1e-9):
-    """Vertex nodes of the rectangles: one node per distinct vertex position (positions
+    """Vertex nodes of the elements: one node per distinct vertex position (positions
     closer than rel_tol times the largest half side are one node).  Returns conn (N, 4)
-    int32 -- the element's vertices in the order (-a, -b), (+a, -b), (+a, +b), (-a, +b)
-    of its (s1, s2) frame -- and the node count."""
+    int32 -- a rectangle's vertices in the order (-a, -b), (+a, -b), (+a, +b), (-a, +b)
+    of its (s1, s2) frame, a triangle's three vertices in their given order and -1 --
+    and the node count."""
     sg = np.array([[-1, -1], [1, -1], [1, 1], [-1, 1]], dtype=np.float64)
     V = (el.c[:, None, :] + sg[None, :, 0:1] * el.a[:, None, None] * el.s1[:, None, :]
          + sg[None, :, 1:2] * el.b[:, None, None] * el.s2[:, None, :])
+    tri = np.asarray(el.shape) == 1
+    V[tri, :3] = np.asarray(el.tri)[tri].reshape(-1, 3, 3)
     q = max(float(el.a.max()), float(el.b.max())) * rel_tol
-    keys = np.round(V.reshape(-1, 3) / q).astype(np.int64)
+    keep = np.ones((el.N, 4), dtype=bool)
+    keep[tri, 3] = False
+    keys = np.round(V[keep] / q).astype(np.int64)
     _, inv = np.unique(keys, axis=0, return_inverse=True)
-    conn = inv.reshape(el.N, 4).astype(np.int32)
+    conn = np.full((el.N, 4), -1, dtype=np.int32)
+    conn[keep] = inv.ravel()
     return np.ascontiguousarray(conn), int(inv.max()) + 1

@@ -709,7 +709,9 @@ def run_triangles(args, dev, torch, hmat, synth):
     eta 2, eps 1e-6, FP32 + BF16 factors: assembly time and blocks per second, the FP32
     product (F32 vectors) against the HBM peak, and GMRES time to 1e-8 under a uniform
     unit pressure (leaf block-Jacobi, plain FP64 and mixed BF16 + FP64 refinement) with
-    the error of the opening against Sneddon's solution."""
+    the error of the opening against Sneddon's solution; and the coupled hydro-mechanical
+    Jacobian solve on it with linear pressure on the triangles (the state and right-hand
+    side recipe of the coupled workload, h = 2/180)."""
     import numpy as np
     el = synth.tri_disk_mesh(180)
     t0 = time.perf_counter()
@@ -757,6 +759,28 @@ def run_triangles(args, dev, torch, hmat, synth):
         opening = xs.cpu().numpy().reshape(-1, 3)[:, 2]
         gm[mode] = {"seconds": min(times), "iters": inf["iters"], "relres": inf["relres"],
                     "sneddon_rel_error": float(np.linalg.norm(opening - exact) / np.linalg.norm(exact))}
+    conn, nn = synth.node_connectivity(el)
+    h = 2.0 / 180
+    fl = hmat.Flow(conn, nn, el.a, el.b, el.shape, el.tri)
+    rng = np.random.default_rng(1609)
+    fl.assemble(dict(mu=0.8, M=4.0, w0=0.25 * h, dt=0.1), torch.as_tensor(rng.uniform(0.0, 0.25 * h, el.N), device=dev),
+                torch.as_tensor(rng.normal(size=nn) * 0.1, device=dev), torch.as_tensor(rng.normal(size=nn) * 0.1, device=dev))
+    kc = torch.as_tensor(np.exp(rng.uniform(np.log(1e-2), np.log(1e1), size=el.N)) / h, device=dev)
+    xstar = torch.as_tensor(rng.normal(size=3 * el.N + nn), device=dev)
+    bc = torch.empty_like(xstar)
+    fl.matvec(H, xstar, bc, kc, shift=0.3 / h)
+    xc = torch.zeros_like(bc)
+    fl.solve(H, bc, xc, kc, shift=0.3 / h, raise_on_error=False)
+    ct = []
+    for _ in range(2):
+        xc.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        cinf = fl.solve(H, bc, xc, kc, shift=0.3 / h, raise_on_error=False)
+        torch.cuda.synchronize()
+        ct.append(time.perf_counter() - t1)
+    coupled = {**cinf, "seconds": min(ct), "pressure_nodes": nn,
+               "rel_error_vs_xstar": float(torch.linalg.norm(xc - xstar) / torch.linalg.norm(xstar))}
     line = {"metric": "H-matrix product of triangular elements, effective HBM bandwidth", "unit": "GB/s",
             "value": B / (ms * 1e-3) / 1e9, "ms_per_product": ms, "n_gpus": 1, "steps": steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -764,7 +788,7 @@ def run_triangles(args, dev, torch, hmat, synth):
             "config": {"workload": "triangulated disk fault 180x180 lattice: N=%d triangles" % el.N,
                        "setup_s": setup, "stored_bytes": B, "algorithmic_bytes_per_product": B,
                        "hbm_peak_gbs": hbm, "peak_source": peak_kind},
-            "frac_of_hbm": B / (ms * 1e-3) / 1e9 / hbm, "gmres_uniform_pressure": gm,
+            "frac_of_hbm": B / (ms * 1e-3) / 1e9 / hbm, "gmres_uniform_pressure": gm, "coupled_solve": coupled,
             "assembly": {"seconds": info["assemble_seconds"], "coeff_blocks": info["coeff_blocks"],
                          "blocks_per_s": info["coeff_blocks"] / info["assemble_seconds"],
                          "rank_mean": info["rank_mean"], "rank_max": info["rank_max"]}}

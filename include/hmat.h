@@ -359,8 +359,8 @@ hm_status hm_ilu_apply(const hm_hmat* h, const double* r_dev, double* z_dev, int
  *   r_f = V Delta delta_n + (S + dt L) Delta p + dt L (p^n - p^o) - dt f_f.
  * The Jacobian of [r_m; r_f] in [Delta delta (3N, user order); Delta p (nodes)]:
  *   A11 = E - diag(k) - C^ep - shift I (shift = eta/dt), A12 = N_p (the mean of an
- *   element's nodal pressures on its normal row: the bilinear value at the collocation
- *   point), A21 = d r_f / d Delta delta (only the normal DD: V^e + m^e Delta p^e / M +
+ *   element's nodal pressures on its normal row: the interpolated value at the
+ *   centroid), A21 = d r_f / d Delta delta (only the normal DD: V^e + m^e Delta p^e / M +
  *   dt (3 w^2 / 12 mu) k^e (Delta p^e + p^n,e - p^o,e) per element), A22 = S + dt L.
  * No-flux outer boundary; the flow is the same on every plane (no matrix permeability). */
 typedef struct hm_flow hm_flow;
@@ -378,6 +378,18 @@ typedef struct {
  * element or a non-positive half side. */
 hm_status hm_flow_create(int64_t N, const int32_t* conn, int64_t n_nodes, const double* a, const double* b,
                          hm_flow** out);
+/* The same for a mesh of rectangles (bilinear pressure) and triangles (linear pressure,
+ * the paper's elements, Sec. 3.2): shape (host, N; NULL: all rectangles) HM_SHAPE_RECT /
+ * HM_SHAPE_TRI; conn (host, N x 4): a rectangle's four nodes as above, a triangle's
+ * three nodes in the order of its vertices and -1; a, b the rectangles' half sides (the
+ * entries of triangles unread); tri (host, N x 9; NULL if no triangle) the triangles'
+ * global vertices, in the order of their nodes.  Element matrices are computed here:
+ * closed forms of the bilinear rectangle, and for a triangle of area A the mass
+ * A/12 (1 + delta_ij), the load A/3 and the stiffness (e_i . e_j) / (4 A), e_i the edge
+ * opposite node i.  HM_EINVAL also for a degenerate triangle or a triangle without -1 in
+ * its fourth slot; HM_ENAN for a non-finite vertex. */
+hm_status hm_flow_create_mesh(int64_t N, const int32_t* shape, const int32_t* conn, int64_t n_nodes,
+                              const double* a, const double* b, const double* tri, hm_flow** out);
 void hm_flow_destroy(hm_flow* f);
 /* The flow blocks at the current iterate (device arrays): dn_dev (N) delta_n at t^(n+1),
  * dp_dev (n_nodes) Delta p, pn_dev (n_nodes) p^n - p^o (either may be NULL: zero).
@@ -386,7 +398,8 @@ hm_status hm_flow_assemble(hm_flow* f, const hm_flow_params* prm, const double* 
                            const double* pn_dev, void* stream);
 /* To host arrays (any may be NULL): nnz_out; rowptr[n_nodes + 1], col[nnz] the node
  * pattern (columns increasing); a22[nnz] = S + dt L; a21[4N]: A21's column of every
- * element's normal DD, on its four nodes in connectivity order.  Synchronises. */
+ * element's normal DD, on its nodes in connectivity order (a triangle's fourth entry is
+ * 0).  Synchronises. */
 hm_status hm_flow_export(const hm_flow* f, int64_t* nnz_out, int64_t* rowptr, int32_t* col, double* a22,
                          double* a21, void* stream);
 /* y = J x for x, y of length 3N + n_nodes (device; A11 by the compensated FP64 product

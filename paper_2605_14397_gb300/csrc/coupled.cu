@@ -37,6 +37,9 @@ struct hm_flow {
     hm::DevBuf<int64_t> rowptr, cptr, nptr;
     hm::DevBuf<uint8_t> cij, nloc;
     hm::DevBuf<double> a, b, a22, a21, ecoef;
+    // per element: mass m (4 x 4), stiffness k (4 x 4) and load v (4), row-major; a
+    // triangle (conn[4e + 3] = -1) fills the leading 3 x 3 and 3
+    hm::DevBuf<double> emat;
     bool assembled = false;
 };
 
@@ -46,62 +49,61 @@ namespace {
 constexpr int NT = 256;
 inline unsigned gsz(int64_t n) { return (unsigned)std::max<int64_t>(1, ceil_div(n, NT)); }
 
-// closed-form element matrices of the bilinear rectangle (local order (-,-), (+,-), (+,+), (-,+))
-__device__ __forceinline__ double mass_ij(double a, double b, int i, int j) {
-    // A/36 times 4 on the diagonal, 2 along an edge, 1 across the diagonal
-    const int d = (i - j + 4) & 3;
-    const double w = d == 0 ? 4.0 : (d == 2 ? 1.0 : 2.0);
-    return 4.0 * a * b / 36.0 * w;
-}
-__device__ __forceinline__ double stiff_ij(double a, double b, int i, int j) {
-    const double xi[4] = {-1.0, 1.0, 1.0, -1.0}, et[4] = {-1.0, -1.0, 1.0, 1.0};
-    // (b/a)/12 xi_i xi_j (3 + eta_i eta_j) + (a/b)/12 eta_i eta_j (3 + xi_i xi_j)
-    const double xx = xi[i] * xi[j], ee = et[i] * et[j];
-    return (b / a) / 12.0 * xx * (3.0 + ee) + (a / b) / 12.0 * ee * (3.0 + xx);
+// nodes of element e: 4 (rectangle) or 3 (triangle: -1 in the fourth slot)
+__device__ __forceinline__ int nodes_of(const int32_t* __restrict__ conn, int64_t e) {
+    return conn[4 * e + 3] < 0 ? 3 : 4;
 }
 
 // per element: storage and conductance coefficients, and A21's column
 //   A21[:, e] = v^e + m^e dp^e / M + dt c'(w) k^e (dp^e + pn^e),  c(w) = w^3 / (12 mu)
-__global__ void k_flow_elem(int64_t N, const int32_t* __restrict__ conn, const double* __restrict__ a,
-                            const double* __restrict__ b, const double* __restrict__ dn,
-                            const double* __restrict__ dp, const double* __restrict__ pn, double mu, double M,
-                            double w0, double dt, double* __restrict__ ecoef, double* __restrict__ a21) {
+__global__ void k_flow_elem(int64_t N, const int32_t* __restrict__ conn, const double* __restrict__ emat,
+                            const double* __restrict__ dn, const double* __restrict__ dp,
+                            const double* __restrict__ pn, double mu, double M, double w0, double dt,
+                            double* __restrict__ ecoef, double* __restrict__ a21) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N) return;
-    const double ae = a[e], be = b[e], w = w0 + dn[e];
+    const int nv = nodes_of(conn, e);
+    const double* m = emat + 36 * e;
+    const double* k = m + 16;
+    const double* v = m + 32;
+    const double w = w0 + dn[e];
     ecoef[2 * e] = w / M;
     ecoef[2 * e + 1] = dt * w * w * w / (12.0 * mu);
     const double dc = dt * 3.0 * w * w / (12.0 * mu);
     double q[4], u[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int nd = conn[4 * e + i];
-        q[i] = dp ? dp[nd] : 0.0;
-        u[i] = q[i] + (pn ? pn[nd] : 0.0);
+        const int nd = i < nv ? conn[4 * e + i] : -1;
+        q[i] = (nd >= 0 && dp) ? dp[nd] : 0.0;
+        u[i] = q[i] + ((nd >= 0 && pn) ? pn[nd] : 0.0);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        double s = ae * be;  // int N_i dS = A / 4
+        double s = 0.0;
+        if (i < nv) {
+            s = v[i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) s += mass_ij(ae, be, i, j) * q[j] / M + dc * stiff_ij(ae, be, i, j) * u[j];
+            for (int j = 0; j < 4; ++j) s += m[4 * i + j] * q[j] / M + dc * k[4 * i + j] * u[j];
+        }
         a21[4 * e + i] = s;
     }
 }
 
 // A22 (or S~ with dsub) entry by entry: the listed element contributions in order;
-// S~ subtracts A21[i, e] (1/4) / d_e for every element pair entry
+// S~ subtracts A21[i, e] N_p / d_e for every element pair entry (N_p = 1 / nodes)
 __global__ void k_flow_gather(int64_t nnz, const int64_t* __restrict__ cptr, const int32_t* __restrict__ cel,
-                              const uint8_t* __restrict__ cij, const double* __restrict__ a,
-                              const double* __restrict__ b, const double* __restrict__ ecoef,
+                              const uint8_t* __restrict__ cij, const int32_t* __restrict__ conn,
+                              const double* __restrict__ emat, const double* __restrict__ ecoef,
                               const double* __restrict__ a21, const double* __restrict__ dinv,
                               double* __restrict__ out) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nnz) return;
     double s = 0.0;
     for (int64_t t = cptr[q]; t < cptr[q + 1]; ++t) {
-        const int e = cel[t], i = cij[t] >> 2, j = cij[t] & 3;
-        s += ecoef[2 * e] * mass_ij(a[e], b[e], i, j) + ecoef[2 * e + 1] * stiff_ij(a[e], b[e], i, j);
-        if (dinv) s -= a21[4 * (int64_t)e + i] * 0.25 * dinv[e];
+        const int64_t e = cel[t];
+        const int i = cij[t] >> 2, j = cij[t] & 3;
+        s += ecoef[2 * e] * emat[36 * e + 4 * i + j] + ecoef[2 * e + 1] * emat[36 * e + 16 + 4 * i + j];
+        if (dinv) s -= a21[4 * e + i] * (1.0 / nodes_of(conn, e)) * dinv[e];
     }
     out[q] = s;
 }
@@ -124,13 +126,15 @@ __global__ void k_flow_rows(int64_t nn, const int64_t* __restrict__ rowptr, cons
     y2[r] = s;
 }
 
-// y1[3e + 2] += sgn * (1/4) sum_i x2[conn[e][i]]  (A12 = N_p)
+// y1[3e + 2] += sgn * (1 / nodes) sum_i x2[conn[e][i]]  (A12 = N_p)
 __global__ void k_np_add(int64_t N, const int32_t* __restrict__ conn, const double* __restrict__ x2, double sgn,
                          double* __restrict__ y1) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N) return;
-    const double s = x2[conn[4 * e]] + x2[conn[4 * e + 1]] + x2[conn[4 * e + 2]] + x2[conn[4 * e + 3]];
-    y1[3 * e + 2] += sgn * 0.25 * s;
+    const int nv = nodes_of(conn, e);
+    double s = x2[conn[4 * e]] + x2[conn[4 * e + 1]] + x2[conn[4 * e + 2]];
+    if (nv == 4) s += x2[conn[4 * e + 3]];
+    y1[3 * e + 2] += sgn * s / nv;
 }
 
 __global__ void k_normal_inv(int64_t N, const double* __restrict__ diag, double* __restrict__ dinv,
@@ -208,13 +212,13 @@ void flow_assemble(hm_flow& F, const hm_flow_params& p, const double* dn, const 
         fail(HM_EINVAL, "flow_assemble: mu, M, dt must be > 0 and w0 >= 0, all finite");
     if (!dn) fail(HM_EINVAL, "flow_assemble: NULL normal DD");
     if (F.N > 0) {
-        k_flow_elem<<<gsz(F.N), NT, 0, st>>>(F.N, F.conn.p, F.a.p, F.b.p, dn, dp, pn, p.mu, p.M, p.w0, p.dt,
+        k_flow_elem<<<gsz(F.N), NT, 0, st>>>(F.N, F.conn.p, F.emat.p, dn, dp, pn, p.mu, p.M, p.w0, p.dt,
                                              F.ecoef.p, F.a21.p);
         HM_LAUNCH_CHECK();
     }
     if (F.nnz > 0) {
-        k_flow_gather<<<gsz(F.nnz), NT, 0, st>>>(F.nnz, F.cptr.p, F.cel.p, F.cij.p, F.a.p, F.b.p, F.ecoef.p,
-                                                 F.a21.p, nullptr, F.a22.p);
+        k_flow_gather<<<gsz(F.nnz), NT, 0, st>>>(F.nnz, F.cptr.p, F.cel.p, F.cij.p, F.conn.p, F.emat.p,
+                                                 F.ecoef.p, F.a21.p, nullptr, F.a22.p);
         HM_LAUNCH_CHECK();
     }
     F.assembled = true;
@@ -420,7 +424,7 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
     HM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
     tangent_diag_user(H, kel, cep, shift, diag.p, st);
     k_normal_inv<<<gsz(F.N), NT, 0, st>>>(F.N, diag.p, dinv.p, bad.p);
-    k_flow_gather<<<gsz(F.nnz), NT, 0, st>>>(F.nnz, F.cptr.p, F.cel.p, F.cij.p, F.a.p, F.b.p, F.ecoef.p, F.a21.p,
+    k_flow_gather<<<gsz(F.nnz), NT, 0, st>>>(F.nnz, F.cptr.p, F.cel.p, F.cij.p, F.conn.p, F.emat.p, F.ecoef.p, F.a21.p,
                                              dinv.p, sval.p);
     k_diag_of<<<gsz(n2), NT, 0, st>>>(n2, F.rowptr.p, F.col.p, sval.p, sdinv.p, bad.p);
     HM_LAUNCH_CHECK();
@@ -546,32 +550,95 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
 
 // ---------------------------------------------------------------- C ABI
 
+namespace hm {
+namespace {
+
+// element matrices on the host (row-major m, k, v of 16, 16, 4 entries): the closed
+// forms of the bilinear rectangle (nodes (-a,-b), (+a,-b), (+a,+b), (-a,+b)) and of the
+// linear triangle (mass A/12 (1 + delta), load A/3, stiffness e_i . e_j / (4 A) with e_i
+// the edge opposite node i)
+void rect_matrices(double a, double b, double* T) {
+    const double xi[4] = {-1.0, 1.0, 1.0, -1.0}, et[4] = {-1.0, -1.0, 1.0, 1.0};
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            const int d = (i - j + 4) & 3;  // 4 on the diagonal, 2 along an edge, 1 across
+            T[4 * i + j] = 4.0 * a * b / 36.0 * (d == 0 ? 4.0 : (d == 2 ? 1.0 : 2.0));
+            const double xx = xi[i] * xi[j], ee = et[i] * et[j];
+            T[16 + 4 * i + j] = (b / a) / 12.0 * xx * (3.0 + ee) + (a / b) / 12.0 * ee * (3.0 + xx);
+        }
+        T[32 + i] = a * b;
+    }
+}
+
+double tri_matrices(const double* P, double* T) {
+    double e[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int d = 0; d < 3; ++d) e[i][d] = P[3 * ((i + 2) % 3) + d] - P[3 * ((i + 1) % 3) + d];
+    // twice the area: |e_2 x e_0| (e_2 = P1 - P0, e_0 = P2 - P1)
+    const double cx = e[2][1] * e[0][2] - e[2][2] * e[0][1], cy = e[2][2] * e[0][0] - e[2][0] * e[0][2],
+                 cz = e[2][0] * e[0][1] - e[2][1] * e[0][0];
+    const double A = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    for (int q = 0; q < 36; ++q) T[q] = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            T[4 * i + j] = A / 12.0 * (i == j ? 2.0 : 1.0);
+            T[16 + 4 * i + j] = (e[i][0] * e[j][0] + e[i][1] * e[j][1] + e[i][2] * e[j][2]) / (4.0 * A);
+        }
+        T[32 + i] = A / 3.0;
+    }
+    return A;
+}
+
+}  // namespace
+}  // namespace hm
+
 extern "C" hm_status hm_flow_create(int64_t N, const int32_t* conn, int64_t n_nodes, const double* a,
                                     const double* b, hm_flow** out) {
+    return hm_flow_create_mesh(N, nullptr, conn, n_nodes, a, b, nullptr, out);
+}
+
+extern "C" hm_status hm_flow_create_mesh(int64_t N, const int32_t* shape, const int32_t* conn, int64_t n_nodes,
+                                         const double* a, const double* b, const double* tri, hm_flow** out) {
     using namespace hm;
     HM_API_BEGIN
     if (!out) fail(HM_EINVAL, "flow_create: NULL output");
     *out = nullptr;
     if (N <= 0 || n_nodes <= 0 || !conn || !a || !b) fail(HM_EINVAL, "flow_create: empty mesh or NULL array");
     if (n_nodes > INT32_MAX || N > INT32_MAX) fail(HM_EINVAL, "flow_create: mesh too large");
-    for (int64_t q = 0; q < 4 * N; ++q)
-        if (conn[q] < 0 || conn[q] >= n_nodes) fail(HM_EINVAL, "flow_create: node index out of range");
+    std::vector<double> emat((size_t)36 * N);
+    std::vector<int> nv(N);
     for (int64_t e = 0; e < N; ++e) {
-        if (!(a[e] > 0.0) || !(b[e] > 0.0) || !std::isfinite(a[e]) || !std::isfinite(b[e]))
-            fail(HM_EINVAL, "flow_create: half sides must be finite and > 0");
-        for (int i = 0; i < 4; ++i)
-            for (int j = i + 1; j < 4; ++j)
+        const int sh = shape ? shape[e] : HM_SHAPE_RECT;
+        if (sh != HM_SHAPE_RECT && sh != HM_SHAPE_TRI) fail(HM_EINVAL, "flow_create: unknown element shape");
+        nv[e] = sh == HM_SHAPE_TRI ? 3 : 4;
+        if (sh == HM_SHAPE_TRI && conn[4 * e + 3] != -1)
+            fail(HM_EINVAL, "flow_create: a triangle's fourth node slot must be -1");
+        for (int i = 0; i < nv[e]; ++i)
+            if (conn[4 * e + i] < 0 || conn[4 * e + i] >= n_nodes) fail(HM_EINVAL, "flow_create: node index out of range");
+        for (int i = 0; i < nv[e]; ++i)
+            for (int j = i + 1; j < nv[e]; ++j)
                 if (conn[4 * e + i] == conn[4 * e + j]) fail(HM_EINVAL, "flow_create: an element repeats a node");
+        if (sh == HM_SHAPE_RECT) {
+            if (!(a[e] > 0.0) || !(b[e] > 0.0) || !std::isfinite(a[e]) || !std::isfinite(b[e]))
+                fail(HM_EINVAL, "flow_create: half sides must be finite and > 0");
+            rect_matrices(a[e], b[e], emat.data() + 36 * e);
+        } else {
+            if (!tri) fail(HM_EINVAL, "flow_create: triangles need their vertices (tri)");
+            for (int q = 0; q < 9; ++q)
+                if (!std::isfinite(tri[9 * e + q])) fail(HM_ENAN, "flow_create: non-finite triangle vertex");
+            const double A = tri_matrices(tri + 9 * e, emat.data() + 36 * e);
+            if (!(A > 0.0)) fail(HM_EINVAL, "flow_create: degenerate triangle");
+        }
     }
     auto F = std::make_unique<hm_flow>();
     F->N = N;
     F->nn = n_nodes;
     F->h_conn.assign(conn, conn + 4 * N);
-    // node-node pattern (the 4 x 4 blocks of the elements), columns increasing
+    // node-node pattern (the blocks of the elements), columns increasing
     std::vector<std::vector<int32_t>> adj(n_nodes);
     for (int64_t e = 0; e < N; ++e)
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) adj[conn[4 * e + i]].push_back(conn[4 * e + j]);
+        for (int i = 0; i < nv[e]; ++i)
+            for (int j = 0; j < nv[e]; ++j) adj[conn[4 * e + i]].push_back(conn[4 * e + j]);
     std::vector<int64_t> rp(n_nodes + 1, 0);
     std::vector<int32_t> cl;
     for (int64_t r = 0; r < n_nodes; ++r) {
@@ -586,10 +653,10 @@ extern "C" hm_status hm_flow_create(int64_t N, const int32_t* conn, int64_t n_no
     std::vector<std::vector<std::pair<int32_t, uint8_t>>> con(nnz);
     std::vector<std::vector<std::pair<int32_t, uint8_t>>> nodal(n_nodes);
     for (int64_t e = 0; e < N; ++e)
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < nv[e]; ++i) {
             const int32_t r = conn[4 * e + i];
             nodal[r].push_back({(int32_t)e, (uint8_t)i});
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < nv[e]; ++j) {
                 const int32_t c = conn[4 * e + j];
                 const int64_t q = std::lower_bound(cl.begin() + rp[r], cl.begin() + rp[r + 1], c) - cl.begin();
                 con[q].push_back({(int32_t)e, (uint8_t)(4 * i + j)});
@@ -626,6 +693,7 @@ extern "C" hm_status hm_flow_create(int64_t N, const int32_t* conn, int64_t n_no
     F->nloc.upload(nloc, st);
     F->a.upload(std::vector<double>(a, a + N), st);
     F->b.upload(std::vector<double>(b, b + N), st);
+    F->emat.upload(emat, st);
     F->a22.alloc(nnz);
     F->a21.alloc(4 * N);
     F->ecoef.alloc(2 * N);

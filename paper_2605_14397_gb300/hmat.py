@@ -179,6 +179,7 @@ SIGNATURES = [
     ("hm_hmat_get_tile_shape", _I, [_VP, ctypes.POINTER(hm_tile_shape)]),
     ("hm_tune_tile_shape", _I, [_VP, _VP, _I, _I, ctypes.c_char_p, ctypes.c_size_t, _VP]),
     ("hm_flow_create", _I, [_I64, _VP, _I64, _VP, _VP, ctypes.POINTER(_VP)]),
+    ("hm_flow_create_mesh", _I, [_I64, _VP, _VP, _I64, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
     ("hm_flow_destroy", None, [_VP]),
     ("hm_flow_assemble", _I, [_VP, ctypes.POINTER(hm_flow_params), _VP, _VP, _VP, _VP]),
     ("hm_flow_export", _I, [_VP, _P64, _VP, _VP, _VP, _VP, _VP]),
@@ -778,16 +779,24 @@ _PRECONDS = {"none": HM_PRECOND_NONE, "blockj": HM_PRECOND_BLOCKJ, "jacobi3": HM
 
 class Flow:
     """Fracture flow mesh and matrices (hm_flow_*): conn (N, 4) int32 node indices,
-    n_nodes, half sides a, b (N,)."""
+    n_nodes, half sides a, b (N,); for meshes with triangles (linear pressure) also
+    shape (N,) and the triangles' vertices tri (N, 9) (hm_flow_create_mesh)."""
 
-    def __init__(self, conn, n_nodes, a, b):
+    def __init__(self, conn, n_nodes, a, b, shape=None, tri=None):
         conn = np.ascontiguousarray(conn, dtype=np.int32)
         a = np.ascontiguousarray(a, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         self.N, self.n_nodes = conn.shape[0], int(n_nodes)
         h = ctypes.c_void_p()
-        _check(lib().hm_flow_create(self.N, conn.ctypes.data_as(_VP), self.n_nodes, a.ctypes.data_as(_VP),
-                                    b.ctypes.data_as(_VP), ctypes.byref(h)))
+        if shape is not None and np.any(np.asarray(shape) != 0):
+            sh = np.ascontiguousarray(shape, dtype=np.int32)
+            tv = np.ascontiguousarray(tri, dtype=np.float64)
+            _check(lib().hm_flow_create_mesh(self.N, sh.ctypes.data_as(_VP), conn.ctypes.data_as(_VP), self.n_nodes,
+                                             a.ctypes.data_as(_VP), b.ctypes.data_as(_VP), tv.ctypes.data_as(_VP),
+                                             ctypes.byref(h)))
+        else:
+            _check(lib().hm_flow_create(self.N, conn.ctypes.data_as(_VP), self.n_nodes, a.ctypes.data_as(_VP),
+                                        b.ctypes.data_as(_VP), ctypes.byref(h)))
         self.handle = h
 
     def __del__(self):

@@ -256,3 +256,26 @@ def test_flow_create_argument_checks(L):
     assert L.hm_flow_create(2, vp(conn), 6, vp(a), vp(-b), ctypes.byref(h)) == hmat.HM_EINVAL
     assert L.hm_flow_create(0, vp(conn), 6, vp(a), vp(b), ctypes.byref(h)) == hmat.HM_EINVAL
     assert L.hm_flow_create(2, None, 6, vp(a), vp(b), ctypes.byref(h)) == hmat.HM_EINVAL
+    # a rectangle and a triangle sharing two nodes (hm_flow_create_mesh)
+    shape = np.array([0, 1], dtype=np.int32)
+    cm = np.array([[0, 1, 2, 3], [1, 4, 2, -1]], dtype=np.int32)
+    tri = np.zeros((2, 9))
+    tri[1] = [1.0, 0.0, 0.0, 2.0, 0.5, 0.0, 1.0, 1.0, 0.0]
+
+    def mesh(shape_, conn_, tri_):
+        return L.hm_flow_create_mesh(2, vp(shape_), vp(conn_), 5, vp(a), vp(b),
+                                     vp(tri_) if tri_ is not None else None, ctypes.byref(h))
+    bad = cm.copy()
+    bad[1, 3] = 0
+    assert mesh(shape, bad, tri) == hmat.HM_EINVAL and "fourth" in hmat.last_error()
+    flat = tri.copy()
+    flat[1, 6:9] = [1.5, 0.25, 0.0]  # collinear with the first two vertices
+    assert mesh(shape, cm, flat) == hmat.HM_EINVAL and "degenerate" in hmat.last_error()
+    nan = tri.copy()
+    nan[1, 4] = np.nan
+    assert mesh(shape, cm, nan) == hmat.HM_ENAN
+    assert mesh(shape, cm, None) == hmat.HM_EINVAL
+    assert mesh(np.array([0, 7], dtype=np.int32), cm, tri) == hmat.HM_EINVAL
+    bad = cm.copy()
+    bad[1, 2] = 1
+    assert mesh(shape, bad, tri) == hmat.HM_EINVAL and "repeats" in hmat.last_error()

@@ -12,6 +12,9 @@ through the C-ABI.
   and matches the dense LU solution of the oracle's Jacobian, with diag(k) and with a
   block-diagonal C^ep; on three intersecting planes the shared nodes couple the planes'
   pressures.
+* The same on a triangulated penny (the paper's linear triangles for the pressure and
+  constant-DD triangles for the mechanics) and on a mesh of triangles and rectangles
+  sharing nodes.
 """
 import math
 
@@ -39,15 +42,33 @@ def dev():
     return torch.device("cuda:0")
 
 
-@pytest.fixture(scope="module", params=["planes10", "penny16"])
+def mixed_mesh():
+    """A rectangular grid whose left half is split into triangles on the same vertices."""
+    el = synth.plane_grid(10, 6, -0.5, 0.5, -0.3, 0.3, (0, 0, 1))
+    parts, tris = [], []
+    for e in range(el.N):
+        c, a, b, s1, s2 = el.c[e], el.a[e], el.b[e], el.s1[e], el.s2[e]
+        P = [c - a * s1 - b * s2, c + a * s1 - b * s2, c + a * s1 + b * s2, c - a * s1 + b * s2]
+        if c[0] < 0:
+            tris += [(P[0], P[1], P[2]), (P[0], P[2], P[3])]
+        else:
+            parts.append(el.subset([e]))
+    return synth.Elements.concat([synth.triangles(np.array(tris), (0, 0, 1))] + parts)
+
+
+MESHES = {"planes10": (lambda: synth.config_three_planes(10), 0.2), "penny16": (lambda: synth.config_penny(16), 0.125),
+          "tripenny12": (lambda: synth.tri_disk_mesh(12), 2.0 / 12), "mixed": (mixed_mesh, 0.1)}
+
+
+@pytest.fixture(scope="module", params=list(MESHES))
 def case(request, dev):
     import torch
-    el = synth.config_three_planes(10) if request.param == "planes10" else synth.config_penny(16)
-    h = 2.0 / (10 if request.param == "planes10" else 16)
+    mk, h = MESHES[request.param]
+    el = mk()
     conn, nn = synth.node_connectivity(el)
     T = hmat.ClusterTree(el, 32, 2.0)
     H = hmat.HMatrix(T, el, E, NU, 1e-8, "both")
-    fl = hmat.Flow(conn, nn, el.a, el.b)
+    fl = hmat.Flow(conn, nn, el.a, el.b, el.shape, el.tri)
     rng = np.random.default_rng(71)
     dn = rng.uniform(0.0, 0.05, el.N)
     dp = rng.normal(size=nn) * 0.1
@@ -55,7 +76,8 @@ def case(request, dev):
     fl.assemble(PAR, torch.as_tensor(dn, device=dev), torch.as_tensor(dp, device=dev),
                 torch.as_tensor(pn, device=dev))
     k = np.exp(rng.uniform(math.log(1e-2), math.log(1e1), size=el.N)) * (E / h)
-    A12, A21, A22 = F.jacobian_blocks(conn, nn, el.a, el.b, dn, dp, pn, PAR["M"], PAR["mu"], PAR["w0"], PAR["dt"])
+    A12, A21, A22 = F.jacobian_blocks(conn, nn, el.a, el.b, dn, dp, pn, PAR["M"], PAR["mu"], PAR["w0"], PAR["dt"],
+                                      shape=el.shape, tri=el.tri)
     Em = O.dense_matrix(el, E, NU)
     return dict(el=el, conn=conn, nn=nn, H=H, fl=fl, dn=dn, dp=dp, pn=pn, k=k, h=h, Em=Em, A12=A12, A21=A21,
                 A22=A22)
@@ -74,7 +96,10 @@ def test_flow_matrices_match_the_oracle(dev, case):
     assert np.abs(dense - A22).max() <= 1e-12 * np.abs(A22).max()
     A21 = case["A21"]
     conn = case["conn"]
-    ref = np.stack([A21[conn[e], 3 * e + 2] for e in range(case["el"].N)])
+    ref = np.zeros((case["el"].N, 4))
+    for e in range(case["el"].N):
+        nv = 3 if conn[e, 3] < 0 else 4
+        ref[e, :nv] = A21[conn[e, :nv], 3 * e + 2]
     # a node shared twice by one element does not occur: the columns are the element's own
     assert np.abs(ex["a21"] - ref).max() <= 1e-12 * np.abs(ref).max()
     case["fl"].assemble(PAR, torch.as_tensor(case["dn"], device=dev), torch.as_tensor(case["dp"], device=dev),

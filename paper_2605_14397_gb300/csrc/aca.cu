@@ -392,6 +392,61 @@ __device__ void cgs2_qr(double* A, int m, int r, double* Rm, double* cbuf, doubl
     }
 }
 
+// One-sided Jacobi on the columns of the r x r matrix M (column-major), the rotations
+// accumulated in Z: round-robin pairs, a warp per pair; stops after a sweep without a
+// rotation (|g| <= thresh sqrt(a b) for every pair) or after max_sweeps.
+template <typename T>
+__device__ __forceinline__ void jacobi_sweeps(T* M, T* Z, int r, double thresh, int max_sweeps, int* s_rot) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int n = (r + 1) & ~1;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) *s_rot = 0;
+        __syncthreads();
+        for (int t = 0; t < n - 1; ++t) {
+            for (int k = w; k < n / 2; k += ACA_NW) {
+                int p = (t + k) % (n - 1);
+                int q = k == 0 ? n - 1 : (t - k + n - 1) % (n - 1);
+                if (p >= r || q >= r) continue;
+                if (p > q) { const int tt = p; p = q; q = tt; }
+                T* mp = M + (size_t)p * r;
+                T* mq = M + (size_t)q * r;
+                T a = 0, b = 0, g = 0;
+                for (int i = lane; i < r; i += 32) {
+                    a += mp[i] * mp[i];
+                    b += mq[i] * mq[i];
+                    g += mp[i] * mq[i];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                if (g != T(0) && fabs((double)g) > thresh * sqrt((double)a * (double)b)) {
+                    const T zeta = (b - a) / (T(2) * g);
+                    const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                    const T c = T(1) / sqrt(T(1) + tt * tt), sn = c * tt;
+                    T* zp = Z + (size_t)p * r;
+                    T* zq = Z + (size_t)q * r;
+                    for (int i = lane; i < r; i += 32) {
+                        const T x = mp[i], y = mq[i];
+                        mp[i] = c * x - sn * y;
+                        mq[i] = sn * x + c * y;
+                        const T u = zp[i], v = zq[i];
+                        zp[i] = c * u - sn * v;
+                        zq[i] = sn * u + c * v;
+                    }
+                    if (lane == 0) *s_rot = 1;
+                }
+            }
+            __syncthreads();
+        }
+        const int rot = *s_rot;
+        __syncthreads();
+        if (!rot) break;
+    }
+}
+
 __global__ void __launch_bounds__(ACA_NT) k_recompress(const RecJob* __restrict__ jobs, double* __restrict__ ws,
                                                        double* __restrict__ small, double tau,
                                                        int32_t* __restrict__ rank_out) {
@@ -427,51 +482,39 @@ __global__ void __launch_bounds__(ACA_NT) k_recompress(const RecJob* __restrict_
         Z[q] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    // one-sided Jacobi on the columns of M
-    const int n = (r + 1) & ~1;
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        for (int t = 0; t < n - 1; ++t) {
-            for (int k = w; k < n / 2; k += ACA_NW) {
-                int p = (t + k) % (n - 1);
-                int q = k == 0 ? n - 1 : (t - k + n - 1) % (n - 1);
-                if (p >= r || q >= r) continue;
-                if (p > q) { const int tt = p; p = q; q = tt; }
-                double* mp = M + (size_t)p * r;
-                double* mq = M + (size_t)q * r;
-                double a = 0.0, b = 0.0, g = 0.0;
-                for (int i = lane; i < r; i += 32) {
-                    a += mp[i] * mp[i];
-                    b += mq[i] * mq[i];
-                    g += mp[i] * mq[i];
-                }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                g = warp_sum(g);
-                if (g != 0.0 && fabs(g) > 1e-15 * sqrt(a * b)) {
-                    const double zeta = (b - a) / (2.0 * g);
-                    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-                    double* zp = Z + (size_t)p * r;
-                    double* zq = Z + (size_t)q * r;
-                    for (int i = lane; i < r; i += 32) {
-                        const double x = mp[i], y = mq[i];
-                        mp[i] = c * x - s * y;
-                        mq[i] = s * x + c * y;
-                        const double u = zp[i], v = zq[i];
-                        zp[i] = c * u - s * v;
-                        zq[i] = s * u + c * v;
-                    }
-                    if (lane == 0) s_rot = 1;
-                }
-            }
-            __syncthreads();
-        }
-        const int rot = s_rot;
-        __syncthreads();
-        if (!rot) break;
+    // one-sided Jacobi on the columns of M: sweeps on an FP32 copy to FP32 convergence,
+    // then the accumulated rotations made orthonormal in FP64 (CGS2), M <- M Z in FP64
+    // and FP64 sweeps to the end (one or two: the columns are nearly orthogonal already).
+    // Z stays orthogonal and M = M_0 Z to FP64 rounding whatever the FP32 phase did; it
+    // only spares most of the FP64 sweeps (the FP64 pipe bounds this kernel on GB300).
+    float* Mf = reinterpret_cast<float*>(ord + r);
+    float* Zf = Mf + (size_t)r * r;
+    double f2 = 0.0;
+    for (int q = tid; q < r * r; q += ACA_NT) f2 += M[q] * M[q];
+    const double fn = sqrt(block_sum(f2, sv));  // rotations do not see the scale: M / ||M||_F in FP32
+    for (int q = tid; q < r * r; q += ACA_NT) {
+        Mf[q] = fn > 0.0 ? (float)(M[q] / fn) : 0.f;
+        Zf[q] = (q % r == q / r) ? 1.f : 0.f;
     }
+    __syncthreads();
+    jacobi_sweeps<float>(Mf, Zf, r, 1e-5, 15, &s_rot);
+    int bad = 0;
+    for (int q = tid; q < r * r; q += ACA_NT) bad |= !isfinite(Zf[q]);
+    bad = __syncthreads_or(bad);
+    for (int q = tid; q < r * r; q += ACA_NT) Z[q] = bad ? ((q % r == q / r) ? 1.0 : 0.0) : (double)Zf[q];
+    __syncthreads();
+    cgs2_qr(Z, r, r, RU, cbuf, sv);  // RU is free once M is formed
+    // RV <- M Z, then back into M
+    for (int q = tid; q < r * r; q += ACA_NT) {
+        const int i = q % r, j = q / r;
+        double acc = 0.0;
+        for (int l = 0; l < r; ++l) acc += M[(size_t)l * r + i] * Z[(size_t)j * r + l];
+        RV[q] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < r * r; q += ACA_NT) M[q] = RV[q];
+    __syncthreads();
+    jacobi_sweeps<double>(M, Z, r, 1e-15, 30, &s_rot);
     // singular values, order by decreasing value, truncation rank
     for (int j = w; j < r; j += ACA_NW) {
         double a = 0.0;
@@ -503,30 +546,23 @@ __global__ void __launch_bounds__(ACA_NT) k_recompress(const RecJob* __restrict_
     }
 }
 
+// U <- Q_U (M columns in singular-value order)_k, V <- Q_V Z_k, rows of one item
 __global__ void k_expand(const ExpandJob* __restrict__ jobs, const double* __restrict__ ws,
                          const double* __restrict__ small, float* __restrict__ store) {
     const ExpandJob J = jobs[blockIdx.x];
     const int r = J.r, k = J.k;
-    const double* Q = ws + J.ws_off;
-    const double* QV = Q + (size_t)J.mS * (J.R + 3);
+    const int m = J.side ? J.mT : J.mS;
+    const double* Q = ws + J.ws_off + (J.side ? (size_t)J.mS * (J.R + 3) : 0);
     const double* M = small + J.sm_off + 2 * (size_t)r * r;
-    const double* Z = M + (size_t)r * r;
-    const double* ord = Z + (size_t)r * r;
-    float* dU = store + J.dst;
-    float* dV = dU + (size_t)J.mS * k;
-    for (int64_t q = threadIdx.x; q < (int64_t)J.mS * k; q += blockDim.x) {
-        const int row = (int)(q % J.mS), j = (int)(q / J.mS);
+    const double* C = J.side ? M + (size_t)r * r : M;  // Z for V, M for U
+    const double* ord = M + 2 * (size_t)r * r;
+    float* d = store + J.dst + (J.side ? (size_t)J.mS * k : 0);
+    for (int64_t q = threadIdx.x; q < (int64_t)J.rows * k; q += blockDim.x) {
+        const int row = J.row0 + (int)(q % J.rows), j = (int)(q / J.rows);
         const int o = (int)ord[j];
         double s = 0.0;
-        for (int i = 0; i < r; ++i) s += Q[(size_t)i * J.mS + row] * M[(size_t)o * r + i];
-        dU[q] = (float)s;
-    }
-    for (int64_t q = threadIdx.x; q < (int64_t)J.mT * k; q += blockDim.x) {
-        const int row = (int)(q % J.mT), j = (int)(q / J.mT);
-        const int o = (int)ord[j];
-        double s = 0.0;
-        for (int i = 0; i < r; ++i) s += QV[(size_t)i * J.mT + row] * Z[(size_t)o * r + i];
-        dV[q] = (float)s;
+        for (int i = 0; i < r; ++i) s += Q[(size_t)i * m + row] * C[(size_t)o * r + i];
+        d[(size_t)j * m + row] = (float)s;
     }
 }
 

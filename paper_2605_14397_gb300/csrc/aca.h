@@ -15,14 +15,16 @@ struct AcaJob {
 
 struct RecJob {
     int64_t ws_off;  // ACA workspace of the block (U then V)
-    int64_t sm_off;  // small workspace: R_U, R_V, M, Z (r x r each) then the order (r)
+    int64_t sm_off;  // small workspace: R_U, R_V, M, Z (r x r each), the order (r), FP32 M and Z
     int32_t mS, mT, r, R;
 };
 
+// One item of the expansion: rows [row0, row0 + rows) of one factor (side 0: U, 1: V)
+// of one block, so that the largest blocks are spread over many CTAs.
 struct ExpandJob {
     int64_t ws_off, sm_off;
-    int64_t dst;  // compact store offset: U (mS x k) then V (mT x k), FP32 column-major
-    int32_t mS, mT, r, k, R, pad_;
+    int64_t dst;  // compact store offset of the block: U (mS x k) then V (mT x k), FP32 column-major
+    int32_t mS, mT, r, k, R, side, row0, rows;
 };
 
 // ACA of every job (one CTA each) to relative accuracy eps; rank_out / status_out per

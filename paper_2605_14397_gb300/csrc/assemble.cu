@@ -271,7 +271,7 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
             J.R = R;
             rj.push_back(J);
             rj_block.push_back(b);
-            slen += 4LL * J.r * J.r + J.r;
+            slen += 5LL * J.r * J.r + J.r;  // R_U, R_V, M, Z, order, FP32 copies of M and Z
         }
         std::vector<int32_t> krank(rj.size(), 0);
         if (!rj.empty()) {
@@ -304,8 +304,16 @@ void assemble(const Tree& T, const hm_assemble_opts& opt, cudaStream_t st, HMat&
             e.r = J.r;
             e.k = k;
             e.R = R;
-            e.pad_ = 0;
-            ej.push_back(e);
+            constexpr int EXPAND_ROWS = 512;  // rows per item: a large block spreads over many CTAs
+            for (int side = 0; side < 2; ++side) {
+                const int m = side ? J.mT : J.mS;
+                for (int r0 = 0; r0 < m; r0 += EXPAND_ROWS) {
+                    e.side = side;
+                    e.row0 = r0;
+                    e.rows = std::min(EXPAND_ROWS, m - r0);
+                    ej.push_back(e);
+                }
+            }
             fac_off[b] = store_len + clen;
             clen += (int64_t)k * (J.mS + J.mT);
         }

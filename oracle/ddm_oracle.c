@@ -1,6 +1,6 @@
 /*
  * CPU FP64 oracle for the constant-displacement-discontinuity (DD) influence
- * coefficients of rectangular elements in a 3D full space.
+ * coefficients of rectangular and triangular elements in a 3D full space.
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the CPU-baseline leg
  * of the benchmark may load this library.  It shares no code with the CUDA path.
@@ -23,8 +23,11 @@
  *     u_{k,j} = -1/(8 pi (1-v)) [ 2(1-v) d_km phi_{3j} - (1-2v)(d_m3 phi_{kj}
  *               - d_k3 phi_{mj}) - d_j3 phi_{mk} - x3 phi_{mkj} ].
  *   Stress follows from Hooke's law, traction from the receiver normal.
- *   phi's second and third derivatives are corner sums of elementary antiderivatives
- *   (no logarithm or arctangent is needed at this order).
+ *   phi's second and third derivatives are integrals over the element's edges (Stokes'
+ *   theorem, below), each edge integrated numerically by adaptive Gauss-Legendre
+ *   quadrature: the oracle shares no closed-form antiderivative with the device kernel,
+ *   whose rectangle derivatives are corner sums and whose triangle ones are closed-form
+ *   edge sums.
  * parity pinned by: the coplanar closed forms and self terms, brute-force quadrature
  * of the point source, far-field asymptotics, Sneddon's penny crack (tests).
  */
@@ -34,79 +37,6 @@
 
 #define ORC_OK 0
 #define ORC_SINGULAR (-4)
-
-/* d2[i][j] = phi_ij, d3[i][j][k] = phi_ijk at the source-local point (x1,x2,x3) for the
- * rectangle |xi| <= a, |eta| <= b.  Returns ORC_SINGULAR when the point lies on the
- * rectangle's boundary (in-plane, within tol). */
-static int phi_derivatives(const double x[3], double a, double b, double tol,
-                           double d2[3][3], double d3[3][3][3])
-{
-    /* phi is even in each coordinate: evaluate at |x| and restore the signs below. */
-    double sg[3], y[3];
-    for (int i = 0; i < 3; ++i) {
-        sg[i] = x[i] < 0.0 ? -1.0 : 1.0;
-        y[i] = fabs(x[i]);
-    }
-    if (y[2] <= tol) {
-        int on_edge_1 = fabs(y[0] - a) <= tol && y[1] <= b + tol;
-        int on_edge_2 = fabs(y[1] - b) <= tol && y[0] <= a + tol;
-        if (on_edge_1 || on_edge_2) return ORC_SINGULAR;
-    }
-    double z = y[2];
-    double s11 = 0, s22 = 0, s12 = 0, s13 = 0, s23 = 0;
-    double t111 = 0, t112 = 0, t122 = 0, t222 = 0, t113 = 0, t123 = 0, t223 = 0;
-    for (int cu = 0; cu < 2; ++cu) {
-        for (int cv = 0; cv < 2; ++cv) {
-            double su = cu == 0 ? 1.0 : -1.0;
-            double sv = cv == 0 ? 1.0 : -1.0;
-            double s = su * sv;              /* corner sign of the double integral */
-            double u = y[0] + su * a;        /* u = x1 - xi at xi = -su a */
-            double v = y[1] + sv * b;
-            double R = sqrt(u * u + v * v + z * z);
-            double p = 1.0 / R;
-            /* Av = 1/(v+R), Au = 1/(u+R), rationalised when the sum cancels */
-            double Av = v >= 0.0 ? 1.0 / (v + R) : (R - v) / (u * u + z * z);
-            double Au = u >= 0.0 ? 1.0 / (u + R) : (R - u) / (v * v + z * z);
-            /* phi_1 = sum s ln(v+R), phi_2 = sum s ln(u+R); differentiate those */
-            s11 += s * u * p * Av;
-            s22 += s * v * p * Au;
-            s12 += s * p;
-            s13 += s * z * p * Av;
-            s23 += s * z * p * Au;
-            t111 += s * (p * Av - u * u * p * p * Av * (p + Av));
-            t222 += s * (p * Au - v * v * p * p * Au * (p + Au));
-            t112 += s * (-u * p * p * p);
-            t122 += s * (-v * p * p * p);
-            t123 += s * (-z * p * p * p);
-            t113 += s * (-u * z * p * p * Av * (p + Av));
-            t223 += s * (-v * z * p * p * Au * (p + Au));
-        }
-    }
-    /* phi is harmonic off the element: the x3-x3 derivatives follow */
-    double s33 = -s11 - s22;
-    double t133 = -t111 - t122;
-    double t233 = -t112 - t222;
-    double t333 = -t113 - t223;
-
-    double D2[3][3] = {{s11, s12, s13}, {s12, s22, s23}, {s13, s23, s33}};
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            d2[i][j] = D2[i][j] * sg[i] * sg[j];
-    /* fill the symmetric third-derivative tensor from its 10 distinct entries */
-    double T[3][3][3];
-    int idx[10][3] = {{0,0,0},{0,0,1},{0,1,1},{1,1,1},{0,0,2},{0,1,2},{1,1,2},{0,2,2},{1,2,2},{2,2,2}};
-    double val[10] = {t111, t112, t122, t222, t113, t123, t223, t133, t233, t333};
-    for (int q = 0; q < 10; ++q) {
-        int i = idx[q][0], j = idx[q][1], k = idx[q][2];
-        double w = val[q];
-        T[i][j][k] = T[i][k][j] = T[j][i][k] = T[j][k][i] = T[k][i][j] = T[k][j][i] = w;
-    }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            for (int k = 0; k < 3; ++k)
-                d3[i][j][k] = T[i][j][k] * sg[i] * sg[j] * sg[k];
-    return ORC_OK;
-}
 
 /* ---------------------------------------------------------------- triangles
  * The paper's element (Sec. 3.1) is a triangle.  phi = int int_T 1/R over the triangle;
@@ -193,21 +123,27 @@ static void edge_adapt(const double x[3], const double A[2], const double tau[2]
     edge_adapt(x, A, tau, m, s1, r, scale, depth + 1, acc);
 }
 
-/* d2, d3 of phi at the point x (coordinates in the triangle's plane frame, triangle in
- * x3 = 0 with vertices (tv[0], tv[1]), (tv[2], tv[3]), (tv[4], tv[5])).  Returns
- * ORC_SINGULAR when the point lies on the triangle's boundary (in-plane, within tol). */
-static int tri_phi_derivatives(const double x[3], const double tv[6], double tol, double d2[3][3],
-                               double d3[3][3][3])
+/* d2, d3 of phi at the point x (coordinates in the element's plane frame, element in
+ * x3 = 0: the convex polygon with the nv vertices (pv[0], pv[1]), (pv[2], pv[3]), ... in
+ * either orientation).  Returns ORC_SINGULAR when the point lies on the polygon's
+ * boundary (in-plane, within tol). */
+static int poly_phi_derivatives(const double x[3], const double* pv, int nv, double tol, double d2[3][3],
+                                double d3[3][3][3])
 {
     gl_init();
-    int ord[3] = {0, 1, 2};
-    double area2 = (tv[2] - tv[0]) * (tv[5] - tv[1]) - (tv[3] - tv[1]) * (tv[4] - tv[0]);
-    if (area2 < 0.0) { ord[1] = 2; ord[2] = 1; }  /* traverse counter-clockwise */
+    double area2 = 0.0;  /* shoelace */
+    for (int k = 0; k < nv; ++k) {
+        const double* P = pv + 2 * k;
+        const double* Q = pv + 2 * ((k + 1) % nv);
+        area2 += P[0] * Q[1] - Q[0] * P[1];
+    }
+    const int rev = area2 < 0.0;  /* traverse counter-clockwise */
     double s[3][3] = {{0}}, t[2][EDGE_NF] = {{0}};
     /* s[alpha][beta] for alpha in-plane; t[alpha][c] the sums of n_alpha * integrand c */
-    for (int e = 0; e < 3; ++e) {
-        const double* P = tv + 2 * ord[e];
-        const double* Q = tv + 2 * ord[(e + 1) % 3];
+    for (int e = 0; e < nv; ++e) {
+        const int ia = rev ? (nv - e) % nv : e, ib = rev ? (nv - e - 1 + nv) % nv : (e + 1) % nv;
+        const double* P = pv + 2 * ia;
+        const double* Q = pv + 2 * ib;
         double L = hypot(Q[0] - P[0], Q[1] - P[1]);
         double tau[2] = {(Q[0] - P[0]) / L, (Q[1] - P[1]) / L};
         double nrm[2] = {tau[1], -tau[0]};
@@ -246,6 +182,20 @@ static int tri_phi_derivatives(const double x[3], const double tv[6], double tol
         d3[i][j][k] = d3[i][k][j] = d3[j][i][k] = d3[j][k][i] = d3[k][i][j] = d3[k][j][i] = v;
     }
     return ORC_OK;
+}
+
+/* The rectangle |x1| <= a, |x2| <= b and the triangle tv as polygons. */
+static int phi_derivatives(const double x[3], double a, double b, double tol, double d2[3][3],
+                           double d3[3][3][3])
+{
+    const double pv[8] = {-a, -b, a, -b, a, b, -a, b};
+    return poly_phi_derivatives(x, pv, 4, tol, d2, d3);
+}
+
+static int tri_phi_derivatives(const double x[3], const double tv[6], double tol, double d2[3][3],
+                               double d3[3][3][3])
+{
+    return poly_phi_derivatives(x, tv, 3, tol, d2, d3);
 }
 
 /* Frames are given as three unit vectors s1, s2, n (global components). */

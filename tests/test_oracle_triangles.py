@@ -3,8 +3,8 @@ collocation at centroids), each against something other than the oracle's own ed
 quadrature:
 
 * a rectangle is two triangles: phi's second and third derivatives of the rectangle
-  (the oracle's pinned corner sums) equal the sum over its two triangles at points in
-  and off its plane, and so does the whole 3x3 influence block;
+  equal the sum over its two triangles at points in and off its plane (the shared
+  diagonal's integrals cancel), and so does the whole 3x3 influence block;
 * at a point inside a triangle, in its plane, the derivatives equal the finite parts
   written in polar coordinates about the point -- one-dimensional integrals over the
   angle of the distance to the boundary, an independent formula;

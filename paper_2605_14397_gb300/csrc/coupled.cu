@@ -424,8 +424,8 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
     HM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
     tangent_diag_user(H, kel, cep, shift, diag.p, st);
     k_normal_inv<<<gsz(F.N), NT, 0, st>>>(F.N, diag.p, dinv.p, bad.p);
-    k_flow_gather<<<gsz(F.nnz), NT, 0, st>>>(F.nnz, F.cptr.p, F.cel.p, F.cij.p, F.conn.p, F.emat.p, F.ecoef.p, F.a21.p,
-                                             dinv.p, sval.p);
+    k_flow_gather<<<gsz(F.nnz), NT, 0, st>>>(F.nnz, F.cptr.p, F.cel.p, F.cij.p, F.conn.p, F.emat.p, F.ecoef.p,
+                                             F.a21.p, dinv.p, sval.p);
     k_diag_of<<<gsz(n2), NT, 0, st>>>(n2, F.rowptr.p, F.col.p, sval.p, sdinv.p, bad.p);
     HM_LAUNCH_CHECK();
     {
@@ -614,7 +614,8 @@ extern "C" hm_status hm_flow_create_mesh(int64_t N, const int32_t* shape, const 
         if (sh == HM_SHAPE_TRI && conn[4 * e + 3] != -1)
             fail(HM_EINVAL, "flow_create: a triangle's fourth node slot must be -1");
         for (int i = 0; i < nv[e]; ++i)
-            if (conn[4 * e + i] < 0 || conn[4 * e + i] >= n_nodes) fail(HM_EINVAL, "flow_create: node index out of range");
+            if (conn[4 * e + i] < 0 || conn[4 * e + i] >= n_nodes)
+                fail(HM_EINVAL, "flow_create: node index out of range");
         for (int i = 0; i < nv[e]; ++i)
             for (int j = i + 1; j < nv[e]; ++j)
                 if (conn[4 * e + i] == conn[4 * e + j]) fail(HM_EINVAL, "flow_create: an element repeats a node");

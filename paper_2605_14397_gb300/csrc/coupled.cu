@@ -451,7 +451,8 @@ void coupled_solve(HMat& H, const hm_flow& F, const double* kel, const double* c
     // weighs both blocks; the solve runs on diag(I, sr I) J, its residual in that norm
     double sr = o.flow_scale;
     if (!(sr > 0.0))
-        sr = std::sqrt(D.dot(n1, diag.p, diag.p, st) / (double)n1) * std::sqrt(D.dot(n2, sdinv.p, sdinv.p, st) / (double)n2);
+        sr = std::sqrt(D.dot(n1, diag.p, diag.p, st) / (double)n1) *
+             std::sqrt(D.dot(n2, sdinv.p, sdinv.p, st) / (double)n2);
     if (!(sr > 0.0) || !std::isfinite(sr)) sr = 1.0;
     HM_CUDA(cudaMemcpyAsync(bs.p, bv, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     axpby(n2, 0.0, bs.p + n1, sr, bs.p + n1, st);

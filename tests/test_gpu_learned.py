@@ -289,3 +289,30 @@ def test_trained_near_correction_takes_fewer_iterations(dev, system):
           "untrained %.2f (gamma %.1f)" % (it_bj, it_l, g_l, it_u, g_u))
     assert it_l <= 0.75 * it_bj
     assert abs(it_l - it_u) <= 1.0
+
+
+@pytest.mark.parametrize("nr", [3, 5, 16])
+def test_near_correction_several_rhs_equal_one_by_one(dev, system, nr):
+    """The near product's RHS-count variants (4, 8 and 16 slots for 3, 5 and 16 RHS) give
+    every RHS the bits of its own single-RHS application (each RHS sums its products in
+    the same order), and a 3-RHS solve with the near correction matches the dense LU."""
+    import torch
+    el, T, H, perm, begin, end, h = system
+    k = torch.as_tensor(synth.k_loguniform(el.N, 1611, h=h), device=dev)
+    m = hmat.LearnedCorrection(random_theta(15), hidden=HID)
+    m.set_kind("near", 0.8)
+    R = torch.as_tensor(synth.rhs_normal(3 * el.N, 25, nrhs=nr), device=dev).contiguous()
+    Z = torch.empty_like(R)
+    H.precond_apply(R, Z, k, precond="learned", model=m)
+    for q in range(nr):
+        z1 = torch.empty_like(R[q])
+        H.precond_apply(R[q].contiguous(), z1, k, precond="learned", model=m)
+        assert torch.equal(Z[q], z1), q
+    if nr == 3:
+        X = torch.zeros_like(R)
+        infos = H.solve(R, X, k, precond="learned", model=m)
+        assert all(i["status"] == 0 and i["relres"] <= 1e-8 for i in infos)
+        A = O.tangent_dense(O.dense_matrix(el, E, NU), k.cpu().numpy())
+        for q in range(3):
+            xl = np.linalg.solve(A, R[q].cpu().numpy())
+            assert rel(X[q].cpu().numpy(), xl) <= 1e-6

@@ -9,7 +9,9 @@ the CPU FP64 oracle, through the C-ABI.
   matches the dense oracle product to eps + 1e-6, alone and mixed with rectangles, and
   on 300 sampled rows of a 40,000-triangle fault.
 * GMRES on the triangulated penny crack gives the dense LU solution and Sneddon's
-  opening to the oracle's discrete error.
+  opening to the oracle's discrete error; ILU + BiCGSTAB and point Jacobi + FGMRES on
+  its tangent give the LU solution; a batch of a triangle and a rectangle fault gives
+  each fault's dense product.
 """
 import numpy as np
 import pytest
@@ -161,3 +163,48 @@ def test_full_size_triangle_fault_sampled_rows(dev):
         e = rel(y.cpu().numpy().astype(np.float64)[dof], ref)
         assert e <= bar, (dt, e)
         print("40k triangles, %s vectors: sampled-row error %.2e" % (dt, e))
+
+
+@pytest.mark.parametrize("precond,method", [("ilu", "bicgstab"), ("jacobi3", "fgmres")])
+def test_triangle_tangent_solves_with_the_papers_preconditioners(dev, precond, method):
+    """The ILU of Sec. 3.3.1 with BiCGSTAB and the point Jacobi with FGMRES on the tangent
+    of a triangulated penny (k log-uniform): the dense LU solution of the oracle's
+    tangent."""
+    import torch
+    el = synth.tri_disk_mesh(14)
+    h = 2.0 / 14
+    T = hmat.ClusterTree(el, 32, 2.0)
+    H = hmat.HMatrix(T, el, E, NU, 1e-8, "both")
+    k = synth.k_loguniform(el.N, 1630, E=E, h=h)
+    A = O.tangent_dense(O.dense_matrix(el, E, NU), k)
+    b = synth.rhs_normal(3 * el.N, 1631)
+    x = torch.zeros(3 * el.N, dtype=torch.float64, device=dev)
+    info = H.solve(torch.as_tensor(b, device=dev), x, torch.as_tensor(k, device=dev), precond=precond,
+                   method=method, ilu_p=0.01)[0]
+    assert info["status"] == 0 and info["relres"] <= 1e-8
+    assert rel(x.cpu().numpy(), np.linalg.solve(A, b)) <= 1e-6
+
+
+def test_batch_of_a_triangle_and_a_rectangle_fault(dev):
+    """Independent faults of both shapes in one arena: each part of the batched product
+    equals the dense oracle product of its fault."""
+    import torch
+    els = [synth.tri_disk_mesh(20, seed=3), synth.config_penny(18)]
+    trees, parts = [], []
+    for el in els:
+        T = hmat.ClusterTree(el, 32, 2.0)
+        trees.append(T)
+        parts.append(hmat.HMatrix(T, el, E, NU, 1e-6, "f32"))
+    B = hmat.HMatrix.batch(parts)
+    n = [3 * el.N for el in els]
+    x = synth.rhs_normal(sum(n), 1632)
+    xt = torch.as_tensor(x, dtype=torch.float32, device=dev)
+    yt = torch.empty_like(xt)
+    B.matvec(xt, yt)
+    B.check()
+    y = yt.cpu().numpy().astype(np.float64)
+    off = 0
+    for el, nf in zip(els, n):
+        ref = O.dense_matrix(el, E, NU) @ x[off:off + nf]
+        assert rel(y[off:off + nf], ref) <= 1e-6 + 1e-6
+        off += nf

@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--batch-storage", default="bf16", choices=["f32", "bf16"],
                    help="factor storage of the 64-fault batch (BF16 factors, FP32 near field)")
     p.add_argument("--tune", action="store_true", help="also run the leaf-size autotuner on the workload")
+    p.add_argument("--record-dir", default=None,
+                   help="write the operator summary (entry counts, algorithmic bytes) of the fault as JSON here")
     return p.parse_args()
 
 
@@ -1041,10 +1043,9 @@ def main():
         line["autotune"] = hmat.autotune(el, E, nu, eps, "f32", leaves=(32, 48, 64, 96, 128), etas=(1.5, 2.0, 3.0),
                                          budget_ms=180000)
 
-    if rank == 0 and args.grid == 256 and args.storage == "f32":
-        out_dir = os.path.join(ROOT, "gpurun_out")
-        if os.path.isdir(out_dir):
-            record_operator(info, B, out_dir)
+    if rank == 0 and args.record_dir and args.grid == 256 and args.storage == "f32":
+        os.makedirs(args.record_dir, exist_ok=True)
+        record_operator(info, B, args.record_dir)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, rows, dt = oracle_rows_rate(el, E, nu)
         full = el.N / rate
